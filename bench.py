@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Leaf DtN build throughput on one GB300: boxes/s and algorithmic TFLOP/s.
+
+Workload: the 8 x 8 x 8 grid of leaf boxes of the unit cube (h = 1/8) at
+p = 16 (n = 2744 interior, m = 1176 face nodes per box), kappa = 40, b a
+seeded sum of 16 random Fourier modes clipped to [0.5, 1.5] (seed 20250304).
+One step = hps_leaf_build_dtn over all 512 boxes: operator assembly, FP32 LU
+with tcgen05 tensor-core update products, FP64 iterative refinement of
+S = -A_ii^{-1} A_ib, and the FP64 D_n product T = A_bb + A_bi S.  Inputs are
+resident in HBM; the working set (~90 GB) is far larger than L2, so no L2
+flush is needed between steps.
+
+Also reported: the plain FP64 GPU path on a 32-box sample of the same
+workload (speedup and max relative difference), the end-to-end rate through
+the C ABI with host buffers (b in, T out, copies inside the timed region),
+per-kernel-class CUDA-event timings with the roofline of the dominant class,
+and the FP64 CPU oracle's rate on a bounded sample of boxes.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+paper has; it has no code) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import hps_inputs as hi  # noqa: E402
+
+P, NBOX, KAPPA, GRID = 16, 512, 40.0, (8, 8, 8)
+WORKLOAD = ("8x8x8 leaf boxes of the unit cube, p=16 Chebyshev-Lobatto (n=2744, m=1176), kappa=40, "
+            "b = clip(1 + 0.5 * sum of 16 seeded Fourier modes |k|<=4, [0.5, 1.5]), seed 20250304")
+METRIC = "leaf DtN builds/s at p=16 (FP32 tcgen05 LU + FP64 refinement, rel err <= 1e-10 vs FP64)"
+
+# TF32 dense tensor peak derived from the measured BF16 peak and NVIDIA's
+# nominal TF32:BF16 ratio (1.1 : 2.25 PFLOP/s dense).
+TF32_OVER_BF16 = 1.1 / 2.25
+# FP64 issue peak: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop (1.26 TFLOP/s,
+# the part's nominal 1.25 TFLOP/s FP64).
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12
+FP32_CUDACORE_PEAK_TFLOPS = 152 * 2.070e9 * 128 * 2 / 1e12
+
+CLASS_BOUND = {
+    "update_tcgen05": "tensor", "update_cudacore": "alu", "residual_fp64": "alu", "dn_fp64": "alu",
+    "panel": "alu", "build": "hbm", "gather_pack": "hbm", "refine_update": "hbm",
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32ir", "fp64"), default="fp32ir")
+    ap.add_argument("--nbox", type=int, default=NBOX)
+    ap.add_argument("--fp64-sample", type=int, default=32)
+    ap.add_argument("--cpu-sample", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def box_lows():
+    lows, h = hi.box_grid_lo(GRID)
+    return lows, h
+
+
+def flops_per_box(p: int) -> float:
+    """The dense method's count: LU 2/3 n^3 + TRSM 2 n^2 m + structured D_n 2 q m^2."""
+    q = p - 2
+    n, m = q ** 3, 6 * q * q
+    return 2.0 / 3.0 * n ** 3 + 2.0 * n * n * m + 2.0 * q * m * m
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.out.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_rate(nbox_sample: int, threads: int | None = None):
+    """Boxes/s of the FP64 CPU oracle (as it stands) on the first boxes of the workload."""
+    import oracle
+    lows, h = box_lows()
+    field = hi.fourier_b_field()
+    sel = np.linspace(0, NBOX - 1, nbox_sample).astype(int)
+    bs = [field.b(oracle.node_coords(P, lows[i], h)) for i in sel]
+    t0 = time.perf_counter()
+    for b in bs:
+        _, _, info = oracle.leaf_dtn(P, h, KAPPA, b, want_S=False)
+        assert info == 0
+    dt = time.perf_counter() - t0
+    return nbox_sample / dt, dt, oracle.max_threads()
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step is one box of the workload (the
+    oracle's LU and solves use every core), W untimed, K timed."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    lows, h = box_lows()
+    field = hi.fourier_b_field()
+    for i in range(args.warmup):
+        oracle.leaf_dtn(P, h, KAPPA, field.b(oracle.node_coords(P, lows[i], h)), want_S=False)
+    times = []
+    for s in range(args.steps):
+        b = field.b(oracle.node_coords(P, lows[(7 * s + 3) % NBOX], h))
+        t0 = time.perf_counter()
+        _, _, info = oracle.leaf_dtn(P, h, KAPPA, b, want_S=False)
+        times.append(time.perf_counter() - t0)
+        assert info == 0
+    ms = 1e3 * sum(times) / len(times)
+    value = 1e3 / ms
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nbox_per_step": 1, "p": P, "kappa": KAPPA},
+        "tflops": value * flops_per_box(P) / 1e12,
+        "cpu_baseline": {"value": value, "unit": "boxes/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} boxes of the workload, one per step, FP64 oracle LU + solves "
+                                   f"with OpenMP over {cores} threads"},
+        "e2e": {"value": value, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2503_04033_gb300 as H
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allmax(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    nbox = args.nbox
+    lows, h = box_lows()
+    lows = lows[np.arange(nbox) % NBOX]
+    field = hi.fourier_b_field()
+    b_np = np.stack([field.b(H.hps_leaf_nodes(P, lo, h)) for lo in lows])
+    n, m = H.hps_leaf_sizes(P)
+    prec = H.HPS_FP32_IR if args.precision == "fp32ir" else H.HPS_FP64
+    kind = H.LeafKind(P, h, KAPPA)
+    ctx = H.hps_create(local, 0)
+    stream = torch.cuda.current_stream(dev)
+    b = torch.from_numpy(b_np).to(dev)
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
+    st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+
+    def step():
+        H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, prec, st, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    bad = int((st != 0).sum().item())
+
+    # ---- timed region (device-resident inputs), per-kernel events on the stream
+    H.hps_profile_enable(ctx, True)
+    H.hps_profile_reset(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    barrier()
+    ms = allmax(e0.elapsed_time(e1) / args.steps)
+    H.hps_profile_enable(ctx, False)
+    prof = {}
+    launches_total = 0
+    for cls, name in enumerate(H.KERNEL_CLASSES):
+        nl, kms, fl, by = H.hps_profile_get(ctx, cls)
+        if nl:
+            prof[name] = {"launches": nl // args.steps, "ms_per_step": kms / args.steps, "flops": fl / args.steps,
+                          "bytes": by / args.steps}
+            launches_total += nl
+    value = world * nbox / (ms / 1e3)
+    it, rel = H.hps_last_refinement(ctx, nbox)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == H.HPS_FP32_IR else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nbox_per_gpu": nbox, "p": P, "kappa": KAPPA,
+                   "precision": args.precision, "l2": "inputs larger than L2 (~90 GB working set), no flush",
+                   "step": "hps_leaf_build_dtn over all boxes (T out, S not stored)"},
+        "tflops": value * flops_per_box(P) / 1e12,
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "box_failures": bad,
+        "refinement": {"corrections_max": int(it.max()), "corrections_mean": float(it.mean()),
+                       "rel_correction_max": float(rel.max())},
+        "gpu_launches": launches_total // args.steps * args.steps,
+        "kernels": prof,
+        "clocks": clocks.summary(),
+    }
+
+    # ---- roofline of the dominant kernel class
+    peaks, src = measured_peaks()
+    if prof:
+        dom = max(prof, key=lambda k: prof[k]["ms_per_step"])
+        d = prof[dom]
+        sec = d["ms_per_step"] / 1e3
+        bound = CLASS_BOUND.get(dom, "hbm")
+        if bound == "tensor":
+            peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+            ach = d["flops"] / sec / 1e12
+            unit = "TFLOP/s"
+            note = f"TF32 dense peak = {src} sustained BF16 x 1.1/2.25; achieved counts 2MNK once (3 TF32 MMAs issued)"
+        elif bound == "alu":
+            fp64 = dom in ("residual_fp64", "dn_fp64") or prec == H.HPS_FP64
+            peak = FP64_PEAK_TFLOPS if fp64 else FP32_CUDACORE_PEAK_TFLOPS
+            ach = d["flops"] / sec / 1e12
+            unit = "TFLOP/s"
+            note = "FP64 issue peak 152 SM x 2.07 GHz x 4 flop/clk" if fp64 else "FP32 CUDA-core issue peak"
+        else:
+            peak = peaks["hbm_gbs"]
+            ach = d["bytes"] / sec / 1e9
+            unit = "GB/s"
+            note = f"{src} HBM copy bandwidth"
+        line["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                            "frac": ach / peak, "traffic": None, "peak_source": note,
+                            "launches_per_step": d["launches"]}
+
+    # ---- plain FP64 GPU path on a sample of the same boxes
+    if not args.no_fp64 and prec == H.HPS_FP32_IR and args.fp64_sample > 0:
+        k = min(args.fp64_sample, nbox)
+        sel = torch.from_numpy(np.linspace(0, nbox - 1, k).astype(np.int64)).to(dev)
+        b64 = b.index_select(0, sel).contiguous()
+        T64 = torch.empty(k, m, m, dtype=torch.float64, device=dev)
+        st64 = torch.zeros(k, dtype=torch.int32, device=dev)
+        H.hps_leaf_build_dtn(ctx, kind, 2, b64, T64, None, H.HPS_FP64, st64, stream)   # warm
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        H.hps_leaf_build_dtn(ctx, kind, k, b64, T64, None, H.HPS_FP64, st64, stream)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64_rate = k / (f0.elapsed_time(f1) / 1e3)
+        Ts = T.index_select(0, sel)
+        relerr = ((Ts - T64).flatten(1).norm(dim=1) / T64.flatten(1).norm(dim=1)).max().item()
+        line["fp64_path"] = {"value": fp64_rate, "unit": "boxes/s", "sample_boxes": k,
+                             "tflops": fp64_rate * flops_per_box(P) / 1e12,
+                             "failures": int((st64 != 0).sum().item())}
+        line["speedup_vs_fp64_path"] = value / world / fp64_rate
+        line["rel_err_vs_fp64_path"] = relerr
+        del T64, b64
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        b_host = torch.from_numpy(b_np).pin_memory()
+        T_host = torch.empty(nbox, m, m, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            b.copy_(b_host, non_blocking=True)
+            H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, prec, st, stream)
+            T_host.copy_(T, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        g0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = allmax(g0.elapsed_time(g1) / args.steps)
+        line["e2e"] = {"value": world * nbox / (e2e_ms / 1e3), "unit": "boxes/s",
+                       "h2d_bytes_per_step": b_host.numel() * 8, "d2h_bytes_per_step": T_host.numel() * 8,
+                       "ms_per_step": e2e_ms}
+        del T_host, b_host
+
+    # ---- the oracle on this host's cores (rank 0 at N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu and args.cpu_sample > 0:
+        rate, dt, cores = oracle_rate(args.cpu_sample)
+        line["cpu_baseline"] = {"value": rate, "unit": "boxes/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_sample} boxes spread over the workload, FP64 oracle "
+                                          f"(LU, solves, A_bb + A_bi S) with OpenMP over {cores} threads, "
+                                          f"{dt:.1f} s"}
+    H.hps_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

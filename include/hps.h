@@ -1,0 +1,191 @@
+/*
+ * hps.h -- C ABI of the GB300 (sm_103a) library for the batched leaf-box
+ * reduction of the two-level HPS solver (Kump, Yesypenko, Martinsson,
+ * "A Two-Level Direct Solver for the Hierarchical Poincare-Steklov Method",
+ * arXiv:2503.04033).
+ *
+ * The PDE (Eq. 1, Eq. 2):  -Lap u - kappa^2 b(x) u = f in the box, u = g on
+ * its boundary.  Each leaf box carries a p x p x p tensor grid of
+ * Chebyshev-Lobatto nodes (Sec. 2.1).  Edge and corner nodes are dropped
+ * (Remark 1), which leaves
+ *     n = (p-2)^3 interior nodes and m = 6 (p-2)^2 face nodes per box.
+ * The library computes, for every box in a batch, the blocks of the paper's
+ * static condensation (Sec. 2.2, Eq. 5 to Eq. 8):
+ *     S = -A_ii^{-1} A_ib        solution operator   (n x m)
+ *     T = A_bb + A_bi S          DtN map             (m x m)
+ *     v = A_ii^{-1} f_i,  h = A_bi v                 particular solution, flux
+ *     u_i = v + S u_b                                interior reconstruction
+ *
+ * Layouts (all row-major, boxes outermost, double precision, device memory
+ * unless stated):
+ *   grid node (i,j,k), 0 <= i,j,k < p            index i + p j + p^2 k
+ *   interior node (i,j,k), 1 <= i,j,k <= p-2      index (i-1) + q (j-1) + q^2 (k-1), q = p-2
+ *   face f in the order x-, x+, y-, y+, z-, z+   face node (a,b) (a the lower free axis,
+ *                                                 1 <= a,b <= q) has index f q^2 + (a-1) + q (b-1)
+ *   b  [nbox][p^3]    f  [nbox][nrhs][p^3]    S  [nbox][n][m]    T  [nbox][m][m]
+ *   v  [nbox][nrhs][n]   h  [nbox][nrhs][m]   u_b [nbox][nrhs][m]   u_i [nbox][nrhs][n]
+ * Face rows of T and h take the OUTWARD normal derivative of each box (the
+ * flux-continuity rows of Eq. 4 sum the two boxes' outward derivatives).
+ *
+ * Ownership: the caller owns every input and output buffer.  The context owns
+ * its workspace (device memory it allocates on first use, up to the limit given
+ * to hps_create) and small per-(p, h) operator tables.
+ *
+ * Asynchrony: the leaf calls enqueue work on `stream` (a cudaStream_t passed as
+ * void*, NULL = legacy default stream) and return once it is enqueued.  The
+ * return value covers argument, allocation and launch errors.  Per-box numerical
+ * outcome is written to box_status[nbox] (device int array, may be NULL) and is
+ * valid after the stream has been synchronised:
+ *   0              the box succeeded
+ *   HPS_ESINGULAR  an exactly zero pivot appeared in the LU of A_ii
+ *   HPS_ENOCONV    mixed precision: the FP64 refinement did not reach its tolerance
+ *   HPS_EINVAL     a non-finite value of b (or f, u_b) was seen in the box
+ * No C++ exception crosses this interface.  A context may be used by one host
+ * thread at a time; calls on the same context serialise on its workspace.
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hps_ctx hps_ctx;
+
+typedef enum {
+    HPS_OK = 0,
+    HPS_EINVAL = 1,      /* bad argument (size, pointer, non-finite parameter) */
+    HPS_ENOMEM = 2,      /* workspace limit too small for one box, or allocation failed */
+    HPS_ESINGULAR = 3,   /* per box: zero pivot in the LU of A_ii */
+    HPS_ENOCONV = 4,     /* per box: FP64 refinement did not converge */
+    HPS_ECUDA = 5,       /* a CUDA runtime call failed */
+    HPS_ETIMEOUT = 6     /* reserved: a bounded device wait gave up */
+} hps_status;
+
+/* Arithmetic of the LU and the triangular solves.  HPS_FP64 runs everything
+ * in FP64 (the plain path).  HPS_FP32_IR factors A_ii in FP32 on the tensor
+ * cores (3-term TF32 split products with FP32 accumulation) and recovers FP64
+ * accuracy by iterative refinement: residuals R = -A_ib - A_ii X computed
+ * matrix-free in FP64, corrections solved with the FP32 factors, X updated in
+ * FP64; the D_n product forming T is FP64.  HPS_BF16_IR is reserved and
+ * currently returns HPS_EINVAL. */
+typedef enum { HPS_FP64 = 0, HPS_FP32_IR = 1, HPS_BF16_IR = 2 } hps_precision;
+
+/* One class of boxes: polynomial order p (3 <= p <= 24), box side lengths
+ * h[0..2] (> 0), wavenumber kappa (finite).  All boxes of a call share it. */
+typedef struct {
+    int p;
+    double h[3];
+    double kappa;
+} hps_leaf_kind;
+
+/* Tunables for hps_set_option (value is a double). */
+typedef enum {
+    HPS_OPT_IR_MAX_ITERS = 1,   /* corrections in FP32_IR mode, default 3, range 0..20 */
+    HPS_OPT_IR_TOL = 2,         /* converged when ||dX||_F <= tol ||X||_F, default 1e-12 */
+    HPS_OPT_BLOCK = 3,          /* LU block size NB: 0 = automatic, else 32, 64 or 128 */
+    HPS_OPT_TENSOR_CORES = 4,   /* FP32 products on tcgen05 (1, default) or CUDA cores (0) */
+    HPS_OPT_SYNC = 5,           /* 1: synchronise the stream and return the first box failure */
+    HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
+                                        which makes that box exactly singular (host-side fault injection) */
+} hps_option;
+
+/* Creates a context on CUDA device `device`.  workspace_bytes_max bounds the
+ * device workspace the context may allocate (0 = 85% of the memory free at
+ * the first leaf call).  Batches larger than the workspace holds are processed
+ * in chunks.  *ctx is NULL on failure. */
+hps_status hps_create(hps_ctx** ctx, int device, size_t workspace_bytes_max);
+
+/* Frees the context and its device memory.  Synchronises the device first. */
+void hps_destroy(hps_ctx* ctx);
+
+hps_status hps_set_option(hps_ctx* ctx, int option, double value);
+
+/* n = (p-2)^3 and m = 6 (p-2)^2 (Remark 1); HPS_EINVAL unless 3 <= p <= 24. */
+hps_status hps_leaf_sizes(int p, int* n, int* m);
+
+/* Host helper: coordinates of the p^3 Chebyshev-Lobatto nodes of the box
+ * [lo, lo + h] (Sec. 2.1), written to host array xyz[p^3][3] in grid order. */
+hps_status hps_leaf_nodes(int p, const double lo[3], const double h[3], double* xyz);
+
+/* Device workspace bytes one box needs for a DtN build at order p. */
+size_t hps_workspace_per_box(int p, hps_precision prec);
+
+/* Build stage, per box (Algorithm 1, the loop over boxes; Eq. 8):
+ * forms A^tau from b, factors A_ii with partial pivoting, and writes
+ *   T[nbox][m][m] = A_bb + A_bi S            (required)
+ *   S[nbox][n][m] = -A_ii^{-1} A_ib          (optional: NULL = do not store S)
+ * b[nbox][p^3] holds b at every grid node; only interior values enter.
+ * nbox = 0 is a no-op.  HPS_EINVAL for nbox < 0, T == NULL with nbox > 0,
+ * a bad kind or precision. */
+hps_status hps_leaf_build_dtn(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox,
+                              const double* b, double* T, double* S,
+                              hps_precision prec, int* box_status, void* stream);
+
+/* Solve stage, first loop (Sec. 2.2 steps 1-2; Algorithm 2): re-forms and
+ * re-factors A_ii (the paper recomputes rather than stores it) and writes
+ *   v[nbox][nrhs][n] = A_ii^{-1} f_i,   h[nbox][nrhs][m] = A_bi v.
+ * The caller's equivalent load on the faces is g_b = f_b - h (f_b = 0 on
+ * interfaces).  1 <= nrhs <= 256. */
+hps_status hps_leaf_particular(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int nrhs,
+                               const double* b, const double* f, double* v, double* h,
+                               hps_precision prec, int* box_status, void* stream);
+
+/* Solve stage, last loop (Sec. 2.2 step 4; Algorithm 2): u_i = v + S u_b.
+ * If S is non-NULL ([nbox][n][m], e.g. from hps_leaf_build_dtn) it is applied
+ * directly; if NULL, S u_b is recomputed as -A_ii^{-1} (A_ib u_b) from b
+ * (the paper's recompute mode).  v may be NULL (treated as zero). */
+hps_status hps_leaf_reconstruct(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int nrhs,
+                                const double* b, const double* S, const double* v,
+                                const double* ub, double* ui,
+                                hps_precision prec, int* box_status, void* stream);
+
+/* Host helper for the interface system (Sec. 3.1: row and column index
+ * arrays that align each T^tau with the global interface unknowns; Fig. 5).
+ * Boxes form an nb[0] x nb[1] x nb[2] grid, box index bx + nx (by + ny bz).
+ * Interface faces are numbered x-normal first ((ix-1) + (nx-1)(by + ny bz)),
+ * then y-normal (Fx + bx + nx((iy-1) + (ny-1) bz)), then z-normal
+ * (Fx + Fy + bx + nx(by + ny (iz-1))); boundary (Dirichlet) faces x-normal
+ * (s + 2(by + ny bz)), then y (Dx + s + 2(bx + nx bz)), then z
+ * (Dx + Dy + s + 2(bx + nx by)), s = 0 low side, 1 high side.  A face's q^2
+ * nodes keep the box-local face order, so global id = face id * q^2 + local.
+ * Outputs (host arrays, unsummed COO triplets in box order, row-major within a
+ * box block): interface x interface entries of every T^tau in
+ * rows/cols/vals, interface x Dirichlet entries in rows_d/cols_d/vals_d.
+ * Duplicate (row, col) pairs are to be summed (two boxes share each face).
+ * Call with NULL arrays to query nnz, nnz_d, n_iface and n_dir.
+ * T_host is [nbox][m][m] on the host. */
+hps_status hps_assemble_interface_blocks(int p, const int nb[3], const double* T_host,
+                                         int64_t* nnz, int64_t* rows, int64_t* cols, double* vals,
+                                         int64_t* nnz_d, int64_t* rows_d, int64_t* cols_d, double* vals_d,
+                                         int64_t* n_iface, int64_t* n_dir);
+
+/* Diagnostics of the last leaf call on this context: per box, the number of
+ * refinement corrections applied and the final relative correction
+ * ||dX||_F/||X||_F (0 for FP64).  Host arrays of length nbox (either may be
+ * NULL); synchronises the context's last stream. */
+hps_status hps_last_refinement(hps_ctx* ctx, int nbox, int* iters, double* rel_correction);
+
+/* Optional per-kernel timing.  hps_profile_enable(ctx, 1) makes the leaf calls
+ * bracket every kernel launch with CUDA events on the caller's stream and
+ * record each launch's algorithmic flops (2 M N K for an update product, the
+ * dense method's count) and bytes.  hps_profile_get synchronises and returns,
+ * for kernel class cls (0 operator build, 1 panel factorisation, 2 CUDA-core
+ * update product, 3 tensor-core update product, 4 row gather / operand pack,
+ * 5 FP64 refinement residual, 6 refinement update, 7 D_n product), the
+ * accumulated launches, milliseconds, flops and bytes since the last reset.
+ * Returns HPS_EINVAL for cls outside 0..7. */
+hps_status hps_profile_enable(hps_ctx* ctx, int on);
+hps_status hps_profile_reset(hps_ctx* ctx);
+hps_status hps_profile_get(hps_ctx* ctx, int cls, long long* launches, double* ms, double* flops, double* bytes);
+
+const char* hps_status_string(hps_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPS_H */

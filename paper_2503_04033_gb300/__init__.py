@@ -1,0 +1,269 @@
+"""Python binding of the HPS leaf-reduction library (C ABI in include/hps.h).
+
+Argument marshalling only: every step of the leaf reduction runs in the CUDA
+kernels of ``libhps.so``.  Functions keep the C names.  Buffer arguments take
+a torch tensor (its ``data_ptr()`` is passed; dtype, device and contiguity are
+checked), a raw integer address, or None for a NULL pointer.  A non-OK status
+raises ``HpsError``.  If the library has not been built, importing works but
+the first call raises: there is no CPU fallback.
+
+Build it with ``python -m paper_2503_04033_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "HPS_OK", "HPS_EINVAL", "HPS_ENOMEM", "HPS_ESINGULAR", "HPS_ENOCONV", "HPS_ECUDA", "HPS_ETIMEOUT",
+    "HPS_FP64", "HPS_FP32_IR", "HPS_BF16_IR", "HPS_OPT_IR_MAX_ITERS", "HPS_OPT_IR_TOL", "HPS_OPT_BLOCK",
+    "HPS_OPT_TENSOR_CORES", "HPS_OPT_SYNC", "HPS_OPT_TEST_SINGULAR_BOX", "HpsError", "LeafKind", "load_library", "library_path",
+    "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
+    "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
+    "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
+    "EXPORTED_SYMBOLS", "KERNEL_CLASSES",
+]
+
+HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
+HPS_FP64, HPS_FP32_IR, HPS_BF16_IR = 0, 1, 2
+HPS_OPT_IR_MAX_ITERS, HPS_OPT_IR_TOL, HPS_OPT_BLOCK, HPS_OPT_TENSOR_CORES, HPS_OPT_SYNC = 1, 2, 3, 4, 5
+HPS_OPT_TEST_SINGULAR_BOX = 100
+
+EXPORTED_SYMBOLS = (
+    "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
+    "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
+    "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
+)
+
+# Kernel classes of hps_profile_get.
+KERNEL_CLASSES = ("build", "panel", "update_cudacore", "update_tcgen05", "gather_pack", "residual_fp64",
+                  "refine_update", "dn_fp64")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libhps.so")
+
+
+class HpsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {hps_status_string(status)} (status {status})")
+
+
+class LeafKind(ctypes.Structure):
+    """hps_leaf_kind: polynomial order p, box sides h[3], wavenumber kappa."""
+    _fields_ = [("p", ctypes.c_int), ("h", ctypes.c_double * 3), ("kappa", ctypes.c_double)]
+
+    def __init__(self, p: int, h, kappa: float):
+        hh = list(h) if hasattr(h, "__len__") else [h, h, h]
+        super().__init__(int(p), (ctypes.c_double * 3)(*[float(x) for x in hh]), float(kappa))
+
+
+def load_library() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -m paper_2503_04033_gb300.build); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    kp = ctypes.POINTER(LeafKind)
+    sig = {
+        "hps_create": (i, [ctypes.POINTER(vp), i, sz]),
+        "hps_destroy": (None, [vp]),
+        "hps_set_option": (i, [vp, i, d]),
+        "hps_leaf_sizes": (i, [i, ip, ip]),
+        "hps_leaf_nodes": (i, [i, dp, dp, dp]),
+        "hps_workspace_per_box": (sz, [i, i]),
+        "hps_leaf_build_dtn": (i, [vp, kp, i, vp, vp, vp, i, vp, vp]),
+        "hps_leaf_particular": (i, [vp, kp, i, i, vp, vp, vp, vp, i, vp, vp]),
+        "hps_leaf_reconstruct": (i, [vp, kp, i, i, vp, vp, vp, vp, vp, i, vp, vp]),
+        "hps_assemble_interface_blocks": (i, [i, ip, dp, i64p, i64p, i64p, dp, i64p, i64p, i64p, dp, i64p, i64p]),
+        "hps_last_refinement": (i, [vp, i, ip, dp]),
+        "hps_profile_enable": (i, [vp, i]),
+        "hps_profile_reset": (i, [vp]),
+        "hps_profile_get": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
+        "hps_status_string": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != HPS_OK:
+        raise HpsError(status, where)
+
+
+def _ptr(x, dtype=None):
+    """Device address of a tensor (checked), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"expected a torch tensor, int or None, got {type(x)}")
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and x.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {x.dtype}")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f64():
+    import torch
+    return torch.float64
+
+
+def _i32():
+    import torch
+    return torch.int32
+
+
+def hps_status_string(status: int) -> str:
+    try:
+        return load_library().hps_status_string(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def hps_create(device: int = 0, workspace_bytes_max: int = 0) -> int:
+    ctx = ctypes.c_void_p()
+    _check(load_library().hps_create(ctypes.byref(ctx), int(device), int(workspace_bytes_max)), "hps_create")
+    return ctx.value
+
+
+def hps_destroy(ctx: int) -> None:
+    load_library().hps_destroy(ctx)
+
+
+def hps_set_option(ctx: int, option: int, value: float) -> None:
+    _check(load_library().hps_set_option(ctx, int(option), float(value)), "hps_set_option")
+
+
+def hps_leaf_sizes(p: int):
+    n, m = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().hps_leaf_sizes(int(p), ctypes.byref(n), ctypes.byref(m)), "hps_leaf_sizes")
+    return n.value, m.value
+
+
+def hps_leaf_nodes(p: int, lo, h):
+    import numpy as np
+    lo3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    hh = list(h) if hasattr(h, "__len__") else [h, h, h]
+    h3 = (ctypes.c_double * 3)(*[float(v) for v in hh])
+    out = np.empty((p ** 3, 3), dtype=np.float64)
+    _check(load_library().hps_leaf_nodes(int(p), lo3, h3, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "hps_leaf_nodes")
+    return out
+
+
+def hps_workspace_per_box(p: int, prec: int = HPS_FP32_IR) -> int:
+    return int(load_library().hps_workspace_per_box(int(p), int(prec)))
+
+
+def hps_leaf_build_dtn(ctx, kind: LeafKind, nbox: int, b, T, S=None, prec: int = HPS_FP32_IR,
+                       box_status=None, stream=None) -> None:
+    f64 = _f64() if not isinstance(b, int) else None
+    _check(load_library().hps_leaf_build_dtn(
+        ctx, ctypes.byref(kind), int(nbox), _ptr(b, f64), _ptr(T, f64), _ptr(S, f64), int(prec),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_build_dtn")
+
+
+def hps_leaf_particular(ctx, kind: LeafKind, nbox: int, nrhs: int, b, f, v, h, prec: int = HPS_FP32_IR,
+                        box_status=None, stream=None) -> None:
+    f64 = _f64() if not isinstance(b, int) else None
+    _check(load_library().hps_leaf_particular(
+        ctx, ctypes.byref(kind), int(nbox), int(nrhs), _ptr(b, f64), _ptr(f, f64), _ptr(v, f64), _ptr(h, f64),
+        int(prec), _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_particular")
+
+
+def hps_leaf_reconstruct(ctx, kind: LeafKind, nbox: int, nrhs: int, b, S, v, ub, ui, prec: int = HPS_FP32_IR,
+                         box_status=None, stream=None) -> None:
+    f64 = _f64() if not isinstance(ub, int) else None
+    _check(load_library().hps_leaf_reconstruct(
+        ctx, ctypes.byref(kind), int(nbox), int(nrhs), _ptr(b, f64), _ptr(S, f64), _ptr(v, f64), _ptr(ub, f64),
+        _ptr(ui, f64), int(prec),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_reconstruct")
+
+
+def hps_last_refinement(ctx, nbox: int):
+    import numpy as np
+    it = np.zeros(nbox, dtype=np.int32)
+    rel = np.zeros(nbox, dtype=np.float64)
+    _check(load_library().hps_last_refinement(ctx, int(nbox), it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                              rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "hps_last_refinement")
+    return it, rel
+
+
+def hps_assemble_interface_blocks(p: int, nb, T_host=None):
+    """Returns (rows, cols, vals, rows_d, cols_d, vals_d, n_iface, n_dir) as numpy
+    arrays (COO, unsummed) from host DtN blocks T_host [nbox, m, m]."""
+    import numpy as np
+    lib = load_library()
+    nb3 = (ctypes.c_int * 3)(*[int(v) for v in nb])
+    c64 = ctypes.c_int64
+    nnz, nnz_d, ni, nd = c64(), c64(), c64(), c64()
+    _check(lib.hps_assemble_interface_blocks(int(p), nb3, None, ctypes.byref(nnz), None, None, None,
+                                             ctypes.byref(nnz_d), None, None, None, ctypes.byref(ni),
+                                             ctypes.byref(nd)), "hps_assemble_interface_blocks")
+    if T_host is None:
+        return nnz.value, nnz_d.value, ni.value, nd.value
+    T_host = np.ascontiguousarray(T_host, dtype=np.float64)
+    rows, cols, vals = (np.empty(nnz.value, np.int64), np.empty(nnz.value, np.int64), np.empty(nnz.value))
+    rd, cd, vd = (np.empty(nnz_d.value, np.int64), np.empty(nnz_d.value, np.int64), np.empty(nnz_d.value))
+    P = ctypes.POINTER
+    i64 = lambda a: a.ctypes.data_as(P(c64))
+    f64 = lambda a: a.ctypes.data_as(P(ctypes.c_double))
+    _check(lib.hps_assemble_interface_blocks(int(p), nb3, f64(T_host), ctypes.byref(nnz), i64(rows), i64(cols),
+                                             f64(vals), ctypes.byref(nnz_d), i64(rd), i64(cd), f64(vd),
+                                             ctypes.byref(ni), ctypes.byref(nd)), "hps_assemble_interface_blocks")
+    return rows, cols, vals, rd, cd, vd, ni.value, nd.value
+
+
+def hps_profile_enable(ctx, on: bool = True) -> None:
+    _check(load_library().hps_profile_enable(ctx, int(bool(on))), "hps_profile_enable")
+
+
+def hps_profile_reset(ctx) -> None:
+    _check(load_library().hps_profile_reset(ctx), "hps_profile_reset")
+
+
+def hps_profile_get(ctx, cls: int):
+    """(launches, ms, flops, bytes) accumulated for kernel class cls."""
+    n = ctypes.c_longlong()
+    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().hps_profile_get(ctx, int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                          ctypes.byref(by)), "hps_profile_get")
+    return n.value, ms.value, fl.value, by.value

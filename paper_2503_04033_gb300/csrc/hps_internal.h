@@ -1,0 +1,229 @@
+// Internal declarations of the HPS leaf library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <algorithm>
+#include <vector>
+
+#include "../../include/hps.h"
+
+namespace hps {
+
+constexpr int kMaxP = 24;
+constexpr int kMaxNB = 128;          // largest LU block (K of every update product)
+constexpr int kPanelThreads = 512;   // threads of the panel-factorisation CTA
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+enum RhsKind { RHS_DTN = 0, RHS_LOAD = 1, RHS_TRACE = 2 };
+
+// Update-product epilogue modes (see gemm description in hps_kernels.cuh).
+enum GemmMode { GM_SET = 0, GM_ACC = 1, GM_FWD = 2, GM_BWD = 3 };
+
+// Per-(p, h) device tables: physical first and second derivative matrices,
+// [3][p][p] each (axis-major), FP64.
+struct Geometry {
+    int p = 0, q = 0, n = 0, m = 0;
+    double h[3] = {0, 0, 0};
+    double* dD = nullptr;
+    double* dD2 = nullptr;
+};
+
+// Batched O = src + alpha * A * B over boxes (blockIdx.z), all row-major.
+template <typename T>
+struct GemmArgs {
+    const T* A; long long lda, sA;
+    const T* B; long long ldb, sB;
+    T* O;       long long ldo, sO;
+    int M, N, K;
+    T alpha;
+    int mode, split;
+    const int* perm; long long sP;   // GM_FWD: source row of local row r (relative)
+    const T* W; long long ldw, sW;   // GM_FWD: saved rows of the panel
+    const int* skip;                 // per box: nonzero = leave untouched
+};
+
+// ---------------------------------------------------------------- LU plans
+
+struct Plan {
+    int n = 0, r = 0, NB = 0, ib = 0, nsteps = 0;
+    long long ldm = 0;
+    size_t elt = 0;                  // bytes per LU element
+    bool tc = false;                 // FP32 products on the tensor cores
+    std::vector<int> k0, nbs;
+    std::vector<long long> fw_off, bw_off, perm_off;
+    long long fw_elems = 0, bw_elems = 0, perm_elems = 0;
+    // per-box byte sizes of the workspace pieces
+    size_t bM = 0, bF = 0, bB = 0, bW = 0, bG = 0, bP = 0, bX = 0, bFp = 0, bBp = 0, bGp = 0;
+    size_t per_box = 0;
+};
+
+inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x)
+{
+    Plan P;
+    P.n = n;
+    P.r = r;
+    const bool fp64 = (prec == HPS_FP64);
+    P.elt = fp64 ? 8 : 4;
+    P.tc = !fp64 && use_tc;
+    int NB = nb_opt > 0 ? nb_opt : (fp64 ? 64 : 128);
+    if (fp64 && NB > 64) NB = 64;
+    if (NB > kMaxNB) NB = kMaxNB;
+    P.NB = NB;
+    P.ldm = (long long)align_up((size_t)(n + r), 8);
+    // panel inner-block width: the block column of the panel lives in shared memory
+    const size_t static_smem = 32 * kMaxNB * P.elt + 1024;
+    const size_t budget = 227 * 1024 - static_smem;
+    int ib = 32;
+    while (ib > 1 && (size_t)ib * n * P.elt > budget) ib >>= 1;
+    if (ib > NB) ib = NB;
+    P.ib = ib;
+    for (int k = 0; k < n; k += NB) {
+        const int nb = std::min(NB, n - k);
+        P.k0.push_back(k);
+        P.nbs.push_back(nb);
+        P.fw_off.push_back(P.fw_elems);
+        P.bw_off.push_back(P.bw_elems);
+        P.perm_off.push_back(P.perm_elems);
+        P.fw_elems += (long long)(n - k) * NB;
+        P.bw_elems += (long long)(k + nb) * NB;
+        P.perm_elems += (n - k);
+    }
+    P.nsteps = (int)P.k0.size();
+    const size_t A = 256;
+    P.bM = align_up((size_t)n * P.ldm * P.elt, A);
+    P.bF = align_up((size_t)P.fw_elems * P.elt, A);
+    P.bB = align_up((size_t)P.bw_elems * P.elt, A);
+    P.bW = align_up((size_t)NB * P.ldm * P.elt, A);
+    P.bG = P.bW;
+    P.bP = align_up((size_t)P.perm_elems * sizeof(int), A);
+    P.bX = need_x ? align_up((size_t)n * r * sizeof(double), A) : 0;
+    if (P.tc) {
+        // split (hi, lo) K-major copies of F, B and G for the tensor-core products
+        P.bFp = align_up((size_t)P.fw_elems * 2 * sizeof(float), A);
+        P.bBp = align_up((size_t)P.bw_elems * 2 * sizeof(float), A);
+        P.bGp = align_up((size_t)P.ldm * NB * 2 * sizeof(float), A);
+    }
+    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + 64;
+    return P;
+}
+
+// Pointers of one chunk's workspace.
+template <typename T>
+struct Work {
+    T *M, *F, *B, *W, *G;
+    int* perm;
+    double* X;
+    float *Fp, *Bp, *Gp;
+    double* norms;
+    int* skip;
+    long long sM, sF, sB, sG, sP, sX, sFp, sBp, sGp;
+};
+
+template <typename T>
+inline Work<T> carve(const Plan& P, void* base, int nbox)
+{
+    Work<T> w{};
+    char* c = static_cast<char*>(base);
+    auto take = [&](size_t per_box) { char* r = c; c += per_box * (size_t)nbox; return r; };
+    w.M = reinterpret_cast<T*>(take(P.bM));
+    w.F = reinterpret_cast<T*>(take(P.bF));
+    w.B = reinterpret_cast<T*>(take(P.bB));
+    w.W = reinterpret_cast<T*>(take(P.bW));
+    w.G = reinterpret_cast<T*>(take(P.bG));
+    w.perm = reinterpret_cast<int*>(take(P.bP));
+    w.X = P.bX ? reinterpret_cast<double*>(take(P.bX)) : nullptr;
+    w.Fp = P.bFp ? reinterpret_cast<float*>(take(P.bFp)) : nullptr;
+    w.Bp = P.bBp ? reinterpret_cast<float*>(take(P.bBp)) : nullptr;
+    w.Gp = P.bGp ? reinterpret_cast<float*>(take(P.bGp)) : nullptr;
+    w.norms = reinterpret_cast<double*>(take(align_up(2 * sizeof(double), 16)));
+    w.skip = reinterpret_cast<int*>(take(align_up(sizeof(int), 16)));
+    w.sM = (long long)(P.bM / P.elt);
+    w.sF = (long long)(P.bF / P.elt);
+    w.sB = (long long)(P.bB / P.elt);
+    w.sG = (long long)(P.bG / P.elt);
+    w.sP = (long long)(P.bP / sizeof(int));
+    w.sX = (long long)(P.bX / sizeof(double));
+    w.sFp = (long long)(P.bFp / sizeof(float));
+    w.sBp = (long long)(P.bBp / sizeof(float));
+    w.sGp = (long long)(P.bGp / sizeof(float));
+    return w;
+}
+
+
+// ---------------------------------------------------------------- profiling
+
+// Kernel classes timed by the optional event profiler (HPS_OPT_PROFILE).
+enum KernelClass {
+    KC_BUILD = 0, KC_PANEL, KC_UPDATE_CUDACORE, KC_UPDATE_TC, KC_GATHER, KC_RESIDUAL, KC_REFINE, KC_DN,
+    KC_COUNT
+};
+
+// When profiling is on for the calling thread, prof_begin/prof_end bracket a
+// launch with CUDA events on its stream and record its algorithmic flops and
+// bytes; otherwise they do nothing.
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st, double flops, double bytes);
+
+// Host launchers (hps_lu.cu).
+template <typename T>
+void launch_build_aug(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
+                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                      T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st);
+
+template <typename T>
+void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int ib,
+                  int* perm, long long sP, T* Ftop, long long ldf, long long sF,
+                  T* Btop, long long ldb, long long sB, int* status, const int* skip,
+                  int nbox, cudaStream_t st);
+
+template <typename T>
+void launch_gather(const T* M, long long ldm, long long sM, int k, int nb, int c0, int ncols,
+                   const int* perm, long long sP, T* W, T* G, long long ldg, long long sG,
+                   const int* skip, int nbox, cudaStream_t st);
+
+template <typename T>
+void launch_gemm(const GemmArgs<T>& a, int nbox, cudaStream_t st);
+
+void launch_dn(const Geometry& g, int nbox, const double* X, long long ldx, long long sX,
+               int ncols, double* out, long long sOut, int transposed_out, int add_abb,
+               cudaStream_t st);
+
+template <typename TS>
+void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
+                    double* X, long long ldx, long long sX, int nbox, cudaStream_t st);
+
+void launch_residual(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
+                     int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                     const double* X, long long ldx, long long sX,
+                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st);
+
+void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
+                      double* X, long long ldx, long long sX, double* norms /*[nbox][2]*/,
+                      const int* skip, int nbox, cudaStream_t st);
+
+void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
+                     int* iters, double* relcorr, int* status, cudaStream_t st);
+
+void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,
+                          const double* v, double* out, int nbox, cudaStream_t st);
+
+void launch_recon_stored(const double* S, int n, int m, int nrhs, const double* v,
+                         const double* ub, double* ui, int nbox, cudaStream_t st);
+
+void launch_fill_int(int* p, int value, long long count, cudaStream_t st);
+
+// Tensor-core (tcgen05, 3-term TF32 split) versions of the LU sequences (hps_tc.cu).
+// They return false when a TMA descriptor cannot be encoded.  A tensor-core
+// launch whose bounded wait gave up raises a device-wide abort flag (checked
+// with tc_abort_raised, cleared by tc_reset_abort) and marks its box
+// HPS_ETIMEOUT.
+void tc_reset_abort(cudaStream_t st);
+bool tc_abort_raised();
+bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStream_t st);
+bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st);
+bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st);
+
+}  // namespace hps

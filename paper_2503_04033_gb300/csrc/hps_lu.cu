@@ -1,0 +1,768 @@
+// CUDA-core kernels of the leaf reduction: operator assembly, the blocked LU
+// with partial pivoting (panel factorisation with warp-shuffle pivot search),
+// the row-gather and update products that carry the triangular solves, the
+// FP64 refinement residual, and the D_n / flux products.
+//
+// Storage of one box's working matrix M (row-major, leading dimension ldm):
+//   M = [ A_ii | RHS ]   n rows, n + r used columns,
+// where RHS is -A_ib (DtN build, Sec. 2.2: S = -A_ii^{-1} A_ib), the body loads
+// f_i (particular solution) or -A_ib u_b (recomputed reconstruction).
+//
+// Blocked right-looking LU, step s covers columns [k, k + nb):
+//   panel:  P_s [A11; A21] = [L11; L21] U11 (partial pivoting), with
+//           F_s = [-L11^{-1}; L21 L11^{-1}]  and  B_s top = -U11^{-1}.
+//   update: for all columns right of the panel (remaining A_ii columns and RHS)
+//           G = (P_s M)[k:k+nb],  W = M[k:k+nb] (rows before the swaps), then
+//           M[r] <- src(r) - F_s[r-k] G   for r >= k,
+//           src(r) = 0 for r < k + nb (so the rows become U12 = L11^{-1} G),
+//           src(r) = old row pi_s(r) otherwise (from W when it sat in the panel).
+//   The row interchanges are therefore never applied as a separate pass; the
+//   permutation rides in the update's epilogue.
+// Backward substitution (U x = y) runs the same product with
+//   B_s = [U[0:k, k:k+nb] U11^{-1}; -U11^{-1}], src(r) = M[r] for r < k, 0 after.
+// Forward substitution of new right-hand sides replays the stored (pi_s, F_s).
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+__device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+// ---------------------------------------------------------------- assembly
+
+// M[r][c] for one box.  Interior row r = (i,j,k) carries the Helmholtz
+// operator of Eq. 2 collocated with the 1-D second-derivative matrices
+// (interior block A_ii); the RHS columns hold -A_ib (couplings of the row to
+// the face nodes on its three grid lines), loads f_i, or -A_ib u_b.
+template <typename T>
+__global__ void k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
+                            double kappa2, const double* __restrict__ b, long long sb, int rhs_kind,
+                            const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M,
+                            long long ldm, long long sM, int* status, int zero_row_box)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int box = blockIdx.z;
+    if (r >= n || c >= ldm_cols) return;
+    const int q = p - 2, qq = q * q, pp = p * p;
+    const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
+    const double* D2x = D2;
+    const double* D2y = D2 + pp;
+    const double* D2z = D2 + 2 * pp;
+    double v = 0.0;
+    if (c < n) {
+        const int i2 = c % q + 1, j2 = (c / q) % q + 1, k2 = c / qq + 1;
+        if (j == j2 && k == k2) v -= __ldg(D2x + i * p + i2);
+        if (i == i2 && k == k2) v -= __ldg(D2y + j * p + j2);
+        if (i == i2 && j == j2) v -= __ldg(D2z + k * p + k2);
+        if (r == c) {
+            const double bv = __ldg(b + box * sb + i + p * j + pp * k);
+            if (!isfinite(bv)) status[box] = HPS_EINVAL;
+            v -= kappa2 * bv;
+        }
+    } else if (c < n + nrhs) {
+        const int cf = c - n;
+        if (rhs_kind == RHS_DTN) {
+            // -A_ib: face node (f, a, bb) couples to the interior row on its line.
+            const int f = cf / qq, s = cf % qq, a = s % q + 1, bb = s / q + 1;
+            const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
+            if (axis == 0 && j == a && k == bb) v = __ldg(D2x + i * p + e);
+            else if (axis == 1 && i == a && k == bb) v = __ldg(D2y + j * p + e);
+            else if (axis == 2 && i == a && j == bb) v = __ldg(D2z + k * p + e);
+        } else if (rhs_kind == RHS_LOAD) {
+            v = __ldg(rhs + box * s_rhs + (long long)cf * p * pp + i + p * j + pp * k);
+            if (!isfinite(v)) status[box] = HPS_EINVAL;
+        } else {
+            // -A_ib u_b: the six face nodes on this row's three grid lines.
+            const double* ub = rhs + box * s_rhs + (long long)cf * 6 * qq;
+            const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
+            v = __ldg(D2x + i * p) * ub[0 * qq + sx] + __ldg(D2x + i * p + p - 1) * ub[1 * qq + sx]
+              + __ldg(D2y + j * p) * ub[2 * qq + sy] + __ldg(D2y + j * p + p - 1) * ub[3 * qq + sy]
+              + __ldg(D2z + k * p) * ub[4 * qq + sz] + __ldg(D2z + k * p + p - 1) * ub[5 * qq + sz];
+            if (!isfinite(v)) status[box] = HPS_EINVAL;
+        }
+    }
+    if (box == zero_row_box && r == 0 && c < n) v = 0.0;   // test hook: exactly singular A_ii
+    M[box * sM + (long long)r * ldm + c] = T(v);
+}
+
+// ---------------------------------------------------------------- panel
+
+// Arg-max of |value| over the CTA with ties to the lowest index.
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi)
+{
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+}
+
+// One CTA factors one box's panel M[k:n, k:k+nb] (Algorithm 1's batched LU,
+// P A_ii = L U with partial pivoting).  The panel is processed in inner blocks
+// of ib columns that live in shared memory (column-major, R rows); the pivot
+// search is a warp-shuffle arg-max followed by a cross-warp pass.  After the
+// panel: the step's row permutation perm[r] (source row of local row r),
+// F top = -L11^{-1} and B top = -U11^{-1}.
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads)
+k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, int ib,
+        int* __restrict__ perm, long long sP, T* __restrict__ Ftop, long long ldf, long long sF,
+        T* __restrict__ Btop, long long ldb, long long sB, int* status, const int* skip)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Sb = reinterpret_cast<T*>(smem_raw);
+    __shared__ int swp[kMaxNB];
+    __shared__ T red_v[kPanelThreads / 32];
+    __shared__ int red_i[kPanelThreads / 32];
+    __shared__ int s_piv;
+    __shared__ int s_sing;
+    __shared__ T Xs[32 * kMaxNB];
+
+    const int box = blockIdx.x;
+    if (skip && skip[box]) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kPanelThreads / 32;
+    T* Mb = M + box * sM;
+    const int R0 = n - k;
+    if (tid == 0) s_sing = 0;
+
+    for (int jb = 0; jb < nb; jb += ib) {
+        const int w = imin(ib, nb - jb);
+        const int R = R0 - jb;
+        T* base = Mb + (long long)(k + jb) * ldm + (k + jb);
+        for (int idx = tid; idx < R * w; idx += kPanelThreads) {
+            const int r = idx / w, c = idx - r * w;
+            Sb[c * R + r] = base[(long long)r * ldm + c];
+        }
+        __syncthreads();
+        for (int c = 0; c < w; ++c) {
+            T bv = T(-1);
+            int bi = INT_MAX;
+            for (int r = c + tid; r < R; r += kPanelThreads) argmax_merge(bv, bi, tabs(Sb[c * R + r]), r);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                argmax_merge(bv, bi, ov, oi);
+            }
+            if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+            __syncthreads();
+            if (warp == 0) {
+                bv = lane < NW ? red_v[lane] : T(-1);
+                bi = lane < NW ? red_i[lane] : INT_MAX;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    argmax_merge(bv, bi, ov, oi);
+                }
+                if (lane == 0) {
+                    if (bi < c || bi >= R) bi = c;   // all candidates NaN: keep the diagonal row
+                    s_piv = bi;
+                    swp[jb + c] = jb + bi;
+                }
+            }
+            __syncthreads();
+            const int pr = s_piv;
+            if (pr != c)
+                for (int cc = tid; cc < w; cc += kPanelThreads) {
+                    const T t = Sb[cc * R + c];
+                    Sb[cc * R + c] = Sb[cc * R + pr];
+                    Sb[cc * R + pr] = t;
+                }
+            __syncthreads();
+            T piv = Sb[c * R + c];
+            if (piv == T(0)) {
+                // Exactly singular: record it and keep the arithmetic finite.
+                if (tid == 0) s_sing = 1;
+                piv = T(1);
+            }
+            for (int r = c + 1 + tid; r < R; r += kPanelThreads) {
+                const T l = Sb[c * R + r] / piv;
+                Sb[c * R + r] = l;
+                for (int cc = c + 1; cc < w; ++cc) Sb[cc * R + r] -= l * Sb[cc * R + c];
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < R * w; idx += kPanelThreads) {
+            const int r = idx / w, c = idx - r * w;
+            base[(long long)r * ldm + c] = Sb[c * R + r];
+        }
+        __syncthreads();
+        // This block's interchanges on the panel's other columns.
+        for (int col = tid; col < nb; col += kPanelThreads) {
+            if (col >= jb && col < jb + w) continue;
+            T* cp = Mb + k + col;
+            for (int c = 0; c < w; ++c) {
+                const int a = k + jb + c, bb = k + swp[jb + c];
+                if (a != bb) {
+                    const T t = cp[(long long)a * ldm];
+                    cp[(long long)a * ldm] = cp[(long long)bb * ldm];
+                    cp[(long long)bb * ldm] = t;
+                }
+            }
+        }
+        __syncthreads();
+        // Right-looking update of the panel columns [jb+w, nb).
+        const int ncr = nb - jb - w;
+        if (ncr > 0) {
+            T* rb = Mb + (long long)(k + jb) * ldm + (k + jb + w);
+            for (int col = tid; col < ncr; col += kPanelThreads) {
+                for (int c = 0; c < w; ++c) {
+                    T x = rb[(long long)c * ldm + col];
+                    for (int c2 = 0; c2 < c; ++c2) x -= Sb[c2 * R + c] * Xs[c2 * kMaxNB + col];
+                    Xs[c * kMaxNB + col] = x;
+                    rb[(long long)c * ldm + col] = x;
+                }
+            }
+            __syncthreads();
+            for (int r = w + warp; r < R; r += NW) {
+                T* row = rb + (long long)r * ldm;
+                for (int col = lane; col < ncr; col += 32) {
+                    T acc = row[col];
+                    for (int c = 0; c < w; ++c) acc -= Sb[c * R + r] * Xs[c * kMaxNB + col];
+                    row[col] = acc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // Row permutation of the step: position r holds the old row perm[r].
+    int* pb = perm + box * sP;
+    for (int r = tid; r < R0; r += kPanelThreads) pb[r] = r;
+    __syncthreads();
+    if (tid == 0)
+        for (int i = 0; i < nb; ++i) {
+            const int a = i, bb = swp[i];
+            if (a != bb) { const int t = pb[a]; pb[a] = pb[bb]; pb[bb] = t; }
+        }
+    if (tid == 0 && s_sing && status[box] == 0) status[box] = HPS_ESINGULAR;
+
+    // Inverses of the diagonal blocks (one column per thread).
+    T* L = Sb;                  // nb x nb, row-major: L11 (unit lower) and U11
+    T* X = Sb + nb * nb;        // inverse being built, row-major
+    for (int idx = tid; idx < nb * nb; idx += kPanelThreads) {
+        const int r = idx / nb, c = idx - r * nb;
+        L[idx] = Mb[(long long)(k + r) * ldm + k + c];
+    }
+    __syncthreads();
+    for (int c = tid; c < nb; c += kPanelThreads) {
+        X[c * nb + c] = T(1);
+        for (int r = c + 1; r < nb; ++r) {
+            T acc = T(0);
+            for (int t = c; t < r; ++t) acc -= L[r * nb + t] * X[t * nb + c];
+            X[r * nb + c] = acc;
+        }
+        for (int r = 0; r < c; ++r) X[r * nb + c] = T(0);
+    }
+    __syncthreads();
+    T* Fb = Ftop + box * sF;
+    for (int idx = tid; idx < nb * nb; idx += kPanelThreads) {
+        const int r = idx / nb, c = idx - r * nb;
+        Fb[r * ldf + c] = -X[idx];
+    }
+    __syncthreads();
+    for (int c = tid; c < nb; c += kPanelThreads) {
+        T d = L[c * nb + c];
+        if (d == T(0)) d = T(1);
+        X[c * nb + c] = T(1) / d;
+        for (int r = c - 1; r >= 0; --r) {
+            T acc = T(0);
+            for (int t = r + 1; t <= c; ++t) acc -= L[r * nb + t] * X[t * nb + c];
+            T dr = L[r * nb + r];
+            if (dr == T(0)) dr = T(1);
+            X[r * nb + c] = acc / dr;
+        }
+        for (int r = c + 1; r < nb; ++r) X[r * nb + c] = T(0);
+    }
+    __syncthreads();
+    T* Bb = Btop + box * sB;
+    for (int idx = tid; idx < nb * nb; idx += kPanelThreads) {
+        const int r = idx / nb, c = idx - r * nb;
+        Bb[r * ldb + c] = -X[idx];
+    }
+}
+
+// ---------------------------------------------------------------- gather
+
+// W = M[k:k+nb, c0:c0+ncols] and G = M[k + perm[i], c0:c0+ncols] (perm NULL:
+// identity, W skipped when NULL).
+template <typename T>
+__global__ void k_gather(const T* __restrict__ M, long long ldm, long long sM, int k, int nb, int c0,
+                         int ncols, const int* __restrict__ perm, long long sP, T* __restrict__ W,
+                         T* __restrict__ G, long long ldg, long long sG, const int* skip)
+{
+    const int box = blockIdx.z;
+    if (skip && skip[box]) return;
+    const int i = blockIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols || i >= nb) return;
+    const T* Mb = M + box * sM;
+    const int src = perm ? k + perm[box * sP + i] : k + i;
+    G[box * sG + (long long)i * ldg + c] = Mb[(long long)src * ldm + c0 + c];
+    if (W) W[box * sG + (long long)i * ldg + c] = Mb[(long long)(k + i) * ldm + c0 + c];
+}
+
+// ---------------------------------------------------------------- update product
+
+// O = src + alpha * A B, register-tiled on the CUDA cores (TM x TN outputs per
+// thread).  Modes: GM_SET src = 0; GM_ACC src = O; GM_FWD rows < split take
+// 0 and the others their permuted source row (in place or from W); GM_BWD
+// rows < split keep O, the others take 0.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm(GemmArgs<T> g)
+{
+    constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN];
+    const int box = blockIdx.z;
+    if (g.skip && g.skip[box]) return;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const T* A = g.A + box * g.sA;
+    const T* B = g.B + box * g.sB;
+    T* O = g.O + box * g.sO;
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    T acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[a][c] = T(0);
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += NT) {
+            const int i = idx / BK, kk = idx - i * BK;
+            const int r = m0 + i, kc = k0 + kk;
+            As[kk][i] = (r < g.M && kc < g.K) ? A[(long long)r * g.lda + kc] : T(0);
+        }
+        for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
+            const int kk = idx / BN, jj = idx - kk * BN;
+            const int kc = k0 + kk, c = n0 + jj;
+            Bs[kk][jj] = (kc < g.K && c < g.N) ? B[(long long)kc * g.ldb + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[TM], bv[TN];
+#pragma unroll
+            for (int a = 0; a < TM; ++a) av[a] = As[kk][ty * TM + a];
+#pragma unroll
+            for (int c = 0; c < TN; ++c) bv[c] = Bs[kk][tx * TN + c];
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[a][c] += av[a] * bv[c];
+        }
+        __syncthreads();
+    }
+    const T* Wb = g.W ? g.W + box * g.sW : nullptr;
+    const int* Pb = g.perm ? g.perm + box * g.sP : nullptr;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+        const int r = m0 + ty * TM + a;
+        if (r >= g.M) continue;
+        const T* srow = nullptr;
+        bool zero = false;
+        if (g.mode == GM_SET) zero = true;
+        else if (g.mode == GM_ACC) srow = O + (long long)r * g.ldo;
+        else if (g.mode == GM_FWD) {
+            if (r < g.split) zero = true;
+            else {
+                const int pr = Pb[r];
+                srow = (pr >= g.split) ? O + (long long)r * g.ldo : Wb + (long long)pr * g.ldw;
+            }
+        } else {
+            if (r < g.split) srow = O + (long long)r * g.ldo;
+            else zero = true;
+        }
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int cc = n0 + tx * TN + c;
+            if (cc >= g.N) continue;
+            const T s = zero ? T(0) : srow[cc];
+            O[(long long)r * g.ldo + cc] = s + g.alpha * acc[a][c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- D_n products
+
+// out(row r, column c) = sign_f ( sum_{l interior} D_a[e, l] X[line(r, l), c]
+//                                 + [add_abb] (D_a[e, e] [c = r] + D_a[e, e'] [c = opp(r)]) )
+// for face row r on face f (axis a, own index e, opposite e').  With X = S this
+// is T = A_bb + A_bi S (Eq. 8); with X = v and no A_bb it is h = A_bi v.
+__global__ void k_dn(int p, int n, int m, int ncols, const double* __restrict__ D,
+                     const double* __restrict__ X, long long ldx, long long sX, double* __restrict__ out,
+                     long long sOut, int transposed_out, int add_abb)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    const int box = blockIdx.z;
+    if (c >= ncols) return;
+    const int q = p - 2, qq = q * q;
+    const int f = r / qq, s = r - f * qq, a = s % q + 1, bb = s / q + 1;
+    const int axis = f >> 1, e = (f & 1) ? p - 1 : 0, eo = (f & 1) ? 0 : p - 1;
+    const double sg = (f & 1) ? 1.0 : -1.0;
+    const double* Da = D + axis * p * p + e * p;
+    const double* Xb = X + box * sX;
+    long long base, stride;
+    if (axis == 0) { base = q * (a - 1) + qq * (bb - 1) - 1; stride = 1; }
+    else if (axis == 1) { base = (a - 1) + qq * (bb - 1) - q; stride = q; }
+    else { base = (a - 1) + q * (bb - 1) - qq; stride = qq; }
+    double acc = 0.0;
+    for (int l = 1; l <= q; ++l) acc += __ldg(Da + l) * Xb[(base + l * stride) * ldx + c];
+    if (add_abb) {
+        if (c == r) acc += __ldg(Da + e);
+        if (c == ((f ^ 1) * qq + s)) acc += __ldg(Da + eo);
+    }
+    acc *= sg;
+    if (transposed_out) out[box * sOut + (long long)c * m + r] = acc;
+    else out[box * sOut + (long long)r * m + c] = acc;
+}
+
+// ---------------------------------------------------------------- refinement
+
+template <typename TS>
+__global__ void k_extract(const TS* __restrict__ src, long long lds, long long sS, int n, int ncols,
+                          double* __restrict__ X, long long ldx, long long sX)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    const int box = blockIdx.z;
+    if (c >= ncols || r >= n) return;
+    X[box * sX + (long long)r * ldx + c] = double(src[box * sS + (long long)r * lds + c]);
+}
+
+// R = B - A_ii X in FP64, matrix-free: A_ii X applies the 1-D second-derivative
+// matrices along the three grid lines through each interior node plus the
+// kappa^2 b diagonal (the Kronecker structure of Eq. 2's collocation); B is
+// -A_ib (DTN), f_i (LOAD) or -A_ib u_b (TRACE).  One CTA holds a tile of ct
+// columns of X for one box in shared memory.  R is written in FP32 for the
+// correction solve.
+__global__ void k_residual(int p, int n, int nrhs, int ct, const double* __restrict__ D2, double kappa2,
+                           const double* __restrict__ b, long long sb, int rhs_kind,
+                           const double* __restrict__ rhs, long long s_rhs, const double* __restrict__ X,
+                           long long ldx, long long sX, float* __restrict__ R, long long ldr, long long sR,
+                           const int* skip)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int box = blockIdx.y;
+    if (skip && skip[box]) return;
+    const int c0 = blockIdx.x * ct;
+    const int q = p - 2, qq = q * q, pp = p * p;
+    double* Xs = reinterpret_cast<double*>(smem_raw);       // [n][ct]
+    double* D2s = Xs + (long long)n * ct;                    // [3][p][p]
+    const double* Xb = X + box * sX;
+    const int nc = imin(ct, nrhs - c0);
+    for (int idx = threadIdx.x; idx < n * ct; idx += blockDim.x) {
+        const int r = idx / ct, c = idx - r * ct;
+        Xs[idx] = c < nc ? Xb[(long long)r * ldx + c0 + c] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < 3 * pp; idx += blockDim.x) D2s[idx] = D2[idx];
+    __syncthreads();
+    const double* bb = b + box * sb;
+    for (int idx = threadIdx.x; idx < n * ct; idx += blockDim.x) {
+        const int r = idx / ct, c = idx - r * ct;
+        if (c >= nc) continue;
+        const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
+        const double* rx = D2s + i * p;
+        const double* ry = D2s + pp + j * p;
+        const double* rz = D2s + 2 * pp + k * p;
+        const int bx = (r - (i - 1)) * ct + c;               // node (1, j, k)
+        const int by = (r - (j - 1) * q) * ct + c;           // node (i, 1, k)
+        const int bz = (r - (k - 1) * qq) * ct + c;          // node (i, j, 1)
+        double lap = 0.0;
+        for (int l = 1; l <= q; ++l) {
+            lap += rx[l] * Xs[bx + (l - 1) * ct];
+            lap += ry[l] * Xs[by + (l - 1) * q * ct];
+            lap += rz[l] * Xs[bz + (l - 1) * qq * ct];
+        }
+        const double xv = Xs[r * ct + c];
+        const int gi = i + p * j + pp * k;
+        double bval;
+        const int cg = c0 + c;
+        if (rhs_kind == RHS_DTN) {
+            const int f = cg / qq, s = cg % qq, a = s % q + 1, b2 = s / q + 1;
+            const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
+            bval = 0.0;
+            if (axis == 0 && j == a && k == b2) bval = rx[e];
+            else if (axis == 1 && i == a && k == b2) bval = ry[e];
+            else if (axis == 2 && i == a && j == b2) bval = rz[e];
+        } else if (rhs_kind == RHS_LOAD) {
+            bval = rhs[box * s_rhs + (long long)cg * p * pp + gi];
+        } else {
+            const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
+            const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
+            bval = rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] + ry[p - 1] * ub[3 * qq + sy]
+                 + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
+        }
+        // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
+        const double res = bval + lap + kappa2 * bb[gi] * xv;
+        R[box * sR + (long long)r * ldr + cg] = float(res);
+    }
+}
+
+// X += D (the FP32 correction) in FP64; accumulates ||D||^2 and ||X||^2 per box.
+__global__ void k_ir_update(const float* __restrict__ D, long long ldd, long long sD, int n, int ncols,
+                            double* __restrict__ X, long long ldx, long long sX, double* norms,
+                            const int* skip)
+{
+    const int box = blockIdx.y;
+    if (skip && skip[box]) return;
+    double dn = 0.0, xn = 0.0;
+    const long long total = (long long)n * ncols;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long r = idx / ncols, c = idx - r * ncols;
+        const double d = double(D[box * sD + r * ldd + c]);
+        double* xp = X + box * sX + r * ldx + c;
+        const double x = *xp + d;
+        *xp = x;
+        dn += d * d;
+        xn += x * x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dn += __shfl_xor_sync(0xffffffffu, dn, off);
+        xn += __shfl_xor_sync(0xffffffffu, xn, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(norms + 2 * box, dn);
+        atomicAdd(norms + 2 * box + 1, xn);
+    }
+}
+
+__global__ void k_ir_check(int nbox, double* norms, double tol, int last, int* skip, int* iters,
+                           double* relcorr, int* status)
+{
+    const int box = blockIdx.x * blockDim.x + threadIdx.x;
+    if (box >= nbox || skip[box]) return;
+    const double dn = norms[2 * box], xn = norms[2 * box + 1];
+    const double rel = xn > 0.0 ? sqrt(dn / xn) : sqrt(dn);
+    iters[box] += 1;
+    relcorr[box] = rel;
+    norms[2 * box] = 0.0;
+    norms[2 * box + 1] = 0.0;
+    if (rel <= tol) skip[box] = 1;
+    else if (last && status[box] == 0) status[box] = isfinite(rel) ? HPS_ENOCONV : HPS_EINVAL;
+}
+
+// out[c][r] = X[r][c] (+ v[c][r]) for the [nrhs][n] output layouts.
+__global__ void k_transpose_add(const double* __restrict__ X, long long ldx, long long sX, int n, int ncols,
+                                const double* __restrict__ v, double* __restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    const int box = blockIdx.z;
+    if (r >= n) return;
+    const long long o = ((long long)box * ncols + c) * n + r;
+    double x = X[box * sX + (long long)r * ldx + c];
+    if (v) x += v[o];
+    out[o] = x;
+}
+
+// u_i = v + S u_b with a stored S (one warp per interior row).
+__global__ void k_recon_stored(const double* __restrict__ S, int n, int m, int nrhs,
+                               const double* __restrict__ v, const double* __restrict__ ub,
+                               double* __restrict__ ui)
+{
+    const int warps = blockDim.x >> 5;
+    const int r = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int box = blockIdx.y;
+    if (r >= n) return;
+    const double* Srow = S + ((long long)box * n + r) * m;
+    for (int c = 0; c < nrhs; ++c) {
+        const double* u = ub + ((long long)box * nrhs + c) * m;
+        double acc = 0.0;
+        for (int l = lane; l < m; l += 32) acc += Srow[l] * u[l];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            const long long o = ((long long)box * nrhs + c) * n + r;
+            ui[o] = acc + (v ? v[o] : 0.0);
+        }
+    }
+}
+
+__global__ void k_fill_int(int* p, int value, long long count)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = value;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+template <typename T>
+void launch_build_aug(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
+                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                      T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st)
+{
+    dim3 blk(32, 8);
+    dim3 grd((unsigned)((ldm + 31) / 32), (unsigned)((g.n + 7) / 8), (unsigned)nbox);
+    prof_begin(KC_BUILD, st);
+    k_build_aug<T><<<grd, blk, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, b, sb, rhs_kind,
+                                        rhs_src, s_rhs, M, ldm, sM, status, zero_row_box);
+    prof_end(KC_BUILD, st, 0.0, (double)nbox * g.n * ldm * sizeof(T));
+}
+
+template <typename T>
+void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int ib,
+                  int* perm, long long sP, T* Ftop, long long ldf, long long sF,
+                  T* Btop, long long ldb, long long sB, int* status, const int* skip,
+                  int nbox, cudaStream_t st)
+{
+    const size_t s1 = (size_t)ib * (size_t)(n - k) * sizeof(T);
+    const size_t s2 = (size_t)2 * nb * nb * sizeof(T);
+    const size_t smem = s1 > s2 ? s1 : s2;
+    cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prof_begin(KC_PANEL, st);
+    k_panel<T><<<nbox, kPanelThreads, smem, st>>>(M, ldm, sM, n, k, nb, ib, perm, sP, Ftop, ldf, sF,
+                                                  Btop, ldb, sB, status, skip);
+    prof_end(KC_PANEL, st, (double)nbox * (n - k) * (double)nb * nb, (double)nbox * 2.0 * (n - k) * nb * sizeof(T));
+}
+
+template <typename T>
+void launch_gather(const T* M, long long ldm, long long sM, int k, int nb, int c0, int ncols,
+                   const int* perm, long long sP, T* W, T* G, long long ldg, long long sG,
+                   const int* skip, int nbox, cudaStream_t st)
+{
+    dim3 grd((unsigned)((ncols + 127) / 128), (unsigned)nb, (unsigned)nbox);
+    prof_begin(KC_GATHER, st);
+    k_gather<T><<<grd, 128, 0, st>>>(M, ldm, sM, k, nb, c0, ncols, perm, sP, W, G, ldg, sG, skip);
+    prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)ncols * sizeof(T) * (W ? 3 : 2));
+}
+
+template <>
+void launch_gemm<double>(const GemmArgs<double>& a, int nbox, cudaStream_t st)
+{
+    constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+    dim3 grd((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM), (unsigned)nbox);
+    if (a.M <= 0 || a.N <= 0) return;
+    prof_begin(KC_UPDATE_CUDACORE, st);
+    k_gemm<double, BM, BN, BK, TM, TN><<<grd, (BM / TM) * (BN / TN), 0, st>>>(a);
+    prof_end(KC_UPDATE_CUDACORE, st, 2.0 * nbox * a.M * (double)a.N * a.K, (double)nbox * ((double)a.M * a.K + (double)a.K * a.N + 2.0 * a.M * a.N) * 8);
+}
+
+template <>
+void launch_gemm<float>(const GemmArgs<float>& a, int nbox, cudaStream_t st)
+{
+    constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+    dim3 grd((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM), (unsigned)nbox);
+    if (a.M <= 0 || a.N <= 0) return;
+    prof_begin(KC_UPDATE_CUDACORE, st);
+    k_gemm<float, BM, BN, BK, TM, TN><<<grd, (BM / TM) * (BN / TN), 0, st>>>(a);
+    prof_end(KC_UPDATE_CUDACORE, st, 2.0 * nbox * a.M * (double)a.N * a.K, (double)nbox * ((double)a.M * a.K + (double)a.K * a.N + 2.0 * a.M * a.N) * 4);
+}
+
+void launch_dn(const Geometry& g, int nbox, const double* X, long long ldx, long long sX,
+               int ncols, double* out, long long sOut, int transposed_out, int add_abb,
+               cudaStream_t st)
+{
+    dim3 grd((unsigned)((ncols + 127) / 128), (unsigned)g.m, (unsigned)nbox);
+    prof_begin(KC_DN, st);
+    k_dn<<<grd, 128, 0, st>>>(g.p, g.n, g.m, ncols, g.dD, X, ldx, sX, out, sOut, transposed_out, add_abb);
+    prof_end(KC_DN, st, 2.0 * nbox * g.m * (double)ncols * g.q, (double)nbox * ((double)g.n + g.m) * ncols * 8);
+}
+
+template <typename TS>
+void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
+                    double* X, long long ldx, long long sX, int nbox, cudaStream_t st)
+{
+    dim3 grd((unsigned)((ncols + 127) / 128), (unsigned)n, (unsigned)nbox);
+    prof_begin(KC_REFINE, st);
+    k_extract<TS><<<grd, 128, 0, st>>>(src, lds, sS, n, ncols, X, ldx, sX);
+    prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * (sizeof(TS) + 8));
+}
+
+void launch_residual(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
+                     int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                     const double* X, long long ldx, long long sX,
+                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st)
+{
+    // Column tile: as many columns as fit next to the operator tables.
+    const size_t budget = 200 * 1024 - (size_t)3 * g.p * g.p * sizeof(double);
+    int ct = 16;
+    while (ct > 1 && (size_t)g.n * ct * sizeof(double) > budget) ct >>= 1;
+    const size_t smem = ((size_t)g.n * ct + (size_t)3 * g.p * g.p) * sizeof(double);
+    cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grd((unsigned)((nrhs + ct - 1) / ct), (unsigned)nbox);
+    prof_begin(KC_RESIDUAL, st);
+    k_residual<<<grd, 512, smem, st>>>(g.p, g.n, nrhs, ct, g.dD2, kappa * kappa, b, sb, rhs_kind, rhs_src,
+                                       s_rhs, X, ldx, sX, R, ldr, sR, skip);
+    prof_end(KC_RESIDUAL, st, (double)nbox * g.n * (double)nrhs * (6.0 * g.q + 4.0), (double)nbox * g.n * (double)nrhs * 12.0);
+}
+
+void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
+                      double* X, long long ldx, long long sX, double* norms,
+                      const int* skip, int nbox, cudaStream_t st)
+{
+    long long total = (long long)n * ncols;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 64) blocks = 64;
+    dim3 grd((unsigned)blocks, (unsigned)nbox);
+    prof_begin(KC_REFINE, st);
+    k_ir_update<<<grd, 256, 0, st>>>(D, ldd, sD, n, ncols, X, ldx, sX, norms, skip);
+    prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * 20.0);
+}
+
+void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
+                     int* iters, double* relcorr, int* status, cudaStream_t st)
+{
+    k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, last, skip, iters, relcorr, status);
+}
+
+void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,
+                          const double* v, double* out, int nbox, cudaStream_t st)
+{
+    dim3 grd((unsigned)((n + 127) / 128), (unsigned)ncols, (unsigned)nbox);
+    k_transpose_add<<<grd, 128, 0, st>>>(X, ldx, sX, n, ncols, v, out);
+}
+
+void launch_recon_stored(const double* S, int n, int m, int nrhs, const double* v,
+                         const double* ub, double* ui, int nbox, cudaStream_t st)
+{
+    dim3 grd((unsigned)((n + 7) / 8), (unsigned)nbox);
+    k_recon_stored<<<grd, 256, 0, st>>>(S, n, m, nrhs, v, ub, ui);
+}
+
+void launch_fill_int(int* p, int value, long long count, cudaStream_t st)
+{
+    if (count <= 0) return;
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    k_fill_int<<<blocks, 256, 0, st>>>(p, value, count);
+}
+
+template void launch_build_aug<float>(const Geometry&, double, int, const double*, long long, int, int,
+                                      const double*, long long, float*, long long, long long, int*, int,
+                                      cudaStream_t);
+template void launch_build_aug<double>(const Geometry&, double, int, const double*, long long, int, int,
+                                       const double*, long long, double*, long long, long long, int*, int,
+                                       cudaStream_t);
+template void launch_panel<float>(float*, long long, long long, int, int, int, int, int*, long long, float*,
+                                  long long, long long, float*, long long, long long, int*, const int*, int,
+                                  cudaStream_t);
+template void launch_panel<double>(double*, long long, long long, int, int, int, int, int*, long long, double*,
+                                   long long, long long, double*, long long, long long, int*, const int*, int,
+                                   cudaStream_t);
+template void launch_gather<float>(const float*, long long, long long, int, int, int, int, const int*, long long,
+                                   float*, float*, long long, long long, const int*, int, cudaStream_t);
+template void launch_gather<double>(const double*, long long, long long, int, int, int, int, const int*,
+                                    long long, double*, double*, long long, long long, const int*, int,
+                                    cudaStream_t);
+template void launch_extract<float>(const float*, long long, long long, int, int, double*, long long, long long,
+                                    int, cudaStream_t);
+template void launch_extract<double>(const double*, long long, long long, int, int, double*, long long,
+                                     long long, int, cudaStream_t);
+
+}  // namespace hps

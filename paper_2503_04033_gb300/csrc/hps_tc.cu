@@ -1,0 +1,544 @@
+// Tensor-core update products of the FP32 LU (sm_103a, tcgen05 + TMA).
+//
+// Every trailing update and triangular-solve step of the blocked LU is a
+// product O <- src - A G with A = F_s or B_s (rows x NB) and G the step's
+// gathered rows (NB x N); see hps_lu.cu for the scheme.  Here that product
+// runs on the 5th-generation tensor cores with FP32 accuracy from TF32 inputs:
+// every operand x is split as x = hi + lo with hi = tf32(x), lo = tf32(x - hi),
+// and A G ~ A_hi G_hi + A_hi G_lo + A_lo G_hi (the lo*lo term is below FP32
+// rounding).  The split operands are packed K-major (A as [row][k], G
+// transposed to [col][k]) so that TMA brings 128-byte rows into shared memory
+// in the 128B-swizzled layout that tcgen05.mma reads directly.
+//
+// One CTA computes a 128 x 64 tile: warp 4 issues the TMA loads (2-stage
+// ring over 32-wide K chunks), warp 5 owns the TMEM accumulator and issues
+// the MMAs (one elected lane), warps 0-3 drain TMEM with tcgen05.ld and apply
+// the epilogue (source rows: zero, in place, or saved pivot rows).  All
+// mbarrier waits are bounded; a wait that gives up marks the box HPS_ETIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 64;
+constexpr int TC_BK = 32;                                   // FP32 values per 128-byte row
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 16 KiB
+constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 8 KiB
+constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + 1024;
+constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
+
+struct TcArgs {
+    float* O; long long ldo, sO;
+    int M, N, kch;
+    int mode, split;
+    const int* perm; long long sP;
+    const float* W; long long ldw, sW;
+    const int* skip;
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Set by the first CTA whose wait gives up; every other wait then returns at
+// once, so a broken launch ends in about WAIT_NS instead of spinning per CTA.
+__device__ int g_tc_abort;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*reinterpret_cast<volatile int*>(&g_tc_abort)) return false;
+            if (global_ns() - t0 > WAIT_NS) {
+                atomicExch(&g_tc_abort, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1,
+                                            int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D(tmem) (+)= A(smem) * B(smem)^T, M = 128, N = TC_BN, K = 8, TF32 in, FP32 accumulate.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N, M.
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void __launch_bounds__(TC_THREADS)
+k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+
+    const int box = blockIdx.z;
+    if (a.skip && a.skip[box]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&acc_bar), 1);
+        fail_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) tmem_alloc(smem_u32(&tmem_base_sh), TC_BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+            int issued = 0;
+            for (int ch = 0; ch < a.kch; ++ch) {
+                const int s = ch % TC_STAGES;
+                const uint32_t use = ch / TC_STAGES;
+                if (ch >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[s]), (use - 1) & 1)) {
+                    fail_sh = 1;
+                    break;
+                }
+                const uint32_t fb = smem_u32(&full_bar[s]);
+                const uint32_t st = sbase + s * STAGE_BYTES;
+                mbar_expect_tx(fb, STAGE_BYTES);
+                tma_load_4d(st, &tmA, fb, ch * TC_BK, m0, 0, box);
+                tma_load_4d(st + A_TILE, &tmA, fb, ch * TC_BK, m0, 1, box);
+                tma_load_4d(st + 2 * A_TILE, &tmB, fb, ch * TC_BK, n0, 0, box);
+                tma_load_4d(st + 2 * A_TILE + B_TILE, &tmB, fb, ch * TC_BK, n0, 1, box);
+                ++issued;
+            }
+            // Drain: every load this thread issued has landed before the CTA may exit.
+            for (int ch = (issued > TC_STAGES ? issued - TC_STAGES : 0); ch < issued; ++ch)
+                if (!mbar_wait(smem_u32(&full_bar[ch % TC_STAGES]), (ch / TC_STAGES) & 1)) fail_sh = 1;
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tf32_idesc(TC_BM, TC_BN);
+            for (int ch = 0; ch < a.kch; ++ch) {
+                const int s = ch % TC_STAGES;
+                const uint32_t use = ch / TC_STAGES;
+                if (!mbar_wait(smem_u32(&full_bar[s]), use & 1)) {
+                    fail_sh = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + s * STAGE_BYTES;
+                const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_TILE);
+                const uint64_t bh = sw128_desc(st + 2 * A_TILE), bl = sw128_desc(st + 2 * A_TILE + B_TILE);
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 8; ++kk) {
+                    const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 8 TF32 values = 32 bytes
+                    mma_tf32(tmem, ah + o, bh + o, idesc, (ch | kk) != 0);
+                    mma_tf32(tmem, ah + o, bl + o, idesc, 1);
+                    mma_tf32(tmem, al + o, bh + o, idesc, 1);
+                }
+                mma_commit(smem_u32(&empty_bar[s]));
+            }
+            mma_commit(smem_u32(&acc_bar));
+        }
+    } else {
+        // Epilogue: warp w reads TMEM lanes [32w, 32w + 32) = tile rows.
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_bar), 0));
+        tc_fence_after();
+        const int r = m0 + warp * 32 + lane;
+        const bool rv = ok && r < a.M;
+        float* Ob = a.O + box * a.sO;
+        const float* srow = nullptr;
+        if (rv) {
+            if (a.mode == GM_ACC) srow = Ob + (long long)r * a.ldo;
+            else if (a.mode == GM_FWD) {
+                if (r >= a.split) {
+                    const int pr = a.perm[box * a.sP + r];
+                    srow = (pr >= a.split) ? Ob + (long long)r * a.ldo : a.W + box * a.sW + (long long)pr * a.ldw;
+                }
+            } else if (a.mode == GM_BWD) {
+                if (r < a.split) srow = Ob + (long long)r * a.ldo;
+            }
+        }
+        float* orow = Ob + (long long)r * a.ldo;
+        if (ok) {
+#pragma unroll 1
+            for (int j0 = 0; j0 < TC_BN; j0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
+                if (rv) {
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int c = n0 + j0 + jj;
+                        if (c < a.N) orow[c] = (srow ? srow[c] : 0.0f) - __uint_as_float(v[jj]);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            fail_sh = 1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TC_BN);
+    }
+    if (threadIdx.x == 0 && fail_sh && a.status) a.status[box] = HPS_ETIMEOUT;
+}
+
+// dst = [hi plane | lo plane] of the first nb columns of src (rows x NB,
+// zero beyond nb), hi = tf32(x), lo = tf32(x - hi).
+__global__ void k_pack_split(const float* __restrict__ src, long long sS, int rows, int NB, int nb,
+                             float* __restrict__ dst, long long sD)
+{
+    const int box = blockIdx.y;
+    const long long total = (long long)rows * NB;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % NB);
+        const float x = c < nb ? src[box * sS + idx] : 0.0f;
+        const float hi = to_tf32(x);
+        dst[box * sD + idx] = hi;
+        dst[box * sD + total + idx] = to_tf32(x - hi);
+    }
+}
+
+// Gather the step's rows (through perm), save the unpermuted rows to W, and
+// write the split, transposed G: Gp[plane][c][i] for i < NB (zero for i >= nb).
+__global__ void k_gather_pack(const float* __restrict__ M, long long ldm, long long sM, int k, int nb, int NB,
+                              int c0, int nc, const int* __restrict__ perm, long long sP, float* __restrict__ W,
+                              long long ldw, long long sW, float* __restrict__ Gp, long long plane, long long sGp,
+                              const int* skip)
+{
+    __shared__ float tile[32][33];
+    const int box = blockIdx.z;
+    if (skip && skip[box]) return;
+    const int i0 = blockIdx.y * 32, cb = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const float* Mb = M + box * sM;
+    for (int ii = ty; ii < 32; ii += 8) {
+        const int i = i0 + ii, c = cb + tx;
+        float v = 0.0f;
+        if (i < nb && c < nc) {
+            const int src = k + (perm ? perm[box * sP + i] : i);
+            v = Mb[(long long)src * ldm + c0 + c];
+            if (W) W[box * sW + (long long)i * ldw + c] = Mb[(long long)(k + i) * ldm + c0 + c];
+        }
+        tile[ii][tx] = v;
+    }
+    __syncthreads();
+    float* G = Gp + box * sGp;
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int c = cb + cc, i = i0 + tx;
+        if (c < nc) {
+            const float v = tile[tx][cc];
+            const float hi = to_tf32(v);
+            G[(long long)c * NB + i] = hi;
+            G[plane + (long long)c * NB + i] = to_tf32(v - hi);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 4-D map over split K-major operands: (k, row, plane, box).
+bool make_map(CUtensorMap* tm, const float* base, int K, long long rows, long long plane_elems, long long box_elems,
+              int nbox, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, 2, (cuuint64_t)nbox};
+    cuuint64_t strides[3] = {(cuuint64_t)K * 4, (cuuint64_t)plane_elems * 4, (cuuint64_t)box_elems * 4};
+    cuuint32_t boxd[4] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, boxd, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const float* Gp, long long g_plane,
+                      long long sGp, int NB, int K, const TcArgs& args, int nbox, cudaStream_t st)
+{
+    if (args.M <= 0 || args.N <= 0) return true;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, Ap, NB, a_rows, a_rows * NB, sAp, nbox, TC_BM) ||
+        !make_map(&tb, Gp, NB, args.N, g_plane, sGp, nbox, TC_BN))
+        return false;
+    TcArgs a = args;
+    a.kch = (K + TC_BK - 1) / TC_BK;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        attr = true;
+    }
+    dim3 grd((unsigned)((a.N + TC_BN - 1) / TC_BN), (unsigned)((a.M + TC_BM - 1) / TC_BM), (unsigned)nbox);
+    prof_begin(KC_UPDATE_TC, st);
+    k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, a);
+    const double kk = (double)K;
+    prof_end(KC_UPDATE_TC, st, 2.0 * nbox * a.M * (double)a.N * kk,
+             (double)nbox * (2.0 * (a.M + (double)a.N) * kk * 4 + 2.0 * a.M * (double)a.N * 4));
+    return true;
+}
+
+void launch_pack_split(const float* src, long long sS, int rows, int NB, int nb, float* dst, long long sD, int nbox,
+                       cudaStream_t st)
+{
+    const long long total = (long long)rows * NB;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 256);
+    dim3 grd((unsigned)blocks, (unsigned)nbox);
+    prof_begin(KC_GATHER, st);
+    k_pack_split<<<grd, 256, 0, st>>>(src, sS, rows, NB, nb, dst, sD);
+    prof_end(KC_GATHER, st, 0.0, (double)nbox * total * 12.0);
+}
+
+void launch_gather_pack(const Plan& P, Work<float>& w, int k, int nb, int c0, int nc, const int* perm, bool save_w,
+                        const int* skip, int nbox, cudaStream_t st)
+{
+    dim3 grd((unsigned)((nc + 31) / 32), (unsigned)(P.NB / 32), (unsigned)nbox);
+    prof_begin(KC_GATHER, st);
+    k_gather_pack<<<grd, dim3(32, 8), 0, st>>>(w.M, P.ldm, w.sM, k, nb, P.NB, c0, nc, perm, w.sP,
+                                               save_w ? w.W : nullptr, P.ldm, w.sG, w.Gp, P.ldm * P.NB, w.sGp, skip);
+    prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * 4 * (save_w ? 4 : 3));
+}
+
+TcArgs targs(float* O, long long ldo, long long sO, int M, int N, int mode, int split)
+{
+    TcArgs a{};
+    a.O = O; a.ldo = ldo; a.sO = sO; a.M = M; a.N = N; a.mode = mode; a.split = split;
+    return a;
+}
+
+}  // namespace
+
+void tc_reset_abort(cudaStream_t st)
+{
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tc_abort) == cudaSuccess) cudaMemsetAsync(p, 0, sizeof(int), st);
+}
+
+bool tc_abort_raised()
+{
+    int v = 0;
+    cudaMemcpyFromSymbol(&v, g_tc_abort, sizeof(int));
+    return v != 0;
+}
+
+bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStream_t st)
+{
+    const int n = P.n, NB = P.NB;
+    const long long ldm = P.ldm;
+    for (int s = 0; s < P.nsteps; ++s) {
+        const int k = P.k0[s], nb = P.nbs[s];
+        float* Fs = w.F + P.fw_off[s];
+        float* Bs = w.B + P.bw_off[s];
+        int* Ps = w.perm + P.perm_off[s];
+        launch_panel<float>(w.M, ldm, w.sM, n, k, nb, P.ib, Ps, w.sP, Fs, NB, w.sF, Bs + (long long)k * NB, NB,
+                            w.sB, status, nullptr, nbox, st);
+        if (n - k - nb > 0) {
+            GemmArgs<float> a{};
+            a.alpha = -1.0f;
+            a.A = w.M + (long long)(k + nb) * ldm + k; a.lda = ldm; a.sA = w.sM;
+            a.B = Fs; a.ldb = NB; a.sB = w.sF;
+            a.O = Fs + (long long)nb * NB; a.ldo = NB; a.sO = w.sF;
+            a.M = n - k - nb; a.N = nb; a.K = nb; a.mode = GM_SET;
+            launch_gemm<float>(a, nbox, st);
+        }
+        if (k > 0) {
+            GemmArgs<float> a{};
+            a.alpha = -1.0f;
+            a.A = w.M + k; a.lda = ldm; a.sA = w.sM;
+            a.B = Bs + (long long)k * NB; a.ldb = NB; a.sB = w.sB;
+            a.O = Bs; a.ldo = NB; a.sO = w.sB;
+            a.M = k; a.N = nb; a.K = nb; a.mode = GM_SET;
+            launch_gemm<float>(a, nbox, st);
+        }
+        launch_pack_split(Fs, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
+        launch_pack_split(Bs, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
+        const int c0 = k + nb, nc = n + P.r - c0;
+        if (nc > 0) {
+            launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st);
+            TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
+            a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
+            if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
+                                  nb, a, nbox, st))
+                return false;
+        }
+    }
+    return true;
+}
+
+bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st)
+{
+    const int n = P.n, NB = P.NB;
+    const long long ldm = P.ldm;
+    for (int s = 0; s < P.nsteps; ++s) {
+        const int k = P.k0[s], nb = P.nbs[s];
+        int* Ps = w.perm + P.perm_off[s];
+        launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, skip, nbox, st);
+        TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
+        a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
+        if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
+                              nb, a, nbox, st))
+            return false;
+    }
+    return true;
+}
+
+bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st)
+{
+    const int NB = P.NB;
+    const long long ldm = P.ldm;
+    for (int s = P.nsteps - 1; s >= 0; --s) {
+        const int k = P.k0[s], nb = P.nbs[s];
+        launch_gather_pack(P, w, k, nb, c0, nc, nullptr, false, skip, nbox, st);
+        TcArgs a = targs(w.M + c0, ldm, w.sM, k + nb, nc, GM_BWD, k);
+        a.skip = skip;
+        if (!launch_tc_update(w.Bp + 2 * P.bw_off[s], k + nb, w.sBp, w.Gp, ldm * NB, w.sGp, NB,
+                              nb, a, nbox, st))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace hps

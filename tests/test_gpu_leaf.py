@@ -1,0 +1,278 @@
+"""Parity of the CUDA leaf reduction against the FP64 oracle, through the C ABI.
+
+Tolerances (relative Frobenius error per box, against the oracle):
+  FP64 path            1e-11 on T, S, v, h, u_i
+  FP32 + refinement    1e-10 on T, S, v, h, u_i
+Both bounds sit well above the forward error of either side (cond(A_ii) is
+~1e3-1e4 on these workloads, times FP64 rounding) and far below what an
+indexing or sign mistake would give.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import hps_inputs as hi
+import oracle
+import paper_2503_04033_gb300 as H
+from tests._cases import box_b, config_grid, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [
+    pytest.param(H.HPS_FP64, 0, 1e-11, id="fp64"),
+    pytest.param(H.HPS_FP32_IR, 0, 1e-10, id="fp32ir-cudacore"),
+    pytest.param(H.HPS_FP32_IR, 1, 1e-10, id="fp32ir-tcgen05"),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.hps_create(0, 0)
+    yield c
+    H.hps_destroy(c)
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def gpu_dtn(ctx, p, h, kappa, b_np, prec, tc, want_S=True, block=0):
+    import torch
+    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, tc)
+    H.hps_set_option(ctx, H.HPS_OPT_BLOCK, block)
+    n, m = H.hps_leaf_sizes(p)
+    nbox = b_np.shape[0]
+    b = _dev(b_np)
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(nbox, n, m, dtype=torch.float64, device="cuda") if want_S else None
+    st = torch.full((nbox,), -1, dtype=torch.int32, device="cuda")
+    H.hps_leaf_build_dtn(ctx, H.LeafKind(p, h, kappa), nbox, b, T, S, prec, st)
+    torch.cuda.synchronize()
+    return T.cpu().numpy(), (S.cpu().numpy() if want_S else None), st.cpu().numpy()
+
+
+def _lows(nbox, h, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 4, size=(nbox, 3)) * np.asarray(h)
+
+
+@pytest.mark.parametrize("prec,tc,tol", PRECS)
+@pytest.mark.parametrize("p,nbox", [(3, 2), (5, 3), (8, 4), (9, 3), (10, 2)])
+def test_dtn_parity_small(ctx, p, nbox, prec, tc, tol):
+    h = np.array([0.125, 0.2, 0.15])
+    kappa = 12.0
+    lows = _lows(nbox, h, p)
+    field = hi.fourier_b_field().b
+    b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
+    b_or = box_b(oracle.node_coords, p, lows, h, field)
+    T, S, st = gpu_dtn(ctx, p, h, kappa, b_gpu, prec, tc)
+    To, So, sto = oracle.batch_dtn(p, h, kappa, b_or, want_S=True)
+    assert (sto == 0).all() and (st == 0).all(), st
+    assert rel_fro(T, To).max() < tol, rel_fro(T, To)
+    assert rel_fro(S, So).max() < tol, rel_fro(S, So)
+
+
+@pytest.mark.parametrize("prec,tc,tol", PRECS)
+@pytest.mark.parametrize("block", [32, 64])
+def test_dtn_parity_block_sizes(ctx, prec, tc, tol, block):
+    """Several LU blocks with a ragged last block (n = 343 at p = 9)."""
+    p, h, kappa = 9, np.array([0.25, 0.25, 0.25]), 7.0
+    lows = _lows(2, h, 3)
+    field = hi.gaussian_dip_b
+    T, S, st = gpu_dtn(ctx, p, h, kappa, box_b(H.hps_leaf_nodes, p, lows, h, field), prec, tc, block=block)
+    To, So, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=True)
+    assert (st == 0).all()
+    assert rel_fro(T, To).max() < tol and rel_fro(S, So).max() < tol
+
+
+@pytest.mark.parametrize("prec,tc,tol", PRECS)
+@pytest.mark.parametrize("kappa", [0.0, 10.0])
+def test_dtn_manufactured_grid(ctx, prec, tc, tol, kappa):
+    p, h, _, lows, field = config_grid("manufactured")
+    T, S, st = gpu_dtn(ctx, p, h, kappa, box_b(H.hps_leaf_nodes, p, lows, h, field), prec, tc)
+    To, So, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=True)
+    assert (st == 0).all()
+    assert rel_fro(T, To).max() < tol and rel_fro(S, So).max() < tol
+    if kappa == 0.0:
+        assert np.abs(T.sum(axis=2)).max() < 1e-9 * np.abs(T).max()      # T 1 = 0
+
+
+@pytest.mark.parametrize("prec,tc,tol", [PRECS[0], PRECS[2]])
+def test_dtn_dip_512_boxes_sampled(ctx, prec, tc, tol):
+    """Full 8x8x8 grid at p = 12 on the GPU; sampled boxes against the oracle."""
+    p, h, kappa, lows, field = config_grid("dip")
+    T, S, st = gpu_dtn(ctx, p, h, kappa, box_b(H.hps_leaf_nodes, p, lows, h, field), prec, tc)
+    assert (st == 0).all()
+    for box in (0, 273, 511):
+        To, So, info = oracle.leaf_dtn(p, h, kappa, field(oracle.node_coords(p, lows[box], h)))
+        assert info == 0
+        assert rel_fro(T[box:box + 1], To[None]).max() < tol
+        assert rel_fro(S[box:box + 1], So[None]).max() < tol
+
+
+def test_dtn_fourier16_512_boxes_sampled(ctx):
+    """The p = 16 mixed-precision workload at full size (512 boxes, kappa = 40),
+    tensor-core FP32 LU + FP64 refinement; two boxes against the oracle, and
+    every box against the plain FP64 GPU path."""
+    import torch
+    p, h, kappa, lows, field = config_grid("fourier16")
+    b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
+    T, _, st = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, want_S=False)
+    assert (st == 0).all(), np.unique(st, return_counts=True)
+    it, rel = H.hps_last_refinement(ctx, len(lows))
+    assert (rel <= 1e-12).all(), rel.max()
+    for box in (5, 300):
+        To, _, info = oracle.leaf_dtn(p, h, kappa, field(oracle.node_coords(p, lows[box], h)), want_S=False)
+        assert info == 0
+        assert rel_fro(T[box:box + 1], To[None]).max() < 1e-10
+    sel = np.arange(0, 512, 16)
+    T64, _, st64 = gpu_dtn(ctx, p, h, kappa, b_gpu[sel], H.HPS_FP64, 0, want_S=False)
+    assert (st64 == 0).all()
+    assert rel_fro(T[sel], T64).max() < 1e-10
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec,tc,tol", PRECS)
+def test_particular_parity(ctx, prec, tc, tol):
+    import torch
+    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, tc)
+    p, h, kappa, nbox, nrhs = 9, np.array([0.125] * 3), 20.0, 3, 4
+    lows = _lows(nbox, h, 9)
+    field = hi.fourier_b_field().b
+    loads = hi.fourier_b_per_box(nrhs, 77)
+    fg = np.stack([hi.load_values(loads, H.hps_leaf_nodes(p, lo, h)) for lo in lows])
+    n, m = H.hps_leaf_sizes(p)
+    v = torch.empty(nbox, nrhs, n, dtype=torch.float64, device="cuda")
+    hf = torch.empty(nbox, nrhs, m, dtype=torch.float64, device="cuda")
+    st = torch.full((nbox,), -1, dtype=torch.int32, device="cuda")
+    H.hps_leaf_particular(ctx, H.LeafKind(p, h, kappa), nbox, nrhs, _dev(box_b(H.hps_leaf_nodes, p, lows, h, field)),
+                          _dev(fg), v, hf, prec, st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    for bx in range(nbox):
+        xyz = oracle.node_coords(p, lows[bx], h)
+        vo, ho, info = oracle.leaf_particular(p, h, kappa, field(xyz), hi.load_values(loads, xyz))
+        assert info == 0
+        assert rel_fro(v[bx:bx + 1].cpu().numpy(), vo[None]).max() < tol
+        assert rel_fro(hf[bx:bx + 1].cpu().numpy(), ho[None]).max() < tol
+
+
+@pytest.mark.parametrize("prec,tc,tol", PRECS)
+@pytest.mark.parametrize("stored", [True, False])
+def test_reconstruct_parity(ctx, prec, tc, tol, stored):
+    import torch
+    p, h, kappa, nbox, nrhs = 8, np.array([0.125] * 3), 15.0, 3, 2
+    lows = _lows(nbox, h, 4)
+    field = hi.gaussian_dip_b
+    n, m = H.hps_leaf_sizes(p)
+    b = _dev(box_b(H.hps_leaf_nodes, p, lows, h, field))
+    ub_np = hi.random_boundary_data(nbox, nrhs, m)
+    v_np = np.random.default_rng(5).standard_normal((nbox, nrhs, n))
+    S = None
+    if stored:
+        _, S_np, st = gpu_dtn(ctx, p, h, kappa, box_b(H.hps_leaf_nodes, p, lows, h, field), prec, tc)
+        S = _dev(S_np)
+    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, tc)
+    ui = torch.empty(nbox, nrhs, n, dtype=torch.float64, device="cuda")
+    st = torch.full((nbox,), -1, dtype=torch.int32, device="cuda")
+    H.hps_leaf_reconstruct(ctx, H.LeafKind(p, h, kappa), nbox, nrhs, b, S, _dev(v_np), _dev(ub_np), ui, prec, st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    for bx in range(nbox):
+        uo, info = oracle.leaf_reconstruct(p, h, kappa, field(oracle.node_coords(p, lows[bx], h)), v_np[bx], ub_np[bx])
+        assert rel_fro(ui[bx:bx + 1].cpu().numpy(), uo[None]).max() < tol
+
+
+@pytest.mark.parametrize("prec", [H.HPS_FP64, H.HPS_FP32_IR])
+def test_status_singular_and_nonfinite(ctx, prec):
+    """Host-side fault injection: the test hook zeroes row 0 of box 1's A_ii,
+    which partial pivoting must meet as an exactly zero pivot; a NaN in box 2's
+    b is reported as invalid input.  Box 0 is untouched."""
+    p, h, kappa = 6, np.array([0.25] * 3), 5.0
+    b = np.ones((3, p ** 3))
+    b[2, 1 + p + p * p] = np.nan            # interior node (1,1,1)
+    H.hps_set_option(ctx, H.HPS_OPT_TEST_SINGULAR_BOX, 1)
+    try:
+        _, _, st = gpu_dtn(ctx, p, h, kappa, b, prec, 1)
+    finally:
+        H.hps_set_option(ctx, H.HPS_OPT_TEST_SINGULAR_BOX, -1)
+    assert st[0] == 0 and st[1] == H.HPS_ESINGULAR and st[2] == H.HPS_EINVAL, st
+
+
+def test_argument_errors(ctx):
+    import torch
+    T = torch.empty(1, 6, 6, dtype=torch.float64, device="cuda")
+    b = torch.ones(1, 27, dtype=torch.float64, device="cuda")
+    with pytest.raises(H.HpsError) as e:
+        H.hps_leaf_build_dtn(ctx, H.LeafKind(2, 1.0, 0.0), 1, b, T)
+    assert e.value.status == H.HPS_EINVAL
+    with pytest.raises(H.HpsError):
+        H.hps_leaf_build_dtn(ctx, H.LeafKind(3, 1.0, 0.0), 1, b, T, prec=H.HPS_BF16_IR)
+    H.hps_leaf_build_dtn(ctx, H.LeafKind(3, 1.0, 0.0), 0, b, T)            # nbox = 0: no-op
+
+
+def test_chunked_workspace_matches(ctx):
+    """A workspace that holds 3 boxes processes 8 boxes in chunks, bit-identically."""
+    p, h, kappa = 8, np.array([0.125] * 3), 25.0
+    lows = _lows(8, h, 8)
+    b = box_b(H.hps_leaf_nodes, p, lows, h, hi.fourier_b_field().b)
+    T_all, _, _ = gpu_dtn(ctx, p, h, kappa, b, H.HPS_FP32_IR, 1, want_S=False)
+    small = H.hps_create(0, 3 * H.hps_workspace_per_box(p, H.HPS_FP32_IR) + 4096)
+    try:
+        T_ch, _, st = gpu_dtn(small, p, h, kappa, b, H.HPS_FP32_IR, 1, want_S=False)
+    finally:
+        H.hps_destroy(small)
+    assert (st == 0).all()
+    np.testing.assert_array_equal(T_all, T_ch)
+
+
+def test_end_to_end_manufactured(ctx):
+    """Config of the manufactured solution: the GPU's T, v, h feed the library's
+    interface assembly and a host sparse LU; the GPU reconstructs u_i.  Matches
+    the oracle's own two-level solve to 1e-11 and the exact solution to the
+    discretisation error."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import torch
+    from oracle import global_solve as gs
+    kappa = 10.0
+    p, h, _, lows, field = config_grid("manufactured")
+    nbox = len(lows)
+    n, m = H.hps_leaf_sizes(p)
+    kind = H.LeafKind(p, h, kappa)
+    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, 1)
+    b = _dev(box_b(H.hps_leaf_nodes, p, lows, h, field))
+    f = _dev(np.stack([hi.manufactured(H.hps_leaf_nodes(p, lo, h), kappa)[1] for lo in lows])[:, None, :])
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device="cuda")
+    v = torch.empty(nbox, 1, n, dtype=torch.float64, device="cuda")
+    hf = torch.empty(nbox, 1, m, dtype=torch.float64, device="cuda")
+    H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, H.HPS_FP64)
+    H.hps_leaf_particular(ctx, kind, nbox, 1, b, f, v, hf, H.HPS_FP64)
+    torch.cuda.synchronize()
+    rows, cols, vals, rd, cd, vd, ni, nd = H.hps_assemble_interface_blocks(p, (2, 2, 2), T.cpu().numpy())
+    Tg = sp.coo_matrix((vals, (rows, cols)), shape=(ni, ni)).tocsc()
+    grid = gs.InterfaceGrid(p, (2, 2, 2))
+    g = hi.manufactured(grid.dirichlet_coords(), kappa)[2]
+    rhs = -sp.coo_matrix((vd, (rd, cd)), shape=(ni, nd)) @ g
+    hf_np = hf.cpu().numpy()[:, 0, :]
+    ub = np.empty((nbox, m))
+    for bx in range(nbox):
+        isi, gid = grid.local_to_global(bx)
+        np.add.at(rhs, gid[isi], -hf_np[bx, isi])
+    u_if = spla.splu(Tg).solve(rhs)
+    for bx in range(nbox):
+        isi, gid = grid.local_to_global(bx)
+        ub[bx, isi] = u_if[gid[isi]]
+        ub[bx, ~isi] = g[gid[~isi]]
+    ui = torch.empty(nbox, 1, n, dtype=torch.float64, device="cuda")
+    H.hps_leaf_reconstruct(ctx, kind, nbox, 1, b, None, v, _dev(ub[:, None, :]), ui, H.HPS_FP32_IR)
+    torch.cuda.synchronize()
+    ref = gs.hps_solve(grid, kappa, lambda x: np.ones(len(x)), lambda x: hi.manufactured(x, kappa)[1],
+                       lambda x: hi.manufactured(x, kappa)[2])
+    scale = np.abs(ref["u_int"]).max()
+    assert np.abs(u_if - ref["u_iface"]).max() < 1e-11 * scale
+    assert np.abs(ui.cpu().numpy()[:, 0, :] - ref["u_int"]).max() < 1e-10 * scale
+    exact = hi.manufactured(gs.interior_coords(grid), kappa)[0]
+    assert np.abs(ui.cpu().numpy()[:, 0, :] - exact).max() < 1e-4
