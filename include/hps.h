@@ -84,8 +84,10 @@ typedef struct {
 
 /* Tunables for hps_set_option (value is a double). */
 typedef enum {
-    HPS_OPT_IR_MAX_ITERS = 1,   /* corrections in FP32_IR mode, default 3, range 0..20 */
-    HPS_OPT_IR_TOL = 2,         /* converged when ||dX||_F <= tol ||X||_F, default 1e-12 */
+    HPS_OPT_IR_MAX_ITERS = 1,   /* corrections in FP32_IR mode, default 8, range 0..20 */
+    HPS_OPT_IR_TOL = 2,         /* a box stops refining when ||dX||_F <= tol ||X||_F (default 1e-12),
+                                   or when ||dX|| is below 1e-11 ||X|| and shrank by less than half
+                                   (the FP64 residual's noise floor); converged boxes skip later steps */
     HPS_OPT_BLOCK = 3,          /* LU block size NB: 0 = automatic, else 32, 64 or 128 */
     HPS_OPT_TENSOR_CORES = 4,   /* FP32 products on tcgen05 (1, default) or CUDA cores (0) */
     HPS_OPT_SYNC = 5,           /* 1: synchronise the stream and return the first box failure */

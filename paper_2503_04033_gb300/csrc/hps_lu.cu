@@ -538,18 +538,23 @@ __global__ void k_ir_update(const float* __restrict__ D, long long ldd, long lon
     }
 }
 
-__global__ void k_ir_check(int nbox, double* norms, double tol, int last, int* skip, int* iters,
+// Per-box stopping rule of the refinement: converged when the correction is
+// below tol relative to X, or when it has stopped shrinking (less than a halving)
+// while already below stag_tol, i.e. X sits at the FP64 residual's noise floor.
+__global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol, int last, int* skip, int* iters,
                            double* relcorr, int* status)
 {
     const int box = blockIdx.x * blockDim.x + threadIdx.x;
     if (box >= nbox || skip[box]) return;
     const double dn = norms[2 * box], xn = norms[2 * box + 1];
     const double rel = xn > 0.0 ? sqrt(dn / xn) : sqrt(dn);
+    const double prev = relcorr[box];
     iters[box] += 1;
     relcorr[box] = rel;
     norms[2 * box] = 0.0;
     norms[2 * box + 1] = 0.0;
-    if (rel <= tol) skip[box] = 1;
+    const bool stagnated = iters[box] > 1 && rel <= stag_tol && rel > 0.5 * prev;
+    if (rel <= tol || stagnated) skip[box] = 1;
     else if (last && status[box] == 0) status[box] = isfinite(rel) ? HPS_ENOCONV : HPS_EINVAL;
 }
 
@@ -718,7 +723,7 @@ void launch_ir_update(const float* D, long long ldd, long long sD, int n, int nc
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
                      int* iters, double* relcorr, int* status, cudaStream_t st)
 {
-    k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, last, skip, iters, relcorr, status);
+    k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, 1e-11, last, skip, iters, relcorr, status);
 }
 
 void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,

@@ -26,13 +26,13 @@ namespace hps {
 
 namespace {
 
-constexpr int TC_BM = 128;
-constexpr int TC_BN = 64;
+constexpr int TC_BM = 128;                                  // tile rows = TMEM lanes
+constexpr int TC_BN = 256;                                  // tile columns = TMEM columns per buffer
 constexpr int TC_BK = 32;                                   // FP32 values per 128-byte row
 constexpr int TC_STAGES = 2;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 192;                             // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 16 KiB
-constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 8 KiB
+constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 32 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + 1024;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
@@ -40,6 +40,8 @@ constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
 struct TcArgs {
     float* O; long long ldo, sO;
     int M, N, kch;
+    int tiles_m, tiles_n, tiles;
+    int vec;                         // rows of O and W are 16-byte aligned: float4 epilogue
     int mode, split;
     const int* perm; long long sP;
     const float* W; long long ldw, sW;
@@ -185,131 +187,200 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(TC_THREADS)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent update product O <- src - A G over (box, row tile, column tile).
+// Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (box-major, so
+// a box's A and G stay in L2 while its tiles run).  TMEM holds two 128 x 256
+// FP32 accumulators: the epilogue drains one while the MMAs fill the other.
+__global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
-    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ __align__(8) uint64_t tfull_bar[2];
+    __shared__ __align__(8) uint64_t tempty_bar[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
 
-    const int box = blockIdx.z;
-    if (a.skip && a.skip[box]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const int per_box = a.tiles_m * a.tiles_n;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&acc_bar), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull_bar[b]), 1);
+            mbar_init(smem_u32(&tempty_bar[b]), 4);
+        }
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) tmem_alloc(smem_u32(&tmem_base_sh), TC_BN);
+    if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 2 * TC_BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    if (warp == 4) {
+    if (warp == 0) {
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-            int issued = 0;
-            for (int ch = 0; ch < a.kch; ++ch) {
-                const int s = ch % TC_STAGES;
-                const uint32_t use = ch / TC_STAGES;
-                if (ch >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[s]), (use - 1) & 1)) {
-                    fail_sh = 1;
-                    break;
+            uint32_t g = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+                const int box = t / per_box, rem = t - box * per_box;
+                if (a.skip && a.skip[box]) continue;
+                const int m0 = (rem / a.tiles_n) * TC_BM, n0 = (rem % a.tiles_n) * TC_BN;
+                for (int ch = 0; ch < a.kch; ++ch, ++g) {
+                    const int s = g % TC_STAGES;
+                    const uint32_t use = g / TC_STAGES;
+                    if (g >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[s]), (use - 1) & 1)) {
+                        fail_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    const uint32_t st = sbase + s * STAGE_BYTES;
+                    mbar_expect_tx(fb, STAGE_BYTES);
+                    tma_load_4d(st, &tmA, fb, ch * TC_BK, m0, 0, box);
+                    tma_load_4d(st + A_TILE, &tmA, fb, ch * TC_BK, m0, 1, box);
+                    tma_load_4d(st + 2 * A_TILE, &tmB, fb, ch * TC_BK, n0, 0, box);
+                    tma_load_4d(st + 2 * A_TILE + B_TILE, &tmB, fb, ch * TC_BK, n0, 1, box);
                 }
-                const uint32_t fb = smem_u32(&full_bar[s]);
-                const uint32_t st = sbase + s * STAGE_BYTES;
-                mbar_expect_tx(fb, STAGE_BYTES);
-                tma_load_4d(st, &tmA, fb, ch * TC_BK, m0, 0, box);
-                tma_load_4d(st + A_TILE, &tmA, fb, ch * TC_BK, m0, 1, box);
-                tma_load_4d(st + 2 * A_TILE, &tmB, fb, ch * TC_BK, n0, 0, box);
-                tma_load_4d(st + 2 * A_TILE + B_TILE, &tmB, fb, ch * TC_BK, n0, 1, box);
-                ++issued;
             }
-            // Drain: every load this thread issued has landed before the CTA may exit.
-            for (int ch = (issued > TC_STAGES ? issued - TC_STAGES : 0); ch < issued; ++ch)
-                if (!mbar_wait(smem_u32(&full_bar[ch % TC_STAGES]), (ch / TC_STAGES) & 1)) fail_sh = 1;
+            // Drain: the last loads issued into each stage have landed.
+            for (uint32_t h = (g > TC_STAGES ? g - TC_STAGES : 0); h < g; ++h)
+                if (!mbar_wait(smem_u32(&full_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
         }
-    } else if (warp == 5) {
+    } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tf32_idesc(TC_BM, TC_BN);
-            for (int ch = 0; ch < a.kch; ++ch) {
-                const int s = ch % TC_STAGES;
-                const uint32_t use = ch / TC_STAGES;
-                if (!mbar_wait(smem_u32(&full_bar[s]), use & 1)) {
-                    fail_sh = 1;
-                    break;
-                }
+            uint32_t g = 0, j = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
+                const int box = t / per_box;
+                if (a.skip && a.skip[box]) continue;
+                const int b = j & 1;
+                const uint32_t uj = j >> 1;
+                if (j >= 2 && !mbar_wait(smem_u32(&tempty_bar[b]), (uj - 1) & 1)) { fail_sh = 1; break; }
                 tc_fence_after();
-                const uint32_t st = sbase + s * STAGE_BYTES;
-                const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_TILE);
-                const uint64_t bh = sw128_desc(st + 2 * A_TILE), bl = sw128_desc(st + 2 * A_TILE + B_TILE);
+                const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+                for (int ch = 0; ch < a.kch; ++ch, ++g) {
+                    const int s = g % TC_STAGES;
+                    if (!mbar_wait(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1)) { fail_sh = 1; ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t st = sbase + s * STAGE_BYTES;
+                    const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_TILE);
+                    const uint64_t bh = sw128_desc(st + 2 * A_TILE), bl = sw128_desc(st + 2 * A_TILE + B_TILE);
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 8; ++kk) {
-                    const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 8 TF32 values = 32 bytes
-                    mma_tf32(tmem, ah + o, bh + o, idesc, (ch | kk) != 0);
-                    mma_tf32(tmem, ah + o, bl + o, idesc, 1);
-                    mma_tf32(tmem, al + o, bh + o, idesc, 1);
+                    for (int kk = 0; kk < TC_BK / 8; ++kk) {
+                        const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 8 TF32 values = 32 bytes
+                        mma_tf32(d, ah + o, bh + o, idesc, (ch | kk) != 0);
+                        mma_tf32(d, ah + o, bl + o, idesc, 1);
+                        mma_tf32(d, al + o, bh + o, idesc, 1);
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));
                 }
-                mma_commit(smem_u32(&empty_bar[s]));
+                mma_commit(smem_u32(&tfull_bar[b]));
+                ++j;
             }
-            mma_commit(smem_u32(&acc_bar));
         }
     } else {
-        // Epilogue: warp w reads TMEM lanes [32w, 32w + 32) = tile rows.
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_bar), 0));
-        tc_fence_after();
-        const int r = m0 + warp * 32 + lane;
-        const bool rv = ok && r < a.M;
-        float* Ob = a.O + box * a.sO;
-        const float* srow = nullptr;
-        if (rv) {
-            if (a.mode == GM_ACC) srow = Ob + (long long)r * a.ldo;
-            else if (a.mode == GM_FWD) {
-                if (r >= a.split) {
-                    const int pr = a.perm[box * a.sP + r];
-                    srow = (pr >= a.split) ? Ob + (long long)r * a.ldo : a.W + box * a.sW + (long long)pr * a.ldw;
-                }
-            } else if (a.mode == GM_BWD) {
-                if (r < a.split) srow = Ob + (long long)r * a.ldo;
+        // Epilogue warps 2..5 own TMEM lane quarter (warp % 4): tile row 32*qd + lane.
+        // Each thread streams its row in 32-column chunks (8 x float4), with the
+        // next chunk's source values loaded before the current one is stored.
+        const int qd = warp & 3;
+        uint32_t j = 0;
+        for (int t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+            const int box = t / per_box, rem = t - box * per_box;
+            if (a.skip && a.skip[box]) continue;
+            const int m0 = (rem / a.tiles_n) * TC_BM, n0 = (rem % a.tiles_n) * TC_BN;
+            const int b = j & 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1));
+            if (!ok) {
+                if (lane == 0) fail_sh = 1;
+                break;
             }
-        }
-        float* orow = Ob + (long long)r * a.ldo;
-        if (ok) {
-#pragma unroll 1
-            for (int j0 = 0; j0 < TC_BN; j0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
-                if (rv) {
+            tc_fence_after();
+            const int myr = m0 + qd * 32 + lane;
+            const bool rv = myr < a.M;
+            float* Ob = a.O + box * a.sO;
+            const float* srow = nullptr;
+            if (rv) {
+                if (a.mode == GM_FWD) {
+                    if (myr >= a.split) {
+                        const int pr = a.perm[box * a.sP + myr];
+                        srow = (pr >= a.split) ? Ob + (long long)myr * a.ldo
+                                               : a.W + box * a.sW + (long long)pr * a.ldw;
+                    }
+                } else if (a.mode == GM_BWD) {
+                    if (myr < a.split) srow = Ob + (long long)myr * a.ldo;
+                } else if (a.mode == GM_ACC) {
+                    srow = Ob + (long long)myr * a.ldo;
+                }
+            }
+            float* orow = Ob + (long long)myr * a.ldo;
+            const int nchunks = min(TC_BN, a.N - n0 + 31) / 32;
+            float4 cur[8], nxt[8];
+            auto load_src = [&](int cb, float4 (&dst)[8]) {
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const int c = n0 + j0 + jj;
-                        if (c < a.N) orow[c] = (srow ? srow[c] : 0.0f) - __uint_as_float(v[jj]);
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (rv && srow && a.vec && cb + 32 <= a.N) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dst[q] = *reinterpret_cast<const float4*>(srow + cb + 4 * q);
+                }
+            };
+            load_src(n0, cur);
+#pragma unroll 1
+            for (int cc = 0; cc < nchunks; ++cc) {
+                const int cb = n0 + cc * 32;
+                if (cc + 1 < nchunks) load_src(cb + 32, nxt);
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + cc * 32), v);
+                if (rv) {
+                    if (a.vec && cb + 32 <= a.N) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            float4 o;
+                            o.x = cur[q].x - __uint_as_float(v[4 * q + 0]);
+                            o.y = cur[q].y - __uint_as_float(v[4 * q + 1]);
+                            o.z = cur[q].z - __uint_as_float(v[4 * q + 2]);
+                            o.w = cur[q].w - __uint_as_float(v[4 * q + 3]);
+                            *reinterpret_cast<float4*>(orow + cb + 4 * q) = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const int col = cb + jj;
+                            if (col < a.N) orow[col] = (srow ? srow[col] : 0.0f) - __uint_as_float(v[jj]);
+                        }
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
             }
-        } else if (lane == 0) {
-            fail_sh = 1;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
+            ++j;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, TC_BN);
+        tmem_dealloc(tmem, 2 * TC_BN);
     }
-    if (threadIdx.x == 0 && fail_sh && a.status) a.status[box] = HPS_ETIMEOUT;
+    if (threadIdx.x == 0 && fail_sh && a.status)
+        for (int bx = 0; bx < (a.tiles + per_box - 1) / per_box; ++bx) atomicCAS(a.status + bx, 0, HPS_ETIMEOUT);
 }
 
 // dst = [hi plane | lo plane] of the first nb columns of src (rows x NB,
@@ -407,12 +478,21 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
         return false;
     TcArgs a = args;
     a.kch = (K + TC_BK - 1) / TC_BK;
-    static bool attr = false;
-    if (!attr) {
+    a.tiles_m = (a.M + TC_BM - 1) / TC_BM;
+    a.tiles_n = (a.N + TC_BN - 1) / TC_BN;
+    a.tiles = a.tiles_m * a.tiles_n * nbox;
+    const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) &&
+            (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        attr = true;
+        if (num_sms <= 0) num_sms = 1;
     }
-    dim3 grd((unsigned)((a.N + TC_BN - 1) / TC_BN), (unsigned)((a.M + TC_BM - 1) / TC_BM), (unsigned)nbox);
+    dim3 grd((unsigned)std::min(a.tiles, num_sms));
     prof_begin(KC_UPDATE_TC, st);
     k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, a);
     const double kk = (double)K;
