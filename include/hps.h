@@ -171,6 +171,28 @@ hps_status hps_assemble_interface_blocks(int p, const int nb[3], const double* T
  * NULL); synchronises the context's last stream. */
 hps_status hps_last_refinement(hps_ctx* ctx, int nbox, int* iters, double* rel_correction);
 
+/* FP64 DtN build (the same result as hps_leaf_build_dtn with HPS_FP64 and
+ * S = NULL) for callers that cannot allocate device memory: a host program
+ * whose GPU memory is owned by another allocator (for example a framework's
+ * caching allocator that has reserved the device), or a latency-critical loop
+ * where cudaMalloc/cudaFree would stall on an implicit device synchronisation.
+ * The paper has no counterpart; this is a deployment variant.
+ * It allocates nothing.  All scratch (operator tables, status words, the LU
+ * workspace) lives in one file-scope device array of 64 MiB that every GPU
+ * loading this library holds until the process exits.  The caller passes
+ * b[nbox][p^3], T[nbox][m][m] and optionally box_status[nbox] (device);
+ * batches larger than the scratch holds run in chunks on `stream`.
+ * Returns HPS_ENOMEM (nothing enqueued) when one box's workspace exceeds the
+ * scratch: p <= 13 fits (p = 12 needs ~24 MiB per box, p = 16 ~152 MiB); with
+ * box_status NULL the status words also come from the scratch (4 bytes/box).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind:
+ * calls that overlap on the GPU (concurrent streams, several host threads)
+ * race on it and must be serialised by the caller. */
+hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const double* b, double* T,
+                                      int* box_status, void* stream);
+
 /* Optional per-kernel timing.  hps_profile_enable(ctx, 1) makes the leaf calls
  * bracket every kernel launch with CUDA events on the caller's stream and
  * record each launch's algorithmic flops (2 M N K for an update product, the

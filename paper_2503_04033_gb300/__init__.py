@@ -22,7 +22,7 @@ __all__ = [
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
-    "EXPORTED_SYMBOLS", "KERNEL_CLASSES",
+    "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -34,6 +34,7 @@ EXPORTED_SYMBOLS = (
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
+    "hps_leaf_build_dtn_noalloc",
 )
 
 # Kernel classes of hps_profile_get.
@@ -93,6 +94,7 @@ def load_library() -> ctypes.CDLL:
         "hps_profile_reset": (i, [vp]),
         "hps_profile_get": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
         "hps_status_string": (ctypes.c_char_p, [i]),
+        "hps_leaf_build_dtn_noalloc": (i, [kp, i, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -267,3 +269,12 @@ def hps_profile_get(ctx, cls: int):
     _check(load_library().hps_profile_get(ctx, int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
                                           ctypes.byref(by)), "hps_profile_get")
     return n.value, ms.value, fl.value, by.value
+
+
+def hps_leaf_build_dtn_noalloc(kind: LeafKind, nbox: int, b, T, box_status=None, stream=None) -> None:
+    """FP64 DtN build that allocates no device memory (see include/hps.h)."""
+    f64 = _f64() if not isinstance(b, int) else None
+    _check(load_library().hps_leaf_build_dtn_noalloc(
+        ctypes.byref(kind), int(nbox), _ptr(b, f64), _ptr(T, f64),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_build_dtn_noalloc")

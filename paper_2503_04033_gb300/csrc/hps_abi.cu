@@ -97,15 +97,7 @@ struct hps_ctx {
     std::mutex mu;
 };
 
-namespace {
-
-#define HPS_CUDA_TRY(expr)                                   \
-    do {                                                     \
-        cudaError_t e_ = (expr);                             \
-        if (e_ != cudaSuccess) return HPS_ECUDA;             \
-    } while (0)
-
-bool valid_p(int p) { return p >= 3 && p <= kMaxP; }
+namespace hps {
 
 // ------------------------------------------------------------ 1-D operators
 
@@ -138,72 +130,6 @@ void cheb_diff(int p, double* D)
         }
         D[i * p + i] = -s;
     }
-}
-
-hps_status get_geometry(hps_ctx* ctx, const hps_leaf_kind* kind, Geometry** out)
-{
-    auto key = std::make_tuple(kind->p, kind->h[0], kind->h[1], kind->h[2]);
-    auto it = ctx->geoms.find(key);
-    if (it != ctx->geoms.end()) { *out = &it->second; return HPS_OK; }
-    Geometry g;
-    g.p = kind->p;
-    g.q = g.p - 2;
-    g.n = g.q * g.q * g.q;
-    g.m = 6 * g.q * g.q;
-    const int p = g.p, pp = p * p;
-    std::vector<double> Dhat(pp), D(3 * pp), D2(3 * pp);
-    cheb_diff(p, Dhat.data());
-    for (int a = 0; a < 3; ++a) {
-        g.h[a] = kind->h[a];
-        const double s = 2.0 / kind->h[a];
-        for (int e = 0; e < pp; ++e) D[a * pp + e] = s * Dhat[e];
-        for (int i = 0; i < p; ++i)
-            for (int j = 0; j < p; ++j) {
-                double acc = 0.0;
-                for (int l = 0; l < p; ++l) acc += D[a * pp + i * p + l] * D[a * pp + l * p + j];
-                D2[a * pp + i * p + j] = acc;
-            }
-    }
-    HPS_CUDA_TRY(cudaMalloc(&g.dD, sizeof(double) * 3 * pp));
-    HPS_CUDA_TRY(cudaMalloc(&g.dD2, sizeof(double) * 3 * pp));
-    HPS_CUDA_TRY(cudaMemcpy(g.dD, D.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
-    HPS_CUDA_TRY(cudaMemcpy(g.dD2, D2.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
-    auto res = ctx->geoms.emplace(key, g);
-    *out = &res.first->second;
-    return HPS_OK;
-}
-
-hps_status ensure_workspace(hps_ctx* ctx, const Plan& P, int nbox, int* chunk)
-{
-    size_t limit = ctx->ws_max;
-    if (limit == 0) {
-        size_t fr = 0, tot = 0;
-        HPS_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-        limit = ctx->ws_bytes + (size_t)(0.85 * (double)fr);
-    }
-    if (P.per_box > limit) return HPS_ENOMEM;
-    int c = (int)std::min<size_t>((size_t)nbox, limit / P.per_box);
-    const size_t need = P.per_box * (size_t)c;
-    if (need > ctx->ws_bytes) {
-        if (ctx->ws) { cudaDeviceSynchronize(); cudaFree(ctx->ws); ctx->ws = nullptr; ctx->ws_bytes = 0; }
-        if (cudaMalloc(&ctx->ws, need) != cudaSuccess) { cudaGetLastError(); return HPS_ENOMEM; }
-        ctx->ws_bytes = need;
-    }
-    *chunk = c;
-    return HPS_OK;
-}
-
-hps_status ensure_diag(hps_ctx* ctx, int nbox, cudaStream_t st)
-{
-    if ((size_t)nbox > ctx->diag_cap) {
-        if (ctx->d_iters) { cudaFree(ctx->d_iters); cudaFree(ctx->d_relcorr); }
-        HPS_CUDA_TRY(cudaMalloc(&ctx->d_iters, sizeof(int) * nbox));
-        HPS_CUDA_TRY(cudaMalloc(&ctx->d_relcorr, sizeof(double) * nbox));
-        ctx->diag_cap = nbox;
-    }
-    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int) * nbox, st));
-    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_relcorr, 0, sizeof(double) * nbox, st));
-    return HPS_OK;
 }
 
 // ------------------------------------------------------------ LU sequences
@@ -298,6 +224,90 @@ void lu_backward(const Plan& P, Work<T>& w, int nbox, int c0, int nc, const int*
         a.M = k + nb; a.N = nc; a.K = nb; a.mode = GM_BWD; a.split = k; a.skip = skip;
         launch_gemm<T>(a, nbox, st);
     }
+}
+
+template void lu_factor<double>(const Plan&, Work<double>&, int, int*, cudaStream_t);
+template void lu_factor<float>(const Plan&, Work<float>&, int, int*, cudaStream_t);
+template void lu_forward<float>(const Plan&, Work<float>&, int, int, int, const int*, cudaStream_t);
+template void lu_backward<double>(const Plan&, Work<double>&, int, int, int, const int*, cudaStream_t);
+template void lu_backward<float>(const Plan&, Work<float>&, int, int, int, const int*, cudaStream_t);
+
+}  // namespace hps
+
+namespace {
+
+#define HPS_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return HPS_ECUDA;             \
+    } while (0)
+
+bool valid_p(int p) { return p >= 3 && p <= kMaxP; }
+
+hps_status get_geometry(hps_ctx* ctx, const hps_leaf_kind* kind, Geometry** out)
+{
+    auto key = std::make_tuple(kind->p, kind->h[0], kind->h[1], kind->h[2]);
+    auto it = ctx->geoms.find(key);
+    if (it != ctx->geoms.end()) { *out = &it->second; return HPS_OK; }
+    Geometry g;
+    g.p = kind->p;
+    g.q = g.p - 2;
+    g.n = g.q * g.q * g.q;
+    g.m = 6 * g.q * g.q;
+    const int p = g.p, pp = p * p;
+    std::vector<double> Dhat(pp), D(3 * pp), D2(3 * pp);
+    cheb_diff(p, Dhat.data());
+    for (int a = 0; a < 3; ++a) {
+        g.h[a] = kind->h[a];
+        const double s = 2.0 / kind->h[a];
+        for (int e = 0; e < pp; ++e) D[a * pp + e] = s * Dhat[e];
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < p; ++l) acc += D[a * pp + i * p + l] * D[a * pp + l * p + j];
+                D2[a * pp + i * p + j] = acc;
+            }
+    }
+    HPS_CUDA_TRY(cudaMalloc(&g.dD, sizeof(double) * 3 * pp));
+    HPS_CUDA_TRY(cudaMalloc(&g.dD2, sizeof(double) * 3 * pp));
+    HPS_CUDA_TRY(cudaMemcpy(g.dD, D.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
+    HPS_CUDA_TRY(cudaMemcpy(g.dD2, D2.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
+    auto res = ctx->geoms.emplace(key, g);
+    *out = &res.first->second;
+    return HPS_OK;
+}
+
+hps_status ensure_workspace(hps_ctx* ctx, const Plan& P, int nbox, int* chunk)
+{
+    size_t limit = ctx->ws_max;
+    if (limit == 0) {
+        size_t fr = 0, tot = 0;
+        HPS_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        limit = ctx->ws_bytes + (size_t)(0.85 * (double)fr);
+    }
+    if (P.per_box > limit) return HPS_ENOMEM;
+    int c = (int)std::min<size_t>((size_t)nbox, limit / P.per_box);
+    const size_t need = P.per_box * (size_t)c;
+    if (need > ctx->ws_bytes) {
+        if (ctx->ws) { cudaDeviceSynchronize(); cudaFree(ctx->ws); ctx->ws = nullptr; ctx->ws_bytes = 0; }
+        if (cudaMalloc(&ctx->ws, need) != cudaSuccess) { cudaGetLastError(); return HPS_ENOMEM; }
+        ctx->ws_bytes = need;
+    }
+    *chunk = c;
+    return HPS_OK;
+}
+
+hps_status ensure_diag(hps_ctx* ctx, int nbox, cudaStream_t st)
+{
+    if ((size_t)nbox > ctx->diag_cap) {
+        if (ctx->d_iters) { cudaFree(ctx->d_iters); cudaFree(ctx->d_relcorr); }
+        HPS_CUDA_TRY(cudaMalloc(&ctx->d_iters, sizeof(int) * nbox));
+        HPS_CUDA_TRY(cudaMalloc(&ctx->d_relcorr, sizeof(double) * nbox));
+        ctx->diag_cap = nbox;
+    }
+    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int) * nbox, st));
+    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_relcorr, 0, sizeof(double) * nbox, st));
+    return HPS_OK;
 }
 
 // ------------------------------------------------------------ one chunk of a leaf call

@@ -215,6 +215,20 @@ void launch_recon_stored(const double* S, int n, int m, int nrhs, const double* 
 
 void launch_fill_int(int* p, int value, long long count, cudaStream_t st);
 
+// Host-side 1-D operators (hps_abi.cu): Chebyshev-Lobatto nodes on [-1,1] and
+// the spectral differentiation matrix (row-major p x p).
+void cheb_nodes(int p, double* t);
+void cheb_diff(int p, double* D);
+
+// CUDA-core LU sequences (hps_abi.cu): factorisation carrying the RHS block,
+// forward replay and backward substitution of RHS columns [c0, c0 + nc).
+template <typename T>
+void lu_factor(const Plan& P, Work<T>& w, int nbox, int* status, cudaStream_t st);
+template <typename T>
+void lu_forward(const Plan& P, Work<T>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st);
+template <typename T>
+void lu_backward(const Plan& P, Work<T>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st);
+
 // Tensor-core (tcgen05, 3-term TF32 split) versions of the LU sequences (hps_tc.cu).
 // They return false when a TMA descriptor cannot be encoded.  A tensor-core
 // launch whose bounded wait gave up raises a device-wide abort flag (checked

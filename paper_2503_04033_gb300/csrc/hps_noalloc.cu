@@ -1,0 +1,114 @@
+// hps_leaf_build_dtn_noalloc: the FP64 DtN build with no device allocation.
+//
+// Some callers cannot call cudaMalloc: a host application whose device
+// memory is owned by another allocator (for example a framework's caching
+// allocator that has already reserved the GPU), or a latency-critical loop in
+// which cudaMalloc/cudaFree would stall on an implicit device synchronisation.
+// This entry point serves them.  Its scratch memory (operator tables, status
+// words and the LU workspace) lives in one file-scope __device__ array of
+// kScratchBytes, which every GPU that loads this library holds until the
+// process exits.  The caller still passes b and T; nothing else is allocated.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hps_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = 64ull << 20;   // 64 MiB per device
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+hps_status scratch_address(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return HPS_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HPS_ECUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    return HPS_OK;
+}
+
+}  // namespace
+
+using namespace hps;
+
+extern "C" hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const double* b, double* T,
+                                                 int* box_status, void* stream)
+{
+    if (!kind || kind->p < 3 || kind->p > kMaxP || nbox < 0) return HPS_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(kind->h[a] > 0.0)) return HPS_EINVAL;
+    if (nbox == 0) return HPS_OK;
+    if (!b || !T) return HPS_EINVAL;
+    const int p = kind->p, q = p - 2, n = q * q * q, m = 6 * q * q, pp = p * p;
+    const long long p3 = (long long)pp * p;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // Scratch layout: [D | D2 | status words | per-box LU workspace x chunk].
+    const Plan P = make_plan(n, m, HPS_FP64, 0, false, false);
+    const size_t tables = align_up(2 * 3 * (size_t)pp * sizeof(double), 256);
+    const size_t fixed = tables + (box_status ? 0 : align_up((size_t)nbox * sizeof(int), 256));
+    if (fixed + P.per_box > kScratchBytes) return HPS_ENOMEM;   // one box does not fit: p (or nbox) too large
+    const int chunk = (int)std::min<size_t>((size_t)nbox, (kScratchBytes - fixed) / P.per_box);
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HPS_ECUDA;
+    unsigned char* base = nullptr;
+    hps_status rc = scratch_address(dev, &base);
+    if (rc != HPS_OK) return rc;
+
+    // Operator tables, computed on the host and copied into the scratch.
+    std::vector<double> Dhat(pp), DD(6 * (size_t)pp);
+    cheb_diff(p, Dhat.data());
+    for (int a = 0; a < 3; ++a) {
+        const double s = 2.0 / kind->h[a];
+        double* Da = DD.data() + a * pp;
+        double* D2a = DD.data() + 3 * pp + a * pp;
+        for (int e = 0; e < pp; ++e) Da[e] = s * Dhat[e];
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < p; ++l) acc += Da[i * p + l] * Da[l * p + j];
+                D2a[i * p + j] = acc;
+            }
+    }
+    Geometry g;
+    g.p = p; g.q = q; g.n = n; g.m = m;
+    for (int a = 0; a < 3; ++a) g.h[a] = kind->h[a];
+    g.dD = reinterpret_cast<double*>(base);
+    g.dD2 = g.dD + 3 * pp;
+    if (cudaMemcpyAsync(g.dD, DD.data(), DD.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return HPS_ECUDA;
+    // The copy source is pageable host memory: the call returns once it is staged.
+
+    // Status words must start at zero (the array keeps the previous call's contents).
+    int* status = box_status ? box_status : reinterpret_cast<int*>(base + tables);
+    if (cudaMemsetAsync(status, 0, sizeof(int) * nbox, st) != cudaSuccess) return HPS_ECUDA;
+
+    unsigned char* wbase = base + fixed;
+    for (int b0 = 0; b0 < nbox; b0 += chunk) {
+        const int nc = std::min(chunk, nbox - b0);
+        Work<double> w = carve<double>(P, wbase, nc);
+        launch_build_aug<double>(g, kind->kappa, nc, b + b0 * p3, p3, RHS_DTN, m, nullptr, 0, w.M, P.ldm, w.sM,
+                                 status + b0, -1, st);
+        lu_factor<double>(P, w, nc, status + b0, st);
+        lu_backward<double>(P, w, nc, n, m, nullptr, st);
+        launch_dn(g, nc, w.M + n, P.ldm, w.sM, m, T + (long long)b0 * m * m, (long long)m * m, 0, 1, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
