@@ -85,12 +85,19 @@ typedef struct {
 /* Tunables for hps_set_option (value is a double). */
 typedef enum {
     HPS_OPT_IR_MAX_ITERS = 1,   /* corrections in FP32_IR mode, default 8, range 0..20 */
-    HPS_OPT_IR_TOL = 2,         /* a box stops refining when ||dX||_F <= tol ||X||_F (default 1e-12),
+    HPS_OPT_IR_TOL = 2,         /* a box stops refining when its predicted remaining error is below tol
+                                   relative to ||X||_F (default 1e-12): ||dX_k|| min(1, 10 ||dX_k||/||dX_k-1||),
                                    or when ||dX|| is below 1e-11 ||X|| and shrank by less than half
                                    (the FP64 residual's noise floor); converged boxes skip later steps */
     HPS_OPT_BLOCK = 3,          /* LU block size NB: 0 = automatic, else 32, 64 or 128 */
     HPS_OPT_TENSOR_CORES = 4,   /* FP32 products on tcgen05 (1, default) or CUDA cores (0) */
     HPS_OPT_SYNC = 5,           /* 1: synchronise the stream and return the first box failure */
+    HPS_OPT_AUTOTUNE = 6,       /* 1: time the LU block candidates on each new (p, precision, tensor-core)
+                                   combination (on up to 8 of the call's boxes, synchronising the stream) and
+                                   keep the fastest; the choices persist in the file named by the
+                                   environment variable HPS_TUNE_CACHE, when set */
+    HPS_OPT_GRAPHS = 7,         /* 1: capture each distinct leaf call (same sizes, buffers and options) into a
+                                   CUDA graph on first use and replay the graph afterwards */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;
@@ -144,6 +151,34 @@ hps_status hps_leaf_reconstruct(hps_ctx* ctx, const hps_leaf_kind* kind, int nbo
                                 const double* b, const double* S, const double* v,
                                 const double* ub, double* ui,
                                 hps_precision prec, int* box_status, void* stream);
+
+/* One group of a mixed batch (Sec. 3.2: separate stacked arrays for each
+ * order p when p varies from box to box): boxes of one order p and side h,
+ * each with its own wavenumber.  T (and optionally S) request the DtN build;
+ * nrhs > 0 requests particular solutions for nrhs body loads per box.  Both
+ * come from ONE factorisation of each A_ii, whose right-hand side is
+ * [-A_ib | f_i].  Layouts as for the single-kind calls. */
+typedef struct {
+    int p;
+    double h[3];
+    int nbox;
+    const double* kappa;   /* host [nbox]: wavenumber of each box (finite) */
+    const double* b;       /* device [nbox][p^3] */
+    double* T;             /* device [nbox][m][m] or NULL (no DtN build) */
+    double* S;             /* device [nbox][n][m] or NULL */
+    int nrhs;              /* 0..256 loads per box */
+    const double* f;       /* device [nbox][nrhs][p^3] */
+    double* v;             /* device [nbox][nrhs][n] = A_ii^{-1} f_i */
+    double* hflux;         /* device [nbox][nrhs][m] = A_bi v */
+    int* box_status;       /* device [nbox] or NULL */
+} hps_leaf_group;
+
+/* Runs every group of a mixed batch on `stream` (groups in order, each in
+ * chunks of its workspace), with CUDA-graph replay and block autotuning when
+ * those options are on.  HPS_EINVAL for a bad group (order, sizes, pointers,
+ * non-finite kappa) or a group with neither T nor loads. */
+hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* groups, hps_precision prec,
+                           void* stream);
 
 /* Host helper for the interface system (Sec. 3.1: row and column index
  * arrays that align each T^tau with the global interface unknowns; Fig. 5).
@@ -199,9 +234,12 @@ hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const
  * dense method's count) and bytes.  hps_profile_get synchronises and returns,
  * for kernel class cls (0 operator build, 1 panel factorisation, 2 CUDA-core
  * update product, 3 tensor-core update product, 4 row gather / operand pack,
- * 5 FP64 refinement residual, 6 refinement update, 7 D_n product), the
- * accumulated launches, milliseconds, flops and bytes since the last reset.
- * Returns HPS_EINVAL for cls outside 0..7. */
+ * 5 FP64 refinement residual, 6 refinement update, 7 D_n product,
+ * 8 tensor-core update product of the refinement solves), the accumulated
+ * launches, milliseconds, flops and bytes since the last reset.  Refinement
+ * launches skip boxes that have converged, so classes 5, 6 and 8 count the
+ * work of every box and overstate flops and bytes.
+ * Returns HPS_EINVAL for cls outside 0..8. */
 hps_status hps_profile_enable(hps_ctx* ctx, int on);
 hps_status hps_profile_reset(hps_ctx* ctx);
 hps_status hps_profile_get(hps_ctx* ctx, int cls, long long* launches, double* ms, double* flops, double* bytes);

@@ -22,24 +22,26 @@ __all__ = [
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
-    "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc",
+    "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
+    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
 HPS_FP64, HPS_FP32_IR, HPS_BF16_IR = 0, 1, 2
 HPS_OPT_IR_MAX_ITERS, HPS_OPT_IR_TOL, HPS_OPT_BLOCK, HPS_OPT_TENSOR_CORES, HPS_OPT_SYNC = 1, 2, 3, 4, 5
+HPS_OPT_AUTOTUNE, HPS_OPT_GRAPHS = 6, 7
 HPS_OPT_TEST_SINGULAR_BOX = 100
 
 EXPORTED_SYMBOLS = (
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
-    "hps_leaf_build_dtn_noalloc",
+    "hps_leaf_build_dtn_noalloc", "hps_leaf_groups",
 )
 
 # Kernel classes of hps_profile_get.
 KERNEL_CLASSES = ("build", "panel", "update_cudacore", "update_tcgen05", "gather_pack", "residual_fp64",
-                  "refine_update", "dn_fp64")
+                  "refine_update", "dn_fp64", "update_tcgen05_refine")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -62,6 +64,14 @@ class LeafKind(ctypes.Structure):
     def __init__(self, p: int, h, kappa: float):
         hh = list(h) if hasattr(h, "__len__") else [h, h, h]
         super().__init__(int(p), (ctypes.c_double * 3)(*[float(x) for x in hh]), float(kappa))
+
+
+class LeafGroup(ctypes.Structure):
+    """hps_leaf_group: one order p / box size h of a mixed batch, per-box kappa."""
+    _fields_ = [("p", ctypes.c_int), ("h", ctypes.c_double * 3), ("nbox", ctypes.c_int),
+                ("kappa", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.c_void_p), ("T", ctypes.c_void_p),
+                ("S", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("f", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("hflux", ctypes.c_void_p), ("box_status", ctypes.c_void_p)]
 
 
 def load_library() -> ctypes.CDLL:
@@ -95,6 +105,7 @@ def load_library() -> ctypes.CDLL:
         "hps_profile_get": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), dp, dp, dp]),
         "hps_status_string": (ctypes.c_char_p, [i]),
         "hps_leaf_build_dtn_noalloc": (i, [kp, i, vp, vp, vp, vp]),
+        "hps_leaf_groups": (i, [vp, i, ctypes.POINTER(LeafGroup), i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -278,3 +289,32 @@ def hps_leaf_build_dtn_noalloc(kind: LeafKind, nbox: int, b, T, box_status=None,
         ctypes.byref(kind), int(nbox), _ptr(b, f64), _ptr(T, f64),
         _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
         _stream(stream)), "hps_leaf_build_dtn_noalloc")
+
+
+def hps_leaf_groups(ctx, groups, prec: int = HPS_FP32_IR, stream=None) -> None:
+    """groups: list of dicts with keys p, h, kappa (host sequence, one per box),
+    b, T (or None), S (or None), f/v/hflux (or None) and box_status (or None);
+    nbox is len(kappa) and nrhs is taken from v's shape."""
+    import numpy as np
+    arr = (LeafGroup * max(1, len(groups)))()
+    keep = []
+    f64 = _f64()
+    for i, g in enumerate(groups):
+        kap = np.ascontiguousarray(np.asarray(g["kappa"], dtype=np.float64))
+        keep.append(kap)
+        hh = g["h"] if hasattr(g["h"], "__len__") else [g["h"]] * 3
+        v = g.get("v")
+        arr[i].p = int(g["p"])
+        arr[i].h = (ctypes.c_double * 3)(*[float(x) for x in hh])
+        arr[i].nbox = int(len(kap))
+        arr[i].kappa = kap.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i].b = _ptr(g["b"], f64)
+        arr[i].T = _ptr(g.get("T"), f64)
+        arr[i].S = _ptr(g.get("S"), f64)
+        arr[i].nrhs = int(v.shape[1]) if v is not None else 0
+        arr[i].f = _ptr(g.get("f"), f64)
+        arr[i].v = _ptr(v, f64)
+        arr[i].hflux = _ptr(g.get("hflux"), f64)
+        bs = g.get("box_status")
+        arr[i].box_status = _ptr(bs, _i32() if bs is not None and not isinstance(bs, int) else None)
+    _check(load_library().hps_leaf_groups(ctx, len(groups), arr, int(prec), _stream(stream)), "hps_leaf_groups")

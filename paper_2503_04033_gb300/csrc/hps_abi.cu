@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -89,9 +90,18 @@ struct hps_ctx {
     int zero_row_box = -1;
     bool prof_on = false;
     hps::Profiler prof;
+    int autotune = 0;
+    int graphs = 0;
+    std::map<std::tuple<int, int, int>, int> nb_tuned;      // (p, precision, tensor cores) -> LU block
+    std::map<std::string, cudaGraphExec_t> graph_cache;     // captured calls
     int* d_iters = nullptr;
     double* d_relcorr = nullptr;
     size_t diag_cap = 0;
+    double* d_kappa = nullptr;
+    size_t kappa_cap = 0;
+    int* d_status = nullptr;
+    size_t status_cap = 0;
+    cudaStream_t cap_stream = nullptr;     // stream used only for graph capture
     int last_nbox = 0;
     cudaStream_t last_stream = nullptr;
     std::mutex mu;
@@ -244,22 +254,22 @@ namespace {
 
 bool valid_p(int p) { return p >= 3 && p <= kMaxP; }
 
-hps_status get_geometry(hps_ctx* ctx, const hps_leaf_kind* kind, Geometry** out)
+hps_status get_geometry(hps_ctx* ctx, int p, const double h[3], Geometry** out)
 {
-    auto key = std::make_tuple(kind->p, kind->h[0], kind->h[1], kind->h[2]);
+    auto key = std::make_tuple(p, h[0], h[1], h[2]);
     auto it = ctx->geoms.find(key);
     if (it != ctx->geoms.end()) { *out = &it->second; return HPS_OK; }
     Geometry g;
-    g.p = kind->p;
+    g.p = p;
     g.q = g.p - 2;
     g.n = g.q * g.q * g.q;
     g.m = 6 * g.q * g.q;
-    const int p = g.p, pp = p * p;
+    const int pp = p * p;
     std::vector<double> Dhat(pp), D(3 * pp), D2(3 * pp);
     cheb_diff(p, Dhat.data());
     for (int a = 0; a < 3; ++a) {
-        g.h[a] = kind->h[a];
-        const double s = 2.0 / kind->h[a];
+        g.h[a] = h[a];
+        const double s = 2.0 / h[a];
         for (int e = 0; e < pp; ++e) D[a * pp + e] = s * Dhat[e];
         for (int i = 0; i < p; ++i)
             for (int j = 0; j < p; ++j) {
@@ -277,7 +287,61 @@ hps_status get_geometry(hps_ctx* ctx, const hps_leaf_kind* kind, Geometry** out)
     return HPS_OK;
 }
 
-hps_status ensure_workspace(hps_ctx* ctx, const Plan& P, int nbox, int* chunk)
+void clear_graphs(hps_ctx* ctx)
+{
+    for (auto& kv : ctx->graph_cache) cudaGraphExecDestroy(kv.second);
+    ctx->graph_cache.clear();
+}
+
+// ------------------------------------------------------------ jobs
+
+// One homogeneous batch of a call: boxes of one order p and size h, with a
+// common wavenumber or one per box, and one kind of right-hand side.
+struct Job {
+    const Geometry* g = nullptr;
+    int nbox = 0;
+    double kappa = 0.0;
+    const double* kappa_dev = nullptr;   // device [nbox]: per-box wavenumber (NULL: kappa)
+    const double* b = nullptr;
+    int rhs_kind = RHS_DTN;
+    int nload = 0;                       // load columns (LOAD, DTN_LOAD) or trace columns (TRACE)
+    const double* rhs = nullptr;         // f [nbox][nload][p^3] or u_b [nbox][nload][m]
+    double* T = nullptr;
+    double* S = nullptr;
+    double* v = nullptr;
+    double* hf = nullptr;
+    double* ui = nullptr;
+    const double* vadd = nullptr;
+    int* status = nullptr;               // device [nbox]
+    int diag_off = 0;                    // offset into the refinement diagnostics
+    int nb = 0;                          // LU block (0: context default)
+    int zero_row_box = -1;               // test hook
+};
+
+int job_cols(const Job& j)
+{
+    if (j.rhs_kind == RHS_DTN) return j.g->m;
+    if (j.rhs_kind == RHS_DTN_LOAD) return j.g->m + j.nload;
+    return j.nload;
+}
+
+long long job_srhs(const Job& j)
+{
+    const long long p3 = (long long)j.g->p * j.g->p * j.g->p;
+    if (j.rhs_kind == RHS_LOAD || j.rhs_kind == RHS_DTN_LOAD) return j.nload * p3;
+    if (j.rhs_kind == RHS_TRACE) return (long long)j.nload * j.g->m;
+    return 0;
+}
+
+Plan job_plan(const hps_ctx* ctx, const Job& j, hps_precision prec)
+{
+    return make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64);
+}
+
+// Sizes the workspace for the largest chunk any job will run; all device
+// allocation of a call happens here, before any launch is enqueued.
+hps_status ensure_workspace(hps_ctx* ctx, const std::vector<Plan>& plans, const std::vector<Job>& jobs,
+                            std::vector<int>& chunk)
 {
     size_t limit = ctx->ws_max;
     if (limit == 0) {
@@ -285,71 +349,77 @@ hps_status ensure_workspace(hps_ctx* ctx, const Plan& P, int nbox, int* chunk)
         HPS_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
         limit = ctx->ws_bytes + (size_t)(0.85 * (double)fr);
     }
-    if (P.per_box > limit) return HPS_ENOMEM;
-    int c = (int)std::min<size_t>((size_t)nbox, limit / P.per_box);
-    const size_t need = P.per_box * (size_t)c;
+    size_t need = 0;
+    chunk.assign(jobs.size(), 0);
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        if (plans[i].per_box > limit) return HPS_ENOMEM;
+        chunk[i] = (int)std::min<size_t>((size_t)jobs[i].nbox, limit / plans[i].per_box);
+        need = std::max(need, plans[i].per_box * (size_t)chunk[i]);
+    }
     if (need > ctx->ws_bytes) {
-        if (ctx->ws) { cudaDeviceSynchronize(); cudaFree(ctx->ws); ctx->ws = nullptr; ctx->ws_bytes = 0; }
+        if (ctx->ws) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->ws);
+            ctx->ws = nullptr;
+            ctx->ws_bytes = 0;
+            clear_graphs(ctx);
+        }
         if (cudaMalloc(&ctx->ws, need) != cudaSuccess) { cudaGetLastError(); return HPS_ENOMEM; }
         ctx->ws_bytes = need;
     }
-    *chunk = c;
     return HPS_OK;
 }
 
-hps_status ensure_diag(hps_ctx* ctx, int nbox, cudaStream_t st)
+template <typename T>
+hps_status grow(T** p, size_t* cap, size_t count)
 {
-    if ((size_t)nbox > ctx->diag_cap) {
-        if (ctx->d_iters) { cudaFree(ctx->d_iters); cudaFree(ctx->d_relcorr); }
-        HPS_CUDA_TRY(cudaMalloc(&ctx->d_iters, sizeof(int) * nbox));
-        HPS_CUDA_TRY(cudaMalloc(&ctx->d_relcorr, sizeof(double) * nbox));
-        ctx->diag_cap = nbox;
-    }
-    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int) * nbox, st));
-    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_relcorr, 0, sizeof(double) * nbox, st));
+    if (count <= *cap) return HPS_OK;
+    if (*p) { cudaDeviceSynchronize(); cudaFree(*p); *p = nullptr; *cap = 0; }
+    HPS_CUDA_TRY(cudaMalloc(p, sizeof(T) * count));
+    *cap = count;
     return HPS_OK;
 }
 
-// ------------------------------------------------------------ one chunk of a leaf call
+// ------------------------------------------------------------ one chunk of a job
 
 struct CallSpec {
-    int rhs_kind;        // RhsKind
-    int r;               // RHS columns
-    const double* rhs;   // f or u_b (chunk base), NULL for DTN
-    long long s_rhs;     // per-box stride of rhs
-    int zero_row_box;    // test hook: chunk-local box whose A_ii gets a zero row (-1: none)
+    int rhs_kind;               // RhsKind
+    int r;                      // RHS columns
+    const double* rhs;          // f or u_b (chunk base), NULL for DTN
+    long long s_rhs;            // per-box stride of rhs
+    int zero_row_box;           // test hook: chunk-local box whose A_ii gets a zero row (-1: none)
+    const double* kappa_dev;    // chunk base of the per-box wavenumbers, or NULL
+    double kappa;
 };
 
-// Solves A_ii X = B for one chunk; the FP64 solution ends in X (ld = ldx,
-// per-box stride sX), in the caller's buffer or the workspace.
+// Solves A_ii X = B for one chunk.  FP64: the solution stays in M's RHS
+// columns.  FP32 + refinement: the FP64 solution is written to X.
 template <typename T>
-hps_status solve_chunk(hps_ctx* ctx, const Geometry& g, const hps_leaf_kind* kind, const Plan& P,
-                       Work<T>& w, int nbox, const double* b, const CallSpec& cs, double* X, long long ldx,
-                       long long sX, int* status, int* iters, double* relcorr, cudaStream_t st);
+hps_status solve_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, const Plan& P, Work<T>& w, int nbox,
+                       const double* b, double* X, long long ldx, long long sX, int* status, int* iters,
+                       double* relcorr, cudaStream_t st);
 
 template <>
-hps_status solve_chunk<double>(hps_ctx*, const Geometry& g, const hps_leaf_kind* kind, const Plan& P,
-                               Work<double>& w, int nbox, const double* b, const CallSpec& cs, double* X,
-                               long long ldx, long long sX, int* status, int*, double*, cudaStream_t st)
+hps_status solve_chunk<double>(hps_ctx*, const Geometry& g, const CallSpec& cs, const Plan& P, Work<double>& w,
+                               int nbox, const double* b, double*, long long, long long, int* status, int*, double*,
+                               cudaStream_t st)
 {
     const long long p3 = (long long)g.p * g.p * g.p;
-    launch_build_aug<double>(g, kind->kappa, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M, P.ldm, w.sM,
-                             status, cs.zero_row_box, st);
+    launch_build_aug<double>(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M, P.ldm,
+                             w.sM, status, cs.zero_row_box, st);
     lu_factor<double>(P, w, nbox, status, st);
     lu_backward<double>(P, w, nbox, g.n, cs.r, nullptr, st);
-    if (X) launch_extract<double>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st);
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 template <>
-hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const hps_leaf_kind* kind, const Plan& P,
-                              Work<float>& w, int nbox, const double* b, const CallSpec& cs, double* X,
-                              long long ldx, long long sX, int* status, int* iters, double* relcorr,
-                              cudaStream_t st)
+hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, const Plan& P, Work<float>& w,
+                              int nbox, const double* b, double* X, long long ldx, long long sX, int* status,
+                              int* iters, double* relcorr, cudaStream_t st)
 {
     const long long p3 = (long long)g.p * g.p * g.p;
-    launch_build_aug<float>(g, kind->kappa, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M, P.ldm, w.sM,
-                            status, cs.zero_row_box, st);
+    launch_build_aug<float>(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M, P.ldm,
+                            w.sM, status, cs.zero_row_box, st);
     if (P.tc) {
         tc_reset_abort(st);
         if (!tc_lu_factor(P, w, nbox, status, st)) return HPS_ECUDA;
@@ -365,7 +435,7 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const hps_leaf_ki
     HPS_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(double) * 2 * nbox, st));
     const int its = ctx->ir_iters;
     for (int it = 0; it < its; ++it) {
-        launch_residual(g, kind->kappa, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
+        launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
                         w.M + g.n, P.ldm, w.sM, w.skip, st);
         if (P.tc) {
             if (!tc_lu_forward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;
@@ -380,6 +450,201 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const hps_leaf_ki
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+// Everything a job enqueues: per chunk, the solve and the products that turn
+// the solution X into the requested outputs (T, S, v, h, u_i).
+template <typename T>
+hps_status enqueue_job(hps_ctx* ctx, const Job& j, const Plan& P, int chunk, cudaStream_t st)
+{
+    const Geometry& g = *j.g;
+    const int n = g.n, m = g.m, r = job_cols(j);
+    const long long p3 = (long long)g.p * g.p * g.p, s_rhs = job_srhs(j);
+    for (int b0 = 0; b0 < j.nbox; b0 += chunk) {
+        const int nc = std::min(chunk, j.nbox - b0);
+        Work<T> w = carve<T>(P, ctx->ws, nc);
+        CallSpec cs;
+        cs.rhs_kind = j.rhs_kind;
+        cs.r = r;
+        cs.rhs = j.rhs ? j.rhs + (long long)b0 * s_rhs : nullptr;
+        cs.s_rhs = s_rhs;
+        cs.zero_row_box = (j.zero_row_box >= b0 && j.zero_row_box < b0 + nc) ? j.zero_row_box - b0 : -1;
+        cs.kappa_dev = j.kappa_dev ? j.kappa_dev + b0 : nullptr;
+        cs.kappa = j.kappa;
+        double* X;
+        long long ldx, sX;
+        if (P.elt == 8) {
+            X = reinterpret_cast<double*>(w.M) + n;
+            ldx = P.ldm;
+            sX = w.sM;
+        } else {
+            X = w.X;
+            ldx = r;
+            sX = w.sX;
+        }
+        hps_status rc = solve_chunk<T>(ctx, g, cs, P, w, nc, j.b + (long long)b0 * p3, X, ldx, sX, j.status + b0,
+                                       ctx->d_iters + j.diag_off + b0, ctx->d_relcorr + j.diag_off + b0, st);
+        if (rc != HPS_OK) return rc;
+        if (j.rhs_kind == RHS_DTN || j.rhs_kind == RHS_DTN_LOAD) {
+            launch_dn(g, nc, X, ldx, sX, m, j.T + (long long)b0 * m * m, (long long)m * m, 0, 1, st);
+            if (j.S) launch_extract<double>(X, ldx, sX, n, m, j.S + (long long)b0 * n * m, m, (long long)n * m, nc, st);
+        }
+        if (j.rhs_kind == RHS_LOAD || j.rhs_kind == RHS_DTN_LOAD) {
+            const int off = j.rhs_kind == RHS_DTN_LOAD ? m : 0;
+            launch_transpose_add(X + off, ldx, sX, n, j.nload, nullptr, j.v + (long long)b0 * j.nload * n, nc, st);
+            launch_dn(g, nc, X + off, ldx, sX, j.nload, j.hf + (long long)b0 * j.nload * m, (long long)j.nload * m, 1,
+                      0, st);
+        }
+        if (j.rhs_kind == RHS_TRACE)
+            launch_transpose_add(X, ldx, sX, n, j.nload, j.vadd ? j.vadd + (long long)b0 * j.nload * n : nullptr,
+                                 j.ui + (long long)b0 * j.nload * n, nc, st);
+        if (cudaGetLastError() != cudaSuccess) return HPS_ECUDA;
+    }
+    return HPS_OK;
+}
+
+hps_status enqueue_all(hps_ctx* ctx, const std::vector<Job>& jobs, const std::vector<Plan>& plans,
+                       const std::vector<int>& chunk, hps_precision prec, int total, cudaStream_t st)
+{
+    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int) * total, st));
+    HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_relcorr, 0, sizeof(double) * total, st));
+    for (const Job& j : jobs) HPS_CUDA_TRY(cudaMemsetAsync(j.status, 0, sizeof(int) * j.nbox, st));
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        hps_status rc = prec == HPS_FP64 ? enqueue_job<double>(ctx, jobs[i], plans[i], chunk[i], st)
+                                         : enqueue_job<float>(ctx, jobs[i], plans[i], chunk[i], st);
+        if (rc != HPS_OK) return rc;
+    }
+    return HPS_OK;
+}
+
+// ------------------------------------------------------------ autotuning of the LU block
+
+std::string tune_file() { const char* e = std::getenv("HPS_TUNE_CACHE"); return e ? e : ""; }
+
+void load_tuning(hps_ctx* ctx)
+{
+    const std::string f = tune_file();
+    if (f.empty()) return;
+    FILE* fp = std::fopen(f.c_str(), "r");
+    if (!fp) return;
+    int p, prec, tc, nb;
+    while (std::fscanf(fp, "%d %d %d %d", &p, &prec, &tc, &nb) == 4) ctx->nb_tuned[std::make_tuple(p, prec, tc)] = nb;
+    std::fclose(fp);
+}
+
+void save_tuning(const hps_ctx* ctx)
+{
+    const std::string f = tune_file();
+    if (f.empty()) return;
+    FILE* fp = std::fopen(f.c_str(), "w");
+    if (!fp) return;
+    for (const auto& kv : ctx->nb_tuned)
+        std::fprintf(fp, "%d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                     kv.second);
+    std::fclose(fp);
+}
+
+// Picks the LU block size for (p, precision, tensor cores) by timing each
+// candidate on up to 8 of the job's own boxes (their outputs are rewritten by
+// the real run).  Synchronises the stream; never runs inside a capture.
+hps_status tune_job(hps_ctx* ctx, Job& j, hps_precision prec, cudaStream_t st)
+{
+    const auto key = std::make_tuple(j.g->p, (int)prec, ctx->use_tc);
+    auto it = ctx->nb_tuned.find(key);
+    if (it != ctx->nb_tuned.end()) { j.nb = it->second; return HPS_OK; }
+    const std::vector<int> cands = prec == HPS_FP64 ? std::vector<int>{32, 64} : std::vector<int>{64, 128};
+    Job trial = j;
+    trial.nbox = std::min(j.nbox, 8);
+    trial.zero_row_box = -1;
+    float best = 1e30f;
+    int best_nb = cands.back();
+    cudaEvent_t e0, e1;
+    HPS_CUDA_TRY(cudaEventCreate(&e0));
+    HPS_CUDA_TRY(cudaEventCreate(&e1));
+    for (int nb : cands) {
+        trial.nb = nb;
+        std::vector<Job> jobs{trial};
+        std::vector<Plan> plans{job_plan(ctx, trial, prec)};
+        std::vector<int> chunk;
+        hps_status rc = ensure_workspace(ctx, plans, jobs, chunk);
+        if (rc != HPS_OK) continue;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run warms the code paths
+            cudaEventRecord(e0, st);
+            rc = enqueue_all(ctx, jobs, plans, chunk, prec, trial.nbox, st);
+            cudaEventRecord(e1, st);
+            if (rc != HPS_OK) break;
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (rc == HPS_OK && ms < best) { best = ms; best_nb = nb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->nb_tuned[key] = best_nb;
+    save_tuning(ctx);
+    j.nb = best_nb;
+    return HPS_OK;
+}
+
+// ------------------------------------------------------------ running a call
+
+// Plan phase (geometry, tuning, workspace, diagnostics: every allocation),
+// then the enqueue phase, optionally through a cached CUDA graph.
+hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cudaStream_t st)
+{
+    int total = 0;
+    for (Job& j : jobs) {
+        j.diag_off = total;
+        total += j.nbox;
+    }
+    size_t cap_i = ctx->diag_cap, cap_d = ctx->diag_cap;
+    hps_status rc = grow(&ctx->d_iters, &cap_i, (size_t)total);
+    if (rc != HPS_OK) return rc;
+    rc = grow(&ctx->d_relcorr, &cap_d, (size_t)total);
+    if (rc != HPS_OK) return rc;
+    ctx->diag_cap = std::min(cap_i, cap_d);
+    if (ctx->autotune)
+        for (Job& j : jobs) {
+            rc = tune_job(ctx, j, prec, st);
+            if (rc != HPS_OK) return rc;
+        }
+    std::vector<Plan> plans;
+    for (const Job& j : jobs) plans.push_back(job_plan(ctx, j, prec));
+    std::vector<int> chunk;
+    rc = ensure_workspace(ctx, plans, jobs, chunk);
+    if (rc != HPS_OK) return rc;
+    const bool use_graph = ctx->graphs && !ctx->prof_on;
+    if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
+    std::ostringstream key;
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->ws << ' '
+        << ctx->d_iters << ' ' << ctx->d_relcorr;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const Job& j = jobs[i];
+        key << " | " << j.g->p << ' ' << j.g->h[0] << ' ' << j.g->h[1] << ' ' << j.g->h[2] << ' ' << j.nbox << ' '
+            << j.kappa << ' ' << j.kappa_dev << ' ' << j.b << ' ' << j.rhs_kind << ' ' << j.nload << ' ' << j.rhs
+            << ' ' << j.T << ' ' << j.S << ' ' << j.v << ' ' << j.hf << ' ' << j.ui << ' ' << j.vadd << ' '
+            << j.status << ' ' << plans[i].NB << ' ' << chunk[i] << ' ' << j.zero_row_box;
+    }
+    auto hit = ctx->graph_cache.find(key.str());
+    if (hit == ctx->graph_cache.end()) {
+        // Capture on the context's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); launch on the caller's.
+        if (!ctx->cap_stream) HPS_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        HPS_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_all(ctx, jobs, plans, chunk, prec, total, ctx->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc != HPS_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (ce != cudaSuccess) return HPS_ECUDA;
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return HPS_ECUDA;
+        hit = ctx->graph_cache.emplace(key.str(), exec).first;
+    }
+    HPS_CUDA_TRY(cudaGraphLaunch(hit->second, st));
+    return HPS_OK;
+}
+
 hps_status check_kind(const hps_leaf_kind* kind)
 {
     if (!kind || !valid_p(kind->p)) return HPS_EINVAL;
@@ -389,52 +654,20 @@ hps_status check_kind(const hps_leaf_kind* kind)
     return HPS_OK;
 }
 
-hps_status finish(hps_ctx* ctx, int nbox, int* box_status, cudaStream_t st)
+hps_status finish(hps_ctx* ctx, const std::vector<Job>& jobs, cudaStream_t st)
 {
     if (cudaGetLastError() != cudaSuccess) return HPS_ECUDA;
-    ctx->last_nbox = nbox;
+    int total = 0;
+    for (const Job& j : jobs) total += j.nbox;
+    ctx->last_nbox = total;
     ctx->last_stream = st;
     if (!ctx->sync) return HPS_OK;
     HPS_CUDA_TRY(cudaStreamSynchronize(st));
-    if (box_status && nbox > 0) {
-        std::vector<int> h(nbox);
-        HPS_CUDA_TRY(cudaMemcpy(h.data(), box_status, sizeof(int) * nbox, cudaMemcpyDeviceToHost));
+    for (const Job& j : jobs) {
+        std::vector<int> h(j.nbox);
+        HPS_CUDA_TRY(cudaMemcpy(h.data(), j.status, sizeof(int) * j.nbox, cudaMemcpyDeviceToHost));
         for (int v : h)
             if (v) return (hps_status)v;
-    }
-    return HPS_OK;
-}
-
-// Generic driver: chunks the batch and runs solve_chunk, then `post` per chunk.
-template <typename T, typename Post>
-hps_status run_solve(hps_ctx* ctx, const Geometry& g, const hps_leaf_kind* kind, hps_precision prec, int nbox,
-                     const double* b, int rhs_kind, int r, const double* rhs, long long s_rhs, double* Xuser,
-                     long long ldx_user, long long sX_user, int* box_status, cudaStream_t st, Post post)
-{
-    const bool need_x = (prec != HPS_FP64) && !Xuser;
-    Plan P = make_plan(g.n, r, prec, ctx->nb_opt, ctx->use_tc != 0, need_x || prec == HPS_FP64);
-    int chunk = 0;
-    hps_status rc = ensure_workspace(ctx, P, nbox, &chunk);
-    if (rc != HPS_OK) return rc;
-    rc = ensure_diag(ctx, nbox, st);
-    if (rc != HPS_OK) return rc;
-    int* status = box_status;
-    const long long p3 = (long long)g.p * g.p * g.p;
-    for (int b0 = 0; b0 < nbox; b0 += chunk) {
-        const int nc = std::min(chunk, nbox - b0);
-        Work<T> w = carve<T>(P, ctx->ws, nc);
-        int* stc = status + b0;
-        double* X;
-        long long ldx, sX;
-        if (Xuser) { X = Xuser + (long long)b0 * sX_user; ldx = ldx_user; sX = sX_user; }
-        else { X = w.X; ldx = r; sX = w.sX; }
-        const int zr = (ctx->zero_row_box >= b0 && ctx->zero_row_box < b0 + nc) ? ctx->zero_row_box - b0 : -1;
-        CallSpec cs{rhs_kind, r, rhs ? rhs + (long long)b0 * s_rhs : nullptr, s_rhs, zr};
-        rc = solve_chunk<T>(ctx, g, kind, P, w, nc, b + (long long)b0 * p3, cs, X, ldx, sX, stc,
-                            ctx->d_iters + b0, ctx->d_relcorr + b0, st);
-        if (rc != HPS_OK) return rc;
-        post(b0, nc, X, ldx, sX);
-        if (cudaGetLastError() != cudaSuccess) return HPS_ECUDA;
     }
     return HPS_OK;
 }
@@ -444,21 +677,42 @@ struct ProfScope {
     ~ProfScope() { hps::t_prof = nullptr; }
 };
 
-struct StatusBuf {
-    int* ptr = nullptr;
-    bool owned = false;
-    ~StatusBuf() { if (owned) cudaFree(ptr); }
-};
-
-hps_status prepare_status(int* user, int nbox, cudaStream_t st, StatusBuf& sb)
+// Status words: the caller's array, or a slice of the context's own.
+hps_status status_ptrs(hps_ctx* ctx, std::vector<Job>& jobs, const std::vector<int*>& user)
 {
-    if (user) sb.ptr = user;
-    else {
-        HPS_CUDA_TRY(cudaMalloc(&sb.ptr, sizeof(int) * (nbox > 0 ? nbox : 1)));
-        sb.owned = true;
+    size_t need = 0;
+    for (size_t i = 0; i < jobs.size(); ++i)
+        if (!user[i]) need += jobs[i].nbox;
+    hps_status rc = grow(&ctx->d_status, &ctx->status_cap, need > 0 ? need : 1);
+    if (rc != HPS_OK) return rc;
+    size_t off = 0;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        if (user[i]) jobs[i].status = user[i];
+        else { jobs[i].status = ctx->d_status + off; off += jobs[i].nbox; }
     }
-    HPS_CUDA_TRY(cudaMemsetAsync(sb.ptr, 0, sizeof(int) * nbox, st));
     return HPS_OK;
+}
+
+// Runs a single-kind call (the three leaf entry points).
+hps_status run_single(hps_ctx* ctx, Job j, const hps_leaf_kind* kind, hps_precision prec, int* box_status,
+                      void* stream)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope prof_scope(ctx);
+    Geometry* g = nullptr;
+    hps_status rc = get_geometry(ctx, kind->p, kind->h, &g);
+    if (rc != HPS_OK) return rc;
+    j.g = g;
+    j.kappa = kind->kappa;
+    j.zero_row_box = ctx->zero_row_box;
+    std::vector<Job> jobs{j};
+    rc = status_ptrs(ctx, jobs, {box_status});
+    if (rc != HPS_OK) return rc;
+    rc = run_jobs(ctx, jobs, prec, st);
+    if (rc != HPS_OK) return rc;
+    return finish(ctx, jobs, st);
 }
 
 }  // namespace
@@ -526,6 +780,7 @@ hps_status hps_create(hps_ctx** out, int device, size_t workspace_bytes_max)
     c->device = device;
     c->ws_max = workspace_bytes_max;
     if (const char* e = std::getenv("HPS_TENSOR_CORES")) c->use_tc = std::atoi(e) != 0;
+    load_tuning(c);
     *out = c;
     return HPS_OK;
 }
@@ -535,10 +790,14 @@ void hps_destroy(hps_ctx* ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    clear_graphs(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     for (auto& kv : ctx->geoms) { cudaFree(kv.second.dD); cudaFree(kv.second.dD2); }
     if (ctx->d_iters) cudaFree(ctx->d_iters);
     if (ctx->d_relcorr) cudaFree(ctx->d_relcorr);
+    if (ctx->d_kappa) cudaFree(ctx->d_kappa);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete ctx;
 }
@@ -565,6 +824,12 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
     case HPS_OPT_SYNC:
         ctx->sync = value != 0;
         return HPS_OK;
+    case HPS_OPT_AUTOTUNE:
+        ctx->autotune = value != 0;
+        return HPS_OK;
+    case HPS_OPT_GRAPHS:
+        ctx->graphs = value != 0;
+        return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;
         return HPS_OK;
@@ -581,30 +846,13 @@ hps_status hps_leaf_build_dtn(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox,
     if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
     if (!b || !T) return HPS_EINVAL;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ProfScope prof_scope(ctx);
-    Geometry* g = nullptr;
-    rc = get_geometry(ctx, kind, &g);
-    if (rc != HPS_OK) return rc;
-    StatusBuf sbuf;
-    rc = prepare_status(box_status, nbox, st, sbuf);
-    if (rc != HPS_OK) return rc;
-    const int n = g->n, m = g->m;
-    auto post = [&](int b0, int nc, double* X, long long ldx, long long sX) {
-        launch_dn(*g, nc, X, ldx, sX, m, T + (long long)b0 * m * m, (long long)m * m, 0, 1, st);
-    };
-    if (prec == HPS_FP64) {
-        // FP64: the solution stays in the working matrix; S (if wanted) is copied out.
-        rc = run_solve<double>(ctx, *g, kind, prec, nbox, b, RHS_DTN, m, nullptr, 0, S, m, (long long)n * m,
-                               sbuf.ptr, st, post);
-    } else {
-        rc = run_solve<float>(ctx, *g, kind, prec, nbox, b, RHS_DTN, m, nullptr, 0, S, m, (long long)n * m,
-                              sbuf.ptr, st, post);
-    }
-    if (rc != HPS_OK) return rc;
-    return finish(ctx, nbox, box_status, st);
+    Job j;
+    j.nbox = nbox;
+    j.b = b;
+    j.rhs_kind = RHS_DTN;
+    j.T = T;
+    j.S = S;
+    return run_single(ctx, j, kind, prec, box_status, stream);
 }
 
 hps_status hps_leaf_particular(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int nrhs, const double* b,
@@ -617,30 +865,15 @@ hps_status hps_leaf_particular(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox
     if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
     if (!b || !f || !v || !h) return HPS_EINVAL;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ProfScope prof_scope(ctx);
-    Geometry* g = nullptr;
-    rc = get_geometry(ctx, kind, &g);
-    if (rc != HPS_OK) return rc;
-    StatusBuf sbuf;
-    rc = prepare_status(box_status, nbox, st, sbuf);
-    if (rc != HPS_OK) return rc;
-    const int n = g->n, m = g->m;
-    const long long p3 = (long long)g->p * g->p * g->p;
-    auto post = [&](int b0, int nc, double* X, long long ldx, long long sX) {
-        launch_transpose_add(X, ldx, sX, n, nrhs, nullptr, v + (long long)b0 * nrhs * n, nc, st);
-        launch_dn(*g, nc, X, ldx, sX, nrhs, h + (long long)b0 * nrhs * m, (long long)nrhs * m, 1, 0, st);
-    };
-    if (prec == HPS_FP64)
-        rc = run_solve<double>(ctx, *g, kind, prec, nbox, b, RHS_LOAD, nrhs, f, nrhs * p3, nullptr, 0, 0, sbuf.ptr,
-                               st, post);
-    else
-        rc = run_solve<float>(ctx, *g, kind, prec, nbox, b, RHS_LOAD, nrhs, f, nrhs * p3, nullptr, 0, 0, sbuf.ptr,
-                              st, post);
-    if (rc != HPS_OK) return rc;
-    return finish(ctx, nbox, box_status, st);
+    Job j;
+    j.nbox = nbox;
+    j.b = b;
+    j.rhs_kind = RHS_LOAD;
+    j.nload = nrhs;
+    j.rhs = f;
+    j.v = v;
+    j.hf = h;
+    return run_single(ctx, j, kind, prec, box_status, stream);
 }
 
 hps_status hps_leaf_reconstruct(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int nrhs, const double* b,
@@ -653,33 +886,90 @@ hps_status hps_leaf_reconstruct(hps_ctx* ctx, const hps_leaf_kind* kind, int nbo
     if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
     if (!ub || !ui || (!S && !b)) return HPS_EINVAL;
+    if (S) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        HPS_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        ProfScope prof_scope(ctx);
+        const int q = kind->p - 2, n = q * q * q, m = 6 * q * q;
+        if (box_status) HPS_CUDA_TRY(cudaMemsetAsync(box_status, 0, sizeof(int) * nbox, st));
+        launch_recon_stored(S, n, m, nrhs, v, ub, ui, nbox, st);
+        if (cudaGetLastError() != cudaSuccess) return HPS_ECUDA;
+        ctx->last_nbox = 0;
+        ctx->last_stream = st;
+        return HPS_OK;
+    }
+    Job j;
+    j.nbox = nbox;
+    j.b = b;
+    j.rhs_kind = RHS_TRACE;
+    j.nload = nrhs;
+    j.rhs = ub;
+    j.ui = ui;
+    j.vadd = v;
+    return run_single(ctx, j, kind, prec, box_status, stream);
+}
+
+hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* groups, hps_precision prec,
+                           void* stream)
+{
+    if (!ctx || ngroups < 0 || (ngroups > 0 && !groups)) return HPS_EINVAL;
+    if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
+    size_t nk = 0;
+    for (int i = 0; i < ngroups; ++i) {
+        const hps_leaf_group& G = groups[i];
+        if (!valid_p(G.p) || G.nbox < 0 || G.nrhs < 0 || G.nrhs > 256) return HPS_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if (!(G.h[a] > 0.0) || !std::isfinite(G.h[a])) return HPS_EINVAL;
+        if (G.nbox == 0) continue;
+        if (!G.b || !G.kappa || (!G.T && G.nrhs == 0)) return HPS_EINVAL;
+        if (G.nrhs > 0 && (!G.f || !G.v || !G.hflux)) return HPS_EINVAL;
+        for (int bx = 0; bx < G.nbox; ++bx)
+            if (!std::isfinite(G.kappa[bx])) return HPS_EINVAL;
+        nk += G.nbox;
+    }
+    if (nk == 0) return HPS_OK;
     std::lock_guard<std::mutex> lk(ctx->mu);
     HPS_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ProfScope prof_scope(ctx);
-    Geometry* g = nullptr;
-    rc = get_geometry(ctx, kind, &g);
+    hps_status rc = grow(&ctx->d_kappa, &ctx->kappa_cap, nk);
     if (rc != HPS_OK) return rc;
-    StatusBuf sbuf;
-    rc = prepare_status(box_status, nbox, st, sbuf);
-    if (rc != HPS_OK) return rc;
-    const int n = g->n, m = g->m;
-    if (S) {
-        launch_recon_stored(S, n, m, nrhs, v, ub, ui, nbox, st);
-        return finish(ctx, nbox, box_status, st);
+    std::vector<double> kap;
+    kap.reserve(nk);
+    std::vector<Job> jobs;
+    std::vector<int*> user;
+    for (int i = 0; i < ngroups; ++i) {
+        const hps_leaf_group& G = groups[i];
+        if (G.nbox == 0) continue;
+        Geometry* g = nullptr;
+        rc = get_geometry(ctx, G.p, G.h, &g);
+        if (rc != HPS_OK) return rc;
+        Job j;
+        j.g = g;
+        j.nbox = G.nbox;
+        j.kappa_dev = ctx->d_kappa + kap.size();
+        kap.insert(kap.end(), G.kappa, G.kappa + G.nbox);
+        j.b = G.b;
+        j.T = G.T;
+        j.S = G.T ? G.S : nullptr;
+        if (G.T && G.nrhs > 0) j.rhs_kind = RHS_DTN_LOAD;
+        else if (G.T) j.rhs_kind = RHS_DTN;
+        else j.rhs_kind = RHS_LOAD;
+        j.nload = G.nrhs;
+        j.rhs = G.nrhs ? G.f : nullptr;
+        j.v = G.v;
+        j.hf = G.hflux;
+        jobs.push_back(j);
+        user.push_back(G.box_status);
     }
-    auto post = [&](int b0, int nc, double* X, long long ldx, long long sX) {
-        launch_transpose_add(X, ldx, sX, n, nrhs, v ? v + (long long)b0 * nrhs * n : nullptr,
-                             ui + (long long)b0 * nrhs * n, nc, st);
-    };
-    if (prec == HPS_FP64)
-        rc = run_solve<double>(ctx, *g, kind, prec, nbox, b, RHS_TRACE, nrhs, ub, (long long)nrhs * m, nullptr, 0,
-                               0, sbuf.ptr, st, post);
-    else
-        rc = run_solve<float>(ctx, *g, kind, prec, nbox, b, RHS_TRACE, nrhs, ub, (long long)nrhs * m, nullptr, 0,
-                              0, sbuf.ptr, st, post);
+    // Per-box wavenumbers go to the device outside any captured graph.
+    HPS_CUDA_TRY(cudaMemcpyAsync(ctx->d_kappa, kap.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+    rc = status_ptrs(ctx, jobs, user);
     if (rc != HPS_OK) return rc;
-    return finish(ctx, nbox, box_status, st);
+    rc = run_jobs(ctx, jobs, prec, st);
+    if (rc != HPS_OK) return rc;
+    return finish(ctx, jobs, st);
 }
 
 hps_status hps_profile_enable(hps_ctx* ctx, int on)

@@ -17,7 +17,7 @@ constexpr int kPanelThreads = 512;   // threads of the panel-factorisation CTA
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-enum RhsKind { RHS_DTN = 0, RHS_LOAD = 1, RHS_TRACE = 2 };
+enum RhsKind { RHS_DTN = 0, RHS_LOAD = 1, RHS_TRACE = 2, RHS_DTN_LOAD = 3 };
 
 // Update-product epilogue modes (see gemm description in hps_kernels.cuh).
 enum GemmMode { GM_SET = 0, GM_ACC = 1, GM_FWD = 2, GM_BWD = 3 };
@@ -158,7 +158,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
 // Kernel classes timed by the optional event profiler (HPS_OPT_PROFILE).
 enum KernelClass {
     KC_BUILD = 0, KC_PANEL, KC_UPDATE_CUDACORE, KC_UPDATE_TC, KC_GATHER, KC_RESIDUAL, KC_REFINE, KC_DN,
-    KC_COUNT
+    KC_UPDATE_TC_REFINE, KC_COUNT
 };
 
 // When profiling is on for the calling thread, prof_begin/prof_end bracket a
@@ -169,8 +169,8 @@ void prof_end(int cls, cudaStream_t st, double flops, double bytes);
 
 // Host launchers (hps_lu.cu).
 template <typename T>
-void launch_build_aug(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
-                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b,
+                      long long sb, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                       T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st);
 
 template <typename T>
@@ -195,7 +195,7 @@ template <typename TS>
 void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
                     double* X, long long ldx, long long sX, int nbox, cudaStream_t st);
 
-void launch_residual(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
+void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
                      float* R, long long ldr, long long sR, const int* skip, cudaStream_t st);

@@ -44,7 +44,8 @@ __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 // the face nodes on its three grid lines), loads f_i, or -A_ib u_b.
 template <typename T>
 __global__ void k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
-                            double kappa2, const double* __restrict__ b, long long sb, int rhs_kind,
+                            double kappa2, const double* __restrict__ kappa_box,
+                            const double* __restrict__ b, long long sb, int rhs_kind,
                             const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M,
                             long long ldm, long long sM, int* status, int zero_row_box)
 {
@@ -66,10 +67,16 @@ __global__ void k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* 
         if (r == c) {
             const double bv = __ldg(b + box * sb + i + p * j + pp * k);
             if (!isfinite(bv)) status[box] = HPS_EINVAL;
-            v -= kappa2 * bv;
+            const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
+            v -= k2 * bv;
         }
     } else if (c < n + nrhs) {
-        const int cf = c - n;
+        int cf = c - n;
+        if (rhs_kind == RHS_DTN_LOAD) {
+            // [-A_ib | f_i]: the first m columns are the DtN block, the rest loads.
+            if (cf < 6 * qq) rhs_kind = RHS_DTN;
+            else { rhs_kind = RHS_LOAD; cf -= 6 * qq; }
+        }
         if (rhs_kind == RHS_DTN) {
             // -A_ib: face node (f, a, bb) couples to the interior row on its line.
             const int f = cf / qq, s = cf % qq, a = s % q + 1, bb = s / q + 1;
@@ -446,7 +453,8 @@ __global__ void k_extract(const TS* __restrict__ src, long long lds, long long s
 // columns of X for one box in shared memory.  R is written in FP32 for the
 // correction solve.
 __global__ void k_residual(int p, int n, int nrhs, int ct, const double* __restrict__ D2, double kappa2,
-                           const double* __restrict__ b, long long sb, int rhs_kind,
+                           const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb,
+                           int rhs_kind,
                            const double* __restrict__ rhs, long long s_rhs, const double* __restrict__ X,
                            long long ldx, long long sX, float* __restrict__ R, long long ldr, long long sR,
                            const int* skip)
@@ -467,6 +475,7 @@ __global__ void k_residual(int p, int n, int nrhs, int ct, const double* __restr
     for (int idx = threadIdx.x; idx < 3 * pp; idx += blockDim.x) D2s[idx] = D2[idx];
     __syncthreads();
     const double* bb = b + box * sb;
+    const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
     for (int idx = threadIdx.x; idx < n * ct; idx += blockDim.x) {
         const int r = idx / ct, c = idx - r * ct;
         if (c >= nc) continue;
@@ -486,15 +495,20 @@ __global__ void k_residual(int p, int n, int nrhs, int ct, const double* __restr
         const double xv = Xs[r * ct + c];
         const int gi = i + p * j + pp * k;
         double bval;
-        const int cg = c0 + c;
-        if (rhs_kind == RHS_DTN) {
+        const int cw = c0 + c;          // column of R and X
+        int cg = cw, kind = rhs_kind;   // column of the right-hand side definition
+        if (kind == RHS_DTN_LOAD) {
+            if (cg < 6 * qq) kind = RHS_DTN;
+            else { kind = RHS_LOAD; cg -= 6 * qq; }
+        }
+        if (kind == RHS_DTN) {
             const int f = cg / qq, s = cg % qq, a = s % q + 1, b2 = s / q + 1;
             const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
             bval = 0.0;
             if (axis == 0 && j == a && k == b2) bval = rx[e];
             else if (axis == 1 && i == a && k == b2) bval = ry[e];
             else if (axis == 2 && i == a && j == b2) bval = rz[e];
-        } else if (rhs_kind == RHS_LOAD) {
+        } else if (kind == RHS_LOAD) {
             bval = rhs[box * s_rhs + (long long)cg * p * pp + gi];
         } else {
             const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
@@ -503,8 +517,8 @@ __global__ void k_residual(int p, int n, int nrhs, int ct, const double* __restr
                  + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
         }
         // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
-        const double res = bval + lap + kappa2 * bb[gi] * xv;
-        R[box * sR + (long long)r * ldr + cg] = float(res);
+        const double res = bval + lap + k2 * bb[gi] * xv;
+        R[box * sR + (long long)r * ldr + cw] = float(res);
     }
 }
 
@@ -538,9 +552,12 @@ __global__ void k_ir_update(const float* __restrict__ D, long long ldd, long lon
     }
 }
 
-// Per-box stopping rule of the refinement: converged when the correction is
-// below tol relative to X, or when it has stopped shrinking (less than a halving)
-// while already below stag_tol, i.e. X sits at the FP64 residual's noise floor.
+// Per-box stopping rule of the refinement.  After correction k (relative size
+// rel_k = ||dX_k|| / ||X||) the remaining error is about rho * rel_k, with the
+// contraction rho estimated by rel_k / rel_{k-1}; a box stops when that
+// prediction, with a factor 10 of margin, is below tol, or when the correction
+// has stopped shrinking (less than a halving) while already below stag_tol,
+// i.e. X sits at the FP64 residual's noise floor.
 __global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol, int last, int* skip, int* iters,
                            double* relcorr, int* status)
 {
@@ -553,8 +570,12 @@ __global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol,
     relcorr[box] = rel;
     norms[2 * box] = 0.0;
     norms[2 * box + 1] = 0.0;
-    const bool stagnated = iters[box] > 1 && rel <= stag_tol && rel > 0.5 * prev;
-    if (rel <= tol || stagnated) skip[box] = 1;
+    bool done = rel <= tol;
+    if (iters[box] > 1 && prev > 0.0) {
+        const double rho = rel / prev;
+        done = done || rel * fmin(1.0, 10.0 * rho) <= tol || (rel <= stag_tol && rho > 0.5);
+    }
+    if (done) skip[box] = 1;
     else if (last && status[box] == 0) status[box] = isfinite(rel) ? HPS_ENOCONV : HPS_EINVAL;
 }
 
@@ -608,14 +629,14 @@ __global__ void k_fill_int(int* p, int value, long long count)
 // ---------------------------------------------------------------- launchers
 
 template <typename T>
-void launch_build_aug(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
-                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b,
+                      long long sb, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                       T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st)
 {
     dim3 blk(32, 8);
     dim3 grd((unsigned)((ldm + 31) / 32), (unsigned)((g.n + 7) / 8), (unsigned)nbox);
     prof_begin(KC_BUILD, st);
-    k_build_aug<T><<<grd, blk, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, b, sb, rhs_kind,
+    k_build_aug<T><<<grd, blk, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind,
                                         rhs_src, s_rhs, M, ldm, sM, status, zero_row_box);
     prof_end(KC_BUILD, st, 0.0, (double)nbox * g.n * ldm * sizeof(T));
 }
@@ -629,7 +650,14 @@ void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int i
     const size_t s1 = (size_t)ib * (size_t)(n - k) * sizeof(T);
     const size_t s2 = (size_t)2 * nb * nb * sizeof(T);
     const size_t smem = s1 > s2 ? s1 : s2;
-    cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k_panel<T>);
+        cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(227 * 1024 - fa.sharedSizeBytes));
+        attr = true;
+    }
     prof_begin(KC_PANEL, st);
     k_panel<T><<<nbox, kPanelThreads, smem, st>>>(M, ldm, sM, n, k, nb, ib, perm, sP, Ftop, ldf, sF,
                                                   Btop, ldb, sB, status, skip);
@@ -689,7 +717,7 @@ void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols
     prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * (sizeof(TS) + 8));
 }
 
-void launch_residual(const Geometry& g, double kappa, int nbox, const double* b, long long sb,
+void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
                      float* R, long long ldr, long long sR, const int* skip, cudaStream_t st)
@@ -699,10 +727,14 @@ void launch_residual(const Geometry& g, double kappa, int nbox, const double* b,
     int ct = 16;
     while (ct > 1 && (size_t)g.n * ct * sizeof(double) > budget) ct >>= 1;
     const size_t smem = ((size_t)g.n * ct + (size_t)3 * g.p * g.p) * sizeof(double);
-    cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 16384);
+        attr = true;
+    }
     dim3 grd((unsigned)((nrhs + ct - 1) / ct), (unsigned)nbox);
     prof_begin(KC_RESIDUAL, st);
-    k_residual<<<grd, 512, smem, st>>>(g.p, g.n, nrhs, ct, g.dD2, kappa * kappa, b, sb, rhs_kind, rhs_src,
+    k_residual<<<grd, 512, smem, st>>>(g.p, g.n, nrhs, ct, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind, rhs_src,
                                        s_rhs, X, ldx, sX, R, ldr, sR, skip);
     prof_end(KC_RESIDUAL, st, (double)nbox * g.n * (double)nrhs * (6.0 * g.q + 4.0), (double)nbox * g.n * (double)nrhs * 12.0);
 }
@@ -748,11 +780,11 @@ void launch_fill_int(int* p, int value, long long count, cudaStream_t st)
     k_fill_int<<<blocks, 256, 0, st>>>(p, value, count);
 }
 
-template void launch_build_aug<float>(const Geometry&, double, int, const double*, long long, int, int,
-                                      const double*, long long, float*, long long, long long, int*, int,
+template void launch_build_aug<float>(const Geometry&, double, const double*, int, const double*, long long, int,
+                                      int, const double*, long long, float*, long long, long long, int*, int,
                                       cudaStream_t);
-template void launch_build_aug<double>(const Geometry&, double, int, const double*, long long, int, int,
-                                       const double*, long long, double*, long long, long long, int*, int,
+template void launch_build_aug<double>(const Geometry&, double, const double*, int, const double*, long long, int,
+                                       int, const double*, long long, double*, long long, long long, int*, int,
                                        cudaStream_t);
 template void launch_panel<float>(float*, long long, long long, int, int, int, int, int*, long long, float*,
                                   long long, long long, float*, long long, long long, int*, const int*, int,

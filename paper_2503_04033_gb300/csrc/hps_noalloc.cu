@@ -104,7 +104,7 @@ extern "C" hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int 
     for (int b0 = 0; b0 < nbox; b0 += chunk) {
         const int nc = std::min(chunk, nbox - b0);
         Work<double> w = carve<double>(P, wbase, nc);
-        launch_build_aug<double>(g, kind->kappa, nc, b + b0 * p3, p3, RHS_DTN, m, nullptr, 0, w.M, P.ldm, w.sM,
+        launch_build_aug<double>(g, kind->kappa, nullptr, nc, b + b0 * p3, p3, RHS_DTN, m, nullptr, 0, w.M, P.ldm, w.sM,
                                  status + b0, -1, st);
         lu_factor<double>(P, w, nc, status + b0, st);
         lu_backward<double>(P, w, nc, n, m, nullptr, st);
