@@ -30,7 +30,7 @@ constexpr int TC_BM = 128;                                  // tile rows = TMEM 
 constexpr int TC_BN = 256;                                  // tile columns = TMEM columns per buffer
 constexpr int TC_BK = 32;                                   // FP32 values per 128-byte row
 constexpr int TC_STAGES = 2;
-constexpr int TC_EPI_WARPS = 8;                             // two per TMEM lane quarter
+constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 16 KiB
 constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 32 KiB
@@ -298,14 +298,14 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
         }
     } else {
-        // Epilogue warps 2..9: warp w owns TMEM lane quarter qd = w % 4 (tile
-        // rows 32 qd .. 32 qd + 31) and half hf = (w - 2) / 4 of the columns.
+        // Epilogue warps 2..5: warp w owns TMEM lane quarter qd = w % 4 (tile
+        // rows 32 qd .. 32 qd + 31) and all TC_BN columns.
         // Each 32 x 32 accumulator chunk (thread = row) is transposed through
         // shared memory so that the warp then walks the 32 rows with lane =
         // column: every load and store of a row segment is one 128-byte line.
         // The 32 source loads of the next chunk are issued before the current
         // chunk is used.
-        const int qd = warp & 3, hf = (warp - 2) >> 2;
+        const int qd = warp & 3, hf = 0;
         float* tb = tbuf_all + (warp - 2) * TBUF_FLOATS;
         uint32_t j = 0;
         for (int t = blockIdx.x; t < a.tiles; t += gridDim.x) {
@@ -341,8 +341,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             const unsigned long long sp_bits = reinterpret_cast<unsigned long long>(srow);
             float* orow0 = Ob + (long long)row0 * a.ldo;
-            const int c_lo = n0 + hf * (TC_BN / 2);
-            const int nchunks = max(0, min(TC_BN / 2, a.N - c_lo) + 31) / 32;
+            const int c_lo = n0 + hf * TC_BN;
+            const int nchunks = max(0, min(TC_BN, a.N - c_lo) + 31) / 32;
             float cur[32], nxt[32];
             auto load_src = [&](int cb, float (&dst)[32]) {
                 const int col = cb + lane;
@@ -358,7 +358,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 const int cb = c_lo + cc * 32;
                 if (cc + 1 < nchunks) load_src(cb + 32, nxt);
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + hf * (TC_BN / 2) + cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + hf * TC_BN + cc * 32), v);
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) tb[lane * 32 + (jj ^ lane)] = __uint_as_float(v[jj]);
                 __syncwarp();
