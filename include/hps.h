@@ -180,6 +180,55 @@ typedef struct {
 hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* groups, hps_precision prec,
                            void* stream);
 
+/* ---- Learned low-rank DtN correction (beyond the paper, which always
+ * computes T exactly).  A three-layer MLP maps the p^3 samples of b of a box
+ * (input x = 2 (b - 1)) to factors U, V (m x rank); the predicted map is
+ * T_hat = T0 + s U V^T with T0 the DtN map of the same box for b = 1.
+ * Weights live in FP32 (master, Adam moments) and enter every product as
+ * BF16 with FP32 accumulation; all kernels are this library's own. */
+typedef struct hps_mlp hps_mlp;
+
+/* n_in -> n_h1 -> n_h2 -> 2 m rank, ReLU hidden layers, He-uniform weights
+ * from a splitmix64 stream seeded by `seed`. */
+hps_status hps_mlp_create(int device, int n_in, int n_h1, int n_h2, int m, int rank, unsigned long long seed,
+                          hps_mlp** out);
+void hps_mlp_destroy(hps_mlp* net);
+size_t hps_mlp_num_params(const hps_mlp* net);
+
+/* Copies all parameters (which = 0) or the last gradients (which = 1) as one
+ * FP32 host array W0, c0, W1, c1, W2, c2 (W_l row-major [in][out]); to_device
+ * = 1 loads parameters from the host instead (not allowed for gradients). */
+hps_status hps_mlp_copy_params(hps_mlp* net, int which, float* host, int to_device);
+
+/* U, V [B][m][rank] (device, FP64) from b_in [B][n_in] (device). */
+hps_status hps_mlp_forward(hps_mlp* net, int B, const double* b_in, double* U, double* V, void* stream);
+
+/* Gradients of L = mean over boxes and entries of (U V^T - (T - T0) / scale)^2
+ * for a batch b_in [B][n_in], exact maps T [B][m][m] and the b = 1 map
+ * T0 [m][m] (device); the loss is returned on the host when loss_out is
+ * non-NULL (this synchronises). */
+hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T, const double* T0, double scale,
+                        double* loss_out, void* stream);
+
+/* One Adam update with the last gradients. */
+hps_status hps_mlp_adam_step(hps_mlp* net, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* T[b] = T0 + scale U[b] V[b]^T (device, FP64; T0 [m][m] shared). */
+hps_status hps_lowrank_dtn(int nbox, int m, int rank, const double* T0, double scale, const double* U,
+                           const double* V, double* T, void* stream);
+
+/* Residual gate of predicted maps T_hat [nbox][m][m] (device) for boxes with
+ * coefficients b [nbox][p^3]: for nprobe seeded Gaussian traces phi per box
+ * (splitmix64 of seed and the element index, Box-Muller), T phi is computed as
+ * A_bb phi + A_bi w with A_ii w = -A_ib phi solved by `iters` Richardson steps
+ * preconditioned with the b = 1 block's inverse (FP64 LU, cached per
+ * (p, h, kappa)); err[box] = ||T_hat phi - T phi|| / ||T phi|| and accept[box]
+ * = 1 when err <= tol and the last Richardson step was below 1e-8 relative
+ * (device arrays).  Boxes that fail go to the exact path. */
+hps_status hps_dtn_gate(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const double* b, const double* T_hat,
+                        int nprobe, unsigned long long seed, int iters, double tol, int* accept, double* err,
+                        void* stream);
+
 /* Host helper for the interface system (Sec. 3.1: row and column index
  * arrays that align each T^tau with the global interface unknowns; Fig. 5).
  * Boxes form an nb[0] x nb[1] x nb[2] grid, box index bx + nx (by + ny bz).

@@ -23,7 +23,9 @@ __all__ = [
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
-    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS",
+    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
+    "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
+    "hps_dtn_gate",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -36,7 +38,9 @@ EXPORTED_SYMBOLS = (
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
-    "hps_leaf_build_dtn_noalloc", "hps_leaf_groups",
+    "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
+    "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
+    "hps_dtn_gate",
 )
 
 # Kernel classes of hps_profile_get.
@@ -106,6 +110,15 @@ def load_library() -> ctypes.CDLL:
         "hps_status_string": (ctypes.c_char_p, [i]),
         "hps_leaf_build_dtn_noalloc": (i, [kp, i, vp, vp, vp, vp]),
         "hps_leaf_groups": (i, [vp, i, ctypes.POINTER(LeafGroup), i, vp]),
+        "hps_mlp_create": (i, [i, i, i, i, i, i, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
+        "hps_mlp_destroy": (None, [vp]),
+        "hps_mlp_num_params": (sz, [vp]),
+        "hps_mlp_copy_params": (i, [vp, i, ctypes.POINTER(ctypes.c_float), i]),
+        "hps_mlp_forward": (i, [vp, i, vp, vp, vp, vp]),
+        "hps_mlp_grad": (i, [vp, i, vp, vp, vp, d, dp, vp]),
+        "hps_mlp_adam_step": (i, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]),
+        "hps_lowrank_dtn": (i, [i, i, i, vp, d, vp, vp, vp, vp]),
+        "hps_dtn_gate": (i, [vp, kp, i, vp, vp, i, ctypes.c_ulonglong, i, d, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -318,3 +331,66 @@ def hps_leaf_groups(ctx, groups, prec: int = HPS_FP32_IR, stream=None) -> None:
         bs = g.get("box_status")
         arr[i].box_status = _ptr(bs, _i32() if bs is not None and not isinstance(bs, int) else None)
     _check(load_library().hps_leaf_groups(ctx, len(groups), arr, int(prec), _stream(stream)), "hps_leaf_groups")
+
+
+# ---- learned low-rank correction and its residual gate
+
+def hps_mlp_create(device: int, n_in: int, n_h1: int, n_h2: int, m: int, rank: int, seed: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().hps_mlp_create(int(device), int(n_in), int(n_h1), int(n_h2), int(m), int(rank),
+                                         int(seed), ctypes.byref(h)), "hps_mlp_create")
+    return h.value
+
+
+def hps_mlp_destroy(net) -> None:
+    load_library().hps_mlp_destroy(net)
+
+
+def hps_mlp_num_params(net) -> int:
+    return int(load_library().hps_mlp_num_params(net))
+
+
+def hps_mlp_copy_params(net, which: int = 0, host=None, to_device: bool = False):
+    """which = 0 parameters, 1 gradients; returns the host FP32 array (or loads
+    `host` into the network when to_device)."""
+    import numpy as np
+    if host is None:
+        host = np.empty(hps_mlp_num_params(net), dtype=np.float32)
+    host = np.ascontiguousarray(host, dtype=np.float32)
+    _check(load_library().hps_mlp_copy_params(net, int(which), host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              int(bool(to_device))), "hps_mlp_copy_params")
+    return host
+
+
+def hps_mlp_forward(net, B: int, b, U, V, stream=None) -> None:
+    f64 = _f64()
+    _check(load_library().hps_mlp_forward(net, int(B), _ptr(b, f64), _ptr(U, f64), _ptr(V, f64), _stream(stream)),
+           "hps_mlp_forward")
+
+
+def hps_mlp_grad(net, B: int, b, T, T0, scale: float, want_loss: bool = True, stream=None):
+    f64 = _f64()
+    loss = ctypes.c_double()
+    _check(load_library().hps_mlp_grad(net, int(B), _ptr(b, f64), _ptr(T, f64), _ptr(T0, f64), float(scale),
+                                       ctypes.byref(loss) if want_loss else None, _stream(stream)), "hps_mlp_grad")
+    return loss.value if want_loss else None
+
+
+def hps_mlp_adam_step(net, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                      stream=None) -> None:
+    _check(load_library().hps_mlp_adam_step(net, float(lr), float(beta1), float(beta2), float(eps), _stream(stream)),
+           "hps_mlp_adam_step")
+
+
+def hps_lowrank_dtn(nbox: int, m: int, rank: int, T0, scale: float, U, V, T, stream=None) -> None:
+    f64 = _f64()
+    _check(load_library().hps_lowrank_dtn(int(nbox), int(m), int(rank), _ptr(T0, f64), float(scale), _ptr(U, f64),
+                                          _ptr(V, f64), _ptr(T, f64), _stream(stream)), "hps_lowrank_dtn")
+
+
+def hps_dtn_gate(ctx, kind: LeafKind, nbox: int, b, T_hat, nprobe: int, seed: int, iters: int, tol: float,
+                 accept, err, stream=None) -> None:
+    f64 = _f64()
+    _check(load_library().hps_dtn_gate(ctx, ctypes.byref(kind), int(nbox), _ptr(b, f64), _ptr(T_hat, f64),
+                                       int(nprobe), int(seed), int(iters), float(tol), _ptr(accept, _i32()),
+                                       _ptr(err, f64), _stream(stream)), "hps_dtn_gate")

@@ -102,6 +102,9 @@ struct hps_ctx {
     int* d_status = nullptr;
     size_t status_cap = 0;
     cudaStream_t cap_stream = nullptr;     // stream used only for graph capture
+    std::map<std::tuple<int, double, double, double, double>, float*> a0inv;   // gate preconditioners
+    void* gate_buf = nullptr;
+    size_t gate_cap = 0;
     int last_nbox = 0;
     cudaStream_t last_stream = nullptr;
     std::mutex mu;
@@ -798,6 +801,8 @@ void hps_destroy(hps_ctx* ctx)
     if (ctx->d_kappa) cudaFree(ctx->d_kappa);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (auto& kv : ctx->a0inv) cudaFree(kv.second);
+    if (ctx->gate_buf) cudaFree(ctx->gate_buf);
     for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete ctx;
 }
@@ -970,6 +975,115 @@ hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* grou
     rc = run_jobs(ctx, jobs, prec, st);
     if (rc != HPS_OK) return rc;
     return finish(ctx, jobs, st);
+}
+
+
+// The residual gate of a predicted DtN map (for the learned correction; the
+// paper has no counterpart).  For k seeded probe traces phi per box it forms
+// T phi = A_bb phi + A_bi w with A_ii w = -A_ib phi, solving for w by
+// Richardson iteration preconditioned with A0^{-1}, the interior block of the
+// same box with b = 1 (computed once per (p, h, kappa) with the FP64 LU and
+// kept in FP32); residuals are FP64 and matrix-free.  A box is accepted when
+// ||T_hat phi - T phi|| <= tol ||T phi|| and the iteration has converged.
+hps_status hps_dtn_gate(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const double* b, const double* T_hat,
+                        int nprobe, unsigned long long seed, int iters, double tol, int* accept, double* err,
+                        void* stream)
+{
+    if (!ctx || nbox < 0 || nprobe < 1 || nprobe > 64 || iters < 1 || iters > 200 || !(tol > 0)) return HPS_EINVAL;
+    hps_status rc = check_kind(kind);
+    if (rc != HPS_OK) return rc;
+    if (nbox == 0) return HPS_OK;
+    if (!b || !T_hat || !accept || !err) return HPS_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope prof_scope(ctx);
+    Geometry* g = nullptr;
+    rc = get_geometry(ctx, kind->p, kind->h, &g);
+    if (rc != HPS_OK) return rc;
+    const int p = g->p, n = g->n, m = g->m, k = nprobe;
+    const long long p3 = (long long)p * p * p;
+    const auto key = std::make_tuple(p, kind->h[0], kind->h[1], kind->h[2], kind->kappa);
+    auto it = ctx->a0inv.find(key);
+    if (it == ctx->a0inv.end()) {
+        // A0^{-1}: the FP64 LU of the b = 1 block applied to the identity (n loads).
+        double *ones = nullptr, *f = nullptr, *v = nullptr, *hf = nullptr;
+        float* inv = nullptr;
+        int* stt = nullptr;
+        bool ok = cudaMalloc(&ones, sizeof(double) * p3) == cudaSuccess &&
+                  cudaMalloc(&f, sizeof(double) * n * p3) == cudaSuccess &&
+                  cudaMalloc(&v, sizeof(double) * (size_t)n * n) == cudaSuccess &&
+                  cudaMalloc(&hf, sizeof(double) * (size_t)n * m) == cudaSuccess &&
+                  cudaMalloc(&inv, sizeof(float) * (size_t)n * n) == cudaSuccess &&
+                  cudaMalloc(&stt, sizeof(int)) == cudaSuccess;
+        if (ok) {
+            std::vector<double> h1(p3, 1.0);
+            cudaMemcpy(ones, h1.data(), sizeof(double) * p3, cudaMemcpyHostToDevice);
+            cudaMemsetAsync(f, 0, sizeof(double) * n * p3, st);
+            launch_identity_loads(p, n, f, st);
+            Job j;
+            j.g = g; j.nbox = 1; j.kappa = kind->kappa; j.b = ones; j.rhs_kind = RHS_LOAD; j.nload = n; j.rhs = f;
+            j.v = v; j.hf = hf; j.status = stt;
+            std::vector<Job> jobs{j};
+            const int gsave = ctx->graphs, tsave = ctx->autotune;
+            ctx->graphs = 0;
+            ctx->autotune = 0;
+            rc = run_jobs(ctx, jobs, HPS_FP64, st);
+            ctx->graphs = gsave;
+            ctx->autotune = tsave;
+            if (rc == HPS_OK) launch_transpose_f32(n, v, inv, st);
+            int hs = 0;
+            if (rc == HPS_OK && (cudaMemcpyAsync(&hs, stt, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                                 cudaStreamSynchronize(st) != cudaSuccess))
+                rc = HPS_ECUDA;
+            if (rc == HPS_OK && hs != 0) rc = (hps_status)hs;
+        } else {
+            cudaGetLastError();
+            rc = HPS_ENOMEM;
+        }
+        cudaFree(ones); cudaFree(f); cudaFree(v); cudaFree(hf); cudaFree(stt);
+        if (rc != HPS_OK) { cudaFree(inv); return rc; }
+        it = ctx->a0inv.emplace(key, inv).first;
+    }
+    // Workspace: probes, w (FP64) and R, delta (FP32) laid out [n][nbox k], probe products.
+    const size_t nk = (size_t)nbox * k;
+    const size_t b_phi = align_up(sizeof(double) * nk * m, 256), b_w = align_up(sizeof(double) * nk * n, 256);
+    const size_t b_r = align_up(sizeof(float) * nk * n, 256), b_tp = b_phi;
+    const size_t b_norm = align_up(sizeof(double) * 2 * nbox, 256);
+    const size_t need = b_phi + b_w + 2 * b_r + 2 * b_tp + b_norm;
+    if (need > ctx->gate_cap) {
+        if (ctx->gate_buf) { cudaDeviceSynchronize(); cudaFree(ctx->gate_buf); ctx->gate_buf = nullptr; ctx->gate_cap = 0; }
+        if (cudaMalloc(&ctx->gate_buf, need) != cudaSuccess) { cudaGetLastError(); return HPS_ENOMEM; }
+        ctx->gate_cap = need;
+    }
+    char* c = static_cast<char*>(ctx->gate_buf);
+    double* phi = reinterpret_cast<double*>(c); c += b_phi;
+    double* w = reinterpret_cast<double*>(c); c += b_w;
+    float* R = reinterpret_cast<float*>(c); c += b_r;
+    float* D = reinterpret_cast<float*>(c); c += b_r;
+    double* tp = reinterpret_cast<double*>(c); c += b_tp;
+    double* tph = reinterpret_cast<double*>(c); c += b_tp;
+    double* norms = reinterpret_cast<double*>(c);
+    launch_probes((long long)nk * m, seed, phi, st);
+    HPS_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * nk * n, st));
+    const long long ld = (long long)nk;   // row pitch of w, R, D: all boxes' probes side by side
+    for (int i = 0; i < iters; ++i) {
+        if (i == iters - 1) HPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nbox, st));
+        launch_residual(*g, kind->kappa, nullptr, nbox, b, p3, RHS_TRACE, k, phi, (long long)k * m, w, ld, k, R, ld, k,
+                        nullptr, st);
+        GemmArgs<float> a{};
+        a.A = it->second; a.lda = n; a.sA = 0;
+        a.B = R; a.ldb = ld; a.sB = 0;
+        a.O = D; a.ldo = ld; a.sO = 0;
+        a.M = n; a.N = (int)nk; a.K = n; a.alpha = 1.0f; a.mode = GM_SET;
+        launch_gemm<float>(a, 1, st);
+        launch_ir_update(D, ld, k, n, k, w, ld, k, norms, nullptr, nbox, st);
+    }
+    launch_dn(*g, nbox, w, ld, k, k, tp, (long long)k * m, 1, 0, st);
+    launch_abb_add(*g, nbox, k, phi, tp, st);
+    launch_apply_probes(m, k, nbox, T_hat, phi, tph, st);
+    launch_gate_decide(m, k, nbox, tph, tp, norms, tol, accept, err, st);
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 hps_status hps_profile_enable(hps_ctx* ctx, int on)

@@ -215,6 +215,15 @@ void launch_recon_stored(const double* S, int n, int m, int nrhs, const double* 
 
 void launch_fill_int(int* p, int value, long long count, cudaStream_t st);
 
+// Residual gate of the learned DtN correction (hps_lu.cu).
+void launch_probes(long long total, unsigned long long seed, double* phi, cudaStream_t st);
+void launch_abb_add(const Geometry& g, int nbox, int k, const double* phi, double* out, cudaStream_t st);
+void launch_apply_probes(int m, int k, int nbox, const double* That, const double* phi, double* tp, cudaStream_t st);
+void launch_gate_decide(int m, int k, int nbox, const double* tp_hat, const double* tp, const double* norms,
+                        double tol, int* accept, double* err, cudaStream_t st);
+void launch_identity_loads(int p, int n, double* f, cudaStream_t st);
+void launch_transpose_f32(int n, const double* in, float* out, cudaStream_t st);
+
 // Host-side 1-D operators (hps_abi.cu): Chebyshev-Lobatto nodes on [-1,1] and
 // the spectral differentiation matrix (row-major p x p).
 void cheb_nodes(int p, double* t);

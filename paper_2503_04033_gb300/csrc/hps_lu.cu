@@ -617,6 +617,121 @@ __global__ void k_recon_stored(const double* __restrict__ S, int n, int m, int n
     }
 }
 
+
+// ---------------------------------------------------------------- residual gate
+
+// Seeded Gaussian probe traces phi[box][j][r] (counter-based: splitmix64 of
+// (seed, box, j, r), Box-Muller), so any caller can regenerate them.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_probes(long long total, unsigned long long seed, double* __restrict__ phi)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long a = mix64(seed ^ mix64(2 * (unsigned long long)i));
+        const unsigned long long b = mix64(seed ^ mix64(2 * (unsigned long long)i + 1));
+        const double u1 = ((a >> 11) + 1) * 0x1.0p-53, u2 = (b >> 11) * 0x1.0p-53;
+        phi[i] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    }
+}
+
+// out[box][j][r] += (A_bb phi)[r]: the face row's own and opposite face node.
+__global__ void k_abb_add(int p, int m, int k, const double* __restrict__ D, const double* __restrict__ phi,
+                          double* __restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, box = blockIdx.z;
+    if (r >= m) return;
+    const int q = p - 2, qq = q * q;
+    const int f = r / qq, s = r - f * qq, axis = f >> 1;
+    const int e = (f & 1) ? p - 1 : 0, eo = (f & 1) ? 0 : p - 1;
+    const double sg = (f & 1) ? 1.0 : -1.0;
+    const double* Da = D + axis * p * p + e * p;
+    const double* ph = phi + ((long long)box * k + j) * m;
+    out[((long long)box * k + j) * m + r] += sg * (Da[e] * ph[r] + Da[eo] * ph[(f ^ 1) * qq + s]);
+}
+
+// tp[box][j][r] = sum_c That[box][r][c] phi[box][j][c]  (one warp per row r)
+__global__ void k_apply_probes(int m, int k, const double* __restrict__ That, const double* __restrict__ phi,
+                               double* __restrict__ tp)
+{
+    const int warps = blockDim.x >> 5;
+    const int r = blockIdx.x * warps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int box = blockIdx.y;
+    if (r >= m) return;
+    const double* row = That + ((long long)box * m + r) * m;
+    for (int j = 0; j < k; ++j) {
+        const double* ph = phi + ((long long)box * k + j) * m;
+        double acc = 0.0;
+        for (int c = lane; c < m; c += 32) acc += row[c] * ph[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) tp[((long long)box * k + j) * m + r] = acc;
+    }
+}
+
+// err = ||T_hat phi - T phi|| / ||T phi|| over the probes; accept when err <= tol
+// and the Richardson iteration for T phi has converged (last relative step <= 1e-8).
+__global__ void k_gate_decide(int m, int k, const double* __restrict__ tp_hat, const double* __restrict__ tp,
+                              const double* __restrict__ norms, double tol, int* __restrict__ accept,
+                              double* __restrict__ err)
+{
+    __shared__ double sd[32], sn[32];
+    const int box = blockIdx.x;
+    double d = 0.0, nn = 0.0;
+    for (int i = threadIdx.x; i < m * k; i += blockDim.x) {
+        const double a = tp_hat[(long long)box * m * k + i], b = tp[(long long)box * m * k + i];
+        d += (a - b) * (a - b);
+        nn += b * b;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d += __shfl_xor_sync(0xffffffffu, d, off);
+        nn += __shfl_xor_sync(0xffffffffu, nn, off);
+    }
+    if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = d; sn[threadIdx.x >> 5] = nn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double D2 = 0.0, N2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { D2 += sd[w]; N2 += sn[w]; }
+        const double e = N2 > 0.0 ? sqrt(D2 / N2) : INFINITY;
+        const double step = norms[2 * box + 1] > 0.0 ? sqrt(norms[2 * box] / norms[2 * box + 1]) : INFINITY;
+        err[box] = e;
+        accept[box] = (e <= tol && step <= 1e-8) ? 1 : 0;
+    }
+}
+
+// f[c][grid node of interior node c] = 1: the identity as n loads.
+__global__ void k_identity_loads(int p, int n, double* __restrict__ f)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int q = p - 2, i = c % q + 1, j = (c / q) % q + 1, k = c / (q * q) + 1;
+    f[(long long)c * p * p * p + i + p * j + p * p * k] = 1.0;
+}
+
+// out[r][c] = float(in[c][r]) (n x n)
+__global__ void k_transpose_f32(int n, const double* __restrict__ in, float* __restrict__ out)
+{
+    __shared__ double t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = by + y, c = bx + threadIdx.x;
+        if (r < n && c < n) t[y][threadIdx.x] = in[(long long)r * n + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = bx + y, c = by + threadIdx.x;
+        if (r < n && c < n) out[(long long)r * n + c] = float(t[threadIdx.x][y]);
+    }
+}
+
 __global__ void k_fill_int(int* p, int value, long long count)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -770,6 +885,41 @@ void launch_recon_stored(const double* S, int n, int m, int nrhs, const double* 
 {
     dim3 grd((unsigned)((n + 7) / 8), (unsigned)nbox);
     k_recon_stored<<<grd, 256, 0, st>>>(S, n, m, nrhs, v, ub, ui);
+}
+
+
+void launch_probes(long long total, unsigned long long seed, double* phi, cudaStream_t st)
+{
+    k_probes<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, st>>>(total, seed, phi);
+}
+
+void launch_abb_add(const Geometry& g, int nbox, int k, const double* phi, double* out, cudaStream_t st)
+{
+    dim3 grd((unsigned)((g.m + 127) / 128), (unsigned)k, (unsigned)nbox);
+    k_abb_add<<<grd, 128, 0, st>>>(g.p, g.m, k, g.dD, phi, out);
+}
+
+void launch_apply_probes(int m, int k, int nbox, const double* That, const double* phi, double* tp, cudaStream_t st)
+{
+    dim3 grd((unsigned)((m + 7) / 8), (unsigned)nbox);
+    k_apply_probes<<<grd, 256, 0, st>>>(m, k, That, phi, tp);
+}
+
+void launch_gate_decide(int m, int k, int nbox, const double* tp_hat, const double* tp, const double* norms,
+                        double tol, int* accept, double* err, cudaStream_t st)
+{
+    k_gate_decide<<<nbox, 256, 0, st>>>(m, k, tp_hat, tp, norms, tol, accept, err);
+}
+
+void launch_identity_loads(int p, int n, double* f, cudaStream_t st)
+{
+    k_identity_loads<<<(n + 255) / 256, 256, 0, st>>>(p, n, f);
+}
+
+void launch_transpose_f32(int n, const double* in, float* out, cudaStream_t st)
+{
+    dim3 grd((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+    k_transpose_f32<<<grd, dim3(32, 8), 0, st>>>(n, in, out);
 }
 
 void launch_fill_int(int* p, int value, long long count, cudaStream_t st)
