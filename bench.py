@@ -76,8 +76,12 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=("fourier16", "uneven"), default="fourier16",
-                    help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 loads")
+    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned"), default="fourier16",
+                    help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
+                         "loads; learned: the learned DtN correction at p=12")
+    ap.add_argument("--train-boxes", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--gate-tol", type=float, default=3e-3)
     return ap.parse_args()
 
 
@@ -304,10 +308,24 @@ def run_ours(args):
         sec = d["ms_per_step"] / 1e3
         bound = CLASS_BOUND.get(dom, "hbm")
         if bound == "tensor":
-            peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-            ach = d["flops"] / sec / 1e12
-            unit = "TFLOP/s"
-            note = f"TF32 dense peak = {src} sustained BF16 x 1.1/2.25; achieved counts 2MNK once (3 TF32 MMAs issued)"
+            # The 3-term TF32 split issues 3 MMAs per product: its useful peak is a third
+            # of the TF32 rate, and its ridge against HBM decides which roof binds.
+            tpeak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+            ai = d["flops"] / max(d["bytes"], 1.0)
+            ridge = tpeak / 3 * 1e12 / (peaks["hbm_gbs"] * 1e9)
+            if ai < ridge:
+                bound = "hbm"
+                peak = peaks["hbm_gbs"]
+                ach = d["bytes"] / sec / 1e9
+                unit = "GB/s"
+                note = (f"{src} HBM copy bandwidth; arithmetic intensity {ai:.1f} flop/B is below the 3xTF32 ridge "
+                        f"{ridge:.1f} flop/B (TF32 peak {tpeak:.0f} TFLOP/s / 3); tensor view: "
+                        f"{d['flops'] / sec / 1e12:.1f} TFLOP/s algorithmic")
+            else:
+                peak = tpeak
+                ach = d["flops"] / sec / 1e12
+                unit = "TFLOP/s"
+                note = f"TF32 dense peak = {src} sustained BF16 x 1.1/2.25; achieved counts 2MNK once (3 TF32 MMAs issued)"
         elif bound == "alu":
             fp64 = dom in ("residual_fp64", "dn_fp64") or prec == H.HPS_FP64
             peak = FP64_PEAK_TFLOPS if fp64 else FP32_CUDACORE_PEAK_TFLOPS
@@ -384,6 +402,92 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+LEARNED = ("p=12 boxes of side 1/8, kappa=20, one random Fourier-law b field per box; 20000 training boxes "
+           "(seed 1) with exact DtN maps from the FP32+refinement path, 4096 held-out boxes (seed 2); MLP "
+           "1728->512->512->2*600*32 (rank-32 factors), BF16 weights, FP32 accumulate, Adam")
+
+
+def fourier_fields_torch(fields, xyz, dev):
+    """[nfield, N] values of per-box b fields at the node coordinates [N, 3]
+    of a box at the origin, evaluated on the GPU (input generation only)."""
+    import torch
+    K = torch.tensor(np.stack([f.k for f in fields]), dtype=torch.float64, device=dev)     # [F, 16, 3]
+    A = torch.tensor(np.stack([f.a for f in fields]), dtype=torch.float64, device=dev)     # [F, 16]
+    Ph = torch.tensor(np.stack([f.phi for f in fields]), dtype=torch.float64, device=dev)  # [F, 16]
+    x = torch.from_numpy(xyz).to(dev)
+    out = []
+    for i in range(0, len(fields), 1024):
+        ph = 2 * math.pi * torch.einsum("nd,fqd->fnq", x, K[i:i + 1024]) + Ph[i:i + 1024, None, :]
+        out.append(torch.clamp(1.0 + 0.5 * (torch.cos(ph) * A[i:i + 1024, None, :]).sum(-1), 0.5, 1.5))
+    return torch.cat(out).contiguous()
+
+
+def run_learned(args):
+    """Train the learned DtN correction on exact maps, then serve the held-out
+    boxes through it (with the gate and exact fallback) and through the exact
+    reduction alone."""
+    import torch
+    import paper_2503_04033_gb300 as H
+    from paper_2503_04033_gb300.learned import LearnedDtN
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p, h, kappa = 12, 0.125, 20.0
+    xyz = H.hps_leaf_nodes(p, (0.0, 0.0, 0.0), (h, h, h))
+    ctx = H.hps_create(0, 0)
+    model = LearnedDtN(ctx, p, h, kappa, hidden=(512, 512), rank=32, seed=3)
+    b_tr = fourier_fields_torch(hi.fourier_b_per_box(args.train_boxes, hi.SEED_TRAIN), xyz, dev)
+    b_te = fourier_fields_torch(hi.fourier_b_per_box(4096, hi.SEED_HELDOUT), xyz, dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    ev[0].record()
+    T_tr = model.targets(b_tr)
+    ev[1].record()
+    losses = model.fit(b_tr, T_tr, epochs=args.epochs, batch=256, lr=1e-3)
+    ev[2].record()
+    del T_tr
+    T_te = model.targets(b_te)                        # reference maps for the error report
+    torch.cuda.synchronize()
+    t_data, t_fit = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+
+    def rel(A, B):
+        return ((A - B).flatten(1).norm(dim=1) / B.flatten(1).norm(dim=1)).cpu().numpy()
+
+    That = model.predict(b_te)
+    e_net, e_t0 = rel(That, T_te), rel(model.T0.expand_as(T_te), T_te)
+    tol = args.gate_tol
+    for _ in range(2):                                 # warm both paths
+        model.serve(b_te[:64], tol)
+        model.exact(b_te[:64])
+    torch.cuda.synchronize()
+    ev[3].record()
+    for _ in range(args.steps):
+        T_ex = model.exact(b_te)
+    ev[4].record()
+    for _ in range(args.steps):
+        T_sv, acc, err = model.serve(b_te, tol)
+    ev[5].record()
+    torch.cuda.synchronize()
+    ms_ex = ev[3].elapsed_time(ev[4]) / args.steps
+    ms_sv = ev[4].elapsed_time(ev[5]) / args.steps
+    acc_np = acc.cpu().numpy()
+    e_out = rel(T_sv, T_te)
+    line = {"metric": "learned DtN correction: held-out boxes/s served (surrogate + gate + exact fallback)",
+            "value": 4096 / (ms_sv / 1e3), "unit": "boxes/s", "n_gpus": 1, "steps": args.steps, "warmup": 2,
+            "ms_per_step": ms_sv, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 weights, f32 accumulate; exact path f32+f64", "data": "synthetic",
+            "config": {"workload": LEARNED, "train_boxes": args.train_boxes, "epochs": args.epochs,
+                       "gate_tol": tol, "gate_probes": 4},
+            "exact_path": {"value": 4096 / (ms_ex / 1e3), "unit": "boxes/s", "ms_per_step": ms_ex},
+            "accept_rate": float(acc_np.mean()),
+            "rel_err": {"T0_median": float(np.median(e_t0)), "surrogate_median": float(np.median(e_net)),
+                        "surrogate_p90": float(np.quantile(e_net, 0.9)), "served_max": float(e_out.max()),
+                        "served_max_accepted": float(e_out[acc_np == 1].max()) if acc_np.any() else None},
+            "training": {"data_s": t_data, "fit_s": t_fit, "loss_first": losses[0], "loss_last": losses[-1],
+                         "train_boxes_per_s": args.train_boxes * args.epochs / t_fit}}
+    model.close()
+    H.hps_destroy(ctx)
+    print(json.dumps(line), flush=True)
 
 
 UNEVEN = ("1024 leaf boxes (h=1/8) with p drawn from {8,12,16,20} and kappa from {10,20,40,60}, "
@@ -464,6 +568,8 @@ def main():
         run_reference(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

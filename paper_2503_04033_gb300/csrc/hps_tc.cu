@@ -27,7 +27,7 @@ namespace hps {
 namespace {
 
 constexpr int TC_BM = 128;                                  // tile rows = TMEM lanes
-constexpr int TC_BN = 256;                                  // tile columns = TMEM columns per buffer
+constexpr int TC_BN = 128;                                  // tile columns = TMEM columns per buffer
 constexpr int TC_BK = 32;                                   // FP32 values per 128-byte row
 constexpr int TC_STAGES = 2;
 constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
@@ -36,7 +36,9 @@ constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 16 KiB
 constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 32 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + TC_EPI_WARPS * TBUF_FLOATS * 4 + 1024;
+constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
+constexpr uint32_t EPI_FLOATS = TBUF_FLOATS * (1 + TC_PRE) + 64;   // transpose + source ring + row pointers
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + TC_EPI_WARPS * EPI_FLOATS * 4 + 1024;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
 
 struct TcArgs {
@@ -299,32 +301,29 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else {
         // Epilogue warps 2..5: warp w owns TMEM lane quarter qd = w % 4 (tile
-        // rows 32 qd .. 32 qd + 31) and all TC_BN columns.
-        // Each 32 x 32 accumulator chunk (thread = row) is transposed through
-        // shared memory so that the warp then walks the 32 rows with lane =
-        // column: every load and store of a row segment is one 128-byte line.
-        // The 32 source loads of the next chunk are issued before the current
-        // chunk is used.
-        const int qd = warp & 3, hf = 0;
-        float* tb = tbuf_all + (warp - 2) * TBUF_FLOATS;
+        // rows 32 qd .. 32 qd + 31).  The source rows of each 32 x 32 chunk are
+        // brought into shared memory with cp.async TC_PRE chunks ahead (lane =
+        // column, so every copy instruction reads one 128-byte line; absent rows
+        // and columns are zero-filled); the accumulator chunk (thread = row) is
+        // transposed through shared memory; then each row segment is written
+        // with one coalesced store.
+        const int qd = warp & 3;
+        float* eb = tbuf_all + (warp - 2) * EPI_FLOATS;
+        float* tb = eb;                                       // transpose buffer, XOR-swizzled
+        float* sb = eb + TBUF_FLOATS;                         // TC_PRE source chunks [32][32]
+        const float** sp = reinterpret_cast<const float**>(eb + TBUF_FLOATS * (1 + TC_PRE));
+        const uint32_t sb_u32 = smem_u32(sb);
         uint32_t j = 0;
         for (int t = blockIdx.x; t < a.tiles; t += gridDim.x) {
             const int box = t / per_box, rem = t - box * per_box;
             if (a.skip && a.skip[box]) continue;
             const int m0 = (rem / a.tiles_n) * TC_BM, n0 = (rem % a.tiles_n) * TC_BN;
-            const int b = j & 1;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1));
-            if (!ok) {
-                if (lane == 0) fail_sh = 1;
-                break;
-            }
-            tc_fence_after();
             const int row0 = m0 + qd * 32;
             const int rows_here = max(0, min(32, a.M - row0));
             float* Ob = a.O + box * a.sO;
-            const float* srow = nullptr;           // source row of tile row row0 + lane (NULL: zero)
             {
                 const int myr = row0 + lane;
+                const float* srow = nullptr;
                 if (lane < rows_here) {
                     if (a.mode == GM_FWD) {
                         if (myr >= a.split) {
@@ -338,41 +337,56 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         srow = Ob + (long long)myr * a.ldo;
                     }
                 }
+                sp[lane] = srow;
             }
-            const unsigned long long sp_bits = reinterpret_cast<unsigned long long>(srow);
-            float* orow0 = Ob + (long long)row0 * a.ldo;
-            const int c_lo = n0 + hf * TC_BN;
-            const int nchunks = max(0, min(TC_BN, a.N - c_lo) + 31) / 32;
-            float cur[32], nxt[32];
-            auto load_src = [&](int cb, float (&dst)[32]) {
-                const int col = cb + lane;
-#pragma unroll
+            __syncwarp();
+            const int nchunks = (min(TC_BN, a.N - n0) + 31) / 32;
+            auto prefetch = [&](int cc) {
+                const int col = n0 + cc * 32 + lane;
+                const uint32_t dst = sb_u32 + (uint32_t)(((cc % TC_PRE) * 1024 + lane) * 4);
+#pragma unroll 8
                 for (int rr = 0; rr < 32; ++rr) {
-                    const float* q = reinterpret_cast<const float*>(__shfl_sync(0xffffffffu, sp_bits, rr));
-                    dst[rr] = (q && col < a.N) ? q[col] : 0.0f;
+                    const float* q = sp[rr];
+                    const bool have = q != nullptr && col < a.N;
+                    const float* src = have ? q + col : Ob;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + rr * 128),
+                                 "l"(src), "r"(have ? 4 : 0)
+                                 : "memory");
                 }
             };
-            if (nchunks > 0) load_src(c_lo, cur);
+            for (int cc = 0; cc < TC_PRE - 1; ++cc) {
+                if (cc < nchunks) prefetch(cc);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
+            const int b = j & 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1));
+            if (!ok) {
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                if (lane == 0) fail_sh = 1;
+                break;
+            }
+            tc_fence_after();
+            float* orow0 = Ob + (long long)row0 * a.ldo;
 #pragma unroll 1
             for (int cc = 0; cc < nchunks; ++cc) {
-                const int cb = c_lo + cc * 32;
-                if (cc + 1 < nchunks) load_src(cb + 32, nxt);
+                if (cc + TC_PRE - 1 < nchunks) prefetch(cc + TC_PRE - 1);
+                asm volatile("cp.async.commit_group;" ::: "memory");
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + hf * TC_BN + cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + cc * 32), v);
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj) tb[lane * 32 + (jj ^ lane)] = __uint_as_float(v[jj]);
+                asm volatile("cp.async.wait_group %0;" ::"n"(TC_PRE - 1) : "memory");
                 __syncwarp();
-                const int col = cb + lane;
+                const float* sc = sb + (cc % TC_PRE) * 1024;
+                const int col = n0 + cc * 32 + lane;
                 if (col < a.N) {
-#pragma unroll
-                    for (int rr = 0; rr < 32; ++rr)
-                        if (rr < rows_here)
-                            orow0[(long long)rr * a.ldo + col] = cur[rr] - tb[rr * 32 + (lane ^ rr)];
+#pragma unroll 8
+                    for (int rr = 0; rr < rows_here; ++rr)
+                        orow0[(long long)rr * a.ldo + col] = sc[rr * 32 + lane] - tb[rr * 32 + (lane ^ rr)];
                 }
                 __syncwarp();
-#pragma unroll
-                for (int rr = 0; rr < 32; ++rr) cur[rr] = nxt[rr];
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
