@@ -58,6 +58,12 @@ CLASS_BOUND = {
     "panel": "alu", "build": "hbm", "gather_pack": "hbm", "refine_update": "hbm",
     "update_tcgen05_refine": "tensor",
 }
+# DRAM bytes per launch of the dominant kernel class, from one ncu capture of
+# the factorisation-phase launches on 32 of the workload's boxes, scaled to 512
+# boxes (traffic is proportional to the boxes processed); see
+# profiles/k_tc_update_fourier16_32boxes.md.  Must be re-measured (or set to
+# None) whenever that kernel changes.
+NCU_TRAFFIC_PER_LAUNCH = {"update_tcgen05": 12.36e9}
 # Classes whose launches skip converged boxes: their flop and byte counts are
 # upper bounds, so they are not used for the roofline.
 SKIPPING = ("update_tcgen05_refine", "residual_fp64", "refine_update")
@@ -337,9 +343,11 @@ def run_ours(args):
             ach = d["bytes"] / sec / 1e9
             unit = "GB/s"
             note = f"{src} HBM copy bandwidth"
+        traffic = NCU_TRAFFIC_PER_LAUNCH.get(dom) if nbox == NBOX else None
         line["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                            "frac": ach / peak, "traffic": None, "peak_source": note,
-                            "launches_per_step": d["launches"]}
+                            "frac": ach / peak, "traffic": traffic,
+                            "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                            "peak_source": note, "launches_per_step": d["launches"]}
 
     # ---- plain FP64 GPU path on a sample of the same boxes
     if not args.no_fp64 and prec == H.HPS_FP32_IR and args.fp64_sample > 0:
