@@ -63,7 +63,7 @@ CLASS_BOUND = {
 # boxes (traffic is proportional to the boxes processed); see
 # profiles/k_tc_update_fourier16_32boxes.md.  Must be re-measured (or set to
 # None) whenever that kernel changes.
-NCU_TRAFFIC_PER_LAUNCH = {"update_tcgen05": 12.36e9}
+NCU_TRAFFIC_PER_LAUNCH = {}
 # Classes whose launches skip converged boxes: their flop and byte counts are
 # upper bounds, so they are not used for the roofline.
 SKIPPING = ("update_tcgen05_refine", "residual_fp64", "refine_update")
@@ -89,6 +89,18 @@ def parse_args():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--gate-tol", type=float, default=3e-3)
     return ap.parse_args()
+
+
+def aggregate_step_ms(ms: float, world: int, device) -> float:
+    """The step time the job reports: the maximum over ranks (every rank
+    processes its own boxes; no data crosses ranks)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def box_lows():
@@ -231,11 +243,7 @@ def run_ours(args):
             dist.barrier()
 
     def allmax(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return aggregate_step_ms(x, world, dev)
 
     nbox = args.nbox
     lows, h = box_lows()

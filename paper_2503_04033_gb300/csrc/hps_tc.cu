@@ -7,13 +7,14 @@
 // every operand x is split as x = hi + lo with hi = tf32(x), lo = tf32(x - hi),
 // and A G ~ A_hi G_hi + A_hi G_lo + A_lo G_hi (the lo*lo term is below FP32
 // rounding).  The split operands are packed K-major (A as [row][k], G
-// transposed to [col][k]) so that TMA brings 128-byte rows into shared memory
-// in the 128B-swizzled layout that tcgen05.mma reads directly.
+// transposed to [col][k]) so that TMA brings 64-byte rows (16 values of K)
+// into shared memory in the 64B-swizzled layout that tcgen05.mma reads directly.
 //
-// One CTA computes a 128 x 64 tile: warp 4 issues the TMA loads (2-stage
-// ring over 32-wide K chunks), warp 5 owns the TMEM accumulator and issues
-// the MMAs (one elected lane), warps 0-3 drain TMEM with tcgen05.ld and apply
-// the epilogue (source rows: zero, in place, or saved pivot rows).  All
+// A persistent CTA per SM walks 128 x 128 output tiles: warp 0 issues the TMA
+// loads (4-stage ring over 16-wide K chunks), warp 1 owns two TMEM
+// accumulators and issues the MMAs (one elected lane), warps 2-5 drain TMEM
+// with tcgen05.ld and apply the epilogue (source rows: zero, in place, or saved
+// pivot rows) while the next tile accumulates.  All
 // mbarrier waits are bounded; a wait that gives up marks the box HPS_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -28,12 +29,12 @@ namespace {
 
 constexpr int TC_BM = 128;                                  // tile rows = TMEM lanes
 constexpr int TC_BN = 128;                                  // tile columns = TMEM columns per buffer
-constexpr int TC_BK = 32;                                   // FP32 values per 128-byte row
-constexpr int TC_STAGES = 2;
+constexpr int TC_BK = 16;                                   // FP32 values per 64-byte row (64B swizzle)
+constexpr int TC_STAGES = 4;
 constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
-constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 16 KiB
-constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 32 KiB
+constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 8 KiB
+constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 8 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
 constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
@@ -98,6 +99,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (it >= 8) __nanosleep(it < 64 ? 32 : 128);   // back off: spinning warps steal issue slots
         if ((it & 255u) == 255u) {
             if (*reinterpret_cast<volatile int*>(&g_tc_abort)) return false;
             if (global_ns() - t0 > WAIT_NS) {
@@ -165,16 +167,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
+// 64 bytes (16 FP32 values), 8-row core groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
     d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset
     d |= (uint64_t)1 << 46;                     // descriptor version
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    d |= (uint64_t)4 << 61;                     // 64-byte swizzle
     return d;
 }
 
@@ -284,8 +286,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     if (!mbar_wait(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1)) { fail_sh = 1; ok = false; break; }
                     tc_fence_after();
                     const uint32_t st = sbase + s * STAGE_BYTES;
-                    const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_TILE);
-                    const uint64_t bh = sw128_desc(st + 2 * A_TILE), bl = sw128_desc(st + 2 * A_TILE + B_TILE);
+                    const uint64_t ah = sw64_desc(st), al = sw64_desc(st + A_TILE);
+                    const uint64_t bh = sw64_desc(st + 2 * A_TILE), bl = sw64_desc(st + 2 * A_TILE + B_TILE);
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 8; ++kk) {
                         const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 8 TF32 values = 32 bytes
@@ -302,17 +304,19 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     } else {
         // Epilogue warps 2..5: warp w owns TMEM lane quarter qd = w % 4 (tile
         // rows 32 qd .. 32 qd + 31).  The source rows of each 32 x 32 chunk are
-        // brought into shared memory with cp.async TC_PRE chunks ahead (lane =
-        // column, so every copy instruction reads one 128-byte line; absent rows
-        // and columns are zero-filled); the accumulator chunk (thread = row) is
-        // transposed through shared memory; then each row segment is written
-        // with one coalesced store.
+        // brought into shared memory with cp.async TC_PRE chunks ahead (absent
+        // rows and columns are zero-filled); the accumulator chunk (thread =
+        // row) is transposed through shared memory; then the chunk is written
+        // out row by row with coalesced stores.  When rows are 16-byte aligned
+        // (a.vec) every copy, shared access and store moves 16 bytes: lane l
+        // covers columns 4 (l % 8) .. +3 of rows l / 8 + 4 i.
         const int qd = warp & 3;
         float* eb = tbuf_all + (warp - 2) * EPI_FLOATS;
-        float* tb = eb;                                       // transpose buffer, XOR-swizzled
+        float* tb = eb;                                       // transpose buffer [32][32], 16-byte XOR swizzle
         float* sb = eb + TBUF_FLOATS;                         // TC_PRE source chunks [32][32]
         const float** sp = reinterpret_cast<const float**>(eb + TBUF_FLOATS * (1 + TC_PRE));
         const uint32_t sb_u32 = smem_u32(sb);
+        const int l8 = lane & 7, l3 = lane >> 3;
         uint32_t j = 0;
         for (int t = blockIdx.x; t < a.tiles; t += gridDim.x) {
             const int box = t / per_box, rem = t - box * per_box;
@@ -342,16 +346,29 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             __syncwarp();
             const int nchunks = (min(TC_BN, a.N - n0) + 31) / 32;
             auto prefetch = [&](int cc) {
-                const int col = n0 + cc * 32 + lane;
-                const uint32_t dst = sb_u32 + (uint32_t)(((cc % TC_PRE) * 1024 + lane) * 4);
+                const int cb = n0 + cc * 32;
+                const uint32_t buf = sb_u32 + (uint32_t)((cc % TC_PRE) * 4096);
+                if (a.vec) {
+                    const int col = cb + 4 * l8;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int rr = l3 + 4 * i;
+                        const float* q = sp[rr];
+                        const bool have = q != nullptr && col < a.N;   // N % 4 == 0 when a.vec
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(buf + (rr * 32 + 4 * l8) * 4),
+                                     "l"(have ? q + col : Ob), "r"(have ? 16 : 0)
+                                     : "memory");
+                    }
+                } else {
+                    const int col = cb + lane;
 #pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr) {
-                    const float* q = sp[rr];
-                    const bool have = q != nullptr && col < a.N;
-                    const float* src = have ? q + col : Ob;
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + rr * 128),
-                                 "l"(src), "r"(have ? 4 : 0)
-                                 : "memory");
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const float* q = sp[rr];
+                        const bool have = q != nullptr && col < a.N;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(buf + (rr * 32 + lane) * 4),
+                                     "l"(have ? q + col : Ob), "r"(have ? 4 : 0)
+                                     : "memory");
+                    }
                 }
             };
             for (int cc = 0; cc < TC_PRE - 1; ++cc) {
@@ -359,7 +376,9 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 asm volatile("cp.async.commit_group;" ::: "memory");
             }
             const int b = j & 1;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1));
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) {
                 asm volatile("cp.async.wait_all;" ::: "memory");
                 if (lane == 0) fail_sh = 1;
@@ -373,16 +392,38 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 asm volatile("cp.async.commit_group;" ::: "memory");
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + cc * 32), v);
+                // row = lane; 16-byte group g of the row goes to slot g ^ (lane & 7)
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) tb[lane * 32 + (jj ^ lane)] = __uint_as_float(v[jj]);
+                for (int g = 0; g < 8; ++g)
+                    *reinterpret_cast<float4*>(tb + lane * 32 + 4 * (g ^ (lane & 7))) =
+                        make_float4(__uint_as_float(v[4 * g]), __uint_as_float(v[4 * g + 1]),
+                                    __uint_as_float(v[4 * g + 2]), __uint_as_float(v[4 * g + 3]));
                 asm volatile("cp.async.wait_group %0;" ::"n"(TC_PRE - 1) : "memory");
                 __syncwarp();
                 const float* sc = sb + (cc % TC_PRE) * 1024;
-                const int col = n0 + cc * 32 + lane;
-                if (col < a.N) {
+                const int cb = n0 + cc * 32;
+                if (a.vec) {
+                    const int col = cb + 4 * l8;
+                    if (col < a.N) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int rr = l3 + 4 * i;
+                            if (rr < rows_here) {
+                                const float4 s4 = *reinterpret_cast<const float4*>(sc + rr * 32 + 4 * l8);
+                                const float4 t4 = *reinterpret_cast<const float4*>(tb + rr * 32 + 4 * (l8 ^ (rr & 7)));
+                                *reinterpret_cast<float4*>(orow0 + (long long)rr * a.ldo + col) =
+                                    make_float4(s4.x - t4.x, s4.y - t4.y, s4.z - t4.z, s4.w - t4.w);
+                            }
+                        }
+                    }
+                } else {
+                    const int col = cb + lane;
+                    if (col < a.N) {
 #pragma unroll 8
-                    for (int rr = 0; rr < rows_here; ++rr)
-                        orow0[(long long)rr * a.ldo + col] = sc[rr * 32 + lane] - tb[rr * 32 + (lane ^ rr)];
+                        for (int rr = 0; rr < rows_here; ++rr)
+                            orow0[(long long)rr * a.ldo + col] =
+                                sc[rr * 32 + lane] - tb[rr * 32 + 4 * ((lane >> 2) ^ (rr & 7)) + (lane & 3)];
+                    }
                 }
                 __syncwarp();
             }
@@ -483,7 +524,7 @@ bool make_map(CUtensorMap* tm, const float* base, int K, long long rows, long lo
     cuuint32_t boxd[4] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, boxd, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -502,7 +543,7 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
     a.tiles_n = (a.N + TC_BN - 1) / TC_BN;
     a.tiles = a.tiles_m * a.tiles_n * nbox;
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) &&
+    a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) && (a.N % 4 == 0) &&
             (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
     static int num_sms = 0;
     if (!num_sms) {
