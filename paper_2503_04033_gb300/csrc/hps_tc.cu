@@ -444,9 +444,9 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int bx = 0; bx < (a.tiles + per_box - 1) / per_box; ++bx) atomicCAS(a.status + bx, 0, HPS_ETIMEOUT);
 }
 
-// dst = [hi plane | lo plane] of the first nb columns of src (rows x NB,
-// zero beyond nb), hi = tf32(x), lo = tf32(x - hi).
-__global__ void k_pack_split(const float* __restrict__ src, long long sS, int rows, int NB, int nb,
+// dst = [hi plane | lo plane] of the first nb columns of src (rows of pitch
+// lds; planes rows x NB, zero beyond nb), hi = tf32(x), lo = tf32(x - hi).
+__global__ void k_pack_split(const float* __restrict__ src, long long lds, long long sS, int rows, int NB, int nb,
                              float* __restrict__ dst, long long sD)
 {
     const int box = blockIdx.y;
@@ -454,7 +454,8 @@ __global__ void k_pack_split(const float* __restrict__ src, long long sS, int ro
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(idx % NB);
-        const float x = c < nb ? src[box * sS + idx] : 0.0f;
+        const long long r = idx / NB;
+        const float x = c < nb ? src[box * sS + r * lds + c] : 0.0f;
         const float hi = to_tf32(x);
         dst[box * sD + idx] = hi;
         dst[box * sD + total + idx] = to_tf32(x - hi);
@@ -565,14 +566,14 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
     return true;
 }
 
-void launch_pack_split(const float* src, long long sS, int rows, int NB, int nb, float* dst, long long sD, int nbox,
-                       cudaStream_t st)
+void launch_pack_split(const float* src, long long lds, long long sS, int rows, int NB, int nb, float* dst,
+                       long long sD, int nbox, cudaStream_t st)
 {
     const long long total = (long long)rows * NB;
     int blocks = (int)std::min<long long>((total + 255) / 256, 256);
     dim3 grd((unsigned)blocks, (unsigned)nbox);
     prof_begin(KC_GATHER, st);
-    k_pack_split<<<grd, 256, 0, st>>>(src, sS, rows, NB, nb, dst, sD);
+    k_pack_split<<<grd, 256, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
     prof_end(KC_GATHER, st, 0.0, (double)nbox * total * 12.0);
 }
 
@@ -619,26 +620,34 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         int* Ps = w.perm + P.perm_off[s];
         launch_panel<float>(w.M, ldm, w.sM, n, k, nb, P.ib, Ps, w.sP, Fs, NB, w.sF, Bs + (long long)k * NB, NB,
                             w.sB, status, nullptr, nbox, st);
+        // F rows below the panel, L21 L11^{-1} = -(L21 * F_top), and B rows above
+        // it, U01 U11^{-1} = -(U01 * B_top), as tensor-core products: the left
+        // operand is split into the step's own (not yet filled) pack region,
+        // the right one, transposed, into the G pack.
+        const long long gplane = ldm * NB;
         if (n - k - nb > 0) {
-            GemmArgs<float> a{};
-            a.alpha = -1.0f;
-            a.A = w.M + (long long)(k + nb) * ldm + k; a.lda = ldm; a.sA = w.sM;
-            a.B = Fs; a.ldb = NB; a.sB = w.sF;
-            a.O = Fs + (long long)nb * NB; a.ldo = NB; a.sO = w.sF;
-            a.M = n - k - nb; a.N = nb; a.K = nb; a.mode = GM_SET;
-            launch_gemm<float>(a, nbox, st);
+            float* Fp = w.Fp + 2 * P.fw_off[s];
+            launch_pack_split(w.M + (long long)(k + nb) * ldm + k, ldm, w.sM, n - k - nb, NB, nb, Fp, w.sFp, nbox, st);
+            prof_begin(KC_GATHER, st);
+            k_gather_pack<<<dim3((unsigned)((nb + 31) / 32), (unsigned)(NB / 32), (unsigned)nbox), dim3(32, 8), 0, st>>>(
+                Fs, NB, w.sF, 0, nb, NB, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr);
+            prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
+            TcArgs a = targs(Fs + (long long)nb * NB, NB, w.sF, n - k - nb, nb, GM_SET, 0);
+            if (!launch_tc_update(Fp, n - k - nb, w.sFp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st)) return false;
         }
         if (k > 0) {
-            GemmArgs<float> a{};
-            a.alpha = -1.0f;
-            a.A = w.M + k; a.lda = ldm; a.sA = w.sM;
-            a.B = Bs + (long long)k * NB; a.ldb = NB; a.sB = w.sB;
-            a.O = Bs; a.ldo = NB; a.sO = w.sB;
-            a.M = k; a.N = nb; a.K = nb; a.mode = GM_SET;
-            launch_gemm<float>(a, nbox, st);
+            float* Bp = w.Bp + 2 * P.bw_off[s];
+            launch_pack_split(w.M + k, ldm, w.sM, k, NB, nb, Bp, w.sBp, nbox, st);
+            prof_begin(KC_GATHER, st);
+            k_gather_pack<<<dim3((unsigned)((nb + 31) / 32), (unsigned)(NB / 32), (unsigned)nbox), dim3(32, 8), 0, st>>>(
+                Bs + (long long)k * NB, NB, w.sB, 0, nb, NB, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
+                nullptr);
+            prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
+            TcArgs a = targs(Bs, NB, w.sB, k, nb, GM_SET, 0);
+            if (!launch_tc_update(Bp, k, w.sBp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st)) return false;
         }
-        launch_pack_split(Fs, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
-        launch_pack_split(Bs, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
+        launch_pack_split(Fs, NB, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
+        launch_pack_split(Bs, NB, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
         const int c0 = k + nb, nc = n + P.r - c0;
         if (nc > 0) {
             launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st);
