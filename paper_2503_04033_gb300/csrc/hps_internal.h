@@ -74,10 +74,10 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     P.NB = NB;
     P.ldm = (long long)align_up((size_t)(n + r), 8);
     // panel inner-block width: the block column of the panel lives in shared memory
-    const size_t static_smem = 32 * kMaxNB * P.elt + 1024;
+    const size_t static_smem = 32 * kMaxNB * P.elt + 2048;
     const size_t budget = 227 * 1024 - static_smem;
     int ib = 32;
-    while (ib > 1 && (size_t)ib * n * P.elt > budget) ib >>= 1;
+    while (ib > 1 && (size_t)ib * n * P.elt + (size_t)n * 5 > budget) ib >>= 1;
     if (ib > NB) ib = NB;
     P.ib = ib;
     for (int k = 0; k < n; k += NB) {

@@ -112,10 +112,14 @@ __device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi)
 
 // One CTA factors one box's panel M[k:n, k:k+nb] (Algorithm 1's batched LU,
 // P A_ii = L U with partial pivoting).  The panel is processed in inner blocks
-// of ib columns that live in shared memory (column-major, R rows); the pivot
-// search is a warp-shuffle arg-max followed by a cross-warp pass.  After the
+// of ib columns that live in shared memory (column-major, R rows, in the order
+// the rows were loaded; pos2row maps a pivot position to its loaded row); the
+// pivot search is a warp-shuffle arg-max followed by a cross-warp pass.  After the
 // panel: the step's row permutation perm[r] (source row of local row r),
 // F top = -L11^{-1} and B top = -U11^{-1}.
+constexpr int kRU = 16;                                   // rows per register tile
+constexpr int kSwapPer = (64 * kMaxNB + kPanelThreads - 1) / kPanelThreads;
+
 template <typename T>
 __global__ void __launch_bounds__(kPanelThreads)
 k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, int ib,
@@ -124,11 +128,15 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Sb = reinterpret_cast<T*>(smem_raw);
+    const int R0 = n - k;
+    unsigned short* pos2row = reinterpret_cast<unsigned short*>(smem_raw + (size_t)ib * R0 * sizeof(T));
+    unsigned short* row2pos = pos2row + R0;
+    unsigned char* active = reinterpret_cast<unsigned char*>(row2pos + R0);
     __shared__ int swp[kMaxNB];
-    __shared__ T red_v[kPanelThreads / 32];
-    __shared__ int red_i[kPanelThreads / 32];
-    __shared__ int s_piv;
-    __shared__ int s_sing;
+    __shared__ T red_v[2][kPanelThreads / 32];
+    __shared__ int red_i[2][kPanelThreads / 32];
+    __shared__ int s_sing, s_nmv;
+    __shared__ unsigned short mv[64];
     __shared__ T Xs[32 * kMaxNB];
 
     const int box = blockIdx.x;
@@ -136,7 +144,6 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kPanelThreads / 32;
     T* Mb = M + box * sM;
-    const int R0 = n - k;
     if (tid == 0) s_sing = 0;
 
     for (int jb = 0; jb < nb; jb += ib) {
@@ -147,94 +154,149 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
             const int r = idx / w, c = idx - r * w;
             Sb[c * R + r] = base[(long long)r * ldm + c];
         }
+        for (int r = tid; r < R; r += kPanelThreads) {
+            pos2row[r] = (unsigned short)r;
+            row2pos[r] = (unsigned short)r;
+            active[r] = 1;
+        }
         __syncthreads();
-        for (int c = 0; c < w; ++c) {
+        // Rows stay where they were loaded; interchanges are tracked in
+        // pos2row/row2pos and applied when the block is written back.  Each
+        // thread owns rows tid, tid + 512, ...; the arg-max candidates of the
+        // next column are formed during this column's update, so every pivot
+        // column costs one barrier.  Ties go to the lowest loaded row.
+        {
             T bv = T(-1);
             int bi = INT_MAX;
-            for (int r = c + tid; r < R; r += kPanelThreads) argmax_merge(bv, bi, tabs(Sb[c * R + r]), r);
+            for (int r = tid; r < R; r += kPanelThreads) argmax_merge(bv, bi, tabs(Sb[r]), r);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
                 argmax_merge(bv, bi, ov, oi);
             }
-            if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
-            __syncthreads();
-            if (warp == 0) {
-                bv = lane < NW ? red_v[lane] : T(-1);
-                bi = lane < NW ? red_i[lane] : INT_MAX;
+            if (lane == 0) { red_v[0][warp] = bv; red_i[0][warp] = bi; }
+        }
+        __syncthreads();
+        for (int c = 0; c < w; ++c) {
+            const int cur = c & 1;
+            T bv = red_v[cur][0];
+            int bi = red_i[cur][0];
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                    argmax_merge(bv, bi, ov, oi);
-                }
-                if (lane == 0) {
-                    if (bi < c || bi >= R) bi = c;   // all candidates NaN: keep the diagonal row
-                    s_piv = bi;
-                    swp[jb + c] = jb + bi;
-                }
+            for (int q = 1; q < NW; ++q) argmax_merge(bv, bi, red_v[cur][q], red_i[cur][q]);
+            // Candidates come from rows still active, so a valid index needs no
+            // further test; none (every |value| NaN) keeps the row in place.
+            int pr = bi;
+            if (pr < 0 || pr >= R) pr = pos2row[c];
+            if (tid == 0) {
+                const int pp = row2pos[pr], qr = pos2row[c];
+                pos2row[c] = (unsigned short)pr;
+                pos2row[pp] = (unsigned short)qr;
+                row2pos[pr] = (unsigned short)c;
+                row2pos[qr] = (unsigned short)pp;
+                swp[jb + c] = jb + pp;
+                active[pr] = 0;
             }
-            __syncthreads();
-            const int pr = s_piv;
-            if (pr != c)
-                for (int cc = tid; cc < w; cc += kPanelThreads) {
-                    const T t = Sb[cc * R + c];
-                    Sb[cc * R + c] = Sb[cc * R + pr];
-                    Sb[cc * R + pr] = t;
-                }
-            __syncthreads();
-            T piv = Sb[c * R + c];
+            T piv = Sb[c * R + pr];
             if (piv == T(0)) {
                 // Exactly singular: record it and keep the arithmetic finite.
                 if (tid == 0) s_sing = 1;
                 piv = T(1);
             }
-            for (int r = c + 1 + tid; r < R; r += kPanelThreads) {
+            T nv = T(-1);
+            int ni = INT_MAX;
+            for (int r = tid; r < R; r += kPanelThreads) {
+                if (r == pr || !active[r]) continue;
                 const T l = Sb[c * R + r] / piv;
                 Sb[c * R + r] = l;
-                for (int cc = c + 1; cc < w; ++cc) Sb[cc * R + r] -= l * Sb[cc * R + c];
+                for (int cc = c + 1; cc < w; ++cc) Sb[cc * R + r] -= l * Sb[cc * R + pr];
+                if (c + 1 < w) argmax_merge(nv, ni, tabs(Sb[(c + 1) * R + r]), r);
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, nv, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, ni, off);
+                argmax_merge(nv, ni, ov, oi);
+            }
+            if (lane == 0) { red_v[cur ^ 1][warp] = nv; red_i[cur ^ 1][warp] = ni; }
             __syncthreads();
         }
         for (int idx = tid; idx < R * w; idx += kPanelThreads) {
             const int r = idx / w, c = idx - r * w;
-            base[(long long)r * ldm + c] = Sb[c * R + r];
+            base[(long long)r * ldm + c] = Sb[c * R + pos2row[r]];
         }
         __syncthreads();
-        // This block's interchanges on the panel's other columns.
-        for (int col = tid; col < nb; col += kPanelThreads) {
-            if (col >= jb && col < jb + w) continue;
-            T* cp = Mb + k + col;
-            for (int c = 0; c < w; ++c) {
-                const int a = k + jb + c, bb = k + swp[jb + c];
-                if (a != bb) {
-                    const T t = cp[(long long)a * ldm];
-                    cp[(long long)a * ldm] = cp[(long long)bb * ldm];
-                    cp[(long long)bb * ldm] = t;
+        // This block's interchanges on the panel's other columns: at most 2w
+        // positions moved (pos2row[r] != r); their values are all read before
+        // any is written.
+        if (tid == 0) s_nmv = 0;
+        __syncthreads();
+        for (int r = tid; r < R; r += kPanelThreads)
+            if (pos2row[r] != r) mv[atomicAdd(&s_nmv, 1)] = (unsigned short)r;
+        __syncthreads();
+        {
+            const int nmv = s_nmv, nother = nb - w;
+            T val[kSwapPer];
+#pragma unroll
+            for (int u = 0; u < kSwapPer; ++u) {
+                const int idx = tid + u * kPanelThreads;
+                if (idx < nmv * nother) {
+                    const int q = idx / nother, oc = idx - q * nother;
+                    const int col = oc < jb ? oc : oc + w;
+                    val[u] = Mb[(long long)(k + jb + pos2row[mv[q]]) * ldm + k + col];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kSwapPer; ++u) {
+                const int idx = tid + u * kPanelThreads;
+                if (idx < nmv * nother) {
+                    const int q = idx / nother, oc = idx - q * nother;
+                    const int col = oc < jb ? oc : oc + w;
+                    Mb[(long long)(k + jb + mv[q]) * ldm + k + col] = val[u];
                 }
             }
         }
         __syncthreads();
-        // Right-looking update of the panel columns [jb+w, nb).
+        // Right-looking update of the panel columns [jb+w, nb): U12 rows by a
+        // forward substitution, then the trailing rows in tiles of kRU rows
+        // by 32 columns per warp (kRU independent loads in flight per warp).
         const int ncr = nb - jb - w;
         if (ncr > 0) {
             T* rb = Mb + (long long)(k + jb) * ldm + (k + jb + w);
             for (int col = tid; col < ncr; col += kPanelThreads) {
                 for (int c = 0; c < w; ++c) {
                     T x = rb[(long long)c * ldm + col];
-                    for (int c2 = 0; c2 < c; ++c2) x -= Sb[c2 * R + c] * Xs[c2 * kMaxNB + col];
+                    const int pc = pos2row[c];
+                    for (int c2 = 0; c2 < c; ++c2) x -= Sb[c2 * R + pc] * Xs[c2 * kMaxNB + col];
                     Xs[c * kMaxNB + col] = x;
                     rb[(long long)c * ldm + col] = x;
                 }
             }
             __syncthreads();
-            for (int r = w + warp; r < R; r += NW) {
-                T* row = rb + (long long)r * ldm;
-                for (int col = lane; col < ncr; col += 32) {
-                    T acc = row[col];
-                    for (int c = 0; c < w; ++c) acc -= Sb[c * R + r] * Xs[c * kMaxNB + col];
-                    row[col] = acc;
+            const int nch = (ncr + 31) >> 5, ngr = (R - w + kRU - 1) / kRU;
+            for (int item = warp; item < ngr * nch; item += NW) {
+                const int gi = item / nch, ch = item - gi * nch;
+                const int col = (ch << 5) + lane;
+                const int r0 = w + gi * kRU;
+                const bool cok = col < ncr;
+                T acc[kRU];
+                int src[kRU];
+#pragma unroll
+                for (int u = 0; u < kRU; ++u) {
+                    const int r = r0 + u;
+                    src[u] = r < R ? pos2row[r] : 0;
+                    acc[u] = (r < R && cok) ? rb[(long long)r * ldm + col] : T(0);
+                }
+                for (int c = 0; c < w; ++c) {
+                    const T x = Xs[c * kMaxNB + col];
+#pragma unroll
+                    for (int u = 0; u < kRU; ++u) acc[u] -= Sb[c * R + src[u]] * x;
+                }
+#pragma unroll
+                for (int u = 0; u < kRU; ++u) {
+                    const int r = r0 + u;
+                    if (r < R && cok) rb[(long long)r * ldm + col] = acc[u];
                 }
             }
             __syncthreads();
@@ -762,17 +824,23 @@ void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int i
                   T* Btop, long long ldb, long long sB, int* status, const int* skip,
                   int nbox, cudaStream_t st)
 {
-    const size_t s1 = (size_t)ib * (size_t)(n - k) * sizeof(T);
-    const size_t s2 = (size_t)2 * nb * nb * sizeof(T);
-    const size_t smem = s1 > s2 ? s1 : s2;
-    static bool attr = false;
-    if (!attr) {
+    static size_t dyn_max = 0;
+    if (!dyn_max) {
         cudaFuncAttributes fa{};
         cudaFuncGetAttributes(&fa, k_panel<T>);
-        cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(227 * 1024 - fa.sharedSizeBytes));
-        attr = true;
+        dyn_max = 227 * 1024 - fa.sharedSizeBytes;
+        cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     }
+    // Widest inner block (<= 32 columns, power of two) whose rows fit in what
+    // is left of shared memory; the panel shrinks as k grows, so later steps
+    // take wider blocks.  The plan's ib is the width of the first step.
+    const size_t R0 = (size_t)(n - k);
+    ib = 32;
+    while (ib > 1 && (size_t)ib * R0 * sizeof(T) + R0 * 5 > dyn_max) ib >>= 1;
+    if (ib > nb) ib = nb;
+    const size_t s1 = (size_t)ib * R0 * sizeof(T) + R0 * 5;
+    const size_t s2 = (size_t)2 * nb * nb * sizeof(T);
+    const size_t smem = s1 > s2 ? s1 : s2;
     prof_begin(KC_PANEL, st);
     k_panel<T><<<nbox, kPanelThreads, smem, st>>>(M, ldm, sM, n, k, nb, ib, perm, sP, Ftop, ldf, sF,
                                                   Btop, ldb, sB, status, skip);
