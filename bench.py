@@ -306,6 +306,7 @@ def run_ours(args):
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "box_failures": bad,
         "refinement": {"corrections_max": int(it.max()), "corrections_mean": float(it.mean()),
+                       "corrections_hist": {int(v): int((it == v).sum()) for v in np.unique(it)},
                        "rel_correction_max": float(rel.max())},
         "gpu_launches": launches_total // args.steps * args.steps,
         "kernels": prof,

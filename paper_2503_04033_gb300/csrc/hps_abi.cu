@@ -280,6 +280,18 @@ hps_status get_geometry(hps_ctx* ctx, int p, const double h[3], Geometry** out)
                 for (int l = 0; l < p; ++l) acc += D[a * pp + i * p + l] * D[a * pp + l * p + j];
                 D2[a * pp + i * p + j] = acc;
             }
+        // D^2 of the Chebyshev nodes is centro-symmetric; the product above
+        // is only up to rounding, so hold it exactly (the residual's even/odd
+        // line split relies on it, and the build then uses the same matrix).
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                const int e = a * pp + i * p + j, f = a * pp + (p - 1 - i) * p + (p - 1 - j);
+                if (e < f) {
+                    const double v = 0.5 * (D2[e] + D2[f]);
+                    D2[e] = v;
+                    D2[f] = v;
+                }
+            }
     }
     HPS_CUDA_TRY(cudaMalloc(&g.dD, sizeof(double) * 3 * pp));
     HPS_CUDA_TRY(cudaMalloc(&g.dD2, sizeof(double) * 3 * pp));

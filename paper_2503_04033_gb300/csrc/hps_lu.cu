@@ -508,79 +508,184 @@ __global__ void k_extract(const TS* __restrict__ src, long long lds, long long s
     X[box * sX + (long long)r * ldx + c] = double(src[box * sS + (long long)r * lds + c]);
 }
 
+// Shared-memory loads of the line tables kept in the loop: the tables are
+// invariant across a CTA's lines, and hoisting them would take ~2h^2 registers.
+__device__ __forceinline__ double2 lds_f64x2(const double* p)
+{
+    double2 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ double lds_f64(const double* p)
+{
+    double v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+
+// One line of q interior values along an axis through the interior block of
+// D^2 (centro-symmetric: D2[i][l] = D2[q+1-i][q+1-l], held exactly so on the
+// host).  With e_l = x_l + x_{q+1-l} and o_l = x_l - x_{q+1-l}, the outputs
+// i and q+1-i are (sum_l E[i][l] e_l) +- (sum_l O[i][l] o_l), with
+// E = (D2[i][l] + D2[i][q+1-l]) / 2 and O = (D2[i][l] - D2[i][q+1-l]) / 2, so
+// a pair costs 2h multiply-adds instead of 2q (h = q/2; an odd q adds the
+// middle column).  tab holds (E, O) pairs [h][h], then for odd q the middle
+// column [h], the middle row's E part [h] and its diagonal entry.
+template <int Q, class Emit>
+__device__ __forceinline__ void eo_line(const double* __restrict__ src, int stride, const double* tab, Emit&& emit)
+{
+    constexpr int H = Q / 2;
+    double x[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) x[l] = src[l * stride];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+        const double a = x[l], z = x[Q - 1 - l];
+        x[l] = a + z;
+        x[Q - 1 - l] = a - z;
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        double2 eo = lds_f64x2(tab + 2 * (i * H));
+        double se = eo.x * x[0];
+        double so = eo.y * x[Q - 1];
+#pragma unroll
+        for (int l = 1; l < H; ++l) {
+            eo = lds_f64x2(tab + 2 * (i * H + l));
+            se = fma(eo.x, x[l], se);
+            so = fma(eo.y, x[Q - 1 - l], so);
+        }
+        if constexpr ((Q & 1) != 0) se = fma(lds_f64(tab + 2 * H * H + i), x[H], se);
+        emit(i, se + so);
+        emit(Q - 1 - i, se - so);
+    }
+    if constexpr ((Q & 1) != 0) {
+        const double* Em = tab + 2 * H * H + H;
+        double sm = lds_f64(Em + H) * x[H];
+#pragma unroll
+        for (int l = 0; l < H; ++l) sm = fma(lds_f64(Em + l), x[l], sm);
+        emit(H, sm);
+    }
+}
+
+// Doubles per axis table (even, so every axis table stays 16-byte aligned).
+template <int Q>
+__host__ __device__ constexpr int eo_tab_size()
+{
+    return (2 * (Q / 2) * (Q / 2) + ((Q & 1) ? 2 * (Q / 2) + 1 : 0) + 1) & ~1;
+}
+
+// Threads of the residual CTA (one per grid line of a pass) and the CTAs per
+// SM the register cap allows for (about 96 registers a thread).
+template <int Q>
+__host__ __device__ constexpr int res_threads() { return ((Q * Q + 31) / 32) * 32; }
+template <int Q>
+__host__ __device__ constexpr int res_min_blocks()
+{
+    return 65536 / (res_threads<Q>() * 96) > 1 ? 65536 / (res_threads<Q>() * 96) : 1;
+}
+
 // R = B - A_ii X in FP64, matrix-free: A_ii X applies the 1-D second-derivative
 // matrices along the three grid lines through each interior node plus the
 // kappa^2 b diagonal (the Kronecker structure of Eq. 2's collocation); B is
-// -A_ib (DTN), f_i (LOAD) or -A_ib u_b (TRACE).  One CTA holds a tile of ct
-// columns of X for one box in shared memory.  R is written in FP32 for the
-// correction solve.
-__global__ void k_residual(int p, int n, int nrhs, int ct, const double* __restrict__ D2, double kappa2,
-                           const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb,
-                           int rhs_kind,
-                           const double* __restrict__ rhs, long long s_rhs, const double* __restrict__ X,
-                           long long ldx, long long sX, float* __restrict__ R, long long ldr, long long sR,
-                           const int* skip)
+// -A_ib (DTN), f_i (LOAD) or -A_ib u_b (TRACE).  One CTA takes one column of
+// X for one box, staged in shared memory, with one thread per grid line; the
+// three axes are applied line by line (eo_line) into an accumulator, the z
+// pass finishing each point.  R is written in FP32 for the correction solve.
+template <int Q>
+__global__ void __launch_bounds__(res_threads<Q>(), res_min_blocks<Q>())
+k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
+           const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb, int rhs_kind,
+           const double* __restrict__ rhs, long long s_rhs, const double* __restrict__ X, long long ldx,
+           long long sX, float* __restrict__ R, long long ldr, long long sR, const int* skip)
 {
+    constexpr int H = Q / 2, TA = eo_tab_size<Q>();
+    constexpr int q = Q, qq = Q * Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int box = blockIdx.y;
     if (skip && skip[box]) return;
-    const int c0 = blockIdx.x * ct;
-    const int q = p - 2, qq = q * q, pp = p * p;
-    double* Xs = reinterpret_cast<double*>(smem_raw);       // [n][ct]
-    double* D2s = Xs + (long long)n * ct;                    // [3][p][p]
-    const double* Xb = X + box * sX;
-    const int nc = imin(ct, nrhs - c0);
-    for (int idx = threadIdx.x; idx < n * ct; idx += blockDim.x) {
-        const int r = idx / ct, c = idx - r * ct;
-        Xs[idx] = c < nc ? Xb[(long long)r * ldx + c0 + c] : 0.0;
-    }
+    const int cw = blockIdx.x;                               // column of X and R
+    const int pp = p * p;
+    double* Xs = reinterpret_cast<double*>(smem_raw);       // [n]
+    double* Ac = Xs + n;                                     // [n]
+    double* D2s = Ac + n;                                    // [3][p][p]
+    double* tab = D2s + ((3 * pp + 1) & ~1);                 // [3][TA]
+    const double* Xb = X + box * sX + cw;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = Xb[(long long)r * ldx];
     for (int idx = threadIdx.x; idx < 3 * pp; idx += blockDim.x) D2s[idx] = D2[idx];
     __syncthreads();
-    const double* bb = b + box * sb;
-    const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
-    for (int idx = threadIdx.x; idx < n * ct; idx += blockDim.x) {
-        const int r = idx / ct, c = idx - r * ct;
-        if (c >= nc) continue;
-        const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
-        const double* rx = D2s + i * p;
-        const double* ry = D2s + pp + j * p;
-        const double* rz = D2s + 2 * pp + k * p;
-        const int bx = (r - (i - 1)) * ct + c;               // node (1, j, k)
-        const int by = (r - (j - 1) * q) * ct + c;           // node (i, 1, k)
-        const int bz = (r - (k - 1) * qq) * ct + c;          // node (i, j, 1)
-        double lap = 0.0;
-        for (int l = 1; l <= q; ++l) {
-            lap += rx[l] * Xs[bx + (l - 1) * ct];
-            lap += ry[l] * Xs[by + (l - 1) * q * ct];
-            lap += rz[l] * Xs[bz + (l - 1) * qq * ct];
+    for (int idx = threadIdx.x; idx < 3 * TA; idx += blockDim.x) {
+        const int a = idx / TA, t = idx - a * TA;
+        const double* D = D2s + a * pp;
+        double v;
+        if (t < 2 * H * H) {
+            constexpr int Hd = H > 0 ? H : 1;   // q = 1 has no pairs
+            const int tt = t >> 1, i = tt / Hd + 1, l = tt - (tt / Hd) * Hd + 1;
+            const double u = D[i * p + l], w = D[i * p + (p - 1 - l)];
+            v = (t & 1) ? 0.5 * (u - w) : 0.5 * (u + w);
+        } else if (t >= 2 * H * H + ((Q & 1) ? 2 * H + 1 : 0)) {
+            v = 0.0;                            // padding
+        } else {
+            const int t2 = t - 2 * H * H, mid = H + 1;
+            if (t2 < H) v = D[(t2 + 1) * p + mid];
+            else if (t2 < 2 * H) {
+                const int l = t2 - H + 1;
+                v = 0.5 * (D[mid * p + l] + D[mid * p + (p - 1 - l)]);
+            } else v = D[mid * p + mid];
         }
-        const double xv = Xs[r * ct + c];
-        const int gi = i + p * j + pp * k;
-        double bval;
-        const int cw = c0 + c;          // column of R and X
-        int cg = cw, kind = rhs_kind;   // column of the right-hand side definition
+        tab[idx] = v;
+    }
+    __syncthreads();
+    const int ln = threadIdx.x;
+    // x lines (ln = j0 + q k0): Ac = D2x X
+    if (ln < qq) {
+        const int base = ln * q;
+        eo_line<Q>(Xs + base, 1, tab, [&](int i, double v) { Ac[base + i] = v; });
+    }
+    __syncthreads();
+    // y lines (ln = i0 + q k0): Ac += D2y X
+    if (ln < qq) {
+        const int base = ln % q + qq * (ln / q);
+        eo_line<Q>(Xs + base, q, tab + TA, [&](int j, double v) { Ac[base + q * j] += v; });
+    }
+    __syncthreads();
+    // z lines (ln = i0 + q j0), then every point of the line is finished.
+    if (ln < qq) {
+        const double* bb = b + box * sb;
+        const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
+        const int i = ln % q + 1, j = ln / q + 1;
+        int cg = cw, kind = rhs_kind;
         if (kind == RHS_DTN_LOAD) {
             if (cg < 6 * qq) kind = RHS_DTN;
             else { kind = RHS_LOAD; cg -= 6 * qq; }
         }
-        if (kind == RHS_DTN) {
-            const int f = cg / qq, s = cg % qq, a = s % q + 1, b2 = s / q + 1;
-            const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
-            bval = 0.0;
-            if (axis == 0 && j == a && k == b2) bval = rx[e];
-            else if (axis == 1 && i == a && k == b2) bval = ry[e];
-            else if (axis == 2 && i == a && j == b2) bval = rz[e];
-        } else if (kind == RHS_LOAD) {
-            bval = rhs[box * s_rhs + (long long)cg * p * pp + gi];
-        } else {
-            const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
-            const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
-            bval = rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] + ry[p - 1] * ub[3 * qq + sy]
-                 + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
-        }
-        // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
-        const double res = bval + lap + k2 * bb[gi] * xv;
-        R[box * sR + (long long)r * ldr + cw] = float(res);
+        const double* rx = D2s + i * p;
+        const double* ry = D2s + pp + j * p;
+        float* Rb = R + box * sR + cw;
+        eo_line<Q>(Xs + ln, qq, tab + 2 * TA, [&](int k0, double v) {
+            const int k = k0 + 1, r = ln + qq * k0;
+            const double* rz = D2s + 2 * pp + k * p;
+            const int gi = i + p * j + pp * k;
+            double bval = 0.0;
+            if (kind == RHS_DTN) {
+                const int f = cg / qq, s2 = cg % qq, a = s2 % q + 1, b2 = s2 / q + 1;
+                const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
+                if (axis == 0 && j == a && k == b2) bval = rx[e];
+                else if (axis == 1 && i == a && k == b2) bval = ry[e];
+                else if (axis == 2 && i == a && j == b2) bval = rz[e];
+            } else if (kind == RHS_LOAD) {
+                bval = rhs[box * s_rhs + (long long)cg * p * pp + gi];
+            } else {
+                const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
+                const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
+                bval = rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] +
+                       ry[p - 1] * ub[3 * qq + sy] + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
+            }
+            // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
+            Rb[(long long)r * ldr] = float(bval + (Ac[r] + v) + k2 * bb[gi] * Xs[r]);
+        });
     }
 }
 
@@ -900,26 +1005,49 @@ void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols
     prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * (sizeof(TS) + 8));
 }
 
+namespace {
+template <int Q>
+void residual_q(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
+                int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs, const double* X, long long ldx,
+                long long sX, float* R, long long ldr, long long sR, const int* skip, cudaStream_t st)
+{
+    const size_t tables = (size_t)((3 * g.p * g.p + 1) & ~1) + 3 * eo_tab_size<Q>();
+    const size_t smem = ((size_t)2 * g.n + tables) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_residual<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    dim3 grd((unsigned)nrhs, (unsigned)nbox);
+    // FP64 operations per entry: three line passes (butterfly 1, pairs h + 1
+    // (odd q: + 1 for the middle column), accumulate 1) and the finish (3).
+    const double per = 3.0 * (2.0 + 2.0 * (Q / 2) + ((Q & 1) ? 2.0 : 0.0)) + 3.0;
+    prof_begin(KC_RESIDUAL, st);
+    k_residual<Q><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, nrhs, g.dD2, kappa * kappa, kappa_box, b, sb,
+                                                        rhs_kind, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, skip);
+    prof_end(KC_RESIDUAL, st, (double)nbox * g.n * (double)nrhs * per, (double)nbox * g.n * (double)nrhs * 12.0);
+}
+}  // namespace
+
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
                      float* R, long long ldr, long long sR, const int* skip, cudaStream_t st)
 {
-    // Column tile: as many columns as fit next to the operator tables.
-    const size_t budget = 200 * 1024 - (size_t)3 * g.p * g.p * sizeof(double);
-    int ct = 16;
-    while (ct > 1 && (size_t)g.n * ct * sizeof(double) > budget) ct >>= 1;
-    const size_t smem = ((size_t)g.n * ct + (size_t)3 * g.p * g.p) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 16384);
-        attr = true;
+    static_assert(kMaxP - 2 == 22, "one residual instantiation per interior line length");
+#define HPS_RES_CASE(QV)                                                                                       \
+    case QV:                                                                                                   \
+        residual_q<QV>(g, kappa, kappa_box, nbox, b, sb, rhs_kind, nrhs, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, \
+                       skip, st);                                                                              \
+        break;
+    switch (g.q) {
+        HPS_RES_CASE(1) HPS_RES_CASE(2) HPS_RES_CASE(3) HPS_RES_CASE(4) HPS_RES_CASE(5) HPS_RES_CASE(6)
+        HPS_RES_CASE(7) HPS_RES_CASE(8) HPS_RES_CASE(9) HPS_RES_CASE(10) HPS_RES_CASE(11) HPS_RES_CASE(12)
+        HPS_RES_CASE(13) HPS_RES_CASE(14) HPS_RES_CASE(15) HPS_RES_CASE(16) HPS_RES_CASE(17) HPS_RES_CASE(18)
+        HPS_RES_CASE(19) HPS_RES_CASE(20) HPS_RES_CASE(21) HPS_RES_CASE(22)
+        default: break;
     }
-    dim3 grd((unsigned)((nrhs + ct - 1) / ct), (unsigned)nbox);
-    prof_begin(KC_RESIDUAL, st);
-    k_residual<<<grd, 512, smem, st>>>(g.p, g.n, nrhs, ct, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind, rhs_src,
-                                       s_rhs, X, ldx, sX, R, ldr, sR, skip);
-    prof_end(KC_RESIDUAL, st, (double)nbox * g.n * (double)nrhs * (6.0 * g.q + 4.0), (double)nbox * g.n * (double)nrhs * 12.0);
+#undef HPS_RES_CASE
 }
 
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
