@@ -86,7 +86,9 @@ typedef struct {
 typedef enum {
     HPS_OPT_IR_MAX_ITERS = 1,   /* corrections in FP32_IR mode, default 8, range 0..20 */
     HPS_OPT_IR_TOL = 2,         /* a box stops refining when its predicted remaining error is below tol
-                                   relative to ||X||_F (default 1e-12): ||dX_k|| min(1, 10 ||dX_k||/||dX_k-1||),
+                                   relative to ||X||_F (default 1e-11, a decade below the 1e-10 relative
+                                   accuracy the FP32_IR path is meant to deliver on T and u):
+                                   ||dX_k|| min(1, 10 ||dX_k||/||dX_k-1||),
                                    or when ||dX|| is below 1e-11 ||X|| and shrank by less than half
                                    (the FP64 residual's noise floor); converged boxes skip later steps */
     HPS_OPT_BLOCK = 3,          /* LU block size NB: 0 = automatic, else 32, 64 or 128 */

@@ -83,7 +83,7 @@ struct hps_ctx {
     size_t ws_bytes = 0;
     std::map<std::tuple<int, double, double, double>, Geometry> geoms;
     int ir_iters = 8;
-    double ir_tol = 1e-12;
+    double ir_tol = 1e-11;
     int nb_opt = 0;
     int use_tc = 1;
     int sync = 0;
