@@ -100,6 +100,8 @@ typedef enum {
                                    environment variable HPS_TUNE_CACHE, when set */
     HPS_OPT_GRAPHS = 7,         /* 1: capture each distinct leaf call (same sizes, buffers and options) into a
                                    CUDA graph on first use and replay the graph afterwards */
+    HPS_OPT_TC_EPILOGUE = 8,    /* tcgen05 update epilogue: 0 (default) moves source and result tiles by TMA
+                                   wherever the output is 16-byte aligned, 1 always uses the cp.async form */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;

@@ -85,6 +85,7 @@ struct hps_ctx {
     int ir_iters = 8;
     double ir_tol = 1e-11;
     int nb_opt = 0;
+    int tc_epi_cp = 0;          // 1: tcgen05 epilogue always in the cp.async form
     int use_tc = 1;
     int sync = 0;
     int zero_row_box = -1;
@@ -350,7 +351,9 @@ long long job_srhs(const Job& j)
 
 Plan job_plan(const hps_ctx* ctx, const Job& j, hps_precision prec)
 {
-    return make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64);
+    Plan P = make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64);
+    P.tma_epi = ctx->tc_epi_cp == 0;
+    return P;
 }
 
 // Sizes the workspace for the largest chunk any job will run; all device
@@ -630,7 +633,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     const bool use_graph = ctx->graphs && !ctx->prof_on;
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
@@ -846,6 +849,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
         return HPS_OK;
     case HPS_OPT_GRAPHS:
         ctx->graphs = value != 0;
+        return HPS_OK;
+    case HPS_OPT_TC_EPILOGUE:
+        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        ctx->tc_epi_cp = (int)value;
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;

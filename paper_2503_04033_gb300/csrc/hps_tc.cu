@@ -10,12 +10,15 @@
 // transposed to [col][k]) so that TMA brings 64-byte rows (16 values of K)
 // into shared memory in the 64B-swizzled layout that tcgen05.mma reads directly.
 //
-// A persistent CTA per SM walks 128 x 128 output tiles: warp 0 issues the TMA
-// loads (4-stage ring over 16-wide K chunks), warp 1 owns two TMEM
-// accumulators and issues the MMAs (one elected lane), warps 2-5 drain TMEM
-// with tcgen05.ld and apply the epilogue (source rows: zero, in place, or saved
-// pivot rows) while the next tile accumulates.  All
-// mbarrier waits are bounded; a wait that gives up marks the box HPS_ETIMEOUT.
+// A persistent CTA per SM walks 128 x 256 output tiles: warp 0 issues the TMA
+// loads (3-stage ring over 16-wide K chunks, 48 KiB a stage), warp 1 owns two
+// TMEM accumulators (all 512 columns) and issues the MMAs (one elected lane),
+// warps 2-5 drain TMEM with tcgen05.ld and apply the epilogue (source rows:
+// zero, in place, or saved pivot rows) while the next tile accumulates.  The
+// split operands are the traffic that bounds this kernel (12 bytes per output
+// element at 128 x 256 against 8 for reading and writing O): wider tiles re-read
+// A less often.  All mbarrier waits are bounded; a wait that gives up marks the
+// box HPS_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -28,18 +31,24 @@ namespace hps {
 namespace {
 
 constexpr int TC_BM = 128;                                  // tile rows = TMEM lanes
-constexpr int TC_BN = 128;                                  // tile columns = TMEM columns per buffer
+constexpr int TC_BN = 256;                                  // tile columns = TMEM columns per buffer
 constexpr int TC_BK = 16;                                   // FP32 values per 64-byte row (64B swizzle)
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 3;
 constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 8 KiB
-constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 8 KiB
+constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 16 KiB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
 constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
 constexpr uint32_t EPI_FLOATS = TBUF_FLOATS * (1 + TC_PRE) + 64;   // transpose + source ring + row pointers
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + TC_EPI_WARPS * EPI_FLOATS * 4 + 1024;
+constexpr int TE_PRE = 5;                                  // TMA epilogue: 32 x 32 chunk buffers per warp
+constexpr int TE_LA = 3;                                   // chunks fetched ahead (one store may still read)
+constexpr uint32_t TE_CHUNK = 32 * 32 * 4;                 // 4 KiB, 128-byte rows, 128B swizzle
+constexpr size_t EPI_BYTES_CP = (size_t)TC_EPI_WARPS * EPI_FLOATS * 4;
+constexpr size_t EPI_BYTES_TMA = (size_t)TC_EPI_WARPS * TE_PRE * TE_CHUNK;
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + (EPI_BYTES_CP > EPI_BYTES_TMA ? EPI_BYTES_CP : EPI_BYTES_TMA) +
+                           1024;
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
 
 struct TcArgs {
@@ -47,6 +56,7 @@ struct TcArgs {
     int M, N, kch;
     int tiles_m, tiles_n, tiles;
     int vec;                         // rows of O and W are 16-byte aligned: float4 epilogue
+    int tma_epi;                     // O is 16-byte aligned: source tiles in and results out by TMA
     int mode, split;
     const int* perm; long long sP;
     const float* W; long long ldw, sW;
@@ -110,6 +120,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
+// Bounded wait used only to let copies already in flight land before a CTA
+// that gave up exits (it does not return early on the abort flag).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return;
+        __nanosleep(128);
+        if ((it & 63u) == 63u && global_ns() - t0 > WAIT_NS / 4) return;
+    }
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1,
                                             int c2, int c3)
 {
@@ -119,6 +141,35 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm,
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, uint32_t src, int c0, int c1, int c2)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -203,9 +254,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // a box's A and G stay in L2 while its tiles run).  TMEM holds two 128 x 256
 // FP32 accumulators: the epilogue drains one while the MMAs fill the other.
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
+k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ CUtensorMap tmO, TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t ld_bar[TC_EPI_WARPS][TE_PRE];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2];
@@ -228,6 +281,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             mbar_init(smem_u32(&tfull_bar[b]), 1);
             mbar_init(smem_u32(&tempty_bar[b]), TC_EPI_WARPS);
         }
+        for (int w = 0; w < TC_EPI_WARPS; ++w)
+            for (int q = 0; q < TE_PRE; ++q) mbar_init(smem_u32(&ld_bar[w][q]), 1);
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -301,6 +356,142 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 ++j;
             }
         }
+    } else if (a.tma_epi) {
+        // Epilogue warps 2..5, TMA form: warp w owns TMEM lane quarter qd = w % 4
+        // (tile rows 32 qd .. +31) and a ring of TE_PRE 32 x 32 buffers.  Lane 0
+        // fetches each chunk's source rows from O by TMA TE_LA chunks ahead
+        // (across tiles; rows and columns past O's edge arrive as zeros); each
+        // lane then owns one row: it reads the accumulator row from TMEM,
+        // replaces the staged row by src - acc in place (128B swizzle: 16-byte
+        // unit u of row r sits at u ^ (r % 8), so a quarter-warp touches 8
+        // distinct bank groups) and lane 0 stores the chunk back by TMA, which
+        // clips at O's edge.  Rows whose source is zero (SET, the pivot block
+        // in FWD, below the split in BWD) or a saved row W (FWD rows whose
+        // pivot source lies above the split) ignore the staged row.
+        const int qd = warp & 3, ew = warp - 2;
+        const uint32_t ring = sbase + TC_STAGES * STAGE_BYTES + (uint32_t)ew * (TE_PRE * TE_CHUNK);
+        unsigned char* ring_p = sbase_ptr + TC_STAGES * STAGE_BYTES + (size_t)ew * (TE_PRE * TE_CHUNK);
+        const uint32_t lbar0 = smem_u32(&ld_bar[ew][0]);
+        const bool need_src = a.mode != GM_SET;
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmO)) : "memory");
+        auto first_from = [&](int t) {
+            while (t < a.tiles && a.skip && a.skip[t / per_box]) t += gridDim.x;
+            return t;
+        };
+        auto geom = [&](int t, int& box, int& m0, int& n0, int& nch) {
+            box = t / per_box;
+            const int rem = t - box * per_box;
+            m0 = (rem / a.tiles_n) * TC_BM;
+            n0 = (rem % a.tiles_n) * TC_BN;
+            nch = (min(TC_BN, a.N - n0) + 31) / 32;
+        };
+        // load cursor (lane 0): next chunk to fetch is number lg, chunk lcc of tile lt
+        int lt = first_from(blockIdx.x), lcc = 0;
+        uint32_t lg = 0;
+        auto issue = [&]() {
+            int box, m0, n0, nch;
+            geom(lt, box, m0, n0, nch);
+            const uint32_t buf = lg % TE_PRE;
+            mbar_expect_tx(lbar0 + 8 * buf, TE_CHUNK);
+            tma_load_3d(ring + buf * TE_CHUNK, &tmO, lbar0 + 8 * buf, n0 + 32 * lcc, m0 + 32 * qd, box);
+            ++lg;
+            if (++lcc == nch) {
+                lcc = 0;
+                lt = first_from(lt + gridDim.x);
+            }
+        };
+        if (lane == 0 && need_src)
+            for (int i = 0; i < TE_LA && lt < a.tiles; ++i) issue();
+        uint32_t g = 0, j = 0;
+        bool ok = true;
+        for (int t = first_from(blockIdx.x); t < a.tiles && ok; t = first_from(t + gridDim.x), ++j) {
+            int box, m0, n0, nch;
+            geom(t, box, m0, n0, nch);
+            const int b = j & 1;
+            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            // this lane's row: source 0 = zero, 1 = staged O row, 2 = saved row of W
+            const int myr = m0 + qd * 32 + lane;
+            int srck = 0;
+            const float* wrow = nullptr;
+            if (myr < a.M) {
+                if (a.mode == GM_FWD) {
+                    if (myr >= a.split) {
+                        const int pr = a.perm[box * a.sP + myr];
+                        if (pr >= a.split) srck = 1;
+                        else {
+                            srck = 2;
+                            wrow = a.W + box * a.sW + (long long)pr * a.ldw;
+                        }
+                    }
+                } else if (a.mode == GM_BWD) {
+                    srck = myr < a.split ? 1 : 0;
+                } else if (a.mode == GM_ACC) {
+                    srck = 1;
+                }
+            }
+            for (int cc = 0; cc < nch; ++cc, ++g) {
+                const uint32_t buf = g % TE_PRE;
+                if (lane == 0) {
+                    if (need_src) {
+                        if (lt < a.tiles) {
+                            bulk_wait_read<TE_PRE - TE_LA - 1>();   // the buffer's last store has read it
+                            issue();
+                        }
+                    } else {
+                        bulk_wait_read<TE_PRE - 1>();
+                    }
+                }
+                __syncwarp();
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + cc * 32), v);
+                if (cc == nch - 1) {
+                    // the accumulator is in registers: hand the TMEM buffer back
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
+                }
+                if (need_src && !mbar_wait(lbar0 + 8 * buf, (g / TE_PRE) & 1)) ok = false;
+                if (!__all_sync(0xffffffffu, ok ? 1 : 0)) {
+                    ok = false;
+                    break;
+                }
+                float4* rowp = reinterpret_cast<float4*>(ring_p + buf * TE_CHUNK + lane * 128);
+                const int cb = n0 + cc * 32;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float4* p4 = rowp + (u ^ (lane & 7));
+                    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (srck == 1) {
+                        sv = *p4;
+                    } else if (srck == 2) {
+                        const int c = cb + 4 * u;
+                        sv.x = c < a.N ? wrow[c] : 0.f;
+                        sv.y = c + 1 < a.N ? wrow[c + 1] : 0.f;
+                        sv.z = c + 2 < a.N ? wrow[c + 2] : 0.f;
+                        sv.w = c + 3 < a.N ? wrow[c + 3] : 0.f;
+                    }
+                    *p4 = make_float4(sv.x - __uint_as_float(v[4 * u]), sv.y - __uint_as_float(v[4 * u + 1]),
+                                      sv.z - __uint_as_float(v[4 * u + 2]), sv.w - __uint_as_float(v[4 * u + 3]));
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_3d(&tmO, ring + buf * TE_CHUNK, cb, m0 + qd * 32, box);
+                    bulk_commit();
+                }
+            }
+        }
+        if (lane == 0) {
+            if (!ok) {
+                fail_sh = 1;
+                for (uint32_t h = g; h < lg; ++h) mbar_drain(lbar0 + 8 * (h % TE_PRE), (h / TE_PRE) & 1);
+            }
+            bulk_wait_all();
+        }
+        __syncwarp();
     } else {
         // Epilogue warps 2..5: warp w owns TMEM lane quarter qd = w % 4 (tile
         // rows 32 qd .. 32 qd + 31).  The source rows of each 32 x 32 chunk are
@@ -531,7 +722,7 @@ bool make_map(CUtensorMap* tm, const float* base, int K, long long rows, long lo
 }
 
 bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const float* Gp, long long g_plane,
-                      long long sGp, int NB, int K, const TcArgs& args, int nbox, cudaStream_t st)
+                      long long sGp, int NB, int K, const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma)
 {
     if (args.M <= 0 || args.N <= 0) return true;
     CUtensorMap ta, tb;
@@ -546,6 +737,19 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) && (a.N % 4 == 0) &&
             (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
+    CUtensorMap to{};
+    a.tma_epi = 0;
+    if (al16(a.O) && a.ldo % 4 == 0 && a.sO % 4 == 0 && allow_tma) {
+        auto fn = encode_fn();
+        cuuint64_t dims[3] = {(cuuint64_t)a.N, (cuuint64_t)a.M, (cuuint64_t)nbox};
+        cuuint64_t strides[2] = {(cuuint64_t)a.ldo * 4, (cuuint64_t)a.sO * 4};
+        cuuint32_t boxd[3] = {32, 32, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (fn && fn(&to, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.O, dims, strides, boxd, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            a.tma_epi = 1;
+    }
     static int num_sms = 0;
     if (!num_sms) {
         int dev = 0;
@@ -559,7 +763,7 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
     // as they converge, so their flop counts are upper bounds.
     const int cls = a.skip ? KC_UPDATE_TC_REFINE : KC_UPDATE_TC;
     prof_begin(cls, st);
-    k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, a);
+    k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, to, a);
     const double kk = (double)K;
     prof_end(cls, st, 2.0 * nbox * a.M * (double)a.N * kk,
              (double)nbox * (2.0 * (a.M + (double)a.N) * kk * 4 + 2.0 * a.M * (double)a.N * 4));
@@ -633,7 +837,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
                 Fs, NB, w.sF, 0, nb, NB, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr);
             prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
             TcArgs a = targs(Fs + (long long)nb * NB, NB, w.sF, n - k - nb, nb, GM_SET, 0);
-            if (!launch_tc_update(Fp, n - k - nb, w.sFp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st)) return false;
+            if (!launch_tc_update(Fp, n - k - nb, w.sFp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi)) return false;
         }
         if (k > 0) {
             float* Bp = w.Bp + 2 * P.bw_off[s];
@@ -644,7 +848,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
                 nullptr);
             prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
             TcArgs a = targs(Bs, NB, w.sB, k, nb, GM_SET, 0);
-            if (!launch_tc_update(Bp, k, w.sBp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st)) return false;
+            if (!launch_tc_update(Bp, k, w.sBp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi)) return false;
         }
         launch_pack_split(Fs, NB, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
         launch_pack_split(Bs, NB, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
@@ -654,7 +858,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
             TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
             a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
             if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
-                                  nb, a, nbox, st))
+                                  nb, a, nbox, st, P.tma_epi))
                 return false;
         }
     }
@@ -672,7 +876,7 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
         if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
-                              nb, a, nbox, st))
+                              nb, a, nbox, st, P.tma_epi))
             return false;
     }
     return true;
@@ -688,7 +892,7 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
         TcArgs a = targs(w.M + c0, ldm, w.sM, k + nb, nc, GM_BWD, k);
         a.skip = skip;
         if (!launch_tc_update(w.Bp + 2 * P.bw_off[s], k + nb, w.sBp, w.Gp, ldm * NB, w.sGp, NB,
-                              nb, a, nbox, st))
+                              nb, a, nbox, st, P.tma_epi))
             return false;
     }
     return true;

@@ -74,6 +74,30 @@ def test_dtn_parity_small(ctx, p, nbox, prec, tc, tol):
     assert rel_fro(S, So).max() < tol, rel_fro(S, So)
 
 
+@pytest.mark.parametrize("p,nbox,block", [(8, 3, 0), (9, 3, 32), (12, 2, 64), (16, 2, 0)])
+def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
+    """The TMA epilogue (aligned outputs; n = 343 at p = 9 leaves the
+    right-hand-side block unaligned, so both forms run in one call) and the
+    cp.async epilogue compute src - acc identically: bit-equal T and S, and
+    both match the oracle."""
+    h = np.array([0.125, 0.2, 0.15])
+    kappa = 15.0
+    lows = _lows(nbox, h, 7 + p)
+    field = hi.fourier_b_field().b
+    b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
+    try:
+        H.hps_set_option(ctx, H.HPS_OPT_TC_EPILOGUE, 1)
+        T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+    finally:
+        H.hps_set_option(ctx, H.HPS_OPT_TC_EPILOGUE, 0)
+    T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+    assert (st0 == 0).all() and (st1 == 0).all(), (st0, st1)
+    assert np.array_equal(T0, T1) and np.array_equal(S0, S1)
+    if p <= 12:
+        To, _, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=False)
+        assert rel_fro(T0, To).max() < 1e-10
+
+
 @pytest.mark.parametrize("prec,tc,tol", PRECS)
 @pytest.mark.parametrize("block", [32, 64])
 def test_dtn_parity_block_sizes(ctx, prec, tc, tol, block):
