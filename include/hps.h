@@ -102,6 +102,9 @@ typedef enum {
                                    CUDA graph on first use and replay the graph afterwards */
     HPS_OPT_TC_EPILOGUE = 8,    /* tcgen05 update epilogue: 0 (default) moves source and result tiles by TMA
                                    wherever the output is 16-byte aligned, 1 always uses the cp.async form */
+    HPS_OPT_TC_PAIRS = 9,       /* 1: tcgen05 products run on pairs of CTAs (a thread-block cluster of 2) that
+                                   share the right operand by TMA multicast; 0 (default): single CTAs, which
+                                   measured faster on the p = 16 workload */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;

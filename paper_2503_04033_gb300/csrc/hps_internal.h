@@ -53,6 +53,7 @@ struct Plan {
     size_t elt = 0;                  // bytes per LU element
     bool tc = false;                 // FP32 products on the tensor cores
     bool tma_epi = true;             // tcgen05 epilogue through TMA where O is 16-byte aligned
+    bool tc_pairs = false;           // tcgen05 products by CTA pairs sharing the right operand
     std::vector<int> k0, nbs;
     std::vector<long long> fw_off, bw_off, perm_off;
     long long fw_elems = 0, bw_elems = 0, perm_elems = 0;

@@ -25,6 +25,8 @@
 #include <climits>
 #include <cmath>
 
+#include <type_traits>
+
 #include "hps_internal.h"
 
 namespace hps {
@@ -38,67 +40,113 @@ __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
 // ---------------------------------------------------------------- assembly
 
-// M[r][c] for one box.  Interior row r = (i,j,k) carries the Helmholtz
-// operator of Eq. 2 collocated with the 1-D second-derivative matrices
-// (interior block A_ii); the RHS columns hold -A_ib (couplings of the row to
-// the face nodes on its three grid lines), loads f_i, or -A_ib u_b.
+// Rows per CTA of the operator build.
+constexpr int kBuildRows = 4;
+
+// Builds [A_ii | B] for a batch of boxes straight into the LU workspace
+// (Eq. 2's collocation restricted to the interior rows, Kronecker form:
+// A = -(D2x (x) I (x) I + I (x) D2y (x) I + I (x) I (x) D2z) - kappa^2 diag(b)).
+// A_ii has 3q - 2 nonzeros per row (the three grid lines through the node) and
+// the DtN block -A_ib six (the face nodes at the ends of those lines), so a CTA
+// first clears its kBuildRows rows with 16-byte stores and then writes the
+// nonzeros and the dense load / trace columns; every value is formed in FP64
+// and rounded once to T.  B is -A_ib (DTN), f_i (LOAD), -A_ib u_b (TRACE) or
+// [-A_ib | f_i] (DTN_LOAD).
 template <typename T>
-__global__ void k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
-                            double kappa2, const double* __restrict__ kappa_box,
-                            const double* __restrict__ b, long long sb, int rhs_kind,
-                            const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M,
-                            long long ldm, long long sM, int* status, int zero_row_box)
+__global__ void __launch_bounds__(256)
+k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2, double kappa2,
+            const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb, int rhs_kind,
+            const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M, long long ldm, long long sM,
+            int* status, int zero_row_box)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    const int box = blockIdx.z;
-    if (r >= n || c >= ldm_cols) return;
+    const int box = blockIdx.y;
+    const int r0 = blockIdx.x * kBuildRows;
+    const int rows = imin(kBuildRows, n - r0);
+    T* Mb = M + box * sM + (long long)r0 * ldm;
+    // 1. clear the rows (ldm and the row starts are multiples of 16 bytes)
+    {
+        using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int per = 16 / sizeof(T);
+        const int nv = (int)(ldm / per);
+        V* Mv = reinterpret_cast<V*>(Mb);
+        V z;
+        memset(&z, 0, sizeof(z));
+        for (int idx = threadIdx.x; idx < rows * nv; idx += blockDim.x) {
+            const int rr = idx / nv, cv = idx - rr * nv;
+            Mv[(long long)rr * (ldm / per) + cv] = z;
+        }
+    }
+    __syncthreads();
+    // 2. the nonzeros of A_ii and of the DtN block, and the dense columns
     const int q = p - 2, qq = q * q, pp = p * p;
-    const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
     const double* D2x = D2;
     const double* D2y = D2 + pp;
     const double* D2z = D2 + 2 * pp;
-    double v = 0.0;
-    if (c < n) {
-        const int i2 = c % q + 1, j2 = (c / q) % q + 1, k2 = c / qq + 1;
-        if (j == j2 && k == k2) v -= __ldg(D2x + i * p + i2);
-        if (i == i2 && k == k2) v -= __ldg(D2y + j * p + j2);
-        if (i == i2 && j == j2) v -= __ldg(D2z + k * p + k2);
-        if (r == c) {
-            const double bv = __ldg(b + box * sb + i + p * j + pp * k);
-            if (!isfinite(bv)) status[box] = HPS_EINVAL;
-            const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
-            v -= k2 * bv;
-        }
-    } else if (c < n + nrhs) {
-        int cf = c - n;
-        if (rhs_kind == RHS_DTN_LOAD) {
-            // [-A_ib | f_i]: the first m columns are the DtN block, the rest loads.
-            if (cf < 6 * qq) rhs_kind = RHS_DTN;
-            else { rhs_kind = RHS_LOAD; cf -= 6 * qq; }
-        }
-        if (rhs_kind == RHS_DTN) {
-            // -A_ib: face node (f, a, bb) couples to the interior row on its line.
-            const int f = cf / qq, s = cf % qq, a = s % q + 1, bb = s / q + 1;
-            const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
-            if (axis == 0 && j == a && k == bb) v = __ldg(D2x + i * p + e);
-            else if (axis == 1 && i == a && k == bb) v = __ldg(D2y + j * p + e);
-            else if (axis == 2 && i == a && j == bb) v = __ldg(D2z + k * p + e);
-        } else if (rhs_kind == RHS_LOAD) {
-            v = __ldg(rhs + box * s_rhs + (long long)cf * p * pp + i + p * j + pp * k);
-            if (!isfinite(v)) status[box] = HPS_EINVAL;
+    const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
+    const bool dtn = rhs_kind == RHS_DTN || rhs_kind == RHS_DTN_LOAD;
+    const int ndtn = dtn ? 6 : 0;
+    const int dense0 = rhs_kind == RHS_DTN_LOAD ? 6 * qq : 0;   // first dense column within B
+    const int ndense = rhs_kind == RHS_DTN ? 0 : nrhs - dense0;
+    const int dkind = rhs_kind == RHS_DTN_LOAD ? RHS_LOAD : rhs_kind;
+    const int per_row = 3 * q - 2 + ndtn + ndense;
+    for (int idx = threadIdx.x; idx < rows * per_row; idx += blockDim.x) {
+        const int rr = idx / per_row, e = idx - rr * per_row;
+        const int r = r0 + rr;
+        const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
+        T* row = Mb + (long long)rr * ldm;
+        if (e < 3 * q - 2) {
+            if (box == zero_row_box && r == 0) continue;   // test hook: exactly singular A_ii
+            int c;
+            double v;
+            if (e < q) {                                   // x line, with the diagonal
+                const int i2 = e + 1;
+                c = (i2 - 1) + q * (j - 1) + qq * (k - 1);
+                v = 0.0 - __ldg(D2x + i * p + i2);
+                if (i2 == i) {
+                    v -= __ldg(D2y + j * p + j);
+                    v -= __ldg(D2z + k * p + k);
+                    const double bv = __ldg(b + box * sb + i + p * j + pp * k);
+                    if (!isfinite(bv)) status[box] = HPS_EINVAL;
+                    v -= k2 * bv;
+                }
+            } else if (e < 2 * q - 1) {                    // y line off the diagonal
+                int j2 = e - q + 1;
+                if (j2 >= j) ++j2;
+                c = (i - 1) + q * (j2 - 1) + qq * (k - 1);
+                v = 0.0 - __ldg(D2y + j * p + j2);
+            } else {                                       // z line off the diagonal
+                int k2i = e - (2 * q - 1) + 1;
+                if (k2i >= k) ++k2i;
+                c = (i - 1) + q * (j - 1) + qq * (k2i - 1);
+                v = 0.0 - __ldg(D2z + k * p + k2i);
+            }
+            row[c] = T(v);
+        } else if (e < 3 * q - 2 + ndtn) {
+            // -A_ib: the face node at the end of one of the row's grid lines
+            const int f = e - (3 * q - 2), axis = f >> 1, ep = (f & 1) ? p - 1 : 0;
+            int a, bb;
+            double v;
+            if (axis == 0) { a = j; bb = k; v = __ldg(D2x + i * p + ep); }
+            else if (axis == 1) { a = i; bb = k; v = __ldg(D2y + j * p + ep); }
+            else { a = i; bb = j; v = __ldg(D2z + k * p + ep); }
+            row[n + f * qq + (a - 1) + q * (bb - 1)] = T(v);
         } else {
-            // -A_ib u_b: the six face nodes on this row's three grid lines.
-            const double* ub = rhs + box * s_rhs + (long long)cf * 6 * qq;
-            const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
-            v = __ldg(D2x + i * p) * ub[0 * qq + sx] + __ldg(D2x + i * p + p - 1) * ub[1 * qq + sx]
-              + __ldg(D2y + j * p) * ub[2 * qq + sy] + __ldg(D2y + j * p + p - 1) * ub[3 * qq + sy]
-              + __ldg(D2z + k * p) * ub[4 * qq + sz] + __ldg(D2z + k * p + p - 1) * ub[5 * qq + sz];
+            const int cf = e - (3 * q - 2 + ndtn);
+            double v;
+            if (dkind == RHS_LOAD) {
+                v = __ldg(rhs + box * s_rhs + (long long)cf * p * pp + i + p * j + pp * k);
+            } else {
+                // -A_ib u_b: the six face nodes on this row's three grid lines.
+                const double* ub = rhs + box * s_rhs + (long long)cf * 6 * qq;
+                const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
+                v = __ldg(D2x + i * p) * ub[0 * qq + sx] + __ldg(D2x + i * p + p - 1) * ub[1 * qq + sx]
+                  + __ldg(D2y + j * p) * ub[2 * qq + sy] + __ldg(D2y + j * p + p - 1) * ub[3 * qq + sy]
+                  + __ldg(D2z + k * p) * ub[4 * qq + sz] + __ldg(D2z + k * p + p - 1) * ub[5 * qq + sz];
+            }
             if (!isfinite(v)) status[box] = HPS_EINVAL;
+            row[n + dense0 + cf] = T(v);
         }
     }
-    if (box == zero_row_box && r == 0 && c < n) v = 0.0;   // test hook: exactly singular A_ii
-    M[box * sM + (long long)r * ldm + c] = T(v);
 }
 
 // ---------------------------------------------------------------- panel
@@ -915,10 +963,9 @@ void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, 
                       long long sb, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                       T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st)
 {
-    dim3 blk(32, 8);
-    dim3 grd((unsigned)((ldm + 31) / 32), (unsigned)((g.n + 7) / 8), (unsigned)nbox);
+    dim3 grd((unsigned)((g.n + kBuildRows - 1) / kBuildRows), (unsigned)nbox);
     prof_begin(KC_BUILD, st);
-    k_build_aug<T><<<grd, blk, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind,
+    k_build_aug<T><<<grd, 256, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind,
                                         rhs_src, s_rhs, M, ldm, sM, status, zero_row_box);
     prof_end(KC_BUILD, st, 0.0, (double)nbox * g.n * ldm * sizeof(T));
 }

@@ -55,6 +55,9 @@ struct TcArgs {
     float* O; long long ldo, sO;
     int M, N, kch;
     int tiles_m, tiles_n, tiles;
+    int nbox;
+    int cl;                          // CTA pairs (cluster of 2) sharing B by TMA multicast
+    int units, units_per_box;        // work units: tiles, or row-tile pairs x column tiles when cl
     int vec;                         // rows of O and W are 16-byte aligned: float4 epilogue
     int tma_epi;                     // O is 16-byte aligned: source tiles in and results out by TMA
     int mode, split;
@@ -142,6 +145,41 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm,
         : "memory");
 }
 
+// TMA load delivered to the same shared-memory offset in every CTA of the
+// cluster named in mask, each CTA's mbarrier at bar receiving the bytes.
+__device__ __forceinline__ void tma_load_4d_mc(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1,
+                                               int c2, int c3, uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%3, %4, %5, %6}], [%2], %7;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t nclusters_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1, int c2)
 {
     asm volatile(
@@ -204,6 +242,38 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+// Arrive, once the MMAs issued so far complete, on the mbarrier at bar in every
+// CTA of the cluster named in mask.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                     "r"(bar),
+                 "h"(mask)
+                 : "memory");
+}
+
+// The CTA's sequence of work units.  Alone, a CTA takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... (box-major, so a box's A and G stay in L2 while
+// its tiles run).  In a pair, both CTAs of cluster c take units c, c + nclusters,
+// ...; a unit is a pair of vertically adjacent row tiles at one column tile,
+// the CTA of rank r taking row tile 2 i + r.
+struct TcSched {
+    int u0, ustep, units, upb, tiles_n, rank, cl;
+    __device__ bool skipped(int u, const int* skip) const { return skip && skip[u / upb]; }
+    __device__ int first_from(int u, const int* skip) const
+    {
+        while (u < units && skipped(u, skip)) u += ustep;
+        return u;
+    }
+    __device__ void decode(int u, int& box, int& m0, int& n0) const
+    {
+        box = u / upb;
+        const int rem = u - box * upb, mi = rem / tiles_n;
+        n0 = (rem - mi * tiles_n) * TC_BN;
+        m0 = (cl ? 2 * mi + rank : mi) * TC_BM;
+    }
+};
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 {
     asm volatile(
@@ -249,9 +319,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Persistent update product O <- src - A G over (box, row tile, column tile).
-// Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (box-major, so
-// a box's A and G stay in L2 while its tiles run).  TMEM holds two 128 x 256
+// Persistent update product O <- src - A G over (box, row tile, column tile),
+// in the work-unit order of TcSched.  TMEM holds two 128 x 256
 // FP32 accumulators: the epilogue drains one while the MMAs fill the other.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -268,14 +337,27 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
-    const int per_box = a.tiles_m * a.tiles_n;
     unsigned char* sbase_ptr = smem_raw + (sbase - smem_u32(smem_raw));
+    TcSched sc;
+    sc.cl = a.cl;
+    sc.tiles_n = a.tiles_n;
+    sc.units = a.units;
+    sc.upb = a.units_per_box;
+    if (a.cl) {
+        sc.u0 = (int)cluster_id_x();
+        sc.ustep = (int)nclusters_x();
+        sc.rank = (int)cluster_ctarank();
+    } else {
+        sc.u0 = blockIdx.x;
+        sc.ustep = gridDim.x;
+        sc.rank = 0;
+    }
     float* tbuf_all = reinterpret_cast<float*>(sbase_ptr + TC_STAGES * STAGE_BYTES);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), a.cl ? 2 : 1);   // a pair: both CTAs' MMAs release a stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull_bar[b]), 1);
@@ -289,6 +371,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 2 * TC_BN);
     tc_fence_before();
     __syncthreads();
+    if (a.cl) cluster_sync_all();   // the partner's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
@@ -298,10 +381,10 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
             uint32_t g = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
-                const int box = t / per_box, rem = t - box * per_box;
-                if (a.skip && a.skip[box]) continue;
-                const int m0 = (rem / a.tiles_n) * TC_BM, n0 = (rem % a.tiles_n) * TC_BN;
+            for (int u = sc.u0; u < sc.units && ok; u += sc.ustep) {
+                if (sc.skipped(u, a.skip)) continue;
+                int box, m0, n0;
+                sc.decode(u, box, m0, n0);
                 for (int ch = 0; ch < a.kch; ++ch, ++g) {
                     const int s = g % TC_STAGES;
                     const uint32_t use = g / TC_STAGES;
@@ -315,22 +398,33 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     mbar_expect_tx(fb, STAGE_BYTES);
                     tma_load_4d(st, &tmA, fb, ch * TC_BK, m0, 0, box);
                     tma_load_4d(st + A_TILE, &tmA, fb, ch * TC_BK, m0, 1, box);
-                    tma_load_4d(st + 2 * A_TILE, &tmB, fb, ch * TC_BK, n0, 0, box);
-                    tma_load_4d(st + 2 * A_TILE + B_TILE, &tmB, fb, ch * TC_BK, n0, 1, box);
+                    if (a.cl) {
+                        // this CTA's half of B's rows, into both CTAs of the pair
+                        const uint32_t off = (uint32_t)sc.rank * (B_TILE / 2);
+                        const int nr = n0 + sc.rank * (TC_BN / 2);
+                        tma_load_4d_mc(st + 2 * A_TILE + off, &tmB, fb, ch * TC_BK, nr, 0, box, 0x3);
+                        tma_load_4d_mc(st + 2 * A_TILE + B_TILE + off, &tmB, fb, ch * TC_BK, nr, 1, box, 0x3);
+                    } else {
+                        tma_load_4d(st + 2 * A_TILE, &tmB, fb, ch * TC_BK, n0, 0, box);
+                        tma_load_4d(st + 2 * A_TILE + B_TILE, &tmB, fb, ch * TC_BK, n0, 1, box);
+                    }
                 }
             }
-            // Drain: the last loads issued into each stage have landed.
-            for (uint32_t h = (g > TC_STAGES ? g - TC_STAGES : 0); h < g; ++h)
+            // Drain: the last loads issued into each stage have landed, and
+            // (in a pair) both MMAs have released every stage, so no arrival
+            // from the partner is still on its way when this CTA exits.
+            for (uint32_t h = (g > TC_STAGES ? g - TC_STAGES : 0); h < g; ++h) {
                 if (!mbar_wait(smem_u32(&full_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
+                if (!mbar_wait(smem_u32(&empty_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tf32_idesc(TC_BM, TC_BN);
             uint32_t g = 0, j = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < a.tiles && ok; t += gridDim.x) {
-                const int box = t / per_box;
-                if (a.skip && a.skip[box]) continue;
+            for (int u = sc.u0; u < sc.units && ok; u += sc.ustep) {
+                if (sc.skipped(u, a.skip)) continue;
                 const int b = j & 1;
                 const uint32_t uj = j >> 1;
                 if (j >= 2 && !mbar_wait(smem_u32(&tempty_bar[b]), (uj - 1) & 1)) { fail_sh = 1; break; }
@@ -350,7 +444,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         mma_tf32(d, ah + o, bl + o, idesc, 1);
                         mma_tf32(d, al + o, bh + o, idesc, 1);
                     }
-                    mma_commit(smem_u32(&empty_bar[s]));
+                    if (a.cl) mma_commit_mc(smem_u32(&empty_bar[s]), 0x3);
+                    else mma_commit(smem_u32(&empty_bar[s]));
                 }
                 mma_commit(smem_u32(&tfull_bar[b]));
                 ++j;
@@ -374,19 +469,13 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t lbar0 = smem_u32(&ld_bar[ew][0]);
         const bool need_src = a.mode != GM_SET;
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmO)) : "memory");
-        auto first_from = [&](int t) {
-            while (t < a.tiles && a.skip && a.skip[t / per_box]) t += gridDim.x;
-            return t;
-        };
-        auto geom = [&](int t, int& box, int& m0, int& n0, int& nch) {
-            box = t / per_box;
-            const int rem = t - box * per_box;
-            m0 = (rem / a.tiles_n) * TC_BM;
-            n0 = (rem % a.tiles_n) * TC_BN;
+        auto first_from = [&](int u) { return sc.first_from(u, a.skip); };
+        auto geom = [&](int u, int& box, int& m0, int& n0, int& nch) {
+            sc.decode(u, box, m0, n0);
             nch = (min(TC_BN, a.N - n0) + 31) / 32;
         };
-        // load cursor (lane 0): next chunk to fetch is number lg, chunk lcc of tile lt
-        int lt = first_from(blockIdx.x), lcc = 0;
+        // load cursor (lane 0): next chunk to fetch is number lg, chunk lcc of unit lt
+        int lt = first_from(sc.u0), lcc = 0;
         uint32_t lg = 0;
         auto issue = [&]() {
             int box, m0, n0, nch;
@@ -397,14 +486,14 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             ++lg;
             if (++lcc == nch) {
                 lcc = 0;
-                lt = first_from(lt + gridDim.x);
+                lt = first_from(lt + sc.ustep);
             }
         };
         if (lane == 0 && need_src)
-            for (int i = 0; i < TE_LA && lt < a.tiles; ++i) issue();
+            for (int i = 0; i < TE_LA && lt < sc.units; ++i) issue();
         uint32_t g = 0, j = 0;
         bool ok = true;
-        for (int t = first_from(blockIdx.x); t < a.tiles && ok; t = first_from(t + gridDim.x), ++j) {
+        for (int t = first_from(sc.u0); t < sc.units && ok; t = first_from(t + sc.ustep), ++j) {
             int box, m0, n0, nch;
             geom(t, box, m0, n0, nch);
             const int b = j & 1;
@@ -436,7 +525,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 const uint32_t buf = g % TE_PRE;
                 if (lane == 0) {
                     if (need_src) {
-                        if (lt < a.tiles) {
+                        if (lt < sc.units) {
                             bulk_wait_read<TE_PRE - TE_LA - 1>();   // the buffer's last store has read it
                             issue();
                         }
@@ -509,10 +598,10 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t sb_u32 = smem_u32(sb);
         const int l8 = lane & 7, l3 = lane >> 3;
         uint32_t j = 0;
-        for (int t = blockIdx.x; t < a.tiles; t += gridDim.x) {
-            const int box = t / per_box, rem = t - box * per_box;
-            if (a.skip && a.skip[box]) continue;
-            const int m0 = (rem / a.tiles_n) * TC_BM, n0 = (rem % a.tiles_n) * TC_BN;
+        for (int u = sc.u0; u < sc.units; u += sc.ustep) {
+            if (sc.skipped(u, a.skip)) continue;
+            int box, m0, n0;
+            sc.decode(u, box, m0, n0);
             const int row0 = m0 + qd * 32;
             const int rows_here = max(0, min(32, a.M - row0));
             float* Ob = a.O + box * a.sO;
@@ -627,12 +716,13 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     tc_fence_before();
     __syncthreads();
+    if (a.cl) cluster_sync_all();   // neither CTA of a pair leaves while the other may still reach it
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * TC_BN);
     }
     if (threadIdx.x == 0 && fail_sh && a.status)
-        for (int bx = 0; bx < (a.tiles + per_box - 1) / per_box; ++bx) atomicCAS(a.status + bx, 0, HPS_ETIMEOUT);
+        for (int bx = 0; bx < a.nbox; ++bx) atomicCAS(a.status + bx, 0, HPS_ETIMEOUT);
 }
 
 // dst = [hi plane | lo plane] of the first nb columns of src (rows of pitch
@@ -722,18 +812,50 @@ bool make_map(CUtensorMap* tm, const float* base, int K, long long rows, long lo
 }
 
 bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const float* Gp, long long g_plane,
-                      long long sGp, int NB, int K, const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma)
+                      long long sGp, int NB, int K, const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma,
+                      bool allow_pairs)
 {
     if (args.M <= 0 || args.N <= 0) return true;
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, Ap, NB, a_rows, a_rows * NB, sAp, nbox, TC_BM) ||
-        !make_map(&tb, Gp, NB, args.N, g_plane, sGp, nbox, TC_BN))
-        return false;
+    static int num_sms = 0, max_pairs = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        if (num_sms <= 0) num_sms = 1;
+        // how many CTA pairs fit at once (an SM whose cluster partner is
+        // missing stays idle in pair mode)
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(num_sms & ~1));
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = TC_SMEM;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, (void*)k_tc_update, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            nc = 0;
+        }
+        max_pairs = nc;
+    }
     TcArgs a = args;
     a.kch = (K + TC_BK - 1) / TC_BK;
     a.tiles_m = (a.M + TC_BM - 1) / TC_BM;
     a.tiles_n = (a.N + TC_BN - 1) / TC_BN;
     a.tiles = a.tiles_m * a.tiles_n * nbox;
+    a.nbox = nbox;
+    a.cl = (allow_pairs && max_pairs > 0 && a.tiles_m >= 2) ? 1 : 0;
+    a.units_per_box = (a.cl ? (a.tiles_m + 1) / 2 : a.tiles_m) * a.tiles_n;
+    a.units = a.units_per_box * nbox;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, Ap, NB, a_rows, a_rows * NB, sAp, nbox, TC_BM) ||
+        !make_map(&tb, Gp, NB, args.N, g_plane, sGp, nbox, a.cl ? TC_BN / 2 : TC_BN))
+        return false;
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) && (a.N % 4 == 0) &&
             (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
@@ -750,20 +872,28 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             a.tma_epi = 1;
     }
-    static int num_sms = 0;
-    if (!num_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        if (num_sms <= 0) num_sms = 1;
-    }
-    dim3 grd((unsigned)std::min(a.tiles, num_sms));
     // Refinement replays (skip flags set) are timed apart: their boxes drop out
     // as they converge, so their flop counts are upper bounds.
     const int cls = a.skip ? KC_UPDATE_TC_REFINE : KC_UPDATE_TC;
     prof_begin(cls, st);
-    k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, to, a);
+    if (a.cl) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(2 * std::min(a.units, max_pairs)));
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = TC_SMEM;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k_tc_update, ta, tb, to, a) != cudaSuccess) return false;
+    } else {
+        dim3 grd((unsigned)std::min(a.units, num_sms));
+        k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, to, a);
+    }
     const double kk = (double)K;
     prof_end(cls, st, 2.0 * nbox * a.M * (double)a.N * kk,
              (double)nbox * (2.0 * (a.M + (double)a.N) * kk * 4 + 2.0 * a.M * (double)a.N * 4));
@@ -837,7 +967,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
                 Fs, NB, w.sF, 0, nb, NB, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr);
             prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
             TcArgs a = targs(Fs + (long long)nb * NB, NB, w.sF, n - k - nb, nb, GM_SET, 0);
-            if (!launch_tc_update(Fp, n - k - nb, w.sFp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi)) return false;
+            if (!launch_tc_update(Fp, n - k - nb, w.sFp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi, P.tc_pairs)) return false;
         }
         if (k > 0) {
             float* Bp = w.Bp + 2 * P.bw_off[s];
@@ -848,7 +978,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
                 nullptr);
             prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
             TcArgs a = targs(Bs, NB, w.sB, k, nb, GM_SET, 0);
-            if (!launch_tc_update(Bp, k, w.sBp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi)) return false;
+            if (!launch_tc_update(Bp, k, w.sBp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi, P.tc_pairs)) return false;
         }
         launch_pack_split(Fs, NB, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
         launch_pack_split(Bs, NB, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
@@ -858,7 +988,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
             TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
             a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
             if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
-                                  nb, a, nbox, st, P.tma_epi))
+                                  nb, a, nbox, st, P.tma_epi, P.tc_pairs))
                 return false;
         }
     }
@@ -876,7 +1006,7 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
         if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
-                              nb, a, nbox, st, P.tma_epi))
+                              nb, a, nbox, st, P.tma_epi, P.tc_pairs))
             return false;
     }
     return true;
@@ -892,7 +1022,7 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
         TcArgs a = targs(w.M + c0, ldm, w.sM, k + nb, nc, GM_BWD, k);
         a.skip = skip;
         if (!launch_tc_update(w.Bp + 2 * P.bw_off[s], k + nb, w.sBp, w.Gp, ldm * NB, w.sGp, NB,
-                              nb, a, nbox, st, P.tma_epi))
+                              nb, a, nbox, st, P.tma_epi, P.tc_pairs))
             return false;
     }
     return true;

@@ -78,8 +78,9 @@ def test_dtn_parity_small(ctx, p, nbox, prec, tc, tol):
 def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
     """The TMA epilogue (aligned outputs; n = 343 at p = 9 leaves the
     right-hand-side block unaligned, so both forms run in one call) and the
-    cp.async epilogue compute src - acc identically: bit-equal T and S, and
-    both match the oracle."""
+    cp.async epilogue compute src - acc identically, and CTA pairs sharing the
+    right operand issue the same MMAs as single CTAs: bit-equal T and S in all
+    three forms, and they match the oracle."""
     h = np.array([0.125, 0.2, 0.15])
     kappa = 15.0
     lows = _lows(nbox, h, 7 + p)
@@ -88,11 +89,15 @@ def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
     try:
         H.hps_set_option(ctx, H.HPS_OPT_TC_EPILOGUE, 1)
         T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+        H.hps_set_option(ctx, H.HPS_OPT_TC_PAIRS, 1)
+        T2, S2, st2 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
     finally:
         H.hps_set_option(ctx, H.HPS_OPT_TC_EPILOGUE, 0)
+        H.hps_set_option(ctx, H.HPS_OPT_TC_PAIRS, 0)
     T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
-    assert (st0 == 0).all() and (st1 == 0).all(), (st0, st1)
+    assert (st0 == 0).all() and (st1 == 0).all() and (st2 == 0).all(), (st0, st1, st2)
     assert np.array_equal(T0, T1) and np.array_equal(S0, S1)
+    assert np.array_equal(T0, T2) and np.array_equal(S0, S2)
     if p <= 12:
         To, _, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=False)
         assert rel_fro(T0, To).max() < 1e-10
