@@ -448,11 +448,12 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
         lu_factor<float>(P, w, nbox, status, st);
         lu_backward<float>(P, w, nbox, g.n, cs.r, nullptr, st);
     }
-    launch_extract<float>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st);
     // FP64 iterative refinement: R = B - A_ii X (FP64, matrix-free), solve with
-    // the FP32 factors, X += correction (FP64).
+    // the FP32 factors, X += correction (FP64).  ||X|| for the stopping rule
+    // is taken once, from the first solution.
     HPS_CUDA_TRY(cudaMemsetAsync(w.skip, 0, sizeof(int) * nbox, st));
     HPS_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(double) * 2 * nbox, st));
+    launch_extract<float>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st, w.norms);
     const int its = ctx->ir_iters;
     for (int it = 0; it < its; ++it) {
         launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
@@ -1102,7 +1103,7 @@ hps_status hps_dtn_gate(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const
         a.O = D; a.ldo = ld; a.sO = 0;
         a.M = n; a.N = (int)nk; a.K = n; a.alpha = 1.0f; a.mode = GM_SET;
         launch_gemm<float>(a, 1, st);
-        launch_ir_update(D, ld, k, n, k, w, ld, k, norms, nullptr, nbox, st);
+        launch_ir_update(D, ld, k, n, k, w, ld, k, norms, nullptr, nbox, st, true);
     }
     launch_dn(*g, nbox, w, ld, k, k, tp, (long long)k * m, 1, 0, st);
     launch_abb_add(*g, nbox, k, phi, tp, st);

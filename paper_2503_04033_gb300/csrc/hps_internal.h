@@ -195,7 +195,7 @@ void launch_dn(const Geometry& g, int nbox, const double* X, long long ldx, long
 
 template <typename TS>
 void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
-                    double* X, long long ldx, long long sX, int nbox, cudaStream_t st);
+                    double* X, long long ldx, long long sX, int nbox, cudaStream_t st, double* xnorm = nullptr);
 
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
@@ -204,7 +204,7 @@ void launch_residual(const Geometry& g, double kappa, const double* kappa_box, i
 
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
                       double* X, long long ldx, long long sX, double* norms /*[nbox][2]*/,
-                      const int* skip, int nbox, cudaStream_t st);
+                      const int* skip, int nbox, cudaStream_t st, bool want_xn = false);
 
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
                      int* iters, double* relcorr, int* status, cudaStream_t st);

@@ -21,6 +21,7 @@
 // Backward substitution (U x = y) runs the same product with
 //   B_s = [U[0:k, k:k+nb] U11^{-1}; -U11^{-1}], src(r) = M[r] for r < k, 0 after.
 // Forward substitution of new right-hand sides replays the stored (pi_s, F_s).
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -545,15 +546,44 @@ __global__ void k_dn(int p, int n, int m, int ncols, const double* __restrict__ 
 
 // ---------------------------------------------------------------- refinement
 
-template <typename TS>
-__global__ void k_extract(const TS* __restrict__ src, long long lds, long long sS, int n, int ncols,
-                          double* __restrict__ X, long long ldx, long long sX)
+// Sum of v over the CTA added to *out (one atomic per CTA).
+template <typename V>
+__device__ __forceinline__ void block_sum_add(V v, double* out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    const int box = blockIdx.z;
-    if (c >= ncols || r >= n) return;
-    X[box * sX + (long long)r * ldx + c] = double(src[box * sS + (long long)r * lds + c]);
+    __shared__ V part[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) part[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < nw; ++i) t += (double)part[i];
+        atomicAdd(out, t);
+    }
+}
+
+// X = src in FP64 (the first solution of the refinement); with xnorm, also
+// ||X||^2 per box into xnorm[2 box + 1] (FP32 partial sums: the stopping rule
+// needs the size of X, not its digits).  CTAs loop over rows, threads over
+// columns.
+template <typename TS>
+__global__ void __launch_bounds__(256)
+k_extract(const TS* __restrict__ src, long long lds, long long sS, int n, int ncols, double* __restrict__ X,
+          long long ldx, long long sX, double* xnorm)
+{
+    const int box = blockIdx.y;
+    float xn = 0.0f;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        const TS* srow = src + box * sS + (long long)r * lds;
+        double* xrow = X + box * sX + (long long)r * ldx;
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+            const TS v = srow[c];
+            xrow[c] = double(v);
+            if (xnorm) xn = fmaf((float)v, (float)v, xn);
+        }
+    }
+    if (xnorm) block_sum_add(xn, xnorm + 2 * box + 1);
 }
 
 // Shared-memory loads of the line tables kept in the loop: the tables are
@@ -737,33 +767,32 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
     }
 }
 
-// X += D (the FP32 correction) in FP64; accumulates ||D||^2 and ||X||^2 per box.
-__global__ void k_ir_update(const float* __restrict__ D, long long ldd, long long sD, int n, int ncols,
-                            double* __restrict__ X, long long ldx, long long sX, double* norms,
-                            const int* skip)
+// X += D (the FP32 correction) in FP64.  ||D||^2 per box goes to norms[2 box]
+// (FP32 partial sums, as for ||X|| in k_extract); with want_xn also ||X||^2
+// after the update, in FP64, to norms[2 box + 1].
+__global__ void __launch_bounds__(256)
+k_ir_update(const float* __restrict__ D, long long ldd, long long sD, int n, int ncols, double* __restrict__ X,
+            long long ldx, long long sX, double* norms, const int* skip, int want_xn)
 {
     const int box = blockIdx.y;
     if (skip && skip[box]) return;
-    double dn = 0.0, xn = 0.0;
-    const long long total = (long long)n * ncols;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long r = idx / ncols, c = idx - r * ncols;
-        const double d = double(D[box * sD + r * ldd + c]);
-        double* xp = X + box * sX + r * ldx + c;
-        const double x = *xp + d;
-        *xp = x;
-        dn += d * d;
-        xn += x * x;
+    float dn = 0.0f;
+    double xn = 0.0;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        const float* drow = D + box * sD + (long long)r * ldd;
+        double* xrow = X + box * sX + (long long)r * ldx;
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+            const float d = drow[c];
+            const double x = xrow[c] + double(d);
+            xrow[c] = x;
+            dn = fmaf(d, d, dn);
+            if (want_xn) xn = fma(x, x, xn);
+        }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        dn += __shfl_xor_sync(0xffffffffu, dn, off);
-        xn += __shfl_xor_sync(0xffffffffu, xn, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(norms + 2 * box, dn);
-        atomicAdd(norms + 2 * box + 1, xn);
+    block_sum_add(dn, norms + 2 * box);
+    if (want_xn) {
+        __syncthreads();
+        block_sum_add(xn, norms + 2 * box + 1);
     }
 }
 
@@ -783,8 +812,7 @@ __global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol,
     const double prev = relcorr[box];
     iters[box] += 1;
     relcorr[box] = rel;
-    norms[2 * box] = 0.0;
-    norms[2 * box + 1] = 0.0;
+    norms[2 * box] = 0.0;   // ||X||^2 (from the first solution) is kept
     bool done = rel <= tol;
     if (iters[box] > 1 && prev > 0.0) {
         const double rho = rel / prev;
@@ -1044,11 +1072,11 @@ void launch_dn(const Geometry& g, int nbox, const double* X, long long ldx, long
 
 template <typename TS>
 void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
-                    double* X, long long ldx, long long sX, int nbox, cudaStream_t st)
+                    double* X, long long ldx, long long sX, int nbox, cudaStream_t st, double* xnorm)
 {
-    dim3 grd((unsigned)((ncols + 127) / 128), (unsigned)n, (unsigned)nbox);
+    dim3 grd((unsigned)std::min(n, 96), (unsigned)nbox);
     prof_begin(KC_REFINE, st);
-    k_extract<TS><<<grd, 128, 0, st>>>(src, lds, sS, n, ncols, X, ldx, sX);
+    k_extract<TS><<<grd, 256, 0, st>>>(src, lds, sS, n, ncols, X, ldx, sX, xnorm);
     prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * (sizeof(TS) + 8));
 }
 
@@ -1099,14 +1127,11 @@ void launch_residual(const Geometry& g, double kappa, const double* kappa_box, i
 
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
                       double* X, long long ldx, long long sX, double* norms,
-                      const int* skip, int nbox, cudaStream_t st)
+                      const int* skip, int nbox, cudaStream_t st, bool want_xn)
 {
-    long long total = (long long)n * ncols;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 64) blocks = 64;
-    dim3 grd((unsigned)blocks, (unsigned)nbox);
+    dim3 grd((unsigned)std::min(n, 96), (unsigned)nbox);
     prof_begin(KC_REFINE, st);
-    k_ir_update<<<grd, 256, 0, st>>>(D, ldd, sD, n, ncols, X, ldx, sX, norms, skip);
+    k_ir_update<<<grd, 256, 0, st>>>(D, ldd, sD, n, ncols, X, ldx, sX, norms, skip, want_xn ? 1 : 0);
     prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * 20.0);
 }
 
@@ -1191,8 +1216,8 @@ template void launch_gather<double>(const double*, long long, long long, int, in
                                     long long, double*, double*, long long, long long, const int*, int,
                                     cudaStream_t);
 template void launch_extract<float>(const float*, long long, long long, int, int, double*, long long, long long,
-                                    int, cudaStream_t);
+                                    int, cudaStream_t, double*);
 template void launch_extract<double>(const double*, long long, long long, int, int, double*, long long,
-                                     long long, int, cudaStream_t);
+                                     long long, int, cudaStream_t, double*);
 
 }  // namespace hps
