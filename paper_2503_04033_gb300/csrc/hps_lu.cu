@@ -166,7 +166,6 @@ __device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi)
 // pivot search is a warp-shuffle arg-max followed by a cross-warp pass.  After the
 // panel: the step's row permutation perm[r] (source row of local row r),
 // F top = -L11^{-1} and B top = -U11^{-1}.
-constexpr int kRU = 16;                                   // rows per register tile
 constexpr int kSwapPer = (64 * kMaxNB + kPanelThreads - 1) / kPanelThreads;
 
 template <typename T>
@@ -308,8 +307,10 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
         }
         __syncthreads();
         // Right-looking update of the panel columns [jb+w, nb): U12 rows by a
-        // forward substitution, then the trailing rows in tiles of kRU rows
-        // by 32 columns per warp (kRU independent loads in flight per warp).
+        // forward substitution, then the trailing rows, each thread taking a
+        // 4 x 4 tile (per pivot column: 4 loads of L, one 4-wide load of U12,
+        // 16 multiply-adds); consecutive threads take consecutive column
+        // groups of the same rows, so the global accesses are contiguous.
         const int ncr = nb - jb - w;
         if (ncr > 0) {
             T* rb = Mb + (long long)(k + jb) * ldm + (k + jb + w);
@@ -323,29 +324,50 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
                 }
             }
             __syncthreads();
-            const int nch = (ncr + 31) >> 5, ngr = (R - w + kRU - 1) / kRU;
-            for (int item = warp; item < ngr * nch; item += NW) {
-                const int gi = item / nch, ch = item - gi * nch;
-                const int col = (ch << 5) + lane;
-                const int r0 = w + gi * kRU;
-                const bool cok = col < ncr;
-                T acc[kRU];
-                int src[kRU];
+            const int rg = (R - w + 3) >> 2, cg = (ncr + 3) >> 2;
+            const bool vec = sizeof(T) == 4 && ((reinterpret_cast<uintptr_t>(rb) & 15) == 0) && (ldm & 3) == 0;
+            for (int item = tid; item < rg * cg; item += kPanelThreads) {
+                const int gi = item / cg, gc = item - gi * cg;
+                const int r0 = w + 4 * gi, c0 = 4 * gc;
+                int src[4];
+                T acc[4][4];
 #pragma unroll
-                for (int u = 0; u < kRU; ++u) {
+                for (int u = 0; u < 4; ++u) {
                     const int r = r0 + u;
-                    src[u] = r < R ? pos2row[r] : 0;
-                    acc[u] = (r < R && cok) ? rb[(long long)r * ldm + col] : T(0);
+                    src[u] = pos2row[r < R ? r : w];
+                    T* rowp = rb + (long long)r * ldm + c0;
+                    if (r < R && vec && c0 + 3 < ncr) {
+                        const float4 v4 = *reinterpret_cast<const float4*>(rowp);
+                        acc[u][0] = T(v4.x); acc[u][1] = T(v4.y); acc[u][2] = T(v4.z); acc[u][3] = T(v4.w);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = (r < R && c0 + v < ncr) ? rowp[v] : T(0);
+                    }
                 }
                 for (int c = 0; c < w; ++c) {
-                    const T x = Xs[c * kMaxNB + col];
+                    T a[4], bv[4];
 #pragma unroll
-                    for (int u = 0; u < kRU; ++u) acc[u] -= Sb[c * R + src[u]] * x;
+                    for (int u = 0; u < 4; ++u) a[u] = Sb[c * R + src[u]];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) bv[v] = Xs[c * kMaxNB + c0 + v];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] -= a[u] * bv[v];
                 }
 #pragma unroll
-                for (int u = 0; u < kRU; ++u) {
+                for (int u = 0; u < 4; ++u) {
                     const int r = r0 + u;
-                    if (r < R && cok) rb[(long long)r * ldm + col] = acc[u];
+                    if (r >= R) break;
+                    T* rowp = rb + (long long)r * ldm + c0;
+                    if (vec && c0 + 3 < ncr) {
+                        *reinterpret_cast<float4*>(rowp) =
+                            make_float4(float(acc[u][0]), float(acc[u][1]), float(acc[u][2]), float(acc[u][3]));
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            if (c0 + v < ncr) rowp[v] = acc[u][v];
+                    }
                 }
             }
             __syncthreads();
