@@ -105,6 +105,10 @@ typedef enum {
     HPS_OPT_TC_PAIRS = 9,       /* 1: tcgen05 products run on pairs of CTAs (a thread-block cluster of 2) that
                                    share the right operand by TMA multicast; 0 (default): single CTAs, which
                                    measured faster on the p = 16 workload */
+    HPS_OPT_LU_PAIRS = 10,      /* 1 (default): on the tensor-core path, consecutive LU steps are joined in
+                                   pairs (look-ahead on the next panel, one 2 NB-deep update per pair and one
+                                   product per pair in the solves); 0: one step at a time.  Results agree to
+                                   rounding */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;

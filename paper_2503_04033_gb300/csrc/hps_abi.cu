@@ -87,6 +87,7 @@ struct hps_ctx {
     int nb_opt = 0;
     int tc_epi_cp = 0;          // 1: tcgen05 epilogue always in the cp.async form
     int tc_pairs = 0;           // 1: tcgen05 products by CTA pairs sharing the right operand
+    int lu_pairs = 1;           // 0: no joining of LU steps in pairs on the tcgen05 path
     int use_tc = 1;
     int sync = 0;
     int zero_row_box = -1;
@@ -352,7 +353,8 @@ long long job_srhs(const Job& j)
 
 Plan job_plan(const hps_ctx* ctx, const Job& j, hps_precision prec)
 {
-    Plan P = make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64);
+    Plan P = make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64,
+                       ctx->lu_pairs != 0);
     P.tma_epi = ctx->tc_epi_cp == 0;
     P.tc_pairs = ctx->tc_pairs != 0;
     return P;
@@ -636,7 +638,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     const bool use_graph = ctx->graphs && !ctx->prof_on;
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
@@ -860,6 +862,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
     case HPS_OPT_TC_PAIRS:
         if (!(value == 0 || value == 1)) return HPS_EINVAL;
         ctx->tc_pairs = (int)value;
+        return HPS_OK;
+    case HPS_OPT_LU_PAIRS:
+        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        ctx->lu_pairs = (int)value;
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;

@@ -54,6 +54,8 @@ struct Plan {
     bool tc = false;                 // FP32 products on the tensor cores
     bool tma_epi = true;             // tcgen05 epilogue through TMA where O is 16-byte aligned
     bool tc_pairs = false;           // tcgen05 products by CTA pairs sharing the right operand
+    bool step_pairs = false;         // tcgen05 path: consecutive LU steps joined in pairs
+    int KG = 0;                      // K extent of the gathered right operand (NB, or 2 NB with pairs)
     std::vector<int> k0, nbs;
     std::vector<long long> fw_off, bw_off, perm_off;
     long long fw_elems = 0, bw_elems = 0, perm_elems = 0;
@@ -62,7 +64,7 @@ struct Plan {
     size_t per_box = 0;
 };
 
-inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x)
+inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x, bool step_pairs = true)
 {
     Plan P;
     P.n = n;
@@ -94,11 +96,13 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
         P.perm_elems += (n - k);
     }
     P.nsteps = (int)P.k0.size();
+    P.step_pairs = P.tc && step_pairs && P.nsteps > 1;
+    P.KG = P.step_pairs ? 2 * NB : NB;
     const size_t A = 256;
     P.bM = align_up((size_t)n * P.ldm * P.elt, A);
     P.bF = align_up((size_t)P.fw_elems * P.elt, A);
     P.bB = align_up((size_t)P.bw_elems * P.elt, A);
-    P.bW = align_up((size_t)NB * P.ldm * P.elt, A);
+    P.bW = align_up((size_t)P.KG * P.ldm * P.elt, A);
     P.bG = P.bW;
     P.bP = align_up((size_t)P.perm_elems * sizeof(int), A);
     P.bX = need_x ? align_up((size_t)n * r * sizeof(double), A) : 0;
@@ -106,7 +110,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
         // split (hi, lo) K-major copies of F, B and G for the tensor-core products
         P.bFp = align_up((size_t)P.fw_elems * 2 * sizeof(float), A);
         P.bBp = align_up((size_t)P.bw_elems * 2 * sizeof(float), A);
-        P.bGp = align_up((size_t)P.ldm * NB * 2 * sizeof(float), A);
+        P.bGp = align_up((size_t)P.ldm * P.KG * 2 * sizeof(float), A);
     }
     P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + 64;
     return P;

@@ -23,6 +23,8 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <utility>
+#include <vector>
 
 #include "hps_internal.h"
 
@@ -54,6 +56,7 @@ constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
 struct TcArgs {
     float* O; long long ldo, sO;
     int M, N, kch;
+    int kch1, a2_off;                // K chunks from the first A map; row offset of the second map
     int tiles_m, tiles_n, tiles;
     int nbox;
     int cl;                          // CTA pairs (cluster of 2) sharing B by TMA multicast
@@ -323,8 +326,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // in the work-unit order of TcSched.  TMEM holds two 128 x 256
 // FP32 accumulators: the epilogue drains one while the MMAs fill the other.
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            const __grid_constant__ CUtensorMap tmO, TcArgs a)
+k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+            const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO, TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t ld_bar[TC_EPI_WARPS][TE_PRE];
@@ -378,6 +381,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (warp == 0) {
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
             uint32_t g = 0;
             bool ok = true;
@@ -396,8 +400,13 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     const uint32_t fb = smem_u32(&full_bar[s]);
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     mbar_expect_tx(fb, STAGE_BYTES);
-                    tma_load_4d(st, &tmA, fb, ch * TC_BK, m0, 0, box);
-                    tma_load_4d(st + A_TILE, &tmA, fb, ch * TC_BK, m0, 1, box);
+                    // A's K chunks past kch1 come from the second map, whose row 0 is
+                    // row a2_off of the product (rows above it load as zeros)
+                    const bool second = ch >= a.kch1;
+                    const CUtensorMap* ma = second ? &tmA2 : &tmA;
+                    const int ka = (second ? ch - a.kch1 : ch) * TC_BK, ra = second ? m0 - a.a2_off : m0;
+                    tma_load_4d(st, ma, fb, ka, ra, 0, box);
+                    tma_load_4d(st + A_TILE, ma, fb, ka, ra, 1, box);
                     if (a.cl) {
                         // this CTA's half of B's rows, into both CTAs of the pair
                         const uint32_t off = (uint32_t)sc.rank * (B_TILE / 2);
@@ -811,10 +820,26 @@ bool make_map(CUtensorMap* tm, const float* base, int K, long long rows, long lo
     return r == CUDA_SUCCESS;
 }
 
-bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const float* Gp, long long g_plane,
-                      long long sGp, int NB, int K, const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma,
-                      bool allow_pairs)
+// Left operand of an update product: split rows of NB values (K-major), a_rows
+// rows per box; a second part (rows offset by a2_off, K2 further values of K)
+// joins a pair of LU steps into one product.
+struct TcLeft {
+    const float* A; long long rows, sA;
+    const float* A2; long long rows2, sA2;
+    int K1, K2, a2_off;
+};
+
+TcLeft left1(const float* A, long long rows, long long sA, int K)
 {
+    TcLeft l{};
+    l.A = A; l.rows = rows; l.sA = sA; l.K1 = K;
+    return l;
+}
+
+bool launch_tc_update(const TcLeft& L, const float* Gp, long long g_plane, long long sGp, int gK, int NB,
+                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs)
+{
+    const int K = L.K1 + L.K2;
     if (args.M <= 0 || args.N <= 0) return true;
     static int num_sms = 0, max_pairs = 0;
     if (!num_sms) {
@@ -845,6 +870,8 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
     }
     TcArgs a = args;
     a.kch = (K + TC_BK - 1) / TC_BK;
+    a.kch1 = L.K2 ? L.K1 / TC_BK : a.kch;   // L.K1 is a whole block when a second part follows
+    a.a2_off = L.a2_off;
     a.tiles_m = (a.M + TC_BM - 1) / TC_BM;
     a.tiles_n = (a.N + TC_BN - 1) / TC_BN;
     a.tiles = a.tiles_m * a.tiles_n * nbox;
@@ -852,10 +879,15 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
     a.cl = (allow_pairs && max_pairs > 0 && a.tiles_m >= 2) ? 1 : 0;
     a.units_per_box = (a.cl ? (a.tiles_m + 1) / 2 : a.tiles_m) * a.tiles_n;
     a.units = a.units_per_box * nbox;
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, Ap, NB, a_rows, a_rows * NB, sAp, nbox, TC_BM) ||
-        !make_map(&tb, Gp, NB, args.N, g_plane, sGp, nbox, a.cl ? TC_BN / 2 : TC_BN))
+    CUtensorMap ta, ta2, tb;
+    if (!make_map(&ta, L.A, NB, L.rows, L.rows * NB, L.sA, nbox, TC_BM) ||
+        !make_map(&tb, Gp, gK, args.N, g_plane, sGp, nbox, a.cl ? TC_BN / 2 : TC_BN))
         return false;
+    if (L.K2) {
+        if (!make_map(&ta2, L.A2, NB, L.rows2, L.rows2 * NB, L.sA2, nbox, TC_BM)) return false;
+    } else {
+        ta2 = ta;
+    }
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) && (a.N % 4 == 0) &&
             (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
@@ -889,10 +921,10 @@ bool launch_tc_update(const float* Ap, long long a_rows, long long sAp, const fl
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k_tc_update, ta, tb, to, a) != cudaSuccess) return false;
+        if (cudaLaunchKernelEx(&cfg, k_tc_update, ta, ta2, tb, to, a) != cudaSuccess) return false;
     } else {
         dim3 grd((unsigned)std::min(a.units, num_sms));
-        k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, tb, to, a);
+        k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, ta2, tb, to, a);
     }
     const double kk = (double)K;
     prof_end(cls, st, 2.0 * nbox * a.M * (double)a.N * kk,
@@ -914,10 +946,10 @@ void launch_pack_split(const float* src, long long lds, long long sS, int rows, 
 void launch_gather_pack(const Plan& P, Work<float>& w, int k, int nb, int c0, int nc, const int* perm, bool save_w,
                         const int* skip, int nbox, cudaStream_t st)
 {
-    dim3 grd((unsigned)((nc + 31) / 32), (unsigned)(P.NB / 32), (unsigned)nbox);
+    dim3 grd((unsigned)((nc + 31) / 32), (unsigned)(P.KG / 32), (unsigned)nbox);
     prof_begin(KC_GATHER, st);
-    k_gather_pack<<<grd, dim3(32, 8), 0, st>>>(w.M, P.ldm, w.sM, k, nb, P.NB, c0, nc, perm, w.sP,
-                                               save_w ? w.W : nullptr, P.ldm, w.sG, w.Gp, P.ldm * P.NB, w.sGp, skip);
+    k_gather_pack<<<grd, dim3(32, 8), 0, st>>>(w.M, P.ldm, w.sM, k, nb, P.KG, c0, nc, perm, w.sP,
+                                               save_w ? w.W : nullptr, P.ldm, w.sG, w.Gp, P.ldm * P.KG, w.sGp, skip);
     prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * 4 * (save_w ? 4 : 3));
 }
 
@@ -943,11 +975,114 @@ bool tc_abort_raised()
     return v != 0;
 }
 
+// ---------------------------------------------------------------- LU sequences
+//
+// With step pairs (P.step_pairs), two consecutive LU steps s, s+1 act as one
+// step of 2 NB rows wherever they apply to many columns.  Step s+1 applied to
+// the columns of F_s, and step s applied (backwards) to the columns of
+// B_{s+1}, give the pair's operators:
+//   forward  [F_s' | F_{s+1}] (F_{s+1}'s rows start NB rows lower),
+//   backward [B_s | B_{s+1}'],
+// with the composed row permutation pi_c(i) = pi_s(i) for i < nb_s, else
+// pi_s(nb_s + pi_{s+1}(i - nb_s)).  A row below the pair's block still either
+// stays in place or receives a block row, so the update epilogue is the same
+// with split = 2 NB.  The factorisation updates only the next block's columns
+// with step s (look-ahead), factors that panel, then updates everything else
+// once with the pair; the solves run one product per pair.  Each pass over the
+// trailing rows and right-hand sides then serves two steps.
+
+namespace {
+
+// pi_s <- pi_c (both arrays in shared memory first; one CTA per box).
+__global__ void k_perm_compose(int* __restrict__ perm0, const int* __restrict__ perm1, long long sP, int R, int nb0)
+{
+    extern __shared__ int psh[];
+    int* a = psh;
+    int* b = psh + R;
+    const int box = blockIdx.x;
+    int* p0 = perm0 + box * sP;
+    const int* p1 = perm1 + box * sP;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) a[i] = p0[i];
+    for (int i = threadIdx.x; i < R - nb0; i += blockDim.x) b[i] = p1[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) p0[i] = i < nb0 ? a[i] : a[nb0 + b[i - nb0]];
+}
+
+void launch_perm_compose(int* perm0, const int* perm1, long long sP, int R, int nb0, int nbox, cudaStream_t st)
+{
+    const size_t smem = (size_t)(2 * R - nb0) * sizeof(int);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_perm_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    k_perm_compose<<<nbox, 256, smem, st>>>(perm0, perm1, sP, R, nb0);
+}
+
+void gather_pack_raw(const float* M, long long ldm, long long sM, int k, int nb, int gK, int c0, int nc,
+                     const int* perm, long long sP, float* W, long long ldw, long long sW, float* Gp, long long plane,
+                     long long sGp, const int* skip, int nbox, cudaStream_t st)
+{
+    prof_begin(KC_GATHER, st);
+    k_gather_pack<<<dim3((unsigned)((nc + 31) / 32), (unsigned)(gK / 32), (unsigned)nbox), dim3(32, 8), 0, st>>>(
+        M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, Gp, plane, sGp, skip);
+    prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * 4 * (W ? 4 : 3));
+}
+
+// Left operands of the pair (s, s+1).
+TcLeft left_fwd_pair(const Plan& P, const Work<float>& w, int s)
+{
+    TcLeft l{};
+    l.A = w.Fp + 2 * P.fw_off[s];
+    l.rows = P.n - P.k0[s];
+    l.sA = w.sFp;
+    l.K1 = P.nbs[s];
+    l.A2 = w.Fp + 2 * P.fw_off[s + 1];
+    l.rows2 = P.n - P.k0[s + 1];
+    l.sA2 = w.sFp;
+    l.K2 = P.nbs[s + 1];
+    l.a2_off = P.nbs[s];
+    return l;
+}
+
+TcLeft left_bwd_pair(const Plan& P, const Work<float>& w, int s)
+{
+    TcLeft l{};
+    l.A = w.Bp + 2 * P.bw_off[s];
+    l.rows = P.k0[s] + P.nbs[s];
+    l.sA = w.sBp;
+    l.K1 = P.nbs[s];
+    l.A2 = w.Bp + 2 * P.bw_off[s + 1];
+    l.rows2 = P.k0[s + 1] + P.nbs[s + 1];
+    l.sA2 = w.sBp;
+    l.K2 = P.nbs[s + 1];
+    l.a2_off = 0;
+    return l;
+}
+
+// Units of the solves: (first step, 1 or 2 steps).
+std::vector<std::pair<int, int>> solve_units(const Plan& P)
+{
+    std::vector<std::pair<int, int>> u;
+    for (int s = 0; s < P.nsteps;) {
+        const int len = (P.step_pairs && s + 1 < P.nsteps) ? 2 : 1;
+        u.emplace_back(s, len);
+        s += len;
+    }
+    return u;
+}
+
+}  // namespace
+
 bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStream_t st)
 {
-    const int n = P.n, NB = P.NB;
-    const long long ldm = P.ldm;
-    for (int s = 0; s < P.nsteps; ++s) {
+    const int n = P.n, NB = P.NB, KG = P.KG;
+    const long long ldm = P.ldm, gplane = ldm * KG;
+    auto up = [&](const TcLeft& L, const TcArgs& a) {
+        return launch_tc_update(L, w.Gp, gplane, w.sGp, KG, NB, a, nbox, st, P.tma_epi, P.tc_pairs);
+    };
+    // Panel of step s, its operators F_s and B_s (FP32 and split copies).
+    auto panel_ops = [&](int s) -> bool {
         const int k = P.k0[s], nb = P.nbs[s];
         float* Fs = w.F + P.fw_off[s];
         float* Bs = w.B + P.bw_off[s];
@@ -958,38 +1093,81 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         // it, U01 U11^{-1} = -(U01 * B_top), as tensor-core products: the left
         // operand is split into the step's own (not yet filled) pack region,
         // the right one, transposed, into the G pack.
-        const long long gplane = ldm * NB;
         if (n - k - nb > 0) {
             float* Fp = w.Fp + 2 * P.fw_off[s];
             launch_pack_split(w.M + (long long)(k + nb) * ldm + k, ldm, w.sM, n - k - nb, NB, nb, Fp, w.sFp, nbox, st);
-            prof_begin(KC_GATHER, st);
-            k_gather_pack<<<dim3((unsigned)((nb + 31) / 32), (unsigned)(NB / 32), (unsigned)nbox), dim3(32, 8), 0, st>>>(
-                Fs, NB, w.sF, 0, nb, NB, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr);
-            prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
+            gather_pack_raw(Fs, NB, w.sF, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr,
+                            nbox, st);
             TcArgs a = targs(Fs + (long long)nb * NB, NB, w.sF, n - k - nb, nb, GM_SET, 0);
-            if (!launch_tc_update(Fp, n - k - nb, w.sFp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi, P.tc_pairs)) return false;
+            if (!up(left1(Fp, n - k - nb, w.sFp, nb), a)) return false;
         }
         if (k > 0) {
             float* Bp = w.Bp + 2 * P.bw_off[s];
             launch_pack_split(w.M + k, ldm, w.sM, k, NB, nb, Bp, w.sBp, nbox, st);
-            prof_begin(KC_GATHER, st);
-            k_gather_pack<<<dim3((unsigned)((nb + 31) / 32), (unsigned)(NB / 32), (unsigned)nbox), dim3(32, 8), 0, st>>>(
-                Bs + (long long)k * NB, NB, w.sB, 0, nb, NB, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
-                nullptr);
-            prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nb * 12);
+            gather_pack_raw(Bs + (long long)k * NB, NB, w.sB, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp,
+                            gplane, w.sGp, nullptr, nbox, st);
             TcArgs a = targs(Bs, NB, w.sB, k, nb, GM_SET, 0);
-            if (!launch_tc_update(Bp, k, w.sBp, w.Gp, gplane, w.sGp, NB, nb, a, nbox, st, P.tma_epi, P.tc_pairs)) return false;
+            if (!up(left1(Bp, k, w.sBp, nb), a)) return false;
         }
         launch_pack_split(Fs, NB, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
         launch_pack_split(Bs, NB, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
-        const int c0 = k + nb, nc = n + P.r - c0;
+        return true;
+    };
+    // Step s's update of M's columns [c0, c0 + nc).
+    auto update1 = [&](int s, int c0, int nc) -> bool {
+        if (nc <= 0) return true;
+        const int k = P.k0[s], nb = P.nbs[s];
+        int* Ps = w.perm + P.perm_off[s];
+        launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st);
+        TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
+        a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
+        return up(left1(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, nb), a);
+    };
+    // The pair's operators and permutation from those of its two steps.
+    auto combine = [&](int s) -> bool {
+        const int k = P.k0[s], nb0 = P.nbs[s], k1 = P.k0[s + 1], nb1 = P.nbs[s + 1];
+        float* F0 = w.F + P.fw_off[s];
+        float* B1 = w.B + P.bw_off[s + 1];
+        int* P0 = w.perm + P.perm_off[s];
+        const int* P1 = w.perm + P.perm_off[s + 1];
+        {   // F_s' = forward step s+1 on F_s's rows [nb0, n - k)
+            gather_pack_raw(F0, NB, w.sF, nb0, nb1, KG, 0, nb0, P1, w.sP, w.W, NB, w.sG, w.Gp, gplane, w.sGp, nullptr,
+                            nbox, st);
+            TcArgs a = targs(F0 + (long long)nb0 * NB, NB, w.sF, n - k1, nb0, GM_FWD, nb1);
+            a.perm = P1; a.sP = w.sP; a.W = w.W; a.ldw = NB; a.sW = w.sG; a.status = status;
+            if (!up(left1(w.Fp + 2 * P.fw_off[s + 1], n - k1, w.sFp, nb1), a)) return false;
+            launch_pack_split(F0, NB, w.sF, n - k, NB, nb0, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
+        }
+        {   // B_{s+1}' = backward step s on B_{s+1}'s rows [0, k + nb0)
+            gather_pack_raw(B1, NB, w.sB, k, nb0, KG, 0, nb1, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
+                            nullptr, nbox, st);
+            TcArgs a = targs(B1, NB, w.sB, k + nb0, nb1, GM_BWD, k);
+            a.status = status;
+            if (!up(left1(w.Bp + 2 * P.bw_off[s], k + nb0, w.sBp, nb0), a)) return false;
+            launch_pack_split(B1, NB, w.sB, k1 + nb1, NB, nb1, w.Bp + 2 * P.bw_off[s + 1], w.sBp, nbox, st);
+        }
+        launch_perm_compose(P0, P1, w.sP, n - k, nb0, nbox, st);
+        return true;
+    };
+    for (const auto& u : solve_units(P)) {
+        const int s = u.first, k = P.k0[s];
+        if (u.second == 1) {
+            if (!panel_ops(s)) return false;
+            if (!update1(s, k + P.nbs[s], n + P.r - k - P.nbs[s])) return false;
+            continue;
+        }
+        const int nb0 = P.nbs[s], wp = nb0 + P.nbs[s + 1];
+        if (!panel_ops(s)) return false;
+        if (!update1(s, k + nb0, P.nbs[s + 1])) return false;   // look-ahead: the next panel's columns
+        if (!panel_ops(s + 1)) return false;
+        if (!combine(s)) return false;
+        const int c0 = k + wp, nc = n + P.r - c0;
         if (nc > 0) {
-            launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st);
-            TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
-            a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
-            if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
-                                  nb, a, nbox, st, P.tma_epi, P.tc_pairs))
-                return false;
+            int* Pc = w.perm + P.perm_off[s];
+            launch_gather_pack(P, w, k, wp, c0, nc, Pc, true, nullptr, nbox, st);
+            TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
+            a.perm = Pc; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
+            if (!up(left_fwd_pair(P, w, s), a)) return false;
         }
     }
     return true;
@@ -997,16 +1175,17 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
 
 bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st)
 {
-    const int n = P.n, NB = P.NB;
+    const int n = P.n;
     const long long ldm = P.ldm;
-    for (int s = 0; s < P.nsteps; ++s) {
-        const int k = P.k0[s], nb = P.nbs[s];
+    for (const auto& u : solve_units(P)) {
+        const int s = u.first, k = P.k0[s];
+        const int wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
         int* Ps = w.perm + P.perm_off[s];
-        launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, skip, nbox, st);
-        TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
+        launch_gather_pack(P, w, k, wp, c0, nc, Ps, true, skip, nbox, st);
+        TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
-        if (!launch_tc_update(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, w.Gp, ldm * NB, w.sGp, NB,
-                              nb, a, nbox, st, P.tma_epi, P.tc_pairs))
+        const TcLeft L = u.second == 2 ? left_fwd_pair(P, w, s) : left1(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, wp);
+        if (!launch_tc_update(L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
             return false;
     }
     return true;
@@ -1014,15 +1193,16 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
 
 bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st)
 {
-    const int NB = P.NB;
     const long long ldm = P.ldm;
-    for (int s = P.nsteps - 1; s >= 0; --s) {
-        const int k = P.k0[s], nb = P.nbs[s];
-        launch_gather_pack(P, w, k, nb, c0, nc, nullptr, false, skip, nbox, st);
-        TcArgs a = targs(w.M + c0, ldm, w.sM, k + nb, nc, GM_BWD, k);
+    const auto units = solve_units(P);
+    for (auto it = units.rbegin(); it != units.rend(); ++it) {
+        const int s = it->first, k = P.k0[s];
+        const int wp = it->second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
+        launch_gather_pack(P, w, k, wp, c0, nc, nullptr, false, skip, nbox, st);
+        TcArgs a = targs(w.M + c0, ldm, w.sM, k + wp, nc, GM_BWD, k);
         a.skip = skip;
-        if (!launch_tc_update(w.Bp + 2 * P.bw_off[s], k + nb, w.sBp, w.Gp, ldm * NB, w.sGp, NB,
-                              nb, a, nbox, st, P.tma_epi, P.tc_pairs))
+        const TcLeft L = it->second == 2 ? left_bwd_pair(P, w, s) : left1(w.Bp + 2 * P.bw_off[s], k + wp, w.sBp, wp);
+        if (!launch_tc_update(L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
             return false;
     }
     return true;

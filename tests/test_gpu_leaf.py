@@ -103,6 +103,30 @@ def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
         assert rel_fro(T0, To).max() < 1e-10
 
 
+@pytest.mark.parametrize("p,nbox,block", [(8, 3, 32), (9, 2, 32), (12, 2, 64), (13, 2, 64), (16, 2, 0)])
+def test_tcgen05_step_pairs_match_single_steps(ctx, p, nbox, block):
+    """Joining LU steps in pairs (look-ahead factorisation, 2 NB-deep
+    products) against one step at a time: both within 1e-10 of the oracle and
+    of each other.  The block sizes give an odd number of steps (a single step
+    at the end: p = 9, 13) and a ragged last pair."""
+    h = np.array([0.125, 0.2, 0.15])
+    kappa = 18.0
+    lows = _lows(nbox, h, 11 + p)
+    field = hi.fourier_b_field().b
+    b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
+    try:
+        H.hps_set_option(ctx, H.HPS_OPT_LU_PAIRS, 0)
+        T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+    finally:
+        H.hps_set_option(ctx, H.HPS_OPT_LU_PAIRS, 1)
+    T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+    assert (st0 == 0).all() and (st1 == 0).all(), (st0, st1)
+    assert rel_fro(T0, T1).max() < 1e-10 and rel_fro(S0, S1).max() < 1e-10
+    if p <= 13:
+        To, So, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=True)
+        assert rel_fro(T0, To).max() < 1e-10 and rel_fro(S0, So).max() < 1e-10
+
+
 @pytest.mark.parametrize("prec,tc,tol", PRECS)
 @pytest.mark.parametrize("block", [32, 64])
 def test_dtn_parity_block_sizes(ctx, prec, tc, tol, block):
