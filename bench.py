@@ -55,7 +55,7 @@ FP32_CUDACORE_PEAK_TFLOPS = 152 * 2.070e9 * 128 * 2 / 1e12
 
 CLASS_BOUND = {
     "update_tcgen05": "tensor", "update_cudacore": "alu", "residual_fp64": "alu", "dn_fp64": "alu",
-    "panel": "alu", "build": "hbm", "gather_pack": "hbm", "refine_update": "hbm",
+    "panel": "alu", "build": "hbm", "gather": "hbm", "pack": "hbm", "refine_update": "hbm",
     "update_tcgen05_refine": "tensor",
 }
 # DRAM bytes per launch of the dominant kernel class, from one ncu capture of
@@ -75,7 +75,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32ir", "fp64"), default="fp32ir")
+    ap.add_argument("--precision", choices=("fp32ir", "bf16ir", "fp64"), default="fp32ir")
     ap.add_argument("--nbox", type=int, default=NBOX)
     ap.add_argument("--fp64-sample", type=int, default=32)
     ap.add_argument("--cpu-sample", type=int, default=8)
@@ -253,7 +253,7 @@ def run_ours(args):
     field = hi.fourier_b_field()
     b_np = np.stack([field.b(H.hps_leaf_nodes(P, lo, h)) for lo in lows])
     n, m = H.hps_leaf_sizes(P)
-    prec = H.HPS_FP32_IR if args.precision == "fp32ir" else H.HPS_FP64
+    prec = {"fp32ir": H.HPS_FP32_IR, "bf16ir": H.HPS_BF16_IR, "fp64": H.HPS_FP64}[args.precision]
     kind = H.LeafKind(P, h, KAPPA)
     ctx = H.hps_create(local, 0)
     if args.ir_tol is not None:
@@ -302,7 +302,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if prec == H.HPS_FP32_IR else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {H.HPS_FP32_IR: "f32+f64", H.HPS_BF16_IR: "bf16x3 (f32 accumulate)+f64",
+                                      H.HPS_FP64: "f64"}[prec], "data": "synthetic",
         "config": {"workload": WORKLOAD, "nbox_per_gpu": nbox, "p": P, "kappa": KAPPA,
                    "precision": args.precision, "ir_tol": args.ir_tol, "l2": "inputs larger than L2 (~90 GB working set), no flush",
                    "step": "hps_leaf_build_dtn over all boxes (T out, S not stored)"},
@@ -363,7 +364,7 @@ def run_ours(args):
                             "peak_source": note, "launches_per_step": d["launches"]}
 
     # ---- plain FP64 GPU path on a sample of the same boxes
-    if not args.no_fp64 and prec == H.HPS_FP32_IR and args.fp64_sample > 0:
+    if not args.no_fp64 and prec != H.HPS_FP64 and args.fp64_sample > 0:
         k = min(args.fp64_sample, nbox)
         # half evenly spaced, half the boxes whose refinement ended with the
         # largest corrections (the hardest ones)

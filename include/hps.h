@@ -70,8 +70,12 @@ typedef enum {
  * cores (3-term TF32 split products with FP32 accumulation) and recovers FP64
  * accuracy by iterative refinement: residuals R = -A_ib - A_ii X computed
  * matrix-free in FP64, corrections solved with the FP32 factors, X updated in
- * FP64; the D_n product forming T is FP64.  HPS_BF16_IR is reserved and
- * currently returns HPS_EINVAL. */
+ * FP64; the D_n product forming T is FP64.  HPS_BF16_IR is the same
+ * refinement with the tensor-core products taken in BF16 with FP32
+ * accumulation: each operand is split into three BF16 pieces (successive
+ * roundings of the remainder) and six kind::f16 products per K step keep every
+ * term above FP32 rounding, so the factors are as accurate as FP32's.  Without
+ * tensor cores (HPS_OPT_TENSOR_CORES = 0) it runs as HPS_FP32_IR. */
 typedef enum { HPS_FP64 = 0, HPS_FP32_IR = 1, HPS_BF16_IR = 2 } hps_precision;
 
 /* One class of boxes: polynomial order p (3 <= p <= 24), box side lengths
@@ -293,13 +297,13 @@ hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const
  * record each launch's algorithmic flops (2 M N K for an update product, the
  * dense method's count) and bytes.  hps_profile_get synchronises and returns,
  * for kernel class cls (0 operator build, 1 panel factorisation, 2 CUDA-core
- * update product, 3 tensor-core update product, 4 row gather / operand pack,
+ * update product, 3 tensor-core update product, 4 row gather of the products,
  * 5 FP64 refinement residual, 6 refinement update, 7 D_n product,
- * 8 tensor-core update product of the refinement solves), the accumulated
- * launches, milliseconds, flops and bytes since the last reset.  Refinement
- * launches skip boxes that have converged, so classes 5, 6 and 8 count the
- * work of every box and overstate flops and bytes.
- * Returns HPS_EINVAL for cls outside 0..8. */
+ * 8 tensor-core update product of the refinement solves, 9 split copies of
+ * the LU operators), the accumulated launches, milliseconds, flops and bytes
+ * since the last reset.  Refinement launches skip boxes that have converged,
+ * so classes 5, 6 and 8 count the work of every box and overstate flops and
+ * bytes.  Returns HPS_EINVAL for cls outside 0..9. */
 hps_status hps_profile_enable(hps_ctx* ctx, int on);
 hps_status hps_profile_reset(hps_ctx* ctx);
 hps_status hps_profile_get(hps_ctx* ctx, int cls, long long* launches, double* ms, double* flops, double* bytes);

@@ -880,7 +880,7 @@ hps_status hps_leaf_build_dtn(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox,
     if (!ctx || nbox < 0) return HPS_EINVAL;
     hps_status rc = check_kind(kind);
     if (rc != HPS_OK) return rc;
-    if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
+    if (prec != HPS_FP64 && prec != HPS_FP32_IR && prec != HPS_BF16_IR) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
     if (!b || !T) return HPS_EINVAL;
     Job j;
@@ -899,7 +899,7 @@ hps_status hps_leaf_particular(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox
     if (!ctx || nbox < 0 || nrhs < 1 || nrhs > 256) return HPS_EINVAL;
     hps_status rc = check_kind(kind);
     if (rc != HPS_OK) return rc;
-    if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
+    if (prec != HPS_FP64 && prec != HPS_FP32_IR && prec != HPS_BF16_IR) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
     if (!b || !f || !v || !h) return HPS_EINVAL;
     Job j;
@@ -920,7 +920,7 @@ hps_status hps_leaf_reconstruct(hps_ctx* ctx, const hps_leaf_kind* kind, int nbo
     if (!ctx || nbox < 0 || nrhs < 1 || nrhs > 256) return HPS_EINVAL;
     hps_status rc = check_kind(kind);
     if (rc != HPS_OK) return rc;
-    if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
+    if (prec != HPS_FP64 && prec != HPS_FP32_IR && prec != HPS_BF16_IR) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
     if (!ub || !ui || (!S && !b)) return HPS_EINVAL;
     if (S) {
@@ -951,7 +951,7 @@ hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* grou
                            void* stream)
 {
     if (!ctx || ngroups < 0 || (ngroups > 0 && !groups)) return HPS_EINVAL;
-    if (prec != HPS_FP64 && prec != HPS_FP32_IR) return HPS_EINVAL;
+    if (prec != HPS_FP64 && prec != HPS_FP32_IR && prec != HPS_BF16_IR) return HPS_EINVAL;
     size_t nk = 0;
     for (int i = 0; i < ngroups; ++i) {
         const hps_leaf_group& G = groups[i];

@@ -56,6 +56,7 @@ struct Plan {
     bool tc_pairs = false;           // tcgen05 products by CTA pairs sharing the right operand
     bool step_pairs = false;         // tcgen05 path: consecutive LU steps joined in pairs
     int KG = 0;                      // K extent of the gathered right operand (NB, or 2 NB with pairs)
+    int fmt = 0;                     // tcgen05 operand format: 0 = 3 x TF32, 1 = 3 x BF16
     std::vector<int> k0, nbs;
     std::vector<long long> fw_off, bw_off, perm_off;
     long long fw_elems = 0, bw_elems = 0, perm_elems = 0;
@@ -72,6 +73,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     const bool fp64 = (prec == HPS_FP64);
     P.elt = fp64 ? 8 : 4;
     P.tc = !fp64 && use_tc;
+    P.fmt = (P.tc && prec == HPS_BF16_IR) ? 1 : 0;
     int NB = nb_opt > 0 ? nb_opt : (fp64 ? 64 : 128);
     if (fp64 && NB > 64) NB = 64;
     if (NB > kMaxNB) NB = kMaxNB;
@@ -108,9 +110,11 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     P.bX = need_x ? align_up((size_t)n * r * sizeof(double), A) : 0;
     if (P.tc) {
         // split (hi, lo) K-major copies of F, B and G for the tensor-core products
-        P.bFp = align_up((size_t)P.fw_elems * 2 * sizeof(float), A);
-        P.bBp = align_up((size_t)P.bw_elems * 2 * sizeof(float), A);
-        P.bGp = align_up((size_t)P.ldm * P.KG * 2 * sizeof(float), A);
+        // (3 x TF32: two FP32 planes; 3 x BF16: three 2-byte planes)
+        const size_t pk = P.fmt ? 3 * 2 : 2 * sizeof(float);
+        P.bFp = align_up((size_t)P.fw_elems * pk, A);
+        P.bBp = align_up((size_t)P.bw_elems * pk, A);
+        P.bGp = align_up((size_t)P.ldm * P.KG * pk, A);
     }
     P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + 64;
     return P;
@@ -152,9 +156,10 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
     w.sG = (long long)(P.bG / P.elt);
     w.sP = (long long)(P.bP / sizeof(int));
     w.sX = (long long)(P.bX / sizeof(double));
-    w.sFp = (long long)(P.bFp / sizeof(float));
-    w.sBp = (long long)(P.bBp / sizeof(float));
-    w.sGp = (long long)(P.bGp / sizeof(float));
+    const size_t pke = P.fmt ? 2 : sizeof(float);   // strides of the split operands in their elements
+    w.sFp = (long long)(P.bFp / pke);
+    w.sBp = (long long)(P.bBp / pke);
+    w.sGp = (long long)(P.bGp / pke);
     return w;
 }
 
@@ -164,7 +169,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
 // Kernel classes timed by the optional event profiler (HPS_OPT_PROFILE).
 enum KernelClass {
     KC_BUILD = 0, KC_PANEL, KC_UPDATE_CUDACORE, KC_UPDATE_TC, KC_GATHER, KC_RESIDUAL, KC_REFINE, KC_DN,
-    KC_UPDATE_TC_REFINE, KC_COUNT
+    KC_UPDATE_TC_REFINE, KC_PACK, KC_COUNT
 };
 
 // When profiling is on for the calling thread, prof_begin/prof_end bracket a

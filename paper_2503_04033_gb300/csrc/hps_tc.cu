@@ -20,6 +20,7 @@
 // A less often.  All mbarrier waits are bounded; a wait that gives up marks the
 // box HPS_ETIMEOUT.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <cstdio>
@@ -33,14 +34,35 @@ namespace hps {
 namespace {
 
 constexpr int TC_BM = 128;                                  // tile rows = TMEM lanes
-constexpr int TC_BN = 256;                                  // tile columns = TMEM columns per buffer
-constexpr int TC_BK = 16;                                   // FP32 values per 64-byte row (64B swizzle)
+constexpr uint32_t ROWB = 64;                               // bytes of an operand row in one K chunk (64B swizzle)
+constexpr uint32_t A_TILE = TC_BM * ROWB;                   // 8 KiB per plane
 constexpr int TC_STAGES = 3;
 constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
-constexpr uint32_t A_TILE = TC_BM * TC_BK * 4;              // 8 KiB
-constexpr uint32_t B_TILE = TC_BN * TC_BK * 4;              // 16 KiB
-constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // hi + lo of both operands
+
+// Operand formats of the update product.  FMT 0: each operand x = hi + lo with
+// hi = tf32(x), lo = tf32(x - hi) (2 planes of FP32 containers, kind::tf32,
+// products hi*hi + hi*lo + lo*hi).  FMT 1: x = hi + mid + lo, three BF16
+// roundings of the successive remainders (3 planes, kind::f16 with BF16 A
+// and B, products hi*hi + hi*mid + mid*hi + hi*lo + mid*mid + lo*hi).  Both
+// drop only terms below FP32 rounding and accumulate in FP32.  A K chunk is
+// one 64-byte row: 16 TF32 or 32 BF16 values.
+template <int FMT>
+struct TcFmt;
+template <>
+struct TcFmt<0> {
+    static constexpr int NPL = 2, EB = 4, KPC = 16, BN = 256;
+};
+template <>
+struct TcFmt<1> {
+    static constexpr int NPL = 3, EB = 2, KPC = 32, BN = 128;
+};
+template <int FMT>
+__host__ __device__ constexpr uint32_t b_tile() { return (uint32_t)TcFmt<FMT>::BN * ROWB; }
+template <int FMT>
+__host__ __device__ constexpr uint32_t stage_bytes() { return (uint32_t)TcFmt<FMT>::NPL * (A_TILE + b_tile<FMT>()); }
+constexpr uint32_t STAGE_BYTES = 48 * 1024;
+static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES, "one shared-memory layout");
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
 constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
 constexpr uint32_t EPI_FLOATS = TBUF_FLOATS * (1 + TC_PRE) + 64;   // transpose + source ring + row pointers
@@ -261,7 +283,7 @@ __device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
 // ...; a unit is a pair of vertically adjacent row tiles at one column tile,
 // the CTA of rank r taking row tile 2 i + r.
 struct TcSched {
-    int u0, ustep, units, upb, tiles_n, rank, cl;
+    int u0, ustep, units, upb, tiles_n, rank, cl, bn;
     __device__ bool skipped(int u, const int* skip) const { return skip && skip[u / upb]; }
     __device__ int first_from(int u, const int* skip) const
     {
@@ -272,7 +294,7 @@ struct TcSched {
     {
         box = u / upb;
         const int rem = u - box * upb, mi = rem / tiles_n;
-        n0 = (rem - mi * tiles_n) * TC_BN;
+        n0 = (rem - mi * tiles_n) * bn;
         m0 = (cl ? 2 * mi + rank : mi) * TC_BM;
     }
 };
@@ -304,6 +326,24 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
     return d;
 }
 
+// D(tmem) (+)= A(smem) * B(smem)^T, M = 128, N = BN, K = 16, BF16 in, FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M.
+__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N, M.
 __host__ __device__ constexpr uint32_t tf32_idesc(int M, int N)
 {
@@ -325,10 +365,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // Persistent update product O <- src - A G over (box, row tile, column tile),
 // in the work-unit order of TcSched.  TMEM holds two 128 x 256
 // FP32 accumulators: the epilogue drains one while the MMAs fill the other.
+template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
             const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO, TcArgs a)
 {
+    using Fm = TcFmt<FMT>;
+    constexpr int BN = Fm::BN, KPC = Fm::KPC, NPL = Fm::NPL;
+    constexpr uint32_t B_TILE = b_tile<FMT>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t ld_bar[TC_EPI_WARPS][TE_PRE];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
@@ -342,6 +386,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     unsigned char* sbase_ptr = smem_raw + (sbase - smem_u32(smem_raw));
     TcSched sc;
+    sc.bn = BN;
     sc.cl = a.cl;
     sc.tiles_n = a.tiles_n;
     sc.units = a.units;
@@ -371,7 +416,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 2 * TC_BN);
+    if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 2 * BN);
     tc_fence_before();
     __syncthreads();
     if (a.cl) cluster_sync_all();   // the partner's barriers exist before any multicast reaches them
@@ -404,18 +449,20 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     // row a2_off of the product (rows above it load as zeros)
                     const bool second = ch >= a.kch1;
                     const CUtensorMap* ma = second ? &tmA2 : &tmA;
-                    const int ka = (second ? ch - a.kch1 : ch) * TC_BK, ra = second ? m0 - a.a2_off : m0;
-                    tma_load_4d(st, ma, fb, ka, ra, 0, box);
-                    tma_load_4d(st + A_TILE, ma, fb, ka, ra, 1, box);
+                    const int ka = (second ? ch - a.kch1 : ch) * KPC, ra = second ? m0 - a.a2_off : m0;
+#pragma unroll
+                    for (int pl = 0; pl < NPL; ++pl) tma_load_4d(st + pl * A_TILE, ma, fb, ka, ra, pl, box);
+                    const uint32_t sb0 = st + NPL * A_TILE;
                     if (a.cl) {
                         // this CTA's half of B's rows, into both CTAs of the pair
                         const uint32_t off = (uint32_t)sc.rank * (B_TILE / 2);
-                        const int nr = n0 + sc.rank * (TC_BN / 2);
-                        tma_load_4d_mc(st + 2 * A_TILE + off, &tmB, fb, ch * TC_BK, nr, 0, box, 0x3);
-                        tma_load_4d_mc(st + 2 * A_TILE + B_TILE + off, &tmB, fb, ch * TC_BK, nr, 1, box, 0x3);
+                        const int nr = n0 + sc.rank * (BN / 2);
+#pragma unroll
+                        for (int pl = 0; pl < NPL; ++pl)
+                            tma_load_4d_mc(sb0 + pl * B_TILE + off, &tmB, fb, ch * KPC, nr, pl, box, 0x3);
                     } else {
-                        tma_load_4d(st + 2 * A_TILE, &tmB, fb, ch * TC_BK, n0, 0, box);
-                        tma_load_4d(st + 2 * A_TILE + B_TILE, &tmB, fb, ch * TC_BK, n0, 1, box);
+#pragma unroll
+                        for (int pl = 0; pl < NPL; ++pl) tma_load_4d(sb0 + pl * B_TILE, &tmB, fb, ch * KPC, n0, pl, box);
                     }
                 }
             }
@@ -429,7 +476,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = tf32_idesc(TC_BM, TC_BN);
+            constexpr uint32_t idesc = FMT == 0 ? tf32_idesc(TC_BM, BN) : bf16_idesc(TC_BM, BN);
             uint32_t g = 0, j = 0;
             bool ok = true;
             for (int u = sc.u0; u < sc.units && ok; u += sc.ustep) {
@@ -438,20 +485,35 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 const uint32_t uj = j >> 1;
                 if (j >= 2 && !mbar_wait(smem_u32(&tempty_bar[b]), (uj - 1) & 1)) { fail_sh = 1; break; }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+                const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int ch = 0; ch < a.kch; ++ch, ++g) {
                     const int s = g % TC_STAGES;
                     if (!mbar_wait(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1)) { fail_sh = 1; ok = false; break; }
                     tc_fence_after();
                     const uint32_t st = sbase + s * STAGE_BYTES;
-                    const uint64_t ah = sw64_desc(st), al = sw64_desc(st + A_TILE);
-                    const uint64_t bh = sw64_desc(st + 2 * A_TILE), bl = sw64_desc(st + 2 * A_TILE + B_TILE);
+                    uint64_t ad[NPL], bd[NPL];
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 8; ++kk) {
-                        const uint64_t o = (uint64_t)((kk * 32) >> 4);   // 8 TF32 values = 32 bytes
-                        mma_tf32(d, ah + o, bh + o, idesc, (ch | kk) != 0);
-                        mma_tf32(d, ah + o, bl + o, idesc, 1);
-                        mma_tf32(d, al + o, bh + o, idesc, 1);
+                    for (int pl = 0; pl < NPL; ++pl) {
+                        ad[pl] = sw64_desc(st + pl * A_TILE);
+                        bd[pl] = sw64_desc(st + NPL * A_TILE + pl * B_TILE);
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t o = (uint64_t)((kk * 32) >> 4);   // one MMA's K: 32 bytes of the row
+                        const uint32_t acc0 = (ch | kk) != 0;
+                        if constexpr (FMT == 0) {
+                            mma_tf32(d, ad[0] + o, bd[0] + o, idesc, acc0);
+                            mma_tf32(d, ad[0] + o, bd[1] + o, idesc, 1);
+                            mma_tf32(d, ad[1] + o, bd[0] + o, idesc, 1);
+                        } else {
+                            // smallest terms first
+                            mma_bf16(d, ad[2] + o, bd[0] + o, idesc, acc0);
+                            mma_bf16(d, ad[1] + o, bd[1] + o, idesc, 1);
+                            mma_bf16(d, ad[0] + o, bd[2] + o, idesc, 1);
+                            mma_bf16(d, ad[1] + o, bd[0] + o, idesc, 1);
+                            mma_bf16(d, ad[0] + o, bd[1] + o, idesc, 1);
+                            mma_bf16(d, ad[0] + o, bd[0] + o, idesc, 1);
+                        }
                     }
                     if (a.cl) mma_commit_mc(smem_u32(&empty_bar[s]), 0x3);
                     else mma_commit(smem_u32(&empty_bar[s]));
@@ -481,7 +543,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         auto first_from = [&](int u) { return sc.first_from(u, a.skip); };
         auto geom = [&](int u, int& box, int& m0, int& n0, int& nch) {
             sc.decode(u, box, m0, n0);
-            nch = (min(TC_BN, a.N - n0) + 31) / 32;
+            nch = (min(BN, a.N - n0) + 31) / 32;
         };
         // load cursor (lane 0): next chunk to fetch is number lg, chunk lcc of unit lt
         int lt = first_from(sc.u0), lcc = 0;
@@ -544,7 +606,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 __syncwarp();
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + cc * 32), v);
                 if (cc == nch - 1) {
                     // the accumulator is in registers: hand the TMEM buffer back
                     tc_fence_before();
@@ -633,7 +695,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 sp[lane] = srow;
             }
             __syncwarp();
-            const int nchunks = (min(TC_BN, a.N - n0) + 31) / 32;
+            const int nchunks = (min(BN, a.N - n0) + 31) / 32;
             auto prefetch = [&](int cc) {
                 const int cb = n0 + cc * 32;
                 const uint32_t buf = sb_u32 + (uint32_t)((cc % TC_PRE) * 4096);
@@ -680,7 +742,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (cc + TC_PRE - 1 < nchunks) prefetch(cc + TC_PRE - 1);
                 asm volatile("cp.async.commit_group;" ::: "memory");
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * TC_BN + cc * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + cc * 32), v);
                 // row = lane; 16-byte group g of the row goes to slot g ^ (lane & 7)
 #pragma unroll
                 for (int g = 0; g < 8; ++g)
@@ -728,35 +790,59 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (a.cl) cluster_sync_all();   // neither CTA of a pair leaves while the other may still reach it
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * TC_BN);
+        tmem_dealloc(tmem, 2 * BN);
     }
     if (threadIdx.x == 0 && fail_sh && a.status)
         for (int bx = 0; bx < a.nbox; ++bx) atomicCAS(a.status + bx, 0, HPS_ETIMEOUT);
 }
 
-// dst = [hi plane | lo plane] of the first nb columns of src (rows of pitch
-// lds; planes rows x NB, zero beyond nb), hi = tf32(x), lo = tf32(x - hi).
+// The split pieces of x in operand format FMT, written to plane pl of a
+// buffer of FP32 containers (FMT 0: tf32(x), tf32(x - hi)) or BF16 bits
+// (FMT 1: successive BF16 roundings; every remainder is exact in FP32).
+template <int FMT>
+__device__ __forceinline__ void split_store(void* dst, long long idx, long long plane, float x)
+{
+    if constexpr (FMT == 0) {
+        float* d = static_cast<float*>(dst);
+        const float hi = to_tf32(x);
+        d[idx] = hi;
+        d[plane + idx] = to_tf32(x - hi);
+    } else {
+        unsigned short* d = static_cast<unsigned short*>(dst);
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        d[idx] = __bfloat16_as_ushort(h);
+        d[plane + idx] = __bfloat16_as_ushort(m);
+        d[2 * plane + idx] = __bfloat16_as_ushort(l);
+    }
+}
+
+// dst = the split planes (rows x NB each, zero beyond nb) of the first nb
+// columns of src (rows of pitch lds).
+template <int FMT>
 __global__ void k_pack_split(const float* __restrict__ src, long long lds, long long sS, int rows, int NB, int nb,
-                             float* __restrict__ dst, long long sD)
+                             void* __restrict__ dst, long long sD)
 {
     const int box = blockIdx.y;
     const long long total = (long long)rows * NB;
+    void* db = FMT == 0 ? (void*)(static_cast<float*>(dst) + box * sD) : (void*)(static_cast<unsigned short*>(dst) + box * sD);
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(idx % NB);
         const long long r = idx / NB;
         const float x = c < nb ? src[box * sS + r * lds + c] : 0.0f;
-        const float hi = to_tf32(x);
-        dst[box * sD + idx] = hi;
-        dst[box * sD + total + idx] = to_tf32(x - hi);
+        split_store<FMT>(db, idx, total, x);
     }
 }
 
 // Gather the step's rows (through perm), save the unpermuted rows to W, and
 // write the split, transposed G: Gp[plane][c][i] for i < NB (zero for i >= nb).
+template <int FMT>
 __global__ void k_gather_pack(const float* __restrict__ M, long long ldm, long long sM, int k, int nb, int NB,
                               int c0, int nc, const int* __restrict__ perm, long long sP, float* __restrict__ W,
-                              long long ldw, long long sW, float* __restrict__ Gp, long long plane, long long sGp,
+                              long long ldw, long long sW, void* __restrict__ Gp, long long plane, long long sGp,
                               const int* skip)
 {
     __shared__ float tile[32][33];
@@ -776,15 +862,10 @@ __global__ void k_gather_pack(const float* __restrict__ M, long long ldm, long l
         tile[ii][tx] = v;
     }
     __syncthreads();
-    float* G = Gp + box * sGp;
+    void* G = FMT == 0 ? (void*)(static_cast<float*>(Gp) + box * sGp) : (void*)(static_cast<unsigned short*>(Gp) + box * sGp);
     for (int cc = ty; cc < 32; cc += 8) {
         const int c = cb + cc, i = i0 + tx;
-        if (c < nc) {
-            const float v = tile[tx][cc];
-            const float hi = to_tf32(v);
-            G[(long long)c * NB + i] = hi;
-            G[plane + (long long)c * NB + i] = to_tf32(v - hi);
-        }
+        if (c < nc) split_store<FMT>(G, (long long)c * NB + i, plane, tile[tx][cc]);
     }
 }
 
@@ -804,41 +885,47 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 4-D map over split K-major operands: (k, row, plane, box).
-bool make_map(CUtensorMap* tm, const float* base, int K, long long rows, long long plane_elems, long long box_elems,
+// 4-D map over split K-major operands: (k, row, plane, box); K, strides and
+// the box in elements of format FMT, one 64-byte row of K per box row.
+template <int FMT>
+bool make_map(CUtensorMap* tm, const void* base, int K, long long rows, long long plane_elems, long long box_elems,
               int nbox, int box_rows)
 {
+    using Fm = TcFmt<FMT>;
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, 2, (cuuint64_t)nbox};
-    cuuint64_t strides[3] = {(cuuint64_t)K * 4, (cuuint64_t)plane_elems * 4, (cuuint64_t)box_elems * 4};
-    cuuint32_t boxd[4] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1, 1};
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Fm::NPL, (cuuint64_t)nbox};
+    cuuint64_t strides[3] = {(cuuint64_t)K * Fm::EB, (cuuint64_t)plane_elems * Fm::EB, (cuuint64_t)box_elems * Fm::EB};
+    cuuint32_t boxd[4] = {(cuuint32_t)Fm::KPC, (cuuint32_t)box_rows, 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, boxd, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(tm, FMT == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                    const_cast<void*>(base), dims, strides, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
 // Left operand of an update product: split rows of NB values (K-major), a_rows
 // rows per box; a second part (rows offset by a2_off, K2 further values of K)
-// joins a pair of LU steps into one product.
+// joins a pair of LU steps into one product.  Pointers and strides are in
+// elements of the plan's operand format.
 struct TcLeft {
-    const float* A; long long rows, sA;
-    const float* A2; long long rows2, sA2;
+    const void* A; long long rows, sA;
+    const void* A2; long long rows2, sA2;
     int K1, K2, a2_off;
 };
 
-TcLeft left1(const float* A, long long rows, long long sA, int K)
+TcLeft left1(const void* A, long long rows, long long sA, int K)
 {
     TcLeft l{};
     l.A = A; l.rows = rows; l.sA = sA; l.K1 = K;
     return l;
 }
 
-bool launch_tc_update(const TcLeft& L, const float* Gp, long long g_plane, long long sGp, int gK, int NB,
-                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs)
+template <int FMT>
+bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs)
 {
+    using Fm = TcFmt<FMT>;
     const int K = L.K1 + L.K2;
     if (args.M <= 0 || args.N <= 0) return true;
     static int num_sms = 0, max_pairs = 0;
@@ -846,7 +933,7 @@ bool launch_tc_update(const TcLeft& L, const float* Gp, long long g_plane, long 
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        cudaFuncSetAttribute(k_tc_update<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
         if (num_sms <= 0) num_sms = 1;
         // how many CTA pairs fit at once (an SM whose cluster partner is
         // missing stays idle in pair mode)
@@ -862,29 +949,29 @@ bool launch_tc_update(const TcLeft& L, const float* Gp, long long g_plane, long 
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, (void*)k_tc_update, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&nc, (void*)k_tc_update<FMT>, &cfg) != cudaSuccess) {
             cudaGetLastError();
             nc = 0;
         }
         max_pairs = nc;
     }
     TcArgs a = args;
-    a.kch = (K + TC_BK - 1) / TC_BK;
-    a.kch1 = L.K2 ? L.K1 / TC_BK : a.kch;   // L.K1 is a whole block when a second part follows
+    a.kch = (K + Fm::KPC - 1) / Fm::KPC;
+    a.kch1 = L.K2 ? L.K1 / Fm::KPC : a.kch;   // L.K1 is a whole block when a second part follows
     a.a2_off = L.a2_off;
     a.tiles_m = (a.M + TC_BM - 1) / TC_BM;
-    a.tiles_n = (a.N + TC_BN - 1) / TC_BN;
+    a.tiles_n = (a.N + Fm::BN - 1) / Fm::BN;
     a.tiles = a.tiles_m * a.tiles_n * nbox;
     a.nbox = nbox;
     a.cl = (allow_pairs && max_pairs > 0 && a.tiles_m >= 2) ? 1 : 0;
     a.units_per_box = (a.cl ? (a.tiles_m + 1) / 2 : a.tiles_m) * a.tiles_n;
     a.units = a.units_per_box * nbox;
     CUtensorMap ta, ta2, tb;
-    if (!make_map(&ta, L.A, NB, L.rows, L.rows * NB, L.sA, nbox, TC_BM) ||
-        !make_map(&tb, Gp, gK, args.N, g_plane, sGp, nbox, a.cl ? TC_BN / 2 : TC_BN))
+    if (!make_map<FMT>(&ta, L.A, NB, L.rows, L.rows * NB, L.sA, nbox, TC_BM) ||
+        !make_map<FMT>(&tb, Gp, gK, args.N, g_plane, sGp, nbox, a.cl ? Fm::BN / 2 : Fm::BN))
         return false;
     if (L.K2) {
-        if (!make_map(&ta2, L.A2, NB, L.rows2, L.rows2 * NB, L.sA2, nbox, TC_BM)) return false;
+        if (!make_map<FMT>(&ta2, L.A2, NB, L.rows2, L.rows2 * NB, L.sA2, nbox, TC_BM)) return false;
     } else {
         ta2 = ta;
     }
@@ -921,36 +1008,60 @@ bool launch_tc_update(const TcLeft& L, const float* Gp, long long g_plane, long 
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k_tc_update, ta, ta2, tb, to, a) != cudaSuccess) return false;
+        if (cudaLaunchKernelEx(&cfg, k_tc_update<FMT>, ta, ta2, tb, to, a) != cudaSuccess) return false;
     } else {
         dim3 grd((unsigned)std::min(a.units, num_sms));
-        k_tc_update<<<grd, TC_THREADS, TC_SMEM, st>>>(ta, ta2, tb, to, a);
+        k_tc_update<FMT><<<grd, TC_THREADS, TC_SMEM, st>>>(ta, ta2, tb, to, a);
     }
     const double kk = (double)K;
     prof_end(cls, st, 2.0 * nbox * a.M * (double)a.N * kk,
-             (double)nbox * (2.0 * (a.M + (double)a.N) * kk * 4 + 2.0 * a.M * (double)a.N * 4));
+             (double)nbox * ((a.M + (double)a.N) * kk * Fm::NPL * Fm::EB + 2.0 * a.M * (double)a.N * 4));
     return true;
 }
 
-void launch_pack_split(const float* src, long long lds, long long sS, int rows, int NB, int nb, float* dst,
+bool launch_tc_update(int fmt, const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
+                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs)
+{
+    return fmt ? launch_tc_update_f<1>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs)
+               : launch_tc_update_f<0>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs);
+}
+
+// Element `off` of a split-operand buffer of format fmt.
+void* pk_at(void* base, long long off, int fmt)
+{
+    return fmt ? (void*)(static_cast<unsigned short*>(base) + off) : (void*)(static_cast<float*>(base) + off);
+}
+
+void launch_pack_split(int fmt, const float* src, long long lds, long long sS, int rows, int NB, int nb, void* dst,
                        long long sD, int nbox, cudaStream_t st)
 {
     const long long total = (long long)rows * NB;
     int blocks = (int)std::min<long long>((total + 255) / 256, 256);
     dim3 grd((unsigned)blocks, (unsigned)nbox);
+    prof_begin(KC_PACK, st);
+    if (fmt) k_pack_split<1><<<grd, 256, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
+    else k_pack_split<0><<<grd, 256, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
+    prof_end(KC_PACK, st, 0.0, (double)nbox * total * (4.0 + (fmt ? 6.0 : 8.0)));
+}
+
+void gather_pack_raw(int fmt, const float* M, long long ldm, long long sM, int k, int nb, int gK, int c0, int nc,
+                     const int* perm, long long sP, float* W, long long ldw, long long sW, void* Gp, long long plane,
+                     long long sGp, const int* skip, int nbox, cudaStream_t st)
+{
     prof_begin(KC_GATHER, st);
-    k_pack_split<<<grd, 256, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
-    prof_end(KC_GATHER, st, 0.0, (double)nbox * total * 12.0);
+    const dim3 grd((unsigned)((nc + 31) / 32), (unsigned)(gK / 32), (unsigned)nbox), blk(32, 8);
+    if (fmt)
+        k_gather_pack<1><<<grd, blk, 0, st>>>(M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, Gp, plane, sGp, skip);
+    else
+        k_gather_pack<0><<<grd, blk, 0, st>>>(M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, Gp, plane, sGp, skip);
+    prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * (4.0 + (W ? 4.0 : 0.0) + (fmt ? 6.0 : 8.0)));
 }
 
 void launch_gather_pack(const Plan& P, Work<float>& w, int k, int nb, int c0, int nc, const int* perm, bool save_w,
                         const int* skip, int nbox, cudaStream_t st)
 {
-    dim3 grd((unsigned)((nc + 31) / 32), (unsigned)(P.KG / 32), (unsigned)nbox);
-    prof_begin(KC_GATHER, st);
-    k_gather_pack<<<grd, dim3(32, 8), 0, st>>>(w.M, P.ldm, w.sM, k, nb, P.KG, c0, nc, perm, w.sP,
-                                               save_w ? w.W : nullptr, P.ldm, w.sG, w.Gp, P.ldm * P.KG, w.sGp, skip);
-    prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * 4 * (save_w ? 4 : 3));
+    gather_pack_raw(P.fmt, w.M, P.ldm, w.sM, k, nb, P.KG, c0, nc, perm, w.sP, save_w ? w.W : nullptr, P.ldm, w.sG,
+                    w.Gp, P.ldm * P.KG, w.sGp, skip, nbox, st);
 }
 
 TcArgs targs(float* O, long long ldo, long long sO, int M, int N, int mode, int split)
@@ -1019,25 +1130,20 @@ void launch_perm_compose(int* perm0, const int* perm1, long long sP, int R, int 
     k_perm_compose<<<nbox, 256, smem, st>>>(perm0, perm1, sP, R, nb0);
 }
 
-void gather_pack_raw(const float* M, long long ldm, long long sM, int k, int nb, int gK, int c0, int nc,
-                     const int* perm, long long sP, float* W, long long ldw, long long sW, float* Gp, long long plane,
-                     long long sGp, const int* skip, int nbox, cudaStream_t st)
-{
-    prof_begin(KC_GATHER, st);
-    k_gather_pack<<<dim3((unsigned)((nc + 31) / 32), (unsigned)(gK / 32), (unsigned)nbox), dim3(32, 8), 0, st>>>(
-        M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, Gp, plane, sGp, skip);
-    prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * 4 * (W ? 4 : 3));
-}
+// Start of step s's split F_s / B_s in the operand format of the plan.
+int npl(const Plan& P) { return P.fmt ? 3 : 2; }
+void* fpk(const Plan& P, const Work<float>& w, int s) { return pk_at(w.Fp, (long long)npl(P) * P.fw_off[s], P.fmt); }
+void* bpk(const Plan& P, const Work<float>& w, int s) { return pk_at(w.Bp, (long long)npl(P) * P.bw_off[s], P.fmt); }
 
 // Left operands of the pair (s, s+1).
 TcLeft left_fwd_pair(const Plan& P, const Work<float>& w, int s)
 {
     TcLeft l{};
-    l.A = w.Fp + 2 * P.fw_off[s];
+    l.A = fpk(P, w, s);
     l.rows = P.n - P.k0[s];
     l.sA = w.sFp;
     l.K1 = P.nbs[s];
-    l.A2 = w.Fp + 2 * P.fw_off[s + 1];
+    l.A2 = fpk(P, w, s + 1);
     l.rows2 = P.n - P.k0[s + 1];
     l.sA2 = w.sFp;
     l.K2 = P.nbs[s + 1];
@@ -1048,11 +1154,11 @@ TcLeft left_fwd_pair(const Plan& P, const Work<float>& w, int s)
 TcLeft left_bwd_pair(const Plan& P, const Work<float>& w, int s)
 {
     TcLeft l{};
-    l.A = w.Bp + 2 * P.bw_off[s];
+    l.A = bpk(P, w, s);
     l.rows = P.k0[s] + P.nbs[s];
     l.sA = w.sBp;
     l.K1 = P.nbs[s];
-    l.A2 = w.Bp + 2 * P.bw_off[s + 1];
+    l.A2 = bpk(P, w, s + 1);
     l.rows2 = P.k0[s + 1] + P.nbs[s + 1];
     l.sA2 = w.sBp;
     l.K2 = P.nbs[s + 1];
@@ -1079,10 +1185,10 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
     const int n = P.n, NB = P.NB, KG = P.KG;
     const long long ldm = P.ldm, gplane = ldm * KG;
     auto up = [&](const TcLeft& L, const TcArgs& a) {
-        return launch_tc_update(L, w.Gp, gplane, w.sGp, KG, NB, a, nbox, st, P.tma_epi, P.tc_pairs);
+        return launch_tc_update(P.fmt, L, w.Gp, gplane, w.sGp, KG, NB, a, nbox, st, P.tma_epi, P.tc_pairs);
     };
     // Panel of step s, its operators F_s and B_s (FP32 and split copies).
-    auto panel_ops = [&](int s) -> bool {
+    auto panel_ops = [&](int s, bool pack_b) -> bool {
         const int k = P.k0[s], nb = P.nbs[s];
         float* Fs = w.F + P.fw_off[s];
         float* Bs = w.B + P.bw_off[s];
@@ -1094,23 +1200,24 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         // operand is split into the step's own (not yet filled) pack region,
         // the right one, transposed, into the G pack.
         if (n - k - nb > 0) {
-            float* Fp = w.Fp + 2 * P.fw_off[s];
-            launch_pack_split(w.M + (long long)(k + nb) * ldm + k, ldm, w.sM, n - k - nb, NB, nb, Fp, w.sFp, nbox, st);
-            gather_pack_raw(Fs, NB, w.sF, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr,
+            void* Fp = fpk(P, w, s);
+            launch_pack_split(P.fmt, w.M + (long long)(k + nb) * ldm + k, ldm, w.sM, n - k - nb, NB, nb, Fp, w.sFp,
+                              nbox, st);
+            gather_pack_raw(P.fmt, Fs, NB, w.sF, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr,
                             nbox, st);
             TcArgs a = targs(Fs + (long long)nb * NB, NB, w.sF, n - k - nb, nb, GM_SET, 0);
             if (!up(left1(Fp, n - k - nb, w.sFp, nb), a)) return false;
         }
         if (k > 0) {
-            float* Bp = w.Bp + 2 * P.bw_off[s];
-            launch_pack_split(w.M + k, ldm, w.sM, k, NB, nb, Bp, w.sBp, nbox, st);
-            gather_pack_raw(Bs + (long long)k * NB, NB, w.sB, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp,
+            void* Bp = bpk(P, w, s);
+            launch_pack_split(P.fmt, w.M + k, ldm, w.sM, k, NB, nb, Bp, w.sBp, nbox, st);
+            gather_pack_raw(P.fmt, Bs + (long long)k * NB, NB, w.sB, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp,
                             gplane, w.sGp, nullptr, nbox, st);
             TcArgs a = targs(Bs, NB, w.sB, k, nb, GM_SET, 0);
             if (!up(left1(Bp, k, w.sBp, nb), a)) return false;
         }
-        launch_pack_split(Fs, NB, w.sF, n - k, NB, nb, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
-        launch_pack_split(Bs, NB, w.sB, k + nb, NB, nb, w.Bp + 2 * P.bw_off[s], w.sBp, nbox, st);
+        launch_pack_split(P.fmt, Fs, NB, w.sF, n - k, NB, nb, fpk(P, w, s), w.sFp, nbox, st);
+        if (pack_b) launch_pack_split(P.fmt, Bs, NB, w.sB, k + nb, NB, nb, bpk(P, w, s), w.sBp, nbox, st);
         return true;
     };
     // Step s's update of M's columns [c0, c0 + nc).
@@ -1121,7 +1228,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st);
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
-        return up(left1(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, nb), a);
+        return up(left1(fpk(P, w, s), n - k, w.sFp, nb), a);
     };
     // The pair's operators and permutation from those of its two steps.
     auto combine = [&](int s) -> bool {
@@ -1131,20 +1238,20 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         int* P0 = w.perm + P.perm_off[s];
         const int* P1 = w.perm + P.perm_off[s + 1];
         {   // F_s' = forward step s+1 on F_s's rows [nb0, n - k)
-            gather_pack_raw(F0, NB, w.sF, nb0, nb1, KG, 0, nb0, P1, w.sP, w.W, NB, w.sG, w.Gp, gplane, w.sGp, nullptr,
+            gather_pack_raw(P.fmt, F0, NB, w.sF, nb0, nb1, KG, 0, nb0, P1, w.sP, w.W, NB, w.sG, w.Gp, gplane, w.sGp, nullptr,
                             nbox, st);
             TcArgs a = targs(F0 + (long long)nb0 * NB, NB, w.sF, n - k1, nb0, GM_FWD, nb1);
             a.perm = P1; a.sP = w.sP; a.W = w.W; a.ldw = NB; a.sW = w.sG; a.status = status;
-            if (!up(left1(w.Fp + 2 * P.fw_off[s + 1], n - k1, w.sFp, nb1), a)) return false;
-            launch_pack_split(F0, NB, w.sF, n - k, NB, nb0, w.Fp + 2 * P.fw_off[s], w.sFp, nbox, st);
+            if (!up(left1(fpk(P, w, s + 1), n - k1, w.sFp, nb1), a)) return false;
+            launch_pack_split(P.fmt, F0, NB, w.sF, n - k, NB, nb0, fpk(P, w, s), w.sFp, nbox, st);
         }
         {   // B_{s+1}' = backward step s on B_{s+1}'s rows [0, k + nb0)
-            gather_pack_raw(B1, NB, w.sB, k, nb0, KG, 0, nb1, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
+            gather_pack_raw(P.fmt, B1, NB, w.sB, k, nb0, KG, 0, nb1, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
                             nullptr, nbox, st);
             TcArgs a = targs(B1, NB, w.sB, k + nb0, nb1, GM_BWD, k);
             a.status = status;
-            if (!up(left1(w.Bp + 2 * P.bw_off[s], k + nb0, w.sBp, nb0), a)) return false;
-            launch_pack_split(B1, NB, w.sB, k1 + nb1, NB, nb1, w.Bp + 2 * P.bw_off[s + 1], w.sBp, nbox, st);
+            if (!up(left1(bpk(P, w, s), k + nb0, w.sBp, nb0), a)) return false;
+            launch_pack_split(P.fmt, B1, NB, w.sB, k1 + nb1, NB, nb1, bpk(P, w, s + 1), w.sBp, nbox, st);
         }
         launch_perm_compose(P0, P1, w.sP, n - k, nb0, nbox, st);
         return true;
@@ -1152,14 +1259,14 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
     for (const auto& u : solve_units(P)) {
         const int s = u.first, k = P.k0[s];
         if (u.second == 1) {
-            if (!panel_ops(s)) return false;
+            if (!panel_ops(s, true)) return false;
             if (!update1(s, k + P.nbs[s], n + P.r - k - P.nbs[s])) return false;
             continue;
         }
         const int nb0 = P.nbs[s], wp = nb0 + P.nbs[s + 1];
-        if (!panel_ops(s)) return false;
+        if (!panel_ops(s, true)) return false;
         if (!update1(s, k + nb0, P.nbs[s + 1])) return false;   // look-ahead: the next panel's columns
-        if (!panel_ops(s + 1)) return false;
+        if (!panel_ops(s + 1, false)) return false;             // B_{s+1} is split once combined
         if (!combine(s)) return false;
         const int c0 = k + wp, nc = n + P.r - c0;
         if (nc > 0) {
@@ -1184,8 +1291,8 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
         launch_gather_pack(P, w, k, wp, c0, nc, Ps, true, skip, nbox, st);
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
-        const TcLeft L = u.second == 2 ? left_fwd_pair(P, w, s) : left1(w.Fp + 2 * P.fw_off[s], n - k, w.sFp, wp);
-        if (!launch_tc_update(L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
+        const TcLeft L = u.second == 2 ? left_fwd_pair(P, w, s) : left1(fpk(P, w, s), n - k, w.sFp, wp);
+        if (!launch_tc_update(P.fmt, L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
             return false;
     }
     return true;
@@ -1201,8 +1308,8 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
         launch_gather_pack(P, w, k, wp, c0, nc, nullptr, false, skip, nbox, st);
         TcArgs a = targs(w.M + c0, ldm, w.sM, k + wp, nc, GM_BWD, k);
         a.skip = skip;
-        const TcLeft L = it->second == 2 ? left_bwd_pair(P, w, s) : left1(w.Bp + 2 * P.bw_off[s], k + wp, w.sBp, wp);
-        if (!launch_tc_update(L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
+        const TcLeft L = it->second == 2 ? left_bwd_pair(P, w, s) : left1(bpk(P, w, s), k + wp, w.sBp, wp);
+        if (!launch_tc_update(P.fmt, L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
             return false;
     }
     return true;

@@ -23,6 +23,7 @@ PRECS = [
     pytest.param(H.HPS_FP64, 0, 1e-11, id="fp64"),
     pytest.param(H.HPS_FP32_IR, 0, 1e-10, id="fp32ir-cudacore"),
     pytest.param(H.HPS_FP32_IR, 1, 1e-10, id="fp32ir-tcgen05"),
+    pytest.param(H.HPS_BF16_IR, 1, 1e-10, id="bf16ir-tcgen05"),
 ]
 
 
@@ -262,7 +263,7 @@ def test_argument_errors(ctx):
         H.hps_leaf_build_dtn(ctx, H.LeafKind(2, 1.0, 0.0), 1, b, T)
     assert e.value.status == H.HPS_EINVAL
     with pytest.raises(H.HpsError):
-        H.hps_leaf_build_dtn(ctx, H.LeafKind(3, 1.0, 0.0), 1, b, T, prec=H.HPS_BF16_IR)
+        H.hps_leaf_build_dtn(ctx, H.LeafKind(3, 1.0, 0.0), 1, b, T, prec=7)
     H.hps_leaf_build_dtn(ctx, H.LeafKind(3, 1.0, 0.0), 0, b, T)            # nbox = 0: no-op
 
 
