@@ -82,6 +82,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
     ap.add_argument("--workload", choices=("fourier16", "uneven", "learned"), default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
@@ -393,6 +394,31 @@ def run_ours(args):
         line["speedup_vs_fp64_path"] = value / world / fp64_rate
         line["rel_err_vs_fp64_path"] = relerr
         del T64, b64
+
+    # ---- the other mixed precision on the same boxes (timed the same way)
+    if prec != H.HPS_FP64 and not args.no_alt:
+        alt = H.HPS_BF16_IR if prec == H.HPS_FP32_IR else H.HPS_FP32_IR
+        Ta = torch.empty_like(T)
+        sta = torch.zeros_like(st)
+        for _ in range(2):
+            H.hps_leaf_build_dtn(ctx, kind, nbox, b, Ta, None, alt, sta, stream)
+        torch.cuda.synchronize(dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a0.record(stream)
+        for _ in range(args.steps):
+            H.hps_leaf_build_dtn(ctx, kind, nbox, b, Ta, None, alt, sta, stream)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        alt_ms = allmax(a0.elapsed_time(a1) / args.steps)
+        ita, rela = H.hps_last_refinement(ctx, nbox)
+        rel_ab = ((Ta - T).flatten(1).norm(dim=1) / T.flatten(1).norm(dim=1)).max().item()
+        line["other_precision"] = {
+            "precision": "bf16ir" if alt == H.HPS_BF16_IR else "fp32ir", "value": world * nbox / (alt_ms / 1e3),
+            "unit": "boxes/s", "ms_per_step": alt_ms, "box_failures": int((sta != 0).sum().item()),
+            "corrections_mean": float(ita.mean()), "corrections_max": int(ita.max()),
+            "max_rel_diff_vs_headline_T": rel_ab}
+        del Ta, sta
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:

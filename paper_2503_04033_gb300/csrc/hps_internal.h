@@ -57,11 +57,14 @@ struct Plan {
     bool step_pairs = false;         // tcgen05 path: consecutive LU steps joined in pairs
     int KG = 0;                      // K extent of the gathered right operand (NB, or 2 NB with pairs)
     int fmt = 0;                     // tcgen05 operand format: 0 = 3 x TF32, 1 = 3 x BF16
+    bool fuse_fwd = false;           // forward solves: next G written by the epilogue (scattered stores)
+    bool fuse_bwd = false;           // backward solves: next G written by the epilogue
     std::vector<int> k0, nbs;
     std::vector<long long> fw_off, bw_off, perm_off;
     long long fw_elems = 0, bw_elems = 0, perm_elems = 0;
     // per-box byte sizes of the workspace pieces
     size_t bM = 0, bF = 0, bB = 0, bW = 0, bG = 0, bP = 0, bX = 0, bFp = 0, bBp = 0, bGp = 0;
+    size_t bInv = 0, bGp2 = 0, bW2 = 0;   // tensor-core solves: inverse permutations, second G and W buffers
     size_t per_box = 0;
 };
 
@@ -74,6 +77,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     P.elt = fp64 ? 8 : 4;
     P.tc = !fp64 && use_tc;
     P.fmt = (P.tc && prec == HPS_BF16_IR) ? 1 : 0;
+    P.fuse_bwd = P.tc && P.fmt == 0;
     int NB = nb_opt > 0 ? nb_opt : (fp64 ? 64 : 128);
     if (fp64 && NB > 64) NB = 64;
     if (NB > kMaxNB) NB = kMaxNB;
@@ -115,8 +119,11 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
         P.bFp = align_up((size_t)P.fw_elems * pk, A);
         P.bBp = align_up((size_t)P.bw_elems * pk, A);
         P.bGp = align_up((size_t)P.ldm * P.KG * pk, A);
+        P.bInv = P.bP;
+        P.bGp2 = P.bGp;
+        P.bW2 = P.bW;
     }
-    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + 64;
+    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + P.bInv + P.bGp2 + P.bW2 + 64;
     return P;
 }
 
@@ -127,6 +134,8 @@ struct Work {
     int* perm;
     double* X;
     float *Fp, *Bp, *Gp;
+    int* inv;
+    float *Gp2, *W2;
     double* norms;
     int* skip;
     long long sM, sF, sB, sG, sP, sX, sFp, sBp, sGp;
@@ -148,6 +157,9 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
     w.Fp = P.bFp ? reinterpret_cast<float*>(take(P.bFp)) : nullptr;
     w.Bp = P.bBp ? reinterpret_cast<float*>(take(P.bBp)) : nullptr;
     w.Gp = P.bGp ? reinterpret_cast<float*>(take(P.bGp)) : nullptr;
+    w.inv = P.bInv ? reinterpret_cast<int*>(take(P.bInv)) : nullptr;
+    w.Gp2 = P.bGp2 ? reinterpret_cast<float*>(take(P.bGp2)) : nullptr;
+    w.W2 = P.bW2 ? reinterpret_cast<float*>(take(P.bW2)) : nullptr;
     w.norms = reinterpret_cast<double*>(take(align_up(2 * sizeof(double), 16)));
     w.skip = reinterpret_cast<int*>(take(align_up(sizeof(int), 16)));
     w.sM = (long long)(P.bM / P.elt);

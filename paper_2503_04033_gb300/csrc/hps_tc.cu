@@ -90,6 +90,13 @@ struct TcArgs {
     const float* W; long long ldw, sW;
     const int* skip;
     int* status;
+    // fused gather of the next product (TMA epilogue only): output row r goes
+    // to the next split right operand nG at K index ninv[r - ng_off] (or
+    // r - ng_off without ninv) when that lies in [0, ng_len) and is >= 0, and
+    // rows [nw_off, nw_off + nw_len) are saved to nW
+    void* nG; long long ng_plane, nsG; int ngK;
+    const int* ninv; long long nsInv; int ng_off, ng_len;
+    float* nW; long long nsW, nldw; int nw_off, nw_len;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -357,6 +364,29 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
+// The split pieces of x in operand format FMT, written to plane pl of a
+// buffer of FP32 containers (FMT 0: tf32(x), tf32(x - hi)) or BF16 bits
+// (FMT 1: successive BF16 roundings; every remainder is exact in FP32).
+template <int FMT>
+__device__ __forceinline__ void split_store(void* dst, long long idx, long long plane, float x)
+{
+    if constexpr (FMT == 0) {
+        float* d = static_cast<float*>(dst);
+        const float hi = to_tf32(x);
+        d[idx] = hi;
+        d[plane + idx] = to_tf32(x - hi);
+    } else {
+        unsigned short* d = static_cast<unsigned short*>(dst);
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        d[idx] = __bfloat16_as_ushort(h);
+        d[plane + idx] = __bfloat16_as_ushort(m);
+        d[2 * plane + idx] = __bfloat16_as_ushort(l);
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -574,6 +604,17 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             tc_fence_after();
             // this lane's row: source 0 = zero, 1 = staged O row, 2 = saved row of W
             const int myr = m0 + qd * 32 + lane;
+            int ngi = -1, nwr = -1;   // the row's K index in the next product's G, its row in the next W
+            if (a.nG && myr < a.M) {
+                const int rr = myr - a.ng_off;
+                if (rr >= 0 && rr < a.ng_len) ngi = a.ninv ? a.ninv[box * a.nsInv + rr] : rr;
+                const int wr = myr - a.nw_off;
+                if (a.nW && wr >= 0 && wr < a.nw_len) nwr = wr;
+            }
+            void* nGb = nullptr;
+            if (ngi >= 0)
+                nGb = FMT == 0 ? (void*)(static_cast<float*>(a.nG) + box * a.nsG)
+                               : (void*)(static_cast<unsigned short*>(a.nG) + box * a.nsG);
             int srck = 0;
             const float* wrow = nullptr;
             if (myr < a.M) {
@@ -633,8 +674,19 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         sv.z = c + 2 < a.N ? wrow[c + 2] : 0.f;
                         sv.w = c + 3 < a.N ? wrow[c + 3] : 0.f;
                     }
-                    *p4 = make_float4(sv.x - __uint_as_float(v[4 * u]), sv.y - __uint_as_float(v[4 * u + 1]),
-                                      sv.z - __uint_as_float(v[4 * u + 2]), sv.w - __uint_as_float(v[4 * u + 3]));
+                    const float4 o = make_float4(sv.x - __uint_as_float(v[4 * u]), sv.y - __uint_as_float(v[4 * u + 1]),
+                                                 sv.z - __uint_as_float(v[4 * u + 2]), sv.w - __uint_as_float(v[4 * u + 3]));
+                    *p4 = o;
+                    if (ngi >= 0 || nwr >= 0) {
+                        const int c = cb + 4 * u;
+                        const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if (c + j >= a.N) break;
+                            if (ngi >= 0) split_store<FMT>(nGb, (long long)(c + j) * a.ngK + ngi, a.ng_plane, ov[j]);
+                            if (nwr >= 0) a.nW[box * a.nsW + (long long)nwr * a.nldw + c + j] = ov[j];
+                        }
+                    }
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -796,29 +848,6 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         for (int bx = 0; bx < a.nbox; ++bx) atomicCAS(a.status + bx, 0, HPS_ETIMEOUT);
 }
 
-// The split pieces of x in operand format FMT, written to plane pl of a
-// buffer of FP32 containers (FMT 0: tf32(x), tf32(x - hi)) or BF16 bits
-// (FMT 1: successive BF16 roundings; every remainder is exact in FP32).
-template <int FMT>
-__device__ __forceinline__ void split_store(void* dst, long long idx, long long plane, float x)
-{
-    if constexpr (FMT == 0) {
-        float* d = static_cast<float*>(dst);
-        const float hi = to_tf32(x);
-        d[idx] = hi;
-        d[plane + idx] = to_tf32(x - hi);
-    } else {
-        unsigned short* d = static_cast<unsigned short*>(dst);
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        d[idx] = __bfloat16_as_ushort(h);
-        d[plane + idx] = __bfloat16_as_ushort(m);
-        d[2 * plane + idx] = __bfloat16_as_ushort(l);
-    }
-}
-
 // dst = the split planes (rows x NB each, zero beyond nb) of the first nb
 // columns of src (rows of pitch lds).
 template <int FMT>
@@ -923,7 +952,7 @@ TcLeft left1(const void* A, long long rows, long long sA, int K)
 
 template <int FMT>
 bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs)
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs, bool* fused)
 {
     using Fm = TcFmt<FMT>;
     const int K = L.K1 + L.K2;
@@ -991,6 +1020,11 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             a.tma_epi = 1;
     }
+    if (!a.tma_epi) {   // the next product's gather is fused into the TMA epilogue only
+        a.nG = nullptr;
+        a.nW = nullptr;
+    }
+    if (fused) *fused = a.nG != nullptr;
     // Refinement replays (skip flags set) are timed apart: their boxes drop out
     // as they converge, so their flop counts are upper bounds.
     const int cls = a.skip ? KC_UPDATE_TC_REFINE : KC_UPDATE_TC;
@@ -1020,10 +1054,11 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
 }
 
 bool launch_tc_update(int fmt, const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs)
+                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs,
+                      bool* fused = nullptr)
 {
-    return fmt ? launch_tc_update_f<1>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs)
-               : launch_tc_update_f<0>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs);
+    return fmt ? launch_tc_update_f<1>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused)
+               : launch_tc_update_f<0>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused);
 }
 
 // Element `off` of a split-operand buffer of format fmt.
@@ -1128,6 +1163,16 @@ void launch_perm_compose(int* perm0, const int* perm1, long long sP, int R, int 
         attr = true;
     }
     k_perm_compose<<<nbox, 256, smem, st>>>(perm0, perm1, sP, R, nb0);
+}
+
+// inv[r] = i where perm[i] = r for i < w, -1 for the other rows r < R (one
+// CTA per box): the K index in a product's G of each row it gathers.
+__global__ void k_perm_inverse(const int* __restrict__ perm, int* __restrict__ inv, long long sP, int R, int w)
+{
+    const int box = blockIdx.x;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) inv[box * sP + r] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < w; i += blockDim.x) inv[box * sP + perm[box * sP + i]] = i;
 }
 
 // Start of step s's split F_s / B_s in the operand format of the plan.
@@ -1277,22 +1322,52 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
             if (!up(left_fwd_pair(P, w, s), a)) return false;
         }
     }
+    // Inverse permutations of the solve units, for the gathers fused into the
+    // products of the solves.
+    for (const auto& u : solve_units(P)) {
+        const int s = u.first, wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
+        k_perm_inverse<<<nbox, 256, 0, st>>>(w.perm + P.perm_off[s], w.inv + P.perm_off[s], w.sP, n - P.k0[s], wp);
+    }
     return true;
 }
 
+// The solves alternate between two (G, W) buffers.  In the backward sweep
+// the next unit's G is the block of rows just above the current one, so the
+// current product's epilogue writes it (contiguous K indices, coalesced
+// stores) straight from its results; only the first product of a sweep, a
+// ragged next unit, or an output that is not 16-byte aligned (cp.async
+// epilogue) gathers on its own.  Measured on the p = 16 workload this pays
+// with the 3 x TF32 operands and not with the 3 x BF16 ones (three 2-byte
+// stores per element), hence P.fuse_bwd.
 bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st)
 {
     const int n = P.n;
-    const long long ldm = P.ldm;
-    for (const auto& u : solve_units(P)) {
-        const int s = u.first, k = P.k0[s];
-        const int wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
+    const long long ldm = P.ldm, gplane = ldm * P.KG;
+    void* Gb[2] = {w.Gp, w.Gp2};
+    float* Wb[2] = {w.W, w.W2};
+    const auto units = solve_units(P);
+    auto width = [&](size_t u) { const int s = units[u].first; return units[u].second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s]; };
+    bool have = false;   // the current unit's G and W are in buffer cur
+    for (size_t u = 0; u < units.size(); ++u) {
+        const int s = units[u].first, k = P.k0[s], wp = width(u), cur = (int)(u & 1);
         int* Ps = w.perm + P.perm_off[s];
-        launch_gather_pack(P, w, k, wp, c0, nc, Ps, true, skip, nbox, st);
+        if (!have)
+            gather_pack_raw(P.fmt, w.M, ldm, w.sM, k, wp, P.KG, c0, nc, Ps, w.sP, Wb[cur], ldm, w.sG, Gb[cur], gplane,
+                            w.sGp, skip, nbox, st);
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
-        a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
-        const TcLeft L = u.second == 2 ? left_fwd_pair(P, w, s) : left1(fpk(P, w, s), n - k, w.sFp, wp);
-        if (!launch_tc_update(P.fmt, L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
+        a.perm = Ps; a.sP = w.sP; a.W = Wb[cur]; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
+        // The next unit's G is gathered through its pivot permutation, whose
+        // source rows scatter over the rows this product writes: stores from
+        // the epilogue would not coalesce, so the forward sweep gathers on
+        // its own (the machinery is in place: P.fuse_fwd).
+        if (P.fuse_fwd && u + 1 < units.size() && width(u + 1) % (P.fmt ? 32 : 16) == 0) {
+            const int s1 = units[u + 1].first;
+            a.nG = Gb[cur ^ 1]; a.ng_plane = gplane; a.nsG = w.sGp; a.ngK = P.KG;
+            a.ninv = w.inv + P.perm_off[s1]; a.nsInv = w.sP; a.ng_off = wp; a.ng_len = n - P.k0[s1];
+            a.nW = Wb[cur ^ 1]; a.nsW = w.sG; a.nldw = ldm; a.nw_off = wp; a.nw_len = width(u + 1);
+        }
+        const TcLeft L = units[u].second == 2 ? left_fwd_pair(P, w, s) : left1(fpk(P, w, s), n - k, w.sFp, wp);
+        if (!launch_tc_update(P.fmt, L, Gb[cur], gplane, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs, &have))
             return false;
     }
     return true;
@@ -1300,16 +1375,26 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
 
 bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st)
 {
-    const long long ldm = P.ldm;
+    const long long ldm = P.ldm, gplane = ldm * P.KG;
+    void* Gb[2] = {w.Gp, w.Gp2};
     const auto units = solve_units(P);
-    for (auto it = units.rbegin(); it != units.rend(); ++it) {
-        const int s = it->first, k = P.k0[s];
-        const int wp = it->second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
-        launch_gather_pack(P, w, k, wp, c0, nc, nullptr, false, skip, nbox, st);
+    auto width = [&](size_t u) { const int s = units[u].first; return units[u].second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s]; };
+    bool have = false;
+    int cur = 0;
+    for (size_t q = units.size(); q-- > 0; cur ^= 1) {
+        const int s = units[q].first, k = P.k0[s], wp = width(q);
+        if (!have)
+            gather_pack_raw(P.fmt, w.M, ldm, w.sM, k, wp, P.KG, c0, nc, nullptr, 0, nullptr, 0, 0, Gb[cur], gplane,
+                            w.sGp, skip, nbox, st);
         TcArgs a = targs(w.M + c0, ldm, w.sM, k + wp, nc, GM_BWD, k);
         a.skip = skip;
-        const TcLeft L = it->second == 2 ? left_bwd_pair(P, w, s) : left1(bpk(P, w, s), k + wp, w.sBp, wp);
-        if (!launch_tc_update(P.fmt, L, w.Gp, ldm * P.KG, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs))
+        if (P.fuse_bwd && q > 0 && width(q - 1) % (P.fmt ? 32 : 16) == 0) {
+            const int wq = width(q - 1);
+            a.nG = Gb[cur ^ 1]; a.ng_plane = gplane; a.nsG = w.sGp; a.ngK = P.KG;
+            a.ninv = nullptr; a.ng_off = k - wq; a.ng_len = wq;
+        }
+        const TcLeft L = units[q].second == 2 ? left_bwd_pair(P, w, s) : left1(bpk(P, w, s), k + wp, w.sBp, wp);
+        if (!launch_tc_update(P.fmt, L, Gb[cur], gplane, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs, &have))
             return false;
     }
     return true;
