@@ -63,7 +63,11 @@ CLASS_BOUND = {
 # boxes (traffic is proportional to the boxes processed); see
 # profiles/k_tc_update_fourier16_32boxes.md.  Must be re-measured (or set to
 # None) whenever that kernel changes.
-NCU_TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes per launch of the dominant kernel class from one ncu capture of the
+# factorisation phase at 32 boxes (dram__bytes_read.sum + dram__bytes_write.sum
+# over its 97 launches / 97), scaled to 512 boxes by the box count; see
+# profiles/k_tc_update_fourier16_32boxes.md.
+NCU_TRAFFIC_PER_LAUNCH = {"update_tcgen05": 4.263e9}
 # Classes whose launches skip converged boxes: their flop and byte counts are
 # upper bounds, so they are not used for the roofline.
 SKIPPING = ("update_tcgen05_refine", "residual_fp64", "refine_update")
