@@ -362,7 +362,7 @@ def run_ours(args):
             ach = d["bytes"] / sec / 1e9
             unit = "GB/s"
             note = f"{src} HBM copy bandwidth"
-        traffic = NCU_TRAFFIC_PER_LAUNCH.get(dom) if nbox == NBOX else None
+        traffic = NCU_TRAFFIC_PER_LAUNCH.get(dom) if (nbox == NBOX and prec == H.HPS_FP32_IR) else None
         line["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                             "frac": ach / peak, "traffic": traffic,
                             "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
