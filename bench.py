@@ -87,6 +87,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
+    ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
+                    help="hps_set_option before timing, e.g. TC_PAIRS=1 (name without HPS_OPT_)")
     ap.add_argument("--workload", choices=("fourier16", "uneven", "learned"), default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
@@ -263,6 +265,9 @@ def run_ours(args):
     ctx = H.hps_create(local, 0)
     if args.ir_tol is not None:
         H.hps_set_option(ctx, H.HPS_OPT_IR_TOL, args.ir_tol)
+    for o in args.opt:
+        name, val = o.split("=")
+        H.hps_set_option(ctx, getattr(H, "HPS_OPT_" + name), float(val))
     stream = torch.cuda.current_stream(dev)
     b = torch.from_numpy(b_np).to(dev)
     T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
@@ -310,7 +315,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {H.HPS_FP32_IR: "f32+f64", H.HPS_BF16_IR: "bf16x3 (f32 accumulate)+f64",
                                       H.HPS_FP64: "f64"}[prec], "data": "synthetic",
         "config": {"workload": WORKLOAD, "nbox_per_gpu": nbox, "p": P, "kappa": KAPPA,
-                   "precision": args.precision, "ir_tol": args.ir_tol, "l2": "inputs larger than L2 (~90 GB working set), no flush",
+                   "precision": args.precision, "ir_tol": args.ir_tol, "options": args.opt, "l2": "inputs larger than L2 (~90 GB working set), no flush",
                    "step": "hps_leaf_build_dtn over all boxes (T out, S not stored)"},
         "tflops": value * flops_per_box(P) / 1e12,
         "wall_ms_per_step": 1e3 * wall / args.steps,

@@ -159,6 +159,71 @@ __device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi)
     if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
 }
 
+// Inverse of a triangle held in A (P x P, row-major, P a power of two >= 16,
+// padded with the identity): the unit lower triangle below A's diagonal
+// (lower) or the upper triangle with its diagonal.  The 16 x 16 diagonal
+// blocks are inverted by substitution (a column per thread), then blocks of
+// doubling size b are joined: for [[A1, 0], [C, D]] the off-diagonal block
+// of the inverse is -D^{-1} (C A1^{-1}); for [[A1, B], [0, D]] it is
+// -A1^{-1} (B D^{-1}).  The middle product is parked in the free triangle of
+// A.  X must be zero on entry and receives the inverse.  A zero diagonal
+// entry is read as 1 (the box is already flagged singular).
+template <typename T>
+__device__ void tri_inverse(T* A, T* X, int P, bool lower, int tid)
+{
+    if (tid < P) {
+        const int q0 = (tid >> 4) << 4, c = tid;
+        if (lower) {
+            X[c * P + c] = T(1);
+            for (int r = c + 1; r < q0 + 16; ++r) {
+                T acc = T(0);
+                for (int t = c; t < r; ++t) acc -= A[r * P + t] * X[t * P + c];
+                X[r * P + c] = acc;
+            }
+        } else {
+            T d = A[c * P + c];
+            if (d == T(0)) d = T(1);
+            X[c * P + c] = T(1) / d;
+            for (int r = c - 1; r >= q0; --r) {
+                T acc = T(0);
+                for (int t = r + 1; t <= c; ++t) acc -= A[r * P + t] * X[t * P + c];
+                T dr = A[r * P + r];
+                if (dr == T(0)) dr = T(1);
+                X[r * P + c] = acc / dr;
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = 16; b < P; b *= 2) {
+        const int items = (P / (2 * b)) * b * b;
+        // middle products into the free triangle of A
+        for (int it = tid; it < items; it += kPanelThreads) {
+            const int pr = it / (b * b), e = it - pr * b * b, r = e / b, c = e - r * b, i0 = 2 * b * pr;
+            T acc = T(0);
+            if (lower) {   // C A1^{-1}: C = A[i0+b+r][i0+t], A1^{-1} lower
+                for (int t = c; t < b; ++t) acc += A[(i0 + b + r) * P + i0 + t] * X[(i0 + t) * P + i0 + c];
+                A[(i0 + r) * P + i0 + b + c] = acc;
+            } else {       // B D^{-1}: B = A[i0+r][i0+b+t], D^{-1} upper
+                for (int t = 0; t <= c; ++t) acc += A[(i0 + r) * P + i0 + b + t] * X[(i0 + b + t) * P + i0 + b + c];
+                A[(i0 + b + r) * P + i0 + c] = acc;
+            }
+        }
+        __syncthreads();
+        for (int it = tid; it < items; it += kPanelThreads) {
+            const int pr = it / (b * b), e = it - pr * b * b, r = e / b, c = e - r * b, i0 = 2 * b * pr;
+            T acc = T(0);
+            if (lower) {   // -D^{-1} (C A1^{-1}), D^{-1} lower
+                for (int t = 0; t <= r; ++t) acc -= X[(i0 + b + r) * P + i0 + b + t] * A[(i0 + t) * P + i0 + b + c];
+                X[(i0 + b + r) * P + i0 + c] = acc;
+            } else {       // -A1^{-1} (B D^{-1}), A1^{-1} upper
+                for (int t = r; t < b; ++t) acc -= X[(i0 + r) * P + i0 + t] * A[(i0 + b + t) * P + i0 + c];
+                X[(i0 + r) * P + i0 + b + c] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // One CTA factors one box's panel M[k:n, k:k+nb] (Algorithm 1's batched LU,
 // P A_ii = L U with partial pivoting).  The panel is processed in inner blocks
 // of ib columns that live in shared memory (column-major, R rows, in the order
@@ -385,48 +450,35 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
         }
     if (tid == 0 && s_sing && status[box] == 0) status[box] = HPS_ESINGULAR;
 
-    // Inverses of the diagonal blocks (one column per thread).
-    T* L = Sb;                  // nb x nb, row-major: L11 (unit lower) and U11
-    T* X = Sb + nb * nb;        // inverse being built, row-major
-    for (int idx = tid; idx < nb * nb; idx += kPanelThreads) {
-        const int r = idx / nb, c = idx - r * nb;
-        L[idx] = Mb[(long long)(k + r) * ldm + k + c];
+    // Inverses of the diagonal blocks, L11^{-1} and U11^{-1}, by blocks.
+    int Pd = 16;
+    while (Pd < nb) Pd *= 2;
+    T* Ap = Sb;                 // Pd x Pd, padded with the identity
+    T* X = Sb + Pd * Pd;        // the inverse
+    for (int idx = tid; idx < Pd * Pd; idx += kPanelThreads) {
+        const int r = idx / Pd, c = idx - r * Pd;
+        Ap[idx] = (r < nb && c < r) ? Mb[(long long)(k + r) * ldm + k + c] : T(0);
+        X[idx] = T(0);
     }
     __syncthreads();
-    for (int c = tid; c < nb; c += kPanelThreads) {
-        X[c * nb + c] = T(1);
-        for (int r = c + 1; r < nb; ++r) {
-            T acc = T(0);
-            for (int t = c; t < r; ++t) acc -= L[r * nb + t] * X[t * nb + c];
-            X[r * nb + c] = acc;
-        }
-        for (int r = 0; r < c; ++r) X[r * nb + c] = T(0);
-    }
-    __syncthreads();
+    tri_inverse<T>(Ap, X, Pd, true, tid);
     T* Fb = Ftop + box * sF;
     for (int idx = tid; idx < nb * nb; idx += kPanelThreads) {
         const int r = idx / nb, c = idx - r * nb;
-        Fb[r * ldf + c] = -X[idx];
+        Fb[r * ldf + c] = -X[r * Pd + c];
     }
     __syncthreads();
-    for (int c = tid; c < nb; c += kPanelThreads) {
-        T d = L[c * nb + c];
-        if (d == T(0)) d = T(1);
-        X[c * nb + c] = T(1) / d;
-        for (int r = c - 1; r >= 0; --r) {
-            T acc = T(0);
-            for (int t = r + 1; t <= c; ++t) acc -= L[r * nb + t] * X[t * nb + c];
-            T dr = L[r * nb + r];
-            if (dr == T(0)) dr = T(1);
-            X[r * nb + c] = acc / dr;
-        }
-        for (int r = c + 1; r < nb; ++r) X[r * nb + c] = T(0);
+    for (int idx = tid; idx < Pd * Pd; idx += kPanelThreads) {
+        const int r = idx / Pd, c = idx - r * Pd;
+        Ap[idx] = (r < nb && c >= r && c < nb) ? Mb[(long long)(k + r) * ldm + k + c] : (r == c && r >= nb ? T(1) : T(0));
+        X[idx] = T(0);
     }
     __syncthreads();
+    tri_inverse<T>(Ap, X, Pd, false, tid);
     T* Bb = Btop + box * sB;
     for (int idx = tid; idx < nb * nb; idx += kPanelThreads) {
         const int r = idx / nb, c = idx - r * nb;
-        Bb[r * ldb + c] = -X[idx];
+        Bb[r * ldb + c] = -X[r * Pd + c];
     }
 }
 
@@ -1041,7 +1093,9 @@ void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int i
     while (ib > 1 && (size_t)ib * R0 * sizeof(T) + R0 * 5 > dyn_max) ib >>= 1;
     if (ib > nb) ib = nb;
     const size_t s1 = (size_t)ib * R0 * sizeof(T) + R0 * 5;
-    const size_t s2 = (size_t)2 * nb * nb * sizeof(T);
+    int Pd = 16;
+    while (Pd < nb) Pd *= 2;
+    const size_t s2 = (size_t)2 * Pd * Pd * sizeof(T);   // the padded triangle and its inverse
     const size_t smem = s1 > s2 ? s1 : s2;
     prof_begin(KC_PANEL, st);
     k_panel<T><<<nbox, kPanelThreads, smem, st>>>(M, ldm, sM, n, k, nb, ib, perm, sP, Ftop, ldf, sF,
