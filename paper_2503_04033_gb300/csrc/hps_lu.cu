@@ -316,11 +316,12 @@ k_panel(T* __restrict__ M, long long ldm, long long sM, int n, int k, int nb, in
                 if (tid == 0) s_sing = 1;
                 piv = T(1);
             }
+            const T rinv = T(1) / piv;
             T nv = T(-1);
             int ni = INT_MAX;
             for (int r = tid; r < R; r += kPanelThreads) {
                 if (r == pr || !active[r]) continue;
-                const T l = Sb[c * R + r] / piv;
+                const T l = Sb[c * R + r] * rinv;
                 Sb[c * R + r] = l;
                 for (int cc = c + 1; cc < w; ++cc) Sb[cc * R + r] -= l * Sb[cc * R + pr];
                 if (c + 1 < w) argmax_merge(nv, ni, tabs(Sb[(c + 1) * R + r]), r);
