@@ -457,9 +457,10 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
     HPS_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(double) * 2 * nbox, st));
     launch_extract<float>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st, w.norms);
     const int its = ctx->ir_iters;
+    if (its > 0) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, st);
     for (int it = 0; it < its; ++it) {
         launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
-                        w.M + g.n, P.ldm, w.sM, w.skip, st);
+                        w.M + g.n, P.ldm, w.sM, w.skip, st, w.kb);
         if (P.tc) {
             if (!tc_lu_forward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;
             if (!tc_lu_backward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;

@@ -65,6 +65,7 @@ struct Plan {
     // per-box byte sizes of the workspace pieces
     size_t bM = 0, bF = 0, bB = 0, bW = 0, bG = 0, bP = 0, bX = 0, bFp = 0, bBp = 0, bGp = 0;
     size_t bInv = 0, bGp2 = 0, bW2 = 0;   // tensor-core solves: inverse permutations, second G and W buffers
+    size_t bKB = 0;                       // refinement: kappa^2 b at the interior nodes
     size_t per_box = 0;
 };
 
@@ -112,6 +113,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     P.bG = P.bW;
     P.bP = align_up((size_t)P.perm_elems * sizeof(int), A);
     P.bX = need_x ? align_up((size_t)n * r * sizeof(double), A) : 0;
+    P.bKB = need_x ? align_up((size_t)n * sizeof(double), A) : 0;
     if (P.tc) {
         // split (hi, lo) K-major copies of F, B and G for the tensor-core products
         // (3 x TF32: two FP32 planes; 3 x BF16: three 2-byte planes)
@@ -123,7 +125,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
         P.bGp2 = P.bGp;
         P.bW2 = P.bW;
     }
-    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + P.bInv + P.bGp2 + P.bW2 + 64;
+    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + P.bInv + P.bGp2 + P.bW2 + P.bKB + 64;
     return P;
 }
 
@@ -136,6 +138,7 @@ struct Work {
     float *Fp, *Bp, *Gp;
     int* inv;
     float *Gp2, *W2;
+    double* kb;
     double* norms;
     int* skip;
     long long sM, sF, sB, sG, sP, sX, sFp, sBp, sGp;
@@ -160,6 +163,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
     w.inv = P.bInv ? reinterpret_cast<int*>(take(P.bInv)) : nullptr;
     w.Gp2 = P.bGp2 ? reinterpret_cast<float*>(take(P.bGp2)) : nullptr;
     w.W2 = P.bW2 ? reinterpret_cast<float*>(take(P.bW2)) : nullptr;
+    w.kb = P.bKB ? reinterpret_cast<double*>(take(P.bKB)) : nullptr;
     w.norms = reinterpret_cast<double*>(take(align_up(2 * sizeof(double), 16)));
     w.skip = reinterpret_cast<int*>(take(align_up(sizeof(int), 16)));
     w.sM = (long long)(P.bM / P.elt);
@@ -221,7 +225,10 @@ void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
-                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st);
+                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st,
+                     const double* kb = nullptr);
+void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
+                    double* kb, cudaStream_t st);
 
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
                       double* X, long long ldx, long long sX, double* norms /*[nbox][2]*/,

@@ -752,7 +752,8 @@ __global__ void __launch_bounds__(res_threads<Q>(), res_min_blocks<Q>())
 k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
            const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb, int rhs_kind,
            const double* __restrict__ rhs, long long s_rhs, const double* __restrict__ X, long long ldx,
-           long long sX, float* __restrict__ R, long long ldr, long long sR, const int* skip)
+           long long sX, float* __restrict__ R, long long ldr, long long sR, const int* skip,
+           const double* __restrict__ kb)
 {
     constexpr int H = Q / 2, TA = eo_tab_size<Q>();
     constexpr int q = Q, qq = Q * Q;
@@ -817,27 +818,28 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
         const double* rx = D2s + i * p;
         const double* ry = D2s + pp + j * p;
         float* Rb = R + box * sR + cw;
+        const double* kbb = kb ? kb + (long long)box * n : nullptr;
         eo_line<Q>(Xs + ln, qq, tab + 2 * TA, [&](int k0, double v) {
             const int k = k0 + 1, r = ln + qq * k0;
             const double* rz = D2s + 2 * pp + k * p;
             const int gi = i + p * j + pp * k;
-            double bval = 0.0;
-            if (kind == RHS_DTN) {
+            // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
+            double res = fma(kbb ? kbb[r] : k2 * bb[gi], Xs[r], Ac[r] + v);
+            if (kind == RHS_DTN) {   // -A_ib e_f: nonzero only next to face node f
                 const int f = cg / qq, s2 = cg % qq, a = s2 % q + 1, b2 = s2 / q + 1;
                 const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
-                if (axis == 0 && j == a && k == b2) bval = rx[e];
-                else if (axis == 1 && i == a && k == b2) bval = ry[e];
-                else if (axis == 2 && i == a && j == b2) bval = rz[e];
+                if (axis == 0 && j == a && k == b2) res += rx[e];
+                else if (axis == 1 && i == a && k == b2) res += ry[e];
+                else if (axis == 2 && i == a && j == b2) res += rz[e];
             } else if (kind == RHS_LOAD) {
-                bval = rhs[box * s_rhs + (long long)cg * p * pp + gi];
+                res += rhs[box * s_rhs + (long long)cg * p * pp + gi];
             } else {
                 const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
                 const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
-                bval = rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] +
+                res += rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] +
                        ry[p - 1] * ub[3 * qq + sy] + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
             }
-            // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
-            Rb[(long long)r * ldr] = float(bval + (Ac[r] + v) + k2 * bb[gi] * Xs[r]);
+            Rb[(long long)r * ldr] = float(res);
         });
     }
 }
@@ -1157,11 +1159,33 @@ void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols
     prof_end(KC_REFINE, st, 0.0, (double)nbox * n * (double)ncols * (sizeof(TS) + 8));
 }
 
+// kb[box][r] = kappa^2 b at interior node r (the residual's diagonal term,
+// the same for every column of a box).
+__global__ void k_kappa_b(int p, int n, const double* __restrict__ b, long long sb, double kappa2,
+                          const double* __restrict__ kappa_box, double* __restrict__ kb)
+{
+    const int box = blockIdx.y;
+    const int q = p - 2, qq = q * q, pp = p * p;
+    const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
+        kb[(long long)box * n + r] = k2 * b[box * sb + i + p * j + pp * k];
+    }
+}
+
+void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
+                    double* kb, cudaStream_t st)
+{
+    dim3 grd((unsigned)((g.n + 255) / 256), (unsigned)nbox);
+    k_kappa_b<<<grd, 256, 0, st>>>(g.p, g.n, b, sb, kappa * kappa, kappa_box, kb);
+}
+
 namespace {
 template <int Q>
 void residual_q(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                 int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs, const double* X, long long ldx,
-                long long sX, float* R, long long ldr, long long sR, const int* skip, cudaStream_t st)
+                long long sX, float* R, long long ldr, long long sR, const int* skip, cudaStream_t st,
+                const double* kb)
 {
     const size_t tables = (size_t)((3 * g.p * g.p + 1) & ~1) + 3 * eo_tab_size<Q>();
     const size_t smem = ((size_t)2 * g.n + tables) * sizeof(double);
@@ -1176,7 +1200,7 @@ void residual_q(const Geometry& g, double kappa, const double* kappa_box, int nb
     const double per = 3.0 * (2.0 + 2.0 * (Q / 2) + ((Q & 1) ? 2.0 : 0.0)) + 3.0;
     prof_begin(KC_RESIDUAL, st);
     k_residual<Q><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, nrhs, g.dD2, kappa * kappa, kappa_box, b, sb,
-                                                        rhs_kind, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, skip);
+                                                        rhs_kind, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, skip, kb);
     prof_end(KC_RESIDUAL, st, (double)nbox * g.n * (double)nrhs * per, (double)nbox * g.n * (double)nrhs * 12.0);
 }
 }  // namespace
@@ -1184,13 +1208,13 @@ void residual_q(const Geometry& g, double kappa, const double* kappa_box, int nb
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
-                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st)
+                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st, const double* kb)
 {
     static_assert(kMaxP - 2 == 22, "one residual instantiation per interior line length");
 #define HPS_RES_CASE(QV)                                                                                       \
     case QV:                                                                                                   \
         residual_q<QV>(g, kappa, kappa_box, nbox, b, sb, rhs_kind, nrhs, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, \
-                       skip, st);                                                                              \
+                       skip, st, kb);                                                                          \
         break;
     switch (g.q) {
         HPS_RES_CASE(1) HPS_RES_CASE(2) HPS_RES_CASE(3) HPS_RES_CASE(4) HPS_RES_CASE(5) HPS_RES_CASE(6)
