@@ -15,7 +15,7 @@ from tests._cases import rel_fro
 
 pytestmark = pytest.mark.gpu
 
-TOL = {H.HPS_FP64: 1e-11, H.HPS_FP32_IR: 1e-10}
+TOL = {H.HPS_FP64: 1e-11, H.HPS_FP32_IR: 1e-10, H.HPS_BF16_IR: 1e-10}
 
 
 def _dev(x):
@@ -67,7 +67,7 @@ def ctx():
     H.hps_destroy(c)
 
 
-@pytest.mark.parametrize("prec", [H.HPS_FP64, H.HPS_FP32_IR])
+@pytest.mark.parametrize("prec", [H.HPS_FP64, H.HPS_FP32_IR, H.HPS_BF16_IR])
 def test_groups_mixed_p_kappa_loads(ctx, prec):
     import torch
     H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, 1)

@@ -166,22 +166,25 @@ def test_dtn_dip_512_boxes_sampled(ctx, prec, tc, tol):
         assert rel_fro(S[box:box + 1], So[None]).max() < tol
 
 
-def test_dtn_fourier16_512_boxes_sampled(ctx):
+@pytest.mark.parametrize("prec", [H.HPS_FP32_IR, H.HPS_BF16_IR], ids=["fp32ir", "bf16ir"])
+def test_dtn_fourier16_512_boxes_sampled(ctx, prec):
     """The p = 16 mixed-precision workload at full size (512 boxes, kappa = 40),
-    tensor-core FP32 LU + FP64 refinement; two boxes against the oracle, and
-    every box against the plain FP64 GPU path."""
+    tensor-core LU (3 x TF32 or 3 x BF16) + FP64 refinement; two boxes and the
+    most-refined box against the oracle, and 32 evenly spaced boxes plus the
+    8 most-refined ones against the plain FP64 GPU path."""
     import torch
     p, h, kappa, lows, field = config_grid("fourier16")
     b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
-    T, _, st = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, want_S=False)
+    T, _, st = gpu_dtn(ctx, p, h, kappa, b_gpu, prec, 1, want_S=False)
     assert (st == 0).all(), np.unique(st, return_counts=True)
     it, rel = H.hps_last_refinement(ctx, len(lows))
     assert (it >= 1).all() and (it <= 8).all(), (it.min(), it.max())
-    for box in (5, 300):
+    hardest = np.argsort(-(it * 100.0 + rel / max(rel.max(), 1e-300)))[:8]
+    for box in (5, 300, int(hardest[0])):
         To, _, info = oracle.leaf_dtn(p, h, kappa, field(oracle.node_coords(p, lows[box], h)), want_S=False)
         assert info == 0
         assert rel_fro(T[box:box + 1], To[None]).max() < 1e-10
-    sel = np.arange(0, 512, 16)
+    sel = np.unique(np.concatenate([np.arange(0, 512, 16), hardest]))
     T64, _, st64 = gpu_dtn(ctx, p, h, kappa, b_gpu[sel], H.HPS_FP64, 0, want_S=False)
     assert (st64 == 0).all()
     assert rel_fro(T[sel], T64).max() < 1e-10
