@@ -138,13 +138,16 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Bounded wait on an mbarrier phase; false when it gave up.
+// Bounded wait on an mbarrier phase; false when it gave up.  The epilogue
+// warps back off (spinning warps steal issue slots); the single-thread TMA
+// and MMA roles poll (try_wait already suspends in hardware for a while).
+template <bool kBackoff = true>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (it >= 8) __nanosleep(it < 64 ? 32 : 128);   // back off: spinning warps steal issue slots
+        if (kBackoff && it >= 8) __nanosleep(it < 64 ? 32 : 128);
         if ((it & 255u) == 255u) {
             if (*reinterpret_cast<volatile int*>(&g_tc_abort)) return false;
             if (global_ns() - t0 > WAIT_NS) {
@@ -467,7 +470,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 for (int ch = 0; ch < a.kch; ++ch, ++g) {
                     const int s = g % TC_STAGES;
                     const uint32_t use = g / TC_STAGES;
-                    if (g >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[s]), (use - 1) & 1)) {
+                    if (g >= TC_STAGES && !mbar_wait<false>(smem_u32(&empty_bar[s]), (use - 1) & 1)) {
                         fail_sh = 1;
                         ok = false;
                         break;
@@ -500,8 +503,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             // (in a pair) both MMAs have released every stage, so no arrival
             // from the partner is still on its way when this CTA exits.
             for (uint32_t h = (g > TC_STAGES ? g - TC_STAGES : 0); h < g; ++h) {
-                if (!mbar_wait(smem_u32(&full_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
-                if (!mbar_wait(smem_u32(&empty_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
+                if (!mbar_wait<false>(smem_u32(&full_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
+                if (!mbar_wait<false>(smem_u32(&empty_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
             }
         }
     } else if (warp == 1) {
@@ -513,12 +516,12 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (sc.skipped(u, a.skip)) continue;
                 const int b = j & 1;
                 const uint32_t uj = j >> 1;
-                if (j >= 2 && !mbar_wait(smem_u32(&tempty_bar[b]), (uj - 1) & 1)) { fail_sh = 1; break; }
+                if (j >= 2 && !mbar_wait<false>(smem_u32(&tempty_bar[b]), (uj - 1) & 1)) { fail_sh = 1; break; }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int ch = 0; ch < a.kch; ++ch, ++g) {
                     const int s = g % TC_STAGES;
-                    if (!mbar_wait(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1)) { fail_sh = 1; ok = false; break; }
+                    if (!mbar_wait<false>(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1)) { fail_sh = 1; ok = false; break; }
                     tc_fence_after();
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     uint64_t ad[NPL], bd[NPL];
