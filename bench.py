@@ -82,7 +82,7 @@ def parse_args():
     ap.add_argument("--precision", choices=("fp32ir", "bf16ir", "fp64"), default="fp32ir")
     ap.add_argument("--nbox", type=int, default=NBOX)
     ap.add_argument("--fp64-sample", type=int, default=32)
-    ap.add_argument("--cpu-sample", type=int, default=8)
+    ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
