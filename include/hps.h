@@ -113,6 +113,9 @@ typedef enum {
                                    pairs (look-ahead on the next panel, one 2 NB-deep update per pair and one
                                    product per pair in the solves); 0: one step at a time.  Results agree to
                                    rounding */
+    HPS_OPT_TC_FUSE = 11,       /* gathers of the backward solves written by the previous product's TMA
+                                   epilogue: -1 (default) where that measured faster (3 x TF32 operands),
+                                   0 never, 1 always; results are bit-identical either way */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;

@@ -88,6 +88,7 @@ struct hps_ctx {
     int tc_epi_cp = 0;          // 1: tcgen05 epilogue always in the cp.async form
     int tc_pairs = 0;           // 1: tcgen05 products by CTA pairs sharing the right operand
     int lu_pairs = 1;           // 0: no joining of LU steps in pairs on the tcgen05 path
+    int tc_fuse = -1;           // -1: fused gathers where they measured faster, 0: never, 1: backward sweeps
     int use_tc = 1;
     int sync = 0;
     int zero_row_box = -1;
@@ -357,6 +358,7 @@ Plan job_plan(const hps_ctx* ctx, const Job& j, hps_precision prec)
                        ctx->lu_pairs != 0);
     P.tma_epi = ctx->tc_epi_cp == 0;
     P.tc_pairs = ctx->tc_pairs != 0;
+    if (ctx->tc_fuse >= 0) P.fuse_bwd = P.tc && ctx->tc_fuse != 0;
     return P;
 }
 
@@ -639,7 +641,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     const bool use_graph = ctx->graphs && !ctx->prof_on;
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->tc_fuse << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
@@ -867,6 +869,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
     case HPS_OPT_LU_PAIRS:
         if (!(value == 0 || value == 1)) return HPS_EINVAL;
         ctx->lu_pairs = (int)value;
+        return HPS_OK;
+    case HPS_OPT_TC_FUSE:
+        if (!(value == -1 || value == 0 || value == 1)) return HPS_EINVAL;
+        ctx->tc_fuse = (int)value;
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;
