@@ -313,6 +313,16 @@ hps_status hps_profile_get(hps_ctx* ctx, int cls, long long* launches, double* m
 
 const char* hps_status_string(hps_status s);
 
+/* Self-test of the FP64 <-> FP32 conversions that the refinement kernels run
+ * on the integer pipe (IEEE-754 round to nearest even, hardware conversion for
+ * values outside the normal range): n values on device `device` (random bit
+ * patterns over all exponents, values at the float range limits, exact
+ * rounding ties) are converted both ways and compared bit for bit with the
+ * hardware conversions.  mismatches[0] receives the double -> float
+ * mismatches, mismatches[1] the float -> double ones (host array of 2).
+ * Allocates 16 bytes of device memory for the call; synchronises. */
+hps_status hps_selftest_conversions(int device, long long n, unsigned long long seed, long long* mismatches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ __all__ = [
     "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
     "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_TC_PAIRS", "HPS_OPT_LU_PAIRS", "HPS_OPT_TC_FUSE", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
-    "hps_dtn_gate",
+    "hps_dtn_gate", "hps_selftest_conversions",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = (
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
-    "hps_dtn_gate",
+    "hps_dtn_gate", "hps_selftest_conversions",
 )
 
 # Kernel classes of hps_profile_get.
@@ -98,6 +98,7 @@ def load_library() -> ctypes.CDLL:
         "hps_destroy": (None, [vp]),
         "hps_set_option": (i, [vp, i, d]),
         "hps_leaf_sizes": (i, [i, ip, ip]),
+        "hps_selftest_conversions": (i, [i, ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "hps_leaf_nodes": (i, [i, dp, dp, dp]),
         "hps_workspace_per_box": (sz, [i, i]),
         "hps_leaf_build_dtn": (i, [vp, kp, i, vp, vp, vp, i, vp, vp]),
@@ -193,6 +194,14 @@ def hps_destroy(ctx: int) -> None:
 
 def hps_set_option(ctx: int, option: int, value: float) -> None:
     _check(load_library().hps_set_option(ctx, int(option), float(value)), "hps_set_option")
+
+
+def hps_selftest_conversions(device: int = 0, n: int = 1 << 24, seed: int = 1):
+    """(double->float, float->double) mismatch counts of the integer-pipe
+    conversions against the hardware ones (both 0 when correct)."""
+    out = (ctypes.c_longlong * 2)()
+    _check(load_library().hps_selftest_conversions(int(device), int(n), int(seed), out), "hps_selftest_conversions")
+    return int(out[0]), int(out[1])
 
 
 def hps_leaf_sizes(p: int):

@@ -747,6 +747,27 @@ hps_status run_single(hps_ctx* ctx, Job j, const hps_leaf_kind* kind, hps_precis
 
 extern "C" {
 
+hps_status hps_selftest_conversions(int device, long long n, unsigned long long seed, long long* mismatches)
+{
+    if (n < 0 || !mismatches) return HPS_EINVAL;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return HPS_ECUDA;
+    unsigned long long* d = nullptr;
+    unsigned long long h[2] = {0, 0};
+    hps_status rc = HPS_OK;
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) rc = HPS_ENOMEM;
+    if (rc == HPS_OK && cudaMemset(d, 0, sizeof(h)) != cudaSuccess) rc = HPS_ECUDA;
+    if (rc == HPS_OK) {
+        hps::selftest_conversions(n, seed, d, 0);
+        if (cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HPS_ECUDA;
+    }
+    if (d) cudaFree(d);
+    cudaSetDevice(prev);
+    mismatches[0] = (long long)h[0];
+    mismatches[1] = (long long)h[1];
+    return rc;
+}
+
 const char* hps_status_string(hps_status s)
 {
     switch (s) {

@@ -121,7 +121,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
         P.bFp = align_up((size_t)P.fw_elems * pk, A);
         P.bBp = align_up((size_t)P.bw_elems * pk, A);
         P.bGp = align_up((size_t)P.ldm * P.KG * pk, A);
-        P.bInv = P.bP;
+        P.bInv = P.fuse_fwd ? P.bP : 0;
         P.bGp2 = P.bGp;
         P.bW2 = P.bW;
     }
@@ -227,6 +227,7 @@ void launch_residual(const Geometry& g, double kappa, const double* kappa_box, i
                      const double* X, long long ldx, long long sX,
                      float* R, long long ldr, long long sR, const int* skip, cudaStream_t st,
                      const double* kb = nullptr);
+void selftest_conversions(long long n, unsigned long long seed, unsigned long long* mism_dev, cudaStream_t st);
 void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                     double* kb, cudaStream_t st);
 

@@ -39,6 +39,41 @@ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
+// Conversions between FP64 and FP32 on the integer pipe (on GB300 the FP64
+// pipe that executes the conversion instructions is the residual's and the
+// refinement update's bottleneck).  Both follow the IEEE-754 binary64 /
+// binary32 encodings; anything outside the normal range goes to the hardware
+// conversion.  hps_selftest_conversions checks them bit for bit against it.
+//
+// double -> float, round to nearest even: the 52-bit significand is rounded
+// to 23 bits by adding 0x0FFFFFFF plus the kept part's last bit before the
+// 29-bit shift (a carry into the exponent is the correct result, up to
+// infinity), and the exponent is rebiased from 1023 to 127.
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long a = u & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned e = (unsigned)(a >> 52);
+    if (e - 897u > 253u) return __double2float_rn(x);   // zero, float subnormal or overflow, inf, NaN
+    const unsigned long long r = (a + 0x0FFFFFFFull + ((a >> 29) & 1ull)) >> 29;
+    const unsigned f = (unsigned)(r - (896ull << 23)) | (unsigned)((u >> 32) & 0x80000000u);
+    return __uint_as_float(f);
+}
+
+// float -> double (exact): the significand moves up 29 bits and the exponent
+// is rebiased from 127 to 1023; zero keeps its sign.
+__device__ __forceinline__ double f2d(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+    if (e - 1u > 253u) {
+        if ((u << 1) == 0u) return __longlong_as_double((long long)sgn);
+        return (double)x;                                  // subnormal, inf, NaN
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x7FFFFFFFu) << 29) + (896ull << 52) | sgn));
+}
+
 // ---------------------------------------------------------------- assembly
 
 // Rows per CTA of the operator build.
@@ -654,7 +689,8 @@ k_extract(const TS* __restrict__ src, long long lds, long long sS, int n, int nc
         double* xrow = X + box * sX + (long long)r * ldx;
         for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
             const TS v = srow[c];
-            xrow[c] = double(v);
+            if constexpr (sizeof(TS) == 4) xrow[c] = f2d(v);
+            else xrow[c] = double(v);
             if (xnorm) xn = fmaf((float)v, (float)v, xn);
         }
     }
@@ -839,7 +875,7 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
                 res += rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] +
                        ry[p - 1] * ub[3 * qq + sy] + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
             }
-            Rb[(long long)r * ldr] = float(res);
+            Rb[(long long)r * ldr] = d2f_rn(res);
         });
     }
 }
@@ -860,7 +896,7 @@ k_ir_update(const float* __restrict__ D, long long ldd, long long sD, int n, int
         double* xrow = X + box * sX + (long long)r * ldx;
         for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
             const float d = drow[c];
-            const double x = xrow[c] + double(d);
+            const double x = xrow[c] + f2d(d);
             xrow[c] = x;
             dn = fmaf(d, d, dn);
             if (want_xn) xn = fma(x, x, xn);
@@ -1171,6 +1207,41 @@ __global__ void k_kappa_b(int p, int n, const double* __restrict__ b, long long 
         const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
         kb[(long long)box * n + r] = k2 * b[box * sb + i + p * j + pp * k];
     }
+}
+
+// Self-test of d2f_rn and f2d against the hardware conversions over n
+// values: splitmix64 bit patterns (all exponents), values near the float
+// range limits and rounding ties.  mism[0] counts double -> float
+// mismatches, mism[1] float -> double (bitwise; NaN against NaN).
+__global__ void k_selftest_conv(long long n, unsigned long long seed, unsigned long long* mism)
+{
+    unsigned long long bad_d = 0, bad_f = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        unsigned long long bits = z;
+        const int kind = (int)(i & 7);
+        if (kind == 1) bits = (z & 0x800FFFFFFFFFFFFFull) | ((unsigned long long)(1023 + (int)((z >> 52) % 40) - 20) << 52);
+        if (kind == 2) bits = (z & 0x800FFFFFFFFFFFFFull) | ((unsigned long long)(896 + (int)((z >> 52) % 4)) << 52);
+        if (kind == 3) bits = (z & 0x800FFFFFFFFFFFFFull) | ((unsigned long long)(1148 + (int)((z >> 52) % 4)) << 52);
+        if (kind == 4) bits = (z & 0xFFFFFFFFE0000000ull) | 0x10000000ull;   // exact ties at the 23-bit boundary
+        if (kind == 5) bits = (z & 0xFFFFFFFFE0000000ull) | 0x0FFFFFFFull;
+        const double x = __longlong_as_double((long long)bits);
+        const float a = d2f_rn(x), b = __double2float_rn(x);
+        if (!((a != a && b != b) || __float_as_uint(a) == __float_as_uint(b))) ++bad_d;
+        const float y = __uint_as_float((unsigned)(z >> 7));
+        const double c = f2d(y), d = (double)y;
+        if (!((c != c && d != d) || __double_as_longlong(c) == __double_as_longlong(d))) ++bad_f;
+    }
+    if (bad_d) atomicAdd(mism, bad_d);
+    if (bad_f) atomicAdd(mism + 1, bad_f);
+}
+
+void selftest_conversions(long long n, unsigned long long seed, unsigned long long* mism_dev, cudaStream_t st)
+{
+    k_selftest_conv<<<1024, 256, 0, st>>>(n, seed, mism_dev);
 }
 
 void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,

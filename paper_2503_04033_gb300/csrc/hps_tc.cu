@@ -1325,12 +1325,14 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
             if (!up(left_fwd_pair(P, w, s), a)) return false;
         }
     }
-    // Inverse permutations of the solve units, for the gathers fused into the
-    // products of the solves.
-    for (const auto& u : solve_units(P)) {
-        const int s = u.first, wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
-        k_perm_inverse<<<nbox, 256, 0, st>>>(w.perm + P.perm_off[s], w.inv + P.perm_off[s], w.sP, n - P.k0[s], wp);
-    }
+    // Inverse permutations of the solve units, for gathers fused into the
+    // forward solves.
+    if (P.fuse_fwd)
+        for (const auto& u : solve_units(P)) {
+            const int s = u.first, wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
+            k_perm_inverse<<<nbox, 256, 0, st>>>(w.perm + P.perm_off[s], w.inv + P.perm_off[s], w.sP, n - P.k0[s],
+                                                 wp);
+        }
     return true;
 }
 

@@ -333,3 +333,12 @@ def test_end_to_end_manufactured(ctx):
     assert np.abs(ui.cpu().numpy()[:, 0, :] - ref["u_int"]).max() < 1e-10 * scale
     exact = hi.manufactured(gs.interior_coords(grid), kappa)[0]
     assert np.abs(ui.cpu().numpy()[:, 0, :] - exact).max() < 1e-4
+
+
+@pytest.mark.parametrize("seed", [1, 20250304])
+def test_integer_pipe_conversions_match_hardware(seed):
+    """The refinement kernels convert FP64 <-> FP32 on the integer pipe; over
+    16 M values (all exponents, float range limits, rounding ties) both
+    directions agree bit for bit with the hardware conversions."""
+    assert H.hps_selftest_conversions(0, 1 << 24, seed) == (0, 0)
+
