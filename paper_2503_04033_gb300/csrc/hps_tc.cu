@@ -860,12 +860,12 @@ __global__ void k_pack_split(const float* __restrict__ src, long long lds, long 
     const int box = blockIdx.y;
     const long long total = (long long)rows * NB;
     void* db = FMT == 0 ? (void*)(static_cast<float*>(dst) + box * sD) : (void*)(static_cast<unsigned short*>(dst) + box * sD);
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(idx % NB);
-        const long long r = idx / NB;
-        const float x = c < nb ? src[box * sS + r * lds + c] : 0.0f;
-        split_store<FMT>(db, idx, total, x);
+    const float* sb = src + box * sS;
+    // rows over the grid, columns over the threads (no index division)
+    for (int r = blockIdx.x * blockDim.y + threadIdx.y; r < rows; r += gridDim.x * blockDim.y) {
+        const float* srow = sb + (long long)r * lds;
+        for (int c = threadIdx.x; c < NB; c += blockDim.x)
+            split_store<FMT>(db, (long long)r * NB + c, total, c < nb ? srow[c] : 0.0f);
     }
 }
 
@@ -1074,11 +1074,11 @@ void launch_pack_split(int fmt, const float* src, long long lds, long long sS, i
                        long long sD, int nbox, cudaStream_t st)
 {
     const long long total = (long long)rows * NB;
-    int blocks = (int)std::min<long long>((total + 255) / 256, 256);
-    dim3 grd((unsigned)blocks, (unsigned)nbox);
+    const dim3 blk(32, 8);   // 8 rows of 32-column strips per CTA
+    dim3 grd((unsigned)std::max(1, std::min((rows + 7) / 8, 128)), (unsigned)nbox);
     prof_begin(KC_PACK, st);
-    if (fmt) k_pack_split<1><<<grd, 256, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
-    else k_pack_split<0><<<grd, 256, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
+    if (fmt) k_pack_split<1><<<grd, blk, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
+    else k_pack_split<0><<<grd, blk, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
     prof_end(KC_PACK, st, 0.0, (double)nbox * total * (4.0 + (fmt ? 6.0 : 8.0)));
 }
 
