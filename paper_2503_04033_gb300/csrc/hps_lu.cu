@@ -625,33 +625,46 @@ k_gemm(GemmArgs<T> g)
 //                                 + [add_abb] (D_a[e, e] [c = r] + D_a[e, e'] [c = opp(r)]) )
 // for face row r on face f (axis a, own index e, opposite e').  With X = S this
 // is T = A_bb + A_bi S (Eq. 8); with X = v and no A_bb it is h = A_bi v.
+// One thread forms the outputs of both faces of an axis at the same face
+// position (rows f qq + s and (f + 1) qq + s), which read the same grid line
+// of X: the line is loaded once.
 __global__ void k_dn(int p, int n, int m, int ncols, const double* __restrict__ D,
                      const double* __restrict__ X, long long ldx, long long sX, double* __restrict__ out,
                      long long sOut, int transposed_out, int add_abb)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
+    const int r2 = blockIdx.y;   // axis * qq + s
     const int box = blockIdx.z;
     if (c >= ncols) return;
     const int q = p - 2, qq = q * q;
-    const int f = r / qq, s = r - f * qq, a = s % q + 1, bb = s / q + 1;
-    const int axis = f >> 1, e = (f & 1) ? p - 1 : 0, eo = (f & 1) ? 0 : p - 1;
-    const double sg = (f & 1) ? 1.0 : -1.0;
-    const double* Da = D + axis * p * p + e * p;
+    const int axis = r2 / qq, s = r2 - axis * qq, a = s % q + 1, bb = s / q + 1;
+    const int r0 = 2 * axis * qq + s, r1 = r0 + qq;   // face 2 axis (node index 0), face 2 axis + 1 (p - 1)
+    const double* D0 = D + axis * p * p;               // row 0 of D_axis
+    const double* D1 = D0 + (p - 1) * p;               // row p - 1
     const double* Xb = X + box * sX;
     long long base, stride;
     if (axis == 0) { base = q * (a - 1) + qq * (bb - 1) - 1; stride = 1; }
     else if (axis == 1) { base = (a - 1) + qq * (bb - 1) - q; stride = q; }
     else { base = (a - 1) + q * (bb - 1) - qq; stride = qq; }
-    double acc = 0.0;
-    for (int l = 1; l <= q; ++l) acc += __ldg(Da + l) * Xb[(base + l * stride) * ldx + c];
-    if (add_abb) {
-        if (c == r) acc += __ldg(Da + e);
-        if (c == ((f ^ 1) * qq + s)) acc += __ldg(Da + eo);
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int l = 1; l <= q; ++l) {
+        const double x = Xb[(base + l * stride) * ldx + c];
+        acc0 += __ldg(D0 + l) * x;
+        acc1 += __ldg(D1 + l) * x;
     }
-    acc *= sg;
-    if (transposed_out) out[box * sOut + (long long)c * m + r] = acc;
-    else out[box * sOut + (long long)r * m + c] = acc;
+    if (add_abb) {
+        if (c == r0) { acc0 += __ldg(D0); acc1 += __ldg(D1); }
+        if (c == r1) { acc0 += __ldg(D0 + p - 1); acc1 += __ldg(D1 + p - 1); }
+    }
+    acc0 = -acc0;   // outward normal of the low face is -axis
+    double* ob = out + box * sOut;
+    if (transposed_out) {
+        ob[(long long)c * m + r0] = acc0;
+        ob[(long long)c * m + r1] = acc1;
+    } else {
+        ob[(long long)r0 * m + c] = acc0;
+        ob[(long long)r1 * m + c] = acc1;
+    }
 }
 
 // ---------------------------------------------------------------- refinement
@@ -1179,7 +1192,7 @@ void launch_dn(const Geometry& g, int nbox, const double* X, long long ldx, long
                int ncols, double* out, long long sOut, int transposed_out, int add_abb,
                cudaStream_t st)
 {
-    dim3 grd((unsigned)((ncols + 127) / 128), (unsigned)g.m, (unsigned)nbox);
+    dim3 grd((unsigned)((ncols + 127) / 128), (unsigned)(g.m / 2), (unsigned)nbox);
     prof_begin(KC_DN, st);
     k_dn<<<grd, 128, 0, st>>>(g.p, g.n, g.m, ncols, g.dD, X, ldx, sX, out, sOut, transposed_out, add_abb);
     prof_end(KC_DN, st, 2.0 * nbox * g.m * (double)ncols * g.q, (double)nbox * ((double)g.n + g.m) * ncols * 8);
