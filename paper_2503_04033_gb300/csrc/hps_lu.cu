@@ -20,6 +20,8 @@
 //   permutation rides in the update's epilogue.
 // Backward substitution (U x = y) runs the same product with
 //   B_s = [U[0:k, k:k+nb] U11^{-1}; -U11^{-1}], src(r) = M[r] for r < k, 0 after.
+// (On the tensor-core path two consecutive steps are joined into one product
+// of depth 2 NB; see the LU sequences in hps_tc.cu.)
 // Forward substitution of new right-hand sides replays the stored (pi_s, F_s).
 #include <algorithm>
 #include <cfloat>

@@ -1,24 +1,26 @@
 // Tensor-core update products of the FP32 LU (sm_103a, tcgen05 + TMA).
 //
 // Every trailing update and triangular-solve step of the blocked LU is a
-// product O <- src - A G with A = F_s or B_s (rows x NB) and G the step's
-// gathered rows (NB x N); see hps_lu.cu for the scheme.  Here that product
-// runs on the 5th-generation tensor cores with FP32 accuracy from TF32 inputs:
-// every operand x is split as x = hi + lo with hi = tf32(x), lo = tf32(x - hi),
-// and A G ~ A_hi G_hi + A_hi G_lo + A_lo G_hi (the lo*lo term is below FP32
-// rounding).  The split operands are packed K-major (A as [row][k], G
-// transposed to [col][k]) so that TMA brings 64-byte rows (16 values of K)
-// into shared memory in the 64B-swizzled layout that tcgen05.mma reads directly.
+// product O <- src - A G with A = F_s or B_s (rows x NB, or rows x 2 NB for a
+// pair of steps) and G the step's gathered rows; see hps_lu.cu for the scheme
+// and the LU sequences at the end of this file for the pairs.  Here that
+// product runs on the 5th-generation tensor cores with FP32 accuracy from
+// split operands (TcFmt): 3 x TF32 (x = hi + lo, three kind::tf32 products)
+// or 3 x BF16 (x = hi + mid + lo, six kind::f16 products), FP32 accumulation
+// in TMEM.  The split operands are packed K-major (A as [plane][row][k], G
+// transposed to [plane][col][k]) so that TMA brings 64-byte rows of K into
+// shared memory in the 64B-swizzled layout that tcgen05.mma reads directly.
 //
-// A persistent CTA per SM walks 128 x 256 output tiles: warp 0 issues the TMA
-// loads (3-stage ring over 16-wide K chunks, 48 KiB a stage), warp 1 owns two
-// TMEM accumulators (all 512 columns) and issues the MMAs (one elected lane),
-// warps 2-5 drain TMEM with tcgen05.ld and apply the epilogue (source rows:
-// zero, in place, or saved pivot rows) while the next tile accumulates.  The
-// split operands are the traffic that bounds this kernel (12 bytes per output
-// element at 128 x 256 against 8 for reading and writing O): wider tiles re-read
-// A less often.  All mbarrier waits are bounded; a wait that gives up marks the
-// box HPS_ETIMEOUT.
+// A persistent CTA per SM walks output tiles (128 x 256 for TF32, 128 x 128
+// for BF16): warp 0 issues the TMA loads (3-stage ring of 48 KiB K chunks;
+// the left operand may come from two tensor maps), warp 1 owns two TMEM
+// accumulators and issues the MMAs (one elected lane), warps 2-5 drain TMEM
+// with tcgen05.ld and apply the epilogue (source rows: zero, in place, or
+// saved pivot rows; by TMA in and out where O is 16-byte aligned, cp.async
+// otherwise) while the next tile accumulates.  At K = 2 NB the product sits
+// at the 3 x TF32 ridge: tensor work and operand plus O traffic both matter.
+// All mbarrier waits are bounded; a wait that gives up marks the box
+// HPS_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
