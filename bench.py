@@ -373,6 +373,25 @@ def run_ours(args):
                             "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
                             "peak_source": note, "launches_per_step": d["launches"]}
 
+    # ---- the FP64 residual (the largest kernel by time; its launches skip
+    # converged boxes, so its work is counted from the refinement histogram):
+    # FP64 pipe instructions per (point, column) of the even/odd line form,
+    # 3 (h + 2) + 3 with h = (p - 2) // 2 at even p - 2, against the issue
+    # rate of the FP64 pipes (2 per clock per SM at the SM clock sampled).
+    if "residual_fp64" in prof and prec != H.HPS_FP64:
+        q = P - 2
+        per_entry = 3 * (q // 2 + 2) + 3 + (6 if q % 2 else 0)
+        box_its = float(it.sum())                        # residual evaluations per step (every step alike)
+        instr = box_its * n * m * per_entry
+        rms = prof["residual_fp64"]["ms_per_step"]
+        sm_mhz = (line.get("clocks") or {}).get("sm_mhz") or 2070.0
+        peak_ips = 2.0 * torch.cuda.get_device_properties(dev).multi_processor_count * sm_mhz * 1e6
+        line["roofline_fp64_residual"] = {
+            "kernel": "residual_fp64", "bound": "alu", "achieved": instr / (rms / 1e3) / 1e9,
+            "peak": peak_ips / 1e9, "unit": "G FP64-pipe instr/s", "frac": instr / (rms / 1e3) / peak_ips,
+            "instr_per_entry": per_entry, "box_iterations_per_step": box_its,
+            "peak_source": "2 FP64 instructions per clock per SM x SMs x sampled SM clock"}
+
     # ---- plain FP64 GPU path on a sample of the same boxes
     if not args.no_fp64 and prec != H.HPS_FP64 and args.fp64_sample > 0:
         k = min(args.fp64_sample, nbox)
