@@ -659,6 +659,18 @@ def run_uneven(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
+    # one more call, outside the timed region, with per-kernel events (graphs off)
+    H.hps_set_option(ctx, H.HPS_OPT_GRAPHS, 0)
+    H.hps_profile_enable(ctx, True)
+    H.hps_profile_reset(ctx)
+    H.hps_leaf_groups(ctx, groups, H.HPS_FP32_IR, stream)
+    torch.cuda.synchronize(dev)
+    H.hps_profile_enable(ctx, False)
+    prof = {}
+    for cls, name in enumerate(H.KERNEL_CLASSES):
+        nl, kms, fl, by = H.hps_profile_get(ctx, cls)
+        if nl:
+            prof[name] = {"launches": nl, "ms": kms}
     H.hps_destroy(ctx)
     line = {"metric": "uneven leaf batch: boxes/s (DtN + 32 particular solutions per box, mixed p)",
             "value": 1024 / (ms / 1e3), "unit": "boxes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -666,7 +678,8 @@ def run_uneven(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": UNEVEN, "boxes_per_p": {str(p): int((d["p"] == p).sum()) for p in (8, 12, 16, 20)},
                        "graphs": True, "autotune": True},
-            "tflops": flops / (ms / 1e3) / 1e12, "box_failures": fails, "clocks": clocks.summary()}
+            "tflops": flops / (ms / 1e3) / 1e12, "box_failures": fails, "clocks": clocks.summary(),
+            "kernels_one_call": prof}
     print(json.dumps(line), flush=True)
 
 
