@@ -116,6 +116,12 @@ typedef enum {
     HPS_OPT_TC_FUSE = 11,       /* gathers of the backward solves written by the previous product's TMA
                                    epilogue: -1 (default) where that measured faster (3 x TF32 operands),
                                    0 never, 1 always; results are bit-identical either way */
+    HPS_OPT_RESIDUAL_DF = 12,   /* 1 (default): in FP32_IR and BF16_IR mode with at least 2 corrections, the
+                                   first residual, of the low-precision solution itself, runs in double-float
+                                   arithmetic on the FP32 pipes (about 2^-46 relative to the sum of the
+                                   terms' magnitudes) and that correction never ends the refinement, so every
+                                   result still ends on corrections from the FP64 residual; 0: every residual
+                                   in FP64 */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;
@@ -303,10 +309,11 @@ hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const
  * update product, 3 tensor-core update product, 4 row gather of the products,
  * 5 FP64 refinement residual, 6 refinement update, 7 D_n product,
  * 8 tensor-core update product of the refinement solves, 9 split copies of
- * the LU operators), the accumulated launches, milliseconds, flops and bytes
- * since the last reset.  Refinement launches skip boxes that have converged,
- * so classes 5, 6 and 8 count the work of every box and overstate flops and
- * bytes.  Returns HPS_EINVAL for cls outside 0..9. */
+ * the LU operators, 10 double-float first residual), the accumulated
+ * launches, milliseconds, flops and bytes since the last reset.  Refinement
+ * launches skip boxes that have converged, so classes 5, 6 and 8 count the
+ * work of every box and overstate flops and bytes.  Returns HPS_EINVAL for cls
+ * outside 0..10. */
 hps_status hps_profile_enable(hps_ctx* ctx, int on);
 hps_status hps_profile_reset(hps_ctx* ctx);
 hps_status hps_profile_get(hps_ctx* ctx, int cls, long long* launches, double* ms, double* flops, double* bytes);

@@ -89,6 +89,7 @@ struct hps_ctx {
     int tc_pairs = 0;           // 1: tcgen05 products by CTA pairs sharing the right operand
     int lu_pairs = 1;           // 0: no joining of LU steps in pairs on the tcgen05 path
     int tc_fuse = -1;           // -1: fused gathers where they measured faster, 0: never, 1: backward sweeps
+    int res_df = 1;             // first correction's residual in double-float on the FP32 pipes
     int use_tc = 1;
     int sync = 0;
     int zero_row_box = -1;
@@ -301,6 +302,42 @@ hps_status get_geometry(hps_ctx* ctx, int p, const double h[3], Geometry** out)
     HPS_CUDA_TRY(cudaMalloc(&g.dD2, sizeof(double) * 3 * pp));
     HPS_CUDA_TRY(cudaMemcpy(g.dD, D.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
     HPS_CUDA_TRY(cudaMemcpy(g.dD2, D2.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
+    // Double-float line tables of the first residual: the even/odd (E, O)
+    // pairs, the odd-q middle entries and the boundary couplings of each axis,
+    // every value split as hi = float(v), lo = float(v - hi).
+    {
+        const int q = g.q, H = q / 2, TF = df_tab_f4(q);
+        std::vector<float> DF((size_t)3 * TF * 4, 0.0f);
+        auto split = [](double v, float* o) {
+            o[0] = (float)v;
+            o[1] = (float)(v - (double)o[0]);
+        };
+        for (int a = 0; a < 3; ++a) {
+            const double* Dm = D2.data() + (size_t)a * pp;
+            float* t = DF.data() + (size_t)a * TF * 4;
+            for (int i = 0; i < H; ++i)
+                for (int l = 0; l < H; ++l) {
+                    const double u = Dm[(i + 1) * p + (l + 1)], w = Dm[(i + 1) * p + (p - 2 - l)];
+                    split(0.5 * (u + w), t + 4 * (i * H + l));
+                    split(0.5 * (u - w), t + 4 * (i * H + l) + 2);
+                }
+            int off = 4 * H * H;
+            if (q & 1) {
+                const int mid = H + 1;
+                for (int i = 0; i < H; ++i) split(Dm[(i + 1) * p + mid], t + off + 2 * i);
+                for (int l = 0; l < H; ++l)
+                    split(0.5 * (Dm[mid * p + (l + 1)] + Dm[mid * p + (p - 2 - l)]), t + off + 2 * H + 2 * l);
+                split(Dm[mid * p + mid], t + off + 4 * H);
+                off += 4 * (H + 1);
+            }
+            for (int i = 1; i <= q; ++i) {
+                split(Dm[i * p], t + off + 4 * (i - 1));
+                split(Dm[i * p + p - 1], t + off + 4 * (i - 1) + 2);
+            }
+        }
+        HPS_CUDA_TRY(cudaMalloc(&g.dDF, sizeof(float) * DF.size()));
+        HPS_CUDA_TRY(cudaMemcpy(g.dDF, DF.data(), sizeof(float) * DF.size(), cudaMemcpyHostToDevice));
+    }
     auto res = ctx->geoms.emplace(key, g);
     *out = &res.first->second;
     return HPS_OK;
@@ -459,10 +496,17 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
     HPS_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(double) * 2 * nbox, st));
     launch_extract<float>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st, w.norms);
     const int its = ctx->ir_iters;
-    if (its > 0) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, st);
+    // The first residual, of the FP32 solution itself, may run in double-float
+    // when at least one FP64-residual correction follows it.
+    const bool df = ctx->res_df && its >= 2 && g.dDF;
+    if (its > 0) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, df ? w.kbs : nullptr, st);
     for (int it = 0; it < its; ++it) {
-        launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
-                        w.M + g.n, P.ldm, w.sM, w.skip, st, w.kb);
+        if (df && it == 0)
+            launch_residual_df(g, nbox, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M + g.n, P.ldm, w.sM, w.kbs, w.skip,
+                               st);
+        else
+            launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
+                            w.M + g.n, P.ldm, w.sM, w.skip, st, w.kb);
         if (P.tc) {
             if (!tc_lu_forward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;
             if (!tc_lu_backward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;
@@ -471,7 +515,7 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
             lu_backward<float>(P, w, nbox, g.n, cs.r, w.skip, st);
         }
         launch_ir_update(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, w.norms, w.skip, nbox, st);
-        launch_ir_check(nbox, w.norms, ctx->ir_tol, it == its - 1, w.skip, iters, relcorr, status, st);
+        launch_ir_check(nbox, w.norms, ctx->ir_tol, it == its - 1, w.skip, iters, relcorr, status, st, df && it == 0);
     }
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -641,7 +685,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     const bool use_graph = ctx->graphs && !ctx->prof_on;
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->tc_fuse << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
@@ -839,7 +883,7 @@ void hps_destroy(hps_ctx* ctx)
     cudaDeviceSynchronize();
     clear_graphs(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
-    for (auto& kv : ctx->geoms) { cudaFree(kv.second.dD); cudaFree(kv.second.dD2); }
+    for (auto& kv : ctx->geoms) { cudaFree(kv.second.dD); cudaFree(kv.second.dD2); cudaFree(kv.second.dDF); }
     if (ctx->d_iters) cudaFree(ctx->d_iters);
     if (ctx->d_relcorr) cudaFree(ctx->d_relcorr);
     if (ctx->d_kappa) cudaFree(ctx->d_kappa);
@@ -894,6 +938,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
     case HPS_OPT_TC_FUSE:
         if (!(value == -1 || value == 0 || value == 1)) return HPS_EINVAL;
         ctx->tc_fuse = (int)value;
+        return HPS_OK;
+    case HPS_OPT_RESIDUAL_DF:
+        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        ctx->res_df = (int)value;
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;

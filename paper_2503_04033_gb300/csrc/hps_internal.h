@@ -29,7 +29,19 @@ struct Geometry {
     double h[3] = {0, 0, 0};
     double* dD = nullptr;
     double* dD2 = nullptr;
+    float* dDF = nullptr;   // double-float line tables of the first correction's residual, [3][df_tab_f4(q)] float4
 };
+
+// float4 entries of one axis's double-float line table: the (E, O) pairs of
+// the even/odd split [h][h], for odd q the middle column, middle row and
+// diagonal (2h + 1 float2, padded to h + 1 float4), then the two boundary
+// couplings D2[i][0], D2[i][p-1] of each interior row [q]; every value as a
+// (hi, lo) float pair.
+inline int df_tab_f4(int q)
+{
+    const int h = q / 2;
+    return h * h + ((q & 1) ? h + 1 : 0) + q;
+}
 
 // Batched O = src + alpha * A * B over boxes (blockIdx.z), all row-major.
 template <typename T>
@@ -65,7 +77,7 @@ struct Plan {
     // per-box byte sizes of the workspace pieces
     size_t bM = 0, bF = 0, bB = 0, bW = 0, bG = 0, bP = 0, bX = 0, bFp = 0, bBp = 0, bGp = 0;
     size_t bInv = 0, bGp2 = 0, bW2 = 0;   // tensor-core solves: inverse permutations, second G and W buffers
-    size_t bKB = 0;                       // refinement: kappa^2 b at the interior nodes
+    size_t bKB = 0;                       // refinement: kappa^2 b at the interior nodes (FP64 and split)
     size_t per_box = 0;
 };
 
@@ -113,7 +125,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     P.bG = P.bW;
     P.bP = align_up((size_t)P.perm_elems * sizeof(int), A);
     P.bX = need_x ? align_up((size_t)n * r * sizeof(double), A) : 0;
-    P.bKB = need_x ? align_up((size_t)n * sizeof(double), A) : 0;
+    P.bKB = need_x ? align_up((size_t)n * (sizeof(double) + 2 * sizeof(float)), A) : 0;
     if (P.tc) {
         // split (hi, lo) K-major copies of F, B and G for the tensor-core products
         // (3 x TF32: two FP32 planes; 3 x BF16: three 2-byte planes)
@@ -139,6 +151,7 @@ struct Work {
     int* inv;
     float *Gp2, *W2;
     double* kb;
+    float2* kbs;   // kappa^2 b as (hi, lo) float pairs, [nbox][n] after kb's [nbox][n]
     double* norms;
     int* skip;
     long long sM, sF, sB, sG, sP, sX, sFp, sBp, sGp;
@@ -164,6 +177,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
     w.Gp2 = P.bGp2 ? reinterpret_cast<float*>(take(P.bGp2)) : nullptr;
     w.W2 = P.bW2 ? reinterpret_cast<float*>(take(P.bW2)) : nullptr;
     w.kb = P.bKB ? reinterpret_cast<double*>(take(P.bKB)) : nullptr;
+    w.kbs = w.kb ? reinterpret_cast<float2*>(w.kb + (size_t)nbox * P.n) : nullptr;
     w.norms = reinterpret_cast<double*>(take(align_up(2 * sizeof(double), 16)));
     w.skip = reinterpret_cast<int*>(take(align_up(sizeof(int), 16)));
     w.sM = (long long)(P.bM / P.elt);
@@ -185,7 +199,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
 // Kernel classes timed by the optional event profiler (HPS_OPT_PROFILE).
 enum KernelClass {
     KC_BUILD = 0, KC_PANEL, KC_UPDATE_CUDACORE, KC_UPDATE_TC, KC_GATHER, KC_RESIDUAL, KC_REFINE, KC_DN,
-    KC_UPDATE_TC_REFINE, KC_PACK, KC_COUNT
+    KC_UPDATE_TC_REFINE, KC_PACK, KC_RESIDUAL_DF, KC_COUNT
 };
 
 // When profiling is on for the calling thread, prof_begin/prof_end bracket a
@@ -229,14 +243,21 @@ void launch_residual(const Geometry& g, double kappa, const double* kappa_box, i
                      const double* kb = nullptr);
 void selftest_conversions(long long n, unsigned long long seed, unsigned long long* mism_dev, cudaStream_t st);
 void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
-                    double* kb, cudaStream_t st);
+                    double* kb, float2* kbs, cudaStream_t st);
+
+// Residual of the first solution X0 (FP32, rows of pitch ld, box stride sbx),
+// written over X0 in place as FP32: R = B - A_ii X0 in double-float
+// arithmetic.  Needs g.dDF and the split kappa^2 b (launch_kappa_b).
+void launch_residual_df(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                        float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip,
+                        cudaStream_t st);
 
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
                       double* X, long long ldx, long long sX, double* norms /*[nbox][2]*/,
                       const int* skip, int nbox, cudaStream_t st, bool want_xn = false);
 
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
-                     int* iters, double* relcorr, int* status, cudaStream_t st);
+                     int* iters, double* relcorr, int* status, cudaStream_t st, bool hold = false);
 
 void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,
                           const double* v, double* out, int nbox, cudaStream_t st);

@@ -895,6 +895,213 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
     }
 }
 
+// ------------------------------------------- double-float first residual
+// The first correction starts from the FP32 solution X0, whose error (about
+// the LU's precision times the conditioning) leaves room for a residual less
+// accurate than FP64: with about 2^-46 relative to sum |terms| it adds an
+// error near cond(A_ii) 2^-46 to X1, far below X0's.  That residual runs on
+// the FP32 pipes as double-float ("hi + lo" float pairs): each X0 entry is
+// exactly one float, a line's even/odd butterfly is exact (TwoSum), the
+// products take their leading part exactly (TwoProduct by FMA) and sums carry
+// their rounding error (TwoSum, Knuth).  The _rn intrinsics keep the compiler
+// from contracting or reassociating these steps.
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (h, l) = (ah + al)(bh + bl), al bl dropped (2^-48 relative)
+__device__ __forceinline__ void df_mul(float& h, float& l, float ah, float al, float bh, float bl)
+{
+    h = __fmul_rn(ah, bh);
+    l = __fmaf_rn(ah, bh, -h);
+    l = __fmaf_rn(ah, bl, l);
+    l = __fmaf_rn(al, bh, l);
+}
+// (h, l) += (ah + al)(bh + bl)
+__device__ __forceinline__ void df_mac(float& h, float& l, float ah, float al, float bh, float bl)
+{
+    float p, e, s, c;
+    df_mul(p, e, ah, al, bh, bl);
+    two_sum(h, p, s, c);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(c, e));
+}
+// (h, l) += (ah + al) b for a float b
+__device__ __forceinline__ void df_mac1(float& h, float& l, float ah, float al, float b)
+{
+    const float p = __fmul_rn(ah, b);
+    float e = __fmaf_rn(ah, b, -p);
+    e = __fmaf_rn(al, b, e);
+    float s, c;
+    two_sum(h, p, s, c);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(c, e));
+}
+// (h, l) += (bh, bl)
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl)
+{
+    float s, c;
+    two_sum(h, bh, s, c);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(c, bl));
+}
+__device__ __forceinline__ float4 lds_f32x4(const float4* p)
+{
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 lds_f32x2(const float2* p)
+{
+    float2 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+
+template <int Q>
+__host__ __device__ constexpr int df_tab_q() { return (Q / 2) * (Q / 2) + ((Q & 1) ? Q / 2 + 1 : 0) + Q; }
+
+// eo_line in double-float: one line of FP32 values through the split tables
+// (E, O as (hi, lo) pairs); emit(i, hi, lo).
+template <int Q, class Emit>
+__device__ __forceinline__ void eo_line_df(const float* __restrict__ src, int stride, const float4* tab, Emit&& emit)
+{
+    constexpr int H = Q / 2;
+    float x[Q], y[Q];   // after the butterfly: (x, y)[l] = e_l and (x, y)[Q-1-l] = o_l, exactly
+#pragma unroll
+    for (int l = 0; l < Q; ++l) x[l] = src[l * stride];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+        const float a = x[l], z = x[Q - 1 - l];
+        two_sum(a, z, x[l], y[l]);
+        two_sum(a, -z, x[Q - 1 - l], y[Q - 1 - l]);
+    }
+    const float2* t2 = reinterpret_cast<const float2*>(tab + H * H);   // odd q: middle column, row, diagonal
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        float4 t = lds_f32x4(tab + i * H);
+        float seh, sel, soh, sol;
+        df_mul(seh, sel, t.x, t.y, x[0], y[0]);
+        df_mul(soh, sol, t.z, t.w, x[Q - 1], y[Q - 1]);
+#pragma unroll
+        for (int l = 1; l < H; ++l) {
+            t = lds_f32x4(tab + i * H + l);
+            df_mac(seh, sel, t.x, t.y, x[l], y[l]);
+            df_mac(soh, sol, t.z, t.w, x[Q - 1 - l], y[Q - 1 - l]);
+        }
+        if constexpr ((Q & 1) != 0) {
+            const float2 mc = lds_f32x2(t2 + i);
+            df_mac1(seh, sel, mc.x, mc.y, x[H]);
+        }
+        float ph = seh, pl = sel;
+        df_add(ph, pl, soh, sol);
+        emit(i, ph, pl);
+        df_add(seh, sel, -soh, -sol);
+        emit(Q - 1 - i, seh, sel);
+    }
+    if constexpr ((Q & 1) != 0) {
+        const float2 dg = lds_f32x2(t2 + 2 * H);
+        float smh = __fmul_rn(dg.x, x[H]), sml = __fmaf_rn(dg.x, x[H], -smh);
+        sml = __fmaf_rn(dg.y, x[H], sml);
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            const float2 em = lds_f32x2(t2 + H + l);
+            df_mac(smh, sml, em.x, em.y, x[l], y[l]);
+        }
+        emit(H, smh, sml);
+    }
+}
+
+// R = B - A_ii X0 for the FP32 first solution X0, in double-float, written
+// over X0 (each CTA reads its whole column before it writes).  Same passes
+// and CTA shape as k_residual; DTN right-hand sides are added in
+// double-float, LOAD and TRACE ones in FP64 at the end.
+template <int Q>
+__global__ void __launch_bounds__(res_threads<Q>(), res_min_blocks<Q>())
+k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restrict__ kbs, int rhs_kind,
+              const double* __restrict__ rhs, long long s_rhs, float* X0R, long long ld, long long sbx,
+              const int* skip)
+{
+    constexpr int TF = df_tab_q<Q>(), q = Q, qq = Q * Q;
+    constexpr int BO = TF - Q;   // boundary couplings within an axis table
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int box = blockIdx.y;
+    if (skip && skip[box]) return;
+    const int cw = blockIdx.x;
+    float4* tab = reinterpret_cast<float4*>(smem_raw);       // [3][TF]
+    float2* Ac = reinterpret_cast<float2*>(tab + 3 * TF);   // [n]
+    float* Xs = reinterpret_cast<float*>(Ac + n);           // [n]
+    float* col = X0R + box * sbx + cw;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = col[(long long)r * ld];
+    for (int idx = threadIdx.x; idx < 3 * TF; idx += blockDim.x) tab[idx] = DF[idx];
+    __syncthreads();
+    const int ln = threadIdx.x;
+    if (ln < qq) {
+        const int base = ln * q;
+        eo_line_df<Q>(Xs + base, 1, tab, [&](int i, float h, float l) { Ac[base + i] = make_float2(h, l); });
+    }
+    __syncthreads();
+    if (ln < qq) {
+        const int base = ln % q + qq * (ln / q);
+        eo_line_df<Q>(Xs + base, q, tab + TF, [&](int j, float h, float l) {
+            float2 a = Ac[base + q * j];
+            df_add(a.x, a.y, h, l);
+            Ac[base + q * j] = a;
+        });
+    }
+    __syncthreads();
+    if (ln < qq) {
+        const int i = ln % q + 1, j = ln / q + 1;
+        int cg = cw, kind = rhs_kind;
+        if (kind == RHS_DTN_LOAD) {
+            if (cg < 6 * qq) kind = RHS_DTN;
+            else { kind = RHS_LOAD; cg -= 6 * qq; }
+        }
+        const float2* kbb = kbs + (long long)box * n;
+        eo_line_df<Q>(Xs + ln, qq, tab + 2 * TF, [&](int k0, float h, float l) {
+            const int k = k0 + 1, r = ln + qq * k0;
+            float2 a = Ac[r];
+            df_add(a.x, a.y, h, l);
+            const float2 kk = kbb[r];
+            df_mac1(a.x, a.y, kk.x, kk.y, Xs[r]);
+            float out;
+            if (kind == RHS_DTN) {   // -A_ib e_f: D2[.][0] or D2[.][p-1] next to face node f
+                const int f = cg / qq, s2 = cg % qq, u = s2 % q + 1, v = s2 / q + 1;
+                const int axis = f >> 1;
+                const bool hit = (axis == 0 && j == u && k == v) || (axis == 1 && i == u && k == v) ||
+                                 (axis == 2 && i == u && j == v);
+                if (hit) {
+                    const int row = axis == 0 ? i : (axis == 1 ? j : k);
+                    const float4 c = tab[axis * TF + BO + row - 1];
+                    if (f & 1) df_add(a.x, a.y, c.z, c.w);
+                    else df_add(a.x, a.y, c.x, c.y);
+                }
+                out = __fadd_rn(a.x, a.y);
+            } else {
+                double res = f2d(a.x) + f2d(a.y);
+                const int gi = i + p * j + p * p * k;
+                if (kind == RHS_LOAD) {
+                    res += rhs[box * s_rhs + (long long)cg * p * p * p + gi];
+                } else {
+                    const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
+                    const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
+                    const float4 cx = tab[BO + i - 1], cy = tab[TF + BO + j - 1], cz = tab[2 * TF + BO + k - 1];
+                    res += (f2d(cx.x) + f2d(cx.y)) * ub[sx] + (f2d(cx.z) + f2d(cx.w)) * ub[qq + sx] +
+                           (f2d(cy.x) + f2d(cy.y)) * ub[2 * qq + sy] + (f2d(cy.z) + f2d(cy.w)) * ub[3 * qq + sy] +
+                           (f2d(cz.x) + f2d(cz.y)) * ub[4 * qq + sz] + (f2d(cz.z) + f2d(cz.w)) * ub[5 * qq + sz];
+                }
+                out = d2f_rn(res);
+            }
+            col[(long long)r * ld] = out;
+        });
+    }
+}
+
 // X += D (the FP32 correction) in FP64.  ||D||^2 per box goes to norms[2 box]
 // (FP32 partial sums, as for ||X|| in k_extract); with want_xn also ||X||^2
 // after the update, in FP64, to norms[2 box + 1].
@@ -931,7 +1138,7 @@ k_ir_update(const float* __restrict__ D, long long ldd, long long sD, int n, int
 // has stopped shrinking (less than a halving) while already below stag_tol,
 // i.e. X sits at the FP64 residual's noise floor.
 __global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol, int last, int* skip, int* iters,
-                           double* relcorr, int* status)
+                           double* relcorr, int* status, int hold)
 {
     const int box = blockIdx.x * blockDim.x + threadIdx.x;
     if (box >= nbox || skip[box]) return;
@@ -946,6 +1153,7 @@ __global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol,
         const double rho = rel / prev;
         done = done || rel * fmin(1.0, 10.0 * rho) <= tol || (rel <= stag_tol && rho > 0.5);
     }
+    if (hold) done = false;   // this correction came from the double-float residual: one more in FP64
     if (done) skip[box] = 1;
     else if (last && status[box] == 0) status[box] = isfinite(rel) ? HPS_ENOCONV : HPS_EINVAL;
 }
@@ -1213,14 +1421,19 @@ void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols
 // kb[box][r] = kappa^2 b at interior node r (the residual's diagonal term,
 // the same for every column of a box).
 __global__ void k_kappa_b(int p, int n, const double* __restrict__ b, long long sb, double kappa2,
-                          const double* __restrict__ kappa_box, double* __restrict__ kb)
+                          const double* __restrict__ kappa_box, double* __restrict__ kb, float2* __restrict__ kbs)
 {
     const int box = blockIdx.y;
     const int q = p - 2, qq = q * q, pp = p * p;
     const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
-        kb[(long long)box * n + r] = k2 * b[box * sb + i + p * j + pp * k];
+        const double v = k2 * b[box * sb + i + p * j + pp * k];
+        kb[(long long)box * n + r] = v;
+        if (kbs) {
+            const float hi = __double2float_rn(v);
+            kbs[(long long)box * n + r] = make_float2(hi, __double2float_rn(v - (double)hi));
+        }
     }
 }
 
@@ -1260,10 +1473,10 @@ void selftest_conversions(long long n, unsigned long long seed, unsigned long lo
 }
 
 void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
-                    double* kb, cudaStream_t st)
+                    double* kb, float2* kbs, cudaStream_t st)
 {
     dim3 grd((unsigned)((g.n + 255) / 256), (unsigned)nbox);
-    k_kappa_b<<<grd, 256, 0, st>>>(g.p, g.n, b, sb, kappa * kappa, kappa_box, kb);
+    k_kappa_b<<<grd, 256, 0, st>>>(g.p, g.n, b, sb, kappa * kappa, kappa_box, kb, kbs);
 }
 
 namespace {
@@ -1312,6 +1525,45 @@ void launch_residual(const Geometry& g, double kappa, const double* kappa_box, i
 #undef HPS_RES_CASE
 }
 
+namespace {
+template <int Q>
+void residual_df_q(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                   float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st)
+{
+    const size_t smem = (size_t)3 * df_tab_q<Q>() * sizeof(float4) + (size_t)g.n * (sizeof(float2) + sizeof(float));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_residual_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    dim3 grd((unsigned)nrhs, (unsigned)nbox);
+    prof_begin(KC_RESIDUAL_DF, st);
+    k_residual_df<Q><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, reinterpret_cast<const float4*>(g.dDF), kbs,
+                                                           rhs_kind, rhs_src, s_rhs, X0R, ld, sbx, skip);
+    // work counted as for the FP64 residual (its operations per entry); bytes:
+    // X0 and R in FP32, the split kappa^2 b
+    const double per = 3.0 * (2.0 + 2.0 * (Q / 2) + ((Q & 1) ? 2.0 : 0.0)) + 3.0;
+    prof_end(KC_RESIDUAL_DF, st, (double)nbox * g.n * (double)nrhs * per, (double)nbox * g.n * (double)nrhs * 8.0);
+}
+}  // namespace
+
+void launch_residual_df(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                        float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st)
+{
+#define HPS_RES_CASE(QV)                                                                           \
+    case QV:                                                                                       \
+        residual_df_q<QV>(g, nbox, rhs_kind, nrhs, rhs_src, s_rhs, X0R, ld, sbx, kbs, skip, st); \
+        break;
+    switch (g.q) {
+        HPS_RES_CASE(1) HPS_RES_CASE(2) HPS_RES_CASE(3) HPS_RES_CASE(4) HPS_RES_CASE(5) HPS_RES_CASE(6)
+        HPS_RES_CASE(7) HPS_RES_CASE(8) HPS_RES_CASE(9) HPS_RES_CASE(10) HPS_RES_CASE(11) HPS_RES_CASE(12)
+        HPS_RES_CASE(13) HPS_RES_CASE(14) HPS_RES_CASE(15) HPS_RES_CASE(16) HPS_RES_CASE(17) HPS_RES_CASE(18)
+        HPS_RES_CASE(19) HPS_RES_CASE(20) HPS_RES_CASE(21) HPS_RES_CASE(22)
+        default: break;
+    }
+#undef HPS_RES_CASE
+}
+
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
                       double* X, long long ldx, long long sX, double* norms,
                       const int* skip, int nbox, cudaStream_t st, bool want_xn)
@@ -1323,9 +1575,10 @@ void launch_ir_update(const float* D, long long ldd, long long sD, int n, int nc
 }
 
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
-                     int* iters, double* relcorr, int* status, cudaStream_t st)
+                     int* iters, double* relcorr, int* status, cudaStream_t st, bool hold)
 {
-    k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, 1e-11, last, skip, iters, relcorr, status);
+    k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, 1e-11, last, skip, iters, relcorr, status,
+                                                    hold ? 1 : 0);
 }
 
 void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,

@@ -128,6 +128,38 @@ def test_tcgen05_step_pairs_match_single_steps(ctx, p, nbox, block):
         assert rel_fro(T0, To).max() < 1e-10 and rel_fro(S0, So).max() < 1e-10
 
 
+@pytest.mark.parametrize("prec", [H.HPS_FP32_IR, H.HPS_BF16_IR], ids=["fp32ir", "bf16ir"])
+@pytest.mark.parametrize("p,nbox", [(9, 3), (12, 2), (16, 2)])
+def test_double_float_first_residual(ctx, prec, p, nbox):
+    """The first correction's residual in double-float on the FP32 pipes
+    against the FP64 residual, on T and S: the two results within 1e-10 of
+    each other (and of the oracle at p <= 12).  With it every box takes at
+    least two corrections (the double-float one never ends the refinement)
+    and at most one more than with the FP64 residual.  p = 9 has an odd line
+    length (q = 7)."""
+    h = np.array([0.125, 0.2, 0.15])
+    kappa = 18.0
+    lows = _lows(nbox, h, 5 + p)
+    field = hi.fourier_b_field().b
+    b_np = box_b(H.hps_leaf_nodes, p, lows, h, field)
+    res = {}
+    try:
+        for df in (0, 1):
+            H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, df)
+            T, S, st = gpu_dtn(ctx, p, h, kappa, b_np, prec, 1)
+            assert (st == 0).all(), st
+            its, _ = H.hps_last_refinement(ctx, nbox)
+            res[df] = (T, S, its.copy())
+    finally:
+        H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, 1)
+    (T0, S0, i0), (T1, S1, i1) = res[0], res[1]
+    assert rel_fro(T0, T1).max() < 1e-10 and rel_fro(S0, S1).max() < 1e-10
+    assert (i1 >= 2).all() and (i1 <= i0 + 1).all(), (i0, i1)
+    if p <= 12:
+        To, So, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=True)
+        assert rel_fro(T1, To).max() < 1e-10 and rel_fro(S1, So).max() < 1e-10
+
+
 @pytest.mark.parametrize("prec,tc,tol", PRECS)
 @pytest.mark.parametrize("block", [32, 64])
 def test_dtn_parity_block_sizes(ctx, prec, tc, tol, block):
