@@ -48,6 +48,17 @@ METRIC = "leaf DtN builds/s at p=16 (FP32 tcgen05 LU + FP64 refinement, rel err 
 # TF32 dense tensor peak derived from the measured BF16 peak and NVIDIA's
 # nominal TF32:BF16 ratio (1.1 : 2.25 PFLOP/s dense).
 TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def operand_format(prec, opts):
+    """(name, MMA rate relative to BF16, MMAs per product) of the tensor-core
+    update products for a precision and the --opt settings."""
+    import paper_2503_04033_gb300 as H
+    if prec == H.HPS_BF16_IR:
+        return "3 x BF16", 1.0, 6
+    if float(opts.get("FP16_OPERANDS", 1)) != 0:
+        return "scaled 2 x FP16", 1.0, 3
+    return "3 x TF32", TF32_OVER_BF16, 3
 # FP64 issue peak: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop (1.26 TFLOP/s,
 # the part's nominal 1.25 TFLOP/s FP64).
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12
@@ -56,18 +67,15 @@ FP32_CUDACORE_PEAK_TFLOPS = 152 * 2.070e9 * 128 * 2 / 1e12
 CLASS_BOUND = {
     "update_tcgen05": "tensor", "update_cudacore": "alu", "residual_fp64": "alu", "dn_fp64": "alu",
     "panel": "alu", "build": "hbm", "gather": "hbm", "pack": "hbm", "refine_update": "hbm",
-    "update_tcgen05_refine": "tensor",
+    "update_tcgen05_refine": "tensor", "residual_df": "alu",
 }
-# DRAM bytes per launch of the dominant kernel class, from one ncu capture of
-# the factorisation-phase launches on 32 of the workload's boxes, scaled to 512
-# boxes (traffic is proportional to the boxes processed); see
-# profiles/k_tc_update_fourier16_32boxes.md.  Must be re-measured (or set to
-# None) whenever that kernel changes.
-# DRAM bytes per launch of the dominant kernel class from one ncu capture of the
-# factorisation phase at 32 boxes (dram__bytes_read.sum + dram__bytes_write.sum
-# over its 97 launches / 97), scaled to 512 boxes by the box count; see
-# profiles/k_tc_update_fourier16_32boxes.md.
-NCU_TRAFFIC_PER_LAUNCH = {"update_tcgen05": 4.263e9}
+# DRAM bytes per launch of the dominant kernel class, by operand format, from
+# one ncu capture of the factorisation phase at 32 boxes
+# (dram__bytes_read.sum + dram__bytes_write.sum over its 97 launches / 97),
+# scaled to 512 boxes by the box count (traffic is proportional to the boxes
+# processed); see profiles/k_tc_update_fourier16_32boxes.md.  None until
+# measured; must be re-measured (or set to None) whenever that kernel changes.
+NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): 3.444e9, ("update_tcgen05", "3 x TF32"): None}
 # Classes whose launches skip converged boxes: their flop and byte counts are
 # upper bounds, so they are not used for the roofline.
 SKIPPING = ("update_tcgen05_refine", "residual_fp64", "refine_update")
@@ -265,8 +273,8 @@ def run_ours(args):
     ctx = H.hps_create(local, 0)
     if args.ir_tol is not None:
         H.hps_set_option(ctx, H.HPS_OPT_IR_TOL, args.ir_tol)
-    for o in args.opt:
-        name, val = o.split("=")
+    opts = dict(o.split("=") for o in args.opt)
+    for name, val in opts.items():
         H.hps_set_option(ctx, getattr(H, "HPS_OPT_" + name), float(val))
     stream = torch.cuda.current_stream(dev)
     b = torch.from_numpy(b_np).to(dev)
@@ -338,24 +346,27 @@ def run_ours(args):
         sec = d["ms_per_step"] / 1e3
         bound = CLASS_BOUND.get(dom, "hbm")
         if bound == "tensor":
-            # The 3-term TF32 split issues 3 MMAs per product: its useful peak is a third
-            # of the TF32 rate, and its ridge against HBM decides which roof binds.
-            tpeak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+            # A split-operand product issues several MMAs per 2MNK: its useful
+            # peak is the MMA rate of its format over that count, and its ridge
+            # against HBM decides which roof binds.
+            fmt_name, rate, nmma = operand_format(prec, opts)
+            tpeak = peaks["bf16_tflops_sustained"] * rate / nmma
             ai = d["flops"] / max(d["bytes"], 1.0)
-            ridge = tpeak / 3 * 1e12 / (peaks["hbm_gbs"] * 1e9)
+            ridge = tpeak * 1e12 / (peaks["hbm_gbs"] * 1e9)
             if ai < ridge:
                 bound = "hbm"
                 peak = peaks["hbm_gbs"]
                 ach = d["bytes"] / sec / 1e9
                 unit = "GB/s"
-                note = (f"{src} HBM copy bandwidth; arithmetic intensity {ai:.1f} flop/B is below the 3xTF32 ridge "
-                        f"{ridge:.1f} flop/B (TF32 peak {tpeak:.0f} TFLOP/s / 3); tensor view: "
-                        f"{d['flops'] / sec / 1e12:.1f} TFLOP/s algorithmic")
+                note = (f"{src} HBM copy bandwidth; arithmetic intensity {ai:.1f} flop/B is below the {fmt_name} "
+                        f"ridge {ridge:.1f} flop/B ({nmma} MMAs per product at {peaks['bf16_tflops_sustained'] * rate:.0f} "
+                        f"TFLOP/s); tensor view: {d['flops'] / sec / 1e12:.1f} TFLOP/s algorithmic")
             else:
                 peak = tpeak
                 ach = d["flops"] / sec / 1e12
                 unit = "TFLOP/s"
-                note = f"TF32 dense peak = {src} sustained BF16 x 1.1/2.25; achieved counts 2MNK once (3 TF32 MMAs issued)"
+                note = (f"{fmt_name}: {src} sustained BF16 rate x {rate:.3f} / {nmma} MMAs per product; "
+                        f"achieved counts 2MNK once")
         elif bound == "alu":
             fp64 = dom in ("residual_fp64", "dn_fp64") or prec == H.HPS_FP64
             peak = FP64_PEAK_TFLOPS if fp64 else FP32_CUDACORE_PEAK_TFLOPS
@@ -367,21 +378,26 @@ def run_ours(args):
             ach = d["bytes"] / sec / 1e9
             unit = "GB/s"
             note = f"{src} HBM copy bandwidth"
-        traffic = NCU_TRAFFIC_PER_LAUNCH.get(dom) if (nbox == NBOX and prec == H.HPS_FP32_IR) else None
+        traffic = (NCU_TRAFFIC_PER_LAUNCH.get((dom, operand_format(prec, opts)[0]))
+                   if (nbox == NBOX and prec == H.HPS_FP32_IR) else None)
         line["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                             "frac": ach / peak, "traffic": traffic,
                             "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
                             "peak_source": note, "launches_per_step": d["launches"]}
 
-    # ---- the FP64 residual (the largest kernel by time; its launches skip
-    # converged boxes, so its work is counted from the refinement histogram):
+    # ---- the FP64 residual (its launches skip converged boxes, so its work is
+    # counted from the refinement histogram):
     # FP64 pipe instructions per (point, column) of the even/odd line form,
     # 3 (h + 2) + 3 with h = (p - 2) // 2 at even p - 2, against the issue
     # rate of the FP64 pipes (2 per clock per SM at the SM clock sampled).
     if "residual_fp64" in prof and prec != H.HPS_FP64:
         q = P - 2
         per_entry = 3 * (q // 2 + 2) + 3 + (6 if q % 2 else 0)
-        box_its = float(it.sum())                        # residual evaluations per step (every step alike)
+        # FP64 residual evaluations per step (every step alike); with the
+        # double-float first residual (on unless switched off) each box's
+        # first evaluation runs on the FP32 pipes instead
+        df = float(opts.get("RESIDUAL_DF", 1)) != 0 and float(opts.get("IR_MAX_ITERS", 8)) >= 2
+        box_its = float(it.sum()) - (nbox if df else 0)
         instr = box_its * n * m * per_entry
         rms = prof["residual_fp64"]["ms_per_step"]
         sm_mhz = (line.get("clocks") or {}).get("sm_mhz") or 2070.0
@@ -391,6 +407,24 @@ def run_ours(args):
             "peak": peak_ips / 1e9, "unit": "G FP64-pipe instr/s", "frac": instr / (rms / 1e3) / peak_ips,
             "instr_per_entry": per_entry, "box_iterations_per_step": box_its,
             "peak_source": "2 FP64 instructions per clock per SM x SMs x sampled SM clock"}
+    # ---- the double-float first residual (every box, one launch a step):
+    # FP32 operations per (point, column) as written in the kernel: per axis
+    # and output 12 h + 6 (exact butterfly, TwoProduct/TwoSum multiply-adds,
+    # the even/odd recombination), 12 h + 12 at odd q, plus 28 to accumulate
+    # the axes, the kappa^2 b term and round; against 128 FP32 lanes per SM.
+    if "residual_df" in prof:
+        q = P - 2
+        hq = q // 2
+        per_df = 3 * (12 * hq + (12 if q % 2 else 6)) + 28
+        ops = float(nbox) * n * m * per_df
+        rms = prof["residual_df"]["ms_per_step"]
+        sm_mhz = (line.get("clocks") or {}).get("sm_mhz") or 2070.0
+        peak_ops = 128.0 * torch.cuda.get_device_properties(dev).multi_processor_count * sm_mhz * 1e6
+        line["roofline_df_residual"] = {
+            "kernel": "residual_df", "bound": "alu", "achieved": ops / (rms / 1e3) / 1e9,
+            "peak": peak_ops / 1e9, "unit": "G FP32 ops/s", "frac": ops / (rms / 1e3) / peak_ops,
+            "ops_per_entry": per_df,
+            "peak_source": "128 FP32 lanes per SM x SMs x sampled SM clock"}
 
     # ---- plain FP64 GPU path on a sample of the same boxes
     if not args.no_fp64 and prec != H.HPS_FP64 and args.fp64_sample > 0:

@@ -122,6 +122,10 @@ typedef enum {
                                    terms' magnitudes) and that correction never ends the refinement, so every
                                    result still ends on corrections from the FP64 residual; 0: every residual
                                    in FP64 */
+    HPS_OPT_FP16_OPERANDS = 13, /* 1 (default): FP32_IR tensor-core products split each operand into two FP16
+                                   values (hi + lo, 22 bits as with 3 x TF32) under exact power-of-two scales
+                                   of the left operand's K columns and the right operand's columns, which
+                                   halves the operand bytes and doubles the MMA rate; 0: 3 x TF32 */
     HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
 } hps_option;

@@ -90,6 +90,7 @@ struct hps_ctx {
     int lu_pairs = 1;           // 0: no joining of LU steps in pairs on the tcgen05 path
     int tc_fuse = -1;           // -1: fused gathers where they measured faster, 0: never, 1: backward sweeps
     int res_df = 1;             // first correction's residual in double-float on the FP32 pipes
+    int fp16_ops = 1;           // FP32_IR tensor-core products on scaled 2 x FP16 operands (format 2)
     int use_tc = 1;
     int sync = 0;
     int zero_row_box = -1;
@@ -392,10 +393,11 @@ long long job_srhs(const Job& j)
 Plan job_plan(const hps_ctx* ctx, const Job& j, hps_precision prec)
 {
     Plan P = make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64,
-                       ctx->lu_pairs != 0);
+                       ctx->lu_pairs != 0, ctx->fp16_ops != 0);
     P.tma_epi = ctx->tc_epi_cp == 0;
     P.tc_pairs = ctx->tc_pairs != 0;
     if (ctx->tc_fuse >= 0) P.fuse_bwd = P.tc && ctx->tc_fuse != 0;
+    if (P.fmt == 2) P.fuse_bwd = false;   // the fused gather writes unscaled operands
     return P;
 }
 
@@ -685,7 +687,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     const bool use_graph = ctx->graphs && !ctx->prof_on;
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->fp16_ops << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
@@ -855,7 +857,7 @@ size_t hps_workspace_per_box(int p, hps_precision prec)
 {
     if (!valid_p(p)) return 0;
     const int q = p - 2, n = q * q * q, m = 6 * q * q;
-    return make_plan(n, m, prec, 0, true, prec != HPS_FP64).per_box;
+    return make_plan(n, m, prec, 0, true, prec != HPS_FP64, true, true).per_box;
 }
 
 hps_status hps_create(hps_ctx** out, int device, size_t workspace_bytes_max)
@@ -942,6 +944,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
     case HPS_OPT_RESIDUAL_DF:
         if (!(value == 0 || value == 1)) return HPS_EINVAL;
         ctx->res_df = (int)value;
+        return HPS_OK;
+    case HPS_OPT_FP16_OPERANDS:
+        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        ctx->fp16_ops = (int)value;
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;

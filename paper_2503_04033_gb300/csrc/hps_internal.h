@@ -68,7 +68,7 @@ struct Plan {
     bool tc_pairs = false;           // tcgen05 products by CTA pairs sharing the right operand
     bool step_pairs = false;         // tcgen05 path: consecutive LU steps joined in pairs
     int KG = 0;                      // K extent of the gathered right operand (NB, or 2 NB with pairs)
-    int fmt = 0;                     // tcgen05 operand format: 0 = 3 x TF32, 1 = 3 x BF16
+    int fmt = 0;                     // tcgen05 operand format: 0 = 3 x TF32, 1 = 3 x BF16, 2 = scaled 2 x FP16
     bool fuse_fwd = false;           // forward solves: next G written by the epilogue (scattered stores)
     bool fuse_bwd = false;           // backward solves: next G written by the epilogue
     std::vector<int> k0, nbs;
@@ -78,10 +78,12 @@ struct Plan {
     size_t bM = 0, bF = 0, bB = 0, bW = 0, bG = 0, bP = 0, bX = 0, bFp = 0, bBp = 0, bGp = 0;
     size_t bInv = 0, bGp2 = 0, bW2 = 0;   // tensor-core solves: inverse permutations, second G and W buffers
     size_t bKB = 0;                       // refinement: kappa^2 b at the interior nodes (FP64 and split)
+    size_t bRC = 0, bIT = 0;              // format 2: K scales of the F and B packs, column scales of a G
     size_t per_box = 0;
 };
 
-inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x, bool step_pairs = true)
+inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x, bool step_pairs = true,
+                      bool fp16_ops = false)
 {
     Plan P;
     P.n = n;
@@ -89,7 +91,7 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     const bool fp64 = (prec == HPS_FP64);
     P.elt = fp64 ? 8 : 4;
     P.tc = !fp64 && use_tc;
-    P.fmt = (P.tc && prec == HPS_BF16_IR) ? 1 : 0;
+    P.fmt = !P.tc ? 0 : (prec == HPS_BF16_IR ? 1 : (fp16_ops ? 2 : 0));
     P.fuse_bwd = P.tc && P.fmt == 0;
     int NB = nb_opt > 0 ? nb_opt : (fp64 ? 64 : 128);
     if (fp64 && NB > 64) NB = 64;
@@ -129,15 +131,20 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
     if (P.tc) {
         // split (hi, lo) K-major copies of F, B and G for the tensor-core products
         // (3 x TF32: two FP32 planes; 3 x BF16: three 2-byte planes)
-        const size_t pk = P.fmt ? 3 * 2 : 2 * sizeof(float);
+        const size_t pk = P.fmt == 1 ? 3 * 2 : (P.fmt == 2 ? 2 * 2 : 2 * sizeof(float));
         P.bFp = align_up((size_t)P.fw_elems * pk, A);
         P.bBp = align_up((size_t)P.bw_elems * pk, A);
         P.bGp = align_up((size_t)P.ldm * P.KG * pk, A);
         P.bInv = P.fuse_fwd ? P.bP : 0;
         P.bGp2 = P.bGp;
         P.bW2 = P.bW;
+        if (P.fmt == 2) {
+            P.bRC = align_up((size_t)P.nsteps * NB * sizeof(float), A);
+            P.bIT = align_up((size_t)(P.ldm + 64) * sizeof(float), A);
+        }
     }
-    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + P.bInv + P.bGp2 + P.bW2 + P.bKB + 64;
+    P.per_box = P.bM + P.bF + P.bB + P.bW + P.bG + P.bP + P.bX + P.bFp + P.bBp + P.bGp + P.bInv + P.bGp2 + P.bW2 + P.bKB +
+                2 * P.bRC + 2 * P.bIT + 64;
     return P;
 }
 
@@ -152,9 +159,11 @@ struct Work {
     float *Gp2, *W2;
     double* kb;
     float2* kbs;   // kappa^2 b as (hi, lo) float pairs, [nbox][n] after kb's [nbox][n]
+    float *rcF, *rcB;   // format 2: 1 / (power-of-two scale) of each K column of F_s, B_s ([step][NB] per box)
+    float *it1, *it2;   // format 2: 1 / (power-of-two scale) of each column of the G in Gp, Gp2
     double* norms;
     int* skip;
-    long long sM, sF, sB, sG, sP, sX, sFp, sBp, sGp;
+    long long sM, sF, sB, sG, sP, sX, sFp, sBp, sGp, sRC, sIT;
 };
 
 template <typename T>
@@ -178,6 +187,12 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
     w.W2 = P.bW2 ? reinterpret_cast<float*>(take(P.bW2)) : nullptr;
     w.kb = P.bKB ? reinterpret_cast<double*>(take(P.bKB)) : nullptr;
     w.kbs = w.kb ? reinterpret_cast<float2*>(w.kb + (size_t)nbox * P.n) : nullptr;
+    w.rcF = P.bRC ? reinterpret_cast<float*>(take(P.bRC)) : nullptr;
+    w.rcB = P.bRC ? reinterpret_cast<float*>(take(P.bRC)) : nullptr;
+    w.it1 = P.bIT ? reinterpret_cast<float*>(take(P.bIT)) : nullptr;
+    w.it2 = P.bIT ? reinterpret_cast<float*>(take(P.bIT)) : nullptr;
+    w.sRC = (long long)(P.bRC / sizeof(float));
+    w.sIT = (long long)(P.bIT / sizeof(float));
     w.norms = reinterpret_cast<double*>(take(align_up(2 * sizeof(double), 16)));
     w.skip = reinterpret_cast<int*>(take(align_up(sizeof(int), 16)));
     w.sM = (long long)(P.bM / P.elt);

@@ -982,7 +982,9 @@ __device__ __forceinline__ void eo_line_df(const float* __restrict__ src, int st
         two_sum(a, -z, x[Q - 1 - l], y[Q - 1 - l]);
     }
     const float2* t2 = reinterpret_cast<const float2*>(tab + H * H);   // odd q: middle column, row, diagonal
-#pragma unroll
+    // The pair loop stays rolled (x and y are indexed by l only): unrolled, the
+    // three passes outgrow the instruction cache.
+#pragma unroll 1
     for (int i = 0; i < H; ++i) {
         float4 t = lds_f32x4(tab + i * H);
         float seh, sel, soh, sol;
@@ -1035,9 +1037,13 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
     const int cw = blockIdx.x;
     float4* tab = reinterpret_cast<float4*>(smem_raw);       // [3][TF]
     float2* Ac = reinterpret_cast<float2*>(tab + 3 * TF);   // [n]
-    float* Xs = reinterpret_cast<float*>(Ac + n);           // [n]
+    float2* Ks = Ac + n;                                     // [n] kappa^2 b
+    float* Xs = reinterpret_cast<float*>(Ks + n);           // [n]
     float* col = X0R + box * sbx + cw;
+    const float2* kbb = kbs + (long long)box * n;
+#pragma unroll 4
     for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = col[(long long)r * ld];
+    for (int r = threadIdx.x; r < n; r += blockDim.x) Ks[r] = kbb[r];
     for (int idx = threadIdx.x; idx < 3 * TF; idx += blockDim.x) tab[idx] = DF[idx];
     __syncthreads();
     const int ln = threadIdx.x;
@@ -1062,12 +1068,11 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
             if (cg < 6 * qq) kind = RHS_DTN;
             else { kind = RHS_LOAD; cg -= 6 * qq; }
         }
-        const float2* kbb = kbs + (long long)box * n;
         eo_line_df<Q>(Xs + ln, qq, tab + 2 * TF, [&](int k0, float h, float l) {
             const int k = k0 + 1, r = ln + qq * k0;
             float2 a = Ac[r];
             df_add(a.x, a.y, h, l);
-            const float2 kk = kbb[r];
+            const float2 kk = Ks[r];
             df_mac1(a.x, a.y, kk.x, kk.y, Xs[r]);
             float out;
             if (kind == RHS_DTN) {   // -A_ib e_f: D2[.][0] or D2[.][p-1] next to face node f
@@ -1530,7 +1535,7 @@ template <int Q>
 void residual_df_q(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                    float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st)
 {
-    const size_t smem = (size_t)3 * df_tab_q<Q>() * sizeof(float4) + (size_t)g.n * (sizeof(float2) + sizeof(float));
+    const size_t smem = (size_t)3 * df_tab_q<Q>() * sizeof(float4) + (size_t)g.n * (2 * sizeof(float2) + sizeof(float));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_residual_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

@@ -23,6 +23,7 @@
 // HPS_ETIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <cstdio>
@@ -47,8 +48,17 @@ constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 
 // products hi*hi + hi*lo + lo*hi).  FMT 1: x = hi + mid + lo, three BF16
 // roundings of the successive remainders (3 planes, kind::f16 with BF16 A
 // and B, products hi*hi + hi*mid + mid*hi + hi*lo + mid*mid + lo*hi).  Both
-// drop only terms below FP32 rounding and accumulate in FP32.  A K chunk is
-// one 64-byte row: 16 TF32 or 32 BF16 values.
+// drop only terms below FP32 rounding and accumulate in FP32.  FMT 2: x = hi
+// + lo, two FP16 roundings (2 planes, kind::f16 with FP16 A and B, products
+// hi*hi + hi*lo + lo*hi): the same 22 bits as FMT 0 in half the bytes, with
+// twice the MMA rate.  FP16's range is kept by power-of-two scales: each K
+// column of the left operand is scaled to a maximum below 2^15 and the
+// matching row of the right operand by the inverse (the product is
+// unchanged), then each column of the right operand is scaled to a maximum
+// below 2^15 and the epilogue multiplies the accumulator column by the
+// inverse.  Values far below their column's maximum lose bits only at 2^-39
+// of that maximum.  A K chunk is one 64-byte row: 16 TF32 or 32 BF16 / FP16
+// values.
 template <int FMT>
 struct TcFmt;
 template <>
@@ -59,12 +69,17 @@ template <>
 struct TcFmt<1> {
     static constexpr int NPL = 3, EB = 2, KPC = 32, BN = 128;
 };
+template <>
+struct TcFmt<2> {
+    static constexpr int NPL = 2, EB = 2, KPC = 32, BN = 256;
+};
 template <int FMT>
 __host__ __device__ constexpr uint32_t b_tile() { return (uint32_t)TcFmt<FMT>::BN * ROWB; }
 template <int FMT>
 __host__ __device__ constexpr uint32_t stage_bytes() { return (uint32_t)TcFmt<FMT>::NPL * (A_TILE + b_tile<FMT>()); }
 constexpr uint32_t STAGE_BYTES = 48 * 1024;
-static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES, "one shared-memory layout");
+static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES && stage_bytes<2>() == STAGE_BYTES,
+              "one shared-memory layout");
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
 constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
 constexpr uint32_t EPI_FLOATS = TBUF_FLOATS * (1 + TC_PRE) + 64;   // transpose + source ring + row pointers
@@ -92,6 +107,7 @@ struct TcArgs {
     const float* W; long long ldw, sW;
     const int* skip;
     int* status;
+    const float* invt; long long sInvt;   // format 2: 1 / scale of each column of the right operand
     // fused gather of the next product (TMA epilogue only): output row r goes
     // to the next split right operand nG at K index ninv[r - ng_off] (or
     // r - ng_off without ninv) when that lies in [0, ng_len) and is >= 0, and
@@ -356,6 +372,12 @@ __host__ __device__ constexpr uint32_t bf16_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, both K-major, N, M.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N, M.
 __host__ __device__ constexpr uint32_t tf32_idesc(int M, int N)
 {
@@ -371,7 +393,8 @@ __device__ __forceinline__ float to_tf32(float x)
 
 // The split pieces of x in operand format FMT, written to plane pl of a
 // buffer of FP32 containers (FMT 0: tf32(x), tf32(x - hi)) or BF16 bits
-// (FMT 1: successive BF16 roundings; every remainder is exact in FP32).
+// (FMT 1: successive BF16 roundings; FMT 2: FP16 roundings of x and x - hi,
+// x already scaled; every remainder is exact in FP32).
 template <int FMT>
 __device__ __forceinline__ void split_store(void* dst, long long idx, long long plane, float x)
 {
@@ -380,6 +403,11 @@ __device__ __forceinline__ void split_store(void* dst, long long idx, long long 
         const float hi = to_tf32(x);
         d[idx] = hi;
         d[plane + idx] = to_tf32(x - hi);
+    } else if constexpr (FMT == 2) {
+        __half* d = static_cast<__half*>(dst);
+        const __half h = __float2half_rn(x);
+        d[idx] = h;
+        d[plane + idx] = __float2half_rn(x - __half2float(h));
     } else {
         unsigned short* d = static_cast<unsigned short*>(dst);
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -390,6 +418,24 @@ __device__ __forceinline__ void split_store(void* dst, long long idx, long long 
         d[plane + idx] = __bfloat16_as_ushort(m);
         d[2 * plane + idx] = __bfloat16_as_ushort(l);
     }
+}
+
+// Format 2: the accumulator chunk's 32 columns times 1 / their right-operand
+// scale.  Lane l holds the scales of columns l, l + 32, ... of the tile in
+// its8 (loaded once per tile); each chunk takes its8[0] by shuffles and
+// shifts the rest down.
+__device__ __forceinline__ void scale_chunk(uint32_t (&v)[32], float (&its8)[8])
+{
+    const float sl = its8[0];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __float_as_uint(__uint_as_float(v[c]) * __shfl_sync(0xffffffffu, sl, c));
+#pragma unroll
+    for (int c8 = 0; c8 < 7; ++c8) its8[c8] = its8[c8 + 1];
+}
+__device__ __forceinline__ void load_tile_scales(float (&its8)[8], const float* ib, int nch, int lane)
+{
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) its8[c8] = c8 < nch ? __ldg(ib + 32 * c8 + lane) : 1.0f;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
@@ -511,7 +557,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = FMT == 0 ? tf32_idesc(TC_BM, BN) : bf16_idesc(TC_BM, BN);
+            constexpr uint32_t idesc =
+                FMT == 0 ? tf32_idesc(TC_BM, BN) : (FMT == 1 ? bf16_idesc(TC_BM, BN) : f16_idesc(TC_BM, BN));
             uint32_t g = 0, j = 0;
             bool ok = true;
             for (int u = sc.u0; u < sc.units && ok; u += sc.ustep) {
@@ -540,6 +587,10 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             mma_tf32(d, ad[0] + o, bd[0] + o, idesc, acc0);
                             mma_tf32(d, ad[0] + o, bd[1] + o, idesc, 1);
                             mma_tf32(d, ad[1] + o, bd[0] + o, idesc, 1);
+                        } else if constexpr (FMT == 2) {
+                            mma_bf16(d, ad[1] + o, bd[0] + o, idesc, acc0);
+                            mma_bf16(d, ad[0] + o, bd[1] + o, idesc, 1);
+                            mma_bf16(d, ad[0] + o, bd[0] + o, idesc, 1);
                         } else {
                             // smallest terms first
                             mma_bf16(d, ad[2] + o, bd[0] + o, idesc, acc0);
@@ -603,6 +654,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int box, m0, n0, nch;
             geom(t, box, m0, n0, nch);
             const int b = j & 1;
+            float its8[8];   // format 2 column scales (the loads overlap the wait)
+            if constexpr (FMT == 2) load_tile_scales(its8, a.invt + box * a.sInvt + n0, nch, lane);
             if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
@@ -619,7 +672,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             void* nGb = nullptr;
             if (ngi >= 0)
                 nGb = FMT == 0 ? (void*)(static_cast<float*>(a.nG) + box * a.nsG)
-                               : (void*)(static_cast<unsigned short*>(a.nG) + box * a.nsG);
+                               : (void*)(static_cast<unsigned short*>(a.nG) + box * a.nsG);   // not with FMT 2
             int srck = 0;
             const float* wrow = nullptr;
             if (myr < a.M) {
@@ -666,21 +719,27 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 float4* rowp = reinterpret_cast<float4*>(ring_p + buf * TE_CHUNK + lane * 128);
                 const int cb = n0 + cc * 32;
+                if constexpr (FMT == 2) scale_chunk(v, its8);
+                // all eight source reads first, then the eight results
+                float4 sv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    sv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (srck == 1) {
+                        sv[u] = rowp[u ^ (lane & 7)];
+                    } else if (srck == 2) {
+                        const int c = cb + 4 * u;
+                        sv[u].x = c < a.N ? wrow[c] : 0.f;
+                        sv[u].y = c + 1 < a.N ? wrow[c + 1] : 0.f;
+                        sv[u].z = c + 2 < a.N ? wrow[c + 2] : 0.f;
+                        sv[u].w = c + 3 < a.N ? wrow[c + 3] : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     float4* p4 = rowp + (u ^ (lane & 7));
-                    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (srck == 1) {
-                        sv = *p4;
-                    } else if (srck == 2) {
-                        const int c = cb + 4 * u;
-                        sv.x = c < a.N ? wrow[c] : 0.f;
-                        sv.y = c + 1 < a.N ? wrow[c + 1] : 0.f;
-                        sv.z = c + 2 < a.N ? wrow[c + 2] : 0.f;
-                        sv.w = c + 3 < a.N ? wrow[c + 3] : 0.f;
-                    }
-                    const float4 o = make_float4(sv.x - __uint_as_float(v[4 * u]), sv.y - __uint_as_float(v[4 * u + 1]),
-                                                 sv.z - __uint_as_float(v[4 * u + 2]), sv.w - __uint_as_float(v[4 * u + 3]));
+                    const float4 o = make_float4(sv[u].x - __uint_as_float(v[4 * u]), sv[u].y - __uint_as_float(v[4 * u + 1]),
+                                                 sv[u].z - __uint_as_float(v[4 * u + 2]), sv[u].w - __uint_as_float(v[4 * u + 3]));
                     *p4 = o;
                     if (ngi >= 0 || nwr >= 0) {
                         const int c = cb + 4 * u;
@@ -753,6 +812,8 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             __syncwarp();
             const int nchunks = (min(BN, a.N - n0) + 31) / 32;
+            float its8[8];   // format 2 column scales
+            if constexpr (FMT == 2) load_tile_scales(its8, a.invt + box * a.sInvt + n0, nchunks, lane);
             auto prefetch = [&](int cc) {
                 const int cb = n0 + cc * 32;
                 const uint32_t buf = sb_u32 + (uint32_t)((cc % TC_PRE) * 4096);
@@ -800,6 +861,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 asm volatile("cp.async.commit_group;" ::: "memory");
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + cc * 32), v);
+                if constexpr (FMT == 2) scale_chunk(v, its8);
                 // row = lane; 16-byte group g of the row goes to slot g ^ (lane & 7)
 #pragma unroll
                 for (int g = 0; g < 8; ++g)
@@ -903,6 +965,106 @@ __global__ void k_gather_pack(const float* __restrict__ M, long long ldm, long l
     }
 }
 
+// Format 2 scales: 2^(15 - e) for a column maximum mx < 2^e (so every scaled
+// value stays below 2^15, inside FP16's range after rounding), 1 for an empty
+// or all-zero column; exponents are clamped to +-100.  Built from the
+// exponent field, so both the scale and its inverse are exact powers of two.
+__device__ __forceinline__ int scale_exp(float mx)
+{
+    if (!(mx > 0.0f)) return 0;
+    const int eb = (int)((__float_as_uint(mx) >> 23) & 0xffu);   // mx < 2^(eb - 126) (subnormals: 2^-126)
+    if (eb == 0xff) return 0;                                     // inf: left unscaled, it shows in the result
+    int e = 15 - (eb == 0 ? -126 : eb - 126);
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Format 2 left operand: dst = the split planes (rows x NB, zero beyond nb)
+// of src's first nb columns, each column k scaled by 2^s_k (scale_exp of its
+// maximum over the rows); rc[k] = 2^-s_k, the factor the right operand's row
+// k takes.  One CTA per box and 32 columns: a pass for the maxima, a pass
+// for the values.
+__global__ void k_pack_f16(const float* __restrict__ src, long long lds, long long sS, int rows, int NB, int nb,
+                           __half* __restrict__ dst, long long sD, float* __restrict__ rc, long long sC)
+{
+    __shared__ float red[8][33];
+    __shared__ float scl[32];
+    const int box = blockIdx.y, tx = threadIdx.x, ty = threadIdx.y;
+    const int c = blockIdx.x * 32 + tx;
+    const float* sb = src + box * sS;
+    float mx = 0.0f;
+    if (c < nb)
+        for (int r = ty; r < rows; r += 8) mx = fmaxf(mx, fabsf(sb[(long long)r * lds + c]));
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+        float m = red[0][tx];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) m = fmaxf(m, red[i][tx]);
+        const int e = scale_exp(m);
+        scl[tx] = pow2f(e);
+        if (c < NB) rc[box * sC + c] = pow2f(-e);
+    }
+    __syncthreads();
+    if (c >= NB) return;
+    const float sc = scl[tx];
+    const long long total = (long long)rows * NB;
+    __half* db = dst + box * sD;
+    for (int r = ty; r < rows; r += 8)
+        split_store<2>(db, (long long)r * NB + c, total, c < nb ? sb[(long long)r * lds + c] * sc : 0.0f);
+}
+
+// Format 2 right operand: as k_gather_pack, with row i of the gathered block
+// multiplied by rc[i] (the left operand's K scale inverse) and then each
+// column c scaled by 2^t_c (scale_exp of its maximum); invt[c] = 2^-t_c for
+// the epilogue.  One CTA per box and 32 columns, the whole K extent (gK rows)
+// in shared memory.
+__global__ void k_gather_pack_f16(const float* __restrict__ M, long long ldm, long long sM, int k, int nb, int gK,
+                                  int c0, int nc, const int* __restrict__ perm, long long sP, float* __restrict__ W,
+                                  long long ldw, long long sW, __half* __restrict__ Gp, long long plane, long long sGp,
+                                  const float* __restrict__ rc, long long sC, float* __restrict__ invt,
+                                  long long sIt, const int* skip)
+{
+    extern __shared__ float gt[];   // [gK][33]
+    __shared__ float red[8][33];
+    __shared__ float scl[32];
+    const int box = blockIdx.y;
+    if (skip && skip[box]) return;
+    const int cb = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+    const float* Mb = M + box * sM;
+    const float* rcb = rc + box * sC;
+    const int c = cb + tx;
+    float mx = 0.0f;
+    for (int i = ty; i < gK; i += 8) {
+        float v = 0.0f;
+        if (i < nb && c < nc) {
+            const int srcr = k + (perm ? perm[box * sP + i] : i);
+            v = Mb[(long long)srcr * ldm + c0 + c] * rcb[i];
+            if (W) W[box * sW + (long long)i * ldw + c] = Mb[(long long)(k + i) * ldm + c0 + c];
+            mx = fmaxf(mx, fabsf(v));
+        }
+        gt[i * 33 + tx] = v;
+    }
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+        float m = red[0][tx];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) m = fmaxf(m, red[i][tx]);
+        const int e = scale_exp(m);
+        scl[tx] = pow2f(e);
+        invt[box * sIt + c] = pow2f(-e);
+    }
+    __syncthreads();
+    __half* G = Gp + box * sGp;
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int col = cb + cc;
+        if (col >= nc) break;
+        const float sc = scl[cc];
+        for (int i = tx; i < gK; i += 32) split_store<2>(G, (long long)col * gK + i, plane, gt[i * 33 + cc] * sc);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -932,7 +1094,9 @@ bool make_map(CUtensorMap* tm, const void* base, int K, long long rows, long lon
     cuuint64_t strides[3] = {(cuuint64_t)K * Fm::EB, (cuuint64_t)plane_elems * Fm::EB, (cuuint64_t)box_elems * Fm::EB};
     cuuint32_t boxd[4] = {(cuuint32_t)Fm::KPC, (cuuint32_t)box_rows, 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = fn(tm, FMT == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+    const CUtensorMapDataType dt = FMT == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                            : (FMT == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    CUresult r = fn(tm, dt, 4,
                     const_cast<void*>(base), dims, strides, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -1062,6 +1226,7 @@ bool launch_tc_update(int fmt, const TcLeft& L, const void* Gp, long long g_plan
                       const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs,
                       bool* fused = nullptr)
 {
+    if (fmt == 2) return launch_tc_update_f<2>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused);
     return fmt ? launch_tc_update_f<1>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused)
                : launch_tc_update_f<0>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused);
 }
@@ -1072,23 +1237,41 @@ void* pk_at(void* base, long long off, int fmt)
     return fmt ? (void*)(static_cast<unsigned short*>(base) + off) : (void*)(static_cast<float*>(base) + off);
 }
 
+// rc (format 2 only): the K scales' inverses of this pack, per box stride sC.
 void launch_pack_split(int fmt, const float* src, long long lds, long long sS, int rows, int NB, int nb, void* dst,
-                       long long sD, int nbox, cudaStream_t st)
+                       long long sD, int nbox, cudaStream_t st, float* rc = nullptr, long long sC = 0)
 {
     const long long total = (long long)rows * NB;
     const dim3 blk(32, 8);   // 8 rows of 32-column strips per CTA
-    dim3 grd((unsigned)std::max(1, std::min((rows + 7) / 8, 128)), (unsigned)nbox);
     prof_begin(KC_PACK, st);
+    if (fmt == 2) {
+        k_pack_f16<<<dim3((unsigned)((NB + 31) / 32), (unsigned)nbox), blk, 0, st>>>(
+            src, lds, sS, rows, NB, nb, static_cast<__half*>(dst), sD, rc, sC);
+        prof_end(KC_PACK, st, 0.0, (double)nbox * total * (4.0 + 4.0));
+        return;
+    }
+    dim3 grd((unsigned)std::max(1, std::min((rows + 7) / 8, 128)), (unsigned)nbox);
     if (fmt) k_pack_split<1><<<grd, blk, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
     else k_pack_split<0><<<grd, blk, 0, st>>>(src, lds, sS, rows, NB, nb, dst, sD);
     prof_end(KC_PACK, st, 0.0, (double)nbox * total * (4.0 + (fmt ? 6.0 : 8.0)));
 }
 
+// rc, sC (format 2 only): the left operand's K scale inverses for the
+// gathered rows; invt, sIt: where the column scale inverses go.
 void gather_pack_raw(int fmt, const float* M, long long ldm, long long sM, int k, int nb, int gK, int c0, int nc,
                      const int* perm, long long sP, float* W, long long ldw, long long sW, void* Gp, long long plane,
-                     long long sGp, const int* skip, int nbox, cudaStream_t st)
+                     long long sGp, const int* skip, int nbox, cudaStream_t st, const float* rc = nullptr,
+                     long long sC = 0, float* invt = nullptr, long long sIt = 0)
 {
     prof_begin(KC_GATHER, st);
+    if (fmt == 2) {
+        const dim3 grd((unsigned)((nc + 31) / 32), (unsigned)nbox), blk(32, 8);
+        k_gather_pack_f16<<<grd, blk, (size_t)gK * 33 * sizeof(float), st>>>(
+            M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, static_cast<__half*>(Gp), plane, sGp, rc, sC, invt,
+            sIt, skip);
+        prof_end(KC_GATHER, st, 0.0, (double)nbox * nb * (double)nc * (4.0 + (W ? 4.0 : 0.0) + 4.0));
+        return;
+    }
     const dim3 grd((unsigned)((nc + 31) / 32), (unsigned)(gK / 32), (unsigned)nbox), blk(32, 8);
     if (fmt)
         k_gather_pack<1><<<grd, blk, 0, st>>>(M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, Gp, plane, sGp, skip);
@@ -1098,10 +1281,10 @@ void gather_pack_raw(int fmt, const float* M, long long ldm, long long sM, int k
 }
 
 void launch_gather_pack(const Plan& P, Work<float>& w, int k, int nb, int c0, int nc, const int* perm, bool save_w,
-                        const int* skip, int nbox, cudaStream_t st)
+                        const int* skip, int nbox, cudaStream_t st, const float* rc)
 {
     gather_pack_raw(P.fmt, w.M, P.ldm, w.sM, k, nb, P.KG, c0, nc, perm, w.sP, save_w ? w.W : nullptr, P.ldm, w.sG,
-                    w.Gp, P.ldm * P.KG, w.sGp, skip, nbox, st);
+                    w.Gp, P.ldm * P.KG, w.sGp, skip, nbox, st, rc, w.sRC, w.it1, w.sIT);
 }
 
 TcArgs targs(float* O, long long ldo, long long sO, int M, int N, int mode, int split)
@@ -1181,7 +1364,12 @@ __global__ void k_perm_inverse(const int* __restrict__ perm, int* __restrict__ i
 }
 
 // Start of step s's split F_s / B_s in the operand format of the plan.
-int npl(const Plan& P) { return P.fmt ? 3 : 2; }
+int npl(const Plan& P) { return P.fmt == 1 ? 3 : 2; }
+// Format 2: K scale inverses of F_s and B_s (null otherwise).
+const float* rcf(const Plan& P, const Work<float>& w, int s) { return w.rcF ? w.rcF + (long long)s * P.NB : nullptr; }
+const float* rcb(const Plan& P, const Work<float>& w, int s) { return w.rcB ? w.rcB + (long long)s * P.NB : nullptr; }
+float* rcf_w(const Plan& P, Work<float>& w, int s) { return w.rcF ? w.rcF + (long long)s * P.NB : nullptr; }
+float* rcb_w(const Plan& P, Work<float>& w, int s) { return w.rcB ? w.rcB + (long long)s * P.NB : nullptr; }
 void* fpk(const Plan& P, const Work<float>& w, int s) { return pk_at(w.Fp, (long long)npl(P) * P.fw_off[s], P.fmt); }
 void* bpk(const Plan& P, const Work<float>& w, int s) { return pk_at(w.Bp, (long long)npl(P) * P.bw_off[s], P.fmt); }
 
@@ -1234,7 +1422,9 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
 {
     const int n = P.n, NB = P.NB, KG = P.KG;
     const long long ldm = P.ldm, gplane = ldm * KG;
-    auto up = [&](const TcLeft& L, const TcArgs& a) {
+    auto up = [&](const TcLeft& L, TcArgs a) {
+        a.invt = w.it1;
+        a.sInvt = w.sIT;
         return launch_tc_update(P.fmt, L, w.Gp, gplane, w.sGp, KG, NB, a, nbox, st, P.tma_epi, P.tc_pairs);
     };
     // Panel of step s, its operators F_s and B_s (FP32 and split copies).
@@ -1252,22 +1442,23 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         if (n - k - nb > 0) {
             void* Fp = fpk(P, w, s);
             launch_pack_split(P.fmt, w.M + (long long)(k + nb) * ldm + k, ldm, w.sM, n - k - nb, NB, nb, Fp, w.sFp,
-                              nbox, st);
+                              nbox, st, rcf_w(P, w, s), w.sRC);
             gather_pack_raw(P.fmt, Fs, NB, w.sF, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp, nullptr,
-                            nbox, st);
+                            nbox, st, rcf(P, w, s), w.sRC, w.it1, w.sIT);
             TcArgs a = targs(Fs + (long long)nb * NB, NB, w.sF, n - k - nb, nb, GM_SET, 0);
             if (!up(left1(Fp, n - k - nb, w.sFp, nb), a)) return false;
         }
         if (k > 0) {
             void* Bp = bpk(P, w, s);
-            launch_pack_split(P.fmt, w.M + k, ldm, w.sM, k, NB, nb, Bp, w.sBp, nbox, st);
+            launch_pack_split(P.fmt, w.M + k, ldm, w.sM, k, NB, nb, Bp, w.sBp, nbox, st, rcb_w(P, w, s), w.sRC);
             gather_pack_raw(P.fmt, Bs + (long long)k * NB, NB, w.sB, 0, nb, KG, 0, nb, nullptr, 0, nullptr, 0, 0, w.Gp,
-                            gplane, w.sGp, nullptr, nbox, st);
+                            gplane, w.sGp, nullptr, nbox, st, rcb(P, w, s), w.sRC, w.it1, w.sIT);
             TcArgs a = targs(Bs, NB, w.sB, k, nb, GM_SET, 0);
             if (!up(left1(Bp, k, w.sBp, nb), a)) return false;
         }
-        launch_pack_split(P.fmt, Fs, NB, w.sF, n - k, NB, nb, fpk(P, w, s), w.sFp, nbox, st);
-        if (pack_b) launch_pack_split(P.fmt, Bs, NB, w.sB, k + nb, NB, nb, bpk(P, w, s), w.sBp, nbox, st);
+        launch_pack_split(P.fmt, Fs, NB, w.sF, n - k, NB, nb, fpk(P, w, s), w.sFp, nbox, st, rcf_w(P, w, s), w.sRC);
+        if (pack_b)
+            launch_pack_split(P.fmt, Bs, NB, w.sB, k + nb, NB, nb, bpk(P, w, s), w.sBp, nbox, st, rcb_w(P, w, s), w.sRC);
         return true;
     };
     // Step s's update of M's columns [c0, c0 + nc).
@@ -1275,7 +1466,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         if (nc <= 0) return true;
         const int k = P.k0[s], nb = P.nbs[s];
         int* Ps = w.perm + P.perm_off[s];
-        launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st);
+        launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st, rcf(P, w, s));
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
         return up(left1(fpk(P, w, s), n - k, w.sFp, nb), a);
@@ -1289,19 +1480,21 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         const int* P1 = w.perm + P.perm_off[s + 1];
         {   // F_s' = forward step s+1 on F_s's rows [nb0, n - k)
             gather_pack_raw(P.fmt, F0, NB, w.sF, nb0, nb1, KG, 0, nb0, P1, w.sP, w.W, NB, w.sG, w.Gp, gplane, w.sGp, nullptr,
-                            nbox, st);
+                            nbox, st, rcf(P, w, s + 1), w.sRC, w.it1, w.sIT);
             TcArgs a = targs(F0 + (long long)nb0 * NB, NB, w.sF, n - k1, nb0, GM_FWD, nb1);
             a.perm = P1; a.sP = w.sP; a.W = w.W; a.ldw = NB; a.sW = w.sG; a.status = status;
             if (!up(left1(fpk(P, w, s + 1), n - k1, w.sFp, nb1), a)) return false;
-            launch_pack_split(P.fmt, F0, NB, w.sF, n - k, NB, nb0, fpk(P, w, s), w.sFp, nbox, st);
+            launch_pack_split(P.fmt, F0, NB, w.sF, n - k, NB, nb0, fpk(P, w, s), w.sFp, nbox, st, rcf_w(P, w, s),
+                              w.sRC);
         }
         {   // B_{s+1}' = backward step s on B_{s+1}'s rows [0, k + nb0)
             gather_pack_raw(P.fmt, B1, NB, w.sB, k, nb0, KG, 0, nb1, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
-                            nullptr, nbox, st);
+                            nullptr, nbox, st, rcb(P, w, s), w.sRC, w.it1, w.sIT);
             TcArgs a = targs(B1, NB, w.sB, k + nb0, nb1, GM_BWD, k);
             a.status = status;
             if (!up(left1(bpk(P, w, s), k + nb0, w.sBp, nb0), a)) return false;
-            launch_pack_split(P.fmt, B1, NB, w.sB, k1 + nb1, NB, nb1, bpk(P, w, s + 1), w.sBp, nbox, st);
+            launch_pack_split(P.fmt, B1, NB, w.sB, k1 + nb1, NB, nb1, bpk(P, w, s + 1), w.sBp, nbox, st,
+                              rcb_w(P, w, s + 1), w.sRC);
         }
         launch_perm_compose(P0, P1, w.sP, n - k, nb0, nbox, st);
         return true;
@@ -1321,7 +1514,7 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
         const int c0 = k + wp, nc = n + P.r - c0;
         if (nc > 0) {
             int* Pc = w.perm + P.perm_off[s];
-            launch_gather_pack(P, w, k, wp, c0, nc, Pc, true, nullptr, nbox, st);
+            launch_gather_pack(P, w, k, wp, c0, nc, Pc, true, nullptr, nbox, st, rcf(P, w, s));
             TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
             a.perm = Pc; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
             if (!up(left_fwd_pair(P, w, s), a)) return false;
@@ -1352,6 +1545,7 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
     const long long ldm = P.ldm, gplane = ldm * P.KG;
     void* Gb[2] = {w.Gp, w.Gp2};
     float* Wb[2] = {w.W, w.W2};
+    float* Ib[2] = {w.it1, w.it2};
     const auto units = solve_units(P);
     auto width = [&](size_t u) { const int s = units[u].first; return units[u].second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s]; };
     bool have = false;   // the current unit's G and W are in buffer cur
@@ -1360,9 +1554,10 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
         int* Ps = w.perm + P.perm_off[s];
         if (!have)
             gather_pack_raw(P.fmt, w.M, ldm, w.sM, k, wp, P.KG, c0, nc, Ps, w.sP, Wb[cur], ldm, w.sG, Gb[cur], gplane,
-                            w.sGp, skip, nbox, st);
+                            w.sGp, skip, nbox, st, rcf(P, w, s), w.sRC, Ib[cur], w.sIT);
         TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
         a.perm = Ps; a.sP = w.sP; a.W = Wb[cur]; a.ldw = ldm; a.sW = w.sG; a.skip = skip;
+        a.invt = Ib[cur]; a.sInvt = w.sIT;
         // The next unit's G is gathered through its pivot permutation, whose
         // source rows scatter over the rows this product writes: stores from
         // the epilogue would not coalesce, so the forward sweep gathers on
@@ -1384,6 +1579,7 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
 {
     const long long ldm = P.ldm, gplane = ldm * P.KG;
     void* Gb[2] = {w.Gp, w.Gp2};
+    float* Ib[2] = {w.it1, w.it2};
     const auto units = solve_units(P);
     auto width = [&](size_t u) { const int s = units[u].first; return units[u].second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s]; };
     bool have = false;
@@ -1392,9 +1588,10 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
         const int s = units[q].first, k = P.k0[s], wp = width(q);
         if (!have)
             gather_pack_raw(P.fmt, w.M, ldm, w.sM, k, wp, P.KG, c0, nc, nullptr, 0, nullptr, 0, 0, Gb[cur], gplane,
-                            w.sGp, skip, nbox, st);
+                            w.sGp, skip, nbox, st, rcb(P, w, s), w.sRC, Ib[cur], w.sIT);
         TcArgs a = targs(w.M + c0, ldm, w.sM, k + wp, nc, GM_BWD, k);
         a.skip = skip;
+        a.invt = Ib[cur]; a.sInvt = w.sIT;
         if (P.fuse_bwd && q > 0 && width(q - 1) % (P.fmt ? 32 : 16) == 0) {
             const int wq = width(q - 1);
             a.nG = Gb[cur ^ 1]; a.ng_plane = gplane; a.nsG = w.sGp; a.ngK = P.KG;

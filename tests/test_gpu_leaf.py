@@ -24,7 +24,15 @@ PRECS = [
     pytest.param(H.HPS_FP32_IR, 0, 1e-10, id="fp32ir-cudacore"),
     pytest.param(H.HPS_FP32_IR, 1, 1e-10, id="fp32ir-tcgen05"),
     pytest.param(H.HPS_BF16_IR, 1, 1e-10, id="bf16ir-tcgen05"),
+    pytest.param(H.HPS_FP32_IR, 2, 1e-10, id="fp32ir-tcgen05-fp16"),
 ]
+
+
+def set_tc(ctx, tc):
+    """tc: 0 CUDA cores, 1 tcgen05 (the default operand format), 2 tcgen05
+    with the scaled 2 x FP16 operands."""
+    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, 1 if tc else 0)
+    H.hps_set_option(ctx, H.HPS_OPT_FP16_OPERANDS, 1 if tc == 2 else 0)
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +49,7 @@ def _dev(x):
 
 def gpu_dtn(ctx, p, h, kappa, b_np, prec, tc, want_S=True, block=0):
     import torch
-    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, tc)
+    set_tc(ctx, tc)
     H.hps_set_option(ctx, H.HPS_OPT_BLOCK, block)
     n, m = H.hps_leaf_sizes(p)
     nbox = b_np.shape[0]
@@ -75,8 +83,9 @@ def test_dtn_parity_small(ctx, p, nbox, prec, tc, tol):
     assert rel_fro(S, So).max() < tol, rel_fro(S, So)
 
 
+@pytest.mark.parametrize("tc", [1, 2], ids=["tf32", "fp16"])
 @pytest.mark.parametrize("p,nbox,block", [(8, 3, 0), (9, 3, 32), (12, 2, 64), (16, 2, 0)])
-def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
+def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block, tc):
     """The TMA epilogue (aligned outputs; n = 343 at p = 9 leaves the
     right-hand-side block unaligned, so both forms run in one call) and the
     cp.async epilogue compute src - acc identically, and CTA pairs sharing the
@@ -89,13 +98,13 @@ def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
     b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
     try:
         H.hps_set_option(ctx, H.HPS_OPT_TC_EPILOGUE, 1)
-        T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+        T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, tc, block=block)
         H.hps_set_option(ctx, H.HPS_OPT_TC_PAIRS, 1)
-        T2, S2, st2 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+        T2, S2, st2 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, tc, block=block)
     finally:
         H.hps_set_option(ctx, H.HPS_OPT_TC_EPILOGUE, 0)
         H.hps_set_option(ctx, H.HPS_OPT_TC_PAIRS, 0)
-    T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+    T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, tc, block=block)
     assert (st0 == 0).all() and (st1 == 0).all() and (st2 == 0).all(), (st0, st1, st2)
     assert np.array_equal(T0, T1) and np.array_equal(S0, S1)
     assert np.array_equal(T0, T2) and np.array_equal(S0, S2)
@@ -104,8 +113,9 @@ def test_tcgen05_epilogue_forms_agree(ctx, p, nbox, block):
         assert rel_fro(T0, To).max() < 1e-10
 
 
+@pytest.mark.parametrize("tc", [1, 2], ids=["tf32", "fp16"])
 @pytest.mark.parametrize("p,nbox,block", [(8, 3, 32), (9, 2, 32), (12, 2, 64), (13, 2, 64), (16, 2, 0)])
-def test_tcgen05_step_pairs_match_single_steps(ctx, p, nbox, block):
+def test_tcgen05_step_pairs_match_single_steps(ctx, p, nbox, block, tc):
     """Joining LU steps in pairs (look-ahead factorisation, 2 NB-deep
     products) against one step at a time: both within 1e-10 of the oracle and
     of each other.  The block sizes give an odd number of steps (a single step
@@ -117,10 +127,10 @@ def test_tcgen05_step_pairs_match_single_steps(ctx, p, nbox, block):
     b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
     try:
         H.hps_set_option(ctx, H.HPS_OPT_LU_PAIRS, 0)
-        T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+        T1, S1, st1 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, tc, block=block)
     finally:
         H.hps_set_option(ctx, H.HPS_OPT_LU_PAIRS, 1)
-    T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, 1, block=block)
+    T0, S0, st0 = gpu_dtn(ctx, p, h, kappa, b_gpu, H.HPS_FP32_IR, tc, block=block)
     assert (st0 == 0).all() and (st1 == 0).all(), (st0, st1)
     assert rel_fro(T0, T1).max() < 1e-10 and rel_fro(S0, S1).max() < 1e-10
     if p <= 13:
@@ -198,16 +208,17 @@ def test_dtn_dip_512_boxes_sampled(ctx, prec, tc, tol):
         assert rel_fro(S[box:box + 1], So[None]).max() < tol
 
 
-@pytest.mark.parametrize("prec", [H.HPS_FP32_IR, H.HPS_BF16_IR], ids=["fp32ir", "bf16ir"])
-def test_dtn_fourier16_512_boxes_sampled(ctx, prec):
+@pytest.mark.parametrize("prec,tc", [(H.HPS_FP32_IR, 1), (H.HPS_BF16_IR, 1), (H.HPS_FP32_IR, 2)],
+                         ids=["fp32ir", "bf16ir", "fp32ir-fp16"])
+def test_dtn_fourier16_512_boxes_sampled(ctx, prec, tc):
     """The p = 16 mixed-precision workload at full size (512 boxes, kappa = 40),
-    tensor-core LU (3 x TF32 or 3 x BF16) + FP64 refinement; two boxes and the
+    tensor-core LU (3 x TF32, 3 x BF16 or scaled 2 x FP16) + FP64 refinement; two boxes and the
     most-refined box against the oracle, and 32 evenly spaced boxes plus the
     8 most-refined ones against the plain FP64 GPU path."""
     import torch
     p, h, kappa, lows, field = config_grid("fourier16")
     b_gpu = box_b(H.hps_leaf_nodes, p, lows, h, field)
-    T, _, st = gpu_dtn(ctx, p, h, kappa, b_gpu, prec, 1, want_S=False)
+    T, _, st = gpu_dtn(ctx, p, h, kappa, b_gpu, prec, tc, want_S=False)
     assert (st == 0).all(), np.unique(st, return_counts=True)
     it, rel = H.hps_last_refinement(ctx, len(lows))
     assert (it >= 1).all() and (it <= 8).all(), (it.min(), it.max())
@@ -226,7 +237,7 @@ def test_dtn_fourier16_512_boxes_sampled(ctx, prec):
 @pytest.mark.parametrize("prec,tc,tol", PRECS)
 def test_particular_parity(ctx, prec, tc, tol):
     import torch
-    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, tc)
+    set_tc(ctx, tc)
     p, h, kappa, nbox, nrhs = 9, np.array([0.125] * 3), 20.0, 3, 4
     lows = _lows(nbox, h, 9)
     field = hi.fourier_b_field().b
@@ -263,7 +274,7 @@ def test_reconstruct_parity(ctx, prec, tc, tol, stored):
     if stored:
         _, S_np, st = gpu_dtn(ctx, p, h, kappa, box_b(H.hps_leaf_nodes, p, lows, h, field), prec, tc)
         S = _dev(S_np)
-    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, tc)
+    set_tc(ctx, tc)
     ui = torch.empty(nbox, nrhs, n, dtype=torch.float64, device="cuda")
     st = torch.full((nbox,), -1, dtype=torch.int32, device="cuda")
     H.hps_leaf_reconstruct(ctx, H.LeafKind(p, h, kappa), nbox, nrhs, b, S, _dev(v_np), _dev(ub_np), ui, prec, st)
@@ -331,7 +342,7 @@ def test_end_to_end_manufactured(ctx):
     nbox = len(lows)
     n, m = H.hps_leaf_sizes(p)
     kind = H.LeafKind(p, h, kappa)
-    H.hps_set_option(ctx, H.HPS_OPT_TENSOR_CORES, 1)
+    set_tc(ctx, 1)
     b = _dev(box_b(H.hps_leaf_nodes, p, lows, h, field))
     f = _dev(np.stack([hi.manufactured(H.hps_leaf_nodes(p, lo, h), kappa)[1] for lo in lows])[:, None, :])
     T = torch.empty(nbox, m, m, dtype=torch.float64, device="cuda")
