@@ -313,11 +313,13 @@ hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const
  * update product, 3 tensor-core update product, 4 row gather of the products,
  * 5 FP64 refinement residual, 6 refinement update, 7 D_n product,
  * 8 tensor-core update product of the refinement solves, 9 split copies of
- * the LU operators, 10 double-float first residual), the accumulated
- * launches, milliseconds, flops and bytes since the last reset.  Refinement
- * launches skip boxes that have converged, so classes 5, 6 and 8 count the
- * work of every box and overstate flops and bytes.  Returns HPS_EINVAL for cls
- * outside 0..10. */
+ * the LU operators, 10 double-float first residual, 11 bookkeeping:
+ * permutation composition and inversion, refinement checks, kappa^2 b,
+ * output transposes and stored-S reconstruction), the accumulated launches,
+ * milliseconds, flops and bytes since the last reset.  Refinement launches
+ * skip boxes that have converged, so classes 5, 6 and 8 count the work of
+ * every box and overstate flops and bytes.  Returns HPS_EINVAL for cls
+ * outside 0..11. */
 hps_status hps_profile_enable(hps_ctx* ctx, int on);
 hps_status hps_profile_reset(hps_ctx* ctx);
 hps_status hps_profile_get(hps_ctx* ctx, int cls, long long* launches, double* ms, double* flops, double* bytes);

@@ -47,7 +47,8 @@ EXPORTED_SYMBOLS = (
 
 # Kernel classes of hps_profile_get.
 KERNEL_CLASSES = ("build", "panel", "update_cudacore", "update_tcgen05", "gather", "residual_fp64",
-                  "refine_update", "dn_fp64", "update_tcgen05_refine", "pack", "residual_df")
+                  "refine_update", "dn_fp64", "update_tcgen05_refine", "pack", "residual_df",
+                  "bookkeeping")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None

@@ -214,7 +214,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
 // Kernel classes timed by the optional event profiler (HPS_OPT_PROFILE).
 enum KernelClass {
     KC_BUILD = 0, KC_PANEL, KC_UPDATE_CUDACORE, KC_UPDATE_TC, KC_GATHER, KC_RESIDUAL, KC_REFINE, KC_DN,
-    KC_UPDATE_TC_REFINE, KC_PACK, KC_RESIDUAL_DF, KC_COUNT
+    KC_UPDATE_TC_REFINE, KC_PACK, KC_RESIDUAL_DF, KC_MISC, KC_COUNT
 };
 
 // When profiling is on for the calling thread, prof_begin/prof_end bracket a

@@ -1481,7 +1481,9 @@ void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, in
                     double* kb, float2* kbs, cudaStream_t st)
 {
     dim3 grd((unsigned)((g.n + 255) / 256), (unsigned)nbox);
+    prof_begin(KC_MISC, st);
     k_kappa_b<<<grd, 256, 0, st>>>(g.p, g.n, b, sb, kappa * kappa, kappa_box, kb, kbs);
+    prof_end(KC_MISC, st, 0.0, (double)nbox * g.n * 24.0);
 }
 
 namespace {
@@ -1582,22 +1584,28 @@ void launch_ir_update(const float* D, long long ldd, long long sD, int n, int nc
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
                      int* iters, double* relcorr, int* status, cudaStream_t st, bool hold)
 {
+    prof_begin(KC_MISC, st);
     k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, 1e-11, last, skip, iters, relcorr, status,
                                                     hold ? 1 : 0);
+    prof_end(KC_MISC, st, 0.0, (double)nbox * 40.0);
 }
 
 void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,
                           const double* v, double* out, int nbox, cudaStream_t st)
 {
     dim3 grd((unsigned)((n + 127) / 128), (unsigned)ncols, (unsigned)nbox);
+    prof_begin(KC_MISC, st);
     k_transpose_add<<<grd, 128, 0, st>>>(X, ldx, sX, n, ncols, v, out);
+    prof_end(KC_MISC, st, 0.0, (double)nbox * n * (double)ncols * (v ? 24.0 : 16.0));
 }
 
 void launch_recon_stored(const double* S, int n, int m, int nrhs, const double* v,
                          const double* ub, double* ui, int nbox, cudaStream_t st)
 {
     dim3 grd((unsigned)((n + 7) / 8), (unsigned)nbox);
+    prof_begin(KC_MISC, st);
     k_recon_stored<<<grd, 256, 0, st>>>(S, n, m, nrhs, v, ub, ui);
+    prof_end(KC_MISC, st, 2.0 * nbox * n * (double)m * nrhs, (double)nbox * n * (double)m * 8.0);
 }
 
 

@@ -1350,7 +1350,9 @@ void launch_perm_compose(int* perm0, const int* perm1, long long sP, int R, int 
         cudaFuncSetAttribute(k_perm_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr = true;
     }
+    prof_begin(KC_MISC, st);
     k_perm_compose<<<nbox, 256, smem, st>>>(perm0, perm1, sP, R, nb0);
+    prof_end(KC_MISC, st, 0.0, (double)nbox * (3.0 * R - nb0) * 4.0);
 }
 
 // inv[r] = i where perm[i] = r for i < w, -1 for the other rows r < R (one
@@ -1525,8 +1527,10 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
     if (P.fuse_fwd)
         for (const auto& u : solve_units(P)) {
             const int s = u.first, wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
+            prof_begin(KC_MISC, st);
             k_perm_inverse<<<nbox, 256, 0, st>>>(w.perm + P.perm_off[s], w.inv + P.perm_off[s], w.sP, n - P.k0[s],
                                                  wp);
+            prof_end(KC_MISC, st, 0.0, (double)nbox * (n - P.k0[s]) * 8.0);
         }
     return true;
 }
