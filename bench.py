@@ -482,6 +482,33 @@ def run_ours(args):
             "max_rel_diff_vs_headline_T": rel_ab}
         del Ta, sta
 
+    # ---- the same precision with every residual in FP64 (the double-float
+    # first residual switched off), timed the same way
+    if prec != H.HPS_FP64 and not args.no_alt and float(opts.get("RESIDUAL_DF", 1)) != 0:
+        H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, 0)
+        Tf = torch.empty_like(T)
+        stf = torch.zeros_like(st)
+        for _ in range(2):
+            H.hps_leaf_build_dtn(ctx, kind, nbox, b, Tf, None, prec, stf, stream)
+        torch.cuda.synchronize(dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a0.record(stream)
+        for _ in range(args.steps):
+            H.hps_leaf_build_dtn(ctx, kind, nbox, b, Tf, None, prec, stf, stream)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms = allmax(a0.elapsed_time(a1) / args.steps)
+        itf, _ = H.hps_last_refinement(ctx, nbox)
+        rel_f = ((Tf - T).flatten(1).norm(dim=1) / T.flatten(1).norm(dim=1)).max().item()
+        H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, 1)
+        line["all_fp64_residuals"] = {
+            "value": world * nbox / (f_ms / 1e3), "unit": "boxes/s", "ms_per_step": f_ms,
+            "box_failures": int((stf != 0).sum().item()), "corrections_mean": float(itf.mean()),
+            "max_rel_diff_vs_headline_T": rel_f,
+            "note": "HPS_OPT_RESIDUAL_DF = 0: the first correction's residual in FP64 as well"}
+        del Tf, stf
+
     # ---- end to end through the C ABI with host buffers.  Every step copies
     # its b from pinned host memory and its T back; as in a serving loop the
     # copies run on their own stream, so step i's T copy overlaps step i+1's
