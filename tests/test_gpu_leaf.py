@@ -138,6 +138,23 @@ def test_tcgen05_step_pairs_match_single_steps(ctx, p, nbox, block, tc):
         assert rel_fro(T0, To).max() < 1e-10 and rel_fro(S0, So).max() < 1e-10
 
 
+@pytest.mark.parametrize("tc", [1, 2], ids=["tf32", "fp16"])
+@pytest.mark.parametrize("hs,kappa", [(1e-3, 1.2e3), (4.0, 0.3)], ids=["tiny", "huge"])
+def test_tcgen05_extreme_box_sizes(ctx, tc, hs, kappa):
+    """Boxes of side 1e-3 and 4 put the entries of A_ii near 1e11 and 0.1
+    (D^2 scales as 1/h^2): far outside FP16's range before its power-of-two
+    operand scaling, and the refinement's stopping rule sees the same
+    relative sizes.  Both tensor-core formats match the oracle to 1e-10."""
+    p, nbox = 9, 2
+    h = np.array([hs, 1.25 * hs, 0.8 * hs])
+    lows = _lows(nbox, h, 3)
+    field = hi.gaussian_dip_b
+    T, S, st = gpu_dtn(ctx, p, h, kappa, box_b(H.hps_leaf_nodes, p, lows, h, field), H.HPS_FP32_IR, tc)
+    To, So, _ = oracle.batch_dtn(p, h, kappa, box_b(oracle.node_coords, p, lows, h, field), want_S=True)
+    assert (st == 0).all(), st
+    assert rel_fro(T, To).max() < 1e-10 and rel_fro(S, So).max() < 1e-10
+
+
 @pytest.mark.parametrize("prec", [H.HPS_FP32_IR, H.HPS_BF16_IR], ids=["fp32ir", "bf16ir"])
 @pytest.mark.parametrize("p,nbox", [(9, 3), (12, 2), (16, 2)])
 def test_double_float_first_residual(ctx, prec, p, nbox):
