@@ -511,14 +511,17 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers.  Every step copies
     # its b from pinned host memory and its T back; as in a serving loop the
-    # copies run on their own stream, so step i's T copy overlaps step i+1's
-    # solve (b and T are double-buffered, events order each buffer's uses).
+    # copies run on their own streams (uploads and downloads apart, so an
+    # upload never queues behind a download), so step i's T copy overlaps step
+    # i+1's solve (b and T are double-buffered, events order each buffer's
+    # uses).
     if not args.no_e2e:
         b_host = torch.from_numpy(b_np).pin_memory()
         T_host = [torch.empty(nbox, m, m, dtype=torch.float64, pin_memory=True) for _ in range(2)]
         b_dev = [b, torch.empty_like(b)]
         T_dev = [T, torch.empty_like(T)]
-        cs = torch.cuda.Stream(dev)
+        cs = torch.cuda.Stream(dev)    # uploads
+        cd = torch.cuda.Stream(dev)    # downloads
         ev_in = [torch.cuda.Event() for _ in range(2)]    # b[j] is on the device
         ev_out = [torch.cuda.Event() for _ in range(2)]   # T[j] is computed
         ev_free = [torch.cuda.Event() for _ in range(2)]  # T[j] has reached the host
@@ -533,10 +536,10 @@ def run_ours(args):
             stream.wait_event(ev_free[j])                  # T[j]'s previous copy has left the device
             H.hps_leaf_build_dtn(ctx, kind, nbox, b_dev[j], T_dev[j], None, prec, st, stream)
             ev_out[j].record(stream)
-            with torch.cuda.stream(cs):
-                cs.wait_event(ev_out[j])
+            with torch.cuda.stream(cd):
+                cd.wait_event(ev_out[j])
                 T_host[j].copy_(T_dev[j], non_blocking=True)
-                ev_free[j].record(cs)
+                ev_free[j].record(cd)
 
         for i in range(2):
             ev_out[i].record(stream)
@@ -549,16 +552,17 @@ def run_ours(args):
         g0.record(stream)
         for i in range(args.steps):
             e2e_step(i)
-        cs_done = torch.cuda.Event()
-        cs_done.record(cs)
-        stream.wait_event(cs_done)                          # the last T is on the host
+        cd_done = torch.cuda.Event()
+        cd_done.record(cd)
+        stream.wait_event(cd_done)                          # the last T is on the host
         g1.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = allmax(g0.elapsed_time(g1) / args.steps)
         line["e2e"] = {"value": world * nbox / (e2e_ms / 1e3), "unit": "boxes/s",
                        "h2d_bytes_per_step": b_host.numel() * 8, "d2h_bytes_per_step": T_host[0].numel() * 8,
                        "ms_per_step": e2e_ms,
-                       "pipelining": "copies on a second stream; step i's T copy overlaps step i+1's solve"}
+                       "pipelining": "uploads and downloads on two more streams; step i's T copy overlaps step "
+                                     "i+1's solve"}
         del T_host, b_host, b_dev, T_dev
 
     # ---- the oracle on this host's cores (rank 0 at N = 1 only)

@@ -408,15 +408,16 @@ def test_largest_orders_mixed_vs_fp64(ctx, p):
     """The largest supported orders (n = 6859 and 10648 interior nodes: the
     panel's inner block shrinks to a few columns, the tables and operator
     copies are at their largest), one box: both mixed precisions against the
-    plain FP64 GPU path (the CPU oracle would take minutes at this size)."""
+    plain FP64 GPU path (the CPU oracle would take minutes at this size), the
+    FP32 path in both of its operand formats."""
     import torch
     h = np.array([0.125] * 3)
     lows = np.array([[0.25, 0.5, 0.125]])
     b = box_b(H.hps_leaf_nodes, p, lows, h, hi.fourier_b_field().b)
     T64, _, st64 = gpu_dtn(ctx, p, h, 30.0, b, H.HPS_FP64, 0, want_S=False)
     assert (st64 == 0).all()
-    for prec in (H.HPS_FP32_IR, H.HPS_BF16_IR):
-        T, _, st = gpu_dtn(ctx, p, h, 30.0, b, prec, 1, want_S=False)
+    for prec, tc in ((H.HPS_FP32_IR, 1), (H.HPS_FP32_IR, 2), (H.HPS_BF16_IR, 1)):
+        T, _, st = gpu_dtn(ctx, p, h, 30.0, b, prec, tc, want_S=False)
         assert (st == 0).all(), st
         assert rel_fro(T, T64).max() < 1e-10, rel_fro(T, T64)
     torch.cuda.empty_cache()
