@@ -97,7 +97,7 @@ def parse_args():
     ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
                     help="hps_set_option before timing, e.g. TC_PAIRS=1 (name without HPS_OPT_)")
-    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned"), default="fourier16",
+    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored"), default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
     ap.add_argument("--train-boxes", type=int, default=20000)
@@ -748,6 +748,88 @@ def run_uneven(args):
     print(json.dumps(line), flush=True)
 
 
+def run_factored(args):
+    """Factor once, solve many: the p = 16 workload's 512 boxes factored once
+    (hps_leaf_factor), then every step solves 32 new loads per box with the
+    stored factors (hps_leaf_solve_factored) -- the reuse of the build stage
+    that time stepping relies on.  Beside it: the same loads through the
+    one-shot hps_leaf_particular (which factors again), and the difference
+    from the plain FP64 path on a sample of boxes."""
+    import torch
+    import paper_2503_04033_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nbox, nl = args.nbox, 32
+    lows, h = box_lows()
+    lows = lows[np.arange(nbox) % NBOX]
+    field = hi.fourier_b_field()
+    xyz = np.stack([H.hps_leaf_nodes(P, lo, h) for lo in lows])
+    b = torch.from_numpy(field.b(xyz)).to(dev)
+    f = load_field_torch(hi.fourier_b_per_box(nl, 20250306), xyz, dev)
+    n, m = H.hps_leaf_sizes(P)
+    kind = H.LeafKind(P, h, KAPPA)
+    v = torch.empty(nbox, nl, n, dtype=torch.float64, device=dev)
+    hf = torch.empty(nbox, nl, m, dtype=torch.float64, device=dev)
+    st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+    ctx = H.hps_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    F = H.hps_leaf_factor(ctx, kind, nbox, b, nl, H.HPS_FP32_IR, st, stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    factor_ms = ev[0].elapsed_time(ev[1])
+    fact_fail = int((st != 0).sum().item())
+    for _ in range(args.warmup):
+        H.hps_leaf_solve_factored(F, nl, f, v, hf, st, stream)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(0) as clocks:
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            H.hps_leaf_solve_factored(F, nl, f, v, hf, st, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    fails = int((st != 0).sum().item())
+    H.hps_leaf_factors_destroy(F)
+    # the one-shot call on the same loads (factors again), timed once after a warm call
+    v1, h1 = torch.empty_like(v), torch.empty_like(hf)
+    H.hps_leaf_particular(ctx, kind, nbox, nl, b, f, v1, h1, H.HPS_FP32_IR, st, stream)
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    H.hps_leaf_particular(ctx, kind, nbox, nl, b, f, v1, h1, H.HPS_FP32_IR, st, stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    once_ms = ev[0].elapsed_time(ev[1])
+    rel_once = ((v1 - v).flatten(1).norm(dim=1) / v1.flatten(1).norm(dim=1)).max().item()
+    del v1, h1
+    # the plain FP64 path on a sample of boxes
+    k = min(16, nbox)
+    sel = torch.from_numpy(np.linspace(0, nbox - 1, k).astype(np.int64)).to(dev)
+    v64 = torch.empty(k, nl, n, dtype=torch.float64, device=dev)
+    h64 = torch.empty(k, nl, m, dtype=torch.float64, device=dev)
+    st64 = torch.zeros(k, dtype=torch.int32, device=dev)
+    H.hps_leaf_particular(ctx, kind, k, nl, b.index_select(0, sel).contiguous(), f.index_select(0, sel).contiguous(),
+                          v64, h64, H.HPS_FP64, st64, stream)
+    torch.cuda.synchronize(dev)
+    vs = v.index_select(0, sel)
+    rel64 = ((vs - v64).flatten(1).norm(dim=1) / v64.flatten(1).norm(dim=1)).max().item()
+    H.hps_destroy(ctx)
+    flops = nbox * (4.0 * n * n * nl + 2.0 * (P - 2) * m * nl)   # forward + backward solves and A_bi v
+    line = {"metric": "particular solutions/s at p=16 with stored factors (32 loads per box, FP32 LU + FP64 refinement)",
+            "value": nbox * nl / (ms / 1e3), "unit": "solutions/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{nbox} boxes of the p=16 workload (kappa=40, Fourier-law b), {nl} Gaussian "
+                                   f"random smooth loads per box (seed 20250306); factors kept between steps"},
+            "factor_ms": factor_ms, "factor_failures": fact_fail, "box_failures": fails,
+            "tflops_solves": flops / (ms / 1e3) / 1e12,
+            "one_shot_particular": {"ms": once_ms, "value": nbox * nl / (once_ms / 1e3), "unit": "solutions/s",
+                                    "max_rel_diff_v": rel_once},
+            "rel_err_vs_fp64_path": rel64, "fp64_sample_boxes": k, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.warmup < 3:
@@ -758,6 +840,8 @@ def main():
         run_uneven(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "factored":
+        run_factored(args)
     else:
         run_ours(args)
 

@@ -305,6 +305,40 @@ hps_status hps_last_refinement(hps_ctx* ctx, int nbox, int* iters, double* rel_c
 hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const double* b, double* T,
                                       int* box_status, void* stream);
 
+/* ---- Stored factorisations (factor once, solve many) ----------------------
+ *
+ * The interior blocks of a batch of boxes factored once and kept on the
+ * device, so that later loads reuse them: the build stage applied once and
+ * every time step (or load batch) only solves, as the paper does for its
+ * Crank-Nicolson time stepping, where the same operator serves every step
+ * (Sec. 4.4).  hps_leaf_factor builds and factors A_ii of nbox boxes of one
+ * kind (b as in hps_leaf_build_dtn; it is not read after the call returns,
+ * kappa^2 b being kept) in the given precision, allocating device memory for
+ * the factors and for solves of up to nrhs_max (1..256) right-hand sides, and
+ * returns the handle in *out.  box_status (device [nbox], or NULL) receives
+ * each box's factorisation status (HPS_ESINGULAR for a singular A_ii).
+ * Returns HPS_ENOMEM when the factors do not fit.  The handle belongs to ctx
+ * (destroy it before the context) and its calls are serialised with ctx's.
+ *
+ * hps_leaf_solve_factored: v = A_ii^{-1} f_i and h = A_bi v for nrhs <=
+ * nrhs_max loads, layouts as in hps_leaf_particular (Sec. 2.2 steps 1-2,
+ * Algorithm 2).  hps_leaf_reconstruct_factored: u_i = v + S u_b with S
+ * applied by solves, layouts as in hps_leaf_reconstruct (Sec. 2.2 step 4).
+ * Both refine to FP64 accuracy on the mixed paths as the one-shot calls do,
+ * write each box's status to box_status (device [nbox], or NULL; a box whose
+ * factorisation failed keeps that status) and return HPS_EINVAL for nrhs out
+ * of range or NULL arrays.  Several solves may follow one factorisation; they
+ * share the handle's workspace, so solves on different streams must be
+ * ordered by the caller. */
+typedef struct hps_leaf_factors hps_leaf_factors;
+hps_status hps_leaf_factor(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const double* b, int nrhs_max,
+                           hps_precision precision, int* box_status, void* stream, hps_leaf_factors** out);
+hps_status hps_leaf_solve_factored(hps_leaf_factors* factors, int nrhs, const double* f, double* v, double* h,
+                                   int* box_status, void* stream);
+hps_status hps_leaf_reconstruct_factored(hps_leaf_factors* factors, int nrhs, const double* v, const double* ub,
+                                         double* ui, int* box_status, void* stream);
+void hps_leaf_factors_destroy(hps_leaf_factors* factors);
+
 /* Optional per-kernel timing.  hps_profile_enable(ctx, 1) makes the leaf calls
  * bracket every kernel launch with CUDA events on the caller's stream and
  * record each launch's algorithmic flops (2 M N K for an update product, the

@@ -25,7 +25,8 @@ __all__ = [
     "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
     "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_TC_PAIRS", "HPS_OPT_LU_PAIRS", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
-    "hps_dtn_gate", "hps_selftest_conversions",
+    "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
+    "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -42,7 +43,8 @@ EXPORTED_SYMBOLS = (
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
-    "hps_dtn_gate", "hps_selftest_conversions",
+    "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
+    "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy",
 )
 
 # Kernel classes of hps_profile_get.
@@ -106,6 +108,10 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_build_dtn": (i, [vp, kp, i, vp, vp, vp, i, vp, vp]),
         "hps_leaf_particular": (i, [vp, kp, i, i, vp, vp, vp, vp, i, vp, vp]),
         "hps_leaf_reconstruct": (i, [vp, kp, i, i, vp, vp, vp, vp, vp, i, vp, vp]),
+        "hps_leaf_factor": (i, [vp, kp, i, vp, i, i, vp, vp, ctypes.POINTER(vp)]),
+        "hps_leaf_solve_factored": (i, [vp, i, vp, vp, vp, vp, vp]),
+        "hps_leaf_reconstruct_factored": (i, [vp, i, vp, vp, vp, vp, vp]),
+        "hps_leaf_factors_destroy": (None, [vp]),
         "hps_assemble_interface_blocks": (i, [i, ip, dp, i64p, i64p, i64p, dp, i64p, i64p, i64p, dp, i64p, i64p]),
         "hps_last_refinement": (i, [vp, i, ip, dp]),
         "hps_profile_enable": (i, [vp, i]),
@@ -253,6 +259,38 @@ def hps_leaf_reconstruct(ctx, kind: LeafKind, nbox: int, nrhs: int, b, S, v, ub,
         _ptr(ui, f64), int(prec),
         _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
         _stream(stream)), "hps_leaf_reconstruct")
+
+
+def hps_leaf_factor(ctx, kind: LeafKind, nbox: int, b, nrhs_max: int, prec: int = HPS_FP32_IR, box_status=None,
+                    stream=None):
+    """Factors A_ii of every box once; returns the handle for
+    hps_leaf_solve_factored / hps_leaf_reconstruct_factored."""
+    out = ctypes.c_void_p()
+    _check(load_library().hps_leaf_factor(
+        ctx, ctypes.byref(kind), int(nbox), _ptr(b, _f64() if not isinstance(b, int) else None), int(nrhs_max),
+        int(prec), _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream), ctypes.byref(out)), "hps_leaf_factor")
+    return out
+
+
+def hps_leaf_solve_factored(factors, nrhs: int, f, v, h, box_status=None, stream=None) -> None:
+    f64 = _f64() if not isinstance(f, int) else None
+    _check(load_library().hps_leaf_solve_factored(
+        factors, int(nrhs), _ptr(f, f64), _ptr(v, f64), _ptr(h, f64),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_solve_factored")
+
+
+def hps_leaf_reconstruct_factored(factors, nrhs: int, v, ub, ui, box_status=None, stream=None) -> None:
+    f64 = _f64() if not isinstance(ub, int) else None
+    _check(load_library().hps_leaf_reconstruct_factored(
+        factors, int(nrhs), _ptr(v, f64), _ptr(ub, f64), _ptr(ui, f64),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_reconstruct_factored")
+
+
+def hps_leaf_factors_destroy(factors) -> None:
+    load_library().hps_leaf_factors_destroy(factors)
 
 
 def hps_last_refinement(ctx, nbox: int):

@@ -116,6 +116,22 @@ struct hps_ctx {
     std::mutex mu;
 };
 
+// A stored factorisation of every box's A_ii (hps_leaf_factor): the workspace
+// of one chunk holding all the boxes, kept between calls.
+struct hps_leaf_factors {
+    hps_ctx* ctx = nullptr;
+    hps::Geometry* g = nullptr;
+    hps::Plan P;
+    hps_precision prec = HPS_FP64;
+    int nbox = 0, nrhs_max = 0;
+    double kappa = 0.0;
+    void* buf = nullptr;            // the chunk workspace (factors, operator copies, kappa^2 b, solve buffers)
+    int* d_fstatus = nullptr;       // per box: status of the factorisation
+    int* d_status = nullptr;        // per box: status of the last solve when the caller passes none
+    int* d_iters = nullptr;         // refinement diagnostics of the last solve
+    double* d_relcorr = nullptr;
+};
+
 namespace hps {
 
 // ------------------------------------------------------------ 1-D operators
@@ -248,6 +264,7 @@ void lu_backward(const Plan& P, Work<T>& w, int nbox, int c0, int nc, const int*
 template void lu_factor<double>(const Plan&, Work<double>&, int, int*, cudaStream_t);
 template void lu_factor<float>(const Plan&, Work<float>&, int, int*, cudaStream_t);
 template void lu_forward<float>(const Plan&, Work<float>&, int, int, int, const int*, cudaStream_t);
+template void lu_forward<double>(const Plan&, Work<double>&, int, int, int, const int*, cudaStream_t);
 template void lu_backward<double>(const Plan&, Work<double>&, int, int, int, const int*, cudaStream_t);
 template void lu_backward<float>(const Plan&, Work<float>&, int, int, int, const int*, cudaStream_t);
 
@@ -475,6 +492,10 @@ hps_status solve_chunk<double>(hps_ctx*, const Geometry& g, const CallSpec& cs, 
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, const Plan& P, Work<float>& w, int nbox,
+                        const double* b, double* X, long long ldx, long long sX, int* status, int* iters,
+                        double* relcorr, cudaStream_t st, bool have_kb);
+
 template <>
 hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, const Plan& P, Work<float>& w,
                               int nbox, const double* b, double* X, long long ldx, long long sX, int* status,
@@ -491,9 +512,19 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
         lu_factor<float>(P, w, nbox, status, st);
         lu_backward<float>(P, w, nbox, g.n, cs.r, nullptr, st);
     }
-    // FP64 iterative refinement: R = B - A_ii X (FP64, matrix-free), solve with
-    // the FP32 factors, X += correction (FP64).  ||X|| for the stopping rule
-    // is taken once, from the first solution.
+    return refine_chunk(ctx, g, cs, P, w, nbox, b, X, ldx, sX, status, iters, relcorr, st, false);
+}
+
+// FP64 iterative refinement of the first solution in M's right-hand-side
+// columns: R = B - A_ii X (FP64, matrix-free), solve with the FP32 factors,
+// X += correction (FP64).  ||X|| for the stopping rule is taken once, from
+// the first solution.  have_kb: kappa^2 b (and its split) is already in w.kb
+// (a stored factorisation), b is then not read.
+hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, const Plan& P, Work<float>& w, int nbox,
+                        const double* b, double* X, long long ldx, long long sX, int* status, int* iters,
+                        double* relcorr, cudaStream_t st, bool have_kb)
+{
+    const long long p3 = (long long)g.p * g.p * g.p;
     HPS_CUDA_TRY(cudaMemsetAsync(w.skip, 0, sizeof(int) * nbox, st));
     HPS_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(double) * 2 * nbox, st));
     launch_extract<float>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st, w.norms);
@@ -501,7 +532,7 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
     // The first residual, of the FP32 solution itself, may run in double-float
     // when at least one FP64-residual correction follows it.
     const bool df = ctx->res_df && its >= 2 && g.dDF;
-    if (its > 0) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, df ? w.kbs : nullptr, st);
+    if (its > 0 && !have_kb) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, df ? w.kbs : nullptr, st);
     for (int it = 0; it < its; ++it) {
         if (df && it == 0)
             launch_residual_df(g, nbox, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M + g.n, P.ldm, w.sM, w.kbs, w.skip,
@@ -787,6 +818,110 @@ hps_status run_single(hps_ctx* ctx, Job j, const hps_leaf_kind* kind, hps_precis
     return finish(ctx, jobs, st);
 }
 
+// ------------------------------------------------------------ stored factorisations
+
+template <typename T>
+hps_status factors_factor(hps_leaf_factors* F, const double* b, cudaStream_t st)
+{
+    const Geometry& g = *F->g;
+    const long long p3 = (long long)g.p * g.p * g.p;
+    Work<T> w = carve<T>(F->P, F->buf, F->nbox);
+    HPS_CUDA_TRY(cudaMemsetAsync(F->d_fstatus, 0, sizeof(int) * F->nbox, st));
+    launch_build_aug<T>(g, F->kappa, nullptr, F->nbox, b, p3, RHS_LOAD, 0, nullptr, 0, w.M, F->P.ldm, w.sM,
+                        F->d_fstatus, F->ctx->zero_row_box, st);
+    if constexpr (sizeof(T) == 8) {
+        lu_factor<double>(F->P, w, F->nbox, F->d_fstatus, st);
+    } else {
+        if (F->P.tc) {
+            tc_reset_abort(st);
+            if (!tc_lu_factor(F->P, w, F->nbox, F->d_fstatus, st)) return HPS_ECUDA;
+        } else {
+            lu_factor<float>(F->P, w, F->nbox, F->d_fstatus, st);
+        }
+        launch_kappa_b(g, F->kappa, nullptr, F->nbox, b, p3, w.kb, w.kbs, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+// X = A_ii^{-1} B for B = f_i (LOAD) or -A_ib u_b (TRACE), nrhs columns, with
+// the stored factors (and the FP64 refinement of the mixed path); then the
+// outputs: v and h = A_bi v (LOAD) or u_i = X + v (TRACE).
+template <typename T>
+hps_status factors_solve(hps_leaf_factors* F, int rhs_kind, int nrhs, const double* rhs, const double* vadd,
+                         double* out0, double* out1, int* status, cudaStream_t st)
+{
+    const Geometry& g = *F->g;
+    const int n = g.n, m = g.m, nbox = F->nbox;
+    const long long p3 = (long long)g.p * g.p * g.p;
+    const long long s_rhs = rhs_kind == RHS_LOAD ? nrhs * p3 : (long long)nrhs * m;
+    Work<T> w = carve<T>(F->P, F->buf, nbox);
+    HPS_CUDA_TRY(cudaMemcpyAsync(status, F->d_fstatus, sizeof(int) * nbox, cudaMemcpyDeviceToDevice, st));
+    launch_load_rhs<T>(g, nbox, rhs_kind, nrhs, rhs, s_rhs, w.M, F->P.ldm, w.sM, status, st);
+    double* X;
+    long long ldx, sX;
+    if constexpr (sizeof(T) == 8) {
+        lu_forward<double>(F->P, w, nbox, n, nrhs, nullptr, st);
+        lu_backward<double>(F->P, w, nbox, n, nrhs, nullptr, st);
+        X = reinterpret_cast<double*>(w.M) + n;
+        ldx = F->P.ldm;
+        sX = w.sM;
+    } else {
+        if (F->P.tc) {
+            tc_reset_abort(st);
+            if (!tc_lu_forward(F->P, w, nbox, n, nrhs, nullptr, st)) return HPS_ECUDA;
+            if (!tc_lu_backward(F->P, w, nbox, n, nrhs, nullptr, st)) return HPS_ECUDA;
+        } else {
+            lu_forward<float>(F->P, w, nbox, n, nrhs, nullptr, st);
+            lu_backward<float>(F->P, w, nbox, n, nrhs, nullptr, st);
+        }
+        X = w.X;
+        ldx = nrhs;
+        sX = w.sX;
+        CallSpec cs;
+        cs.rhs_kind = rhs_kind;
+        cs.r = nrhs;
+        cs.rhs = rhs;
+        cs.s_rhs = s_rhs;
+        cs.zero_row_box = -1;
+        cs.kappa_dev = nullptr;
+        cs.kappa = F->kappa;
+        HPS_CUDA_TRY(cudaMemsetAsync(F->d_iters, 0, sizeof(int) * nbox, st));
+        HPS_CUDA_TRY(cudaMemsetAsync(F->d_relcorr, 0, sizeof(double) * nbox, st));
+        hps_status rc = refine_chunk(F->ctx, g, cs, F->P, w, nbox, nullptr, X, ldx, sX, status, F->d_iters,
+                                     F->d_relcorr, st, true);
+        if (rc != HPS_OK) return rc;
+    }
+    if (rhs_kind == RHS_LOAD) {
+        launch_transpose_add(X, ldx, sX, n, nrhs, nullptr, out0, nbox, st);
+        launch_dn(g, nbox, X, ldx, sX, nrhs, out1, (long long)nrhs * m, 1, 0, st);
+    } else {
+        launch_transpose_add(X, ldx, sX, n, nrhs, vadd, out0, nbox, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+hps_status factors_run(hps_leaf_factors* F, int rhs_kind, int nrhs, const double* rhs, const double* vadd,
+                       double* out0, double* out1, int* box_status, void* stream)
+{
+    hps_ctx* ctx = F->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope prof_scope(ctx);
+    int* status = box_status ? box_status : F->d_status;
+    hps_status rc = F->prec == HPS_FP64
+                        ? factors_solve<double>(F, rhs_kind, nrhs, rhs, vadd, out0, out1, status, st)
+                        : factors_solve<float>(F, rhs_kind, nrhs, rhs, vadd, out0, out1, status, st);
+    if (rc != HPS_OK) return rc;
+    if (!ctx->sync) return HPS_OK;
+    HPS_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> h(F->nbox);
+    HPS_CUDA_TRY(cudaMemcpy(h.data(), status, sizeof(int) * F->nbox, cudaMemcpyDeviceToHost));
+    for (int v : h)
+        if (v) return (hps_status)v;
+    return HPS_OK;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1027,6 +1162,99 @@ hps_status hps_leaf_reconstruct(hps_ctx* ctx, const hps_leaf_kind* kind, int nbo
     j.ui = ui;
     j.vadd = v;
     return run_single(ctx, j, kind, prec, box_status, stream);
+}
+
+
+hps_status hps_leaf_factor(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const double* b, int nrhs_max,
+                           hps_precision prec, int* box_status, void* stream, hps_leaf_factors** out)
+{
+    if (!out) return HPS_EINVAL;
+    *out = nullptr;
+    if (!ctx || nbox < 1 || nrhs_max < 1 || nrhs_max > 256 || !b) return HPS_EINVAL;
+    hps_status rc = check_kind(kind);
+    if (rc != HPS_OK) return rc;
+    if (prec != HPS_FP64 && prec != HPS_FP32_IR && prec != HPS_BF16_IR) return HPS_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope prof_scope(ctx);
+    hps::Geometry* g = nullptr;
+    rc = get_geometry(ctx, kind->p, kind->h, &g);
+    if (rc != HPS_OK) return rc;
+    Job j;
+    j.g = g;
+    j.nbox = nbox;
+    j.rhs_kind = RHS_LOAD;
+    j.nload = nrhs_max;
+    hps_leaf_factors* F = new hps_leaf_factors;
+    F->ctx = ctx;
+    F->g = g;
+    F->P = job_plan(ctx, j, prec);
+    F->prec = prec;
+    F->nbox = nbox;
+    F->nrhs_max = nrhs_max;
+    F->kappa = kind->kappa;
+    const size_t bytes = F->P.per_box * (size_t)nbox;
+    if (cudaMalloc(&F->buf, bytes) != cudaSuccess || cudaMalloc(&F->d_fstatus, sizeof(int) * nbox) != cudaSuccess ||
+        cudaMalloc(&F->d_status, sizeof(int) * nbox) != cudaSuccess ||
+        cudaMalloc(&F->d_iters, sizeof(int) * nbox) != cudaSuccess ||
+        cudaMalloc(&F->d_relcorr, sizeof(double) * nbox) != cudaSuccess) {
+        cudaGetLastError();
+        hps_leaf_factors_destroy(F);
+        return HPS_ENOMEM;
+    }
+    rc = prec == HPS_FP64 ? factors_factor<double>(F, b, st) : factors_factor<float>(F, b, st);
+    if (rc == HPS_OK && box_status)
+        rc = cudaMemcpyAsync(box_status, F->d_fstatus, sizeof(int) * nbox, cudaMemcpyDeviceToDevice, st) ==
+                     cudaSuccess
+                 ? HPS_OK
+                 : HPS_ECUDA;
+    if (rc == HPS_OK && ctx->sync) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = HPS_ECUDA;
+        else {
+            std::vector<int> h(nbox);
+            if (cudaMemcpy(h.data(), F->d_fstatus, sizeof(int) * nbox, cudaMemcpyDeviceToHost) != cudaSuccess)
+                rc = HPS_ECUDA;
+            for (int v : h)
+                if (rc == HPS_OK && v) rc = (hps_status)v;
+            if (rc != HPS_OK && rc != HPS_ECUDA) {   // a box failed: the factors still exist
+                *out = F;
+                return rc;
+            }
+        }
+    }
+    if (rc != HPS_OK) {
+        hps_leaf_factors_destroy(F);
+        return rc;
+    }
+    *out = F;
+    return HPS_OK;
+}
+
+hps_status hps_leaf_solve_factored(hps_leaf_factors* F, int nrhs, const double* f, double* v, double* h,
+                                   int* box_status, void* stream)
+{
+    if (!F || nrhs < 1 || nrhs > F->nrhs_max || !f || !v || !h) return HPS_EINVAL;
+    return factors_run(F, RHS_LOAD, nrhs, f, nullptr, v, h, box_status, stream);
+}
+
+hps_status hps_leaf_reconstruct_factored(hps_leaf_factors* F, int nrhs, const double* v, const double* ub,
+                                         double* ui, int* box_status, void* stream)
+{
+    if (!F || nrhs < 1 || nrhs > F->nrhs_max || !ub || !ui) return HPS_EINVAL;
+    return factors_run(F, RHS_TRACE, nrhs, ub, v, ui, nullptr, box_status, stream);
+}
+
+void hps_leaf_factors_destroy(hps_leaf_factors* F)
+{
+    if (!F) return;
+    if (F->ctx) cudaSetDevice(F->ctx->device);
+    cudaFree(F->buf);
+    cudaFree(F->d_fstatus);
+    cudaFree(F->d_status);
+    cudaFree(F->d_iters);
+    cudaFree(F->d_relcorr);
+    delete F;
 }
 
 hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* groups, hps_precision prec,

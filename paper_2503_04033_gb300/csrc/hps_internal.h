@@ -251,6 +251,12 @@ template <typename TS>
 void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
                     double* X, long long ldx, long long sX, int nbox, cudaStream_t st, double* xnorm = nullptr);
 
+// M's right-hand-side columns n .. n + nrhs (LOAD: f_i, TRACE: -A_ib u_b), the
+// factors in M's first n columns left as they are.
+template <typename T>
+void launch_load_rhs(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                     T* M, long long ldm, long long sM, int* status, cudaStream_t st);
+
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,

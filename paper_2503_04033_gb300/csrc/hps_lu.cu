@@ -187,6 +187,39 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
     }
 }
 
+// The right-hand-side columns n .. n + nrhs of M alone, for solves with a
+// stored factorisation: f_i (LOAD) or -A_ib u_b (TRACE) per column, the rest
+// of M (the factors) untouched.  Thread per (row, column), rows over the grid.
+template <typename T>
+__global__ void k_load_rhs(int p, int n, int nrhs, const double* __restrict__ D2, int rhs_kind,
+                           const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M, long long ldm,
+                           long long sM, int* status)
+{
+    const int box = blockIdx.y;
+    const int q = p - 2, qq = q * q, pp = p * p;
+    const double* D2x = D2;
+    const double* D2y = D2 + pp;
+    const double* D2z = D2 + 2 * pp;
+    const long long total = (long long)n * nrhs;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / nrhs), cf = (int)(idx - (long long)r * nrhs);
+        const int i = r % q + 1, j = (r / q) % q + 1, k = r / qq + 1;
+        double v;
+        if (rhs_kind == RHS_LOAD) {
+            v = __ldg(rhs + box * s_rhs + (long long)cf * p * pp + i + p * j + pp * k);
+        } else {
+            const double* ub = rhs + box * s_rhs + (long long)cf * 6 * qq;
+            const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
+            v = __ldg(D2x + i * p) * ub[0 * qq + sx] + __ldg(D2x + i * p + p - 1) * ub[1 * qq + sx]
+              + __ldg(D2y + j * p) * ub[2 * qq + sy] + __ldg(D2y + j * p + p - 1) * ub[3 * qq + sy]
+              + __ldg(D2z + k * p) * ub[4 * qq + sz] + __ldg(D2z + k * p + p - 1) * ub[5 * qq + sz];
+        }
+        if (!isfinite(v)) status[box] = HPS_EINVAL;
+        M[box * sM + (long long)r * ldm + n + cf] = T(v);
+    }
+}
+
 // ---------------------------------------------------------------- panel
 
 // Arg-max of |value| over the CTA with ties to the lowest index.
@@ -1340,6 +1373,17 @@ void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, 
 }
 
 template <typename T>
+void launch_load_rhs(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                     T* M, long long ldm, long long sM, int* status, cudaStream_t st)
+{
+    const long long total = (long long)g.n * nrhs;
+    dim3 grd((unsigned)std::min<long long>((total + 255) / 256, 256), (unsigned)nbox);
+    prof_begin(KC_BUILD, st);
+    k_load_rhs<T><<<grd, 256, 0, st>>>(g.p, g.n, nrhs, g.dD2, rhs_kind, rhs_src, s_rhs, M, ldm, sM, status);
+    prof_end(KC_BUILD, st, 0.0, (double)nbox * total * (8.0 + sizeof(T)));
+}
+
+template <typename T>
 void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int ib,
                   int* perm, long long sP, T* Ftop, long long ldf, long long sF,
                   T* Btop, long long ldb, long long sB, int* status, const int* skip,
@@ -1657,6 +1701,10 @@ template void launch_build_aug<float>(const Geometry&, double, const double*, in
 template void launch_build_aug<double>(const Geometry&, double, const double*, int, const double*, long long, int,
                                        int, const double*, long long, double*, long long, long long, int*, int,
                                        cudaStream_t);
+template void launch_load_rhs<float>(const Geometry&, int, int, int, const double*, long long, float*, long long,
+                                     long long, int*, cudaStream_t);
+template void launch_load_rhs<double>(const Geometry&, int, int, int, const double*, long long, double*, long long,
+                                      long long, int*, cudaStream_t);
 template void launch_panel<float>(float*, long long, long long, int, int, int, int, int*, long long, float*,
                                   long long, long long, float*, long long, long long, int*, const int*, int,
                                   cudaStream_t);
