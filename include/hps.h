@@ -339,6 +339,16 @@ hps_status hps_leaf_reconstruct_factored(hps_leaf_factors* factors, int nrhs, co
                                          double* ui, int* box_status, void* stream);
 void hps_leaf_factors_destroy(hps_leaf_factors* factors);
 
+/* The collocation operator applied to full nodal fields: out = A u at every
+ * interior node of each box, the interior rows of Eq. 2 (-Laplacian by the
+ * three grid lines through the node, minus kappa^2 b u), and 0 at the face,
+ * edge and corner nodes.  u and out: device [nbox][nfield][p^3] in node order
+ * (edge and corner values of u are not read), b as in hps_leaf_build_dtn.
+ * Time stepping uses it for the right-hand side (I + dt/2 A) u^n of a
+ * Crank-Nicolson step (Sec. 4.4).  HPS_EINVAL for bad sizes or NULL arrays. */
+hps_status hps_leaf_apply(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int nfield, const double* b,
+                          const double* u, double* out, void* stream);
+
 /* Optional per-kernel timing.  hps_profile_enable(ctx, 1) makes the leaf calls
  * bracket every kernel launch with CUDA events on the caller's stream and
  * record each launch's algorithmic flops (2 M N K for an update product, the

@@ -140,6 +140,19 @@ def leaf_matrix(p: int, h, kappa: float, b: np.ndarray) -> np.ndarray:
     return A
 
 
+def apply_interior(p: int, h, kappa: float, b: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """A u at the interior nodes for a full nodal field u [p^3] (grid order):
+    the interior rows of the kept-node collocation matrix (Eq. 2), applied
+    to u's interior and face values; 0 at every other node."""
+    from .global_solve import face_node_grid_indices, interior_grid_indices
+    n, m = sizes(p)
+    ii, fi = interior_grid_indices(p), face_node_grid_indices(p)
+    A = leaf_matrix(p, h, kappa, b)
+    out = np.zeros(p ** 3)
+    out[ii] = A[:n, :] @ np.concatenate([u[ii], u[fi]])
+    return out
+
+
 def split_blocks(p: int, A: np.ndarray):
     n, m = sizes(p)
     Aii, Aib, Abi, Abb = (np.empty(s) for s in ((n, n), (n, m), (m, n), (m, m)))

@@ -136,16 +136,23 @@ def hps_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn):
     b_fn, f_fn, g_fn map an [N,3] coordinate array to values.  Returns a dict
     with the interface solution, per-box interior solutions and coordinates.
     """
+    p = grid.p
+    xyz = [node_coords(p, grid.box_lo(box), grid.h) for box in range(grid.nbox)]
+    g_dir = g_fn(grid.dirichlet_coords()) if grid.n_dir else np.zeros(0)
+    return hps_solve_boxes(grid, kappa, [b_fn(x) for x in xyz], [f_fn(x) for x in xyz], g_dir)
+
+
+def hps_solve_boxes(grid: InterfaceGrid, kappa: float, b_boxes, f_boxes, g_dir):
+    """hps_solve with b and f given per box as nodal arrays [p^3] (grid order)
+    and the Dirichlet values g_dir [n_dir]."""
     p, (n, m) = grid.p, sizes(grid.p)
     nbox = grid.nbox
     rows, cols, vals = [], [], []
     rhs = np.zeros(grid.n_iface)
-    g_dir = g_fn(grid.dirichlet_coords()) if grid.n_dir else np.zeros(0)
     S_all, v_all, maps = [], [], []
     for box in range(nbox):
-        xyz = node_coords(p, grid.box_lo(box), grid.h)
-        b = b_fn(xyz)
-        f = f_fn(xyz)
+        b = b_boxes[box]
+        f = f_boxes[box]
         T, S, info = leaf_dtn(p, grid.h, kappa, b)
         assert info == 0, f"box {box}: singular A_ii"
         v, hf, info = leaf_particular(p, grid.h, kappa, b, f[None, :])
@@ -192,13 +199,14 @@ def interior_coords(grid: InterfaceGrid) -> np.ndarray:
     return np.stack([node_coords(p, grid.box_lo(b), grid.h)[ii] for b in range(grid.nbox)])
 
 
-def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn):
+def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn, f_boxes=None):
     """Brute force: the full collocation system, assembled and solved densely.
 
     Unknowns: every box's interior nodes, then interface nodes, then Dirichlet
     nodes.  Rows: each box's interior rows of A^tau (Eq. 3); on each shared
     face node the sum of both boxes' outward normal derivatives (Eq. 4) = 0;
-    u = g on Dirichlet nodes.
+    u = g on Dirichlet nodes.  f_boxes (per-box nodal arrays) replaces f_fn
+    when given.
     """
     p, (n, m) = grid.p, sizes(grid.p)
     nbox = grid.nbox
@@ -213,7 +221,7 @@ def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn):
         isi, gid = grid.local_to_global(box)
         glob = np.concatenate([box * n + np.arange(n), np.where(isi, off_i + gid, off_d + gid)])
         G[np.ix_(glob[:n], glob)] += A[:n, :]
-        rhs[glob[:n]] += f_fn(xyz)[ii]
+        rhs[glob[:n]] += (f_boxes[box] if f_boxes is not None else f_fn(xyz))[ii]
         fr = np.nonzero(isi)[0]
         G[np.ix_(off_i + gid[fr], glob)] += A[n + fr, :]
     if grid.n_dir:
@@ -223,3 +231,43 @@ def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn):
         rhs[off_d + d] = g_fn(grid.dirichlet_coords())
     u = np.linalg.solve(G, rhs)
     return {"u_int": u[:off_i].reshape(nbox, n), "u_iface": u[off_i:off_d], "u_dir": u[off_d:]}
+
+
+def full_fields(grid: InterfaceGrid, u_int, u_iface, g_dir):
+    """Per-box nodal arrays [nbox, p^3]: interior values from u_int, face values
+    from the interface solution or the Dirichlet data; edges and corners 0
+    (no kept-node row reads them)."""
+    p = grid.p
+    ii, fi = interior_grid_indices(p), face_node_grid_indices(p)
+    out = np.zeros((grid.nbox, p ** 3))
+    for box in range(grid.nbox):
+        isi, gid = grid.local_to_global(box)
+        out[box, ii] = u_int[box]
+        out[box, fi] = np.where(isi, u_iface[np.where(isi, gid, 0)] if grid.n_iface else 0.0,
+                                g_dir[np.where(~isi, gid, 0)] if grid.n_dir else 0.0)
+    return out
+
+
+def crank_nicolson_heat(grid: InterfaceGrid, kappa_d: float, dt: float, nsteps: int, u0_fn):
+    """u_t = kappa_d Lap u on the grid's domain, u = 0 on its boundary, by the
+    Crank-Nicolson steps of Sec. 4.4 with the HPS solve of every step.
+
+    With c = 2 / (dt kappa_d) a step is (c - Lap) u^{n+1} = 2 c u^n - (c - Lap) u^n,
+    i.e. the leaf operator -Lap - kappa^2 b with kappa^2 = c and b = -1, whose
+    interior rows apply_interior evaluates for the right-hand side.  Returns
+    the interior and interface values after nsteps (and the full fields).
+    """
+    from . import apply_interior
+    p = grid.p
+    c = 2.0 / (dt * kappa_d)
+    kappa = float(np.sqrt(c))
+    b = -np.ones(p ** 3)
+    xyz = [node_coords(p, grid.box_lo(box), grid.h) for box in range(grid.nbox)]
+    u = np.stack([u0_fn(x) for x in xyz])
+    g_dir = np.zeros(grid.n_dir)
+    res = None
+    for _ in range(nsteps):
+        f = [2.0 * c * u[box] - apply_interior(p, grid.h, kappa, b, u[box]) for box in range(grid.nbox)]
+        res = hps_solve_boxes(grid, kappa, [b] * grid.nbox, f, g_dir)
+        u = full_fields(grid, res["u_int"], res["u_iface"], g_dir)
+    return {"u_int": res["u_int"], "u_iface": res["u_iface"], "u_full": u, "kappa": kappa, "c": c}

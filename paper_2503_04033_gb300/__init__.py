@@ -26,7 +26,7 @@ __all__ = [
     "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_TC_PAIRS", "HPS_OPT_LU_PAIRS", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
-    "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy",
+    "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -44,7 +44,7 @@ EXPORTED_SYMBOLS = (
     "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
-    "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy",
+    "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
 )
 
 # Kernel classes of hps_profile_get.
@@ -112,6 +112,7 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_solve_factored": (i, [vp, i, vp, vp, vp, vp, vp]),
         "hps_leaf_reconstruct_factored": (i, [vp, i, vp, vp, vp, vp, vp]),
         "hps_leaf_factors_destroy": (None, [vp]),
+        "hps_leaf_apply": (i, [vp, kp, i, i, vp, vp, vp, vp]),
         "hps_assemble_interface_blocks": (i, [i, ip, dp, i64p, i64p, i64p, dp, i64p, i64p, i64p, dp, i64p, i64p]),
         "hps_last_refinement": (i, [vp, i, ip, dp]),
         "hps_profile_enable": (i, [vp, i]),
@@ -287,6 +288,13 @@ def hps_leaf_reconstruct_factored(factors, nrhs: int, v, ub, ui, box_status=None
         factors, int(nrhs), _ptr(v, f64), _ptr(ub, f64), _ptr(ui, f64),
         _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
         _stream(stream)), "hps_leaf_reconstruct_factored")
+
+
+def hps_leaf_apply(ctx, kind: LeafKind, nbox: int, nfield: int, b, u, out, stream=None) -> None:
+    """out = A u at the interior nodes of full nodal fields [nbox, nfield, p^3]."""
+    f64 = _f64() if not isinstance(u, int) else None
+    _check(load_library().hps_leaf_apply(ctx, ctypes.byref(kind), int(nbox), int(nfield), _ptr(b, f64), _ptr(u, f64),
+                                         _ptr(out, f64), _stream(stream)), "hps_leaf_apply")
 
 
 def hps_leaf_factors_destroy(factors) -> None:

@@ -1245,6 +1245,25 @@ hps_status hps_leaf_reconstruct_factored(hps_leaf_factors* F, int nrhs, const do
     return factors_run(F, RHS_TRACE, nrhs, ub, v, ui, nullptr, box_status, stream);
 }
 
+hps_status hps_leaf_apply(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int nfield, const double* b,
+                          const double* u, double* out, void* stream)
+{
+    if (!ctx || nbox < 0 || nfield < 1) return HPS_EINVAL;
+    hps_status rc = check_kind(kind);
+    if (rc != HPS_OK) return rc;
+    if (nbox == 0) return HPS_OK;
+    if (!b || !u || !out) return HPS_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    HPS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope prof_scope(ctx);
+    Geometry* g = nullptr;
+    rc = get_geometry(ctx, kind->p, kind->h, &g);
+    if (rc != HPS_OK) return rc;
+    launch_apply_op(*g, kind->kappa, nbox, nfield, b, u, out, st);
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
 void hps_leaf_factors_destroy(hps_leaf_factors* F)
 {
     if (!F) return;

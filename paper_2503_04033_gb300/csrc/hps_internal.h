@@ -251,6 +251,10 @@ template <typename TS>
 void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols,
                     double* X, long long ldx, long long sX, int nbox, cudaStream_t st, double* xnorm = nullptr);
 
+// out = A u at the interior nodes of full nodal fields (zero at the others).
+void launch_apply_op(const Geometry& g, double kappa, int nbox, int nfield, const double* b, const double* u,
+                     double* out, cudaStream_t st);
+
 // M's right-hand-side columns n .. n + nrhs (LOAD: f_i, TRACE: -A_ib u_b), the
 // factors in M's first n columns left as they are.
 template <typename T>

@@ -220,6 +220,38 @@ __global__ void k_load_rhs(int p, int n, int nrhs, const double* __restrict__ D2
     }
 }
 
+// out = A u at the interior nodes of full nodal fields u (all p^3 values of a
+// box): the interior rows of Eq. 2's collocation, -(D2x + D2y + D2z) along the
+// three grid lines through each node, minus kappa^2 b u; zero at the other
+// nodes.  One CTA per (field, box), the field staged in shared memory.
+__global__ void k_apply_op(int p, int nfield, const double* __restrict__ D2, double kappa2,
+                           const double* __restrict__ b, long long sb, const double* __restrict__ u,
+                           double* __restrict__ out)
+{
+    extern __shared__ double us[];
+    const int c = blockIdx.x, box = blockIdx.y;
+    const int pp = p * p, p3 = pp * p;
+    const double* ub = u + ((long long)box * nfield + c) * p3;
+    double* ob = out + ((long long)box * nfield + c) * p3;
+    for (int idx = threadIdx.x; idx < p3; idx += blockDim.x) us[idx] = ub[idx];
+    __syncthreads();
+    const double* D2x = D2;
+    const double* D2y = D2 + pp;
+    const double* D2z = D2 + 2 * pp;
+    for (int idx = threadIdx.x; idx < p3; idx += blockDim.x) {
+        const int i = idx % p, j = (idx / p) % p, k = idx / pp;
+        if (i == 0 || j == 0 || k == 0 || i == p - 1 || j == p - 1 || k == p - 1) {
+            ob[idx] = 0.0;
+            continue;
+        }
+        double acc = 0.0;
+        for (int l = 0; l < p; ++l)
+            acc += __ldg(D2x + i * p + l) * us[l + p * j + pp * k] + __ldg(D2y + j * p + l) * us[i + p * l + pp * k] +
+                   __ldg(D2z + k * p + l) * us[i + p * j + pp * l];
+        ob[idx] = -acc - kappa2 * __ldg(b + box * sb + idx) * us[idx];
+    }
+}
+
 // ---------------------------------------------------------------- panel
 
 // Arg-max of |value| over the CTA with ties to the lowest index.
@@ -1370,6 +1402,22 @@ void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, 
     k_build_aug<T><<<grd, 256, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind,
                                         rhs_src, s_rhs, M, ldm, sM, status, zero_row_box);
     prof_end(KC_BUILD, st, 0.0, (double)nbox * g.n * ldm * sizeof(T));
+}
+
+void launch_apply_op(const Geometry& g, double kappa, int nbox, int nfield, const double* b, const double* u,
+                     double* out, cudaStream_t st)
+{
+    const size_t smem = (size_t)g.p * g.p * g.p * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_apply_op, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = true;
+    }
+    dim3 grd((unsigned)nfield, (unsigned)nbox);
+    prof_begin(KC_MISC, st);
+    k_apply_op<<<grd, 256, smem, st>>>(g.p, nfield, g.dD2, kappa * kappa, b, (long long)g.p * g.p * g.p, u, out);
+    prof_end(KC_MISC, st, (double)nbox * nfield * g.n * (6.0 * g.p + 3.0),
+             (double)nbox * nfield * g.p * g.p * g.p * 24.0);
 }
 
 template <typename T>

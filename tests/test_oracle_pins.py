@@ -279,6 +279,60 @@ def test_manufactured_spectral_convergence():
     assert errs[-1] < 2e-10, errs
 
 
+# ------------------------------------------------------------------ time stepping (Sec. 4.4)
+
+@pytest.mark.parametrize("kappa", [0.0, 3.0])
+def test_apply_interior_exact_on_polynomials(kappa):
+    """A u at the interior nodes for a polynomial field of degree < p in each
+    variable: the collocation Laplacian is exact there, so A u = -Lap u - kappa^2 b u
+    to rounding (an independent closed form; a wrong sign, axis or scale of a
+    line term fails it)."""
+    p, h, lo = 8, np.array([0.5, 0.4, 0.3]), np.array([0.1, 0.2, 0.3])
+    xyz = oracle.node_coords(p, lo, h)
+    x, y, z = xyz.T
+    u = x ** 2 * y + z ** 3 + x * y * z - 2.0 * y ** 4
+    lap = 2.0 * y + 6.0 * z - 24.0 * y ** 2
+    b = np.cos(x) + 2.0
+    out = oracle.apply_interior(p, h, kappa, b, u)
+    ii = gs.interior_grid_indices(p)
+    exp = -lap - kappa ** 2 * b * u
+    assert np.abs(out[ii] - exp[ii]).max() < 1e-11 * np.abs(exp[ii]).max()
+    mask = np.ones(p ** 3, dtype=bool)
+    mask[ii] = False
+    assert np.all(out[mask] == 0.0)
+
+
+def test_crank_nicolson_step_equals_dense_bruteforce():
+    """One Crank-Nicolson step through the two-level HPS solve equals the dense
+    solve of the same global collocation system with the same right-hand
+    side."""
+    grid = gs.InterfaceGrid(6, (2, 1, 2), L=(1.0, 0.5, 1.0))
+    u0 = lambda X: np.sin(np.pi * X[:, 0]) * np.sin(2 * np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
+    r = gs.crank_nicolson_heat(grid, 0.1, 0.05, 1, u0)
+    p, b = grid.p, -np.ones(grid.p ** 3)
+    xyz = [oracle.node_coords(p, grid.box_lo(bx), grid.h) for bx in range(grid.nbox)]
+    f = [2 * r["c"] * u0(x) - oracle.apply_interior(p, grid.h, r["kappa"], b, u0(x)) for x in xyz]
+    d = gs.dense_global_solve(grid, r["kappa"], lambda X: -np.ones(len(X)), None, lambda X: 0 * X[:, 0],
+                              f_boxes=f)
+    scale = np.abs(d["u_int"]).max()
+    assert np.abs(r["u_int"] - d["u_int"]).max() < 1e-11 * scale
+    assert np.abs(r["u_iface"] - d["u_iface"]).max() < 1e-11 * scale
+
+
+def test_crank_nicolson_second_order_in_time():
+    """u_t = kappa_d Lap u on the unit cube with u = 0 on its boundary: from
+    u0 = sin(pi x) sin(pi y) sin(pi z) the exact solution decays as
+    exp(-3 pi^2 kappa_d t).  At p = 10 the spatial error is far below the time
+    error, so halving dt divides the error by four (second order)."""
+    grid = gs.InterfaceGrid(10, (2, 2, 2))
+    u0 = lambda X: np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
+    kd, T = 0.05, 0.5
+    ex = np.exp(-3 * np.pi ** 2 * kd * T) * u0(gs.interior_coords(grid).reshape(-1, 3)).reshape(grid.nbox, -1)
+    err = [np.abs(gs.crank_nicolson_heat(grid, kd, T / s, s, u0)["u_int"] - ex).max() for s in (5, 10)]
+    assert 3.8 < err[0] / err[1] < 4.2, err
+    assert err[1] < 2e-4, err
+
+
 # ------------------------------------------------------------------ planted mistakes
 
 def test_pins_catch_planted_mistakes():
