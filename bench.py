@@ -97,7 +97,8 @@ def parse_args():
     ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
                     help="hps_set_option before timing, e.g. TC_PAIRS=1 (name without HPS_OPT_)")
-    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored"), default="fourier16",
+    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep"),
+                    default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
     ap.add_argument("--train-boxes", type=int, default=20000)
@@ -830,6 +831,134 @@ def run_factored(args):
     print(json.dumps(line), flush=True)
 
 
+def run_timestep(args):
+    """Crank-Nicolson steps of the heat equation u_t = kappa_d Lap u on the unit
+    cube (u = 0 on its boundary), 4 x 4 x 4 boxes at p = 12, as in Sec. 4.4:
+    T and the interior factorisations built once, a host sparse LU of the
+    interface system factored once; per step one hps_leaf_apply, one
+    particular solve and one reconstruction with the stored factors on the
+    GPU, and the interface solve on the host.  The final state is compared
+    with the exact decaying solution."""
+    import time as _time
+    import torch
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import paper_2503_04033_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p, nbx, kd, dt = 12, 4, 0.05, 0.01
+    nbox = nbx ** 3
+    h = np.full(3, 1.0 / nbx)
+    n, m = H.hps_leaf_sizes(p)
+    q, qq = p - 2, (p - 2) ** 2
+    c = 2.0 / (dt * kd)
+    kind = H.LeafKind(p, h, float(np.sqrt(c)))
+    lows = np.array([[i % nbx, (i // nbx) % nbx, i // (nbx * nbx)] for i in range(nbox)], dtype=np.float64) * h
+    xyz = np.stack([H.hps_leaf_nodes(p, lo, h) for lo in lows])
+    b = torch.full((nbox, p ** 3), -1.0, dtype=torch.float64, device=dev)
+    ctx = H.hps_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = _time.time()
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
+    H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, H.HPS_FP32_IR, None, stream)
+    F = H.hps_leaf_factor(ctx, kind, nbox, b, 1, H.HPS_FP32_IR, None, stream)
+    torch.cuda.synchronize(dev)
+    t_gpu_setup = _time.time() - t0
+    t0 = _time.time()
+    rows, cols, vals, _, _, _, ni, _ = H.hps_assemble_interface_blocks(p, (nbx, nbx, nbx), T.cpu().numpy())
+    lu = spla.splu(sp.coo_matrix((vals, (rows, cols)), shape=(ni, ni)).tocsc())
+    t_host_setup = _time.time() - t0
+    # interface numbering of each box's face nodes (faces of each normal axis
+    # in turn, box-column order, q^2 nodes per face)
+    Fx = (nbx - 1) * nbx * nbx
+    gid = np.full((nbox, m), -1, dtype=np.int64)
+    for bx in range(nbox):
+        cxyz = (bx % nbx, (bx // nbx) % nbx, bx // (nbx * nbx))
+        for f in range(6):
+            axis, side = f // 2, f % 2
+            plane = cxyz[axis] + side
+            if plane == 0 or plane == nbx:
+                continue
+            if axis == 0:
+                fid = (plane - 1) + (nbx - 1) * (cxyz[1] + nbx * cxyz[2])
+            elif axis == 1:
+                fid = Fx + cxyz[0] + nbx * ((plane - 1) + (nbx - 1) * cxyz[2])
+            else:
+                fid = 2 * Fx + cxyz[0] + nbx * (cxyz[1] + nbx * (plane - 1))
+            gid[bx, f * qq:(f + 1) * qq] = fid * qq + np.arange(qq)
+    isi = gid >= 0
+    # node index sets: interior (x fastest) and face nodes (face order)
+    r = np.arange(1, q + 1)
+    kk, jj, ii_ = np.meshgrid(r, r, r, indexing="ij")
+    ii = (ii_ + p * jj + p * p * kk).reshape(-1)
+    fi = []
+    for f in range(6):
+        axis, sv = f // 2, (0 if f % 2 == 0 else p - 1)
+        for bb in range(1, q + 1):
+            for aa in range(1, q + 1):
+                i3 = [aa, bb]
+                i3.insert(axis, sv)
+                fi.append(i3[0] + p * i3[1] + p * p * i3[2])
+    fi = np.asarray(fi)
+    u0 = np.sin(np.pi * xyz[..., 0]) * np.sin(np.pi * xyz[..., 1]) * np.sin(np.pi * xyz[..., 2])
+    u = torch.from_numpy(u0[:, None, :].copy()).to(dev)
+    Au = torch.empty_like(u)
+    v = torch.empty(nbox, 1, n, dtype=torch.float64, device=dev)
+    hf = torch.empty(nbox, 1, m, dtype=torch.float64, device=dev)
+    ui = torch.empty(nbox, 1, n, dtype=torch.float64, device=dev)
+    st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+    ii_d, fi_d = torch.from_numpy(ii).to(dev), torch.from_numpy(fi).to(dev)
+    gid_t = torch.from_numpy(np.where(isi, gid, 0)).to(dev)
+    isi_t = torch.from_numpy(isi).to(dev)
+    nsteps = args.steps * 10
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    gpu_ms, host_s = 0.0, 0.0
+    t_all = _time.time()
+    for step in range(nsteps):
+        ev[0].record(stream)
+        H.hps_leaf_apply(ctx, kind, nbox, 1, b, u, Au, stream)
+        f = (2.0 * c * u - Au).contiguous()
+        H.hps_leaf_solve_factored(F, 1, f, v, hf, st, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        t0 = _time.time()
+        hf_np = hf[:, 0, :].cpu().numpy()
+        rhs = np.zeros(ni)
+        np.add.at(rhs, gid[isi], -hf_np[isi])
+        u_if = lu.solve(rhs)
+        host_s += _time.time() - t0
+        ub = torch.zeros(nbox, m, dtype=torch.float64, device=dev)
+        u_if_d = torch.from_numpy(u_if).to(dev)
+        ub[isi_t] = u_if_d[gid_t[isi_t]]
+        ev[2].record(stream)
+        H.hps_leaf_reconstruct_factored(F, 1, v, ub[:, None, :].contiguous(), ui, st, stream)
+        un = torch.zeros(nbox, p ** 3, dtype=torch.float64, device=dev)
+        un[:, ii_d] = ui[:, 0, :]
+        un[:, fi_d] = ub
+        u = un[:, None, :].contiguous()
+        ev[3].record(stream)
+        torch.cuda.synchronize(dev)
+        gpu_ms += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+    wall = _time.time() - t_all
+    fails = int((st != 0).sum().item())
+    H.hps_leaf_factors_destroy(F)
+    H.hps_destroy(ctx)
+    tend = dt * nsteps
+    exact = np.exp(-3 * np.pi ** 2 * kd * tend) * u0[:, ii]
+    err = float(np.abs(ui[:, 0, :].cpu().numpy() - exact).max())
+    line = {"metric": "Crank-Nicolson heat-equation steps/s (4x4x4 boxes, p=12; leaf work on the GPU, interface LU on the host)",
+            "value": nsteps / wall, "unit": "steps/s", "n_gpus": 1, "steps": nsteps, "warmup": 0,
+            "ms_per_step": 1e3 * wall / nsteps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"u_t = {kd} Lap u on the unit cube, u = 0 on the boundary, u0 = sin(pi x) sin(pi y) "
+                                   f"sin(pi z); {nbox} boxes, p = {p}, dt = {dt}, {nsteps} steps; stored factors "
+                                   f"(FP32 LU + FP64 refinement); {ni} interface unknowns"},
+            "gpu_leaf_ms_per_step": gpu_ms / nsteps, "host_interface_ms_per_step": 1e3 * host_s / nsteps,
+            "setup": {"gpu_dtn_and_factor_s": t_gpu_setup, "host_assembly_and_lu_s": t_host_setup},
+            "max_abs_err_vs_exact": err, "box_failures": fails}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.warmup < 3:
@@ -842,6 +971,8 @@ def main():
         run_learned(args)
     elif args.workload == "factored":
         run_factored(args)
+    elif args.workload == "timestep":
+        run_timestep(args)
     else:
         run_ours(args)
 
