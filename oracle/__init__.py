@@ -64,13 +64,13 @@ def _load():
                 "oc_diff": (None, [c_int, dp]),
                 "oc_node_coords": (None, [c_int, dp, dp, dp]),
                 "oc_kept_index": (c_int, [c_int, c_int, c_int, c_int]),
-                "oc_leaf_matrix": (None, [c_int, dp, c_double, dp, dp]),
+                "oc_leaf_matrix": (None, [c_int, dp, c_double, dp, dp, dp]),
                 "oc_split_blocks": (None, [c_int, dp, dp, dp, dp, dp]),
                 "oc_lu": (c_int, [c_int, dp, ip]),
                 "oc_lu_solve": (None, [c_int, dp, ip, c_int, dp]),
-                "oc_leaf_dtn": (c_int, [c_int, dp, c_double, dp, dp, dp]),
-                "oc_leaf_particular": (c_int, [c_int, dp, c_double, dp, c_int, dp, dp, dp]),
-                "oc_leaf_reconstruct": (c_int, [c_int, dp, c_double, dp, c_int, dp, dp, dp]),
+                "oc_leaf_dtn": (c_int, [c_int, dp, c_double, dp, dp, dp, dp]),
+                "oc_leaf_particular": (c_int, [c_int, dp, c_double, dp, dp, c_int, dp, dp, dp]),
+                "oc_leaf_reconstruct": (c_int, [c_int, dp, c_double, dp, dp, c_int, dp, dp, dp]),
                 "oc_batch_dtn": (None, [c_int, dp, c_double, c_int, dp, dp, dp, ip, c_int]),
                 "oc_max_threads": (c_int, []),
             }
@@ -133,21 +133,32 @@ def kept_index(p: int, i: int, j: int, k: int) -> int:
     return int(_load().oc_kept_index(p, i, j, k))
 
 
-def leaf_matrix(p: int, h, kappa: float, b: np.ndarray) -> np.ndarray:
+def _beta(beta, p: int):
+    """None, or the velocity-like field as a contiguous [3, p^3] array."""
+    if beta is None:
+        return None
+    return np.ascontiguousarray(np.asarray(beta, np.float64).reshape(3, p ** 3))
+
+
+def leaf_matrix(p: int, h, kappa: float, b: np.ndarray, beta=None) -> np.ndarray:
+    """Kept-node collocation matrix of -Lap u + div(beta u) - kappa^2 b u
+    (beta None: no first-order term)."""
     n, m = sizes(p)
     A = np.empty((n + m, n + m))
-    _load().oc_leaf_matrix(p, _dp(_h3(h)), float(kappa), _dp(np.ascontiguousarray(b, np.float64)), _dp(A))
+    bt = _beta(beta, p)
+    _load().oc_leaf_matrix(p, _dp(_h3(h)), float(kappa), _dp(np.ascontiguousarray(b, np.float64)),
+                           _dp(bt) if bt is not None else None, _dp(A))
     return A
 
 
-def apply_interior(p: int, h, kappa: float, b: np.ndarray, u: np.ndarray) -> np.ndarray:
+def apply_interior(p: int, h, kappa: float, b: np.ndarray, u: np.ndarray, beta=None) -> np.ndarray:
     """A u at the interior nodes for a full nodal field u [p^3] (grid order):
     the interior rows of the kept-node collocation matrix (Eq. 2), applied
     to u's interior and face values; 0 at every other node."""
     from .global_solve import face_node_grid_indices, interior_grid_indices
     n, m = sizes(p)
     ii, fi = interior_grid_indices(p), face_node_grid_indices(p)
-    A = leaf_matrix(p, h, kappa, b)
+    A = leaf_matrix(p, h, kappa, b, beta)
     out = np.zeros(p ** 3)
     out[ii] = A[:n, :] @ np.concatenate([u[ii], u[fi]])
     return out
@@ -178,17 +189,17 @@ def lu_solve(LU: np.ndarray, piv: np.ndarray, B: np.ndarray) -> np.ndarray:
     return X.reshape(B.shape)
 
 
-def leaf_dtn(p: int, h, kappa: float, b: np.ndarray, want_S: bool = True):
+def leaf_dtn(p: int, h, kappa: float, b: np.ndarray, want_S: bool = True, beta=None):
     """(T [m,m], S [n,m] or None, info) for one box."""
     n, m = sizes(p)
     T = np.empty((m, m))
     S = np.empty((n, m)) if want_S else None
     info = _load().oc_leaf_dtn(p, _dp(_h3(h)), float(kappa),
-                               _dp(np.ascontiguousarray(b, np.float64)), _dp(T), _dp(S))
+                               _dp(np.ascontiguousarray(b, np.float64)), _dp(_beta(beta, p)), _dp(T), _dp(S))
     return T, S, int(info)
 
 
-def leaf_particular(p: int, h, kappa: float, b: np.ndarray, f: np.ndarray):
+def leaf_particular(p: int, h, kappa: float, b: np.ndarray, f: np.ndarray, beta=None):
     """(v [nrhs,n], h [nrhs,m], info); f is [nrhs, p^3] (or [p^3])."""
     n, m = sizes(p)
     f2 = np.ascontiguousarray(np.atleast_2d(f), np.float64)
@@ -196,19 +207,19 @@ def leaf_particular(p: int, h, kappa: float, b: np.ndarray, f: np.ndarray):
     v = np.empty((nrhs, n))
     hf = np.empty((nrhs, m))
     info = _load().oc_leaf_particular(p, _dp(_h3(h)), float(kappa),
-                                      _dp(np.ascontiguousarray(b, np.float64)), nrhs,
+                                      _dp(np.ascontiguousarray(b, np.float64)), _dp(_beta(beta, p)), nrhs,
                                       _dp(f2), _dp(v), _dp(hf))
     return v, hf, int(info)
 
 
-def leaf_reconstruct(p: int, h, kappa: float, b: np.ndarray, v: np.ndarray, ub: np.ndarray):
+def leaf_reconstruct(p: int, h, kappa: float, b: np.ndarray, v: np.ndarray, ub: np.ndarray, beta=None):
     """(u_i [nrhs,n], info) with u_i = v + S u_b."""
     n, m = sizes(p)
     v2 = np.ascontiguousarray(np.atleast_2d(v), np.float64)
     ub2 = np.ascontiguousarray(np.atleast_2d(ub), np.float64)
     ui = np.empty_like(v2)
     info = _load().oc_leaf_reconstruct(p, _dp(_h3(h)), float(kappa),
-                                       _dp(np.ascontiguousarray(b, np.float64)), v2.shape[0],
+                                       _dp(np.ascontiguousarray(b, np.float64)), _dp(_beta(beta, p)), v2.shape[0],
                                        _dp(v2), _dp(ub2), _dp(ui))
     return ui, int(info)
 

@@ -142,9 +142,10 @@ def hps_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn):
     return hps_solve_boxes(grid, kappa, [b_fn(x) for x in xyz], [f_fn(x) for x in xyz], g_dir)
 
 
-def hps_solve_boxes(grid: InterfaceGrid, kappa: float, b_boxes, f_boxes, g_dir):
+def hps_solve_boxes(grid: InterfaceGrid, kappa: float, b_boxes, f_boxes, g_dir, beta_boxes=None):
     """hps_solve with b and f given per box as nodal arrays [p^3] (grid order)
-    and the Dirichlet values g_dir [n_dir]."""
+    and the Dirichlet values g_dir [n_dir]; beta_boxes (per box [3, p^3], or
+    None) adds the first-order term div(beta u) to the operator."""
     p, (n, m) = grid.p, sizes(grid.p)
     nbox = grid.nbox
     rows, cols, vals = [], [], []
@@ -153,9 +154,10 @@ def hps_solve_boxes(grid: InterfaceGrid, kappa: float, b_boxes, f_boxes, g_dir):
     for box in range(nbox):
         b = b_boxes[box]
         f = f_boxes[box]
-        T, S, info = leaf_dtn(p, grid.h, kappa, b)
+        beta = beta_boxes[box] if beta_boxes is not None else None
+        T, S, info = leaf_dtn(p, grid.h, kappa, b, beta=beta)
         assert info == 0, f"box {box}: singular A_ii"
-        v, hf, info = leaf_particular(p, grid.h, kappa, b, f[None, :])
+        v, hf, info = leaf_particular(p, grid.h, kappa, b, f[None, :], beta=beta)
         assert info == 0
         isi, gid = grid.local_to_global(box)
         ri = np.nonzero(isi)[0]
@@ -199,14 +201,14 @@ def interior_coords(grid: InterfaceGrid) -> np.ndarray:
     return np.stack([node_coords(p, grid.box_lo(b), grid.h)[ii] for b in range(grid.nbox)])
 
 
-def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn, f_boxes=None):
+def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn, f_boxes=None, beta_boxes=None):
     """Brute force: the full collocation system, assembled and solved densely.
 
     Unknowns: every box's interior nodes, then interface nodes, then Dirichlet
     nodes.  Rows: each box's interior rows of A^tau (Eq. 3); on each shared
     face node the sum of both boxes' outward normal derivatives (Eq. 4) = 0;
     u = g on Dirichlet nodes.  f_boxes (per-box nodal arrays) replaces f_fn
-    when given.
+    when given; beta_boxes adds div(beta u) as in hps_solve_boxes.
     """
     p, (n, m) = grid.p, sizes(grid.p)
     nbox = grid.nbox
@@ -217,7 +219,7 @@ def dense_global_solve(grid: InterfaceGrid, kappa: float, b_fn, f_fn, g_fn, f_bo
     ii = interior_grid_indices(p)
     for box in range(nbox):
         xyz = node_coords(p, grid.box_lo(box), grid.h)
-        A = leaf_matrix(p, grid.h, kappa, b_fn(xyz))
+        A = leaf_matrix(p, grid.h, kappa, b_fn(xyz), beta_boxes[box] if beta_boxes is not None else None)
         isi, gid = grid.local_to_global(box)
         glob = np.concatenate([box * n + np.arange(n), np.where(isi, off_i + gid, off_d + gid)])
         G[np.ix_(glob[:n], glob)] += A[:n, :]
@@ -248,14 +250,16 @@ def full_fields(grid: InterfaceGrid, u_int, u_iface, g_dir):
     return out
 
 
-def crank_nicolson_heat(grid: InterfaceGrid, kappa_d: float, dt: float, nsteps: int, u0_fn):
-    """u_t = kappa_d Lap u on the grid's domain, u = 0 on its boundary, by the
-    Crank-Nicolson steps of Sec. 4.4 with the HPS solve of every step.
+def crank_nicolson_heat(grid: InterfaceGrid, kappa_d: float, dt: float, nsteps: int, u0_fn, vel_fn=None):
+    """u_t = kappa_d Lap u - div(vel u) on the grid's domain (vel_fn None: the
+    heat equation), u = 0 on its boundary, by the Crank-Nicolson steps of
+    Sec. 4.4 with the HPS solve of every step.
 
-    With c = 2 / (dt kappa_d) a step is (c - Lap) u^{n+1} = 2 c u^n - (c - Lap) u^n,
-    i.e. the leaf operator -Lap - kappa^2 b with kappa^2 = c and b = -1, whose
-    interior rows apply_interior evaluates for the right-hand side.  Returns
-    the interior and interface values after nsteps (and the full fields).
+    With c = 2 / (dt kappa_d) and L = c - Lap + div(beta .), beta = vel / kappa_d,
+    a step is L u^{n+1} = 2 c u^n - L u^n, and L is the leaf operator
+    -Lap + div(beta u) - kappa^2 b u with kappa^2 = c and b = -1, whose interior
+    rows apply_interior evaluates for the right-hand side.  Returns the
+    interior and interface values after nsteps (and the full fields).
     """
     from . import apply_interior
     p = grid.p
@@ -263,11 +267,14 @@ def crank_nicolson_heat(grid: InterfaceGrid, kappa_d: float, dt: float, nsteps: 
     kappa = float(np.sqrt(c))
     b = -np.ones(p ** 3)
     xyz = [node_coords(p, grid.box_lo(box), grid.h) for box in range(grid.nbox)]
+    beta = [vel_fn(x).T / kappa_d for x in xyz] if vel_fn is not None else [None] * grid.nbox
     u = np.stack([u0_fn(x) for x in xyz])
     g_dir = np.zeros(grid.n_dir)
     res = None
     for _ in range(nsteps):
-        f = [2.0 * c * u[box] - apply_interior(p, grid.h, kappa, b, u[box]) for box in range(grid.nbox)]
-        res = hps_solve_boxes(grid, kappa, [b] * grid.nbox, f, g_dir)
+        f = [2.0 * c * u[box] - apply_interior(p, grid.h, kappa, b, u[box], beta[box]) for box in range(grid.nbox)]
+        res = hps_solve_boxes(grid, kappa, [b] * grid.nbox, f, g_dir,
+                              beta if vel_fn is not None else None)
         u = full_fields(grid, res["u_int"], res["u_iface"], g_dir)
-    return {"u_int": res["u_int"], "u_iface": res["u_iface"], "u_full": u, "kappa": kappa, "c": c}
+    return {"u_int": res["u_int"], "u_iface": res["u_iface"], "u_full": u, "kappa": kappa, "c": c,
+            "beta": beta}

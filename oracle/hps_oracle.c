@@ -158,8 +158,12 @@ static void physical_d(int p, double h, const double* Dhat, double* D, double* D
  *   face row on side s of axis a (outward normal n = -e_a on the low side,
  *   +e_a on the high side):  (n . e_a) sum_l D_a[e,l] u(... l ...),
  *   e the face's own grid index along a.
- * b holds all p^3 node values; only interior ones enter. */
-void oc_leaf_matrix(int p, const double* h, double kappa, const double* b, double* A)
+ * b holds all p^3 node values; only interior ones enter.  beta (NULL, or
+ * [3][p^3] node values of a velocity-like field) adds the divergence-form
+ * first-order term div(beta u) to the interior rows:
+ *   + sum_i' Dx[i,i'] beta_x(i',j,k) u(i',j,k) + (the same along y and z),
+ * the product rule of collocation differentiation applied to beta_a u. */
+void oc_leaf_matrix(int p, const double* h, double kappa, const double* b, const double* beta, double* A)
 {
     int q = p - 2, n = q * q * q, m = 6 * q * q, N = n + m, e = p - 1;
     double* Dhat = (double*)malloc(sizeof(double) * p * p);
@@ -179,6 +183,14 @@ void oc_leaf_matrix(int p, const double* h, double kappa, const double* b, doubl
                 Ar[oc_kept_index(p, i, j, l)] -= D2[2 * p * p + k * p + l];
             }
             Ar[row] -= kappa * kappa * b[i + p * j + p * p * k];
+            if (beta) {
+                const int P3 = p * p * p;
+                for (int l = 0; l < p; ++l) {
+                    Ar[oc_kept_index(p, l, j, k)] += D[0 * p * p + i * p + l] * beta[0 * P3 + l + p * j + p * p * k];
+                    Ar[oc_kept_index(p, i, l, k)] += D[1 * p * p + j * p + l] * beta[1 * P3 + i + p * l + p * p * k];
+                    Ar[oc_kept_index(p, i, j, l)] += D[2 * p * p + k * p + l] * beta[2 * P3 + i + p * j + p * p * l];
+                }
+            }
         } else {
             int f = (row - n) / (q * q), axis = f / 2;
             double sgn = (f % 2 == 0) ? -1.0 : 1.0;
@@ -306,7 +318,7 @@ static void matmul_add(int r, int s, int t, const double* A, const double* B, co
  *   S = -A_ii^{-1} A_ib      (n x m, row-major; may be NULL),
  *   T = A_bb + A_bi S        (m x m, row-major; may be NULL).
  * Returns 0, or the 1-based zero-pivot position if A_ii is singular. */
-int oc_leaf_dtn(int p, const double* h, double kappa, const double* b, double* T, double* S)
+int oc_leaf_dtn(int p, const double* h, double kappa, const double* b, const double* beta, double* T, double* S)
 {
     int q = p - 2, n = q * q * q, m = 6 * q * q, N = n + m;
     double* A = (double*)malloc(sizeof(double) * (size_t)N * N);
@@ -315,7 +327,7 @@ int oc_leaf_dtn(int p, const double* h, double kappa, const double* b, double* T
     double* Abi = (double*)malloc(sizeof(double) * (size_t)m * n);
     double* Abb = (double*)malloc(sizeof(double) * (size_t)m * m);
     int* piv = (int*)malloc(sizeof(int) * n);
-    oc_leaf_matrix(p, h, kappa, b, A);
+    oc_leaf_matrix(p, h, kappa, b, beta, A);
     oc_split_blocks(p, A, Aii, X, Abi, Abb);           /* X <- A_ib */
     free(A);
     for (size_t e = 0; e < (size_t)n * m; ++e) X[e] = -X[e];   /* X <- -A_ib */
@@ -333,7 +345,7 @@ int oc_leaf_dtn(int p, const double* h, double kappa, const double* b, double* T
  * Algorithm 2, first loop):  v = A_ii^{-1} f_i,  h = A_bi v.
  * f is [nrhs][p^3] (grid order; only interior values enter), v is [nrhs][n],
  * hflux is [nrhs][m]. */
-int oc_leaf_particular(int p, const double* h, double kappa, const double* b, int nrhs,
+int oc_leaf_particular(int p, const double* h, double kappa, const double* b, const double* beta, int nrhs,
                        const double* f, double* v, double* hflux)
 {
     int q = p - 2, n = q * q * q, m = 6 * q * q, N = n + m;
@@ -342,7 +354,7 @@ int oc_leaf_particular(int p, const double* h, double kappa, const double* b, in
     double* Abi = (double*)malloc(sizeof(double) * (size_t)m * n);
     double* X = (double*)malloc(sizeof(double) * (size_t)n * nrhs);
     int* piv = (int*)malloc(sizeof(int) * n);
-    oc_leaf_matrix(p, h, kappa, b, A);
+    oc_leaf_matrix(p, h, kappa, b, beta, A);
     oc_split_blocks(p, A, Aii, NULL, Abi, NULL);
     free(A);
     for (int r = 0; r < n; ++r) {                      /* X[r][c] = f_c(interior node r) */
@@ -370,12 +382,12 @@ int oc_leaf_particular(int p, const double* h, double kappa, const double* b, in
 /* Interior reconstruction (Sec. 2.2 step 4; Algorithm 2, last loop):
  * u_i = v + S u_b with S recomputed as in oc_leaf_dtn.  v, ui are [nrhs][n],
  * ub is [nrhs][m]. */
-int oc_leaf_reconstruct(int p, const double* h, double kappa, const double* b, int nrhs,
+int oc_leaf_reconstruct(int p, const double* h, double kappa, const double* b, const double* beta, int nrhs,
                         const double* v, const double* ub, double* ui)
 {
     int q = p - 2, n = q * q * q, m = 6 * q * q;
     double* S = (double*)malloc(sizeof(double) * (size_t)n * m);
-    int info = oc_leaf_dtn(p, h, kappa, b, NULL, S);
+    int info = oc_leaf_dtn(p, h, kappa, b, beta, NULL, S);
     if (info == 0)
         for (int c = 0; c < nrhs; ++c)
             for (int r = 0; r < n; ++r) {
@@ -402,7 +414,7 @@ void oc_batch_dtn(int p, const double* h, double kappa, int nbox, const double* 
 #pragma omp parallel for schedule(dynamic) num_threads(nthreads)
 #endif
     for (int bx = 0; bx < nbox; ++bx)
-        status[bx] = oc_leaf_dtn(p, h, kappa, b + bx * P3,
+        status[bx] = oc_leaf_dtn(p, h, kappa, b + bx * P3, NULL,
                                  T ? T + (size_t)bx * m * m : NULL,
                                  S ? S + (size_t)bx * n * m : NULL);
     (void)nthreads;

@@ -302,6 +302,46 @@ def test_apply_interior_exact_on_polynomials(kappa):
     assert np.all(out[mask] == 0.0)
 
 
+@pytest.mark.parametrize("p", [6, 9])
+def test_first_order_term_exact_on_polynomials(p):
+    """div(beta u) for polynomial beta and u (each product of degree < p in every
+    variable) is exact under collocation: the interior rows of A with beta
+    reproduce -Lap u + div(beta u) - kappa^2 b u to rounding."""
+    h, lo, kappa = np.array([0.4, 0.5, 0.3]), np.array([0.2, -0.1, 0.3]), 2.0
+    xyz = oracle.node_coords(p, lo, h)
+    x, y, z = xyz.T
+    u = x * y + z ** 2
+    beta = np.stack([y, x * z, 1.0 + x])
+    b = 1.0 + 0.5 * np.sin(x + y)
+    div = y ** 2 + x * z * x + (1.0 + x) * 2.0 * z        # d/dx(y u) + d/dy(x z u) + d/dz((1 + x) u)
+    exp = -2.0 + div - kappa ** 2 * b * u
+    ii = gs.interior_grid_indices(p)
+    out = oracle.apply_interior(p, h, kappa, b, u, beta)
+    assert np.abs(out[ii] - exp[ii]).max() < 1e-11 * np.abs(exp[ii]).max()
+    # the same matrix with the sign of the first-order term flipped misses by its size
+    bad = oracle.apply_interior(p, h, kappa, b, u, -beta)
+    assert np.abs(bad[ii] - exp[ii]).max() > 0.1 * np.abs(div[ii]).max()
+
+
+def test_convection_diffusion_step_equals_dense_bruteforce():
+    """One Crank-Nicolson step of u_t = kappa_d Lap u - div(vel u) through the
+    two-level HPS solve equals the dense solve of the same global system."""
+    grid = gs.InterfaceGrid(6, (2, 1, 2), L=(1.0, 0.5, 1.0))
+    u0 = lambda X: np.sin(np.pi * X[:, 0]) * np.sin(2 * np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
+    vel = lambda X: np.stack([-np.cos(X[:, 0]) * np.sin(X[:, 1]) * X[:, 2],
+                              np.sin(X[:, 0]) * np.cos(X[:, 1]) * X[:, 2], 0 * X[:, 0]], axis=1)
+    r = gs.crank_nicolson_heat(grid, 0.05, 0.05, 1, u0, vel)
+    p, b = grid.p, -np.ones(grid.p ** 3)
+    xyz = [oracle.node_coords(p, grid.box_lo(bx), grid.h) for bx in range(grid.nbox)]
+    f = [2 * r["c"] * u0(x) - oracle.apply_interior(p, grid.h, r["kappa"], b, u0(x), r["beta"][bx])
+         for bx, x in enumerate(xyz)]
+    d = gs.dense_global_solve(grid, r["kappa"], lambda X: -np.ones(len(X)), None, lambda X: 0 * X[:, 0],
+                              f_boxes=f, beta_boxes=r["beta"])
+    scale = np.abs(d["u_int"]).max()
+    assert np.abs(r["u_int"] - d["u_int"]).max() < 1e-11 * scale
+    assert np.abs(r["u_iface"] - d["u_iface"]).max() < 1e-11 * scale
+
+
 def test_crank_nicolson_step_equals_dense_bruteforce():
     """One Crank-Nicolson step through the two-level HPS solve equals the dense
     solve of the same global collocation system with the same right-hand
