@@ -79,11 +79,20 @@ typedef enum {
 typedef enum { HPS_FP64 = 0, HPS_FP32_IR = 1, HPS_BF16_IR = 2 } hps_precision;
 
 /* One class of boxes: polynomial order p (3 <= p <= 24), box side lengths
- * h[0..2] (> 0), wavenumber kappa (finite).  All boxes of a call share it. */
+ * h[0..2] (> 0), wavenumber kappa (finite).  All boxes of a call share it.
+ * beta: NULL for the operator of Eq. 2, -Lap u - kappa^2 b u; or device
+ * [nbox][3][p^3] (per box, like b: the x, y and z components at every node)
+ * for -Lap u + div(beta u) - kappa^2 b u, the first-order term of the
+ * convection-diffusion example of Sec. 4.4 (collocated by the product rule
+ * along each grid line).  Read by the leaf calls, hps_leaf_factor (which
+ * keeps a copy) and hps_leaf_apply; hps_dtn_gate and the no-allocation entry
+ * point take NULL only.  With beta the first refinement residual is FP64
+ * too. */
 typedef struct {
     int p;
     double h[3];
     double kappa;
+    const double* beta;
 } hps_leaf_kind;
 
 /* Tunables for hps_set_option (value is a double). */

@@ -67,12 +67,17 @@ class HpsError(RuntimeError):
 
 
 class LeafKind(ctypes.Structure):
-    """hps_leaf_kind: polynomial order p, box sides h[3], wavenumber kappa."""
-    _fields_ = [("p", ctypes.c_int), ("h", ctypes.c_double * 3), ("kappa", ctypes.c_double)]
+    """hps_leaf_kind: polynomial order p, box sides h[3], wavenumber kappa, and
+    optionally the first-order field beta (device [nbox, 3, p^3] float64 tensor
+    or address) of -Lap u + div(beta u) - kappa^2 b u."""
+    _fields_ = [("p", ctypes.c_int), ("h", ctypes.c_double * 3), ("kappa", ctypes.c_double),
+                ("beta", ctypes.c_void_p)]
 
-    def __init__(self, p: int, h, kappa: float):
+    def __init__(self, p: int, h, kappa: float, beta=None):
         hh = list(h) if hasattr(h, "__len__") else [h, h, h]
-        super().__init__(int(p), (ctypes.c_double * 3)(*[float(x) for x in hh]), float(kappa))
+        super().__init__(int(p), (ctypes.c_double * 3)(*[float(x) for x in hh]), float(kappa),
+                         _ptr(beta, _f64() if beta is not None and not isinstance(beta, int) else None))
+        self._beta_ref = beta   # keeps the tensor alive while the kind is
 
 
 class LeafGroup(ctypes.Structure):

@@ -130,6 +130,7 @@ struct hps_leaf_factors {
     int* d_status = nullptr;        // per box: status of the last solve when the caller passes none
     int* d_iters = nullptr;         // refinement diagnostics of the last solve
     double* d_relcorr = nullptr;
+    double* beta = nullptr;         // copy of the first-order field [nbox][3][p^3], or NULL
 };
 
 namespace hps {
@@ -390,6 +391,7 @@ struct Job {
     int diag_off = 0;                    // offset into the refinement diagnostics
     int nb = 0;                          // LU block (0: context default)
     int zero_row_box = -1;               // test hook
+    const double* beta = nullptr;        // device [nbox][3][p^3]: first-order term div(beta u), or NULL
 };
 
 int job_cols(const Job& j)
@@ -470,6 +472,7 @@ struct CallSpec {
     int zero_row_box;           // test hook: chunk-local box whose A_ii gets a zero row (-1: none)
     const double* kappa_dev;    // chunk base of the per-box wavenumbers, or NULL
     double kappa;
+    const double* beta = nullptr;   // chunk base of the first-order field [box][3][p^3], or NULL
 };
 
 // Solves A_ii X = B for one chunk.  FP64: the solution stays in M's RHS
@@ -486,7 +489,7 @@ hps_status solve_chunk<double>(hps_ctx*, const Geometry& g, const CallSpec& cs, 
 {
     const long long p3 = (long long)g.p * g.p * g.p;
     launch_build_aug<double>(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M, P.ldm,
-                             w.sM, status, cs.zero_row_box, st);
+                             w.sM, status, cs.zero_row_box, st, cs.beta);
     lu_factor<double>(P, w, nbox, status, st);
     lu_backward<double>(P, w, nbox, g.n, cs.r, nullptr, st);
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
@@ -503,7 +506,7 @@ hps_status solve_chunk<float>(hps_ctx* ctx, const Geometry& g, const CallSpec& c
 {
     const long long p3 = (long long)g.p * g.p * g.p;
     launch_build_aug<float>(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M, P.ldm,
-                            w.sM, status, cs.zero_row_box, st);
+                            w.sM, status, cs.zero_row_box, st, cs.beta);
     if (P.tc) {
         tc_reset_abort(st);
         if (!tc_lu_factor(P, w, nbox, status, st)) return HPS_ECUDA;
@@ -531,7 +534,7 @@ hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, con
     const int its = ctx->ir_iters;
     // The first residual, of the FP32 solution itself, may run in double-float
     // when at least one FP64-residual correction follows it.
-    const bool df = ctx->res_df && its >= 2 && g.dDF;
+    const bool df = ctx->res_df && its >= 2 && g.dDF && !cs.beta;   // the double-float form has no first-order term
     if (its > 0 && !have_kb) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, df ? w.kbs : nullptr, st);
     for (int it = 0; it < its; ++it) {
         if (df && it == 0)
@@ -539,7 +542,7 @@ hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, con
                                st);
         else
             launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
-                            w.M + g.n, P.ldm, w.sM, w.skip, st, w.kb);
+                            w.M + g.n, P.ldm, w.sM, w.skip, st, w.kb, cs.beta);
         if (P.tc) {
             if (!tc_lu_forward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;
             if (!tc_lu_backward(P, w, nbox, g.n, cs.r, w.skip, st)) return HPS_ECUDA;
@@ -572,6 +575,7 @@ hps_status enqueue_job(hps_ctx* ctx, const Job& j, const Plan& P, int chunk, cud
         cs.zero_row_box = (j.zero_row_box >= b0 && j.zero_row_box < b0 + nc) ? j.zero_row_box - b0 : -1;
         cs.kappa_dev = j.kappa_dev ? j.kappa_dev + b0 : nullptr;
         cs.kappa = j.kappa;
+        cs.beta = j.beta ? j.beta + (long long)b0 * 3 * p3 : nullptr;
         double* X;
         long long ldx, sX;
         if (P.elt == 8) {
@@ -725,7 +729,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
         key << " | " << j.g->p << ' ' << j.g->h[0] << ' ' << j.g->h[1] << ' ' << j.g->h[2] << ' ' << j.nbox << ' '
             << j.kappa << ' ' << j.kappa_dev << ' ' << j.b << ' ' << j.rhs_kind << ' ' << j.nload << ' ' << j.rhs
             << ' ' << j.T << ' ' << j.S << ' ' << j.v << ' ' << j.hf << ' ' << j.ui << ' ' << j.vadd << ' '
-            << j.status << ' ' << plans[i].NB << ' ' << chunk[i] << ' ' << j.zero_row_box;
+            << j.status << ' ' << plans[i].NB << ' ' << chunk[i] << ' ' << j.zero_row_box << ' ' << j.beta;
     }
     auto hit = ctx->graph_cache.find(key.str());
     if (hit == ctx->graph_cache.end()) {
@@ -809,6 +813,7 @@ hps_status run_single(hps_ctx* ctx, Job j, const hps_leaf_kind* kind, hps_precis
     if (rc != HPS_OK) return rc;
     j.g = g;
     j.kappa = kind->kappa;
+    j.beta = kind->beta;
     j.zero_row_box = ctx->zero_row_box;
     std::vector<Job> jobs{j};
     rc = status_ptrs(ctx, jobs, {box_status});
@@ -828,7 +833,7 @@ hps_status factors_factor(hps_leaf_factors* F, const double* b, cudaStream_t st)
     Work<T> w = carve<T>(F->P, F->buf, F->nbox);
     HPS_CUDA_TRY(cudaMemsetAsync(F->d_fstatus, 0, sizeof(int) * F->nbox, st));
     launch_build_aug<T>(g, F->kappa, nullptr, F->nbox, b, p3, RHS_LOAD, 0, nullptr, 0, w.M, F->P.ldm, w.sM,
-                        F->d_fstatus, F->ctx->zero_row_box, st);
+                        F->d_fstatus, F->ctx->zero_row_box, st, F->beta);
     if constexpr (sizeof(T) == 8) {
         lu_factor<double>(F->P, w, F->nbox, F->d_fstatus, st);
     } else {
@@ -856,7 +861,7 @@ hps_status factors_solve(hps_leaf_factors* F, int rhs_kind, int nrhs, const doub
     const long long s_rhs = rhs_kind == RHS_LOAD ? nrhs * p3 : (long long)nrhs * m;
     Work<T> w = carve<T>(F->P, F->buf, nbox);
     HPS_CUDA_TRY(cudaMemcpyAsync(status, F->d_fstatus, sizeof(int) * nbox, cudaMemcpyDeviceToDevice, st));
-    launch_load_rhs<T>(g, nbox, rhs_kind, nrhs, rhs, s_rhs, w.M, F->P.ldm, w.sM, status, st);
+    launch_load_rhs<T>(g, nbox, rhs_kind, nrhs, rhs, s_rhs, w.M, F->P.ldm, w.sM, status, st, F->beta);
     double* X;
     long long ldx, sX;
     if constexpr (sizeof(T) == 8) {
@@ -885,6 +890,7 @@ hps_status factors_solve(hps_leaf_factors* F, int rhs_kind, int nrhs, const doub
         cs.zero_row_box = -1;
         cs.kappa_dev = nullptr;
         cs.kappa = F->kappa;
+        cs.beta = F->beta;
         HPS_CUDA_TRY(cudaMemsetAsync(F->d_iters, 0, sizeof(int) * nbox, st));
         HPS_CUDA_TRY(cudaMemsetAsync(F->d_relcorr, 0, sizeof(double) * nbox, st));
         hps_status rc = refine_chunk(F->ctx, g, cs, F->P, w, nbox, nullptr, X, ldx, sX, status, F->d_iters,
@@ -1198,10 +1204,17 @@ hps_status hps_leaf_factor(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, co
     if (cudaMalloc(&F->buf, bytes) != cudaSuccess || cudaMalloc(&F->d_fstatus, sizeof(int) * nbox) != cudaSuccess ||
         cudaMalloc(&F->d_status, sizeof(int) * nbox) != cudaSuccess ||
         cudaMalloc(&F->d_iters, sizeof(int) * nbox) != cudaSuccess ||
-        cudaMalloc(&F->d_relcorr, sizeof(double) * nbox) != cudaSuccess) {
+        cudaMalloc(&F->d_relcorr, sizeof(double) * nbox) != cudaSuccess ||
+        (kind->beta && cudaMalloc(&F->beta, sizeof(double) * 3 * (size_t)g->p * g->p * g->p * nbox) != cudaSuccess)) {
         cudaGetLastError();
         hps_leaf_factors_destroy(F);
         return HPS_ENOMEM;
+    }
+    if (F->beta &&
+        cudaMemcpyAsync(F->beta, kind->beta, sizeof(double) * 3 * (size_t)g->p * g->p * g->p * nbox,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        hps_leaf_factors_destroy(F);
+        return HPS_ECUDA;
     }
     rc = prec == HPS_FP64 ? factors_factor<double>(F, b, st) : factors_factor<float>(F, b, st);
     if (rc == HPS_OK && box_status)
@@ -1260,7 +1273,7 @@ hps_status hps_leaf_apply(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, int
     Geometry* g = nullptr;
     rc = get_geometry(ctx, kind->p, kind->h, &g);
     if (rc != HPS_OK) return rc;
-    launch_apply_op(*g, kind->kappa, nbox, nfield, b, u, out, st);
+    launch_apply_op(*g, kind->kappa, nbox, nfield, b, u, out, st, kind->beta);
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
@@ -1273,6 +1286,7 @@ void hps_leaf_factors_destroy(hps_leaf_factors* F)
     cudaFree(F->d_status);
     cudaFree(F->d_iters);
     cudaFree(F->d_relcorr);
+    cudaFree(F->beta);
     delete F;
 }
 
@@ -1353,6 +1367,7 @@ hps_status hps_dtn_gate(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const
     if (!ctx || nbox < 0 || nprobe < 1 || nprobe > 64 || iters < 1 || iters > 200 || !(tol > 0)) return HPS_EINVAL;
     hps_status rc = check_kind(kind);
     if (rc != HPS_OK) return rc;
+    if (kind->beta) return HPS_EINVAL;   // the gate's preconditioner has no first-order term
     if (nbox == 0) return HPS_OK;
     if (!b || !T_hat || !accept || !err) return HPS_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->mu);

@@ -227,7 +227,8 @@ void prof_end(int cls, cudaStream_t st, double flops, double bytes);
 template <typename T>
 void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b,
                       long long sb, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
-                      T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st);
+                      T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st,
+                      const double* beta = nullptr);
 
 template <typename T>
 void launch_panel(T* M, long long ldm, long long sM, int n, int k, int nb, int ib,
@@ -253,19 +254,19 @@ void launch_extract(const TS* src, long long lds, long long sS, int n, int ncols
 
 // out = A u at the interior nodes of full nodal fields (zero at the others).
 void launch_apply_op(const Geometry& g, double kappa, int nbox, int nfield, const double* b, const double* u,
-                     double* out, cudaStream_t st);
+                     double* out, cudaStream_t st, const double* beta = nullptr);
 
 // M's right-hand-side columns n .. n + nrhs (LOAD: f_i, TRACE: -A_ib u_b), the
 // factors in M's first n columns left as they are.
 template <typename T>
 void launch_load_rhs(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
-                     T* M, long long ldm, long long sM, int* status, cudaStream_t st);
+                     T* M, long long ldm, long long sM, int* status, cudaStream_t st, const double* beta = nullptr);
 
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
                      float* R, long long ldr, long long sR, const int* skip, cudaStream_t st,
-                     const double* kb = nullptr);
+                     const double* kb = nullptr, const double* beta = nullptr);
 void selftest_conversions(long long n, unsigned long long seed, unsigned long long* mism_dev, cudaStream_t st);
 void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                     double* kb, float2* kbs, cudaStream_t st);

@@ -89,13 +89,17 @@ constexpr int kBuildRows = 4;
 // first clears its kBuildRows rows with 16-byte stores and then writes the
 // nonzeros and the dense load / trace columns; every value is formed in FP64
 // and rounded once to T.  B is -A_ib (DTN), f_i (LOAD), -A_ib u_b (TRACE) or
-// [-A_ib | f_i] (DTN_LOAD).
+// [-A_ib | f_i] (DTN_LOAD).  With beta (per box [3][p^3]) the operator gains
+// the first-order term div(beta u): + D_a[i][l] beta_a(l) on every entry of
+// the a-line (the product rule of collocation differentiation), couplings
+// included; the pattern of nonzeros is the same.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2, double kappa2,
             const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb, int rhs_kind,
             const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M, long long ldm, long long sM,
-            int* status, int zero_row_box)
+            int* status, int zero_row_box, const double* __restrict__ D1, const double* __restrict__ beta,
+            long long sbeta)
 {
     const int box = blockIdx.y;
     const int r0 = blockIdx.x * kBuildRows;
@@ -121,6 +125,12 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
     const double* D2y = D2 + pp;
     const double* D2z = D2 + 2 * pp;
     const double k2 = kappa_box ? kappa_box[box] * kappa_box[box] : kappa2;
+    const int p3 = pp * p;
+    const double* bt = beta ? beta + box * sbeta : nullptr;   // [3][p^3] of this box
+    // first-order coefficient of node (ii, jj, kk) on its a-line at position l
+    auto c1 = [&](int a, int own, int l, int ii, int jj, int kk) -> double {
+        return bt ? __ldg(D1 + a * pp + own * p + l) * __ldg(bt + a * p3 + ii + p * jj + pp * kk) : 0.0;
+    };
     const bool dtn = rhs_kind == RHS_DTN || rhs_kind == RHS_DTN_LOAD;
     const int ndtn = dtn ? 6 : 0;
     const int dense0 = rhs_kind == RHS_DTN_LOAD ? 6 * qq : 0;   // first dense column within B
@@ -139,10 +149,11 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
             if (e < q) {                                   // x line, with the diagonal
                 const int i2 = e + 1;
                 c = (i2 - 1) + q * (j - 1) + qq * (k - 1);
-                v = 0.0 - __ldg(D2x + i * p + i2);
+                v = 0.0 - __ldg(D2x + i * p + i2) + c1(0, i, i2, i2, j, k);
                 if (i2 == i) {
                     v -= __ldg(D2y + j * p + j);
                     v -= __ldg(D2z + k * p + k);
+                    v += c1(1, j, j, i, j, k) + c1(2, k, k, i, j, k);
                     const double bv = __ldg(b + box * sb + i + p * j + pp * k);
                     if (!isfinite(bv)) status[box] = HPS_EINVAL;
                     v -= k2 * bv;
@@ -151,12 +162,12 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
                 int j2 = e - q + 1;
                 if (j2 >= j) ++j2;
                 c = (i - 1) + q * (j2 - 1) + qq * (k - 1);
-                v = 0.0 - __ldg(D2y + j * p + j2);
+                v = 0.0 - __ldg(D2y + j * p + j2) + c1(1, j, j2, i, j2, k);
             } else {                                       // z line off the diagonal
                 int k2i = e - (2 * q - 1) + 1;
                 if (k2i >= k) ++k2i;
                 c = (i - 1) + q * (j - 1) + qq * (k2i - 1);
-                v = 0.0 - __ldg(D2z + k * p + k2i);
+                v = 0.0 - __ldg(D2z + k * p + k2i) + c1(2, k, k2i, i, j, k2i);
             }
             row[c] = T(v);
         } else if (e < 3 * q - 2 + ndtn) {
@@ -164,9 +175,9 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
             const int f = e - (3 * q - 2), axis = f >> 1, ep = (f & 1) ? p - 1 : 0;
             int a, bb;
             double v;
-            if (axis == 0) { a = j; bb = k; v = __ldg(D2x + i * p + ep); }
-            else if (axis == 1) { a = i; bb = k; v = __ldg(D2y + j * p + ep); }
-            else { a = i; bb = j; v = __ldg(D2z + k * p + ep); }
+            if (axis == 0) { a = j; bb = k; v = __ldg(D2x + i * p + ep) - c1(0, i, ep, ep, j, k); }
+            else if (axis == 1) { a = i; bb = k; v = __ldg(D2y + j * p + ep) - c1(1, j, ep, i, ep, k); }
+            else { a = i; bb = j; v = __ldg(D2z + k * p + ep) - c1(2, k, ep, i, j, ep); }
             row[n + f * qq + (a - 1) + q * (bb - 1)] = T(v);
         } else {
             const int cf = e - (3 * q - 2 + ndtn);
@@ -177,9 +188,13 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
                 // -A_ib u_b: the six face nodes on this row's three grid lines.
                 const double* ub = rhs + box * s_rhs + (long long)cf * 6 * qq;
                 const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
-                v = __ldg(D2x + i * p) * ub[0 * qq + sx] + __ldg(D2x + i * p + p - 1) * ub[1 * qq + sx]
-                  + __ldg(D2y + j * p) * ub[2 * qq + sy] + __ldg(D2y + j * p + p - 1) * ub[3 * qq + sy]
-                  + __ldg(D2z + k * p) * ub[4 * qq + sz] + __ldg(D2z + k * p + p - 1) * ub[5 * qq + sz];
+                const int e1 = p - 1;
+                v = (__ldg(D2x + i * p) - c1(0, i, 0, 0, j, k)) * ub[0 * qq + sx]
+                  + (__ldg(D2x + i * p + e1) - c1(0, i, e1, e1, j, k)) * ub[1 * qq + sx]
+                  + (__ldg(D2y + j * p) - c1(1, j, 0, i, 0, k)) * ub[2 * qq + sy]
+                  + (__ldg(D2y + j * p + e1) - c1(1, j, e1, i, e1, k)) * ub[3 * qq + sy]
+                  + (__ldg(D2z + k * p) - c1(2, k, 0, i, j, 0)) * ub[4 * qq + sz]
+                  + (__ldg(D2z + k * p + e1) - c1(2, k, e1, i, j, e1)) * ub[5 * qq + sz];
             }
             if (!isfinite(v)) status[box] = HPS_EINVAL;
             row[n + dense0 + cf] = T(v);
@@ -193,7 +208,7 @@ k_build_aug(int p, int n, int nrhs, int ldm_cols, const double* __restrict__ D2,
 template <typename T>
 __global__ void k_load_rhs(int p, int n, int nrhs, const double* __restrict__ D2, int rhs_kind,
                            const double* __restrict__ rhs, long long s_rhs, T* __restrict__ M, long long ldm,
-                           long long sM, int* status)
+                           long long sM, int* status, const double* __restrict__ D1, const double* __restrict__ beta)
 {
     const int box = blockIdx.y;
     const int q = p - 2, qq = q * q, pp = p * p;
@@ -211,9 +226,21 @@ __global__ void k_load_rhs(int p, int n, int nrhs, const double* __restrict__ D2
         } else {
             const double* ub = rhs + box * s_rhs + (long long)cf * 6 * qq;
             const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
-            v = __ldg(D2x + i * p) * ub[0 * qq + sx] + __ldg(D2x + i * p + p - 1) * ub[1 * qq + sx]
-              + __ldg(D2y + j * p) * ub[2 * qq + sy] + __ldg(D2y + j * p + p - 1) * ub[3 * qq + sy]
-              + __ldg(D2z + k * p) * ub[4 * qq + sz] + __ldg(D2z + k * p + p - 1) * ub[5 * qq + sz];
+            double cx0 = __ldg(D2x + i * p), cx1 = __ldg(D2x + i * p + p - 1);
+            double cy0 = __ldg(D2y + j * p), cy1 = __ldg(D2y + j * p + p - 1);
+            double cz0 = __ldg(D2z + k * p), cz1 = __ldg(D2z + k * p + p - 1);
+            if (beta) {   // minus the first-order couplings D_a[i][e] beta_a(face node)
+                const int p3 = pp * p, e1 = p - 1;
+                const double* bt = beta + box * 3LL * p3;
+                cx0 -= __ldg(D1 + i * p) * bt[0 + p * j + pp * k];
+                cx1 -= __ldg(D1 + i * p + e1) * bt[e1 + p * j + pp * k];
+                cy0 -= __ldg(D1 + pp + j * p) * bt[p3 + i + pp * k];
+                cy1 -= __ldg(D1 + pp + j * p + e1) * bt[p3 + i + p * e1 + pp * k];
+                cz0 -= __ldg(D1 + 2 * pp + k * p) * bt[2 * p3 + i + p * j];
+                cz1 -= __ldg(D1 + 2 * pp + k * p + e1) * bt[2 * p3 + i + p * j + pp * e1];
+            }
+            v = cx0 * ub[0 * qq + sx] + cx1 * ub[1 * qq + sx] + cy0 * ub[2 * qq + sy] + cy1 * ub[3 * qq + sy] +
+                cz0 * ub[4 * qq + sz] + cz1 * ub[5 * qq + sz];
         }
         if (!isfinite(v)) status[box] = HPS_EINVAL;
         M[box * sM + (long long)r * ldm + n + cf] = T(v);
@@ -226,7 +253,7 @@ __global__ void k_load_rhs(int p, int n, int nrhs, const double* __restrict__ D2
 // nodes.  One CTA per (field, box), the field staged in shared memory.
 __global__ void k_apply_op(int p, int nfield, const double* __restrict__ D2, double kappa2,
                            const double* __restrict__ b, long long sb, const double* __restrict__ u,
-                           double* __restrict__ out)
+                           double* __restrict__ out, const double* __restrict__ D1, const double* __restrict__ beta)
 {
     extern __shared__ double us[];
     const int c = blockIdx.x, box = blockIdx.y;
@@ -248,7 +275,17 @@ __global__ void k_apply_op(int p, int nfield, const double* __restrict__ D2, dou
         for (int l = 0; l < p; ++l)
             acc += __ldg(D2x + i * p + l) * us[l + p * j + pp * k] + __ldg(D2y + j * p + l) * us[i + p * l + pp * k] +
                    __ldg(D2z + k * p + l) * us[i + p * j + pp * l];
-        ob[idx] = -acc - kappa2 * __ldg(b + box * sb + idx) * us[idx];
+        double conv = 0.0;   // div(beta u): D_a applied to beta_a u along the three lines
+        if (beta) {
+            const double* bt = beta + box * 3LL * p3;
+            for (int l = 0; l < p; ++l) {
+                const int nx = l + p * j + pp * k, ny = i + p * l + pp * k, nz = i + p * j + pp * l;
+                conv += __ldg(D1 + i * p + l) * __ldg(bt + nx) * us[nx] +
+                        __ldg(D1 + pp + j * p + l) * __ldg(bt + p3 + ny) * us[ny] +
+                        __ldg(D1 + 2 * pp + k * p + l) * __ldg(bt + 2 * p3 + nz) * us[nz];
+            }
+        }
+        ob[idx] = -acc + conv - kappa2 * __ldg(b + box * sb + idx) * us[idx];
     }
 }
 
@@ -863,13 +900,16 @@ __host__ __device__ constexpr int res_min_blocks()
 // X for one box, staged in shared memory, with one thread per grid line; the
 // three axes are applied line by line (eo_line) into an accumulator, the z
 // pass finishing each point.  R is written in FP32 for the correction solve.
-template <int Q>
+// CONV: the operator also has the first-order term div(beta u) (beta per box
+// [3][p^3]): each pass subtracts D_a (beta_a X) along its lines (the interior
+// part; the face part is in B), by a plain q-term sum per output.
+template <int Q, bool CONV>
 __global__ void __launch_bounds__(res_threads<Q>(), res_min_blocks<Q>())
 k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
            const double* __restrict__ kappa_box, const double* __restrict__ b, long long sb, int rhs_kind,
            const double* __restrict__ rhs, long long s_rhs, const double* __restrict__ X, long long ldx,
            long long sX, float* __restrict__ R, long long ldr, long long sR, const int* skip,
-           const double* __restrict__ kb)
+           const double* __restrict__ kb, const double* __restrict__ D1, const double* __restrict__ beta)
 {
     constexpr int H = Q / 2, TA = eo_tab_size<Q>();
     constexpr int q = Q, qq = Q * Q;
@@ -882,6 +922,19 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
     double* Ac = Xs + n;                                     // [n]
     double* D2s = Ac + n;                                    // [3][p][p]
     double* tab = D2s + ((3 * pp + 1) & ~1);                 // [3][TA]
+    double* D1s = tab + 3 * TA;                              // CONV: [3][p][p]
+    const int p3 = pp * p;
+    const double* bt = CONV ? beta + (long long)box * 3 * p3 : nullptr;
+    if constexpr (CONV)
+        for (int idx = threadIdx.x; idx < 3 * pp; idx += blockDim.x) D1s[idx] = D1[idx];
+    // CONV: sum_l D_a[o][l] beta_a(node l) X(node l) over the interior nodes l of a line
+    auto conv_line = [&](int a, int o, const double* xline, int xstride, const double* bline, int bstride) {
+        double cv = 0.0;
+#pragma unroll 2
+        for (int l = 1; l <= Q; ++l)
+            cv = fma(D1s[a * pp + o * p + l], __ldg(bline + l * bstride) * xline[(l - 1) * xstride], cv);
+        return cv;
+    };
     const double* Xb = X + box * sX + cw;
     for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = Xb[(long long)r * ldx];
     for (int idx = threadIdx.x; idx < 3 * pp; idx += blockDim.x) D2s[idx] = D2[idx];
@@ -913,12 +966,22 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
     if (ln < qq) {
         const int base = ln * q;
         eo_line<Q>(Xs + base, 1, tab, [&](int i, double v) { Ac[base + i] = v; });
+        if constexpr (CONV) {
+            const int j = ln % q + 1, k = ln / q + 1;
+            const double* bl = bt + p * j + pp * k;   // beta_x along this line (node index l)
+            for (int i = 0; i < q; ++i) Ac[base + i] -= conv_line(0, i + 1, Xs + base, 1, bl, 1);
+        }
     }
     __syncthreads();
     // y lines (ln = i0 + q k0): Ac += D2y X
     if (ln < qq) {
         const int base = ln % q + qq * (ln / q);
         eo_line<Q>(Xs + base, q, tab + TA, [&](int j, double v) { Ac[base + q * j] += v; });
+        if constexpr (CONV) {
+            const int i = ln % q + 1, k = ln / q + 1;
+            const double* bl = bt + p3 + i + pp * k;   // beta_y along this line
+            for (int j = 0; j < q; ++j) Ac[base + q * j] -= conv_line(1, j + 1, Xs + base, q, bl, p);
+        }
     }
     __syncthreads();
     // z lines (ln = i0 + q j0), then every point of the line is finished.
@@ -935,25 +998,36 @@ k_residual(int p, int n, int nrhs, const double* __restrict__ D2, double kappa2,
         const double* ry = D2s + pp + j * p;
         float* Rb = R + box * sR + cw;
         const double* kbb = kb ? kb + (long long)box * n : nullptr;
+        // CONV: the first-order coupling of interior node (i, j, k) to face node
+        // e of axis a is D_a[own][e] beta_a(face node); B = -A_ib carries minus it
+        auto c1 = [&](int a, int own, int e, int ii, int jj, int kk) -> double {
+            if constexpr (CONV) return D1s[a * pp + own * p + e] * __ldg(bt + a * p3 + ii + p * jj + pp * kk);
+            else return 0.0;
+        };
         eo_line<Q>(Xs + ln, qq, tab + 2 * TA, [&](int k0, double v) {
             const int k = k0 + 1, r = ln + qq * k0;
             const double* rz = D2s + 2 * pp + k * p;
             const int gi = i + p * j + pp * k;
-            // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x
+            // R = B - A_ii x = B + (D2 sums) x + kappa^2 b x (- div(beta x) with CONV)
             double res = fma(kbb ? kbb[r] : k2 * bb[gi], Xs[r], Ac[r] + v);
+            if constexpr (CONV) res -= conv_line(2, k, Xs + ln, qq, bt + 2 * p3 + i + p * j, pp);
             if (kind == RHS_DTN) {   // -A_ib e_f: nonzero only next to face node f
                 const int f = cg / qq, s2 = cg % qq, a = s2 % q + 1, b2 = s2 / q + 1;
                 const int axis = f >> 1, e = (f & 1) ? p - 1 : 0;
-                if (axis == 0 && j == a && k == b2) res += rx[e];
-                else if (axis == 1 && i == a && k == b2) res += ry[e];
-                else if (axis == 2 && i == a && j == b2) res += rz[e];
+                if (axis == 0 && j == a && k == b2) res += rx[e] - c1(0, i, e, e, j, k);
+                else if (axis == 1 && i == a && k == b2) res += ry[e] - c1(1, j, e, i, e, k);
+                else if (axis == 2 && i == a && j == b2) res += rz[e] - c1(2, k, e, i, j, e);
             } else if (kind == RHS_LOAD) {
                 res += rhs[box * s_rhs + (long long)cg * p * pp + gi];
             } else {
                 const double* ub = rhs + box * s_rhs + (long long)cg * 6 * qq;
                 const int sx = (j - 1) + q * (k - 1), sy = (i - 1) + q * (k - 1), sz = (i - 1) + q * (j - 1);
-                res += rx[0] * ub[sx] + rx[p - 1] * ub[qq + sx] + ry[0] * ub[2 * qq + sy] +
-                       ry[p - 1] * ub[3 * qq + sy] + rz[0] * ub[4 * qq + sz] + rz[p - 1] * ub[5 * qq + sz];
+                const int e1 = p - 1;
+                res += (rx[0] - c1(0, i, 0, 0, j, k)) * ub[sx] + (rx[e1] - c1(0, i, e1, e1, j, k)) * ub[qq + sx] +
+                       (ry[0] - c1(1, j, 0, i, 0, k)) * ub[2 * qq + sy] +
+                       (ry[e1] - c1(1, j, e1, i, e1, k)) * ub[3 * qq + sy] +
+                       (rz[0] - c1(2, k, 0, i, j, 0)) * ub[4 * qq + sz] +
+                       (rz[e1] - c1(2, k, e1, i, j, e1)) * ub[5 * qq + sz];
             }
             Rb[(long long)r * ldr] = d2f_rn(res);
         });
@@ -1395,17 +1469,19 @@ __global__ void k_fill_int(int* p, int value, long long count)
 template <typename T>
 void launch_build_aug(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b,
                       long long sb, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
-                      T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st)
+                      T* M, long long ldm, long long sM, int* status, int zero_row_box, cudaStream_t st,
+                      const double* beta)
 {
     dim3 grd((unsigned)((g.n + kBuildRows - 1) / kBuildRows), (unsigned)nbox);
     prof_begin(KC_BUILD, st);
     k_build_aug<T><<<grd, 256, 0, st>>>(g.p, g.n, nrhs, (int)ldm, g.dD2, kappa * kappa, kappa_box, b, sb, rhs_kind,
-                                        rhs_src, s_rhs, M, ldm, sM, status, zero_row_box);
+                                        rhs_src, s_rhs, M, ldm, sM, status, zero_row_box, g.dD, beta,
+                                        3LL * g.p * g.p * g.p);
     prof_end(KC_BUILD, st, 0.0, (double)nbox * g.n * ldm * sizeof(T));
 }
 
 void launch_apply_op(const Geometry& g, double kappa, int nbox, int nfield, const double* b, const double* u,
-                     double* out, cudaStream_t st)
+                     double* out, cudaStream_t st, const double* beta)
 {
     const size_t smem = (size_t)g.p * g.p * g.p * sizeof(double);
     static bool attr = false;
@@ -1415,19 +1491,21 @@ void launch_apply_op(const Geometry& g, double kappa, int nbox, int nfield, cons
     }
     dim3 grd((unsigned)nfield, (unsigned)nbox);
     prof_begin(KC_MISC, st);
-    k_apply_op<<<grd, 256, smem, st>>>(g.p, nfield, g.dD2, kappa * kappa, b, (long long)g.p * g.p * g.p, u, out);
+    k_apply_op<<<grd, 256, smem, st>>>(g.p, nfield, g.dD2, kappa * kappa, b, (long long)g.p * g.p * g.p, u, out,
+                                       g.dD, beta);
     prof_end(KC_MISC, st, (double)nbox * nfield * g.n * (6.0 * g.p + 3.0),
              (double)nbox * nfield * g.p * g.p * g.p * 24.0);
 }
 
 template <typename T>
 void launch_load_rhs(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
-                     T* M, long long ldm, long long sM, int* status, cudaStream_t st)
+                     T* M, long long ldm, long long sM, int* status, cudaStream_t st, const double* beta)
 {
     const long long total = (long long)g.n * nrhs;
     dim3 grd((unsigned)std::min<long long>((total + 255) / 256, 256), (unsigned)nbox);
     prof_begin(KC_BUILD, st);
-    k_load_rhs<T><<<grd, 256, 0, st>>>(g.p, g.n, nrhs, g.dD2, rhs_kind, rhs_src, s_rhs, M, ldm, sM, status);
+    k_load_rhs<T><<<grd, 256, 0, st>>>(g.p, g.n, nrhs, g.dD2, rhs_kind, rhs_src, s_rhs, M, ldm, sM, status, g.dD,
+                                       beta);
     prof_end(KC_BUILD, st, 0.0, (double)nbox * total * (8.0 + sizeof(T)));
 }
 
@@ -1579,26 +1657,28 @@ void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, in
 }
 
 namespace {
-template <int Q>
+template <int Q, bool CONV>
 void residual_q(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                 int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs, const double* X, long long ldx,
                 long long sX, float* R, long long ldr, long long sR, const int* skip, cudaStream_t st,
-                const double* kb)
+                const double* kb, const double* beta)
 {
-    const size_t tables = (size_t)((3 * g.p * g.p + 1) & ~1) + 3 * eo_tab_size<Q>();
+    const size_t tables = (size_t)((3 * g.p * g.p + 1) & ~1) + 3 * eo_tab_size<Q>() + (CONV ? 3 * g.p * g.p : 0);
     const size_t smem = ((size_t)2 * g.n + tables) * sizeof(double);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_residual<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_residual<Q, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr = true;
     }
     dim3 grd((unsigned)nrhs, (unsigned)nbox);
     // FP64 operations per entry: three line passes (butterfly 1, pairs h + 1
-    // (odd q: + 1 for the middle column), accumulate 1) and the finish (3).
-    const double per = 3.0 * (2.0 + 2.0 * (Q / 2) + ((Q & 1) ? 2.0 : 0.0)) + 3.0;
+    // (odd q: + 1 for the middle column), accumulate 1) and the finish (3);
+    // the first-order term adds q + 1 per line pass.
+    const double per = 3.0 * (2.0 + 2.0 * (Q / 2) + ((Q & 1) ? 2.0 : 0.0)) + 3.0 + (CONV ? 3.0 * (Q + 1) : 0.0);
     prof_begin(KC_RESIDUAL, st);
-    k_residual<Q><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, nrhs, g.dD2, kappa * kappa, kappa_box, b, sb,
-                                                        rhs_kind, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, skip, kb);
+    k_residual<Q, CONV><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, nrhs, g.dD2, kappa * kappa, kappa_box, b, sb,
+                                                              rhs_kind, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, skip,
+                                                              kb, g.dD, beta);
     prof_end(KC_RESIDUAL, st, (double)nbox * g.n * (double)nrhs * per, (double)nbox * g.n * (double)nrhs * 12.0);
 }
 }  // namespace
@@ -1606,13 +1686,18 @@ void residual_q(const Geometry& g, double kappa, const double* kappa_box, int nb
 void launch_residual(const Geometry& g, double kappa, const double* kappa_box, int nbox, const double* b, long long sb,
                      int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                      const double* X, long long ldx, long long sX,
-                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st, const double* kb)
+                     float* R, long long ldr, long long sR, const int* skip, cudaStream_t st, const double* kb,
+                     const double* beta)
 {
     static_assert(kMaxP - 2 == 22, "one residual instantiation per interior line length");
-#define HPS_RES_CASE(QV)                                                                                       \
-    case QV:                                                                                                   \
-        residual_q<QV>(g, kappa, kappa_box, nbox, b, sb, rhs_kind, nrhs, rhs_src, s_rhs, X, ldx, sX, R, ldr, sR, \
-                       skip, st, kb);                                                                          \
+#define HPS_RES_CASE(QV)                                                                                         \
+    case QV:                                                                                                     \
+        if (beta)                                                                                                \
+            residual_q<QV, true>(g, kappa, kappa_box, nbox, b, sb, rhs_kind, nrhs, rhs_src, s_rhs, X, ldx, sX, R, \
+                                 ldr, sR, skip, st, kb, beta);                                                   \
+        else                                                                                                     \
+            residual_q<QV, false>(g, kappa, kappa_box, nbox, b, sb, rhs_kind, nrhs, rhs_src, s_rhs, X, ldx, sX,   \
+                                  R, ldr, sR, skip, st, kb, nullptr);                                            \
         break;
     switch (g.q) {
         HPS_RES_CASE(1) HPS_RES_CASE(2) HPS_RES_CASE(3) HPS_RES_CASE(4) HPS_RES_CASE(5) HPS_RES_CASE(6)
@@ -1745,14 +1830,14 @@ void launch_fill_int(int* p, int value, long long count, cudaStream_t st)
 
 template void launch_build_aug<float>(const Geometry&, double, const double*, int, const double*, long long, int,
                                       int, const double*, long long, float*, long long, long long, int*, int,
-                                      cudaStream_t);
+                                      cudaStream_t, const double*);
 template void launch_build_aug<double>(const Geometry&, double, const double*, int, const double*, long long, int,
                                        int, const double*, long long, double*, long long, long long, int*, int,
-                                       cudaStream_t);
+                                       cudaStream_t, const double*);
 template void launch_load_rhs<float>(const Geometry&, int, int, int, const double*, long long, float*, long long,
-                                     long long, int*, cudaStream_t);
+                                     long long, int*, cudaStream_t, const double*);
 template void launch_load_rhs<double>(const Geometry&, int, int, int, const double*, long long, double*, long long,
-                                      long long, int*, cudaStream_t);
+                                      long long, int*, cudaStream_t, const double*);
 template void launch_panel<float>(float*, long long, long long, int, int, int, int, int*, long long, float*,
                                   long long, long long, float*, long long, long long, int*, const int*, int,
                                   cudaStream_t);

@@ -50,7 +50,7 @@ using namespace hps;
 extern "C" hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const double* b, double* T,
                                                  int* box_status, void* stream)
 {
-    if (!kind || kind->p < 3 || kind->p > kMaxP || nbox < 0) return HPS_EINVAL;
+    if (!kind || kind->p < 3 || kind->p > kMaxP || nbox < 0 || kind->beta) return HPS_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!(kind->h[a] > 0.0)) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
