@@ -338,7 +338,9 @@ hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const
  * factorisation failed keeps that status) and return HPS_EINVAL for nrhs out
  * of range or NULL arrays.  Several solves may follow one factorisation; they
  * share the handle's workspace, so solves on different streams must be
- * ordered by the caller. */
+ * ordered by the caller.  With HPS_OPT_GRAPHS each distinct solve (same
+ * arrays, nrhs and refinement options) is captured into a CUDA graph once
+ * and replayed afterwards, as the time steps of a loop are. */
 typedef struct hps_leaf_factors hps_leaf_factors;
 hps_status hps_leaf_factor(hps_ctx* ctx, const hps_leaf_kind* kind, int nbox, const double* b, int nrhs_max,
                            hps_precision precision, int* box_status, void* stream, hps_leaf_factors** out);

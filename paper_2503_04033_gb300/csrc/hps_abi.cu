@@ -131,6 +131,7 @@ struct hps_leaf_factors {
     int* d_iters = nullptr;         // refinement diagnostics of the last solve
     double* d_relcorr = nullptr;
     double* beta = nullptr;         // copy of the first-order field [nbox][3][p^3], or NULL
+    std::map<std::string, cudaGraphExec_t> graphs;   // captured solves (HPS_OPT_GRAPHS)
 };
 
 namespace hps {
@@ -915,9 +916,36 @@ hps_status factors_run(hps_leaf_factors* F, int rhs_kind, int nrhs, const double
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ProfScope prof_scope(ctx);
     int* status = box_status ? box_status : F->d_status;
-    hps_status rc = F->prec == HPS_FP64
-                        ? factors_solve<double>(F, rhs_kind, nrhs, rhs, vadd, out0, out1, status, st)
-                        : factors_solve<float>(F, rhs_kind, nrhs, rhs, vadd, out0, out1, status, st);
+    auto enqueue = [&](cudaStream_t s) {
+        return F->prec == HPS_FP64 ? factors_solve<double>(F, rhs_kind, nrhs, rhs, vadd, out0, out1, status, s)
+                                   : factors_solve<float>(F, rhs_kind, nrhs, rhs, vadd, out0, out1, status, s);
+    };
+    hps_status rc = HPS_OK;
+    if (ctx->graphs && !ctx->prof_on) {
+        // one captured graph per distinct solve (same buffers and options), as
+        // for the one-shot calls; time steps replay it
+        std::ostringstream key;
+        key << rhs_kind << ' ' << nrhs << ' ' << rhs << ' ' << vadd << ' ' << out0 << ' ' << out1 << ' ' << status
+            << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->res_df;
+        auto hit = F->graphs.find(key.str());
+        if (hit == F->graphs.end()) {
+            if (!ctx->cap_stream) HPS_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            HPS_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue(ctx->cap_stream);
+            cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (rc != HPS_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+            if (ce != cudaSuccess) return HPS_ECUDA;
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return HPS_ECUDA;
+            hit = F->graphs.emplace(key.str(), exec).first;
+        }
+        HPS_CUDA_TRY(cudaGraphLaunch(hit->second, st));
+    } else {
+        rc = enqueue(st);
+    }
     if (rc != HPS_OK) return rc;
     if (!ctx->sync) return HPS_OK;
     HPS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1287,6 +1315,7 @@ void hps_leaf_factors_destroy(hps_leaf_factors* F)
     cudaFree(F->d_iters);
     cudaFree(F->d_relcorr);
     cudaFree(F->beta);
+    for (auto& kv : F->graphs) cudaGraphExecDestroy(kv.second);
     delete F;
 }
 

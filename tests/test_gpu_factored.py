@@ -143,3 +143,37 @@ def test_factored_singular_box_and_arguments(ctx):
             H.hps_leaf_solve_factored(F, 3, f, v, hf, st)
     finally:
         H.hps_leaf_factors_destroy(F)
+
+
+def test_factored_solves_replay_as_graphs(ctx):
+    """With HPS_OPT_GRAPHS a stored-factor solve is captured once and replayed:
+    new load values in the same arrays give the results of an uncaptured
+    solve, bit for bit."""
+    import torch
+    p, h, kappa, nbox, nrhs = 9, np.array([0.125] * 3), 15.0, 3, 2
+    lows = np.random.default_rng(6).integers(0, 4, size=(nbox, 3)) * h
+    b = _dev(box_b(H.hps_leaf_nodes, p, lows, h, hi.fourier_b_field().b))
+    kind = H.LeafKind(p, h, kappa)
+    n, m = H.hps_leaf_sizes(p)
+    F = H.hps_leaf_factor(ctx, kind, nbox, b, nrhs, H.HPS_FP32_IR)
+    f = torch.empty(nbox, nrhs, p ** 3, dtype=torch.float64, device="cuda")
+    v = torch.empty(nbox, nrhs, n, dtype=torch.float64, device="cuda")
+    hf = torch.empty(nbox, nrhs, m, dtype=torch.float64, device="cuda")
+    try:
+        results = {}
+        for graphs in (0, 1):
+            H.hps_set_option(ctx, H.HPS_OPT_GRAPHS, graphs)
+            out = []
+            for seed in (40, 41, 42):    # same arrays, new values: the graph is replayed
+                loads = hi.fourier_b_per_box(nrhs, seed)
+                f.copy_(_dev(np.stack([hi.load_values(loads, H.hps_leaf_nodes(p, lo, h)) for lo in lows])))
+                H.hps_leaf_solve_factored(F, nrhs, f, v, hf)
+                torch.cuda.synchronize()
+                out.append((v.cpu().numpy().copy(), hf.cpu().numpy().copy()))
+            results[graphs] = out
+        for (v0, h0), (v1, h1) in zip(results[0], results[1]):
+            assert np.array_equal(v0, v1) and np.array_equal(h0, h1)
+    finally:
+        H.hps_set_option(ctx, H.HPS_OPT_GRAPHS, 0)
+        H.hps_leaf_factors_destroy(F)
+
