@@ -78,6 +78,7 @@ __host__ __device__ constexpr uint32_t b_tile() { return (uint32_t)TcFmt<FMT>::B
 template <int FMT>
 __host__ __device__ constexpr uint32_t stage_bytes() { return (uint32_t)TcFmt<FMT>::NPL * (A_TILE + b_tile<FMT>()); }
 constexpr uint32_t STAGE_BYTES = 48 * 1024;
+constexpr int TC_BN_NARROW = 64;                            // tile width for products of at most 64 columns
 static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES && stage_bytes<2>() == STAGE_BYTES,
               "one shared-memory layout");
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
@@ -444,16 +445,20 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // Persistent update product O <- src - A G over (box, row tile, column tile),
-// in the work-unit order of TcSched.  TMEM holds two 128 x 256
-// FP32 accumulators: the epilogue drains one while the MMAs fill the other.
-template <int FMT>
+// in the work-unit order of TcSched.  TMEM holds two 128 x BN FP32
+// accumulators: the epilogue drains one while the MMAs fill the other.  BN
+// is the format's tile width, or TC_BN_NARROW for products with few columns
+// (the solves of a few right-hand sides), which would otherwise spend most
+// of each MMA on padding.
+template <int FMT, int BNT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
             const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO, TcArgs a)
 {
     using Fm = TcFmt<FMT>;
-    constexpr int BN = Fm::BN, KPC = Fm::KPC, NPL = Fm::NPL;
-    constexpr uint32_t B_TILE = b_tile<FMT>();
+    constexpr int BN = BNT, KPC = Fm::KPC, NPL = Fm::NPL;
+    constexpr uint32_t B_TILE = (uint32_t)BN * ROWB;
+    constexpr uint32_t STAGE_TX = (uint32_t)NPL * (A_TILE + B_TILE);   // bytes a stage receives
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t ld_bar[TC_EPI_WARPS][TE_PRE];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
@@ -525,7 +530,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     }
                     const uint32_t fb = smem_u32(&full_bar[s]);
                     const uint32_t st = sbase + s * STAGE_BYTES;
-                    mbar_expect_tx(fb, STAGE_BYTES);
+                    mbar_expect_tx(fb, STAGE_TX);
                     // A's K chunks past kch1 come from the second map, whose row 0 is
                     // row a2_off of the product (rows above it load as zeros)
                     const bool second = ch >= a.kch1;
@@ -1119,8 +1124,8 @@ TcLeft left1(const void* A, long long rows, long long sA, int K)
     return l;
 }
 
-template <int FMT>
-bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
+template <int FMT, int BNT>
+bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
                         const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs, bool* fused)
 {
     using Fm = TcFmt<FMT>;
@@ -1131,7 +1136,7 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_tc_update<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        cudaFuncSetAttribute(k_tc_update<FMT, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
         if (num_sms <= 0) num_sms = 1;
         // how many CTA pairs fit at once (an SM whose cluster partner is
         // missing stays idle in pair mode)
@@ -1147,7 +1152,7 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, (void*)k_tc_update<FMT>, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&nc, (void*)k_tc_update<FMT, BNT>, &cfg) != cudaSuccess) {
             cudaGetLastError();
             nc = 0;
         }
@@ -1158,7 +1163,7 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
     a.kch1 = L.K2 ? L.K1 / Fm::KPC : a.kch;   // L.K1 is a whole block when a second part follows
     a.a2_off = L.a2_off;
     a.tiles_m = (a.M + TC_BM - 1) / TC_BM;
-    a.tiles_n = (a.N + Fm::BN - 1) / Fm::BN;
+    a.tiles_n = (a.N + BNT - 1) / BNT;
     a.tiles = a.tiles_m * a.tiles_n * nbox;
     a.nbox = nbox;
     a.cl = (allow_pairs && max_pairs > 0 && a.tiles_m >= 2) ? 1 : 0;
@@ -1166,7 +1171,7 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
     a.units = a.units_per_box * nbox;
     CUtensorMap ta, ta2, tb;
     if (!make_map<FMT>(&ta, L.A, NB, L.rows, L.rows * NB, L.sA, nbox, TC_BM) ||
-        !make_map<FMT>(&tb, Gp, gK, args.N, g_plane, sGp, nbox, a.cl ? Fm::BN / 2 : Fm::BN))
+        !make_map<FMT>(&tb, Gp, gK, args.N, g_plane, sGp, nbox, a.cl ? BNT / 2 : BNT))
         return false;
     if (L.K2) {
         if (!make_map<FMT>(&ta2, L.A2, NB, L.rows2, L.rows2 * NB, L.sA2, nbox, TC_BM)) return false;
@@ -1211,15 +1216,26 @@ bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k_tc_update<FMT>, ta, ta2, tb, to, a) != cudaSuccess) return false;
+        if (cudaLaunchKernelEx(&cfg, k_tc_update<FMT, BNT>, ta, ta2, tb, to, a) != cudaSuccess) return false;
     } else {
         dim3 grd((unsigned)std::min(a.units, num_sms));
-        k_tc_update<FMT><<<grd, TC_THREADS, TC_SMEM, st>>>(ta, ta2, tb, to, a);
+        k_tc_update<FMT, BNT><<<grd, TC_THREADS, TC_SMEM, st>>>(ta, ta2, tb, to, a);
     }
     const double kk = (double)K;
     prof_end(cls, st, 2.0 * nbox * a.M * (double)a.N * kk,
              (double)nbox * ((a.M + (double)a.N) * kk * Fm::NPL * Fm::EB + 2.0 * a.M * (double)a.N * 4));
     return true;
+}
+
+template <int FMT>
+bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs, bool* fused)
+{
+    if (args.N <= TC_BN_NARROW && TcFmt<FMT>::BN > TC_BN_NARROW)
+        return launch_tc_update_w<FMT, TC_BN_NARROW>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
+                                                     allow_pairs, fused);
+    return launch_tc_update_w<FMT, TcFmt<FMT>::BN>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
+                                                   allow_pairs, fused);
 }
 
 bool launch_tc_update(int fmt, const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
