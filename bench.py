@@ -104,6 +104,8 @@ def parse_args():
     ap.add_argument("--train-boxes", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--gate-tol", type=float, default=3e-3)
+    ap.add_argument("--interface", choices=("gpu", "host"), default="gpu",
+                    help="timestep workload: interface solve on the GPU (nested dissection) or a host sparse LU")
     ap.add_argument("--ir-tol", type=float, default=None,
                     help="refinement tolerance (HPS_OPT_IR_TOL); library default when omitted")
     return ap.parse_args()
@@ -846,11 +848,13 @@ def run_factored(args):
 def run_timestep(args):
     """Crank-Nicolson steps of the heat equation u_t = kappa_d Lap u on the unit
     cube (u = 0 on its boundary), 4 x 4 x 4 boxes at p = 12, as in Sec. 4.4:
-    T and the interior factorisations built once, a host sparse LU of the
-    interface system factored once; per step one hps_leaf_apply, one
-    particular solve and one reconstruction with the stored factors on the
-    GPU, and the interface solve on the host.  The final state is compared
-    with the exact decaying solution."""
+    T, the interior factorisations and the interface factorisation built once;
+    per step one hps_leaf_apply, one particular solve with the stored factors,
+    one interface solve and one reconstruction, all on the GPU and enqueued on
+    one stream (no host round trip inside a step).  --interface host runs the
+    interface solve with a host sparse LU of the assembled system instead (the
+    paper's arrangement, MUMPS there).  The final state is compared with the
+    exact decaying solution."""
     import time as _time
     import torch
     import scipy.sparse as sp
@@ -871,6 +875,7 @@ def run_timestep(args):
     ctx = H.hps_create(0, 0)
     H.hps_set_option(ctx, H.HPS_OPT_GRAPHS, 1)     # every step replays the same solves
     stream = torch.cuda.current_stream(dev)
+    gpu_iface = args.interface == "gpu"
     t0 = _time.time()
     T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
     H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, H.HPS_FP32_IR, None, stream)
@@ -878,28 +883,8 @@ def run_timestep(args):
     torch.cuda.synchronize(dev)
     t_gpu_setup = _time.time() - t0
     t0 = _time.time()
-    rows, cols, vals, _, _, _, ni, _ = H.hps_assemble_interface_blocks(p, (nbx, nbx, nbx), T.cpu().numpy())
-    lu = spla.splu(sp.coo_matrix((vals, (rows, cols)), shape=(ni, ni)).tocsc())
-    t_host_setup = _time.time() - t0
-    # interface numbering of each box's face nodes (faces of each normal axis
-    # in turn, box-column order, q^2 nodes per face)
-    Fx = (nbx - 1) * nbx * nbx
-    gid = np.full((nbox, m), -1, dtype=np.int64)
-    for bx in range(nbox):
-        cxyz = (bx % nbx, (bx // nbx) % nbx, bx // (nbx * nbx))
-        for f in range(6):
-            axis, side = f // 2, f % 2
-            plane = cxyz[axis] + side
-            if plane == 0 or plane == nbx:
-                continue
-            if axis == 0:
-                fid = (plane - 1) + (nbx - 1) * (cxyz[1] + nbx * cxyz[2])
-            elif axis == 1:
-                fid = Fx + cxyz[0] + nbx * ((plane - 1) + (nbx - 1) * cxyz[2])
-            else:
-                fid = 2 * Fx + cxyz[0] + nbx * (cxyz[1] + nbx * (plane - 1))
-            gid[bx, f * qq:(f + 1) * qq] = fid * qq + np.arange(qq)
-    isi = gid >= 0
+    FI = H.hps_interface_factor(ctx, p, (nbx, nbx, nbx), T, 1, stream) if gpu_iface else None
+    t_iface_setup = _time.time() - t0
     # node index sets: interior (x fastest) and face nodes (face order)
     r = np.arange(1, q + 1)
     kk, jj, ii_ = np.meshgrid(r, r, r, indexing="ij")
@@ -923,60 +908,131 @@ def run_timestep(args):
     ui = torch.empty(nbox, 1, n, dtype=torch.float64, device=dev)
     st = torch.zeros(nbox, dtype=torch.int32, device=dev)
     ii_d, fi_d = torch.from_numpy(ii).to(dev), torch.from_numpy(fi).to(dev)
+
+    # host sparse LU of the assembled interface system: the --interface host
+    # loop uses it, and the GPU loop times a few of its solves for comparison
+    t0 = _time.time()
+    rows, cols, vals, _, _, _, ni, _ = H.hps_assemble_interface_blocks(p, (nbx, nbx, nbx), T.cpu().numpy())
+    lu = spla.splu(sp.coo_matrix((vals, (rows, cols)), shape=(ni, ni)).tocsc())
+    t_host_setup = _time.time() - t0
+    # interface numbering of each box's face nodes (faces of each normal axis
+    # in turn, box-column order, q^2 nodes per face)
+    Fx = (nbx - 1) * nbx * nbx
+    gid = np.full((nbox, m), -1, dtype=np.int64)
+    for bx in range(nbox):
+        cxyz = (bx % nbx, (bx // nbx) % nbx, bx // (nbx * nbx))
+        for f_ in range(6):
+            axis, side = f_ // 2, f_ % 2
+            plane = cxyz[axis] + side
+            if plane == 0 or plane == nbx:
+                continue
+            if axis == 0:
+                fid = (plane - 1) + (nbx - 1) * (cxyz[1] + nbx * cxyz[2])
+            elif axis == 1:
+                fid = Fx + cxyz[0] + nbx * ((plane - 1) + (nbx - 1) * cxyz[2])
+            else:
+                fid = 2 * Fx + cxyz[0] + nbx * (cxyz[1] + nbx * (plane - 1))
+            gid[bx, f_ * qq:(f_ + 1) * qq] = fid * qq + np.arange(qq)
+    isi = gid >= 0
     gid_t = torch.from_numpy(np.where(isi, gid, 0)).to(dev)
     isi_t = torch.from_numpy(isi).to(dev)
     pos = torch.from_numpy(np.flatnonzero(isi)).to(dev)       # face slots that are interface nodes
     gid_pos = torch.from_numpy(gid.reshape(-1)[np.flatnonzero(isi)]).to(dev)
     rhs_d = torch.zeros(ni, dtype=torch.float64, device=dev)
+
+    def host_interface():
+        rhs_d.zero_()
+        rhs_d.index_add_(0, gid_pos, hf[:, 0, :].reshape(-1)[pos], alpha=-1.0)   # -sum of the boxes' fluxes
+        rhs = rhs_d.cpu().numpy()
+        t1 = _time.time()
+        u_if = lu.solve(rhs)
+        dt_host = _time.time() - t1
+        u_if_d = torch.from_numpy(u_if).to(dev)
+        ub[:, 0, :] = torch.where(isi_t, u_if_d[gid_t], 0.0)
+        return dt_host
+
     nsteps = args.steps * 10
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    gpu_ms, host_s = 0.0, 0.0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    leaf_ms, iface_ms, host_s = 0.0, 0.0, 0.0
     for step in range(args.warmup + nsteps):
         if step == args.warmup:   # the warm-up steps (graph capture, first loads) are not timed
             torch.cuda.synchronize(dev)
-            gpu_ms, host_s = 0.0, 0.0
+            leaf_ms, iface_ms, host_s = 0.0, 0.0, 0.0
             t_all = _time.time()
+            ev[4].record(stream)
         ev[0].record(stream)
         H.hps_leaf_apply(ctx, kind, nbox, 1, b, u, Au, stream)
         torch.mul(u, 2.0 * c, out=f)
         f.sub_(Au)
         H.hps_leaf_solve_factored(F, 1, f, v, hf, st, stream)
         ev[1].record(stream)
-        rhs_d.zero_()
-        rhs_d.index_add_(0, gid_pos, hf[:, 0, :].reshape(-1)[pos], alpha=-1.0)   # -sum of the boxes' fluxes
-        rhs = rhs_d.cpu().numpy()
-        t0 = _time.time()
-        u_if = lu.solve(rhs)
-        host_s += _time.time() - t0
-        u_if_d = torch.from_numpy(u_if).to(dev)
-        ub[:, 0, :] = torch.where(isi_t, u_if_d[gid_t], 0.0)
+        if gpu_iface:
+            H.hps_interface_solve(FI, 1, hf, None, ub, stream)
+        else:
+            host_s += host_interface()
         ev[2].record(stream)
         H.hps_leaf_reconstruct_factored(F, 1, v, ub, ui, st, stream)
         u.zero_()
         u[:, 0, ii_d] = ui[:, 0, :]
         u[:, 0, fi_d] = ub[:, 0, :]
         ev[3].record(stream)
-        torch.cuda.synchronize(dev)
-        gpu_ms += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+        if not gpu_iface:
+            torch.cuda.synchronize(dev)
+            leaf_ms += ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+    torch.cuda.synchronize(dev)
     wall = _time.time() - t_all
-    fails = int((st != 0).sum().item())
-    H.hps_leaf_factors_destroy(F)
-    H.hps_destroy(ctx)
+    loop_ms = ev[4].elapsed_time(ev[3])
     tend = dt * (args.warmup + nsteps)
     exact = np.exp(-3 * np.pi ** 2 * kd * tend) * u0[:, ii]
     err = float(np.abs(ui[:, 0, :].cpu().numpy() - exact).max())
-    line = {"metric": "Crank-Nicolson heat-equation steps/s (4x4x4 boxes, p=12; leaf work on the GPU, interface LU on the host)",
-            "value": nsteps / wall, "unit": "steps/s", "n_gpus": 1, "steps": nsteps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * wall / nsteps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
+    fails = int((st != 0).sum().item())
+    if gpu_iface:
+        # per-stage times of one more step (events read after it), then a few
+        # host sparse-LU solves of its right-hand side for comparison
+        ev[0].record(stream)
+        H.hps_leaf_apply(ctx, kind, nbox, 1, b, u, Au, stream)
+        torch.mul(u, 2.0 * c, out=f)
+        f.sub_(Au)
+        H.hps_leaf_solve_factored(F, 1, f, v, hf, st, stream)
+        ev[1].record(stream)
+        H.hps_interface_solve(FI, 1, hf, None, ub, stream)
+        ev[2].record(stream)
+        H.hps_leaf_reconstruct_factored(F, 1, v, ub, ui, st, stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize(dev)
+        leaf_ms = (ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])) * nsteps
+        iface_ms = ev[1].elapsed_time(ev[2]) * nsteps
+        for _ in range(5):
+            host_s += host_interface()
+        host_s *= nsteps / 5.0
+        torch.cuda.synchronize(dev)
+    info = H.hps_interface_info(FI) if gpu_iface else None
+    if FI is not None:
+        H.hps_interface_destroy(FI)
+    H.hps_leaf_factors_destroy(F)
+    H.hps_destroy(ctx)
+    where = "GPU" if gpu_iface else "host sparse LU"
+    line = {"metric": f"Crank-Nicolson heat-equation steps/s (4x4x4 boxes, p=12; leaf work on the GPU, "
+                      f"interface solve: {where})",
+            "value": nsteps / (loop_ms / 1e3) if gpu_iface else nsteps / wall, "unit": "steps/s", "n_gpus": 1,
+            "steps": nsteps, "warmup": args.warmup,
+            "ms_per_step": loop_ms / nsteps if gpu_iface else 1e3 * wall / nsteps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"u_t = {kd} Lap u on the unit cube, u = 0 on the boundary, u0 = sin(pi x) sin(pi y) "
                                    f"sin(pi z); {nbox} boxes, p = {p}, dt = {dt}, {args.warmup} + {nsteps} steps (the "
-                                   f"first untimed); stored factors "
-                                   f"(FP32 LU + FP64 refinement); {ni} interface unknowns"},
-            "gpu_leaf_ms_per_step": gpu_ms / nsteps, "host_interface_ms_per_step": 1e3 * host_s / nsteps,
+                                   f"first untimed); stored leaf factors (FP32 LU + FP64 refinement); {ni} interface "
+                                   f"unknowns, interface solve: {where}", "interface": args.interface},
+            "wall_ms_per_step": 1e3 * wall / nsteps,
+            "gpu_leaf_ms_per_step": leaf_ms / nsteps,
+            "interface_ms_per_step": (iface_ms / nsteps) if gpu_iface else 1e3 * host_s / nsteps,
+            "host_sparse_lu_solve_ms": 1e3 * host_s / nsteps,
             "graphs": True,
-            "setup": {"gpu_dtn_and_factor_s": t_gpu_setup, "host_assembly_and_lu_s": t_host_setup},
+            "setup": {"gpu_dtn_and_factor_s": t_gpu_setup, "gpu_interface_factor_s": t_iface_setup,
+                      "host_assembly_and_lu_s": t_host_setup},
             "max_abs_err_vs_exact": err, "box_failures": fails}
+    if info is not None:
+        line["interface_factor"] = {"merges": info[0], "levels": info[1], "largest_separator": info[2],
+                                    "device_bytes": info[3]}
     print(json.dumps(line), flush=True)
 
 

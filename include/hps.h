@@ -350,6 +350,64 @@ hps_status hps_leaf_reconstruct_factored(hps_leaf_factors* factors, int nrhs, co
                                          double* ui, int* box_status, void* stream);
 void hps_leaf_factors_destroy(hps_leaf_factors* factors);
 
+/* ---- Interface solve on the GPU (nested dissection over the box grid) -----
+ *
+ * The interface system of Sec. 3.1 for an nb[0] x nb[1] x nb[2] grid of leaf
+ * boxes of order p: at every face node shared by two boxes the outward fluxes
+ * T^tau u_b^tau + h^tau of both add up to zero (Eq. 4 with f_b = 0), and u = g
+ * is known on the faces of the outer boundary (moved to the right-hand side).
+ * The paper factors it on the host with MUMPS (Sec. 3.2).  Here it is
+ * factored on the device by the hierarchical merge that Sec. 3 recalls from
+ * the original HPS method: the box range is halved along its longest axis
+ * (in boxes, ties to the lower axis) recursively; each merge of halves a, b
+ * eliminates the nodes of the face between them (3) against the halves'
+ * other boundary nodes (1, 2):
+ *     W = T^a_33 + T^b_33,  S = -W^{-1} [T^a_31  T^b_32],
+ *     merged map  diag(T^a_11, T^b_22) + [T^a_13; T^b_23] S,
+ * with an FP64 LU with partial pivoting of W per merge, all merges of a level
+ * in one batch.  Pivoting is local to each W (MUMPS may pivot more widely).
+ *
+ * hps_interface_factor: T device [nbox][m][m], the leaf DtN maps (boxes x
+ * fastest, then y, then z), read during the call only (their columns on the
+ * outer faces are copied for the Dirichlet term).  nrhs_max (1..256): the
+ * largest nrhs of later solves.  Synchronous: it returns once the
+ * factorisation has finished on `stream`.  Returns HPS_EINVAL for bad
+ * arguments, HPS_ENOMEM when device memory runs out or a separator exceeds
+ * 14,000 nodes (an 8 x 8 x 8 grid at p = 16 has 12,544 at the top),
+ * HPS_ESINGULAR when some W had an exactly zero pivot (no handle is made).
+ *
+ * hps_interface_solve: h device [nbox][nrhs][m], the leaf fluxes (the h of
+ * hps_leaf_particular / hps_leaf_solve_factored); g device [nbox][nrhs][m] or
+ * NULL, the Dirichlet values, read only on each box's faces that lie on the
+ * outer boundary (NULL: g = 0).  Writes u_b device [nbox][nrhs][m], the face
+ * values of every box (the interface solution on shared faces, g on outer
+ * ones) in the layout hps_leaf_reconstruct reads (Sec. 2.2 step 3,
+ * Algorithm 2).  Enqueued on `stream`, allocates nothing; solves on one
+ * handle share its buffers and must not overlap.  HPS_EINVAL for nrhs out
+ * of range or NULL arrays.
+ *
+ * hps_interface_info: merges, levels, largest separator (nodes) and the
+ * device bytes the handle holds.
+ *
+ * hps_interface_plan (host only, no GPU): the merge tree.  *n_merge = nbox - 1
+ * merges, numbered nbox .. 2 nbox - 2 in order of height (root last); leaves
+ * are the boxes 0 .. nbox-1.  nodes [n_merge][8]: child a, child b, height,
+ * axis, na1, nsep, nb2, offset into lists; lists holds a1 (na1), a3 (nsep),
+ * b2 (nb2), b3 (nsep): face slots of the children (a leaf's slot is its local
+ * face 0..5; a merge's slot i is the i-th face of its boundary, which lists
+ * a's faces at a1 and then b's at b2).  a1/b2: faces off the separator,
+ * a3/b3: separator faces, both in the same order.  Call with NULL arrays to
+ * get the sizes. */
+typedef struct hps_interface hps_interface;
+hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const double* T, int nrhs_max, void* stream,
+                                hps_interface** out);
+hps_status hps_interface_solve(hps_interface* iface, int nrhs, const double* h, const double* g, double* ub,
+                               void* stream);
+hps_status hps_interface_info(const hps_interface* iface, int* n_merge, int* n_levels, int* max_separator,
+                              size_t* bytes);
+void hps_interface_destroy(hps_interface* iface);
+hps_status hps_interface_plan(int p, const int nb[3], int* n_merge, int* n_list, int* nodes, int* lists);
+
 /* The collocation operator applied to full nodal fields: out = A u at every
  * interior node of each box, the interior rows of Eq. 2 (-Laplacian by the
  * three grid lines through the node, minus kappa^2 b u), and 0 at the face,

@@ -27,6 +27,8 @@ __all__ = [
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
+    "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
+    "hps_interface_plan",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -45,6 +47,8 @@ EXPORTED_SYMBOLS = (
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
+    "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
+    "hps_interface_plan",
 )
 
 # Kernel classes of hps_profile_get.
@@ -118,6 +122,11 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_reconstruct_factored": (i, [vp, i, vp, vp, vp, vp, vp]),
         "hps_leaf_factors_destroy": (None, [vp]),
         "hps_leaf_apply": (i, [vp, kp, i, i, vp, vp, vp, vp]),
+        "hps_interface_factor": (i, [vp, i, ip, vp, i, vp, ctypes.POINTER(vp)]),
+        "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
+        "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
+        "hps_interface_destroy": (None, [vp]),
+        "hps_interface_plan": (i, [i, ip, ip, ip, ip, ip]),
         "hps_assemble_interface_blocks": (i, [i, ip, dp, i64p, i64p, i64p, dp, i64p, i64p, i64p, dp, i64p, i64p]),
         "hps_last_refinement": (i, [vp, i, ip, dp]),
         "hps_profile_enable": (i, [vp, i]),
@@ -304,6 +313,52 @@ def hps_leaf_apply(ctx, kind: LeafKind, nbox: int, nfield: int, b, u, out, strea
 
 def hps_leaf_factors_destroy(factors) -> None:
     load_library().hps_leaf_factors_destroy(factors)
+
+
+def hps_interface_factor(ctx, p: int, nb, T, nrhs_max: int = 1, stream=None):
+    """Factors the interface system of an nb grid of boxes from their DtN maps
+    T [nbox, m, m] (device); returns the handle for hps_interface_solve."""
+    out = ctypes.c_void_p()
+    nb3 = (ctypes.c_int * 3)(*[int(v) for v in nb])
+    _check(load_library().hps_interface_factor(ctx, int(p), nb3, _ptr(T, _f64() if not isinstance(T, int) else None),
+                                               int(nrhs_max), _stream(stream), ctypes.byref(out)),
+           "hps_interface_factor")
+    return out
+
+
+def hps_interface_solve(iface, nrhs: int, h, g, ub, stream=None) -> None:
+    """u_b [nbox, nrhs, m] on every box face from the leaf fluxes h and the
+    Dirichlet values g (both [nbox, nrhs, m]; g None for g = 0)."""
+    f64 = _f64() if not isinstance(h, int) else None
+    _check(load_library().hps_interface_solve(iface, int(nrhs), _ptr(h, f64), _ptr(g, f64), _ptr(ub, f64),
+                                              _stream(stream)), "hps_interface_solve")
+
+
+def hps_interface_info(iface):
+    """(merges, levels, largest separator in nodes, device bytes held)."""
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(load_library().hps_interface_info(iface, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                             ctypes.byref(d)), "hps_interface_info")
+    return a.value, b.value, c.value, d.value
+
+
+def hps_interface_destroy(iface) -> None:
+    load_library().hps_interface_destroy(iface)
+
+
+def hps_interface_plan(p: int, nb):
+    """The merge tree (host only): (nodes [n_merge, 8] int32, lists int32), see hps.h."""
+    import numpy as np
+    lib = load_library()
+    nb3 = (ctypes.c_int * 3)(*[int(v) for v in nb])
+    nm, nl = ctypes.c_int(), ctypes.c_int()
+    _check(lib.hps_interface_plan(int(p), nb3, ctypes.byref(nm), ctypes.byref(nl), None, None), "hps_interface_plan")
+    nodes = np.zeros((max(nm.value, 1), 8), dtype=np.int32)
+    lists = np.zeros(max(nl.value, 1), dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check(lib.hps_interface_plan(int(p), nb3, ctypes.byref(nm), ctypes.byref(nl), nodes.ctypes.data_as(ip),
+                                  lists.ctypes.data_as(ip)), "hps_interface_plan")
+    return nodes[:nm.value], lists[:nl.value]
 
 
 def hps_last_refinement(ctx, nbox: int):

@@ -136,6 +136,8 @@ struct hps_leaf_factors {
 
 namespace hps {
 
+int ctx_device(const hps_ctx* ctx) { return ctx->device; }
+
 // ------------------------------------------------------------ 1-D operators
 
 // Chebyshev-Lobatto nodes on [-1,1], ascending, t_j = -cos(pi j / N), N = p-1

@@ -1,0 +1,200 @@
+"""GPU interface solve (nested dissection over the box grid) against the
+oracle's two-level solve with the host sparse LU (Sec. 3.1 assembly).
+
+The whole Dirichlet problem runs on the device through the C ABI: leaf DtN
+maps, particular solutions, the interface factorisation and solve, and the
+interior reconstruction.  Face values and interior values must match the
+oracle to 1e-11 (FP64 leaves) or 1e-9 (FP32 leaves with FP64 refinement).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import hps_inputs as hi
+import oracle
+import paper_2503_04033_gb300 as H
+from oracle import global_solve as gs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.hps_create(0, 0)
+    yield c
+    H.hps_destroy(c)
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def gpu_dirichlet_solve(ctx, grid, kappa, b_boxes, f_boxes, g_boxes, prec):
+    """T, v, h on the device, then the GPU interface solve and the
+    reconstruction.  f_boxes [nbox, nrhs, p^3]; g_boxes [nbox, nrhs, m] or None.
+    Returns (u_b [nbox, nrhs, m], u_i [nbox, nrhs, n])."""
+    import torch
+    p, nbox = grid.p, grid.nbox
+    n, m = H.hps_leaf_sizes(p)
+    nrhs = f_boxes.shape[1]
+    kind = H.LeafKind(p, grid.h, kappa)
+    b = _dev(b_boxes)
+    f = _dev(f_boxes)
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device="cuda")
+    v = torch.empty(nbox, nrhs, n, dtype=torch.float64, device="cuda")
+    hf = torch.empty(nbox, nrhs, m, dtype=torch.float64, device="cuda")
+    ub = torch.full((nbox, nrhs, m), np.nan, dtype=torch.float64, device="cuda")
+    ui = torch.empty(nbox, nrhs, n, dtype=torch.float64, device="cuda")
+    st = torch.full((nbox,), -1, dtype=torch.int32, device="cuda")
+    H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, prec, st)
+    H.hps_leaf_particular(ctx, kind, nbox, nrhs, b, f, v, hf, prec, st)
+    F = H.hps_interface_factor(ctx, p, grid.nb, T, nrhs)
+    try:
+        H.hps_interface_solve(F, nrhs, hf, None if g_boxes is None else _dev(g_boxes), ub)
+        H.hps_leaf_reconstruct(ctx, kind, nbox, nrhs, b, None, v, ub, ui, prec, st)
+        torch.cuda.synchronize()
+    finally:
+        H.hps_interface_destroy(F)
+    assert (st.cpu().numpy() == 0).all()
+    return ub.cpu().numpy(), ui.cpu().numpy()
+
+
+def _problem(grid, nrhs, seed, with_g=True):
+    p = grid.p
+    rng = np.random.default_rng(seed)
+    xyz = [H.hps_leaf_nodes(p, grid.box_lo(bx), grid.h) for bx in range(grid.nbox)]
+    b = np.stack([1.0 + 0.4 * np.cos(3 * x[:, 0] - x[:, 1] + 2 * x[:, 2]) for x in xyz])
+    f = np.stack([np.stack([np.sin((r + 1) * x[:, 0] + x[:, 1]) * np.exp(-x[:, 2] * r) for r in range(nrhs)])
+                  for x in xyz])
+    g_dir = rng.standard_normal((nrhs, grid.n_dir)) if with_g else np.zeros((nrhs, grid.n_dir))
+    return b, f, g_dir
+
+
+def _g_boxes(grid, g_dir, m, rng):
+    """g in the library's per-box layout; interface positions hold junk that
+    must not be read."""
+    nrhs = g_dir.shape[0]
+    g = rng.standard_normal((grid.nbox, nrhs, m)) * 1e3
+    for bx in range(grid.nbox):
+        isi, gid = grid.local_to_global(bx)
+        for r in range(nrhs):
+            g[bx, r, ~isi] = g_dir[r, gid[~isi]]
+    return g
+
+
+@pytest.mark.parametrize("nb,p,kappa,nrhs", [((2, 2, 2), 8, 10.0, 1), ((3, 2, 2), 7, 6.0, 2), ((4, 1, 2), 6, 3.0, 3),
+                                             ((2, 3, 3), 6, 8.0, 1)])
+def test_interface_solve_matches_oracle_fp64(ctx, nb, p, kappa, nrhs):
+    grid = gs.InterfaceGrid(p, nb, L=(1.0, 0.9, 1.1))
+    n, m = oracle.sizes(p)
+    b, f, g_dir = _problem(grid, nrhs, 3)
+    g = _g_boxes(grid, g_dir, m, np.random.default_rng(5))
+    ub, ui = gpu_dirichlet_solve(ctx, grid, kappa, b, f, g, H.HPS_FP64)
+    for r in range(nrhs):
+        # the oracle evaluates b and f at its own node coordinates
+        xo = [oracle.node_coords(p, grid.box_lo(bx), grid.h) for bx in range(grid.nbox)]
+        bo = [1.0 + 0.4 * np.cos(3 * x[:, 0] - x[:, 1] + 2 * x[:, 2]) for x in xo]
+        fo = [np.sin((r + 1) * x[:, 0] + x[:, 1]) * np.exp(-x[:, 2] * r) for x in xo]
+        ref = gs.hps_solve_boxes(grid, kappa, bo, fo, g_dir[r])
+        scale = max(np.abs(ref["u_iface"]).max(), np.abs(ref["u_int"]).max())
+        for bx in range(grid.nbox):
+            isi, gid = grid.local_to_global(bx)
+            assert np.abs(ub[bx, r, isi] - ref["u_iface"][gid[isi]]).max() < 1e-11 * scale
+            np.testing.assert_array_equal(ub[bx, r, ~isi], g_dir[r, gid[~isi]])
+        assert np.abs(ui[:, r, :] - ref["u_int"]).max() < 1e-11 * scale
+
+
+def test_interface_manufactured_solution(ctx):
+    """The manufactured-solution workload (2 x 2 x 2 boxes, p = 8, b = 1): the
+    all-GPU solve matches the oracle and the exact solution."""
+    kappa, p = 10.0, 8
+    grid = gs.InterfaceGrid(p, (2, 2, 2))
+    n, m = oracle.sizes(p)
+    b = np.ones((grid.nbox, p ** 3))
+    f = np.stack([hi.manufactured(H.hps_leaf_nodes(p, grid.box_lo(bx), grid.h), kappa)[1]
+                  for bx in range(grid.nbox)])[:, None, :]
+    ub, ui = gpu_dirichlet_solve(ctx, grid, kappa, b, f, None, H.HPS_FP64)
+    ref = gs.hps_solve(grid, kappa, lambda x: np.ones(len(x)), lambda x: hi.manufactured(x, kappa)[1],
+                       lambda x: hi.manufactured(x, kappa)[2])
+    scale = np.abs(ref["u_int"]).max()
+    assert np.abs(ui[:, 0, :] - ref["u_int"]).max() < 1e-11 * scale
+    exact = hi.manufactured(gs.interior_coords(grid), kappa)[0]
+    assert np.abs(ui[:, 0, :] - exact).max() < 1e-4
+
+
+@pytest.mark.parametrize("prec", [H.HPS_FP32_IR, H.HPS_BF16_IR], ids=["fp32ir", "bf16ir"])
+def test_interface_solve_mixed_leaves(ctx, prec):
+    p, kappa = 9, 12.0
+    grid = gs.InterfaceGrid(p, (2, 2, 3))
+    n, m = oracle.sizes(p)
+    b, f, g_dir = _problem(grid, 1, 9)
+    g = _g_boxes(grid, g_dir, m, np.random.default_rng(2))
+    ub, ui = gpu_dirichlet_solve(ctx, grid, kappa, b, f, g, prec)
+    xo = [oracle.node_coords(p, grid.box_lo(bx), grid.h) for bx in range(grid.nbox)]
+    bo = [1.0 + 0.4 * np.cos(3 * x[:, 0] - x[:, 1] + 2 * x[:, 2]) for x in xo]
+    fo = [np.sin(x[:, 0] + x[:, 1]) for x in xo]
+    ref = gs.hps_solve_boxes(grid, kappa, bo, fo, g_dir[0])
+    scale = max(np.abs(ref["u_iface"]).max(), np.abs(ref["u_int"]).max())
+    assert np.abs(ui[:, 0, :] - ref["u_int"]).max() < 1e-9 * scale
+
+
+def test_interface_single_box_and_repeat(ctx):
+    """One box has no shared face: u_b = g everywhere.  Two solves in a row on
+    one handle give the same answer."""
+    import torch
+    p = 6
+    grid = gs.InterfaceGrid(p, (1, 1, 1))
+    n, m = oracle.sizes(p)
+    T = _dev(np.random.default_rng(1).standard_normal((1, m, m)))
+    F = H.hps_interface_factor(ctx, p, (1, 1, 1), T, 2)
+    try:
+        assert H.hps_interface_info(F)[0] == 0
+        g = _dev(np.random.default_rng(2).standard_normal((1, 2, m)))
+        h = _dev(np.zeros((1, 2, m)))
+        ub = torch.empty(1, 2, m, dtype=torch.float64, device="cuda")
+        H.hps_interface_solve(F, 2, h, g, ub)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ub.cpu().numpy(), g.cpu().numpy())
+        H.hps_interface_solve(F, 1, h, None, ub)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ub.cpu().numpy()[:, :1], 0.0)
+    finally:
+        H.hps_interface_destroy(F)
+
+
+def test_interface_nrhs_change_and_errors(ctx):
+    """Solves with fewer loads than the handle was sized for give the same
+    columns; out-of-range arguments are rejected."""
+    import torch
+    p, kappa = 6, 5.0
+    grid = gs.InterfaceGrid(p, (2, 2, 1))
+    n, m = oracle.sizes(p)
+    b, f, g_dir = _problem(grid, 3, 4)
+    kind = H.LeafKind(p, grid.h, kappa)
+    T = torch.empty(grid.nbox, m, m, dtype=torch.float64, device="cuda")
+    H.hps_leaf_build_dtn(ctx, kind, grid.nbox, _dev(b), T, None, H.HPS_FP64)
+    F = H.hps_interface_factor(ctx, p, grid.nb, T, 3)
+    try:
+        n_merge, n_levels, max_sep, nbytes = H.hps_interface_info(F)
+        assert n_merge == 3 and n_levels == 2 and max_sep == 2 * (p - 2) ** 2 and nbytes > 0
+        hv = _dev(np.random.default_rng(3).standard_normal((grid.nbox, 3, m)))
+        u3 = torch.empty(grid.nbox, 3, m, dtype=torch.float64, device="cuda")
+        H.hps_interface_solve(F, 3, hv, None, u3)
+        h1 = hv[:, 1:2, :].contiguous()
+        u1 = torch.empty(grid.nbox, 1, m, dtype=torch.float64, device="cuda")
+        H.hps_interface_solve(F, 1, h1, None, u1)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(u1.cpu().numpy()[:, 0], u3.cpu().numpy()[:, 1], rtol=0, atol=1e-13 *
+                                   np.abs(u3.cpu().numpy()).max())
+        with pytest.raises(H.HpsError):
+            H.hps_interface_solve(F, 4, hv, None, u3)
+        with pytest.raises(H.HpsError):
+            H.hps_interface_solve(F, 0, hv, None, u3)
+    finally:
+        H.hps_interface_destroy(F)
+    with pytest.raises(H.HpsError):
+        H.hps_interface_factor(ctx, p, (0, 2, 2), T, 1)
+    with pytest.raises(H.HpsError):
+        H.hps_interface_factor(ctx, p, grid.nb, T, 0)

@@ -28,8 +28,10 @@ def _u0(X):
     return np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2])
 
 
-def library_crank_nicolson(ctx, grid, kappa_d, dt, nsteps, prec, u0):
-    """The time loop on the library's calls; returns (u_int [nbox, n], u_iface)."""
+def library_crank_nicolson(ctx, grid, kappa_d, dt, nsteps, prec, u0, iface="host"):
+    """The time loop on the library's calls; returns (u_int [nbox, n], u_iface).
+    iface: "host" solves the interface system with a host sparse LU of the
+    assembled blocks, "gpu" with the library's interface factorisation."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
     import torch
@@ -44,6 +46,7 @@ def library_crank_nicolson(ctx, grid, kappa_d, dt, nsteps, prec, u0):
     rows, cols, vals, _, _, _, ni, _ = H.hps_assemble_interface_blocks(p, grid.nb, T.cpu().numpy())
     lu = spla.splu(sp.coo_matrix((vals, (rows, cols)), shape=(ni, ni)).tocsc())
     F = H.hps_leaf_factor(ctx, kind, nbox, b, 1, prec)
+    FI = H.hps_interface_factor(ctx, p, grid.nb, T, 1) if iface == "gpu" else None
     try:
         ii, fi = gs.interior_grid_indices(p), gs.face_node_grid_indices(p)
         maps = [grid.local_to_global(bx) for bx in range(nbox)]
@@ -59,16 +62,25 @@ def library_crank_nicolson(ctx, grid, kappa_d, dt, nsteps, prec, u0):
             H.hps_leaf_apply(ctx, kind, nbox, 1, b, u, Au)
             f = (2.0 * c * u - Au).contiguous()
             H.hps_leaf_solve_factored(F, 1, f, v, hf, st)
-            hf_np = hf.cpu().numpy()[:, 0, :]
-            rhs = np.zeros(ni)
-            for bx in range(nbox):
-                isi, gid = maps[bx]
-                np.add.at(rhs, gid[isi], -hf_np[bx, isi])
-            u_if = lu.solve(rhs)
-            ub = np.zeros((nbox, m))
-            for bx in range(nbox):
-                isi, gid = maps[bx]
-                ub[bx, isi] = u_if[gid[isi]]
+            if FI is not None:
+                ub_d = torch.empty(nbox, 1, m, dtype=torch.float64, device="cuda")
+                H.hps_interface_solve(FI, 1, hf, None, ub_d)
+                ub = ub_d.cpu().numpy()[:, 0, :]
+                u_if = np.zeros(ni)
+                for bx in range(nbox):
+                    isi, gid = maps[bx]
+                    u_if[gid[isi]] = ub[bx, isi]
+            else:
+                hf_np = hf.cpu().numpy()[:, 0, :]
+                rhs = np.zeros(ni)
+                for bx in range(nbox):
+                    isi, gid = maps[bx]
+                    np.add.at(rhs, gid[isi], -hf_np[bx, isi])
+                u_if = lu.solve(rhs)
+                ub = np.zeros((nbox, m))
+                for bx in range(nbox):
+                    isi, gid = maps[bx]
+                    ub[bx, isi] = u_if[gid[isi]]
             H.hps_leaf_reconstruct_factored(F, 1, v, torch.from_numpy(ub[:, None, :].copy()).cuda(), ui, st)
             torch.cuda.synchronize()
             assert (st.cpu().numpy() == 0).all()
@@ -79,6 +91,8 @@ def library_crank_nicolson(ctx, grid, kappa_d, dt, nsteps, prec, u0):
         return ui.cpu().numpy()[:, 0, :], u_if
     finally:
         H.hps_leaf_factors_destroy(F)
+        if FI is not None:
+            H.hps_interface_destroy(FI)
 
 
 def test_apply_matches_oracle(ctx):
@@ -98,11 +112,12 @@ def test_apply_matches_oracle(ctx):
             assert np.abs(got[bx, c] - ref).max() < 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("iface", ["host", "gpu"])
 @pytest.mark.parametrize("prec,tol", [(H.HPS_FP64, 1e-11), (H.HPS_FP32_IR, 1e-9)], ids=["fp64", "fp32ir"])
-def test_crank_nicolson_heat_matches_oracle_and_exact(ctx, prec, tol):
+def test_crank_nicolson_heat_matches_oracle_and_exact(ctx, prec, tol, iface):
     grid = gs.InterfaceGrid(10, (2, 2, 2))
     kd, dt, nsteps = 0.05, 0.05, 10
-    ui, u_if = library_crank_nicolson(ctx, grid, kd, dt, nsteps, prec, _u0)
+    ui, u_if = library_crank_nicolson(ctx, grid, kd, dt, nsteps, prec, _u0, iface)
     ref = gs.crank_nicolson_heat(grid, kd, dt, nsteps, _u0)
     scale = np.abs(ref["u_int"]).max()
     assert np.abs(ui - ref["u_int"]).max() < tol * scale
