@@ -280,53 +280,94 @@ __global__ void k_if_down(const IfDesc* __restrict__ desc, const int* __restrict
     }
 }
 
-// O = [acc] O + alpha A B for a batch of small-N products (N = nrhs <= 8
-// columns per pass): one warp per output row, lanes striding over K, so each
-// row of A is read once, coalesced.  A [M][K] (pitch lda), B [K][N], O [M][N].
-template <int NC>
-__global__ void k_if_mv(int Mr, int K, int N, const double* __restrict__ A, long long lda, long long sA,
-                        const double* __restrict__ B, long long sB, double* __restrict__ O, long long sO,
-                        double alpha, int acc)
+// O = [acc] O + alpha A B for a batch of small-N products (N = nrhs <= 16,
+// NC columns per pass).  TPR threads share one output row (32 .. 256, sized
+// to K so that each thread reads a few elements of it) and a CTA of 256
+// threads takes 256 / TPR rows: rows of A are read once, coalesced, with
+// enough loads in flight per SM whether a level has one merge or hundreds.
+// Partial sums are joined by warp shuffles, across warps through shared
+// memory.  A [M][K] (pitch lda), B [K][N], O [M][N].
+template <int NC, int TPR>
+__global__ void __launch_bounds__(256) k_if_mv(int Mr, int K, int N, const double* __restrict__ A, long long lda,
+                                               long long sA, const double* __restrict__ B, long long sB,
+                                               double* __restrict__ O, long long sO, double alpha, int acc)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= Mr) return;
-    const double* Ar = A + (long long)blockIdx.y * sA + (long long)warp * lda;
+    constexpr int RPC = 256 / TPR, WPR = TPR / 32;
+    __shared__ double red[8][NC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = threadIdx.x % TPR, rloc = threadIdx.x / TPR;
+    const int row = blockIdx.x * RPC + rloc;
+    const bool live = row < Mr;
+    const double* Ar = A + (long long)blockIdx.y * sA + (long long)(live ? row : 0) * lda;
     const double* Bb = B + (long long)blockIdx.y * sB;
-    double* Or = O + (long long)blockIdx.y * sO + (long long)warp * N;
+    double* Or = O + (long long)blockIdx.y * sO + (long long)row * N;
     for (int c0 = 0; c0 < N; c0 += NC) {
         double s[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) s[c] = 0.0;
-        for (int k = lane; k < K; k += 32) {
-            const double a = Ar[k];
-            const double* Bk = Bb + (long long)k * N + c0;
+        if (live) {
+#pragma unroll 4
+            for (int k = t; k < K; k += TPR) {
+                const double a = Ar[k];
+                const double* Bk = Bb + (long long)k * N + c0;
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                if (c0 + c < N) s[c] += a * Bk[c];
+                for (int c = 0; c < NC; ++c)
+                    if (c0 + c < N) s[c] += a * Bk[c];
+            }
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
         }
-        if (lane == 0) {
+        if (WPR == 1) {
+            if (live) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                if (c0 + c < N) Or[c0 + c] = (acc ? Or[c0 + c] : 0.0) + alpha * s[c];
+                for (int c = 0; c < NC; ++c)
+                    if (lane == c && c0 + c < N) Or[c0 + c] = (acc ? Or[c0 + c] : 0.0) + alpha * s[c];
+            }
+        } else {
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) red[warp][c] = s[c];
+            }
+            __syncthreads();
+            if (live && t < NC && c0 + t < N) {
+                double v = 0.0;
+#pragma unroll
+                for (int w = 0; w < WPR; ++w) v += red[rloc * WPR + w][t];
+                Or[c0 + t] = (acc ? Or[c0 + t] : 0.0) + alpha * v;
+            }
+            __syncthreads();
         }
     }
 }
 
-// O = [acc] O + alpha A B over the merges of a level: warp-per-row products
+template <int NC>
+void launch_mv(int nn, int Mr, int N, int K, const double* A, long long lda, long long sA, const double* B,
+               long long sB, double* O, long long sO, double alpha, int acc, cudaStream_t st)
+{
+    // threads per row: about K / 8 elements each, 32 .. 256
+    int tpr = 32;
+    while (tpr < 256 && tpr * 8 < K) tpr *= 2;
+    const unsigned rows_per_cta = 256 / tpr;
+    dim3 grd((unsigned)((Mr + rows_per_cta - 1) / rows_per_cta), (unsigned)nn);
+    if (tpr == 32) k_if_mv<NC, 32><<<grd, 256, 0, st>>>(Mr, K, N, A, lda, sA, B, sB, O, sO, alpha, acc);
+    else if (tpr == 64) k_if_mv<NC, 64><<<grd, 256, 0, st>>>(Mr, K, N, A, lda, sA, B, sB, O, sO, alpha, acc);
+    else if (tpr == 128) k_if_mv<NC, 128><<<grd, 256, 0, st>>>(Mr, K, N, A, lda, sA, B, sB, O, sO, alpha, acc);
+    else k_if_mv<NC, 256><<<grd, 256, 0, st>>>(Mr, K, N, A, lda, sA, B, sB, O, sO, alpha, acc);
+}
+
+// O = [acc] O + alpha A B over the merges of a level: row-split products
 // for few columns, the register-tiled CUDA-core product otherwise.
 void if_product(int nn, int Mr, int N, int K, const double* A, long long lda, long long sA, const double* B,
                 long long sB, double* O, long long sO, double alpha, bool acc, cudaStream_t st)
 {
     if (Mr <= 0 || N <= 0 || nn <= 0) return;
     if (N <= 16) {
-        dim3 grd((unsigned)((Mr + 7) / 8), (unsigned)nn);
         hps::prof_begin(hps::KC_MISC, st);
-        k_if_mv<8><<<grd, 256, 0, st>>>(Mr, K, N, A, lda, sA, B, sB, O, sO, alpha, acc ? 1 : 0);
+        if (N <= 2) launch_mv<2>(nn, Mr, N, K, A, lda, sA, B, sB, O, sO, alpha, acc ? 1 : 0, st);
+        else launch_mv<8>(nn, Mr, N, K, A, lda, sA, B, sB, O, sO, alpha, acc ? 1 : 0, st);
         hps::prof_end(hps::KC_MISC, st, 2.0 * nn * Mr * (double)N * K, 8.0 * nn * ((double)Mr * K + (double)Mr * N));
         return;
     }
