@@ -370,11 +370,19 @@ void hps_leaf_factors_destroy(hps_leaf_factors* factors);
  * hps_interface_factor: T device [nbox][m][m], the leaf DtN maps (boxes x
  * fastest, then y, then z), read during the call only (their columns on the
  * outer faces are copied for the Dirichlet term).  nrhs_max (1..256): the
- * largest nrhs of later solves.  Synchronous: it returns once the
- * factorisation has finished on `stream`.  Returns HPS_EINVAL for bad
- * arguments, HPS_ENOMEM when device memory runs out or a separator exceeds
- * 14,000 nodes (an 8 x 8 x 8 grid at p = 16 has 12,544 at the top),
- * HPS_ESINGULAR when some W had an exactly zero pivot (no handle is made).
+ * largest nrhs of later solves.  precision: HPS_FP64 factors and stores every
+ * W^{-1}, S and merged-map block in FP64; HPS_FP32_IR does so in FP32 (CUDA-
+ * core FP32 LU and products) and keeps a copy of T in FP64, from which each
+ * solve refines its answer: with u the current face values, every box's flux
+ * T^tau u^tau + h^tau sums, over the boxes sharing a node, to the residual of
+ * the interface equations, and solving the system with those fluxes as loads
+ * gives the correction; corrections stop on the device when one is below
+ * 1e-14 of ||u|| or shrank by less than half, after at most 10.  Other
+ * precisions: HPS_EINVAL.  Synchronous: it returns once the factorisation has
+ * finished on `stream`.  Returns HPS_EINVAL for bad arguments, HPS_ENOMEM
+ * when device memory runs out or a separator exceeds 14,000 nodes (an
+ * 8 x 8 x 8 grid at p = 16 has 12,544 at the top), HPS_ESINGULAR when some
+ * W had an exactly zero pivot (no handle is made).
  *
  * hps_interface_solve: h device [nbox][nrhs][m], the leaf fluxes (the h of
  * hps_leaf_particular / hps_leaf_solve_factored); g device [nbox][nrhs][m] or
@@ -387,7 +395,9 @@ void hps_leaf_factors_destroy(hps_leaf_factors* factors);
  * of range or NULL arrays.
  *
  * hps_interface_info: merges, levels, largest separator (nodes) and the
- * device bytes the handle holds.
+ * device bytes the handle holds.  hps_interface_last_refinement
+ * (synchronises the device): the corrections the last HPS_FP32_IR solve took
+ * and its last relative correction ||du|| / ||u|| (0 and 0 for HPS_FP64).
  *
  * hps_interface_plan (host only, no GPU): the merge tree.  *n_merge = nbox - 1
  * merges, numbered nbox .. 2 nbox - 2 in order of height (root last); leaves
@@ -399,12 +409,13 @@ void hps_leaf_factors_destroy(hps_leaf_factors* factors);
  * a3/b3: separator faces, both in the same order.  Call with NULL arrays to
  * get the sizes. */
 typedef struct hps_interface hps_interface;
-hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const double* T, int nrhs_max, void* stream,
-                                hps_interface** out);
+hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const double* T, int nrhs_max,
+                                hps_precision precision, void* stream, hps_interface** out);
 hps_status hps_interface_solve(hps_interface* iface, int nrhs, const double* h, const double* g, double* ub,
                                void* stream);
 hps_status hps_interface_info(const hps_interface* iface, int* n_merge, int* n_levels, int* max_separator,
                               size_t* bytes);
+hps_status hps_interface_last_refinement(hps_interface* iface, int* corrections, double* rel_correction);
 void hps_interface_destroy(hps_interface* iface);
 hps_status hps_interface_plan(int p, const int nb[3], int* n_merge, int* n_list, int* nodes, int* lists);
 

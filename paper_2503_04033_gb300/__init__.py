@@ -28,7 +28,7 @@ __all__ = [
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
-    "hps_interface_plan",
+    "hps_interface_plan", "hps_interface_last_refinement",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = (
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
-    "hps_interface_plan",
+    "hps_interface_plan", "hps_interface_last_refinement",
 )
 
 # Kernel classes of hps_profile_get.
@@ -122,7 +122,8 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_reconstruct_factored": (i, [vp, i, vp, vp, vp, vp, vp]),
         "hps_leaf_factors_destroy": (None, [vp]),
         "hps_leaf_apply": (i, [vp, kp, i, i, vp, vp, vp, vp]),
-        "hps_interface_factor": (i, [vp, i, ip, vp, i, vp, ctypes.POINTER(vp)]),
+        "hps_interface_factor": (i, [vp, i, ip, vp, i, i, vp, ctypes.POINTER(vp)]),
+        "hps_interface_last_refinement": (i, [vp, ip, dp]),
         "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
         "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
         "hps_interface_destroy": (None, [vp]),
@@ -315,15 +316,24 @@ def hps_leaf_factors_destroy(factors) -> None:
     load_library().hps_leaf_factors_destroy(factors)
 
 
-def hps_interface_factor(ctx, p: int, nb, T, nrhs_max: int = 1, stream=None):
+def hps_interface_factor(ctx, p: int, nb, T, nrhs_max: int = 1, prec: int = HPS_FP64, stream=None):
     """Factors the interface system of an nb grid of boxes from their DtN maps
-    T [nbox, m, m] (device); returns the handle for hps_interface_solve."""
+    T [nbox, m, m] (device), in FP64 or FP32 with FP64 refinement in each
+    solve; returns the handle for hps_interface_solve."""
     out = ctypes.c_void_p()
     nb3 = (ctypes.c_int * 3)(*[int(v) for v in nb])
     _check(load_library().hps_interface_factor(ctx, int(p), nb3, _ptr(T, _f64() if not isinstance(T, int) else None),
-                                               int(nrhs_max), _stream(stream), ctypes.byref(out)),
+                                               int(nrhs_max), int(prec), _stream(stream), ctypes.byref(out)),
            "hps_interface_factor")
     return out
+
+
+def hps_interface_last_refinement(iface):
+    """(corrections, last relative correction) of the last FP32_IR solve."""
+    a, b = ctypes.c_int(), ctypes.c_double()
+    _check(load_library().hps_interface_last_refinement(iface, ctypes.byref(a), ctypes.byref(b)),
+           "hps_interface_last_refinement")
+    return a.value, b.value
 
 
 def hps_interface_solve(iface, nrhs: int, h, g, ub, stream=None) -> None:

@@ -31,10 +31,12 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-def gpu_dirichlet_solve(ctx, grid, kappa, b_boxes, f_boxes, g_boxes, prec):
-    """T, v, h on the device, then the GPU interface solve and the
-    reconstruction.  f_boxes [nbox, nrhs, p^3]; g_boxes [nbox, nrhs, m] or None.
-    Returns (u_b [nbox, nrhs, m], u_i [nbox, nrhs, n])."""
+def gpu_dirichlet_solve(ctx, grid, kappa, b_boxes, f_boxes, g_boxes, prec, iprec=H.HPS_FP64, refine=None):
+    """T, v, h on the device, then the GPU interface solve (factors in iprec)
+    and the reconstruction.  f_boxes [nbox, nrhs, p^3]; g_boxes [nbox, nrhs, m]
+    or None.  Returns (u_b [nbox, nrhs, m], u_i [nbox, nrhs, n]); refine, a
+    list, receives the interface solve's (corrections, last relative
+    correction)."""
     import torch
     p, nbox = grid.p, grid.nbox
     n, m = H.hps_leaf_sizes(p)
@@ -50,9 +52,11 @@ def gpu_dirichlet_solve(ctx, grid, kappa, b_boxes, f_boxes, g_boxes, prec):
     st = torch.full((nbox,), -1, dtype=torch.int32, device="cuda")
     H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, prec, st)
     H.hps_leaf_particular(ctx, kind, nbox, nrhs, b, f, v, hf, prec, st)
-    F = H.hps_interface_factor(ctx, p, grid.nb, T, nrhs)
+    F = H.hps_interface_factor(ctx, p, grid.nb, T, nrhs, iprec)
     try:
         H.hps_interface_solve(F, nrhs, hf, None if g_boxes is None else _dev(g_boxes), ub)
+        if refine is not None:
+            refine.append(H.hps_interface_last_refinement(F))
         H.hps_leaf_reconstruct(ctx, kind, nbox, nrhs, b, None, v, ub, ui, prec, st)
         torch.cuda.synchronize()
     finally:
@@ -84,14 +88,23 @@ def _g_boxes(grid, g_dir, m, rng):
     return g
 
 
+@pytest.mark.parametrize("iprec", [H.HPS_FP64, H.HPS_FP32_IR], ids=["fp64", "fp32ir"])
 @pytest.mark.parametrize("nb,p,kappa,nrhs", [((2, 2, 2), 8, 10.0, 1), ((3, 2, 2), 7, 6.0, 2), ((4, 1, 2), 6, 3.0, 3),
-                                             ((2, 3, 3), 6, 8.0, 1)])
-def test_interface_solve_matches_oracle_fp64(ctx, nb, p, kappa, nrhs):
+                                             ((2, 3, 3), 6, 8.0, 1), ((4, 4, 2), 6, 5.0, 5)])
+def test_interface_solve_matches_oracle(ctx, nb, p, kappa, nrhs, iprec):
+    """FP64 leaves; interface factors in FP64, or in FP32 with FP64 refinement
+    in the solve: both match the oracle to 1e-11."""
     grid = gs.InterfaceGrid(p, nb, L=(1.0, 0.9, 1.1))
     n, m = oracle.sizes(p)
     b, f, g_dir = _problem(grid, nrhs, 3)
     g = _g_boxes(grid, g_dir, m, np.random.default_rng(5))
-    ub, ui = gpu_dirichlet_solve(ctx, grid, kappa, b, f, g, H.HPS_FP64)
+    refine = []
+    ub, ui = gpu_dirichlet_solve(ctx, grid, kappa, b, f, g, H.HPS_FP64, iprec, refine)
+    corrections, rel = refine[0]
+    if iprec == H.HPS_FP32_IR:
+        assert 1 <= corrections <= 10 and rel < 1e-10, refine
+    else:
+        assert (corrections, rel) == (0, 0.0)
     for r in range(nrhs):
         # the oracle evaluates b and f at its own node coordinates
         xo = [oracle.node_coords(p, grid.box_lo(bx), grid.h) for bx in range(grid.nbox)]
@@ -164,6 +177,33 @@ def test_interface_single_box_and_repeat(ctx):
         H.hps_interface_destroy(F)
 
 
+def test_interface_fp32_refinement_reaches_fp64_factors(ctx):
+    """The FP32-factor solve refines to the FP64-factor solve's answer."""
+    import torch
+    p, kappa = 7, 9.0
+    grid = gs.InterfaceGrid(p, (3, 3, 2))
+    n, m = oracle.sizes(p)
+    b, f, g_dir = _problem(grid, 2, 8)
+    kind = H.LeafKind(p, grid.h, kappa)
+    T = torch.empty(grid.nbox, m, m, dtype=torch.float64, device="cuda")
+    H.hps_leaf_build_dtn(ctx, kind, grid.nbox, _dev(b), T, None, H.HPS_FP64)
+    hv = _dev(np.random.default_rng(4).standard_normal((grid.nbox, 2, m)))
+    g = _dev(_g_boxes(grid, g_dir, m, np.random.default_rng(6)))
+    out = {}
+    for iprec in (H.HPS_FP64, H.HPS_FP32_IR):
+        F = H.hps_interface_factor(ctx, p, grid.nb, T, 2, iprec)
+        try:
+            u = torch.empty(grid.nbox, 2, m, dtype=torch.float64, device="cuda")
+            H.hps_interface_solve(F, 2, hv, g, u)
+            torch.cuda.synchronize()
+            out[iprec] = (u.cpu().numpy(), H.hps_interface_last_refinement(F))
+        finally:
+            H.hps_interface_destroy(F)
+    u64, u32 = out[H.HPS_FP64][0], out[H.HPS_FP32_IR][0]
+    assert np.abs(u32 - u64).max() < 1e-12 * np.abs(u64).max()
+    assert out[H.HPS_FP32_IR][1][0] >= 1
+
+
 def test_interface_nrhs_change_and_errors(ctx):
     """Solves with fewer loads than the handle was sized for give the same
     columns; out-of-range arguments are rejected."""
@@ -198,3 +238,6 @@ def test_interface_nrhs_change_and_errors(ctx):
         H.hps_interface_factor(ctx, p, (0, 2, 2), T, 1)
     with pytest.raises(H.HpsError):
         H.hps_interface_factor(ctx, p, grid.nb, T, 0)
+    with pytest.raises(H.HpsError):
+        H.hps_interface_factor(ctx, p, grid.nb, T, 1, H.HPS_BF16_IR)
+
