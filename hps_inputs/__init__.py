@@ -11,6 +11,10 @@ data; no dataset is involved):
 * ``manufactured``: u = sin(pi x) sin(2 pi y) sin(pi z) on the unit cube with
   b = 1, so f = (6 pi^2 - kappa^2) u and g = 0 on the boundary.
 * ``gaussian_dip_b``: b = 1 - 0.5 exp(-|x - c|^2 / 0.04), c = (0.5, 0.5, 0.5).
+* ``green``: the accuracy study of Sec. 4.1 on the box GREEN_LO + [0, GREEN_L]
+  = [-1.1, 0.1] x [1, 2] x [1.2, 2.2]: u = cos(kappa |x|) / (4 pi |x|), the
+  free-space Green's function of Lap u + kappa^2 u (kappa = 0: Poisson), used
+  as the exact solution and its boundary values as g (b = 1, f = 0).
 * ``FourierField``: 1 + 0.5 sum_{q=1}^{16} a_q cos(2 pi k_q . x + phi_q), with
   k_q uniform over the nonzero integer vectors of length <= 4,
   a_q ~ N(0, 1/16), phi_q ~ U[0, 2 pi); clipped to [0.5, 1.5] for b, and
@@ -44,6 +48,17 @@ def manufactured(xyz: np.ndarray, kappa: float):
     u = np.sin(math.pi * x) * np.sin(2 * math.pi * y) * np.sin(math.pi * z)
     f = (6 * math.pi ** 2 - kappa ** 2) * u
     return u, f, u
+
+
+GREEN_LO = (-1.1, 1.0, 1.2)
+GREEN_L = (1.2, 1.0, 1.0)
+
+
+def green(xyz: np.ndarray, kappa: float) -> np.ndarray:
+    """cos(kappa |x|) / (4 pi |x|) at coordinates [..., 3] (the origin lies
+    outside the Sec. 4.1 domain)."""
+    r = np.sqrt((xyz ** 2).sum(axis=-1))
+    return np.cos(kappa * r) / (4.0 * math.pi * r)
 
 
 def gaussian_dip_b(xyz: np.ndarray) -> np.ndarray:
