@@ -97,13 +97,15 @@ def parse_args():
     ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
                     help="hps_set_option before timing, e.g. TC_PAIRS=1 (name without HPS_OPT_)")
-    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep", "dirichlet"),
+    ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep", "dirichlet",
+                                                 "accuracy"),
                     default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
     ap.add_argument("--train-boxes", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--gate-tol", type=float, default=3e-3)
+    ap.add_argument("--nb", type=int, default=8, help="dirichlet workload: boxes per axis")
     ap.add_argument("--interface", choices=("gpu", "host"), default="gpu",
                     help="timestep workload: interface solve on the GPU (nested dissection) or a host sparse LU")
     ap.add_argument("--ir-tol", type=float, default=None,
@@ -846,9 +848,9 @@ def run_factored(args):
 
 
 def run_dirichlet(args):
-    """The whole two-stage solve of the 8 x 8 x 8 grid at p = 12 (kappa = 20,
-    b = 1 - 0.5 exp(-|x - c|^2 / 0.04), f = 1, g = 0; 134,400 interface
-    unknowns) on the GPU: build stage = leaf DtN maps (FP32 LU + FP64
+    """The whole two-stage solve of an nb x nb x nb grid of boxes (default
+    8 x 8 x 8: 134,400 interface unknowns) at p = 12 (kappa = 20,
+    b = 1 - 0.5 exp(-|x - c|^2 / 0.04), f = 1, g = 0) on the GPU: build stage = leaf DtN maps (FP32 LU + FP64
     refinement) and the interface factorisation (nested dissection; FP32
     factors refined in FP64 in each solve, and FP64 factors for comparison);
     solve stage = particular solutions, the interface solve and the interior
@@ -858,7 +860,7 @@ def run_dirichlet(args):
     import paper_2503_04033_gb300 as H
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    p, nbx, kappa = 12, 8, 20.0
+    p, nbx, kappa = 12, args.nb, 20.0
     nb = (nbx, nbx, nbx)
     nbox = nbx ** 3
     lows, h = hi.box_grid_lo(nb)
@@ -942,7 +944,8 @@ def run_dirichlet(args):
     for r in results.values():
         r.pop("ui")
     total = head["build_ms"] + head["solve_ms"]
-    line = {"metric": "two-stage Dirichlet solve on the GPU, 8x8x8 boxes at p=12 (build stage, then solve stage)",
+    line = {"metric": f"two-stage Dirichlet solve on the GPU, {nbx}x{nbx}x{nbx} boxes at p=12 (build stage, then solve "
+                      f"stage)",
             "value": 1e3 / total, "unit": "solves/s (build + solve)", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": total, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 leaves, f32+f64 interface", "data": "synthetic",
@@ -950,6 +953,92 @@ def run_dirichlet(args):
                                    f"/ 0.04), f = 1, g = 0; {ni} interface unknowns"},
             "build_ms": head["build_ms"], "solve_ms": head["solve_ms"], "interface_fp32ir": head,
             "interface_fp64": other, "u_int_rel_diff_fp32ir_vs_fp64": diff, "box_failures": fails}
+    print(json.dumps(line), flush=True)
+
+
+def run_accuracy(args):
+    """The accuracy study of Sec. 4.1 run entirely on the GPU: Lap u +
+    kappa^2 u = 0 on [-1.1, 0.1] x [1, 2] x [1.2, 2.2] with the Green's
+    function cos(kappa |x|) / (4 pi |x|) as exact solution and its boundary
+    values as g, under p- and h-refinement (kappa = 0, 16, 30).  Leaf maps,
+    particular solutions and reconstruction in FP64 (S stored), the interface
+    factorised on the GPU in FP64.  Relative l2 error over the interior nodes
+    and, once each, the shared face nodes."""
+    import time as _time
+    import torch
+    import paper_2503_04033_gb300 as H
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = H.hps_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    table = {}
+    best = {}
+    t_all = _time.time()
+    for kappa in (0.0, 16.0, 30.0):
+        for p in (6, 8, 10, 12):
+            for nbx in (2, 4, 8):
+                nb = (nbx, nbx, nbx)
+                lows, h = hi.box_grid_lo(nb, L=hi.GREEN_L, lo=hi.GREEN_LO)
+                nbox = len(lows)
+                n, m = H.hps_leaf_sizes(p)
+                q = p - 2
+                qq = q * q
+                kind = H.LeafKind(p, h, kappa)
+                xyz = np.stack([H.hps_leaf_nodes(p, lo, h) for lo in lows])
+                r1 = np.arange(1, q + 1)
+                kk, jj, ii_ = np.meshgrid(r1, r1, r1, indexing="ij")
+                ii = (ii_ + p * jj + p * p * kk).reshape(-1)
+                fi, fid = [], []
+                for f_ in range(6):
+                    axis, sv = f_ // 2, (0 if f_ % 2 == 0 else p - 1)
+                    for bb in range(1, q + 1):
+                        for aa in range(1, q + 1):
+                            i3 = [aa, bb]
+                            i3.insert(axis, sv)
+                            fi.append(i3[0] + p * i3[1] + p * p * i3[2])
+                            fid.append(f_)
+                fi, fid = np.asarray(fi), np.asarray(fid)
+                b = torch.ones(nbox, p ** 3, dtype=torch.float64, device=dev)
+                f = torch.zeros(nbox, 1, p ** 3, dtype=torch.float64, device=dev)
+                g = torch.from_numpy(hi.green(xyz[:, fi, :], kappa)[:, None, :].copy()).to(dev)
+                T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
+                S = torch.empty(nbox, n, m, dtype=torch.float64, device=dev)
+                v = torch.empty(nbox, 1, n, dtype=torch.float64, device=dev)
+                hf = torch.empty(nbox, 1, m, dtype=torch.float64, device=dev)
+                ub = torch.empty(nbox, 1, m, dtype=torch.float64, device=dev)
+                ui = torch.empty(nbox, 1, n, dtype=torch.float64, device=dev)
+                st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+                H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, S, H.HPS_FP64, st, stream)
+                H.hps_leaf_particular(ctx, kind, nbox, 1, b, f, v, hf, H.HPS_FP64, st, stream)
+                FI = H.hps_interface_factor(ctx, p, nb, T, 1, H.HPS_FP64, stream=stream)
+                H.hps_interface_solve(FI, 1, hf, g, ub, stream)
+                H.hps_leaf_reconstruct(ctx, kind, nbox, 1, b, S, v, ub, ui, H.HPS_FP64, st, stream)
+                torch.cuda.synchronize(dev)
+                H.hps_interface_destroy(FI)
+                ok = int((st != 0).sum().item()) == 0
+                cell = np.rint((lows - np.asarray(hi.GREEN_LO)) / h).astype(int)
+                upper = cell + 1 < np.asarray(nb)[None, :]
+                keep = np.stack([upper[:, fid[r] // 2] & (fid[r] % 2 == 1) for r in range(m)], axis=1)
+                ue_i = hi.green(xyz[:, ii, :], kappa)
+                ue_b = hi.green(xyz[:, fi, :], kappa)[keep]
+                err = np.concatenate([(ui[:, 0, :].cpu().numpy() - ue_i).reshape(-1),
+                                      ub[:, 0, :].cpu().numpy()[keep] - ue_b])
+                rel = float(np.linalg.norm(err) / np.linalg.norm(np.concatenate([ue_i.reshape(-1), ue_b])))
+                table.setdefault(f"kappa={kappa:g}", {}).setdefault(f"p={p}", {})[f"{nbx}^3"] = rel if ok else None
+                if ok:
+                    best[kappa] = min(best.get(kappa, 1.0), rel)
+                del T, S
+    wall = _time.time() - t_all
+    H.hps_destroy(ctx)
+    line = {"metric": "Sec. 4.1 accuracy study on the GPU: smallest relative l2 error vs the Green's function (Poisson)",
+            "value": best.get(0.0), "unit": "relative l2 error", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * wall, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (analytic Green's function)",
+            "config": {"workload": "Lap u + kappa^2 u = 0 on [-1.1, 0.1] x [1, 2] x [1.2, 2.2], u = g = cos(kappa |x|) "
+                                   "/ (4 pi |x|); p in {6, 8, 10, 12}, 2^3 / 4^3 / 8^3 boxes, kappa in {0, 16, 30}"},
+            "best": {f"kappa={k:g}": v for k, v in best.items()},
+            "paper_floors": {"kappa=0": "about 1e-13", "kappa=16": "about 1e-11", "kappa=30": "about 1e-10"},
+            "errors": table}
     print(json.dumps(line), flush=True)
 
 
@@ -1173,7 +1262,8 @@ def main():
         run_timestep(args)
     elif args.workload == "dirichlet":
         run_dirichlet(args)
-
+    elif args.workload == "accuracy":
+        run_accuracy(args)
     else:
         run_ours(args)
 

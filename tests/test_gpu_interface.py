@@ -241,3 +241,67 @@ def test_interface_nrhs_change_and_errors(ctx):
     with pytest.raises(H.HpsError):
         H.hps_interface_factor(ctx, p, grid.nb, T, 1, H.HPS_BF16_IR)
 
+
+def gpu_green_error(ctx, p, nb, kappa, prec=H.HPS_FP64, iprec=H.HPS_FP64):
+    """The Sec. 4.1 study on the device: Lap u + kappa^2 u = 0 on
+    [-1.1, 0.1] x [1, 2] x [1.2, 2.2] with the Green's function's boundary
+    values; relative l2 error over the interior and (once each) the shared
+    face nodes."""
+    import torch
+    lows, h = hi.box_grid_lo(nb, L=hi.GREEN_L, lo=hi.GREEN_LO)
+    nbox = len(lows)
+    n, m = H.hps_leaf_sizes(p)
+    q = p - 2
+    kind = H.LeafKind(p, h, kappa)
+    xyz = np.stack([H.hps_leaf_nodes(p, lo, h) for lo in lows])
+    ii, fi, fid = _kept(p)
+    b = _dev(np.ones((nbox, p ** 3)))
+    f = _dev(np.zeros((nbox, 1, p ** 3)))
+    g = _dev(hi.green(xyz[:, fi, :], kappa)[:, None, :])    # read only on outer faces
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(nbox, n, m, dtype=torch.float64, device="cuda")
+    v = torch.empty(nbox, 1, n, dtype=torch.float64, device="cuda")
+    hf = torch.empty(nbox, 1, m, dtype=torch.float64, device="cuda")
+    ub = torch.empty(nbox, 1, m, dtype=torch.float64, device="cuda")
+    ui = torch.empty(nbox, 1, n, dtype=torch.float64, device="cuda")
+    st = torch.zeros(nbox, dtype=torch.int32, device="cuda")
+    H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, S, prec, st)
+    H.hps_leaf_particular(ctx, kind, nbox, 1, b, f, v, hf, prec, st)
+    F = H.hps_interface_factor(ctx, p, nb, T, 1, iprec)
+    try:
+        H.hps_interface_solve(F, 1, hf, g, ub)
+        H.hps_leaf_reconstruct(ctx, kind, nbox, 1, b, S, v, ub, ui, prec, st)
+        torch.cuda.synchronize()
+    finally:
+        H.hps_interface_destroy(F)
+    assert (st.cpu().numpy() == 0).all()
+    ue_i = hi.green(xyz[:, ii, :], kappa)
+    cell = (lows - np.asarray(hi.GREEN_LO)) / h
+    upper = np.rint(cell).astype(int) + 1 < np.asarray(nb)[None, :]   # this box's + face is shared
+    keep = np.stack([upper[:, fid[r] // 2] & (fid[r] % 2 == 1) for r in range(m)], axis=1)
+    ue_b = hi.green(xyz[:, fi, :], kappa)[keep]
+    err = np.concatenate([(ui.cpu().numpy()[:, 0, :] - ue_i).reshape(-1), ub.cpu().numpy()[:, 0, :][keep] - ue_b])
+    return np.linalg.norm(err) / np.linalg.norm(np.concatenate([ue_i.reshape(-1), ue_b]))
+
+
+def _kept(p):
+    from tests._geom import kept_grid_indices
+    return kept_grid_indices(p)
+
+
+@pytest.mark.parametrize("kappa,p,nb", [(0.0, 10, (2, 2, 2)), (0.0, 12, (2, 2, 2)), (0.0, 8, (3, 3, 3)),
+                                        (16.0, 12, (2, 2, 2))])
+def test_green_function_accuracy_matches_oracle(ctx, kappa, p, nb):
+    """Sec. 4.1's accuracy study run entirely on the device gives the
+    oracle's discretisation error (same discrete system), and the Poisson
+    error at p = 12 is at the paper's floor (about 1e-13)."""
+    from oracle import global_solve as gs
+    err = gpu_green_error(ctx, p, nb, kappa)
+    grid = gs.InterfaceGrid(p, nb, lo=hi.GREEN_LO, L=hi.GREEN_L)
+    gfn = lambda x: hi.green(x, kappa)
+    r = gs.hps_solve(grid, kappa, lambda x: np.ones(len(x)), lambda x: np.zeros(len(x)), gfn)
+    ue = np.concatenate([gfn(gs.interior_coords(grid)).reshape(-1), gfn(gs.iface_coords(grid))])
+    ref = np.linalg.norm(np.concatenate([r["u_int"].reshape(-1), r["u_iface"]]) - ue) / np.linalg.norm(ue)
+    assert abs(err - ref) < 1e-12 + 1e-3 * ref, (err, ref)
+    if kappa == 0.0 and p == 12:
+        assert err < 1e-12
