@@ -106,6 +106,8 @@ def parse_args():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--gate-tol", type=float, default=3e-3)
     ap.add_argument("--nb", type=int, default=8, help="dirichlet workload: boxes per axis")
+    ap.add_argument("--leaf-prec", choices=("fp32ir", "fp64"), default="fp32ir",
+                    help="timestep workload: precision of the stored leaf factors")
     ap.add_argument("--interface", choices=("gpu", "host"), default="gpu",
                     help="timestep workload: interface solve on the GPU (nested dissection) or a host sparse LU")
     ap.add_argument("--ir-tol", type=float, default=None,
@@ -1075,8 +1077,9 @@ def run_timestep(args):
     gpu_iface = args.interface == "gpu"
     t0 = _time.time()
     T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
+    lprec = {"fp32ir": H.HPS_FP32_IR, "fp64": H.HPS_FP64}[args.leaf_prec]
     H.hps_leaf_build_dtn(ctx, kind, nbox, b, T, None, H.HPS_FP32_IR, None, stream)
-    F = H.hps_leaf_factor(ctx, kind, nbox, b, 1, H.HPS_FP32_IR, None, stream)
+    F = H.hps_leaf_factor(ctx, kind, nbox, b, 1, lprec, None, stream)
     torch.cuda.synchronize(dev)
     t_gpu_setup = _time.time() - t0
     t0 = _time.time()
@@ -1214,11 +1217,13 @@ def run_timestep(args):
             "value": nsteps / (loop_ms / 1e3) if gpu_iface else nsteps / wall, "unit": "steps/s", "n_gpus": 1,
             "steps": nsteps, "warmup": args.warmup,
             "ms_per_step": loop_ms / nsteps if gpu_iface else 1e3 * wall / nsteps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.leaf_prec == "fp32ir" else "f64",
+            "data": "synthetic",
             "config": {"workload": f"u_t = {kd} Lap u on the unit cube, u = 0 on the boundary, u0 = sin(pi x) sin(pi y) "
                                    f"sin(pi z); {nbox} boxes, p = {p}, dt = {dt}, {args.warmup} + {nsteps} steps (the "
-                                   f"first untimed); stored leaf factors (FP32 LU + FP64 refinement); {ni} interface "
-                                   f"unknowns, interface solve: {where}", "interface": args.interface},
+                                   f"first untimed); stored leaf factors ({args.leaf_prec}); {ni} interface "
+                                   f"unknowns, interface solve: {where}", "interface": args.interface,
+                       "leaf_factors": args.leaf_prec},
             "wall_ms_per_step": 1e3 * wall / nsteps,
             "gpu_leaf_ms_per_step": leaf_ms / nsteps,
             "interface_ms_per_step": (iface_ms / nsteps) if gpu_iface else 1e3 * host_s / nsteps,

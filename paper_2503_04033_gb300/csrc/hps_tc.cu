@@ -1039,18 +1039,53 @@ __global__ void k_gather_pack_f16(const float* __restrict__ M, long long ldm, lo
     const float* Mb = M + box * sM;
     const float* rcb = rc + box * sC;
     const int c = cb + tx;
-    float mx = 0.0f;
-    for (int i = ty; i < gK; i += 8) {
-        float v = 0.0f;
-        if (i < nb && c < nc) {
-            const int srcr = k + (perm ? perm[box * sP + i] : i);
-            v = Mb[(long long)srcr * ldm + c0 + c] * rcb[i];
-            if (W) W[box * sW + (long long)i * ldw + c] = Mb[(long long)(k + i) * ldm + c0 + c];
-            mx = fmaxf(mx, fabsf(v));
+    const int ncc = min(32, nc - cb);   // columns of this chunk (uniform over the CTA)
+    if (ncc == 32) {
+        float mx = 0.0f;
+        for (int i = ty; i < gK; i += 8) {
+            float v = 0.0f;
+            if (i < nb) {
+                const int srcr = k + (perm ? perm[box * sP + i] : i);
+                v = Mb[(long long)srcr * ldm + c0 + c] * rcb[i];
+                if (W) W[box * sW + (long long)i * ldw + c] = Mb[(long long)(k + i) * ldm + c0 + c];
+                mx = fmaxf(mx, fabsf(v));
+            }
+            gt[i * 33 + tx] = v;
         }
-        gt[i * 33 + tx] = v;
+        red[ty][tx] = mx;
+    } else {
+        // a narrow chunk (few right-hand sides, or the last columns): the 256
+        // threads split into ncc groups of tpc, one group per column, each
+        // thread taking every tpc-th row, so the scattered pivot-row loads of
+        // a column are issued together; column maxima through shared memory.
+        __shared__ float colmax[256];
+        const int tid = ty * 32 + tx;
+        const int tpc = 256 / ncc;               // threads per column, >= 8 (ncc <= 31)
+        const int cc = tid / tpc, r0 = tid - cc * tpc;
+        float mx = 0.0f;
+        if (cc < ncc) {
+            for (int i = r0; i < gK; i += tpc) {
+                float v = 0.0f;
+                if (i < nb) {
+                    const int srcr = k + (perm ? perm[box * sP + i] : i);
+                    v = Mb[(long long)srcr * ldm + c0 + cb + cc] * rcb[i];
+                    if (W) W[box * sW + (long long)i * ldw + cb + cc] = Mb[(long long)(k + i) * ldm + c0 + cb + cc];
+                    mx = fmaxf(mx, fabsf(v));
+                }
+                gt[i * 33 + cc] = v;
+            }
+        }
+        colmax[tid] = mx;
+        __syncthreads();
+        if (tid < 32) {
+            float m = 0.0f;
+            if (tid < ncc)
+                for (int t = tid * tpc; t < (tid + 1) * tpc; ++t) m = fmaxf(m, colmax[t]);
+            red[0][tid] = m;
+#pragma unroll
+            for (int r = 1; r < 8; ++r) red[r][tid] = 0.0f;
+        }
     }
-    red[ty][tx] = mx;
     __syncthreads();
     if (ty == 0) {
         float m = red[0][tx];
