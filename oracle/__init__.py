@@ -16,6 +16,8 @@ each routine computes, with the paper passage it follows:
 * ``leaf_dtn``: S = -A_ii^{-1} A_ib and T = A_bb + A_bi S (Sec. 2.2, Eq. 8).
 * ``leaf_particular``: v = A_ii^{-1} f_i and h = A_bi v (Sec. 2.2 steps 1-2).
 * ``leaf_reconstruct``: u_i = v + S u_b (Sec. 2.2 step 4).
+* ``*_2d``: the same for a p x p grid per box (the 2-D form of the method,
+  Sec. 1 and Sec. 3.2; four edges of p - 2 nodes, corners dropped).
 
 ``oracle.global_solve`` adds the interface system and the dense brute-force
 check; ``oracle.pins`` holds the closed forms the tests pin the oracle to.
@@ -73,6 +75,12 @@ def _load():
                 "oc_leaf_reconstruct": (c_int, [c_int, dp, c_double, dp, dp, c_int, dp, dp, dp]),
                 "oc_batch_dtn": (None, [c_int, dp, c_double, c_int, dp, dp, dp, ip, c_int]),
                 "oc_max_threads": (c_int, []),
+                "oc2_sizes": (c_int, [c_int, ip, ip]),
+                "oc2_node_coords": (None, [c_int, dp, dp, dp]),
+                "oc2_kept_index": (c_int, [c_int, c_int, c_int]),
+                "oc2_leaf_matrix": (None, [c_int, dp, c_double, dp, dp]),
+                "oc2_leaf_dtn": (c_int, [c_int, dp, c_double, dp, dp, dp]),
+                "oc2_leaf_particular": (c_int, [c_int, dp, c_double, dp, c_int, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -234,3 +242,58 @@ def batch_dtn(p: int, h, kappa: float, b: np.ndarray, want_S: bool = False, nthr
     status = np.empty(nbox, dtype=np.int32)
     _load().oc_batch_dtn(p, _dp(_h3(h)), float(kappa), nbox, _dp(b), _dp(T), _dp(S), _ip(status), int(nthreads))
     return T, S, status
+
+
+# ------------------------------------------------------------------ 2-D
+
+
+def sizes_2d(p: int):
+    n, m = ctypes.c_int(), ctypes.c_int()
+    if _load().oc2_sizes(int(p), ctypes.byref(n), ctypes.byref(m)) != 0:
+        raise ValueError(f"p = {p} too small")
+    return n.value, m.value
+
+
+def node_coords_2d(p: int, lo, h) -> np.ndarray:
+    out = np.empty((p * p, 2))
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    h = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (2,)))
+    _load().oc2_node_coords(int(p), _dp(lo), _dp(h), _dp(out))
+    return out
+
+
+def kept_index_2d(p: int, i: int, j: int) -> int:
+    return _load().oc2_kept_index(int(p), int(i), int(j))
+
+
+def _h2(h):
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (2,)))
+
+
+def leaf_matrix_2d(p: int, h, kappa: float, b: np.ndarray) -> np.ndarray:
+    n, m = sizes_2d(p)
+    A = np.empty((n + m, n + m))
+    _load().oc2_leaf_matrix(int(p), _dp(_h2(h)), float(kappa), _dp(np.ascontiguousarray(b, dtype=np.float64)), _dp(A))
+    return A
+
+
+def leaf_dtn_2d(p: int, h, kappa: float, b: np.ndarray, want_S: bool = True):
+    """(T [m, m], S [n, m] or None, info) of one 2-D box."""
+    n, m = sizes_2d(p)
+    T = np.empty((m, m))
+    S = np.empty((n, m)) if want_S else None
+    info = _load().oc2_leaf_dtn(int(p), _dp(_h2(h)), float(kappa), _dp(np.ascontiguousarray(b, dtype=np.float64)),
+                                _dp(T), _dp(S) if S is not None else None)
+    return T, S, info
+
+
+def leaf_particular_2d(p: int, h, kappa: float, b: np.ndarray, f: np.ndarray):
+    """(v [nrhs, n], h [nrhs, m], info) for loads f [nrhs, p^2]."""
+    n, m = sizes_2d(p)
+    f = np.ascontiguousarray(np.atleast_2d(f), dtype=np.float64)
+    nrhs = f.shape[0]
+    v = np.empty((nrhs, n))
+    hf = np.empty((nrhs, m))
+    info = _load().oc2_leaf_particular(int(p), _dp(_h2(h)), float(kappa),
+                                       _dp(np.ascontiguousarray(b, dtype=np.float64)), nrhs, _dp(f), _dp(v), _dp(hf))
+    return v, hf, info

@@ -428,3 +428,168 @@ int oc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ================================================================== 2-D
+ *
+ * The two-dimensional form of the same reduction (Sec. 1 and Sec. 3.2 treat
+ * 2-D and 3-D alike: a p x p Chebyshev grid per box, corners dropped as in
+ * Remark 1, DtN maps of size about 4p x 4p).
+ *
+ * Index conventions:
+ *   grid node (i,j), 0 <= i,j < p, has index i + p*j;
+ *   interior node (i,j), 1 <= i,j <= q = p-2, has index (i-1) + q(j-1);
+ *   edge f in order x-, x+, y-, y+; edge node a (the free index, 1..q) has
+ *   index n + f q + (a-1) in the kept list;  n = q^2, m = 4q.
+ */
+
+int oc2_sizes(int p, int* n, int* m)
+{
+    if (p < 3) return -1;
+    int q = p - 2;
+    *n = q * q;
+    *m = 4 * q;
+    return 0;
+}
+
+/* Coordinates [p^2][2] of a box [lo, lo+h] in grid-node order. */
+void oc2_node_coords(int p, const double* lo, const double* h, double* xy)
+{
+    double* t = (double*)malloc(sizeof(double) * p);
+    oc_nodes(p, t);
+    for (int j = 0; j < p; ++j)
+        for (int i = 0; i < p; ++i) {
+            int g = i + p * j;
+            xy[2 * g + 0] = lo[0] + 0.5 * h[0] * (t[i] + 1.0);
+            xy[2 * g + 1] = lo[1] + 0.5 * h[1] * (t[j] + 1.0);
+        }
+    free(t);
+}
+
+/* Kept index of grid node (i,j) (interior first, then the four edges), or
+ * -1 for a corner. */
+int oc2_kept_index(int p, int i, int j)
+{
+    int q = p - 2, n = q * q, e = p - 1;
+    int bi = (i == 0 || i == e), bj = (j == 0 || j == e);
+    if (!bi && !bj) return (i - 1) + q * (j - 1);
+    if (bi && bj) return -1;
+    if (bi) return n + ((i == 0) ? 0 : 1) * q + (j - 1);
+    return n + ((j == 0) ? 2 : 3) * q + (i - 1);
+}
+
+void oc2_kept_to_grid(int p, int idx, int* gi, int* gj)
+{
+    int q = p - 2, n = q * q, e = p - 1;
+    if (idx < n) { *gi = idx % q + 1; *gj = idx / q + 1; return; }
+    int r = idx - n, f = r / q, a = r % q + 1;
+    int side = (f % 2 == 0) ? 0 : e;
+    if (f / 2 == 0) { *gi = side; *gj = a; }
+    else            { *gi = a; *gj = side; }
+}
+
+/* Local matrix over the kept nodes, (n+m) x (n+m) row-major:
+ *   interior row (i,j): -sum_i' D2x[i,i'] u(i',j) - sum_j' D2y[j,j'] u(i,j') - kappa^2 b(i,j) u(i,j);
+ *   edge row on side s of axis a: (n . e_a) sum_l D_a[e,l] u(... l ...), the
+ *   outward normal derivative, e the edge's own grid index along a.
+ * b holds all p^2 node values. */
+void oc2_leaf_matrix(int p, const double* h, double kappa, const double* b, double* A)
+{
+    int q = p - 2, n = q * q, m = 4 * q, N = n + m, e = p - 1;
+    double* Dhat = (double*)malloc(sizeof(double) * p * p);
+    double* D = (double*)malloc(sizeof(double) * 2 * p * p);
+    double* D2 = (double*)malloc(sizeof(double) * 2 * p * p);
+    oc_diff(p, Dhat);
+    for (int a = 0; a < 2; ++a) physical_d(p, h[a], Dhat, D + a * p * p, D2 + a * p * p);
+    memset(A, 0, sizeof(double) * (size_t)N * N);
+    for (int row = 0; row < N; ++row) {
+        int i, j;
+        oc2_kept_to_grid(p, row, &i, &j);
+        double* Ar = A + (size_t)row * N;
+        if (row < n) {
+            for (int l = 0; l < p; ++l) {
+                Ar[oc2_kept_index(p, l, j)] -= D2[0 * p * p + i * p + l];
+                Ar[oc2_kept_index(p, i, l)] -= D2[1 * p * p + j * p + l];
+            }
+            Ar[row] -= kappa * kappa * b[i + p * j];
+        } else {
+            int f = (row - n) / q, axis = f / 2;
+            double sgn = (f % 2 == 0) ? -1.0 : 1.0;
+            int own = (f % 2 == 0) ? 0 : e;
+            const double* Da = D + axis * p * p + own * p;
+            for (int l = 0; l < p; ++l) {
+                int col = axis == 0 ? oc2_kept_index(p, l, j) : oc2_kept_index(p, i, l);
+                Ar[col] += sgn * Da[l];
+            }
+        }
+    }
+    free(Dhat); free(D); free(D2);
+}
+
+/* S = -A_ii^{-1} A_ib (n x m) and T = A_bb + A_bi S (m x m), either NULL. */
+int oc2_leaf_dtn(int p, const double* h, double kappa, const double* b, double* T, double* S)
+{
+    int q = p - 2, n = q * q, m = 4 * q, N = n + m;
+    double* A = (double*)malloc(sizeof(double) * (size_t)N * N);
+    double* Aii = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* X = (double*)malloc(sizeof(double) * (size_t)n * m);
+    double* Abi = (double*)malloc(sizeof(double) * (size_t)m * n);
+    double* Abb = (double*)malloc(sizeof(double) * (size_t)m * m);
+    int* piv = (int*)malloc(sizeof(int) * n);
+    oc2_leaf_matrix(p, h, kappa, b, A);
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) {
+            double v = A[(size_t)r * N + c];
+            if (r < n && c < n) Aii[(size_t)r * n + c] = v;
+            else if (r < n)     X[(size_t)r * m + (c - n)] = -v;     /* -A_ib */
+            else if (c < n)     Abi[(size_t)(r - n) * n + c] = v;
+            else                Abb[(size_t)(r - n) * m + (c - n)] = v;
+        }
+    free(A);
+    int info = oc_lu(n, Aii, piv);
+    if (info == 0) {
+        oc_lu_solve(n, Aii, piv, m, X);
+        if (S) memcpy(S, X, sizeof(double) * (size_t)n * m);
+        if (T) matmul_add(m, n, m, Abi, X, Abb, T);
+    }
+    free(Aii); free(X); free(Abi); free(Abb); free(piv);
+    return info;
+}
+
+/* v = A_ii^{-1} f_i and h = A_bi v for nrhs loads f [nrhs][p^2] (grid
+ * order); v [nrhs][n], hflux [nrhs][m]. */
+int oc2_leaf_particular(int p, const double* h, double kappa, const double* b, int nrhs, const double* f,
+                        double* v, double* hflux)
+{
+    int q = p - 2, n = q * q, m = 4 * q, N = n + m;
+    double* A = (double*)malloc(sizeof(double) * (size_t)N * N);
+    double* Aii = (double*)malloc(sizeof(double) * (size_t)n * n);
+    double* Abi = (double*)malloc(sizeof(double) * (size_t)m * n);
+    double* X = (double*)malloc(sizeof(double) * (size_t)n * nrhs);
+    int* piv = (int*)malloc(sizeof(int) * n);
+    oc2_leaf_matrix(p, h, kappa, b, A);
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < n; ++c) {
+            if (r < n) Aii[(size_t)r * n + c] = A[(size_t)r * N + c];
+            else       Abi[(size_t)(r - n) * n + c] = A[(size_t)r * N + c];
+        }
+    free(A);
+    for (int r = 0; r < n; ++r) {
+        int i, j;
+        oc2_kept_to_grid(p, r, &i, &j);
+        for (int c = 0; c < nrhs; ++c) X[(size_t)r * nrhs + c] = f[(size_t)c * p * p + i + p * j];
+    }
+    int info = oc_lu(n, Aii, piv);
+    if (info == 0) {
+        oc_lu_solve(n, Aii, piv, nrhs, X);
+        for (int c = 0; c < nrhs; ++c)
+            for (int r = 0; r < n; ++r) v[(size_t)c * n + r] = X[(size_t)r * nrhs + c];
+        for (int c = 0; c < nrhs; ++c)
+            for (int r = 0; r < m; ++r) {
+                double acc = 0.0;
+                for (int l = 0; l < n; ++l) acc += Abi[(size_t)r * n + l] * X[(size_t)l * nrhs + c];
+                hflux[(size_t)c * m + r] = acc;
+            }
+    }
+    free(Aii); free(Abi); free(X); free(piv);
+    return info;
+}
