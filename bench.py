@@ -98,7 +98,7 @@ def parse_args():
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
                     help="hps_set_option before timing, e.g. TC_PAIRS=1 (name without HPS_OPT_)")
     ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep", "dirichlet",
-                                                 "accuracy"),
+                                                 "accuracy", "leaf2d"),
                     default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
@@ -1044,6 +1044,81 @@ def run_accuracy(args):
     print(json.dumps(line), flush=True)
 
 
+def run_leaf2d(args):
+    """The 2-D form of the leaf reduction (FP64): 64 x 64 boxes of the unit
+    square at p = 16 (n = 196 interior, m = 56 edge nodes per box), kappa =
+    40, b = 1 + 0.4 sin(6 x) cos(4 y), one load f = cos(3 x + y); a step is one
+    hps_leaf2d_solve (T, S, v, h of every box).  Inputs resident; the working
+    set (about 2 GB) exceeds L2."""
+    import torch
+    import paper_2503_04033_gb300 as H
+    import oracle
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p, nbx, kappa = 16, 64, 40.0
+    nbox = nbx * nbx
+    h = (1.0 / nbx, 1.0 / nbx)
+    n, m = H.hps_leaf2d_sizes(p)
+    q = p - 2
+    lows = [((bx % nbx) * h[0], (bx // nbx) * h[1]) for bx in range(nbox)]
+    xy = np.stack([H.hps_leaf_nodes(p, (lo[0], lo[1], 0.0), (h[0], h[1], 1.0))[:p * p, :2] for lo in lows])
+    bfn = lambda x: 1.0 + 0.4 * np.sin(6 * x[..., 0]) * np.cos(4 * x[..., 1])
+    ffn = lambda x: np.cos(3 * x[..., 0] + x[..., 1])
+    b = torch.from_numpy(bfn(xy)).to(dev)
+    f = torch.from_numpy(ffn(xy)[:, None, :].copy()).to(dev)
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
+    S = torch.empty(nbox, n, m, dtype=torch.float64, device=dev)
+    v = torch.empty(nbox, 1, n, dtype=torch.float64, device=dev)
+    hf = torch.empty(nbox, 1, m, dtype=torch.float64, device=dev)
+    st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        H.hps_leaf2d_solve(p, h, kappa, nbox, b, 1, f, T, S, v, hf, st, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    fails = int((st != 0).sum().item())
+    # the dense method's flops per box: LU 2/3 n^3, solves with m + 1 right-hand sides, D_n products
+    flops = 2.0 / 3.0 * n ** 3 + 2.0 * n * n * (m + 1) + 2.0 * q * m * (m + 1)
+    value = nbox / (ms / 1e3)
+    tflops = value * flops / 1e12
+    # parity on a sample against the oracle, and the oracle's rate
+    sel = np.linspace(0, nbox - 1, 16).astype(int)
+    worst = 0.0
+    t0 = time.perf_counter()
+    for bx in sel:
+        xo = oracle.node_coords_2d(p, lows[bx], h)
+        To, _, info = oracle.leaf_dtn_2d(p, h, kappa, bfn(xo), want_S=False)
+        worst = max(worst, float(np.linalg.norm(T[bx].cpu().numpy() - To) / np.linalg.norm(To)))
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "2-D leaf DtN builds/s at p=16 (FP64; T, S, v, h per box)", "value": value, "unit": "boxes/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{nbx}x{nbx} boxes of the unit square, p = {p} (n = {n}, m = {m}), kappa = {kappa}, "
+                                   "b = 1 + 0.4 sin(6x) cos(4y), one load f = cos(3x + y)",
+                       "l2": "inputs and workspace larger than L2, no flush"},
+            "tflops": tflops,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 issue rate 152 SMs x 2.07 GHz x 2 FMA/clk (the whole call, its LU "
+                                        "on the CUDA-core FP64 path)"},
+            "rel_err_vs_oracle_max": worst, "box_failures": fails, "clocks": clocks.summary(),
+            "cpu_baseline": {"value": len(sel) / cpu_s, "unit": "boxes/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": f"{len(sel)} boxes spread over the grid, 2-D FP64 oracle "
+                                                         "(T only), one box at a time"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_timestep(args):
     """Crank-Nicolson steps of the heat equation u_t = kappa_d Lap u on the unit
     cube (u = 0 on its boundary), 4 x 4 x 4 boxes at p = 12, as in Sec. 4.4:
@@ -1269,6 +1344,8 @@ def main():
         run_dirichlet(args)
     elif args.workload == "accuracy":
         run_accuracy(args)
+    elif args.workload == "leaf2d":
+        run_leaf2d(args)
     else:
         run_ours(args)
 

@@ -419,6 +419,38 @@ hps_status hps_interface_last_refinement(hps_interface* iface, int* corrections,
 void hps_interface_destroy(hps_interface* iface);
 hps_status hps_interface_plan(int p, const int nb[3], int* n_merge, int* n_list, int* nodes, int* lists);
 
+/* ---- The 2-D leaf reduction (FP64) ----------------------------------------
+ *
+ * The method in two dimensions (Sec. 1; Sec. 3.2 sizes the 2-D DtN maps at
+ * about 4p x 4p): per box a p x p Chebyshev-Lobatto grid on [lo, lo + h],
+ * corners dropped (Remark 1), n = (p-2)^2 interior and m = 4 (p-2) edge nodes,
+ * the operator -Lap u - kappa^2 b u with edge rows the outward normal
+ * derivative.  Layouts (row-major, boxes outermost, device memory):
+ *   grid node (i,j), 0 <= i,j < p                 index i + p j
+ *   interior node (i,j), 1 <= i,j <= p-2           index (i-1) + q (j-1)
+ *   edge f in the order x-, x+, y-, y+; edge node with free index a (1..q)
+ *                                                 index f q + (a-1)
+ *   b [nbox][p^2]   f [nbox][nrhs][p^2]   T [nbox][m][m]   S [nbox][n][m]
+ *   v [nbox][nrhs][n]   h [nbox][nrhs][m]   u_b [nbox][nrhs][m]   u_i [nbox][nrhs][n]
+ *
+ * hps_leaf2d_solve: one FP64 LU with partial pivoting of A_ii per box
+ * carrying [-A_ib | f_i] gives S = -A_ii^{-1} A_ib, T = A_bb + A_bi S
+ * (Sec. 2.2, Eq. 8) and, for nrhs (0..256) loads, v = A_ii^{-1} f_i and
+ * h = A_bi v (Algorithm 2).  T, S: either may be NULL (not both when
+ * nrhs = 0); f, v, h are required when nrhs > 0.  h[2] > 0 are the box
+ * sides, p in 3..24.  box_status (device [nbox] or NULL) as for the 3-D
+ * calls.  Workspace comes from the stream-ordered allocator
+ * (cudaMallocAsync) and is released on the stream.  HPS_EINVAL for bad
+ * arguments, HPS_ENOMEM when the workspace cannot be allocated.
+ *
+ * hps_leaf2d_reconstruct: u_i = v + S u_b (Sec. 2.2 step 4) with S from
+ * hps_leaf2d_solve; v may be NULL (then u_i = S u_b). */
+hps_status hps_leaf2d_solve(int p, const double h[2], double kappa, int nbox, const double* b, int nrhs,
+                            const double* f, double* T, double* S, double* v, double* hflux, int* box_status,
+                            void* stream);
+hps_status hps_leaf2d_reconstruct(int p, int nbox, int nrhs, const double* S, const double* v, const double* ub,
+                                  double* ui, void* stream);
+
 /* The collocation operator applied to full nodal fields: out = A u at every
  * interior node of each box, the interior rows of Eq. 2 (-Laplacian by the
  * three grid lines through the node, minus kappa^2 b u), and 0 at the face,

@@ -28,7 +28,8 @@ __all__ = [
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
-    "hps_interface_plan", "hps_interface_last_refinement",
+    "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
+    "hps_leaf2d_sizes",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -48,7 +49,7 @@ EXPORTED_SYMBOLS = (
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
-    "hps_interface_plan", "hps_interface_last_refinement",
+    "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
 )
 
 # Kernel classes of hps_profile_get.
@@ -124,6 +125,8 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_apply": (i, [vp, kp, i, i, vp, vp, vp, vp]),
         "hps_interface_factor": (i, [vp, i, ip, vp, i, i, vp, ctypes.POINTER(vp)]),
         "hps_interface_last_refinement": (i, [vp, ip, dp]),
+        "hps_leaf2d_solve": (i, [i, dp, d, i, vp, i, vp, vp, vp, vp, vp, vp, vp]),
+        "hps_leaf2d_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
         "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
         "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
         "hps_interface_destroy": (None, [vp]),
@@ -369,6 +372,32 @@ def hps_interface_plan(p: int, nb):
     _check(lib.hps_interface_plan(int(p), nb3, ctypes.byref(nm), ctypes.byref(nl), nodes.ctypes.data_as(ip),
                                   lists.ctypes.data_as(ip)), "hps_interface_plan")
     return nodes[:nm.value], lists[:nl.value]
+
+
+def hps_leaf2d_sizes(p: int):
+    """(n, m) = ((p-2)^2, 4 (p-2)) of a 2-D box."""
+    if p < 3 or p > 24:
+        raise HpsError(HPS_EINVAL, "hps_leaf2d_sizes")
+    return (p - 2) ** 2, 4 * (p - 2)
+
+
+def hps_leaf2d_solve(p: int, h, kappa: float, nbox: int, b, nrhs: int = 0, f=None, T=None, S=None, v=None,
+                     hflux=None, box_status=None, stream=None) -> None:
+    """2-D boxes: T, S, and for nrhs loads v, h (device tensors, see hps.h)."""
+    f64 = _f64() if not isinstance(b, int) else None
+    hh = (ctypes.c_double * 2)(*[float(x) for x in (h if hasattr(h, "__len__") else (h, h))])
+    _check(load_library().hps_leaf2d_solve(
+        int(p), hh, float(kappa), int(nbox), _ptr(b, f64), int(nrhs), _ptr(f, f64), _ptr(T, f64), _ptr(S, f64),
+        _ptr(v, f64), _ptr(hflux, f64),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf2d_solve")
+
+
+def hps_leaf2d_reconstruct(p: int, nbox: int, nrhs: int, S, v, ub, ui, stream=None) -> None:
+    f64 = _f64() if not isinstance(S, int) else None
+    _check(load_library().hps_leaf2d_reconstruct(int(p), int(nbox), int(nrhs), _ptr(S, f64), _ptr(v, f64),
+                                                 _ptr(ub, f64), _ptr(ui, f64), _stream(stream)),
+           "hps_leaf2d_reconstruct")
 
 
 def hps_last_refinement(ctx, nbox: int):
