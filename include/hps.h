@@ -419,6 +419,15 @@ hps_status hps_interface_last_refinement(hps_interface* iface, int* corrections,
 void hps_interface_destroy(hps_interface* iface);
 hps_status hps_interface_plan(int p, const int nb[3], int* n_merge, int* n_list, int* nodes, int* lists);
 
+/* The same for an nb[0] x nb[1] grid of 2-D boxes (hps_leaf2d_solve's maps
+ * T [nbox][m][m], m = 4 (p-2); h, g, u_b [nbox][nrhs][m]): the grid is split
+ * the same way, a "face" being an edge of p - 2 nodes (slots 0..3 of a leaf:
+ * x-, x+, y-, y+).  Solve, info, refinement report and destroy are the
+ * calls above. */
+hps_status hps_interface2d_factor(hps_ctx* ctx, int p, const int nb[2], const double* T, int nrhs_max,
+                                  hps_precision precision, void* stream, hps_interface** out);
+hps_status hps_interface2d_plan(int p, const int nb[2], int* n_merge, int* n_list, int* nodes, int* lists);
+
 /* ---- The 2-D leaf reduction (FP64) ----------------------------------------
  *
  * The method in two dimensions (Sec. 1; Sec. 3.2 sizes the 2-D DtN maps at

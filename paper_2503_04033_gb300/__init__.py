@@ -29,7 +29,7 @@ __all__ = [
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
-    "hps_leaf2d_sizes",
+    "hps_leaf2d_sizes", "hps_interface2d_factor", "hps_interface2d_plan",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -50,6 +50,7 @@ EXPORTED_SYMBOLS = (
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
+    "hps_interface2d_factor", "hps_interface2d_plan",
 )
 
 # Kernel classes of hps_profile_get.
@@ -126,6 +127,8 @@ def load_library() -> ctypes.CDLL:
         "hps_interface_factor": (i, [vp, i, ip, vp, i, i, vp, ctypes.POINTER(vp)]),
         "hps_interface_last_refinement": (i, [vp, ip, dp]),
         "hps_leaf2d_solve": (i, [i, dp, d, i, vp, i, vp, vp, vp, vp, vp, vp, vp]),
+        "hps_interface2d_factor": (i, [vp, i, ip, vp, i, i, vp, ctypes.POINTER(vp)]),
+        "hps_interface2d_plan": (i, [i, ip, ip, ip, ip, ip]),
         "hps_leaf2d_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
         "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
         "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
@@ -329,6 +332,32 @@ def hps_interface_factor(ctx, p: int, nb, T, nrhs_max: int = 1, prec: int = HPS_
                                                int(nrhs_max), int(prec), _stream(stream), ctypes.byref(out)),
            "hps_interface_factor")
     return out
+
+
+def hps_interface2d_factor(ctx, p: int, nb, T, nrhs_max: int = 1, prec: int = HPS_FP64, stream=None):
+    """hps_interface_factor for an nb[0] x nb[1] grid of 2-D boxes (maps T [nbox, m, m], m = 4 (p-2))."""
+    out = ctypes.c_void_p()
+    nb2 = (ctypes.c_int * 2)(*[int(v) for v in nb])
+    _check(load_library().hps_interface2d_factor(ctx, int(p), nb2, _ptr(T, _f64() if not isinstance(T, int) else None),
+                                                 int(nrhs_max), int(prec), _stream(stream), ctypes.byref(out)),
+           "hps_interface2d_factor")
+    return out
+
+
+def hps_interface2d_plan(p: int, nb):
+    """The merge tree of a 2-D grid (host only): (nodes [n_merge, 8], lists)."""
+    import numpy as np
+    lib = load_library()
+    nb2 = (ctypes.c_int * 2)(*[int(v) for v in nb])
+    nm, nl = ctypes.c_int(), ctypes.c_int()
+    _check(lib.hps_interface2d_plan(int(p), nb2, ctypes.byref(nm), ctypes.byref(nl), None, None),
+           "hps_interface2d_plan")
+    nodes = np.zeros((max(nm.value, 1), 8), dtype=np.int32)
+    lists = np.zeros(max(nl.value, 1), dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check(lib.hps_interface2d_plan(int(p), nb2, ctypes.byref(nm), ctypes.byref(nl), nodes.ctypes.data_as(ip),
+                                    lists.ctypes.data_as(ip)), "hps_interface2d_plan")
+    return nodes[:nm.value], lists[:nl.value]
 
 
 def hps_interface_last_refinement(iface):

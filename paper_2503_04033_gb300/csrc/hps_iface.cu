@@ -629,12 +629,10 @@ void solve_sweeps(hps_interface* F, int R, const double* h, const double* g, dou
     }
 }
 
-}  // namespace
-
-extern "C" {
-
-hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const double* T, int nrhs_max,
-                                hps_precision precision, void* stream, hps_interface** out)
+// The factorisation for a grid of 3-D boxes (nfaces = 6, q^2 nodes per face)
+// or of 2-D boxes (nfaces = 4, q nodes per edge, nb[2] = 1).
+hps_status interface_factor(hps_ctx* ctx, int p, const int nb[3], int nfaces, const double* T, int nrhs_max,
+                            hps_precision precision, void* stream, hps_interface** out)
 {
     if (!out) return HPS_EINVAL;
     *out = nullptr;
@@ -642,15 +640,15 @@ hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const doub
     if (precision != HPS_FP64 && precision != HPS_FP32_IR) return HPS_EINVAL;
     hps_interface* F = new (std::nothrow) hps_interface();
     if (!F) return HPS_ENOMEM;
-    if (!hps::build_iface_plan(p, nb, &F->plan)) { delete F; return HPS_EINVAL; }
+    if (!hps::build_iface_plan(p, nb, &F->plan, nfaces)) { delete F; return HPS_EINVAL; }
     F->device = hps::ctx_device(ctx);
     if (cudaSetDevice(F->device) != cudaSuccess) { delete F; return HPS_ECUDA; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const IfPlan& P = F->plan;
     F->p = p;
     F->q = p - 2;
-    F->qq = F->q * F->q;
-    F->m = 6 * F->qq;
+    F->qq = nfaces == 6 ? F->q * F->q : F->q;   // nodes per face slot
+    F->m = nfaces * F->qq;
     F->nbox = P.nbox;
     F->nrhs_max = nrhs_max;
     F->fp32 = precision == HPS_FP32_IR;
@@ -668,7 +666,7 @@ hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const doub
     for (int box = 0; box < P.nbox; ++box) {
         int* di = &F->dinfo[(size_t)8 * box];
         di[1] = F->ndface;
-        for (int f = 0; f < 6; ++f)
+        for (int f = 0; f < nfaces; ++f)
             if (!P.nodes[box].leaf_iface[f]) di[2 + di[0]++] = f;
         F->ndface += di[0];
     }
@@ -789,6 +787,25 @@ fail:
     free_interface(F);
     delete F;
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+hps_status hps_interface_factor(hps_ctx* ctx, int p, const int nb[3], const double* T, int nrhs_max,
+                                hps_precision precision, void* stream, hps_interface** out)
+{
+    return interface_factor(ctx, p, nb, 6, T, nrhs_max, precision, stream, out);
+}
+
+hps_status hps_interface2d_factor(hps_ctx* ctx, int p, const int nb[2], const double* T, int nrhs_max,
+                                  hps_precision precision, void* stream, hps_interface** out)
+{
+    if (out) *out = nullptr;
+    if (!nb) return HPS_EINVAL;
+    const int nb3[3] = {nb[0], nb[1], 1};
+    return interface_factor(ctx, p, nb3, 4, T, nrhs_max, precision, stream, out);
 }
 
 hps_status hps_interface_solve(hps_interface* F, int nrhs, const double* h, const double* g, double* ub,

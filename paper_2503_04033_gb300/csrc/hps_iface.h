@@ -27,9 +27,10 @@ struct IfFace {
 };
 
 // One node of the merge tree.  Leaves (ids 0 .. nbox-1, the box index) keep
-// their six local face slots (x-, x+, y-, y+, z-, z+), Dirichlet ones marked
+// their local face slots (x-, x+, y-, y+[, z-, z+]), Dirichlet ones marked
 // absent; a merge node's boundary is the list `faces` (interface faces only),
-// whose slot i covers positions i q^2 .. (i+1) q^2 - 1 of the node's vectors.
+// whose slot i covers positions i s .. (i+1) s - 1 of the node's vectors
+// (s = q^2 nodes per face in 3-D, q per edge in 2-D).
 // For a merge node with children a and b split at plane `split` of `axis`:
 //   a1: slots of a's faces not on the separator (in a's order)
 //   a3: slots of a's faces on the separator, in separator order
@@ -40,18 +41,21 @@ struct IfNode {
     int child[2] = {-1, -1};
     int height = 0, axis = -1, split = 0;
     std::vector<IfFace> faces;          // merge nodes: boundary faces in slot order
-    std::vector<char> leaf_iface;       // leaves: which of the six local faces are interface faces
+    std::vector<char> leaf_iface;       // leaves: which local faces are interface faces
     std::vector<int> a1, a3, b2, b3;
 };
 
 struct IfPlan {
     int p = 0, q = 0, nb[3] = {0, 0, 0}, nbox = 0;
+    int nfaces = 6;                       // faces of a leaf: 6 (3-D boxes) or 4 (2-D boxes, nb[2] = 1)
     std::vector<IfNode> nodes;            // leaves first (box order), then merges by height, root last
     std::vector<std::vector<int>> levels; // merge-node ids of height 1, 2, ...
 };
 
 // Builds the plan: the box range is halved recursively along its longest axis
-// (in boxes; ties to the lower axis).  Returns false for invalid sizes.
-bool build_iface_plan(int p, const int nb[3], IfPlan* out);
+// (in boxes; ties to the lower axis).  nfaces = 6 for a grid of 3-D boxes,
+// 4 for a grid of 2-D boxes (edges x-, x+, y-, y+; nb[2] must be 1), where a
+// "face" is an edge of q nodes.  Returns false for invalid sizes.
+bool build_iface_plan(int p, const int nb[3], IfPlan* out, int nfaces = 6);
 
 }  // namespace hps

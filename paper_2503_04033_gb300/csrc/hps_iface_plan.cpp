@@ -21,6 +21,7 @@ namespace {
 
 struct Builder {
     const int* nb;
+    int nfaces = 6;
     std::vector<IfNode> tmp;   // merges in creation order
     bool failed = false;
 
@@ -41,7 +42,7 @@ struct Builder {
         out->clear();
         if (id >= 0) {
             const int c[3] = {id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1])};
-            for (int f = 0; f < 6; ++f) {
+            for (int f = 0; f < nfaces; ++f) {
                 const IfFace F = leaf_face(c, f);
                 if (F.plane > 0 && F.plane < nb[F.axis]) out->push_back({F, f});
             }
@@ -102,17 +103,20 @@ struct Builder {
 
 }  // namespace
 
-bool build_iface_plan(int p, const int nb[3], IfPlan* out)
+bool build_iface_plan(int p, const int nb[3], IfPlan* out, int nfaces)
 {
     if (p < 3 || p > 24 || !nb || nb[0] < 1 || nb[1] < 1 || nb[2] < 1) return false;
+    if (nfaces != 6 && !(nfaces == 4 && nb[2] == 1)) return false;
     if ((long long)nb[0] * nb[1] * nb[2] > (1 << 20)) return false;
     IfPlan P;
     P.p = p;
     P.q = p - 2;
     for (int k = 0; k < 3; ++k) P.nb[k] = nb[k];
     P.nbox = nb[0] * nb[1] * nb[2];
+    P.nfaces = nfaces;
     Builder B;
     B.nb = nb;
+    B.nfaces = nfaces;
     const int lo[3] = {0, 0, 0};
     B.make(lo, nb);
     if (B.failed) return false;
@@ -122,8 +126,8 @@ bool build_iface_plan(int p, const int nb[3], IfPlan* out)
         IfNode& L = P.nodes[box];
         const int c[3] = {box % nb[0], (box / nb[0]) % nb[1], box / (nb[0] * nb[1])};
         for (int k = 0; k < 3; ++k) { L.lo[k] = c[k]; L.hi[k] = c[k] + 1; }
-        L.leaf_iface.resize(6);
-        for (int f = 0; f < 6; ++f) {
+        L.leaf_iface.resize(nfaces);
+        for (int f = 0; f < nfaces; ++f) {
             const IfFace F = Builder::leaf_face(c, f);
             L.leaf_iface[f] = (F.plane > 0 && F.plane < nb[F.axis]) ? 1 : 0;
         }
@@ -153,11 +157,33 @@ bool build_iface_plan(int p, const int nb[3], IfPlan* out)
 
 }  // namespace hps
 
+namespace {
+
+hps_status plan_arrays(const hps::IfPlan& P, int* n_merge, int* n_list, int* nodes, int* lists);
+
+}  // namespace
+
 // The merge tree as plain arrays (host, no GPU): see hps.h.
 extern "C" hps_status hps_interface_plan(int p, const int nb[3], int* n_merge, int* n_list, int* nodes, int* lists)
 {
     hps::IfPlan P;
     if (!hps::build_iface_plan(p, nb, &P)) return HPS_EINVAL;
+    return plan_arrays(P, n_merge, n_list, nodes, lists);
+}
+
+extern "C" hps_status hps_interface2d_plan(int p, const int nb[2], int* n_merge, int* n_list, int* nodes, int* lists)
+{
+    if (!nb) return HPS_EINVAL;
+    const int nb3[3] = {nb[0], nb[1], 1};
+    hps::IfPlan P;
+    if (!hps::build_iface_plan(p, nb3, &P, 4)) return HPS_EINVAL;
+    return plan_arrays(P, n_merge, n_list, nodes, lists);
+}
+
+namespace {
+
+hps_status plan_arrays(const hps::IfPlan& P, int* n_merge, int* n_list, int* nodes, int* lists)
+{
     const int nm = (int)P.nodes.size() - P.nbox;
     int nl = 0;
     for (int r = 0; r < nm; ++r) {
@@ -187,3 +213,5 @@ extern "C" hps_status hps_interface_plan(int p, const int nb[3], int* n_merge, i
     }
     return HPS_OK;
 }
+
+}  // namespace

@@ -15,6 +15,13 @@ from oracle import global_solve_2d as g2
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.hps_create(0, 0)
+    yield c
+    H.hps_destroy(c)
+
+
 def _dev(a):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
@@ -120,3 +127,47 @@ def test_leaf2d_argument_errors():
         H.hps_leaf2d_solve(5, (0.5, 0.5), 1.0, 2, b, 1, None, T)   # loads without f, v, h
     with pytest.raises(H.HpsError):
         H.hps_leaf2d_reconstruct(5, 2, 1, None, None, T, T)
+
+
+@pytest.mark.parametrize("iprec", [H.HPS_FP64, H.HPS_FP32_IR], ids=["fp64", "fp32ir"])
+@pytest.mark.parametrize("nb", [(3, 2), (4, 4), (1, 3)])
+def test_leaf2d_all_gpu_two_level_solve(ctx, nb, iprec):
+    """The whole 2-D Dirichlet problem on the device: leaf maps, the interface
+    factorisation and solve (nested dissection over the box grid), the
+    reconstruction; equals the oracle's two-level solve."""
+    import torch
+    p, kappa = 8, 5.0
+    grid = g2.InterfaceGrid2D(p, nb, lo=(0.1, -0.3), L=(1.2, 0.8))
+    nbox = grid.nbox
+    n, m = H.hps_leaf2d_sizes(p)
+    rng = np.random.default_rng(12)
+    xo = [oracle.node_coords_2d(p, grid.box_lo(bx), grid.h) for bx in range(nbox)]
+    g_dir = rng.standard_normal(grid.n_dir)
+    ref = g2.hps_solve_2d(grid, kappa, [_b_field(x) for x in xo], [_loads(x, 1)[0] for x in xo], g_dir)
+    xg = [H.hps_leaf_nodes(p, (*grid.box_lo(bx), 0.0), (*grid.h, 1.0))[:p * p, :2] for bx in range(nbox)]
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device="cuda")
+    S = torch.empty(nbox, n, m, dtype=torch.float64, device="cuda")
+    v = torch.empty(nbox, 1, n, dtype=torch.float64, device="cuda")
+    hf = torch.empty(nbox, 1, m, dtype=torch.float64, device="cuda")
+    H.hps_leaf2d_solve(p, grid.h, kappa, nbox, _dev(np.stack([_b_field(x) for x in xg])), 1,
+                       _dev(np.stack([_loads(x, 1) for x in xg])), T, S, v, hf)
+    g = np.zeros((nbox, 1, m))
+    for bx in range(nbox):
+        isi, gid = grid.local_to_global(bx)
+        g[bx, 0, ~isi] = g_dir[gid[~isi]]
+    ub = torch.empty(nbox, 1, m, dtype=torch.float64, device="cuda")
+    ui = torch.empty(nbox, 1, n, dtype=torch.float64, device="cuda")
+    F = H.hps_interface2d_factor(ctx, p, nb, T, 1, iprec)
+    try:
+        H.hps_interface_solve(F, 1, hf, _dev(g), ub)
+        H.hps_leaf2d_reconstruct(p, nbox, 1, S, v, ub, ui)
+        torch.cuda.synchronize()
+    finally:
+        H.hps_interface_destroy(F)
+    scale = np.abs(ref["u_int"]).max()
+    ubn = ub.cpu().numpy()[:, 0, :]
+    for bx in range(nbox):
+        isi, gid = grid.local_to_global(bx)
+        assert np.abs(ubn[bx, isi] - ref["u_iface"][gid[isi]]).max() < 1e-11 * scale
+    assert np.abs(ui.cpu().numpy()[:, 0, :] - ref["u_int"]).max() < 1e-11 * scale
+

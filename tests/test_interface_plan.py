@@ -141,3 +141,40 @@ def test_plan_rejects_bad_arguments(H):
         H.hps_interface_plan(2, (2, 2, 2))
     with pytest.raises(H.HpsError):
         H.hps_interface_plan(8, (0, 1, 1))
+
+
+@pytest.mark.parametrize("nb,kappa", [((2, 2), 0.0), ((3, 2), 4.0), ((4, 3), 2.0), ((1, 3), 3.0)])
+def test_plan_2d_elimination_matches_sparse_lu(H, nb, kappa):
+    """The 2-D plan (edges of q nodes as the slots): a numpy elimination that
+    follows it on the oracle's 2-D leaf maps equals the oracle's two-level
+    solve with the host sparse LU."""
+    from oracle import global_solve_2d as g2
+    p = 6
+    q = p - 2
+    grid = g2.InterfaceGrid2D(p, nb, lo=(0.2, -0.1), L=(1.1, 0.9))
+    nbox = grid.nbox
+    n, m = oracle.sizes_2d(p)
+    rng = np.random.default_rng(5)
+    xy = [oracle.node_coords_2d(p, grid.box_lo(bx), grid.h) for bx in range(nbox)]
+    b = [1.0 + 0.3 * np.sin(2 * x[:, 0] - x[:, 1]) for x in xy]
+    f = [np.cos(x[:, 0] + 2 * x[:, 1]) for x in xy]
+    g_dir = rng.standard_normal(grid.n_dir)
+    ref = g2.hps_solve_2d(grid, kappa, b, f, g_dir)
+    T = np.empty((nbox, m, m))
+    h = np.empty((nbox, m))
+    for bx in range(nbox):
+        T[bx], _, info = oracle.leaf_dtn_2d(p, grid.h, kappa, b[bx], want_S=False)
+        assert info == 0
+        _, hf, _ = oracle.leaf_particular_2d(p, grid.h, kappa, b[bx], f[bx][None, :])
+        isi, gid = grid.local_to_global(bx)
+        rd = np.nonzero(~isi)[0]
+        h[bx] = hf[0] + T[bx][:, rd] @ g_dir[gid[rd]]
+    nodes, lists = H.hps_interface2d_plan(p, nb)
+    assert len(nodes) == nbox - 1
+    if nbox > 1:
+        assert int(nodes[:, 5].sum()) * q == grid.n_iface
+    ub = merge_solve(nodes, lists, nbox, q, T, h)
+    scale = np.abs(ref["u_iface"]).max()
+    for bx in range(nbox):
+        isi, gid = grid.local_to_global(bx)
+        np.testing.assert_allclose(ub[bx, isi], ref["u_iface"][gid[isi]], rtol=0, atol=1e-11 * scale)
