@@ -185,3 +185,25 @@ def test_manufactured_spectral_convergence():
         errs.append(np.abs(r["u_int"] - ui).max())
     assert all(b < a / 10 for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-9, errs
+
+
+def test_square_symmetries_of_T():
+    """For constant b on a square box the DtN map commutes with the symmetries
+    of the square: the reflection x -> -x swaps edges x- and x+ and keeps the
+    node order on them while reversing it on the y-edges; the transpose
+    (x, y) -> (y, x) swaps the x-edges with the y-edges."""
+    p = 9
+    q = p - 2
+    T, _, info = oracle.leaf_dtn_2d(p, (0.5, 0.5), 3.0, np.ones(p * p), want_S=False)
+    assert info == 0
+    rev = np.arange(q)[::-1]
+    a = np.arange(q)
+    # x -> -x
+    P1 = np.concatenate([1 * q + a, 0 * q + a, 2 * q + rev, 3 * q + rev])
+    # (x, y) -> (y, x)
+    P2 = np.concatenate([2 * q + a, 3 * q + a, 0 * q + a, 1 * q + a])
+    for P in (P1, P2):
+        assert np.abs(T[np.ix_(P, P)] - T).max() < 1e-11 * np.abs(T).max()
+    # a non-square box breaks the transpose symmetry
+    T2, _, _ = oracle.leaf_dtn_2d(p, (0.5, 0.3), 3.0, np.ones(p * p), want_S=False)
+    assert np.abs(T2[np.ix_(P2, P2)] - T2).max() > 1e-3 * np.abs(T2).max()
