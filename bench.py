@@ -214,6 +214,27 @@ def oracle_rate(nbox_sample: int, threads: int | None = None):
     return nbox_sample / dt, dt, oracle.max_threads()
 
 
+def lapack_rate(nbox_sample: int):
+    """Boxes/s of a LAPACK-based CPU path on the first boxes of the workload:
+    the oracle's collocation matrix, then numpy's threaded LU solve for S and
+    one product for T = A_bb + A_bi S (a second, stronger CPU baseline for
+    context; the oracle is the one the contract names)."""
+    import oracle
+    lows, h = box_lows()
+    field = hi.fourier_b_field()
+    n, m = oracle.sizes(P)
+    sel = np.linspace(0, NBOX - 1, nbox_sample).astype(int)
+    bs = [field.b(oracle.node_coords(P, lows[i], h)) for i in sel]
+    t0 = time.perf_counter()
+    for b in bs:
+        A = oracle.leaf_matrix(P, h, KAPPA, b)
+        S = np.linalg.solve(A[:n, :n], -A[:n, n:])
+        T = A[n:, n:] + A[n:, :n] @ S
+        assert np.isfinite(T).all()
+    dt = time.perf_counter() - t0
+    return nbox_sample / dt, dt
+
+
 def run_reference(args):
     """The oracle on the host cores: each step is one box of the workload (the
     oracle's LU and solves use every core), W untimed, K timed."""
@@ -579,6 +600,11 @@ def run_ours(args):
                                 "sample": f"{args.cpu_sample} boxes spread over the workload, FP64 oracle "
                                           f"(LU, solves, A_bb + A_bi S) with OpenMP over {cores} threads, "
                                           f"{dt:.1f} s"}
+        lrate, ldt = lapack_rate(8)
+        line["cpu_lapack_baseline"] = {"value": lrate, "unit": "boxes/s", "cores": os.cpu_count(), "kind": "lapack",
+                                       "sample": f"8 boxes spread over the workload: the oracle's collocation "
+                                                 f"matrix, numpy's threaded LAPACK solve for S and one product for "
+                                                 f"T, {ldt:.1f} s (context)"}
     H.hps_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
