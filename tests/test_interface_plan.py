@@ -178,3 +178,22 @@ def test_plan_2d_elimination_matches_sparse_lu(H, nb, kappa):
     for bx in range(nbox):
         isi, gid = grid.local_to_global(bx)
         np.testing.assert_allclose(ub[bx, isi], ref["u_iface"][gid[isi]], rtol=0, atol=1e-11 * scale)
+
+
+@pytest.mark.parametrize("nb,top,levels", [((4, 4, 4), 16, 6), ((8, 8, 8), 64, 9), ((8, 4, 2), 8, 6)])
+def test_plan_sizes_of_uniform_grids(H, nb, top, levels):
+    """Nested dissection of a uniform grid: the root's separator is the
+    mid-plane across the longest axis (top faces), the tree has
+    ceil(log2) levels per axis, and each level's separators together hold
+    one plane of faces per split."""
+    nodes, lists = H.hps_interface_plan(6, nb)
+    grid = gs.InterfaceGrid(6, nb)
+    assert len(nodes) == grid.nbox - 1
+    assert int(nodes[-1, 5]) == top and nodes[-1, 4] == 0 and nodes[-1, 6] == 0
+    assert int(nodes[:, 2].max()) == levels
+    assert int(nodes[:, 5].sum()) == grid.n_iface_faces
+    # children come from lower levels
+    for row in nodes:
+        for c in row[:2]:
+            if c >= grid.nbox:
+                assert nodes[c - grid.nbox, 2] < row[2]
