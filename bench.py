@@ -18,6 +18,15 @@ and the FP64 CPU oracle's rate on a bounded sample of boxes.
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this
 paper has; it has no code) on the same workload and metric.
+
+Other workloads (``--workload``), each printing its own JSON line: ``uneven``
+(1024 boxes of mixed p and kappa with 32 loads), ``learned`` (the learned
+low-rank DtN correction at p = 12), ``factored`` (stored factorisations, 32
+loads per box), ``timestep`` (Crank-Nicolson steps with every stage on the
+GPU, or the interface on the host with ``--interface host``), ``dirichlet``
+(the two-stage solve of 8 x 8 x 8 boxes at p = 12 with the GPU interface
+factorisation), ``accuracy`` (the Sec. 4.1 Green's-function study) and
+``leaf2d`` (the 2-D leaf reduction).
 """
 from __future__ import annotations
 
