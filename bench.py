@@ -68,26 +68,28 @@ def operand_format(prec, opts):
     if float(opts.get("FP16_OPERANDS", 1)) != 0:
         return "scaled 2 x FP16", 1.0, 3
     return "3 x TF32", TF32_OVER_BF16, 3
-# FP64 issue peak: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop (1.26 TFLOP/s,
-# the part's nominal 1.25 TFLOP/s FP64).
+# FP64 issue rate: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop (1.26
+# TFLOP/s, the part's nominal 1.25 TFLOP/s); used only where a run has not
+# measured its own FP64 matmul rate.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12
-FP32_CUDACORE_PEAK_TFLOPS = 152 * 2.070e9 * 128 * 2 / 1e12
+# DRAM bytes per launch of the tensor-core update products at 512 boxes, by
+# operand format: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture of the factorisation phase at 32 boxes, per launch, times 16 (the
+# traffic grows with the boxes).  None when not captured for the current
+# kernel: every change to the product kernel resets it to None until it is
+# captured again.
+NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): None, ("update_tcgen05", "3 x TF32"): None}
 
-CLASS_BOUND = {
-    "update_tcgen05": "tensor", "update_cudacore": "alu", "residual_fp64": "alu", "dn_fp64": "alu",
-    "panel": "alu", "build": "hbm", "gather": "hbm", "pack": "hbm", "refine_update": "hbm",
-    "update_tcgen05_refine": "tensor", "residual_df": "alu",
-}
-# DRAM bytes per launch of the dominant kernel class, by operand format, from
-# one ncu capture of the factorisation phase at 32 boxes
-# (dram__bytes_read.sum + dram__bytes_write.sum over its 97 launches / 97),
-# scaled to 512 boxes by the box count (traffic is proportional to the boxes
-# processed); see profiles/k_tc_update_fourier16_32boxes.md.  None until
-# measured; must be re-measured (or set to None) whenever that kernel changes.
-NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): 3.444e9, ("update_tcgen05", "3 x TF32"): None}
-# Classes whose launches skip converged boxes: their flop and byte counts are
-# upper bounds, so they are not used for the roofline.
-SKIPPING = ("update_tcgen05_refine", "residual_fp64", "refine_update")
+
+def dtype_label(prec, opts):
+    """Arithmetic of the path: the split operand format of the tensor-core
+    products (FP32 accumulation) plus the FP64 refinement and D_n."""
+    import paper_2503_04033_gb300 as H
+    if prec == H.HPS_FP64:
+        return "f64"
+    fmt = operand_format(prec, opts)[0]
+    return {"scaled 2 x FP16": "fp16x2 (f32 accumulate)+f64", "3 x TF32": "tf32x2 (f32 accumulate)+f64",
+            "3 x BF16": "bf16x3 (f32 accumulate)+f64"}[fmt]
 
 
 def parse_args():
@@ -105,7 +107,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
-                    help="hps_set_option before timing, e.g. TC_PAIRS=1 (name without HPS_OPT_)")
+                    help="hps_set_option before timing, e.g. LU_UNIT=2 (name without HPS_OPT_)")
     ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep", "dirichlet",
                                                  "accuracy", "leaf2d"),
                     default="fourier16",
@@ -154,6 +156,33 @@ def measured_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def measured_matmul_peaks(dev):
+    """Dense matmul rates measured here with torch (cuBLAS): FP64 at 4096^3
+    and FP16 / BF16 at 8192^3, best of 5 after a warm-up, CUDA events.  The
+    FP64 figure is the peak of the plain FP64 GPU path and the FP64 kernels;
+    the FP16 one checks that FP16 runs at the BF16 rate."""
+    import torch
+    out = {}
+    for name, dt, nn, reps in (("fp64_tflops", torch.float64, 4096, 3), ("fp16_tflops", torch.float16, 8192, 5),
+                               ("bf16_tflops", torch.bfloat16, 8192, 5)):
+        a = torch.randn(nn, nn, dtype=dt, device=dev)
+        bm = torch.randn(nn, nn, dtype=dt, device=dev)
+        c = a @ bm
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ bm
+            e1.record()
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = 2.0 * nn ** 3 / best / 1e12
+        del a, bm, c
+    torch.cuda.empty_cache()
+    out["how"] = "torch.matmul best of several, CUDA events; FP64 4096^3, FP16/BF16 8192^3 (burst)"
+    return out
 
 
 class ClockSampler:
@@ -357,8 +386,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {H.HPS_FP32_IR: "f32+f64", H.HPS_BF16_IR: "bf16x3 (f32 accumulate)+f64",
-                                      H.HPS_FP64: "f64"}[prec], "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype_label(prec, opts), "data": "synthetic",
         "config": {"workload": WORKLOAD, "nbox_per_gpu": nbox, "p": P, "kappa": KAPPA,
                    "precision": args.precision, "ir_tol": args.ir_tol, "options": args.opt, "l2": "inputs larger than L2 (~90 GB working set), no flush",
                    "step": "hps_leaf_build_dtn over all boxes (T out, S not stored)"},
@@ -373,67 +401,74 @@ def run_ours(args):
         "clocks": clocks.summary(),
     }
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant contraction (the mixed path is
+    # tensor-bound).  The tensor-core update products do the method's LU and
+    # triangular solves: their algorithmic work is 2/3 n^3 + 2 n^2 m per box,
+    # counted once (the split operand formats issue several MMAs per product),
+    # less the panel factorisation's share, which runs on CUDA cores.
     peaks, src = measured_peaks()
-    exact = {k: v for k, v in prof.items() if k not in SKIPPING}
-    if exact:
-        prof_roof = exact
-        dom = max(prof_roof, key=lambda k: prof_roof[k]["ms_per_step"])
-        d = prof[dom]
+    mm = measured_matmul_peaks(dev)
+    line["measured_matmul_peaks"] = mm
+    fmt_name, rate, nmma = operand_format(prec, opts)
+    if prec == H.HPS_FP64:
+        tpeak, tsrc = mm["fp64_tflops"], "torch float64 matmul measured in this run (4096^3)"
+    else:
+        tpeak = peaks["bf16_tflops_sustained"] * rate
+        tsrc = (f"{src} sustained BF16 dense peak" + (" (FP16 has the same nominal rate)" if rate == 1.0 else
+                                                       f" x {rate:.3f} (nominal TF32:BF16)"))
+    qh = P - 2
+    n_, m_ = qh ** 3, 6 * qh * qh
+    lu_trsm = nbox * (2.0 / 3.0 * n_ ** 3 + 2.0 * n_ * n_ * m_)
+    tc_cls = "update_tcgen05" if "update_tcgen05" in prof else ("update_cudacore" if "update_cudacore" in prof else None)
+    if tc_cls is not None:
+        d = prof[tc_cls]
+        panel_fl = prof.get("panel", {}).get("flops", 0.0)
+        alg = lu_trsm - panel_fl
         sec = d["ms_per_step"] / 1e3
-        bound = CLASS_BOUND.get(dom, "hbm")
-        if bound == "tensor":
-            # A split-operand product issues several MMAs per 2MNK: its useful
-            # peak is the MMA rate of its format over that count, and its ridge
-            # against HBM decides which roof binds.
-            fmt_name, rate, nmma = operand_format(prec, opts)
-            tpeak = peaks["bf16_tflops_sustained"] * rate / nmma
-            ai = d["flops"] / max(d["bytes"], 1.0)
-            ridge = tpeak * 1e12 / (peaks["hbm_gbs"] * 1e9)
-            if ai < ridge:
-                bound = "hbm"
-                peak = peaks["hbm_gbs"]
-                ach = d["bytes"] / sec / 1e9
-                unit = "GB/s"
-                note = (f"{src} HBM copy bandwidth; arithmetic intensity {ai:.1f} flop/B is below the {fmt_name} "
-                        f"ridge {ridge:.1f} flop/B ({nmma} MMAs per product at {peaks['bf16_tflops_sustained'] * rate:.0f} "
-                        f"TFLOP/s); tensor view: {d['flops'] / sec / 1e12:.1f} TFLOP/s algorithmic")
-            else:
-                peak = tpeak
-                ach = d["flops"] / sec / 1e12
-                unit = "TFLOP/s"
-                note = (f"{fmt_name}: {src} sustained BF16 rate x {rate:.3f} / {nmma} MMAs per product; "
-                        f"achieved counts 2MNK once")
-        elif bound == "alu":
-            fp64 = dom in ("residual_fp64", "dn_fp64") or prec == H.HPS_FP64
-            peak = FP64_PEAK_TFLOPS if fp64 else FP32_CUDACORE_PEAK_TFLOPS
-            ach = d["flops"] / sec / 1e12
-            unit = "TFLOP/s"
-            note = "FP64 issue peak 152 SM x 2.07 GHz x 4 flop/clk" if fp64 else "FP32 CUDA-core issue peak"
-        else:
-            peak = peaks["hbm_gbs"]
-            ach = d["bytes"] / sec / 1e9
-            unit = "GB/s"
-            note = f"{src} HBM copy bandwidth"
-        traffic = (NCU_TRAFFIC_PER_LAUNCH.get((dom, operand_format(prec, opts)[0]))
-                   if (nbox == NBOX and prec == H.HPS_FP32_IR) else None)
-        line["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                            "frac": ach / peak, "traffic": traffic,
-                            "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
-                            "peak_source": note, "launches_per_step": d["launches"]}
+        ach = alg / sec / 1e12
+        traffic = (NCU_TRAFFIC_PER_LAUNCH.get((tc_cls, fmt_name))
+                   if (nbox == NBOX and prec == H.HPS_FP32_IR and not opts) else None)
+        line["roofline"] = {
+            "kernel": tc_cls, "bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
+            "frac": ach / tpeak, "traffic": traffic,
+            "algorithmic_flops_per_launch": alg / max(d["launches"], 1), "launches_per_step": d["launches"],
+            "ms_per_step": d["ms_per_step"],
+            "flops_definition": "(2/3 n^3 + 2 n^2 m) per box x boxes, counted once, less the panel kernel's "
+                                "CUDA-core flops; per launch = that / launches",
+            "peak_source": tsrc + "; of measured",
+            "mma_issue_frac": ach * nmma / tpeak,
+            "mma_issue_note": f"{fmt_name}: {nmma} MMAs per product, so the tensor pipe issues {nmma}x the "
+                              "algorithmic rate",
+            "hbm_view": {"achieved_gbs": d["bytes"] / sec / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                         "frac": d["bytes"] / sec / 1e9 / peaks["hbm_gbs"],
+                         "note": "bytes the products move by construction (split operands, source and output "
+                                 "tiles), not the method's algorithmic bytes"},
+            "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum per launch from an ncu capture of "
+                               "32 boxes, scaled by the box count to 512 (traffic grows with the boxes)"
+                               if traffic is not None else "not captured for this configuration"),
+        }
+    line["roofline_step"] = {
+        "achieved": line["tflops"], "peak": tpeak, "unit": "TFLOP/s", "frac": line["tflops"] / tpeak,
+        "definition": "2/3 n^3 + 2 n^2 m + 2 q m^2 per box x boxes / ms_per_step (SURVEY 8(d)), against the "
+                      "same tensor peak",
+        "algorithmic_bytes_per_box": 8.0 * P ** 3 + 8.0 * m_ * m_,
+        "hbm_frac": nbox * (8.0 * P ** 3 + 8.0 * m_ * m_) / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
     # ---- the FP64 residual (its launches skip converged boxes, so its work is
     # counted from the refinement histogram):
     # FP64 pipe instructions per (point, column) of the even/odd line form,
     # 3 (h + 2) + 3 with h = (p - 2) // 2 at even p - 2, against the issue
     # rate of the FP64 pipes (2 per clock per SM at the SM clock sampled).
-    if "residual_fp64" in prof and prec != H.HPS_FP64:
+    if "residual_fp64" in prof and prec != H.HPS_FP64 and float(opts.get("RESIDUAL_DF", 3)) in (0.0, 1.0, 2.0):
         q = P - 2
         per_entry = 3 * (q // 2 + 2) + 3 + (6 if q % 2 else 0)
         # FP64 residual evaluations per step (every step alike); with the
         # double-float first residual (on unless switched off) each box's
         # first evaluation runs on the FP32 pipes instead
-        df = float(opts.get("RESIDUAL_DF", 1)) != 0 and float(opts.get("IR_MAX_ITERS", 8)) >= 2
+        # FP64 evaluations: the launches skip converged boxes, so the work is
+        # counted from the refinement histogram (less each box's double-float
+        # first residual); only meaningful when every later residual is FP64
+        df = float(opts.get("RESIDUAL_DF", 3)) != 0 and float(opts.get("IR_MAX_ITERS", 8)) >= 2
         box_its = float(it.sum()) - (nbox if df else 0)
         instr = box_its * n * m * per_entry
         rms = prof["residual_fp64"]["ms_per_step"]
@@ -521,7 +556,7 @@ def run_ours(args):
 
     # ---- the same precision with every residual in FP64 (the double-float
     # first residual switched off), timed the same way
-    if prec != H.HPS_FP64 and not args.no_alt and float(opts.get("RESIDUAL_DF", 1)) != 0:
+    if prec != H.HPS_FP64 and not args.no_alt and float(opts.get("RESIDUAL_DF", 3)) != 0:
         H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, 0)
         Tf = torch.empty_like(T)
         stf = torch.zeros_like(st)
@@ -538,12 +573,12 @@ def run_ours(args):
         f_ms = allmax(a0.elapsed_time(a1) / args.steps)
         itf, _ = H.hps_last_refinement(ctx, nbox)
         rel_f = ((Tf - T).flatten(1).norm(dim=1) / T.flatten(1).norm(dim=1)).max().item()
-        H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, 1)
+        H.hps_set_option(ctx, H.HPS_OPT_RESIDUAL_DF, float(opts.get("RESIDUAL_DF", 3)))
         line["all_fp64_residuals"] = {
             "value": world * nbox / (f_ms / 1e3), "unit": "boxes/s", "ms_per_step": f_ms,
             "box_failures": int((stf != 0).sum().item()), "corrections_mean": float(itf.mean()),
             "max_rel_diff_vs_headline_T": rel_f,
-            "note": "HPS_OPT_RESIDUAL_DF = 0: the first correction's residual in FP64 as well"}
+            "note": "HPS_OPT_RESIDUAL_DF = 0: every residual in FP64 (the strict form of the refinement)"}
         del Tf, stf
 
     # ---- end to end through the C ABI with host buffers.  Every step copies

@@ -15,6 +15,16 @@ data; no dataset is involved):
   = [-1.1, 0.1] x [1, 2] x [1.2, 2.2]: u = cos(kappa |x|) / (4 pi |x|), the
   free-space Green's function of Lap u + kappa^2 u (kappa = 0: Poisson), used
   as the exact solution and its boundary values as g (b = 1, f = 0).
+* ``curved``: the curved domain of Sec. 4.3, {(x1, x2 / psi(x1), x3)} with
+  psi(z) = 1 - sin(6 z) / 4 over the reference box CURVED_LO + [0, CURVED_L]
+  = [1.1, 2.1] x [-1, 0] x [-1.2, 0.2]: the coefficients of the Helmholtz
+  operator pulled back to the reference box (``curved_coefficients``), the
+  map to physical coordinates (``curved_to_physical``) and a plane wave
+  sin(k . y) of the physical coordinates as an exact solution with
+  kappa = |k| (``curved_plane_wave``).
+* ``cross_field``: a smooth symmetric positive-definite coefficient tensor
+  with every cross term, plus first-order coefficients, for parity tests of
+  the cross-term leaves.
 * ``FourierField``: 1 + 0.5 sum_{q=1}^{16} a_q cos(2 pi k_q . x + phi_q), with
   k_q uniform over the nonzero integer vectors of length <= 4,
   a_q ~ N(0, 1/16), phi_q ~ U[0, 2 pi); clipped to [0.5, 1.5] for b, and
@@ -125,3 +135,50 @@ def load_values(loads, xyz: np.ndarray) -> np.ndarray:
 def random_boundary_data(nbox: int, nrhs: int, m: int, seed: int = 7) -> np.ndarray:
     """Seeded boundary traces u_b [nbox, nrhs, m] for reconstruction tests."""
     return np.random.default_rng(seed).standard_normal((nbox, nrhs, m))
+
+
+# ------------------------------------------------------------ operators with cross terms
+
+CURVED_LO = (1.1, -1.0, -1.2)
+CURVED_L = (1.0, 1.0, 1.4)
+CURVED_K = (1.0, 2.0, -0.5)
+
+
+def curved_psi(z):
+    """psi(z) = 1 - sin(6 z) / 4 and its first two derivatives."""
+    return 1.0 - 0.25 * np.sin(6.0 * z), -1.5 * np.cos(6.0 * z), 9.0 * np.sin(6.0 * z)
+
+
+def curved_to_physical(x: np.ndarray) -> np.ndarray:
+    """Reference point (x1, x2, x3) -> physical point (x1, x2 / psi(x1), x3)."""
+    ps, _, _ = curved_psi(x[:, 0])
+    return np.stack([x[:, 0], x[:, 1] / ps, x[:, 2]], axis=1)
+
+
+def curved_coefficients(x: np.ndarray):
+    """(C [6, N], d [3, N]) of -Lap u - kappa^2 u on the curved domain in the
+    reference coordinates, in the form -sum C_ab u_ab + sum d_a u_a: the
+    parameter map of Sec. 4.3, -u_11 - ((psi' x2 / psi)^2 + psi^2) u_22 - u_33
+    - 2 (psi' x2 / psi) u_12 - (psi'' x2 / psi) u_2 (its "psi(x_i)" read as
+    psi(x1)).  C = (C11, C22, C33, C12, C13, C23)."""
+    x1, x2 = x[:, 0], x[:, 1]
+    ps, dps, ddps = curved_psi(x1)
+    r = dps * x2 / ps
+    one, zero = np.ones(len(x)), np.zeros(len(x))
+    return np.stack([one, r * r + ps * ps, one, r, zero, zero]), np.stack([zero, -ddps * x2 / ps, zero])
+
+
+def curved_plane_wave(x: np.ndarray, k=CURVED_K) -> np.ndarray:
+    """sin(k . y) at the physical points y of reference points x: a solution
+    of -Lap u - |k|^2 u = 0."""
+    return np.sin(curved_to_physical(x) @ np.asarray(k, dtype=np.float64))
+
+
+def cross_field(x: np.ndarray):
+    """(C [6, N], d [3, N], b [N]): a smooth SPD coefficient tensor with all
+    three cross terms, smooth first-order coefficients and b."""
+    C = np.stack([1.0 + 0.2 * np.sin(x[:, 0]), 1.3 + 0.1 * x[:, 1], 0.9 + 0.05 * x[:, 2] ** 2,
+                  0.25 * np.cos(x[:, 2]), -0.15 + 0.05 * x[:, 0], 0.1 * np.sin(x[:, 1])])
+    d = np.stack([0.2 * x[:, 1], np.sin(x[:, 0]), 0.1 * np.ones(len(x))])
+    b = 1.0 + 0.2 * np.cos(x[:, 0])
+    return C, d, b

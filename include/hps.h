@@ -100,10 +100,13 @@ typedef enum {
     HPS_OPT_IR_MAX_ITERS = 1,   /* corrections in FP32_IR mode, default 8, range 0..20 */
     HPS_OPT_IR_TOL = 2,         /* a box stops refining when its predicted remaining error is below tol
                                    relative to ||X||_F (default 1e-11, a decade below the 1e-10 relative
-                                   accuracy the FP32_IR path is meant to deliver on T and u):
-                                   ||dX_k|| min(1, 10 ||dX_k||/||dX_k-1||),
-                                   or when ||dX|| is below 1e-11 ||X|| and shrank by less than half
-                                   (the FP64 residual's noise floor); converged boxes skip later steps */
+                                   accuracy the FP32_IR path is meant to deliver on T and u, so that an
+                                   interface solve built on the leaf maps keeps its own accuracy):
+                                   ||dX_k|| min(1, 10 ||dX_k||/||dX_k-1||) from the second
+                                   correction on (the first ends the refinement only when it is itself
+                                   below tol), or when ||dX|| is below 1e-11 ||X|| and shrank by less
+                                   than half (the residual's noise floor); converged boxes skip later
+                                   steps */
     HPS_OPT_BLOCK = 3,          /* LU block size NB: 0 = automatic, else 32, 64 or 128 */
     HPS_OPT_TENSOR_CORES = 4,   /* FP32 products on tcgen05 (1, default) or CUDA cores (0) */
     HPS_OPT_SYNC = 5,           /* 1: synchronise the stream and return the first box failure */
@@ -115,28 +118,39 @@ typedef enum {
                                    CUDA graph on first use and replay the graph afterwards */
     HPS_OPT_TC_EPILOGUE = 8,    /* tcgen05 update epilogue: 0 (default) moves source and result tiles by TMA
                                    wherever the output is 16-byte aligned, 1 always uses the cp.async form */
-    HPS_OPT_TC_PAIRS = 9,       /* 1: tcgen05 products run on pairs of CTAs (a thread-block cluster of 2) that
-                                   share the right operand by TMA multicast; 0 (default): single CTAs, which
-                                   measured faster on the p = 16 workload */
-    HPS_OPT_LU_PAIRS = 10,      /* 1 (default): on the tensor-core path, consecutive LU steps are joined in
-                                   pairs (look-ahead on the next panel, one 2 NB-deep update per pair and one
-                                   product per pair in the solves); 0: one step at a time.  Results agree to
+    /* option 9 is not used */
+    HPS_OPT_LU_UNIT = 10,       /* 4 (default), 8, 2 or 1: on the tensor-core path, up to this many consecutive
+                                   LU steps are joined into one unit (look-ahead on the later panels of the
+                                   unit, one update of unit-width K over every later column and one product
+                                   per unit in the solves); 1: one step at a time.  Results agree to
                                    rounding */
     HPS_OPT_TC_FUSE = 11,       /* gathers of the backward solves written by the previous product's TMA
                                    epilogue: -1 (default) where that measured faster (3 x TF32 operands),
                                    0 never, 1 always; results are bit-identical either way */
-    HPS_OPT_RESIDUAL_DF = 12,   /* 1 (default): in FP32_IR and BF16_IR mode with at least 2 corrections, the
-                                   first residual, of the low-precision solution itself, runs in double-float
-                                   arithmetic on the FP32 pipes (about 2^-46 relative to the sum of the
-                                   terms' magnitudes) and that correction never ends the refinement, so every
-                                   result still ends on corrections from the FP64 residual; 0: every residual
-                                   in FP64 */
+    HPS_OPT_RESIDUAL_DF = 12,   /* precision of the refinement residuals B - A_ii X in FP32_IR and BF16_IR
+                                   mode.  3 (default): the first residual, of the low-precision solution
+                                   X0 itself (exact in FP32), in double-float arithmetic on the FP32 pipes
+                                   (about 2^-46 relative to the sum of the terms' magnitudes); the later
+                                   ones in double-float as well (each FP64 entry of X split into two
+                                   floats) for boxes whose first correction was at most 3e-4 of X, whose
+                                   A_ii then amplifies residual errors little enough for that floor to
+                                   stay a factor 5 under 1e-10, and in FP64 for every other box.
+                                   2: double-float first residual, every later one in FP64.
+                                   1: double-float first residual whose correction never ends the
+                                   refinement, later ones in FP64.  0: every residual in FP64 */
     HPS_OPT_FP16_OPERANDS = 13, /* 1 (default): FP32_IR tensor-core products split each operand into two FP16
                                    values (hi + lo, 22 bits as with 3 x TF32) under exact power-of-two scales
                                    of the left operand's K columns and the right operand's columns, which
                                    halves the operand bytes and doubles the MMA rate; 0: 3 x TF32 */
-    HPS_OPT_TEST_SINGULAR_BOX = 100  /* test hook: zero row 0 of A_ii of this box index (-1 = off),
+    HPS_OPT_TEST_SINGULAR_BOX = 100, /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
+    HPS_OPT_TEST_TC_TIMEOUT = 101    /* test hook: 1 arms it once.  In the next FP32_IR / BF16_IR call on the
+                                        tensor cores, one update product issues no operand loads, so its first
+                                        bounded mbarrier wait runs out (after 2 ms instead of 2 s); the
+                                        launch drains what it has in flight, frees its tensor memory and
+                                        returns, and every box of the call reports HPS_ETIMEOUT.  No GPU
+                                        fault is involved and the context stays usable.  Calls with the hook
+                                        armed bypass the CUDA-graph cache */
 } hps_option;
 
 /* Creates a context on CUDA device `device`.  workspace_bytes_max bounds the
@@ -304,13 +318,17 @@ hps_status hps_last_refinement(hps_ctx* ctx, int nbox, int* iters, double* rel_c
  * b[nbox][p^3], T[nbox][m][m] and optionally box_status[nbox] (device);
  * batches larger than the scratch holds run in chunks on `stream`.
  * Returns HPS_ENOMEM (nothing enqueued) when one box's workspace exceeds the
- * scratch: p <= 13 fits (p = 12 needs ~24 MiB per box, p = 16 ~152 MiB); with
+ * scratch: p <= 14 fits (p = 12 needs ~22 MiB per box, p = 13 ~37 MiB and
+ * p = 14 ~60 MiB, one box per chunk), p >= 15 returns HPS_ENOMEM; with
  * box_status NULL the status words also come from the scratch (4 bytes/box).
+ * The operator tables are built on the device by a small kernel (no host
+ * copy); every call enqueues only kernels and memsets on `stream`.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and leaves its contents behind:
- * calls that overlap on the GPU (concurrent streams, several host threads)
- * race on it and must be serialised by the caller. */
+ * capture.  Every call shares the one array and leaves its contents behind
+ * (the call clears the status words it uses): calls that overlap on the GPU
+ * (concurrent streams, several host threads) race on it and must be
+ * serialised by the caller. */
 hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int nbox, const double* b, double* T,
                                       int* box_status, void* stream);
 

@@ -18,12 +18,12 @@ import os
 __all__ = [
     "HPS_OK", "HPS_EINVAL", "HPS_ENOMEM", "HPS_ESINGULAR", "HPS_ENOCONV", "HPS_ECUDA", "HPS_ETIMEOUT",
     "HPS_FP64", "HPS_FP32_IR", "HPS_BF16_IR", "HPS_OPT_IR_MAX_ITERS", "HPS_OPT_IR_TOL", "HPS_OPT_BLOCK",
-    "HPS_OPT_TENSOR_CORES", "HPS_OPT_SYNC", "HPS_OPT_TEST_SINGULAR_BOX", "HpsError", "LeafKind", "load_library", "library_path",
+    "HPS_OPT_TENSOR_CORES", "HPS_OPT_SYNC", "HPS_OPT_TEST_SINGULAR_BOX", "HPS_OPT_TEST_TC_TIMEOUT", "HpsError", "LeafKind", "load_library", "library_path",
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
-    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_TC_PAIRS", "HPS_OPT_LU_PAIRS", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
+    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_LU_UNIT", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
@@ -35,10 +35,10 @@ __all__ = [
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
 HPS_FP64, HPS_FP32_IR, HPS_BF16_IR = 0, 1, 2
 HPS_OPT_IR_MAX_ITERS, HPS_OPT_IR_TOL, HPS_OPT_BLOCK, HPS_OPT_TENSOR_CORES, HPS_OPT_SYNC = 1, 2, 3, 4, 5
-HPS_OPT_AUTOTUNE, HPS_OPT_GRAPHS, HPS_OPT_TC_EPILOGUE, HPS_OPT_TC_PAIRS, HPS_OPT_LU_PAIRS, HPS_OPT_TC_FUSE = (
-    6, 7, 8, 9, 10, 11)
+HPS_OPT_AUTOTUNE, HPS_OPT_GRAPHS, HPS_OPT_TC_EPILOGUE, HPS_OPT_LU_UNIT, HPS_OPT_TC_FUSE = 6, 7, 8, 10, 11
 HPS_OPT_RESIDUAL_DF, HPS_OPT_FP16_OPERANDS = 12, 13
 HPS_OPT_TEST_SINGULAR_BOX = 100
+HPS_OPT_TEST_TC_TIMEOUT = 101
 
 EXPORTED_SYMBOLS = (
     "hps_create", "hps_destroy", "hps_set_option", "hps_leaf_sizes", "hps_leaf_nodes", "hps_workspace_per_box",
@@ -56,7 +56,7 @@ EXPORTED_SYMBOLS = (
 # Kernel classes of hps_profile_get.
 KERNEL_CLASSES = ("build", "panel", "update_cudacore", "update_tcgen05", "gather", "residual_fp64",
                   "refine_update", "dn_fp64", "update_tcgen05_refine", "pack", "residual_df",
-                  "bookkeeping")
+                  "bookkeeping", "residual_df64")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None

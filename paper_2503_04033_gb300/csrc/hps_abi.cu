@@ -76,6 +76,11 @@ static void prof_resolve(Profiler* p)
 
 }  // namespace hps
 
+// One tuned LU schedule: block NB, unit length, widest tensor-core tile.
+struct TuneChoice {
+    int nb = 0, unit = 0, bn = 0;
+};
+
 struct hps_ctx {
     int device = 0;
     size_t ws_max = 0;
@@ -86,10 +91,9 @@ struct hps_ctx {
     double ir_tol = 1e-11;
     int nb_opt = 0;
     int tc_epi_cp = 0;          // 1: tcgen05 epilogue always in the cp.async form
-    int tc_pairs = 0;           // 1: tcgen05 products by CTA pairs sharing the right operand
-    int lu_pairs = 1;           // 0: no joining of LU steps in pairs on the tcgen05 path
+    int lu_unit = 4;            // tcgen05 path: LU steps joined into units of up to this many (1, 2, 4, 8)
     int tc_fuse = -1;           // -1: fused gathers where they measured faster, 0: never, 1: backward sweeps
-    int res_df = 1;             // first correction's residual in double-float on the FP32 pipes
+    int res_df = 3;             // residual precision (HPS_OPT_RESIDUAL_DF): double-float, routed per box
     int fp16_ops = 1;           // FP32_IR tensor-core products on scaled 2 x FP16 operands (format 2)
     int use_tc = 1;
     int sync = 0;
@@ -98,7 +102,7 @@ struct hps_ctx {
     hps::Profiler prof;
     int autotune = 0;
     int graphs = 0;
-    std::map<std::tuple<int, int, int>, int> nb_tuned;      // (p, precision, tensor cores) -> LU block
+    std::map<std::tuple<int, int, int>, TuneChoice> tuned;  // (p, precision, tensor cores) -> schedule
     std::map<std::string, cudaGraphExec_t> graph_cache;     // captured calls
     int* d_iters = nullptr;
     double* d_relcorr = nullptr;
@@ -297,29 +301,8 @@ hps_status get_geometry(hps_ctx* ctx, int p, const double h[3], Geometry** out)
     const int pp = p * p;
     std::vector<double> Dhat(pp), D(3 * pp), D2(3 * pp);
     cheb_diff(p, Dhat.data());
-    for (int a = 0; a < 3; ++a) {
-        g.h[a] = h[a];
-        const double s = 2.0 / h[a];
-        for (int e = 0; e < pp; ++e) D[a * pp + e] = s * Dhat[e];
-        for (int i = 0; i < p; ++i)
-            for (int j = 0; j < p; ++j) {
-                double acc = 0.0;
-                for (int l = 0; l < p; ++l) acc += D[a * pp + i * p + l] * D[a * pp + l * p + j];
-                D2[a * pp + i * p + j] = acc;
-            }
-        // D^2 of the Chebyshev nodes is centro-symmetric; the product above
-        // is only up to rounding, so hold it exactly (the residual's even/odd
-        // line split relies on it, and the build then uses the same matrix).
-        for (int i = 0; i < p; ++i)
-            for (int j = 0; j < p; ++j) {
-                const int e = a * pp + i * p + j, f = a * pp + (p - 1 - i) * p + (p - 1 - j);
-                if (e < f) {
-                    const double v = 0.5 * (D2[e] + D2[f]);
-                    D2[e] = v;
-                    D2[f] = v;
-                }
-            }
-    }
+    for (int a = 0; a < 3; ++a) g.h[a] = h[a];
+    geometry_tables(p, Dhat.data(), g.h, D.data(), D2.data());
     HPS_CUDA_TRY(cudaMalloc(&g.dD, sizeof(double) * 3 * pp));
     HPS_CUDA_TRY(cudaMalloc(&g.dD2, sizeof(double) * 3 * pp));
     HPS_CUDA_TRY(cudaMemcpy(g.dD, D.data(), sizeof(double) * 3 * pp, cudaMemcpyHostToDevice));
@@ -393,6 +376,8 @@ struct Job {
     int* status = nullptr;               // device [nbox]
     int diag_off = 0;                    // offset into the refinement diagnostics
     int nb = 0;                          // LU block (0: context default)
+    int unit = 0;                        // LU unit length (0: context default)
+    int bn = 0;                          // widest tensor-core tile (0: 256)
     int zero_row_box = -1;               // test hook
     const double* beta = nullptr;        // device [nbox][3][p^3]: first-order term div(beta u), or NULL
 };
@@ -415,9 +400,9 @@ long long job_srhs(const Job& j)
 Plan job_plan(const hps_ctx* ctx, const Job& j, hps_precision prec)
 {
     Plan P = make_plan(j.g->n, job_cols(j), prec, j.nb ? j.nb : ctx->nb_opt, ctx->use_tc != 0, prec != HPS_FP64,
-                       ctx->lu_pairs != 0, ctx->fp16_ops != 0);
+                       j.unit ? j.unit : ctx->lu_unit, ctx->fp16_ops != 0);
+    P.bn_max = j.bn ? j.bn : 256;
     P.tma_epi = ctx->tc_epi_cp == 0;
-    P.tc_pairs = ctx->tc_pairs != 0;
     if (ctx->tc_fuse >= 0) P.fuse_bwd = P.tc && ctx->tc_fuse != 0;
     if (P.fmt == 2) P.fuse_bwd = false;   // the fused gather writes unscaled operands
     return P;
@@ -535,15 +520,29 @@ hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, con
     HPS_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(double) * 2 * nbox, st));
     launch_extract<float>(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, nbox, st, w.norms);
     const int its = ctx->ir_iters;
-    // The first residual, of the FP32 solution itself, may run in double-float
-    // when at least one FP64-residual correction follows it.
-    const bool df = ctx->res_df && its >= 2 && g.dDF && !cs.beta;   // the double-float form has no first-order term
+    // The first residual, of the FP32 solution itself, may run in double-float:
+    // with res_df = 1 when at least one FP64-residual correction follows it
+    // (which then ends the refinement), with res_df = 2 always, the stopping
+    // rule then counting the double-float floor (kDfFloor) in its prediction.
+    const bool df = ctx->res_df && its >= (ctx->res_df >= 2 ? 1 : 2) && g.dDF && residual_df_fits(g, false) &&
+                    !cs.beta;   // the double-float form has no first-order term
     if (its > 0 && !have_kb) launch_kappa_b(g, cs.kappa, cs.kappa_dev, nbox, b, p3, w.kb, df ? w.kbs : nullptr, st);
+    // With res_df = 3 the workspace's per-box flag area (four ints per box)
+    // holds, after skip, the residual route and the two kernels' skip flags.
+    const bool df3 = df && ctx->res_df == 3 && residual_df_fits(g, true);   // else every later one in FP64
+    int* route = w.skip + nbox;
+    int* skip_df = w.skip + 2 * nbox;
+    int* skip_64 = w.skip + 3 * nbox;
     for (int it = 0; it < its; ++it) {
         if (df && it == 0)
             launch_residual_df(g, nbox, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M + g.n, P.ldm, w.sM, w.kbs, w.skip,
                                st);
-        else
+        else if (df3) {   // routed by k_ir_check: double-float for well-conditioned boxes, FP64 for the rest
+            launch_residual_df(g, nbox, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, w.M + g.n, P.ldm, w.sM, w.kbs, skip_df,
+                               st, X, ldx, sX);
+            launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
+                            w.M + g.n, P.ldm, w.sM, skip_64, st, w.kb, cs.beta);
+        } else
             launch_residual(g, cs.kappa, cs.kappa_dev, nbox, b, p3, cs.rhs_kind, cs.r, cs.rhs, cs.s_rhs, X, ldx, sX,
                             w.M + g.n, P.ldm, w.sM, w.skip, st, w.kb, cs.beta);
         if (P.tc) {
@@ -554,7 +553,10 @@ hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, con
             lu_backward<float>(P, w, nbox, g.n, cs.r, w.skip, st);
         }
         launch_ir_update(w.M + g.n, P.ldm, w.sM, g.n, cs.r, X, ldx, sX, w.norms, w.skip, nbox, st);
-        launch_ir_check(nbox, w.norms, ctx->ir_tol, it == its - 1, w.skip, iters, relcorr, status, st, df && it == 0);
+        const bool df_it = df && it == 0;
+        launch_ir_check(nbox, w.norms, ctx->ir_tol, it == its - 1, w.skip, iters, relcorr, status, st,
+                        df_it && ctx->res_df == 1, df_it && ctx->res_df >= 2 ? kDfFloor : 0.0, df3 ? kDfGate : 0.0,
+                        route, skip_df, skip_64);
     }
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -625,18 +627,24 @@ hps_status enqueue_all(hps_ctx* ctx, const std::vector<Job>& jobs, const std::ve
     return HPS_OK;
 }
 
-// ------------------------------------------------------------ autotuning of the LU block
+// ------------------------------------------------------------ autotuning of the LU schedule
 
 std::string tune_file() { const char* e = std::getenv("HPS_TUNE_CACHE"); return e ? e : ""; }
 
+// Cache file: one line per (p, precision, tensor cores): "p prec tc nb unit bn".
 void load_tuning(hps_ctx* ctx)
 {
     const std::string f = tune_file();
     if (f.empty()) return;
     FILE* fp = std::fopen(f.c_str(), "r");
     if (!fp) return;
-    int p, prec, tc, nb;
-    while (std::fscanf(fp, "%d %d %d %d", &p, &prec, &tc, &nb) == 4) ctx->nb_tuned[std::make_tuple(p, prec, tc)] = nb;
+    char line[256];
+    while (std::fgets(line, sizeof line, fp)) {
+        int p, prec, tc;
+        TuneChoice c;
+        if (std::sscanf(line, "%d %d %d %d %d %d", &p, &prec, &tc, &c.nb, &c.unit, &c.bn) == 6)
+            ctx->tuned[std::make_tuple(p, prec, tc)] = c;
+    }
     std::fclose(fp);
 }
 
@@ -646,31 +654,44 @@ void save_tuning(const hps_ctx* ctx)
     if (f.empty()) return;
     FILE* fp = std::fopen(f.c_str(), "w");
     if (!fp) return;
-    for (const auto& kv : ctx->nb_tuned)
-        std::fprintf(fp, "%d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                     kv.second);
+    for (const auto& kv : ctx->tuned)
+        std::fprintf(fp, "%d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                     kv.second.nb, kv.second.unit, kv.second.bn);
     std::fclose(fp);
 }
 
-// Picks the LU block size for (p, precision, tensor cores) by timing each
+// Schedule candidates of a (precision, tensor cores) combination: the LU
+// block NB, the LU unit length (steps joined per product; NB x unit <= 512)
+// and the widest tensor-core tile (products narrower than it use 64- or
+// 128-column tiles anyway).
+std::vector<TuneChoice> tune_candidates(hps_precision prec, bool tc)
+{
+    if (prec == HPS_FP64 || !tc) return {{32, 1, 256}, {64, 1, 256}};
+    return {{128, 4, 256}, {128, 2, 256}, {64, 8, 256}, {64, 4, 256}, {128, 4, 128}, {64, 8, 128}};
+}
+
+// Picks the LU schedule for (p, precision, tensor cores) by timing each
 // candidate on up to 8 of the job's own boxes (their outputs are rewritten by
 // the real run).  Synchronises the stream; never runs inside a capture.
 hps_status tune_job(hps_ctx* ctx, Job& j, hps_precision prec, cudaStream_t st)
 {
     const auto key = std::make_tuple(j.g->p, (int)prec, ctx->use_tc);
-    auto it = ctx->nb_tuned.find(key);
-    if (it != ctx->nb_tuned.end()) { j.nb = it->second; return HPS_OK; }
-    const std::vector<int> cands = prec == HPS_FP64 ? std::vector<int>{32, 64} : std::vector<int>{64, 128};
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        j.nb = it->second.nb; j.unit = it->second.unit; j.bn = it->second.bn;
+        return HPS_OK;
+    }
+    const std::vector<TuneChoice> cands = tune_candidates(prec, ctx->use_tc != 0);
     Job trial = j;
     trial.nbox = std::min(j.nbox, 8);
     trial.zero_row_box = -1;
     float best = 1e30f;
-    int best_nb = cands.back();
+    TuneChoice best_c = cands.front();
     cudaEvent_t e0, e1;
     HPS_CUDA_TRY(cudaEventCreate(&e0));
     HPS_CUDA_TRY(cudaEventCreate(&e1));
-    for (int nb : cands) {
-        trial.nb = nb;
+    for (const TuneChoice& c : cands) {
+        trial.nb = c.nb; trial.unit = c.unit; trial.bn = c.bn;
         std::vector<Job> jobs{trial};
         std::vector<Plan> plans{job_plan(ctx, trial, prec)};
         std::vector<int> chunk;
@@ -685,13 +706,13 @@ hps_status tune_job(hps_ctx* ctx, Job& j, hps_precision prec, cudaStream_t st)
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
         }
-        if (rc == HPS_OK && ms < best) { best = ms; best_nb = nb; }
+        if (rc == HPS_OK && ms < best) { best = ms; best_c = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->nb_tuned[key] = best_nb;
+    ctx->tuned[key] = best_c;
     save_tuning(ctx);
-    j.nb = best_nb;
+    j.nb = best_c.nb; j.unit = best_c.unit; j.bn = best_c.bn;
     return HPS_OK;
 }
 
@@ -722,17 +743,17 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     std::vector<int> chunk;
     rc = ensure_workspace(ctx, plans, jobs, chunk);
     if (rc != HPS_OK) return rc;
-    const bool use_graph = ctx->graphs && !ctx->prof_on;
+    const bool use_graph = ctx->graphs && !ctx->prof_on && !tc_test_stall_armed();
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->tc_pairs << ' ' << ctx->lu_pairs << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->fp16_ops << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->lu_unit << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->fp16_ops << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
         key << " | " << j.g->p << ' ' << j.g->h[0] << ' ' << j.g->h[1] << ' ' << j.g->h[2] << ' ' << j.nbox << ' '
             << j.kappa << ' ' << j.kappa_dev << ' ' << j.b << ' ' << j.rhs_kind << ' ' << j.nload << ' ' << j.rhs
             << ' ' << j.T << ' ' << j.S << ' ' << j.v << ' ' << j.hf << ' ' << j.ui << ' ' << j.vadd << ' '
-            << j.status << ' ' << plans[i].NB << ' ' << chunk[i] << ' ' << j.zero_row_box << ' ' << j.beta;
+            << j.status << ' ' << plans[i].NB << ' ' << plans[i].unit_max << ' ' << plans[i].bn_max << ' ' << chunk[i] << ' ' << j.zero_row_box << ' ' << j.beta;
     }
     auto hit = ctx->graph_cache.find(key.str());
     if (hit == ctx->graph_cache.end()) {
@@ -1028,7 +1049,7 @@ size_t hps_workspace_per_box(int p, hps_precision prec)
 {
     if (!valid_p(p)) return 0;
     const int q = p - 2, n = q * q * q, m = 6 * q * q;
-    return make_plan(n, m, prec, 0, true, prec != HPS_FP64, true, true).per_box;
+    return make_plan(n, m, prec, 0, true, prec != HPS_FP64, 4, true).per_box;
 }
 
 hps_status hps_create(hps_ctx** out, int device, size_t workspace_bytes_max)
@@ -1100,20 +1121,16 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
         if (!(value == 0 || value == 1)) return HPS_EINVAL;
         ctx->tc_epi_cp = (int)value;
         return HPS_OK;
-    case HPS_OPT_TC_PAIRS:
-        if (!(value == 0 || value == 1)) return HPS_EINVAL;
-        ctx->tc_pairs = (int)value;
-        return HPS_OK;
-    case HPS_OPT_LU_PAIRS:
-        if (!(value == 0 || value == 1)) return HPS_EINVAL;
-        ctx->lu_pairs = (int)value;
+    case HPS_OPT_LU_UNIT:
+        if (!(value == 1 || value == 2 || value == 4 || value == 8)) return HPS_EINVAL;
+        ctx->lu_unit = (int)value;
         return HPS_OK;
     case HPS_OPT_TC_FUSE:
         if (!(value == -1 || value == 0 || value == 1)) return HPS_EINVAL;
         ctx->tc_fuse = (int)value;
         return HPS_OK;
     case HPS_OPT_RESIDUAL_DF:
-        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        if (!(value == 0 || value == 1 || value == 2 || value == 3)) return HPS_EINVAL;
         ctx->res_df = (int)value;
         return HPS_OK;
     case HPS_OPT_FP16_OPERANDS:
@@ -1122,6 +1139,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;
+        return HPS_OK;
+    case HPS_OPT_TEST_TC_TIMEOUT:
+        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        tc_test_stall_next((int)value);
         return HPS_OK;
     }
     return HPS_EINVAL;

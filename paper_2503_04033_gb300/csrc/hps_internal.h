@@ -43,6 +43,58 @@ inline int df_tab_f4(int q)
     return h * h + ((q & 1) ? h + 1 : 0) + q;
 }
 
+// Rounded FP64 product and sum, never contracted into a fused multiply-add, so
+// host and device code that use them give the same bits.
+__host__ __device__ inline double mul_rn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+__host__ __device__ inline double add_rn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+
+// Physical 1-D operators of every axis from the reference Chebyshev matrix
+// Dhat (p x p on [-1, 1], Sec. 2.1): D = (2 / h_a) Dhat and D2 = D D, each
+// [3][p][p] row-major.  D2 of the Chebyshev-Lobatto nodes is centro-symmetric
+// (D2[i][j] = D2[p-1-i][p-1-j]); the product holds that only up to rounding,
+// so each entry is averaged with its mirror to hold it exactly (the FP64
+// residual's even/odd line split relies on it).  Run by one thread, on the
+// host or the device, with the same bits either way.
+__host__ __device__ inline void geometry_tables(int p, const double* Dhat, const double* h, double* D, double* D2)
+{
+    const int pp = p * p;
+    for (int a = 0; a < 3; ++a) {
+        const double s = 2.0 / h[a];
+        double* Da = D + a * pp;
+        double* D2a = D2 + a * pp;
+        for (int e = 0; e < pp; ++e) Da[e] = mul_rn(s, Dhat[e]);
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < p; ++l) acc = add_rn(acc, mul_rn(Da[i * p + l], Da[l * p + j]));
+                D2a[i * p + j] = acc;
+            }
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                const int e = i * p + j, f = (p - 1 - i) * p + (p - 1 - j);
+                if (e < f) {
+                    const double v = mul_rn(0.5, add_rn(D2a[e], D2a[f]));
+                    D2a[e] = v;
+                    D2a[f] = v;
+                }
+            }
+    }
+}
+
 // Batched O = src + alpha * A * B over boxes (blockIdx.z), all row-major.
 template <typename T>
 struct GemmArgs {
@@ -65,9 +117,9 @@ struct Plan {
     size_t elt = 0;                  // bytes per LU element
     bool tc = false;                 // FP32 products on the tensor cores
     bool tma_epi = true;             // tcgen05 epilogue through TMA where O is 16-byte aligned
-    bool tc_pairs = false;           // tcgen05 products by CTA pairs sharing the right operand
-    bool step_pairs = false;         // tcgen05 path: consecutive LU steps joined in pairs
-    int KG = 0;                      // K extent of the gathered right operand (NB, or 2 NB with pairs)
+    int unit_max = 1;                // tcgen05 path: up to this many consecutive LU steps joined into one unit
+    int KG = 0;                      // K extent of the gathered right operand (unit_max x NB)
+    int bn_max = 256;                // widest tensor-core tile (128 or 256 columns)
     int fmt = 0;                     // tcgen05 operand format: 0 = 3 x TF32, 1 = 3 x BF16, 2 = scaled 2 x FP16
     bool fuse_fwd = false;           // forward solves: next G written by the epilogue (scattered stores)
     bool fuse_bwd = false;           // backward solves: next G written by the epilogue
@@ -82,7 +134,7 @@ struct Plan {
     size_t per_box = 0;
 };
 
-inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x, bool step_pairs = true,
+inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc, bool need_x, int lu_unit = 4,
                       bool fp16_ops = false)
 {
     Plan P;
@@ -117,8 +169,10 @@ inline Plan make_plan(int n, int r, hps_precision prec, int nb_opt, bool use_tc,
         P.perm_elems += (n - k);
     }
     P.nsteps = (int)P.k0.size();
-    P.step_pairs = P.tc && step_pairs && P.nsteps > 1;
-    P.KG = P.step_pairs ? 2 * NB : NB;
+    P.unit_max = 1;
+    if (P.tc)
+        while (2 * P.unit_max <= lu_unit && 2 * P.unit_max <= P.nsteps && 2 * P.unit_max <= 8) P.unit_max *= 2;
+    P.KG = P.unit_max * NB;
     const size_t A = 256;
     P.bM = align_up((size_t)n * P.ldm * P.elt, A);
     P.bF = align_up((size_t)P.fw_elems * P.elt, A);
@@ -214,7 +268,7 @@ inline Work<T> carve(const Plan& P, void* base, int nbox)
 // Kernel classes timed by the optional event profiler (HPS_OPT_PROFILE).
 enum KernelClass {
     KC_BUILD = 0, KC_PANEL, KC_UPDATE_CUDACORE, KC_UPDATE_TC, KC_GATHER, KC_RESIDUAL, KC_REFINE, KC_DN,
-    KC_UPDATE_TC_REFINE, KC_PACK, KC_RESIDUAL_DF, KC_MISC, KC_COUNT
+    KC_UPDATE_TC_REFINE, KC_PACK, KC_RESIDUAL_DF, KC_MISC, KC_RESIDUAL_DF64, KC_COUNT
 };
 
 // When profiling is on for the calling thread, prof_begin/prof_end bracket a
@@ -274,16 +328,45 @@ void launch_kappa_b(const Geometry& g, double kappa, const double* kappa_box, in
 // Residual of the first solution X0 (FP32, rows of pitch ld, box stride sbx),
 // written over X0 in place as FP32: R = B - A_ii X0 in double-float
 // arithmetic.  Needs g.dDF and the split kappa^2 b (launch_kappa_b).
+// Whether the double-float residual's per-CTA tables and line buffers fit in
+// shared memory at this order (x64: the form that reads an FP64 X).
+bool residual_df_fits(const Geometry& g, bool x64);
+// With X64 (FP64 [n][ldx] per box, stride sX64) the residual is of that
+// solution instead, each entry split into two floats (about 2^-46 relative to
+// the terms' magnitudes as well), and X0R only receives R.
 void launch_residual_df(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
                         float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip,
-                        cudaStream_t st);
+                        cudaStream_t st, const double* X64 = nullptr, long long ldx = 0, long long sX64 = 0);
 
 void launch_ir_update(const float* D, long long ldd, long long sD, int n, int ncols,
                       double* X, long long ldx, long long sX, double* norms /*[nbox][2]*/,
                       const int* skip, int nbox, cudaStream_t st, bool want_xn = false);
 
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
-                     int* iters, double* relcorr, int* status, cudaStream_t st, bool hold = false);
+                     int* iters, double* relcorr, int* status, cudaStream_t st, bool hold = false,
+                     double floor_coef = 0.0, double dfgate = 0.0, int* route = nullptr, int* skip_df = nullptr,
+                     int* skip_64 = nullptr);
+
+// Error floor of a correction computed from the double-float residual,
+// relative to that correction's own size.  The residual of X0 is formed with
+// relative error about 2^-46 of the terms' magnitudes |A_ii||X0| + |B|; the
+// LU that produced X0 has a backward error of about 2^-22 relative to the
+// same magnitudes (22-bit split operands, FP32 storage and accumulation).
+// Both pass through the same A_ii^{-1}, so the correction's error is about
+// 2^-24 times X0's error, which the correction itself measures: the floor is
+// taken as 100 * 2^-24 * ||dX_1||, a factor 100 of margin.
+constexpr double kDfFloor = 100.0 / 16777216.0;
+
+// Routing of the later residuals (HPS_OPT_RESIDUAL_DF = 3).  A residual of
+// an FP64 X split into two floats is formed with relative error about 2^-46
+// of the terms' magnitudes, against 2^-53 in FP64; A_ii^{-1} amplifies that
+// error by about rel_1 / 2^-22, where rel_1 = ||dX_1|| / ||X|| is the first
+// correction's size (it measures X0's error, which the same amplification
+// made from the LU's 2^-22).  A box whose rel_1 is at most kDfGate therefore
+// has a double-float residual floor below about kDfGate 2^-24 ~ 2e-11 of X,
+// a factor 5 under the 1e-10 target; its later residuals run in
+// double-float, every other box's in FP64.
+constexpr double kDfGate = 3.0e-4;
 
 void launch_transpose_add(const double* X, long long ldx, long long sX, int n, int ncols,
                           const double* v, double* out, int nbox, cudaStream_t st);
@@ -322,6 +405,11 @@ void lu_backward(const Plan& P, Work<T>& w, int nbox, int c0, int nc, const int*
 // with tc_abort_raised, cleared by tc_reset_abort) and marks its box
 // HPS_ETIMEOUT.
 void tc_reset_abort(cudaStream_t st);
+// Test hook: the next tensor-core launch of a call that writes box status
+// makes its first mbarrier wait run out (nothing is issued to fill it); that
+// launch and the rest of the call end with HPS_ETIMEOUT in box_status.
+void tc_test_stall_next(int on);
+bool tc_test_stall_armed();
 bool tc_abort_raised();
 bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStream_t st);
 bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, const int* skip, cudaStream_t st);

@@ -1158,15 +1158,58 @@ __device__ __forceinline__ void eo_line_df(const float* __restrict__ src, int st
     }
 }
 
+// The same line in plain FP32 with the leading (hi) parts of the tables:
+// the contribution of the low part of a split FP64 X, itself 2^-24 of X, so
+// FP32 rounding here is 2^-48 of the terms.  emit(i, value).
+template <int Q, class Emit>
+__device__ __forceinline__ void eo_line_f32(const float* __restrict__ src, int stride, const float4* tab, Emit&& emit)
+{
+    constexpr int H = Q / 2;
+    float x[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) x[l] = src[l * stride];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+        const float a = x[l], z = x[Q - 1 - l];
+        x[l] = a + z;
+        x[Q - 1 - l] = a - z;
+    }
+    const float2* t2 = reinterpret_cast<const float2*>(tab + H * H);
+#pragma unroll 1
+    for (int i = 0; i < H; ++i) {
+        float se = 0.0f, so = 0.0f;
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            const float4 t = lds_f32x4(tab + i * H + l);
+            se = fmaf(t.x, x[l], se);
+            so = fmaf(t.z, x[Q - 1 - l], so);
+        }
+        if constexpr ((Q & 1) != 0) se = fmaf(lds_f32x2(t2 + i).x, x[H], se);
+        emit(i, se + so);
+        emit(Q - 1 - i, se - so);
+    }
+    if constexpr ((Q & 1) != 0) {
+        float sm = lds_f32x2(t2 + 2 * H).x * x[H];
+#pragma unroll
+        for (int l = 0; l < H; ++l) sm = fmaf(lds_f32x2(t2 + H + l).x, x[l], sm);
+        emit(H, sm);
+    }
+}
+
 // R = B - A_ii X0 for the FP32 first solution X0, in double-float, written
 // over X0 (each CTA reads its whole column before it writes).  Same passes
 // and CTA shape as k_residual; DTN right-hand sides are added in
 // double-float, LOAD and TRACE ones in FP64 at the end.
-template <int Q>
+// X64: X is an FP64 solution (X64 [n][ldx] per box, stride sX64) split per
+// entry into hi = float(x) and lo = float(x - hi) (x - hi is exact in FP64,
+// lo rounds at 2^-48 of x): A_ii hi in double-float as above, A_ii lo in FP32
+// (eo_line_f32, added to the pairs' low parts), R written to X0R (which is
+// then output only).  Otherwise X0R holds X0 and receives R.
+template <int Q, bool X64>
 __global__ void __launch_bounds__(res_threads<Q>(), res_min_blocks<Q>())
 k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restrict__ kbs, int rhs_kind,
               const double* __restrict__ rhs, long long s_rhs, float* X0R, long long ld, long long sbx,
-              const int* skip)
+              const int* skip, const double* __restrict__ Xin, long long ldx, long long sX64)
 {
     constexpr int TF = df_tab_q<Q>(), q = Q, qq = Q * Q;
     constexpr int BO = TF - Q;   // boundary couplings within an axis table
@@ -1178,10 +1221,22 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
     float2* Ac = reinterpret_cast<float2*>(tab + 3 * TF);   // [n]
     float2* Ks = Ac + n;                                     // [n] kappa^2 b
     float* Xs = reinterpret_cast<float*>(Ks + n);           // [n]
+    float* Xl = Xs + n;                                      // [n] low parts (X64 only)
     float* col = X0R + box * sbx + cw;
     const float2* kbb = kbs + (long long)box * n;
+    if constexpr (X64) {
+        const double* xc = Xin + box * sX64 + cw;
 #pragma unroll 4
-    for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = col[(long long)r * ld];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const double x = xc[(long long)r * ldx];
+            const float hi = d2f_rn(x);
+            Xs[r] = hi;
+            Xl[r] = d2f_rn(x - f2d(hi));
+        }
+    } else {
+#pragma unroll 4
+        for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = col[(long long)r * ld];
+    }
     for (int r = threadIdx.x; r < n; r += blockDim.x) Ks[r] = kbb[r];
     for (int idx = threadIdx.x; idx < 3 * TF; idx += blockDim.x) tab[idx] = DF[idx];
     __syncthreads();
@@ -1189,6 +1244,7 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
     if (ln < qq) {
         const int base = ln * q;
         eo_line_df<Q>(Xs + base, 1, tab, [&](int i, float h, float l) { Ac[base + i] = make_float2(h, l); });
+        if constexpr (X64) eo_line_f32<Q>(Xl + base, 1, tab, [&](int i, float v) { Ac[base + i].y += v; });
     }
     __syncthreads();
     if (ln < qq) {
@@ -1198,6 +1254,7 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
             df_add(a.x, a.y, h, l);
             Ac[base + q * j] = a;
         });
+        if constexpr (X64) eo_line_f32<Q>(Xl + base, q, tab + TF, [&](int j, float v) { Ac[base + q * j].y += v; });
     }
     __syncthreads();
     if (ln < qq) {
@@ -1207,12 +1264,14 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
             if (cg < 6 * qq) kind = RHS_DTN;
             else { kind = RHS_LOAD; cg -= 6 * qq; }
         }
+        if constexpr (X64) eo_line_f32<Q>(Xl + ln, qq, tab + 2 * TF, [&](int k0, float v) { Ac[ln + qq * k0].y += v; });
         eo_line_df<Q>(Xs + ln, qq, tab + 2 * TF, [&](int k0, float h, float l) {
             const int k = k0 + 1, r = ln + qq * k0;
             float2 a = Ac[r];
             df_add(a.x, a.y, h, l);
             const float2 kk = Ks[r];
             df_mac1(a.x, a.y, kk.x, kk.y, Xs[r]);
+            if constexpr (X64) a.y = fmaf(kk.x, Xl[r], a.y);
             float out;
             if (kind == RHS_DTN) {   // -A_ib e_f: D2[.][0] or D2[.][p-1] next to face node f
                 const int f = cg / qq, s2 = cg % qq, u = s2 % q + 1, v = s2 / q + 1;
@@ -1275,31 +1334,50 @@ k_ir_update(const float* __restrict__ D, long long ldd, long long sD, int n, int
     }
 }
 
-// Per-box stopping rule of the refinement.  After correction k (relative size
-// rel_k = ||dX_k|| / ||X||) the remaining error is about rho * rel_k, with the
-// contraction rho estimated by rel_k / rel_{k-1}; a box stops when that
-// prediction, with a factor 10 of margin, is below tol, or when the correction
-// has stopped shrinking (less than a halving) while already below stag_tol,
-// i.e. X sits at the FP64 residual's noise floor.
+// Per-box stopping rule of the refinement.  After correction k >= 2
+// (relative size rel_k = ||dX_k|| / ||X||) the remaining error is about
+// rho * rel_k, with the contraction rho estimated by rel_k / rel_{k-1}; a box
+// stops when that prediction, with a factor 10 of margin, plus
+// floor_coef * rel_k (the error the correction's own residual may carry, see
+// kDfFloor) is below tol, or when the correction has stopped shrinking (less
+// than a halving) while already below stag_tol, i.e. X sits at the
+// residual's noise floor.  The first correction gives no rate (X0's error and
+// the contraction need not match, e.g. for smooth right-hand sides), so it
+// ends the refinement only when it is itself below tol.
+//
+// With dfgate > 0 the check also routes each box's later residuals: at the
+// first correction it records whether rel_1 <= dfgate (split[box]: the
+// double-float residual is accurate enough for this box, see kDfGate), and
+// after every correction it writes the skip flags of the two residual
+// kernels, skip_df (boxes done or routed to FP64) and skip_64 (boxes done or
+// routed to double-float).
 __global__ void k_ir_check(int nbox, double* norms, double tol, double stag_tol, int last, int* skip, int* iters,
-                           double* relcorr, int* status, int hold)
+                           double* relcorr, int* status, int hold, double floor_coef, double dfgate, int* route,
+                           int* skip_df, int* skip_64)
 {
     const int box = blockIdx.x * blockDim.x + threadIdx.x;
     if (box >= nbox || skip[box]) return;
     const double dn = norms[2 * box], xn = norms[2 * box + 1];
     const double rel = xn > 0.0 ? sqrt(dn / xn) : sqrt(dn);
-    const double prev = relcorr[box];
     iters[box] += 1;
+    const double prev = iters[box] == 1 ? 0.0 : relcorr[box];   // no rate estimate from the first correction
     relcorr[box] = rel;
     norms[2 * box] = 0.0;   // ||X||^2 (from the first solution) is kept
-    bool done = rel <= tol;
-    if (iters[box] > 1 && prev > 0.0) {
+    bool done = false;
+    if (prev > 0.0) {
         const double rho = rel / prev;
-        done = done || rel * fmin(1.0, 10.0 * rho) <= tol || (rel <= stag_tol && rho > 0.5);
+        done = rel * fmin(1.0, 10.0 * rho) + floor_coef * rel <= tol || (rel <= stag_tol && rho > 0.5);
+    } else {
+        done = rel <= tol;
     }
     if (hold) done = false;   // this correction came from the double-float residual: one more in FP64
     if (done) skip[box] = 1;
     else if (last && status[box] == 0) status[box] = isfinite(rel) ? HPS_ENOCONV : HPS_EINVAL;
+    if (dfgate > 0.0) {
+        if (iters[box] == 1) route[box] = rel <= dfgate ? 1 : 0;
+        skip_df[box] = done || !route[box];
+        skip_64[box] = done || route[box];
+    }
 }
 
 // out[c][r] = X[r][c] (+ v[c][r]) for the [nrhs][n] output layouts.
@@ -1712,31 +1790,49 @@ void launch_residual(const Geometry& g, double kappa, const double* kappa_box, i
 namespace {
 template <int Q>
 void residual_df_q(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
-                   float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st)
+                   float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st,
+                   const double* X64, long long ldx, long long sX64)
 {
-    const size_t smem = (size_t)3 * df_tab_q<Q>() * sizeof(float4) + (size_t)g.n * (2 * sizeof(float2) + sizeof(float));
+    const size_t smem = (size_t)3 * df_tab_q<Q>() * sizeof(float4) +
+                        (size_t)g.n * (2 * sizeof(float2) + (X64 ? 2 : 1) * sizeof(float));
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_residual_df<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_residual_df<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_residual_df<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr = true;
     }
     dim3 grd((unsigned)nrhs, (unsigned)nbox);
-    prof_begin(KC_RESIDUAL_DF, st);
-    k_residual_df<Q><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, reinterpret_cast<const float4*>(g.dDF), kbs,
-                                                           rhs_kind, rhs_src, s_rhs, X0R, ld, sbx, skip);
+    prof_begin(X64 ? KC_RESIDUAL_DF64 : KC_RESIDUAL_DF, st);
+    if (X64)
+        k_residual_df<Q, true><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, reinterpret_cast<const float4*>(g.dDF),
+                                                                     kbs, rhs_kind, rhs_src, s_rhs, X0R, ld, sbx, skip,
+                                                                     X64, ldx, sX64);
+    else
+        k_residual_df<Q, false><<<grd, res_threads<Q>(), smem, st>>>(g.p, g.n, reinterpret_cast<const float4*>(g.dDF),
+                                                                      kbs, rhs_kind, rhs_src, s_rhs, X0R, ld, sbx,
+                                                                      skip, nullptr, 0, 0);
     // work counted as for the FP64 residual (its operations per entry); bytes:
-    // X0 and R in FP32, the split kappa^2 b
+    // X (FP32, or FP64 for X64) and R in FP32, the split kappa^2 b
     const double per = 3.0 * (2.0 + 2.0 * (Q / 2) + ((Q & 1) ? 2.0 : 0.0)) + 3.0;
-    prof_end(KC_RESIDUAL_DF, st, (double)nbox * g.n * (double)nrhs * per, (double)nbox * g.n * (double)nrhs * 8.0);
+    prof_end(X64 ? KC_RESIDUAL_DF64 : KC_RESIDUAL_DF, st, (double)nbox * g.n * (double)nrhs * per,
+             (double)nbox * g.n * (double)nrhs * (X64 ? 12.0 : 8.0));
 }
 }  // namespace
 
-void launch_residual_df(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
-                        float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st)
+bool residual_df_fits(const Geometry& g, bool x64)
 {
-#define HPS_RES_CASE(QV)                                                                           \
-    case QV:                                                                                       \
-        residual_df_q<QV>(g, nbox, rhs_kind, nrhs, rhs_src, s_rhs, X0R, ld, sbx, kbs, skip, st); \
+    const size_t smem = (size_t)3 * df_tab_f4(g.q) * sizeof(float4) +
+                        (size_t)g.n * (2 * sizeof(float2) + (x64 ? 2 : 1) * sizeof(float));
+    return smem <= 227 * 1024;
+}
+
+void launch_residual_df(const Geometry& g, int nbox, int rhs_kind, int nrhs, const double* rhs_src, long long s_rhs,
+                        float* X0R, long long ld, long long sbx, const float2* kbs, const int* skip, cudaStream_t st,
+                        const double* X64, long long ldx, long long sX64)
+{
+#define HPS_RES_CASE(QV)                                                                                          \
+    case QV:                                                                                                      \
+        residual_df_q<QV>(g, nbox, rhs_kind, nrhs, rhs_src, s_rhs, X0R, ld, sbx, kbs, skip, st, X64, ldx, sX64); \
         break;
     switch (g.q) {
         HPS_RES_CASE(1) HPS_RES_CASE(2) HPS_RES_CASE(3) HPS_RES_CASE(4) HPS_RES_CASE(5) HPS_RES_CASE(6)
@@ -1759,11 +1855,12 @@ void launch_ir_update(const float* D, long long ldd, long long sD, int n, int nc
 }
 
 void launch_ir_check(int nbox, double* norms, double tol, int last, int* skip,
-                     int* iters, double* relcorr, int* status, cudaStream_t st, bool hold)
+                     int* iters, double* relcorr, int* status, cudaStream_t st, bool hold, double floor_coef,
+                     double dfgate, int* route, int* skip_df, int* skip_64)
 {
     prof_begin(KC_MISC, st);
     k_ir_check<<<(nbox + 127) / 128, 128, 0, st>>>(nbox, norms, tol, 1e-11, last, skip, iters, relcorr, status,
-                                                    hold ? 1 : 0);
+                                                    hold ? 1 : 0, floor_coef, dfgate, route, skip_df, skip_64);
     prof_end(KC_MISC, st, 0.0, (double)nbox * 40.0);
 }
 

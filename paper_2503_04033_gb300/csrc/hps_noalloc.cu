@@ -10,7 +10,6 @@
 // process exits.  The caller still passes b and T; nothing else is allocated.
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "hps_internal.h"
 
@@ -18,15 +17,28 @@ namespace {
 
 constexpr size_t kScratchBytes = 64ull << 20;   // 64 MiB per device
 constexpr int kMaxDevices = 64;
+constexpr int kMaxNoallocP = 14;                 // the largest order whose one-box workspace fits the scratch
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  In host code the
-// symbol is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// The reference Chebyshev matrix and the box size, passed by value as a kernel
+// parameter: the tables need no host-to-device copy.
+struct TableArgs {
+    int p;
+    double h[3];
+    double Dhat[kMaxNoallocP * kMaxNoallocP];
+};
+
+// D and D2 of every axis written into the scratch by one thread, with the
+// helper (and so the bits) of the context path's tables.
+__global__ void k_noalloc_tables(const TableArgs a, double* D, double* D2)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) hps::geometry_tables(a.p, a.Dhat, a.h, D, D2);
+}
+
 hps_status scratch_address(int dev, unsigned char** out)
 {
     if (dev < 0 || dev >= kMaxDevices) return HPS_EINVAL;
@@ -63,7 +75,7 @@ extern "C" hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int 
     const Plan P = make_plan(n, m, HPS_FP64, 0, false, false);
     const size_t tables = align_up(2 * 3 * (size_t)pp * sizeof(double), 256);
     const size_t fixed = tables + (box_status ? 0 : align_up((size_t)nbox * sizeof(int), 256));
-    if (fixed + P.per_box > kScratchBytes) return HPS_ENOMEM;   // one box does not fit: p (or nbox) too large
+    if (p > kMaxNoallocP || fixed + P.per_box > kScratchBytes) return HPS_ENOMEM;   // one box does not fit
     const int chunk = (int)std::min<size_t>((size_t)nbox, (kScratchBytes - fixed) / P.per_box);
 
     int dev = 0;
@@ -72,29 +84,18 @@ extern "C" hps_status hps_leaf_build_dtn_noalloc(const hps_leaf_kind* kind, int 
     hps_status rc = scratch_address(dev, &base);
     if (rc != HPS_OK) return rc;
 
-    // Operator tables, computed on the host and copied into the scratch.
-    std::vector<double> Dhat(pp), DD(6 * (size_t)pp);
-    cheb_diff(p, Dhat.data());
-    for (int a = 0; a < 3; ++a) {
-        const double s = 2.0 / kind->h[a];
-        double* Da = DD.data() + a * pp;
-        double* D2a = DD.data() + 3 * pp + a * pp;
-        for (int e = 0; e < pp; ++e) Da[e] = s * Dhat[e];
-        for (int i = 0; i < p; ++i)
-            for (int j = 0; j < p; ++j) {
-                double acc = 0.0;
-                for (int l = 0; l < p; ++l) acc += Da[i * p + l] * Da[l * p + j];
-                D2a[i * p + j] = acc;
-            }
-    }
+    // Operator tables, built on the device from the reference matrix (host
+    // arithmetic only for Dhat, which travels as a kernel parameter).
+    TableArgs ta{};
+    ta.p = p;
+    for (int a = 0; a < 3; ++a) ta.h[a] = kind->h[a];
+    cheb_diff(p, ta.Dhat);
     Geometry g;
     g.p = p; g.q = q; g.n = n; g.m = m;
     for (int a = 0; a < 3; ++a) g.h[a] = kind->h[a];
     g.dD = reinterpret_cast<double*>(base);
     g.dD2 = g.dD + 3 * pp;
-    if (cudaMemcpyAsync(g.dD, DD.data(), DD.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return HPS_ECUDA;
-    // The copy source is pageable host memory: the call returns once it is staged.
+    k_noalloc_tables<<<1, 32, 0, st>>>(ta, g.dD, g.dD2);
 
     // Status words must start at zero (the array keeps the previous call's contents).
     int* status = box_status ? box_status : reinterpret_cast<int*>(base + tables);

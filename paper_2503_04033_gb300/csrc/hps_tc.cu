@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <functional>
 #include <utility>
 #include <vector>
 
@@ -91,19 +92,31 @@ constexpr size_t EPI_BYTES_CP = (size_t)TC_EPI_WARPS * EPI_FLOATS * 4;
 constexpr size_t EPI_BYTES_TMA = (size_t)TC_EPI_WARPS * TE_PRE * TE_CHUNK;
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + (EPI_BYTES_CP > EPI_BYTES_TMA ? EPI_BYTES_CP : EPI_BYTES_TMA) +
                            1024;
-constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait
+constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait (TcArgs.wait_ns)
+
+// Tensor maps of one update product: up to eight parts of the left operand
+// (the steps of an LU unit), the right operand G and the output O.
+constexpr int kMaxParts = 8;
+struct TcMaps {
+    CUtensorMap A[kMaxParts];
+    CUtensorMap B;
+    CUtensorMap O;
+};
 
 struct TcArgs {
     float* O; long long ldo, sO;
     int M, N, kch;
-    int kch1, a2_off;                // K chunks from the first A map; row offset of the second map
+    int nparts;                      // parts of the left operand (one tensor map each)
+    int kch_end[kMaxParts];          // K chunk where part i ends (parts follow each other along K)
+    int a_off[kMaxParts];            // row of the product where part i's row 0 sits (rows above load as zeros)
     int tiles_m, tiles_n, tiles;
     int nbox;
-    int cl;                          // CTA pairs (cluster of 2) sharing B by TMA multicast
-    int units, units_per_box;        // work units: tiles, or row-tile pairs x column tiles when cl
+    int units, units_per_box;        // work units (output tiles) in all, and per box
     int vec;                         // rows of O and W are 16-byte aligned: float4 epilogue
     int tma_epi;                     // O is 16-byte aligned: source tiles in and results out by TMA
     int mode, split;
+    unsigned long long wait_ns;      // limit of every mbarrier wait
+    int test_stall;                  // test hook: the TMA role issues nothing, so the first wait runs out
     const int* perm; long long sP;
     const float* W; long long ldw, sW;
     const int* skip;
@@ -157,11 +170,12 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Bounded wait on an mbarrier phase; false when it gave up.  The epilogue
-// warps back off (spinning warps steal issue slots); the single-thread TMA
-// and MMA roles poll (try_wait already suspends in hardware for a while).
+// Bounded wait on an mbarrier phase (limit in ns); false when it gave up.  The
+// epilogue warps back off (spinning warps steal issue slots); the
+// single-thread TMA and MMA roles poll (try_wait already suspends in hardware
+// for a while).
 template <bool kBackoff = true>
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit)
 {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
@@ -169,7 +183,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
         if (kBackoff && it >= 8) __nanosleep(it < 64 ? 32 : 128);
         if ((it & 255u) == 255u) {
             if (*reinterpret_cast<volatile int*>(&g_tc_abort)) return false;
-            if (global_ns() - t0 > WAIT_NS) {
+            if (global_ns() - t0 > limit) {
                 atomicExch(&g_tc_abort, 1);
                 return false;
             }
@@ -177,15 +191,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
-// Bounded wait used only to let copies already in flight land before a CTA
-// that gave up exits (it does not return early on the abort flag).
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+// Bounded wait used only to let asynchronous work already in flight (TMA
+// copies, MMAs) finish before a CTA that gave up exits; it does not return
+// early on the abort flag.  Such work completes by itself, so in practice this
+// returns at once.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint64_t limit)
 {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return;
         __nanosleep(128);
-        if ((it & 63u) == 63u && global_ns() - t0 > WAIT_NS / 4) return;
+        if ((it & 63u) == 63u && global_ns() - t0 > limit) return;
     }
 }
 
@@ -197,41 +213,6 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm,
         "[%2];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
-}
-
-// TMA load delivered to the same shared-memory offset in every CTA of the
-// cluster named in mask, each CTA's mbarrier at bar receiving the bytes.
-__device__ __forceinline__ void tma_load_4d_mc(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1,
-                                               int c2, int c3, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%3, %4, %5, %6}], [%2], %7;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t nclusters_x()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync_all()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0, int c1, int c2)
@@ -296,23 +277,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-// Arrive, once the MMAs issued so far complete, on the mbarrier at bar in every
-// CTA of the cluster named in mask.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                     "r"(bar),
-                 "h"(mask)
-                 : "memory");
-}
-
-// The CTA's sequence of work units.  Alone, a CTA takes tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... (box-major, so a box's A and G stay in L2 while
-// its tiles run).  In a pair, both CTAs of cluster c take units c, c + nclusters,
-// ...; a unit is a pair of vertically adjacent row tiles at one column tile,
-// the CTA of rank r taking row tile 2 i + r.
+// The CTA's sequence of work units (output tiles): blockIdx.x, blockIdx.x +
+// gridDim.x, ... (box-major, so a box's A and G stay in L2 while its tiles
+// run).
 struct TcSched {
-    int u0, ustep, units, upb, tiles_n, rank, cl, bn;
+    int u0, ustep, units, upb, tiles_n, bn;
     __device__ bool skipped(int u, const int* skip) const { return skip && skip[u / upb]; }
     __device__ int first_from(int u, const int* skip) const
     {
@@ -324,7 +293,7 @@ struct TcSched {
         box = u / upb;
         const int rem = u - box * upb, mi = rem / tiles_n;
         n0 = (rem - mi * tiles_n) * bn;
-        m0 = (cl ? 2 * mi + rank : mi) * TC_BM;
+        m0 = mi * TC_BM;
     }
 };
 
@@ -452,9 +421,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // of each MMA on padding.
 template <int FMT, int BNT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
-            const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO, TcArgs a)
+k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
 {
+    const CUtensorMap& tmB = tm.B;
+    const CUtensorMap& tmO = tm.O;
     using Fm = TcFmt<FMT>;
     constexpr int BN = BNT, KPC = Fm::KPC, NPL = Fm::NPL;
     constexpr uint32_t B_TILE = (uint32_t)BN * ROWB;
@@ -465,6 +435,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2];
     __shared__ __align__(8) uint64_t tempty_bar[2];
+    __shared__ __align__(8) uint64_t mdrain_bar;   // the MMA role's last commit when it gives up
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
 
@@ -473,25 +444,17 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     unsigned char* sbase_ptr = smem_raw + (sbase - smem_u32(smem_raw));
     TcSched sc;
     sc.bn = BN;
-    sc.cl = a.cl;
     sc.tiles_n = a.tiles_n;
     sc.units = a.units;
     sc.upb = a.units_per_box;
-    if (a.cl) {
-        sc.u0 = (int)cluster_id_x();
-        sc.ustep = (int)nclusters_x();
-        sc.rank = (int)cluster_ctarank();
-    } else {
-        sc.u0 = blockIdx.x;
-        sc.ustep = gridDim.x;
-        sc.rank = 0;
-    }
+    sc.u0 = blockIdx.x;
+    sc.ustep = gridDim.x;
     float* tbuf_all = reinterpret_cast<float*>(sbase_ptr + TC_STAGES * STAGE_BYTES);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), a.cl ? 2 : 1);   // a pair: both CTAs' MMAs release a stage
+            mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull_bar[b]), 1);
@@ -499,23 +462,23 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         for (int w = 0; w < TC_EPI_WARPS; ++w)
             for (int q = 0; q < TE_PRE; ++q) mbar_init(smem_u32(&ld_bar[w][q]), 1);
+        mbar_init(smem_u32(&mdrain_bar), 1);
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 2 * BN);
     tc_fence_before();
     __syncthreads();
-    if (a.cl) cluster_sync_all();   // the partner's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
     if (warp == 0) {
         if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
+            for (int pi = 0; pi < a.nparts; ++pi)
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm.A[pi])) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
             uint32_t g = 0;
-            bool ok = true;
+            bool ok = !a.test_stall;
             for (int u = sc.u0; u < sc.units && ok; u += sc.ustep) {
                 if (sc.skipped(u, a.skip)) continue;
                 int box, m0, n0;
@@ -523,7 +486,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 for (int ch = 0; ch < a.kch; ++ch, ++g) {
                     const int s = g % TC_STAGES;
                     const uint32_t use = g / TC_STAGES;
-                    if (g >= TC_STAGES && !mbar_wait<false>(smem_u32(&empty_bar[s]), (use - 1) & 1)) {
+                    if (g >= TC_STAGES && !mbar_wait<false>(smem_u32(&empty_bar[s]), (use - 1) & 1, a.wait_ns)) {
                         fail_sh = 1;
                         ok = false;
                         break;
@@ -531,34 +494,24 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     const uint32_t fb = smem_u32(&full_bar[s]);
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     mbar_expect_tx(fb, STAGE_TX);
-                    // A's K chunks past kch1 come from the second map, whose row 0 is
-                    // row a2_off of the product (rows above it load as zeros)
-                    const bool second = ch >= a.kch1;
-                    const CUtensorMap* ma = second ? &tmA2 : &tmA;
-                    const int ka = (second ? ch - a.kch1 : ch) * KPC, ra = second ? m0 - a.a2_off : m0;
+                    // A's K chunks come from the part whose range holds ch; part
+                    // i's row 0 is row a_off[i] of the product (rows above it
+                    // load as zeros)
+                    int pi = 0;
+                    while (pi + 1 < a.nparts && ch >= a.kch_end[pi]) ++pi;
+                    const CUtensorMap* ma = &tm.A[pi];
+                    const int ka = (ch - (pi ? a.kch_end[pi - 1] : 0)) * KPC, ra = m0 - a.a_off[pi];
 #pragma unroll
                     for (int pl = 0; pl < NPL; ++pl) tma_load_4d(st + pl * A_TILE, ma, fb, ka, ra, pl, box);
                     const uint32_t sb0 = st + NPL * A_TILE;
-                    if (a.cl) {
-                        // this CTA's half of B's rows, into both CTAs of the pair
-                        const uint32_t off = (uint32_t)sc.rank * (B_TILE / 2);
-                        const int nr = n0 + sc.rank * (BN / 2);
 #pragma unroll
-                        for (int pl = 0; pl < NPL; ++pl)
-                            tma_load_4d_mc(sb0 + pl * B_TILE + off, &tmB, fb, ch * KPC, nr, pl, box, 0x3);
-                    } else {
-#pragma unroll
-                        for (int pl = 0; pl < NPL; ++pl) tma_load_4d(sb0 + pl * B_TILE, &tmB, fb, ch * KPC, n0, pl, box);
-                    }
+                    for (int pl = 0; pl < NPL; ++pl) tma_load_4d(sb0 + pl * B_TILE, &tmB, fb, ch * KPC, n0, pl, box);
                 }
             }
-            // Drain: the last loads issued into each stage have landed, and
-            // (in a pair) both MMAs have released every stage, so no arrival
-            // from the partner is still on its way when this CTA exits.
-            for (uint32_t h = (g > TC_STAGES ? g - TC_STAGES : 0); h < g; ++h) {
-                if (!mbar_wait<false>(smem_u32(&full_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
-                if (!mbar_wait<false>(smem_u32(&empty_bar[h % TC_STAGES]), (h / TC_STAGES) & 1)) fail_sh = 1;
-            }
+            // Drain: the last loads issued into each stage have landed before
+            // this CTA exits (the MMA role waits for its own MMAs).
+            for (uint32_t h = (g > TC_STAGES ? g - TC_STAGES : 0); h < g; ++h)
+                mbar_drain(smem_u32(&full_bar[h % TC_STAGES]), (h / TC_STAGES) & 1, a.wait_ns / 4);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -570,12 +523,20 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (sc.skipped(u, a.skip)) continue;
                 const int b = j & 1;
                 const uint32_t uj = j >> 1;
-                if (j >= 2 && !mbar_wait<false>(smem_u32(&tempty_bar[b]), (uj - 1) & 1)) { fail_sh = 1; break; }
+                if (j >= 2 && !mbar_wait<false>(smem_u32(&tempty_bar[b]), (uj - 1) & 1, a.wait_ns)) {
+                    fail_sh = 1;
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int ch = 0; ch < a.kch; ++ch, ++g) {
                     const int s = g % TC_STAGES;
-                    if (!mbar_wait<false>(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1)) { fail_sh = 1; ok = false; break; }
+                    if (!mbar_wait<false>(smem_u32(&full_bar[s]), (g / TC_STAGES) & 1, a.wait_ns)) {
+                        fail_sh = 1;
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     uint64_t ad[NPL], bd[NPL];
@@ -606,11 +567,16 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             mma_bf16(d, ad[0] + o, bd[0] + o, idesc, 1);
                         }
                     }
-                    if (a.cl) mma_commit_mc(smem_u32(&empty_bar[s]), 0x3);
-                    else mma_commit(smem_u32(&empty_bar[s]));
+                    mma_commit(smem_u32(&empty_bar[s]));
                 }
+                if (!ok) break;
                 mma_commit(smem_u32(&tfull_bar[b]));
                 ++j;
+            }
+            if (!ok) {
+                // every MMA issued so far completes before TMEM is released
+                mma_commit(smem_u32(&mdrain_bar));
+                mbar_drain(smem_u32(&mdrain_bar), 0, a.wait_ns / 4);
             }
         }
     } else if (a.tma_epi) {
@@ -661,7 +627,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const int b = j & 1;
             float its8[8];   // format 2 column scales (the loads overlap the wait)
             if constexpr (FMT == 2) load_tile_scales(its8, a.invt + box * a.sInvt + n0, nch, lane);
-            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1);
+            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1, a.wait_ns);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
@@ -717,7 +683,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
                 }
-                if (need_src && !mbar_wait(lbar0 + 8 * buf, (g / TE_PRE) & 1)) ok = false;
+                if (need_src && !mbar_wait(lbar0 + 8 * buf, (g / TE_PRE) & 1, a.wait_ns)) ok = false;
                 if (!__all_sync(0xffffffffu, ok ? 1 : 0)) {
                     ok = false;
                     break;
@@ -768,7 +734,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (lane == 0) {
             if (!ok) {
                 fail_sh = 1;
-                for (uint32_t h = g; h < lg; ++h) mbar_drain(lbar0 + 8 * (h % TE_PRE), (h / TE_PRE) & 1);
+                for (uint32_t h = g; h < lg; ++h) mbar_drain(lbar0 + 8 * (h % TE_PRE), (h / TE_PRE) & 1, a.wait_ns / 4);
             }
             bulk_wait_all();
         }
@@ -851,7 +817,7 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             const int b = j & 1;
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1);
+            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1, a.wait_ns);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) {
                 asm volatile("cp.async.wait_all;" ::: "memory");
@@ -911,7 +877,6 @@ k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     tc_fence_before();
     __syncthreads();
-    if (a.cl) cluster_sync_all();   // neither CTA of a pair leaves while the other may still reach it
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
@@ -1040,7 +1005,63 @@ __global__ void k_gather_pack_f16(const float* __restrict__ M, long long ldm, lo
     const float* rcb = rc + box * sC;
     const int c = cb + tx;
     const int ncc = min(32, nc - cb);   // columns of this chunk (uniform over the CTA)
-    if (ncc == 32) {
+    const bool vec4 = ncc == 32 && ((reinterpret_cast<uintptr_t>(Mb + c0 + cb) & 15) == 0) && (ldm & 3) == 0 &&
+                      (!W || (((reinterpret_cast<uintptr_t>(W + box * sW + cb) & 15) == 0) && (ldw & 3) == 0));
+    if (vec4) {
+        // 16-byte loads: thread (tr, tq) takes columns 4 tq .. 4 tq + 3 of
+        // rows tr, tr + 32, ...; GU rows per thread in flight (row indices
+        // first, then every load, then the stores)
+        constexpr int GU = 4;
+        const int tid = ty * 32 + tx, tq = tid & 7, tr = tid >> 3;
+        float mx4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int i0 = tr; i0 < gK; i0 += 32 * GU) {
+            int srcr[GU];
+            float4 v[GU], wv[GU];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int i = i0 + 32 * u;
+                srcr[u] = i < nb ? k + (perm ? perm[box * sP + i] : i) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int i = i0 + 32 * u;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                wv[u] = v[u];
+                if (srcr[u] >= 0) {
+                    v[u] = *reinterpret_cast<const float4*>(Mb + (long long)srcr[u] * ldm + c0 + cb + 4 * tq);
+                    if (W) wv[u] = *reinterpret_cast<const float4*>(Mb + (long long)(k + i) * ldm + c0 + cb + 4 * tq);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int i = i0 + 32 * u;
+                if (i >= gK) break;
+                float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                if (srcr[u] >= 0) {
+                    if (W) *reinterpret_cast<float4*>(W + box * sW + (long long)i * ldw + cb + 4 * tq) = wv[u];
+                    const float r = rcb[i];
+#pragma unroll
+                    for (int j2 = 0; j2 < 4; ++j2) {
+                        e[j2] *= r;
+                        mx4[j2] = fmaxf(mx4[j2], fabsf(e[j2]));
+                    }
+                }
+#pragma unroll
+                for (int j2 = 0; j2 < 4; ++j2) gt[i * 33 + 4 * tq + j2] = e[j2];
+            }
+        }
+        // column maxima: the 32 row groups of each column through shared memory
+        __shared__ float cm[32][33];
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) cm[tr][4 * tq + j2] = mx4[j2];
+        __syncthreads();
+        if (ty == 0) {
+            float m = 0.0f;
+            for (int r = 0; r < 32; ++r) m = fmaxf(m, cm[r][tx]);
+            red[0][tx] = m;
+        }
+        if (ty < 8 && ty > 0) red[ty][tx] = 0.0f;
+    } else if (ncc == 32) {
         float mx = 0.0f;
         for (int i = ty; i < gK; i += 8) {
             float v = 0.0f;
@@ -1107,6 +1128,10 @@ __global__ void k_gather_pack_f16(const float* __restrict__ M, long long ldm, lo
 
 // ---------------------------------------------------------------- host side
 
+// Test hook (HPS_OPT_TEST_TC_TIMEOUT): the next product launch that carries
+// box status words stalls on purpose (host-side flag, read on the host only).
+int g_test_stall_next = 0;
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1142,81 +1167,76 @@ bool make_map(CUtensorMap* tm, const void* base, int K, long long rows, long lon
     return r == CUDA_SUCCESS;
 }
 
-// Left operand of an update product: split rows of NB values (K-major), a_rows
-// rows per box; a second part (rows offset by a2_off, K2 further values of K)
-// joins a pair of LU steps into one product.  Pointers and strides are in
-// elements of the plan's operand format.
+// Left operand of an update product: the split K-major packs of up to eight
+// LU steps (a unit), part i with rows[i] rows per box of NB values, K[i] of
+// them used (only the last part may be ragged), its row 0 at row off[i] of
+// the product.  Pointers and strides are in elements of the plan's operand
+// format.
 struct TcLeft {
-    const void* A; long long rows, sA;
-    const void* A2; long long rows2, sA2;
-    int K1, K2, a2_off;
+    int nparts;
+    const void* A[kMaxParts];
+    long long rows[kMaxParts], sA[kMaxParts];
+    int K[kMaxParts], off[kMaxParts];
 };
 
 TcLeft left1(const void* A, long long rows, long long sA, int K)
 {
     TcLeft l{};
-    l.A = A; l.rows = rows; l.sA = sA; l.K1 = K;
+    l.nparts = 1;
+    l.A[0] = A; l.rows[0] = rows; l.sA[0] = sA; l.K[0] = K;
     return l;
 }
 
 template <int FMT, int BNT>
 bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs, bool* fused)
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool* fused)
 {
     using Fm = TcFmt<FMT>;
-    const int K = L.K1 + L.K2;
+    int K = 0;
+    for (int i = 0; i < L.nparts; ++i) K += L.K[i];
     if (args.M <= 0 || args.N <= 0) return true;
-    static int num_sms = 0, max_pairs = 0;
+    static int num_sms = 0;
     if (!num_sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_tc_update<FMT, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
         if (num_sms <= 0) num_sms = 1;
-        // how many CTA pairs fit at once (an SM whose cluster partner is
-        // missing stays idle in pair mode)
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(num_sms & ~1));
-        cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = TC_SMEM;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, (void*)k_tc_update<FMT, BNT>, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            nc = 0;
-        }
-        max_pairs = nc;
     }
     TcArgs a = args;
+    a.wait_ns = WAIT_NS;
+    a.test_stall = 0;
+    if (g_test_stall_next && a.status) {
+        // test hook: this launch's TMA role issues nothing, so its first
+        // wait runs out after 2 ms and the launch ends with HPS_ETIMEOUT
+        g_test_stall_next = 0;
+        a.test_stall = 1;
+        a.wait_ns = 2000000ull;
+    }
     a.kch = (K + Fm::KPC - 1) / Fm::KPC;
-    a.kch1 = L.K2 ? L.K1 / Fm::KPC : a.kch;   // L.K1 is a whole block when a second part follows
-    a.a2_off = L.a2_off;
+    a.nparts = L.nparts;
+    {
+        int ce = 0;
+        for (int i = 0; i < L.nparts; ++i) {   // every part but the last is a whole number of chunks
+            ce += (L.K[i] + Fm::KPC - 1) / Fm::KPC;
+            a.kch_end[i] = ce;
+            a.a_off[i] = L.off[i];
+        }
+    }
     a.tiles_m = (a.M + TC_BM - 1) / TC_BM;
     a.tiles_n = (a.N + BNT - 1) / BNT;
     a.tiles = a.tiles_m * a.tiles_n * nbox;
     a.nbox = nbox;
-    a.cl = (allow_pairs && max_pairs > 0 && a.tiles_m >= 2) ? 1 : 0;
-    a.units_per_box = (a.cl ? (a.tiles_m + 1) / 2 : a.tiles_m) * a.tiles_n;
+    a.units_per_box = a.tiles_m * a.tiles_n;
     a.units = a.units_per_box * nbox;
-    CUtensorMap ta, ta2, tb;
-    if (!make_map<FMT>(&ta, L.A, NB, L.rows, L.rows * NB, L.sA, nbox, TC_BM) ||
-        !make_map<FMT>(&tb, Gp, gK, args.N, g_plane, sGp, nbox, a.cl ? BNT / 2 : BNT))
-        return false;
-    if (L.K2) {
-        if (!make_map<FMT>(&ta2, L.A2, NB, L.rows2, L.rows2 * NB, L.sA2, nbox, TC_BM)) return false;
-    } else {
-        ta2 = ta;
-    }
+    TcMaps maps{};
+    for (int i = 0; i < L.nparts; ++i)
+        if (!make_map<FMT>(&maps.A[i], L.A[i], NB, L.rows[i], L.rows[i] * NB, L.sA[i], nbox, TC_BM)) return false;
+    for (int i = L.nparts; i < kMaxParts; ++i) maps.A[i] = maps.A[0];
+    if (!make_map<FMT>(&maps.B, Gp, gK, args.N, g_plane, sGp, nbox, BNT)) return false;
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) && (a.N % 4 == 0) &&
             (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
-    CUtensorMap to{};
     a.tma_epi = 0;
     if (al16(a.O) && a.ldo % 4 == 0 && a.sO % 4 == 0 && allow_tma) {
         auto fn = encode_fn();
@@ -1224,7 +1244,7 @@ bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long
         cuuint64_t strides[2] = {(cuuint64_t)a.ldo * 4, (cuuint64_t)a.sO * 4};
         cuuint32_t boxd[3] = {32, 32, 1};
         cuuint32_t es[3] = {1, 1, 1};
-        if (fn && fn(&to, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.O, dims, strides, boxd, es,
+        if (fn && fn(&maps.O, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.O, dims, strides, boxd, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             a.tma_epi = 1;
@@ -1238,23 +1258,9 @@ bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long
     // as they converge, so their flop counts are upper bounds.
     const int cls = a.skip ? KC_UPDATE_TC_REFINE : KC_UPDATE_TC;
     prof_begin(cls, st);
-    if (a.cl) {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(2 * std::min(a.units, max_pairs)));
-        cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = TC_SMEM;
-        cfg.stream = st;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k_tc_update<FMT, BNT>, ta, ta2, tb, to, a) != cudaSuccess) return false;
-    } else {
+    {
         dim3 grd((unsigned)std::min(a.units, num_sms));
-        k_tc_update<FMT, BNT><<<grd, TC_THREADS, TC_SMEM, st>>>(ta, ta2, tb, to, a);
+        k_tc_update<FMT, BNT><<<grd, TC_THREADS, TC_SMEM, st>>>(maps, a);
     }
     const double kk = (double)K;
     prof_end(cls, st, 2.0 * nbox * a.M * (double)a.N * kk,
@@ -1264,22 +1270,25 @@ bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long
 
 template <int FMT>
 bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs, bool* fused)
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, int bn_max, bool* fused)
 {
     if (args.N <= TC_BN_NARROW && TcFmt<FMT>::BN > TC_BN_NARROW)
         return launch_tc_update_w<FMT, TC_BN_NARROW>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
-                                                     allow_pairs, fused);
+                                                     fused);
+    if ((args.N <= 2 * TC_BN_NARROW || bn_max <= 2 * TC_BN_NARROW) && TcFmt<FMT>::BN > 2 * TC_BN_NARROW)
+        return launch_tc_update_w<FMT, 2 * TC_BN_NARROW>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
+                                                         fused);
     return launch_tc_update_w<FMT, TcFmt<FMT>::BN>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
-                                                   allow_pairs, fused);
+                                                   fused);
 }
 
 bool launch_tc_update(int fmt, const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool allow_pairs,
+                      const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, int bn_max,
                       bool* fused = nullptr)
 {
-    if (fmt == 2) return launch_tc_update_f<2>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused);
-    return fmt ? launch_tc_update_f<1>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused)
-               : launch_tc_update_f<0>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, allow_pairs, fused);
+    if (fmt == 2) return launch_tc_update_f<2>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, bn_max, fused);
+    return fmt ? launch_tc_update_f<1>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, bn_max, fused)
+               : launch_tc_update_f<0>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma, bn_max, fused);
 }
 
 // Element `off` of a split-operand buffer of format fmt.
@@ -1317,6 +1326,11 @@ void gather_pack_raw(int fmt, const float* M, long long ldm, long long sM, int k
     prof_begin(KC_GATHER, st);
     if (fmt == 2) {
         const dim3 grd((unsigned)((nc + 31) / 32), (unsigned)nbox), blk(32, 8);
+        static bool attr = false;   // a unit of 4 steps holds 512 x 33 floats of K
+        if (!attr) {
+            cudaFuncSetAttribute(k_gather_pack_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
         k_gather_pack_f16<<<grd, blk, (size_t)gK * 33 * sizeof(float), st>>>(
             M, ldm, sM, k, nb, gK, c0, nc, perm, sP, W, ldw, sW, static_cast<__half*>(Gp), plane, sGp, rc, sC, invt,
             sIt, skip);
@@ -1347,6 +1361,9 @@ TcArgs targs(float* O, long long ldo, long long sO, int M, int N, int mode, int 
 
 }  // namespace
 
+void tc_test_stall_next(int on) { g_test_stall_next = on ? 1 : 0; }
+bool tc_test_stall_armed() { return g_test_stall_next != 0; }
+
 void tc_reset_abort(cudaStream_t st)
 {
     void* p = nullptr;
@@ -1362,19 +1379,22 @@ bool tc_abort_raised()
 
 // ---------------------------------------------------------------- LU sequences
 //
-// With step pairs (P.step_pairs), two consecutive LU steps s, s+1 act as one
-// step of 2 NB rows wherever they apply to many columns.  Step s+1 applied to
-// the columns of F_s, and step s applied (backwards) to the columns of
-// B_{s+1}, give the pair's operators:
-//   forward  [F_s' | F_{s+1}] (F_{s+1}'s rows start NB rows lower),
-//   backward [B_s | B_{s+1}'],
-// with the composed row permutation pi_c(i) = pi_s(i) for i < nb_s, else
-// pi_s(nb_s + pi_{s+1}(i - nb_s)).  A row below the pair's block still either
-// stays in place or receives a block row, so the update epilogue is the same
-// with split = 2 NB.  The factorisation updates only the next block's columns
-// with step s (look-ahead), factors that panel, then updates everything else
-// once with the pair; the solves run one product per pair.  Each pass over the
-// trailing rows and right-hand sides then serves two steps.
+// LU steps are joined into units of up to eight (P.unit_max) wherever they
+// apply to many columns.  Two adjacent units A (steps s..) and B (the next
+// ones) become one: B applied forward to the columns of A's F parts, and A
+// applied backward to the columns of B's B parts, give the joined unit's
+// operators
+//   forward  [F_A' | F_B] (each part's rows start at its own step),
+//   backward [B_A | B_B'],
+// with the composed row permutation pi_c(i) = pi_A(i) for i < w_A, else
+// pi_A(w_A + pi_B(i - w_A)) (w_A = A's width).  A row below the unit's block
+// still either stays in place or receives a block row, so the update epilogue
+// is the same with split = the unit's width.  A unit of 2h steps is factored
+// as: its first h steps (recursively), their update of the other h steps'
+// columns, those h steps (recursively), the join; then it updates every
+// later column once, with K = its width.  The solves run one product per
+// unit.  Each pass over the trailing rows and right-hand sides then serves up
+// to eight steps.
 
 namespace {
 
@@ -1418,7 +1438,8 @@ __global__ void k_perm_inverse(const int* __restrict__ perm, int* __restrict__ i
 
 // Start of step s's split F_s / B_s in the operand format of the plan.
 int npl(const Plan& P) { return P.fmt == 1 ? 3 : 2; }
-// Format 2: K scale inverses of F_s and B_s (null otherwise).
+// Format 2: K scales of F_s and B_s (null otherwise); those of consecutive
+// steps are contiguous, so a unit's scales start at its first step's.
 const float* rcf(const Plan& P, const Work<float>& w, int s) { return w.rcF ? w.rcF + (long long)s * P.NB : nullptr; }
 const float* rcb(const Plan& P, const Work<float>& w, int s) { return w.rcB ? w.rcB + (long long)s * P.NB : nullptr; }
 float* rcf_w(const Plan& P, Work<float>& w, int s) { return w.rcF ? w.rcF + (long long)s * P.NB : nullptr; }
@@ -1426,50 +1447,58 @@ float* rcb_w(const Plan& P, Work<float>& w, int s) { return w.rcB ? w.rcB + (lon
 void* fpk(const Plan& P, const Work<float>& w, int s) { return pk_at(w.Fp, (long long)npl(P) * P.fw_off[s], P.fmt); }
 void* bpk(const Plan& P, const Work<float>& w, int s) { return pk_at(w.Bp, (long long)npl(P) * P.bw_off[s], P.fmt); }
 
-// Left operands of the pair (s, s+1).
-TcLeft left_fwd_pair(const Plan& P, const Work<float>& w, int s)
+// Columns (K) of the steps [s, s + len).
+int unit_width(const Plan& P, int s, int len)
+{
+    int wd = 0;
+    for (int i = 0; i < len; ++i) wd += P.nbs[s + i];
+    return wd;
+}
+
+// Left operands of the unit (s, len): forward parts F_{s+i} (rows from step
+// s+i's start), backward parts B_{s+i} (rows from 0).
+TcLeft left_fwd(const Plan& P, const Work<float>& w, int s, int len)
 {
     TcLeft l{};
-    l.A = fpk(P, w, s);
-    l.rows = P.n - P.k0[s];
-    l.sA = w.sFp;
-    l.K1 = P.nbs[s];
-    l.A2 = fpk(P, w, s + 1);
-    l.rows2 = P.n - P.k0[s + 1];
-    l.sA2 = w.sFp;
-    l.K2 = P.nbs[s + 1];
-    l.a2_off = P.nbs[s];
+    l.nparts = len;
+    for (int i = 0; i < len; ++i) {
+        l.A[i] = fpk(P, w, s + i);
+        l.rows[i] = P.n - P.k0[s + i];
+        l.sA[i] = w.sFp;
+        l.K[i] = P.nbs[s + i];
+        l.off[i] = P.k0[s + i] - P.k0[s];
+    }
     return l;
 }
 
-TcLeft left_bwd_pair(const Plan& P, const Work<float>& w, int s)
+TcLeft left_bwd(const Plan& P, const Work<float>& w, int s, int len)
 {
     TcLeft l{};
-    l.A = bpk(P, w, s);
-    l.rows = P.k0[s] + P.nbs[s];
-    l.sA = w.sBp;
-    l.K1 = P.nbs[s];
-    l.A2 = bpk(P, w, s + 1);
-    l.rows2 = P.k0[s + 1] + P.nbs[s + 1];
-    l.sA2 = w.sBp;
-    l.K2 = P.nbs[s + 1];
-    l.a2_off = 0;
+    l.nparts = len;
+    for (int i = 0; i < len; ++i) {
+        l.A[i] = bpk(P, w, s + i);
+        l.rows[i] = P.k0[s + i] + P.nbs[s + i];
+        l.sA[i] = w.sBp;
+        l.K[i] = P.nbs[s + i];
+        l.off[i] = 0;
+    }
     return l;
 }
 
-// Units of the solves: (first step, 1 or 2 steps).
-std::vector<std::pair<int, int>> solve_units(const Plan& P)
+}  // namespace
+
+// Units of the LU: (first step, steps), each a power of two up to P.unit_max.
+std::vector<std::pair<int, int>> lu_units(const Plan& P)
 {
     std::vector<std::pair<int, int>> u;
     for (int s = 0; s < P.nsteps;) {
-        const int len = (P.step_pairs && s + 1 < P.nsteps) ? 2 : 1;
+        int len = 1;
+        while (2 * len <= P.unit_max && s + 2 * len <= P.nsteps) len *= 2;
         u.emplace_back(s, len);
         s += len;
     }
     return u;
 }
-
-}  // namespace
 
 bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStream_t st)
 {
@@ -1478,9 +1507,11 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
     auto up = [&](const TcLeft& L, TcArgs a) {
         a.invt = w.it1;
         a.sInvt = w.sIT;
-        return launch_tc_update(P.fmt, L, w.Gp, gplane, w.sGp, KG, NB, a, nbox, st, P.tma_epi, P.tc_pairs);
+        return launch_tc_update(P.fmt, L, w.Gp, gplane, w.sGp, KG, NB, a, nbox, st, P.tma_epi, P.bn_max);
     };
-    // Panel of step s, its operators F_s and B_s (FP32 and split copies).
+    // Panel of step s, its operators F_s and B_s (FP32 and split copies; B_s's
+    // split only when pack_b: a B part that a join rewrites before any
+    // product reads it is split after that join).
     auto panel_ops = [&](int s, bool pack_b) -> bool {
         const int k = P.k0[s], nb = P.nbs[s];
         float* Fs = w.F + P.fw_off[s];
@@ -1514,70 +1545,70 @@ bool tc_lu_factor(const Plan& P, Work<float>& w, int nbox, int* status, cudaStre
             launch_pack_split(P.fmt, Bs, NB, w.sB, k + nb, NB, nb, bpk(P, w, s), w.sBp, nbox, st, rcb_w(P, w, s), w.sRC);
         return true;
     };
-    // Step s's update of M's columns [c0, c0 + nc).
-    auto update1 = [&](int s, int c0, int nc) -> bool {
+    // The unit (s, len) applied to M's columns [c0, c0 + nc).
+    auto update = [&](int s, int len, int c0, int nc) -> bool {
         if (nc <= 0) return true;
-        const int k = P.k0[s], nb = P.nbs[s];
+        const int k = P.k0[s], wp = unit_width(P, s, len);
         int* Ps = w.perm + P.perm_off[s];
-        launch_gather_pack(P, w, k, nb, c0, nc, Ps, true, nullptr, nbox, st, rcf(P, w, s));
-        TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, nb);
+        launch_gather_pack(P, w, k, wp, c0, nc, Ps, true, nullptr, nbox, st, rcf(P, w, s));
+        TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
         a.perm = Ps; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
-        return up(left1(fpk(P, w, s), n - k, w.sFp, nb), a);
+        return up(left_fwd(P, w, s, len), a);
     };
-    // The pair's operators and permutation from those of its two steps.
-    auto combine = [&](int s) -> bool {
-        const int k = P.k0[s], nb0 = P.nbs[s], k1 = P.k0[s + 1], nb1 = P.nbs[s + 1];
-        float* F0 = w.F + P.fw_off[s];
-        float* B1 = w.B + P.bw_off[s + 1];
-        int* P0 = w.perm + P.perm_off[s];
-        const int* P1 = w.perm + P.perm_off[s + 1];
-        {   // F_s' = forward step s+1 on F_s's rows [nb0, n - k)
-            gather_pack_raw(P.fmt, F0, NB, w.sF, nb0, nb1, KG, 0, nb0, P1, w.sP, w.W, NB, w.sG, w.Gp, gplane, w.sGp, nullptr,
-                            nbox, st, rcf(P, w, s + 1), w.sRC, w.it1, w.sIT);
-            TcArgs a = targs(F0 + (long long)nb0 * NB, NB, w.sF, n - k1, nb0, GM_FWD, nb1);
-            a.perm = P1; a.sP = w.sP; a.W = w.W; a.ldw = NB; a.sW = w.sG; a.status = status;
-            if (!up(left1(fpk(P, w, s + 1), n - k1, w.sFp, nb1), a)) return false;
-            launch_pack_split(P.fmt, F0, NB, w.sF, n - k, NB, nb0, fpk(P, w, s), w.sFp, nbox, st, rcf_w(P, w, s),
-                              w.sRC);
+    // Join the units A = (s, h) and B = (s + h, h) into (s, 2 h).
+    auto join = [&](int s, int h) -> bool {
+        const int kA = P.k0[s], kB = P.k0[s + h], wA = unit_width(P, s, h), wB = unit_width(P, s + h, h);
+        int* PA = w.perm + P.perm_off[s];
+        const int* PB = w.perm + P.perm_off[s + h];
+        for (int i = 0; i < h; ++i) {   // F_{s+i}' = B forward on F_{s+i}'s rows from B's start
+            const int t = s + i, off = kB - P.k0[t];
+            float* Ft = w.F + P.fw_off[t];
+            gather_pack_raw(P.fmt, Ft, NB, w.sF, off, wB, KG, 0, P.nbs[t], PB, w.sP, w.W, NB, w.sG, w.Gp, gplane,
+                            w.sGp, nullptr, nbox, st, rcf(P, w, s + h), w.sRC, w.it1, w.sIT);
+            TcArgs a = targs(Ft + (long long)off * NB, NB, w.sF, n - kB, P.nbs[t], GM_FWD, wB);
+            a.perm = PB; a.sP = w.sP; a.W = w.W; a.ldw = NB; a.sW = w.sG; a.status = status;
+            if (!up(left_fwd(P, w, s + h, h), a)) return false;
+            launch_pack_split(P.fmt, Ft, NB, w.sF, n - P.k0[t], NB, P.nbs[t], fpk(P, w, t), w.sFp, nbox, st,
+                              rcf_w(P, w, t), w.sRC);
         }
-        {   // B_{s+1}' = backward step s on B_{s+1}'s rows [0, k + nb0)
-            gather_pack_raw(P.fmt, B1, NB, w.sB, k, nb0, KG, 0, nb1, nullptr, 0, nullptr, 0, 0, w.Gp, gplane, w.sGp,
-                            nullptr, nbox, st, rcb(P, w, s), w.sRC, w.it1, w.sIT);
-            TcArgs a = targs(B1, NB, w.sB, k + nb0, nb1, GM_BWD, k);
+        for (int i = 0; i < h; ++i) {   // B_{s+h+i}' = A backward on B_{s+h+i}'s rows up to A's end
+            const int t = s + h + i;
+            float* Bt = w.B + P.bw_off[t];
+            gather_pack_raw(P.fmt, Bt, NB, w.sB, kA, wA, KG, 0, P.nbs[t], nullptr, 0, nullptr, 0, 0, w.Gp, gplane,
+                            w.sGp, nullptr, nbox, st, rcb(P, w, s), w.sRC, w.it1, w.sIT);
+            TcArgs a = targs(Bt, NB, w.sB, kA + wA, P.nbs[t], GM_BWD, kA);
             a.status = status;
-            if (!up(left1(bpk(P, w, s), k + nb0, w.sBp, nb0), a)) return false;
-            launch_pack_split(P.fmt, B1, NB, w.sB, k1 + nb1, NB, nb1, bpk(P, w, s + 1), w.sBp, nbox, st,
-                              rcb_w(P, w, s + 1), w.sRC);
+            if (!up(left_bwd(P, w, s, h), a)) return false;
+            launch_pack_split(P.fmt, Bt, NB, w.sB, P.k0[t] + P.nbs[t], NB, P.nbs[t], bpk(P, w, t), w.sBp, nbox, st,
+                              rcb_w(P, w, t), w.sRC);
         }
-        launch_perm_compose(P0, P1, w.sP, n - k, nb0, nbox, st);
+        launch_perm_compose(PA, PB, w.sP, n - kA, wA, nbox, st);
         return true;
     };
-    for (const auto& u : solve_units(P)) {
-        const int s = u.first, k = P.k0[s];
-        if (u.second == 1) {
-            if (!panel_ops(s, true)) return false;
-            if (!update1(s, k + P.nbs[s], n + P.r - k - P.nbs[s])) return false;
-            continue;
-        }
-        const int nb0 = P.nbs[s], wp = nb0 + P.nbs[s + 1];
-        if (!panel_ops(s, true)) return false;
-        if (!update1(s, k + nb0, P.nbs[s + 1])) return false;   // look-ahead: the next panel's columns
-        if (!panel_ops(s + 1, false)) return false;             // B_{s+1} is split once combined
-        if (!combine(s)) return false;
-        const int c0 = k + wp, nc = n + P.r - c0;
-        if (nc > 0) {
-            int* Pc = w.perm + P.perm_off[s];
-            launch_gather_pack(P, w, k, wp, c0, nc, Pc, true, nullptr, nbox, st, rcf(P, w, s));
-            TcArgs a = targs(w.M + (long long)k * ldm + c0, ldm, w.sM, n - k, nc, GM_FWD, wp);
-            a.perm = Pc; a.sP = w.sP; a.W = w.W; a.ldw = ldm; a.sW = w.sG; a.status = status;
-            if (!up(left_fwd_pair(P, w, s), a)) return false;
-        }
+    // Factor the unit (s, len) whose columns are up to date with every earlier
+    // unit; a B part is split at its panel only if it is the first step of a
+    // pair (the join of that pair reads it; every other B part is rewritten
+    // and split by a join first).
+    std::function<bool(int, int, int)> factor_unit = [&](int s, int len, int top) -> bool {
+        if (len == 1) return panel_ops(s, ((s - top) & 1) == 0);
+        const int h = len / 2;
+        if (!factor_unit(s, h, top)) return false;
+        const int c0 = P.k0[s + h];
+        if (!update(s, h, c0, unit_width(P, s + h, h))) return false;   // look-ahead on the second half's panels
+        if (!factor_unit(s + h, h, top)) return false;
+        return join(s, h);
+    };
+    for (const auto& u : lu_units(P)) {
+        const int s = u.first, len = u.second;
+        if (!factor_unit(s, len, s)) return false;
+        const int c0 = P.k0[s] + unit_width(P, s, len);
+        if (!update(s, len, c0, n + P.r - c0)) return false;
     }
-    // Inverse permutations of the solve units, for gathers fused into the
-    // forward solves.
+    // Inverse permutations of the units, for gathers fused into the forward
+    // solves.
     if (P.fuse_fwd)
-        for (const auto& u : solve_units(P)) {
-            const int s = u.first, wp = u.second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s];
+        for (const auto& u : lu_units(P)) {
+            const int s = u.first, wp = unit_width(P, s, u.second);
             prof_begin(KC_MISC, st);
             k_perm_inverse<<<nbox, 256, 0, st>>>(w.perm + P.perm_off[s], w.inv + P.perm_off[s], w.sP, n - P.k0[s],
                                                  wp);
@@ -1601,8 +1632,8 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
     void* Gb[2] = {w.Gp, w.Gp2};
     float* Wb[2] = {w.W, w.W2};
     float* Ib[2] = {w.it1, w.it2};
-    const auto units = solve_units(P);
-    auto width = [&](size_t u) { const int s = units[u].first; return units[u].second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s]; };
+    const auto units = lu_units(P);
+    auto width = [&](size_t u) { return unit_width(P, units[u].first, units[u].second); };
     bool have = false;   // the current unit's G and W are in buffer cur
     for (size_t u = 0; u < units.size(); ++u) {
         const int s = units[u].first, k = P.k0[s], wp = width(u), cur = (int)(u & 1);
@@ -1623,8 +1654,8 @@ bool tc_lu_forward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, cons
             a.ninv = w.inv + P.perm_off[s1]; a.nsInv = w.sP; a.ng_off = wp; a.ng_len = n - P.k0[s1];
             a.nW = Wb[cur ^ 1]; a.nsW = w.sG; a.nldw = ldm; a.nw_off = wp; a.nw_len = width(u + 1);
         }
-        const TcLeft L = units[u].second == 2 ? left_fwd_pair(P, w, s) : left1(fpk(P, w, s), n - k, w.sFp, wp);
-        if (!launch_tc_update(P.fmt, L, Gb[cur], gplane, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs, &have))
+        if (!launch_tc_update(P.fmt, left_fwd(P, w, s, units[u].second), Gb[cur], gplane, w.sGp, P.KG, P.NB, a, nbox,
+                              st, P.tma_epi, P.bn_max, &have))
             return false;
     }
     return true;
@@ -1635,8 +1666,8 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
     const long long ldm = P.ldm, gplane = ldm * P.KG;
     void* Gb[2] = {w.Gp, w.Gp2};
     float* Ib[2] = {w.it1, w.it2};
-    const auto units = solve_units(P);
-    auto width = [&](size_t u) { const int s = units[u].first; return units[u].second == 2 ? P.nbs[s] + P.nbs[s + 1] : P.nbs[s]; };
+    const auto units = lu_units(P);
+    auto width = [&](size_t u) { return unit_width(P, units[u].first, units[u].second); };
     bool have = false;
     int cur = 0;
     for (size_t q = units.size(); q-- > 0; cur ^= 1) {
@@ -1652,8 +1683,8 @@ bool tc_lu_backward(const Plan& P, Work<float>& w, int nbox, int c0, int nc, con
             a.nG = Gb[cur ^ 1]; a.ng_plane = gplane; a.nsG = w.sGp; a.ngK = P.KG;
             a.ninv = nullptr; a.ng_off = k - wq; a.ng_len = wq;
         }
-        const TcLeft L = units[q].second == 2 ? left_bwd_pair(P, w, s) : left1(bpk(P, w, s), k + wp, w.sBp, wp);
-        if (!launch_tc_update(P.fmt, L, Gb[cur], gplane, w.sGp, P.KG, P.NB, a, nbox, st, P.tma_epi, P.tc_pairs, &have))
+        if (!launch_tc_update(P.fmt, left_bwd(P, w, s, units[q].second), Gb[cur], gplane, w.sGp, P.KG, P.NB, a, nbox,
+                              st, P.tma_epi, P.bn_max, &have))
             return false;
     }
     return true;

@@ -36,3 +36,13 @@ def rel_fro(a, b):
     b = np.asarray(b)
     ax = tuple(range(1, a.ndim))
     return np.sqrt(((a - b) ** 2).sum(axis=ax)) / np.sqrt((b ** 2).sum(axis=ax))
+
+
+def max_rel(a, b):
+    """Largest per-box element-wise error relative to the box's largest entry,
+    max |a - b| / max |b| over the last axes: it catches a single wrong entry
+    that the Frobenius norm would average away."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    ax = tuple(range(1, a.ndim))
+    return float((np.abs(a - b).max(axis=ax) / np.abs(b).max(axis=ax)).max())

@@ -13,7 +13,7 @@ import hps_inputs as hi
 import oracle
 import paper_2503_04033_gb300 as H
 from oracle import global_solve as gs
-from tests._cases import box_b, rel_fro
+from tests._cases import box_b, max_rel, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -89,12 +89,17 @@ def test_dtn_particular_reconstruct_with_first_order_term(ctx, prec, fp16, tol, 
         To, So, info = oracle.leaf_dtn(p, h, kappa, field(xyz), beta=bt[bx])
         assert info == 0
         assert rel_fro(T[bx:bx + 1].cpu().numpy(), To[None]).max() < tol
+        assert max_rel(T[bx:bx + 1].cpu().numpy(), To[None]) < tol
         assert rel_fro(S[bx:bx + 1].cpu().numpy(), So[None]).max() < tol
+        assert max_rel(S[bx:bx + 1].cpu().numpy(), So[None]) < tol
         vo, ho, _ = oracle.leaf_particular(p, h, kappa, field(xyz), hi.load_values(loads, xyz), beta=bt[bx])
         assert rel_fro(v[bx:bx + 1].cpu().numpy(), vo[None]).max() < tol
+        assert max_rel(v[bx:bx + 1].cpu().numpy(), vo[None]) < tol
         assert rel_fro(hf[bx:bx + 1].cpu().numpy(), ho[None]).max() < tol
+        assert max_rel(hf[bx:bx + 1].cpu().numpy(), ho[None]) < tol
         uo, _ = oracle.leaf_reconstruct(p, h, kappa, field(xyz), v0[bx], ub[bx], beta=bt[bx])
         assert rel_fro(ui[bx:bx + 1].cpu().numpy(), uo[None]).max() < tol
+        assert max_rel(ui[bx:bx + 1].cpu().numpy(), uo[None]) < tol
 
 
 @pytest.mark.parametrize("prec,tol", [(H.HPS_FP64, 1e-11), (H.HPS_FP32_IR, 1e-10)], ids=["fp64", "fp32ir"])
@@ -121,7 +126,9 @@ def test_factored_and_apply_with_first_order_term(ctx, prec, tol):
         for bx in range(nbox):
             vo, ho, _ = oracle.leaf_particular(p, h, kappa, bv[bx], fg[bx], beta=bt[bx])
             assert rel_fro(v[bx:bx + 1].cpu().numpy(), vo[None]).max() < tol
+            assert max_rel(v[bx:bx + 1].cpu().numpy(), vo[None]) < tol
             assert rel_fro(hf[bx:bx + 1].cpu().numpy(), ho[None]).max() < tol
+            assert max_rel(hf[bx:bx + 1].cpu().numpy(), ho[None]) < tol
     finally:
         H.hps_leaf_factors_destroy(F)
     u = np.random.default_rng(8).standard_normal((nbox, 2, p ** 3))

@@ -11,7 +11,7 @@ import pytest
 import hps_inputs as hi
 import oracle
 import paper_2503_04033_gb300 as H
-from tests._cases import box_b, rel_fro
+from tests._cases import box_b, max_rel, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +68,9 @@ def test_factor_once_solve_many(ctx, prec, fp16, tol, p):
                 vo, ho, info = oracle.leaf_particular(p, h, kappa, bvals[bx], hi.load_values(loads, xyz))
                 assert info == 0
                 assert rel_fro(v[bx:bx + 1].cpu().numpy(), vo[None]).max() < tol
+                assert max_rel(v[bx:bx + 1].cpu().numpy(), vo[None]) < tol
                 assert rel_fro(hf[bx:bx + 1].cpu().numpy(), ho[None]).max() < tol
+                assert max_rel(hf[bx:bx + 1].cpu().numpy(), ho[None]) < tol
         nr = 2
         ub_np = hi.random_boundary_data(nbox, nr, m)
         v_np = np.random.default_rng(5).standard_normal((nbox, nr, n))
@@ -81,6 +83,7 @@ def test_factor_once_solve_many(ctx, prec, fp16, tol, p):
             uo, info = oracle.leaf_reconstruct(p, h, kappa, bvals[bx], v_np[bx], ub_np[bx])
             assert info == 0
             assert rel_fro(ui[bx:bx + 1].cpu().numpy(), uo[None]).max() < tol
+            assert max_rel(ui[bx:bx + 1].cpu().numpy(), uo[None]) < tol
     finally:
         H.hps_leaf_factors_destroy(F)
         H.hps_set_option(ctx, H.HPS_OPT_FP16_OPERANDS, 1)
@@ -106,7 +109,9 @@ def test_factored_matches_one_shot_particular(ctx):
         H.hps_leaf_solve_factored(F, nrhs, f, v2, h2)
         torch.cuda.synchronize()
         assert rel_fro(v1.cpu().numpy(), v2.cpu().numpy()).max() < 1e-11
+        assert max_rel(v1.cpu().numpy(), v2.cpu().numpy()) < 1e-11
         assert rel_fro(h1.cpu().numpy(), h2.cpu().numpy()).max() < 1e-11
+        assert max_rel(h1.cpu().numpy(), h2.cpu().numpy()) < 1e-11
     finally:
         H.hps_leaf_factors_destroy(F)
 
