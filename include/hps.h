@@ -478,6 +478,48 @@ hps_status hps_leaf2d_solve(int p, const double h[2], double kappa, int nbox, co
 hps_status hps_leaf2d_reconstruct(int p, int nbox, int nrhs, const double* S, const double* v, const double* ub,
                                   double* ui, void* stream);
 
+/* Operators with cross terms on Legendre face grids (Remark 1 of Sec. 2.1;
+ * Sec. 4.3's curved domains need them).  The operator is
+ *   A u = -sum_{a,b} C_ab(x) d_a d_b u + sum_a d_a(x) d_a u - kappa^2 b(x) u
+ * with a symmetric coefficient tensor C.  Cross terms couple interior nodes
+ * to edge and corner nodes, so the face data lives on a (p-1) x (p-1) tensor
+ * grid of Gauss-Legendre nodes per face instead of the (p-2) x (p-2)
+ * Chebyshev face nodes: m = 6 (p-1)^2 Legendre face nodes, n = (p-2)^3
+ * interior nodes, p in 4..16.  Boundary Chebyshev nodes take their values
+ * from the faces' Legendre data by polynomial interpolation (degree p-2 per
+ * face coordinate); a node on several faces (edges, corners) takes the
+ * average over them.  Neumann data are the outward normal derivatives at
+ * each face's p x p Chebyshev nodes interpolated (degree p-1) to its Legendre
+ * nodes.  Layouts (row-major, boxes outermost, device memory):
+ *   grid node (i,j,k)                              index i + p j + p^2 k
+ *   interior node (i,j,k), 1 <= i,j,k <= p-2       index (i-1) + q (j-1) + q^2 (k-1)
+ *   Legendre node (s,t) of face f (x-, x+, y-, y+, z-, z+; s along the
+ *   face's lower free axis)                        index f (p-1)^2 + s + (p-1) t
+ *   C [nbox][6][p^3] (C11, C22, C33, C12, C13, C23 at every grid node)
+ *   d [nbox][3][p^3] or NULL   b [nbox][p^3]   f [nbox][nrhs][p^3]
+ *   T [nbox][m][m]   S [nbox][n][m]   v [nbox][nrhs][n]   h [nbox][nrhs][m]
+ *
+ * hps_leaf_cross_sizes: n and m of order p.
+ * hps_leaf_cross_nodes: coordinates xyz [m][3] (host) of the Legendre face
+ * nodes of the box [lo, lo + h].
+ * hps_leaf_cross_solve (FP64): one LU with partial pivoting of A_II per box
+ * carrying [-A_IE P | f_I] gives S = -A_II^{-1} A_IE P (P: Legendre data to
+ * boundary Chebyshev values), T = Q N [S; P] (the DtN map on the Legendre
+ * grids) and, for nrhs (0..256) loads, v = A_II^{-1} f_I and h = Q N [v; 0]
+ * (Sec. 2.2 and Algorithms 1 and 2 with these index sets).  T, S: either may
+ * be NULL (not both when nrhs = 0).  box_status as for the other leaf calls.
+ * Workspace from the stream-ordered allocator, released on the stream;
+ * HPS_EINVAL for bad arguments, HPS_ENOMEM when it cannot be allocated.
+ * hps_leaf_cross_reconstruct: u_i = v + S u_b with S from hps_leaf_cross_solve
+ * (v may be NULL), u_b [nbox][nrhs][m] on the Legendre grids. */
+hps_status hps_leaf_cross_sizes(int p, int* n, int* m);
+hps_status hps_leaf_cross_nodes(int p, const double lo[3], const double h[3], double* xyz);
+hps_status hps_leaf_cross_solve(int p, const double h[3], double kappa, int nbox, const double* C, const double* d,
+                                const double* b, int nrhs, const double* f, double* T, double* S, double* v,
+                                double* hflux, int* box_status, void* stream);
+hps_status hps_leaf_cross_reconstruct(int p, int nbox, int nrhs, const double* S, const double* v, const double* ub,
+                                      double* ui, void* stream);
+
 /* The collocation operator applied to full nodal fields: out = A u at every
  * interior node of each box, the interior rows of Eq. 2 (-Laplacian by the
  * three grid lines through the node, minus kappa^2 b u), and 0 at the face,

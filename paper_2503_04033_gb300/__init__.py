@@ -29,7 +29,8 @@ __all__ = [
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
-    "hps_leaf2d_sizes", "hps_interface2d_factor", "hps_interface2d_plan",
+    "hps_leaf2d_sizes", "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes",
+    "hps_leaf_cross_nodes", "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -50,7 +51,8 @@ EXPORTED_SYMBOLS = (
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
-    "hps_interface2d_factor", "hps_interface2d_plan",
+    "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes", "hps_leaf_cross_nodes",
+    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct",
 )
 
 # Kernel classes of hps_profile_get.
@@ -130,6 +132,10 @@ def load_library() -> ctypes.CDLL:
         "hps_interface2d_factor": (i, [vp, i, ip, vp, i, i, vp, ctypes.POINTER(vp)]),
         "hps_interface2d_plan": (i, [i, ip, ip, ip, ip, ip]),
         "hps_leaf2d_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
+        "hps_leaf_cross_sizes": (i, [i, ip, ip]),
+        "hps_leaf_cross_nodes": (i, [i, dp, dp, dp]),
+        "hps_leaf_cross_solve": (i, [i, dp, d, i, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp]),
+        "hps_leaf_cross_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
         "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
         "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
         "hps_interface_destroy": (None, [vp]),
@@ -427,6 +433,46 @@ def hps_leaf2d_reconstruct(p: int, nbox: int, nrhs: int, S, v, ub, ui, stream=No
     _check(load_library().hps_leaf2d_reconstruct(int(p), int(nbox), int(nrhs), _ptr(S, f64), _ptr(v, f64),
                                                  _ptr(ub, f64), _ptr(ui, f64), _stream(stream)),
            "hps_leaf2d_reconstruct")
+
+
+def hps_leaf_cross_sizes(p: int):
+    """(n, m) = ((p-2)^3, 6 (p-1)^2) of a box with Legendre face grids."""
+    n, m = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().hps_leaf_cross_sizes(int(p), ctypes.byref(n), ctypes.byref(m)), "hps_leaf_cross_sizes")
+    return n.value, m.value
+
+
+def hps_leaf_cross_nodes(p: int, lo, h) -> np.ndarray:
+    """[m, 3] coordinates of the box's Legendre face nodes."""
+    import numpy as np
+    _, m = hps_leaf_cross_sizes(p)
+    lo3 = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.float64), (3,)))
+    h3 = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (3,)))
+    out = np.empty((m, 3))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load_library().hps_leaf_cross_nodes(int(p), lo3.ctypes.data_as(dp), h3.ctypes.data_as(dp),
+                                               out.ctypes.data_as(dp)), "hps_leaf_cross_nodes")
+    return out
+
+
+def hps_leaf_cross_solve(p: int, h, kappa: float, nbox: int, C, d, b, nrhs: int = 0, f=None, T=None, S=None,
+                         v=None, hflux=None, box_status=None, stream=None) -> None:
+    """Cross-term leaves: T, S, and for nrhs loads v, h (device tensors, see hps.h)."""
+    f64 = _f64() if not isinstance(b, int) else None
+    h3 = [float(x) for x in h] if hasattr(h, "__len__") else [float(h)] * 3
+    hh = (ctypes.c_double * 3)(*h3)
+    _check(load_library().hps_leaf_cross_solve(
+        int(p), hh, float(kappa), int(nbox), _ptr(C, f64), _ptr(d, f64), _ptr(b, f64), int(nrhs), _ptr(f, f64),
+        _ptr(T, f64), _ptr(S, f64), _ptr(v, f64), _ptr(hflux, f64),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_cross_solve")
+
+
+def hps_leaf_cross_reconstruct(p: int, nbox: int, nrhs: int, S, v, ub, ui, stream=None) -> None:
+    f64 = _f64() if not isinstance(S, int) else None
+    _check(load_library().hps_leaf_cross_reconstruct(int(p), int(nbox), int(nrhs), _ptr(S, f64), _ptr(v, f64),
+                                                     _ptr(ub, f64), _ptr(ui, f64), _stream(stream)),
+           "hps_leaf_cross_reconstruct")
 
 
 def hps_last_refinement(ctx, nbox: int):
