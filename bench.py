@@ -78,7 +78,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12
 # traffic grows with the boxes).  None when not captured for the current
 # kernel: every change to the product kernel resets it to None until it is
 # captured again.
-NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): None, ("update_tcgen05", "3 x TF32"): None}
+NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): 2.2476e9, ("update_tcgen05", "3 x TF32"): None}
 
 
 def dtype_label(prec, opts):
@@ -106,6 +106,7 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-alt", action="store_true", help="skip timing the other mixed precision")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement in the headline run")
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
                     help="hps_set_option before timing, e.g. LU_UNIT=2 (name without HPS_OPT_)")
     ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep", "dirichlet",
@@ -401,7 +402,7 @@ def run_ours(args):
         "clocks": clocks.summary(),
     }
 
-    # ---- roofline of the dominant contraction (SURVEY 8(d): the mixed path is
+    # ---- roofline of the dominant contraction (the mixed path is
     # tensor-bound).  The tensor-core update products do the method's LU and
     # triangular solves: their algorithmic work is 2/3 n^3 + 2 n^2 m per box,
     # counted once (the split operand formats issue several MMAs per product),
@@ -449,8 +450,8 @@ def run_ours(args):
         }
     line["roofline_step"] = {
         "achieved": line["tflops"], "peak": tpeak, "unit": "TFLOP/s", "frac": line["tflops"] / tpeak,
-        "definition": "2/3 n^3 + 2 n^2 m + 2 q m^2 per box x boxes / ms_per_step (SURVEY 8(d)), against the "
-                      "same tensor peak",
+        "definition": "2/3 n^3 + 2 n^2 m + 2 q m^2 per box x boxes / ms_per_step (LU of A_ii, the solves for "
+                      "S and the product A_bi S), against the same tensor peak",
         "algorithmic_bytes_per_box": 8.0 * P ** 3 + 8.0 * m_ * m_,
         "hbm_frac": nbox * (8.0 * P ** 3 + 8.0 * m_ * m_) / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
@@ -637,6 +638,15 @@ def run_ours(args):
                                      "i+1's solve"}
         del T_host, b_host, b_dev, T_dev
 
+    # ---- the uneven batch (mixed p, kappa per box, 32 loads), timed after the
+    # headline on the same GPU, with its own schedule tuning
+    if not args.no_uneven and world == 1:
+        import tempfile as _tf
+        tune_dir = _tf.mkdtemp()
+        os.environ["HPS_TUNE_CACHE"] = os.path.join(tune_dir, "tune.txt")
+        line["uneven_batch"] = uneven_measurement(3, 2, dev)
+        del os.environ["HPS_TUNE_CACHE"]
+
     # ---- the oracle on this host's cores (rank 0 at N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu and args.cpu_sample > 0:
         rate, dt, cores = oracle_rate(args.cpu_sample)
@@ -763,11 +773,19 @@ def load_field_torch(loads, xyz, dev):
 
 
 def run_uneven(args):
-    """The uneven batch: per p, one group; graphs and block autotuning on."""
+    """The uneven batch as its own JSON line."""
     import torch
-    import paper_2503_04033_gb300 as H
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    print(json.dumps(uneven_measurement(args.steps, args.warmup, dev)), flush=True)
+
+
+def uneven_measurement(steps: int, warmup: int, dev) -> dict:
+    """The uneven batch (1024 boxes, p from {8, 12, 16, 20}, kappa from
+    {10, 20, 40, 60}, 32 loads per box): per p, one group; graphs and the
+    schedule autotuner on."""
+    import torch
+    import paper_2503_04033_gb300 as H
     d = hi.uneven_batch(nbox=1024, nloads=32)
     h = d["h"]
     groups, flops = [], 0.0
@@ -789,18 +807,18 @@ def run_uneven(args):
     H.hps_set_option(ctx, H.HPS_OPT_AUTOTUNE, 1)
     H.hps_set_option(ctx, H.HPS_OPT_GRAPHS, 1)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         H.hps_leaf_groups(ctx, groups, H.HPS_FP32_IR, stream)
     torch.cuda.synchronize(dev)
     fails = sum(int((g["box_status"] != 0).sum().item()) for g in groups)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clocks:
+    with ClockSampler(dev.index or 0) as clocks:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             H.hps_leaf_groups(ctx, groups, H.HPS_FP32_IR, stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     # one more call, outside the timed region, with per-kernel events (graphs off)
     H.hps_set_option(ctx, H.HPS_OPT_GRAPHS, 0)
     H.hps_profile_enable(ctx, True)
@@ -814,15 +832,24 @@ def run_uneven(args):
         if nl:
             prof[name] = {"launches": nl, "ms": kms}
     H.hps_destroy(ctx)
-    line = {"metric": "uneven leaf batch: boxes/s (DtN + 32 particular solutions per box, mixed p)",
-            "value": 1024 / (ms / 1e3), "unit": "boxes/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    tuned = {}
+    cache = os.environ.get("HPS_TUNE_CACHE")
+    if cache and os.path.exists(cache):
+        with open(cache) as fh:
+            for ln in fh:
+                v = ln.split()
+                if len(v) == 6:
+                    tuned[f"p{v[0]}"] = {"nb": int(v[3]), "unit": int(v[4]), "tile": int(v[5])}
+    del groups
+    torch.cuda.empty_cache()
+    return {"metric": "uneven leaf batch: boxes/s (DtN + 32 particular solutions per box, mixed p)",
+            "value": 1024 / (ms / 1e3), "unit": "boxes/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
+            "dtype": dtype_label(H.HPS_FP32_IR, {}), "data": "synthetic",
             "config": {"workload": UNEVEN, "boxes_per_p": {str(p): int((d["p"] == p).sum()) for p in (8, 12, 16, 20)},
                        "graphs": True, "autotune": True},
             "tflops": flops / (ms / 1e3) / 1e12, "box_failures": fails, "clocks": clocks.summary(),
-            "kernels_one_call": prof}
-    print(json.dumps(line), flush=True)
+            "tuned_schedule": tuned, "kernels_one_call": prof}
 
 
 def run_factored(args):

@@ -74,13 +74,21 @@ template <>
 struct TcFmt<2> {
     static constexpr int NPL = 2, EB = 2, KPC = 32, BN = 256;
 };
+// FMT 3: plain BF16 operands, one plane, one kind::f16 product per K step
+// (the learned correction's network: BF16 weights and activations, FP32
+// accumulation).
+template <>
+struct TcFmt<3> {
+    static constexpr int NPL = 1, EB = 2, KPC = 32, BN = 256;
+};
 template <int FMT>
 __host__ __device__ constexpr uint32_t b_tile() { return (uint32_t)TcFmt<FMT>::BN * ROWB; }
 template <int FMT>
 __host__ __device__ constexpr uint32_t stage_bytes() { return (uint32_t)TcFmt<FMT>::NPL * (A_TILE + b_tile<FMT>()); }
 constexpr uint32_t STAGE_BYTES = 48 * 1024;
 constexpr int TC_BN_NARROW = 64;                            // tile width for products of at most 64 columns
-static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES && stage_bytes<2>() == STAGE_BYTES,
+static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES && stage_bytes<2>() == STAGE_BYTES &&
+                  stage_bytes<3>() <= STAGE_BYTES,
               "one shared-memory layout");
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
 constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
@@ -373,6 +381,8 @@ __device__ __forceinline__ void split_store(void* dst, long long idx, long long 
         const float hi = to_tf32(x);
         d[idx] = hi;
         d[plane + idx] = to_tf32(x - hi);
+    } else if constexpr (FMT == 3) {
+        static_cast<__nv_bfloat16*>(dst)[idx] = __float2bfloat16_rn(x);
     } else if constexpr (FMT == 2) {
         __half* d = static_cast<__half*>(dst);
         const __half h = __float2half_rn(x);
@@ -516,7 +526,7 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc =
-                FMT == 0 ? tf32_idesc(TC_BM, BN) : (FMT == 1 ? bf16_idesc(TC_BM, BN) : f16_idesc(TC_BM, BN));
+                FMT == 0 ? tf32_idesc(TC_BM, BN) : ((FMT == 1 || FMT == 3) ? bf16_idesc(TC_BM, BN) : f16_idesc(TC_BM, BN));
             uint32_t g = 0, j = 0;
             bool ok = true;
             for (int u = sc.u0; u < sc.units && ok; u += sc.ustep) {
@@ -553,6 +563,8 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
                             mma_tf32(d, ad[0] + o, bd[0] + o, idesc, acc0);
                             mma_tf32(d, ad[0] + o, bd[1] + o, idesc, 1);
                             mma_tf32(d, ad[1] + o, bd[0] + o, idesc, 1);
+                        } else if constexpr (FMT == 3) {
+                            mma_bf16(d, ad[0] + o, bd[0] + o, idesc, acc0);
                         } else if constexpr (FMT == 2) {
                             mma_bf16(d, ad[1] + o, bd[0] + o, idesc, acc0);
                             mma_bf16(d, ad[0] + o, bd[1] + o, idesc, 1);
@@ -1160,7 +1172,8 @@ bool make_map(CUtensorMap* tm, const void* base, int K, long long rows, long lon
     cuuint32_t boxd[4] = {(cuuint32_t)Fm::KPC, (cuuint32_t)box_rows, 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = FMT == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                            : (FMT == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+                                            : ((FMT == 1 || FMT == 3) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
     CUresult r = fn(tm, dt, 4,
                     const_cast<void*>(base), dims, strides, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1360,6 +1373,21 @@ TcArgs targs(float* O, long long ldo, long long sO, int M, int N, int mode, int 
 }
 
 }  // namespace
+
+// C = (accumulate ? C : 0) - A B^T per batch entry on tcgen05 with BF16
+// operands (format 3) and FP32 accumulation: A [M][K] and B [N][K] BF16,
+// K-major, batch strides sA, sB; C [M][N] FP32 with row pitch ldc, batch
+// stride sC.  K must be a multiple of 8 (16-byte rows for TMA); false when a
+// tensor map cannot be encoded.
+bool tc_gemm_bf16(int M, int N, int K, const void* A, long long sA, const void* B, long long sB, float* C,
+                  long long ldc, long long sC, bool accumulate, int batch, cudaStream_t st)
+{
+    if (K % 8 != 0) return false;
+    if (M <= 0 || N <= 0 || batch <= 0) return true;
+    TcLeft L = left1(A, M, sA, K);
+    TcArgs a = targs(C, ldc, sC, M, N, accumulate ? GM_ACC : GM_SET, 0);
+    return launch_tc_update_f<3>(L, B, (long long)N * K, sB, K, K, a, batch, st, true, 256, nullptr);
+}
 
 void tc_test_stall_next(int on) { g_test_stall_next = on ? 1 : 0; }
 bool tc_test_stall_armed() { return g_test_stall_next != 0; }
