@@ -4,15 +4,25 @@
 // A three-layer MLP maps the sampled coefficient b of a box (all p^3 grid
 // values, input x = 2 (b - 1)) to factors U, V in R^{m x r}; the predicted map
 // is T_hat = T0 + s U V^T, with T0 the DtN map of the same box for b = 1 and s
-// a fixed target scale.  Weights are kept in FP32 (master copy, Adam moments)
-// and used in BF16 by every product, which accumulates in FP32.  Training
-// minimises L = mean over boxes and entries of (U V^T - (T - T0)/s)^2.
+// a fixed target scale.  Training minimises L = mean over boxes and entries of
+// (U V^T - (T - T0)/s)^2.
 //
 // Layers (row-major, weights [in][out]):
 //   a1 = relu(x W0 + c0),  a2 = relu(a1 W1 + c1),  y = a2 W2 + c2,
 //   U = y[:, 0 : m r] as [m][r],  V = y[:, m r : 2 m r] as [m][r].
+//
+// Every product runs on the tensor cores (tcgen05 kind::f16, BF16 operands,
+// FP32 accumulation in TMEM; tc_gemm_bf16 computes C = -A B^T with both
+// operands K-major).  Weights are kept in FP32 (master copy, Adam moments)
+// with two BF16 copies holding -W^T (forward products) and -W (back
+// propagation), so that C = -A B^T gives +A W.  Each product's other operand
+// is rounded to BF16 where it is made: by k_act, which adds the bias, applies
+// ReLU or the ReLU mask and writes the BF16 copies (row-major, and transposed
+// with the batch as the K index for the weight gradients).  Every BF16 buffer
+// has its K extent padded to a multiple of 8 with zeros (16-byte TMA rows).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -20,13 +30,19 @@
 
 #include "hps_internal.h"
 
+namespace {
+inline int pad8(int v) { return (v + 7) & ~7; }
+}
+
 struct hps_mlp {
     int device = 0;
     int dims[4] = {0, 0, 0, 0};        // n_in, h1, h2, n_out
-    int m = 0, rank = 0;
+    int kp[4] = {0, 0, 0, 0};          // dims padded to multiples of 8 (BF16 K extents)
+    int m = 0, rank = 0, rp = 0, mp = 0;   // rank, m padded to multiples of 8
     float* W[3] = {};                  // FP32 master weights [in][out]
     float* c[3] = {};                  // biases [out]
-    __nv_bfloat16* Wb[3] = {};         // BF16 copies used by the products
+    __nv_bfloat16* WnT[3] = {};        // -W^T [out][kp(in)] (forward products)
+    __nv_bfloat16* Wn[3] = {};         // -W [in][kp(out)] (back propagation; layers 1, 2)
     float* gW[3] = {};
     float* gc[3] = {};
     float* mW[3] = {};
@@ -34,111 +50,114 @@ struct hps_mlp {
     float* mc[3] = {};
     float* vc[3] = {};
     long long adam_t = 0;
-    int cap = 0;                       // batch capacity of the activation buffers
-    float *x = nullptr, *a1 = nullptr, *a2 = nullptr, *y = nullptr, *dy = nullptr, *d2 = nullptr,
-          *d1 = nullptr, *E = nullptr;
+    // forward buffers (capacity cap_f boxes)
+    int cap_f = 0;
+    __nv_bfloat16 *xb = nullptr, *a1b = nullptr, *a2b = nullptr;   // [B][kp]
+    float *z = nullptr, *y = nullptr;                            // [B][max(h1, h2)], [B][n_out]
+    // training buffers (capacity cap_t boxes; transposed copies [F][pad8(cap_t)])
+    int cap_t = 0;
+    __nv_bfloat16 *xT = nullptr, *a1T = nullptr, *a2T = nullptr;
+    __nv_bfloat16 *Un = nullptr, *Vb = nullptr, *UT = nullptr, *VT = nullptr;   // [B][m][rp], [B][r][mp]
+    float* E = nullptr;                                                        // [B][m][m]
+    __nv_bfloat16 *Gn = nullptr, *GnT = nullptr;                               // [B][m][mp]
+    float *dy = nullptr, *d2 = nullptr, *d1 = nullptr;                         // [B][F]
+    __nv_bfloat16 *dyb = nullptr, *d2b = nullptr;                              // [B][kp]
+    __nv_bfloat16 *dyTn = nullptr, *d2Tn = nullptr, *d1Tn = nullptr;           // -transposes [F][pad8(B)]
     double* loss = nullptr;
 };
 
 namespace {
 
-// C[b] = alpha opA(A[b]) opB(B[b]) + beta C[b] (+ bias[j]) (relu) (* [mask > 0])
-// opA(i, k) = tA ? A[k lda + i] : A[i lda + k];  opB(k, j) = tB ? B[j ldb + k] : B[k ldb + j].
-template <typename TB>
+// Elementwise stage after a product, on 32 x 32 tiles of an R x C matrix
+// (batch entry blockIdx.z): v = Z (in_kind 0) or float(2 (Z - 1)) (in_kind
+// 1, the network input from b), then + bias[c], relu, and zero where
+// mask[r][c] (BF16) is not positive.  Writes v to Zo (FP32, may alias Z),
+// sN * bf16(v) to Nb [R][ldn] (columns C..ldn-1 zero) and sT * bf16(v) to
+// Tb [C][ldt] transposed (columns R..ldt-1 zero); each output optional.
+template <typename TI>
 __global__ void __launch_bounds__(256)
-k_mm(int M, int N, int K, const float* __restrict__ A, long long sA, int lda, int tA, const TB* __restrict__ B,
-     long long sB, int ldb, int tB, float* __restrict__ C, long long sC, int ldc, float alpha, float beta,
-     const float* __restrict__ bias, int relu, const float* __restrict__ mask, int ldmask)
+k_act(int R, int C, const TI* __restrict__ Z, long long ldz, long long sZ, int in_kind,
+      const float* __restrict__ bias, int relu, const __nv_bfloat16* __restrict__ mask, long long ldmask,
+      long long sMask, float* Zo, long long ldzo, long long sZo, __nv_bfloat16* __restrict__ Nb, long long ldn,
+      long long sN_, float sgnN, __nv_bfloat16* __restrict__ Tb, long long ldt, long long sT_, float sgnT)
 {
-    constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ float As[BK][BM + 1];
-    __shared__ float Bs[BK][BN + 1];
-    const int z = blockIdx.z;
-    A += z * sA;
-    B += z * sB;
-    C += z * sC;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
-            int i, kk;
-            if (tA) { i = idx % BM; kk = idx / BM; } else { kk = idx % BK; i = idx / BK; }
-            const int r = m0 + i, kc = k0 + kk;
-            float v = 0.0f;
-            if (r < M && kc < K) v = tA ? A[(long long)kc * lda + r] : A[(long long)r * lda + kc];
-            As[kk][i] = v;
-        }
-        for (int idx = threadIdx.x; idx < BK * BN; idx += 256) {
-            int jj, kk;
-            if (tB) { kk = idx % BK; jj = idx / BK; } else { jj = idx % BN; kk = idx / BN; }
-            const int c = n0 + jj, kc = k0 + kk;
-            float v = 0.0f;
-            if (c < N && kc < K) v = float(tB ? B[(long long)c * ldb + kc] : B[(long long)kc * ldb + c]);
-            Bs[kk][jj] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
-#pragma unroll
-            for (int bq = 0; bq < 4; ++bq) bv[bq] = Bs[kk][tx * 4 + bq];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int bq = 0; bq < 4; ++bq) acc[a][bq] += av[a] * bv[bq];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int r = m0 + ty * 4 + a;
-        if (r >= M) continue;
-#pragma unroll
-        for (int bq = 0; bq < 4; ++bq) {
-            const int c = n0 + tx * 4 + bq;
-            if (c >= N) continue;
-            float v = alpha * acc[a][bq];
-            if (beta != 0.0f) v += beta * C[(long long)r * ldc + c];
-            if (bias) v += bias[c];
+    __shared__ float tile[32][33];
+    const long long z = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, cc = c0 + tx;
+        float v = 0.0f;
+        if (r < R && cc < C) {
+            const TI zin = Z[z * sZ + (long long)r * ldz + cc];
+            v = in_kind == 1 ? float(2.0 * ((double)zin - 1.0)) : float(zin);
+            if (bias) v += bias[cc];
             if (relu) v = fmaxf(v, 0.0f);
-            if (mask && !(mask[(long long)r * ldmask + c] > 0.0f)) v = 0.0f;
-            C[(long long)r * ldc + c] = v;
+            if (mask && !(__bfloat162float(mask[z * sMask + (long long)r * ldmask + cc]) > 0.0f)) v = 0.0f;
+            if (Zo) Zo[z * sZo + (long long)r * ldzo + cc] = v;
         }
+        tile[rr][tx] = v;
+        if (Nb && r < R && cc < ldn) Nb[z * sN_ + (long long)r * ldn + cc] = __float2bfloat16_rn(sgnN * v);
+    }
+    if (!Tb) return;
+    __syncthreads();
+    for (int cr = ty; cr < 32; cr += 8) {
+        const int cc = c0 + cr, r = r0 + tx;
+        if (cc < C && r < ldt) Tb[z * sT_ + (long long)cc * ldt + r] = __float2bfloat16_rn(sgnT * tile[tx][cr]);
     }
 }
 
-template <typename TB>
-void mm(int M, int N, int K, const float* A, long long sA, int lda, int tA, const TB* B, long long sB, int ldb,
-        int tB, float* C, long long sC, int ldc, float alpha, float beta, const float* bias, int relu,
-        const float* mask, int ldmask, int batch, cudaStream_t st)
+template <typename TI>
+void act(int R, int C, const TI* Z, long long ldz, long long sZ, int in_kind, const float* bias, int relu,
+         const __nv_bfloat16* mask, long long ldmask, long long sMask, float* Zo, long long ldzo, long long sZo,
+         __nv_bfloat16* Nb, long long ldn, long long sN_, float sgnN, __nv_bfloat16* Tb, long long ldt, long long sT_,
+         float sgnT, int batch, cudaStream_t st)
 {
-    dim3 grd((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)batch);
-    k_mm<TB><<<grd, 256, 0, st>>>(M, N, K, A, sA, lda, tA, B, sB, ldb, tB, C, sC, ldc, alpha, beta, bias, relu,
-                                   mask, ldmask);
+    // the tiles cover the padded extents of both outputs
+    const long long rows = std::max<long long>(R, Tb ? ldt : R), cols = std::max<long long>(C, Nb ? ldn : C);
+    dim3 grd((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32), (unsigned)batch);
+    k_act<TI><<<grd, dim3(32, 8), 0, st>>>(R, C, Z, ldz, sZ, in_kind, bias, relu, mask, ldmask, sMask, Zo, ldzo, sZo,
+                                           Nb, ldn, sN_, sgnN, Tb, ldt, sT_, sgnT);
 }
 
-__global__ void k_input(int n, const double* __restrict__ b, float* __restrict__ x)
+// Loss stage on 32 x 32 tiles of box blockIdx.z: e = E - (T - T0) / s (FP32),
+// sum of e^2 into *loss (FP64), and G = g e written as -bf16(G) to Gn
+// [m][ldg] and -bf16(G^T) to GnT [m][ldg] (columns m..ldg-1 zero).
+__global__ void __launch_bounds__(256)
+k_loss(int m, const float* __restrict__ E, const double* __restrict__ T, const double* __restrict__ T0, double inv_s,
+       float g, __nv_bfloat16* __restrict__ Gn, __nv_bfloat16* __restrict__ GnT, int ldg, double* loss)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] = float(2.0 * (b[i] - 1.0));
-}
-
-// E = E - (T - T0) / s (E holds U V^T, T0 shared by the batch); accumulates sum E^2.
-__global__ void k_residual_target(long long n, long long mm2, float* __restrict__ E, const double* __restrict__ T,
-                                  const double* __restrict__ T0, double inv_s, double* loss)
-{
+    __shared__ float tile[32][33];
+    __shared__ double red[8];
+    const long long z = blockIdx.z, mm2 = (long long)m * m, gpl = (long long)m * ldg;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float e = E[i] - float((T[i] - T0[i % mm2]) * inv_s);
-        E[i] = e;
-        acc += (double)e * e;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, cc = c0 + tx;
+        float e = 0.0f;
+        if (r < m && cc < m) {
+            const long long i = (long long)r * m + cc;
+            e = E[z * mm2 + i] - float((T[z * mm2 + i] - T0[i]) * inv_s);
+            acc += (double)e * e;
+        }
+        const float gv = g * e;
+        tile[rr][tx] = gv;
+        if (r < m && cc < ldg) Gn[z * gpl + (long long)r * ldg + cc] = __float2bfloat16_rn(-gv);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+    if (tx == 0) red[ty] = acc;
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        atomicAdd(loss, t);
+    }
+    for (int cr = ty; cr < 32; cr += 8) {
+        const int cc = c0 + cr, r = r0 + tx;
+        if (cc < m && r < ldg) GnT[z * gpl + (long long)cc * ldg + r] = __float2bfloat16_rn(-tile[tx][cr]);
+    }
 }
 
 // g[j] = sum over rows of d[r][j]
@@ -152,8 +171,7 @@ __global__ void k_colsum(int rows, int cols, const float* __restrict__ d, float*
 }
 
 __global__ void k_adam(long long n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ mo,
-                       float* __restrict__ ve, __nv_bfloat16* __restrict__ wb, float lr, float b1, float b2, float eps,
-                       float bc1, float bc2)
+                       float* __restrict__ ve, float lr, float b1, float b2, float eps, float bc1, float bc2)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -161,16 +179,8 @@ __global__ void k_adam(long long n, float* __restrict__ w, const float* __restri
         const float v = b2 * ve[i] + (1.0f - b2) * gi * gi;
         mo[i] = m;
         ve[i] = v;
-        const float wi = w[i] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
-        w[i] = wi;
-        if (wb) wb[i] = __float2bfloat16(wi);
+        w[i] = w[i] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
     }
-}
-
-__global__ void k_to_bf16(long long n, const float* __restrict__ w, __nv_bfloat16* __restrict__ wb)
-{
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        wb[i] = __float2bfloat16(w[i]);
 }
 
 __global__ void k_split_uv(int B, int mr, const float* __restrict__ y, int ldy, double* __restrict__ U,
@@ -211,50 +221,121 @@ unsigned long long splitmix(unsigned long long& s)
 
 int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
 
+template <typename T>
+void free_all(T*& p) { cudaFree(p); p = nullptr; }
+
+void free_fwd(hps_mlp* net)
+{
+    free_all(net->xb); free_all(net->a1b); free_all(net->a2b); free_all(net->z); free_all(net->y);
+    net->cap_f = 0;
+}
+
+void free_train(hps_mlp* net)
+{
+    free_all(net->xT); free_all(net->a1T); free_all(net->a2T);
+    free_all(net->Un); free_all(net->Vb); free_all(net->UT); free_all(net->VT);
+    free_all(net->E); free_all(net->Gn); free_all(net->GnT);
+    free_all(net->dy); free_all(net->d2); free_all(net->d1); free_all(net->dyb); free_all(net->d2b);
+    free_all(net->dyTn); free_all(net->d2Tn); free_all(net->d1Tn);
+    net->cap_t = 0;
+}
+
 void free_mlp(hps_mlp* net)
 {
     for (int l = 0; l < 3; ++l) {
-        cudaFree(net->W[l]); cudaFree(net->c[l]); cudaFree(net->Wb[l]); cudaFree(net->gW[l]); cudaFree(net->gc[l]);
-        cudaFree(net->mW[l]); cudaFree(net->vW[l]); cudaFree(net->mc[l]); cudaFree(net->vc[l]);
+        free_all(net->W[l]); free_all(net->c[l]); free_all(net->WnT[l]); free_all(net->Wn[l]);
+        free_all(net->gW[l]); free_all(net->gc[l]);
+        free_all(net->mW[l]); free_all(net->vW[l]); free_all(net->mc[l]); free_all(net->vc[l]);
     }
-    cudaFree(net->x); cudaFree(net->a1); cudaFree(net->a2); cudaFree(net->y); cudaFree(net->dy);
-    cudaFree(net->d2); cudaFree(net->d1); cudaFree(net->E); cudaFree(net->loss);
+    free_fwd(net);
+    free_train(net);
+    free_all(net->loss);
 }
 
-hps_status ensure_batch(hps_mlp* net, int B)
+template <typename T>
+bool alloc_n(T*& p, size_t n) { return cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)) == cudaSuccess; }
+
+hps_status ensure_fwd(hps_mlp* net, int B)
 {
-    if (B <= net->cap) return HPS_OK;
+    if (B <= net->cap_f) return HPS_OK;
     cudaDeviceSynchronize();
-    cudaFree(net->x); cudaFree(net->a1); cudaFree(net->a2); cudaFree(net->y); cudaFree(net->dy);
-    cudaFree(net->d2); cudaFree(net->d1); cudaFree(net->E);
+    free_fwd(net);
     const int* d = net->dims;
-    const size_t mm2 = (size_t)net->m * net->m;
-    if (cudaMalloc(&net->x, sizeof(float) * (size_t)B * d[0]) != cudaSuccess ||
-        cudaMalloc(&net->a1, sizeof(float) * (size_t)B * d[1]) != cudaSuccess ||
-        cudaMalloc(&net->a2, sizeof(float) * (size_t)B * d[2]) != cudaSuccess ||
-        cudaMalloc(&net->y, sizeof(float) * (size_t)B * d[3]) != cudaSuccess ||
-        cudaMalloc(&net->dy, sizeof(float) * (size_t)B * d[3]) != cudaSuccess ||
-        cudaMalloc(&net->d2, sizeof(float) * (size_t)B * d[2]) != cudaSuccess ||
-        cudaMalloc(&net->d1, sizeof(float) * (size_t)B * d[1]) != cudaSuccess ||
-        cudaMalloc(&net->E, sizeof(float) * (size_t)B * mm2) != cudaSuccess) {
+    const int* k = net->kp;
+    const size_t Bz = (size_t)B;
+    if (!alloc_n(net->xb, Bz * k[0]) || !alloc_n(net->a1b, Bz * k[1]) || !alloc_n(net->a2b, Bz * k[2]) ||
+        !alloc_n(net->z, Bz * std::max(d[1], d[2])) || !alloc_n(net->y, Bz * d[3])) {
         cudaGetLastError();
-        net->cap = 0;
+        free_fwd(net);
         return HPS_ENOMEM;
     }
-    net->cap = B;
+    net->cap_f = B;
     return HPS_OK;
 }
 
-void forward(hps_mlp* net, int B, const double* b_in, cudaStream_t st)
+hps_status ensure_train(hps_mlp* net, int B)
+{
+    if (B <= net->cap_t) return HPS_OK;
+    cudaDeviceSynchronize();
+    free_train(net);
+    const int* d = net->dims;
+    const int* k = net->kp;
+    const size_t Bz = (size_t)B, Bp = (size_t)pad8(B), m = net->m, r = net->rank, rp = net->rp, mp = net->mp;
+    if (!alloc_n(net->xT, d[0] * Bp) || !alloc_n(net->a1T, d[1] * Bp) || !alloc_n(net->a2T, d[2] * Bp) ||
+        !alloc_n(net->Un, Bz * m * rp) || !alloc_n(net->Vb, Bz * m * rp) || !alloc_n(net->UT, Bz * r * mp) ||
+        !alloc_n(net->VT, Bz * r * mp) || !alloc_n(net->E, Bz * m * m) || !alloc_n(net->Gn, Bz * m * mp) ||
+        !alloc_n(net->GnT, Bz * m * mp) || !alloc_n(net->dy, Bz * d[3]) || !alloc_n(net->d2, Bz * d[2]) ||
+        !alloc_n(net->d1, Bz * d[1]) || !alloc_n(net->dyb, Bz * k[3]) || !alloc_n(net->d2b, Bz * k[2]) ||
+        !alloc_n(net->dyTn, d[3] * Bp) || !alloc_n(net->d2Tn, d[2] * Bp) || !alloc_n(net->d1Tn, d[1] * Bp)) {
+        cudaGetLastError();
+        free_train(net);
+        return HPS_ENOMEM;
+    }
+    net->cap_t = B;
+    return HPS_OK;
+}
+
+// The BF16 copies -W^T and -W of layer l's FP32 weights.
+void refresh_copies(hps_mlp* net, int l, cudaStream_t st)
 {
     const int* d = net->dims;
-    k_input<<<blocks_for((long long)B * d[0]), 256, 0, st>>>(B * d[0], b_in, net->x);
-    mm<__nv_bfloat16>(B, d[1], d[0], net->x, 0, d[0], 0, net->Wb[0], 0, d[1], 0, net->a1, 0, d[1], 1.f, 0.f, net->c[0],
-                      1, nullptr, 0, 1, st);
-    mm<__nv_bfloat16>(B, d[2], d[1], net->a1, 0, d[1], 0, net->Wb[1], 0, d[2], 0, net->a2, 0, d[2], 1.f, 0.f, net->c[1],
-                      1, nullptr, 0, 1, st);
-    mm<__nv_bfloat16>(B, d[3], d[2], net->a2, 0, d[2], 0, net->Wb[2], 0, d[3], 0, net->y, 0, d[3], 1.f, 0.f, net->c[2],
-                      0, nullptr, 0, 1, st);
+    const int* k = net->kp;
+    act<float>(d[l], d[l + 1], net->W[l], d[l + 1], 0, 0, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->Wn[l],
+               k[l + 1], 0, -1.0f, net->WnT[l], k[l], 0, -1.0f, 1, st);
+}
+
+// C [M][N] = A B^T for BF16 operands with a negated side (see the header);
+// batch strides of 0 for one entry are given a valid value for the tensor maps.
+bool gemm(int M, int N, int K, const __nv_bfloat16* A, long long sA, const __nv_bfloat16* B, long long sB, float* C,
+          long long ldc, long long sC, int batch, cudaStream_t st)
+{
+    if (batch == 1) {
+        sA = (long long)M * K;
+        sB = (long long)N * K;
+        sC = (long long)M * ldc;
+    }
+    return hps::tc_gemm_bf16(M, N, K, A, sA, B, sB, C, ldc, sC, false, batch, st);
+}
+
+// Forward pass of B boxes into net->y (bias included); with `train`, the
+// transposed BF16 activations for the weight gradients as well.
+bool forward(hps_mlp* net, int B, const double* b_in, bool train, cudaStream_t st)
+{
+    const int* d = net->dims;
+    const int* k = net->kp;
+    const int Bp = pad8(B);
+    act<double>(B, d[0], b_in, d[0], 0, 1, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->xb, k[0], 0, 1.0f,
+                train ? net->xT : nullptr, Bp, 0, 1.0f, 1, st);
+    if (!gemm(B, d[1], k[0], net->xb, 0, net->WnT[0], 0, net->z, d[1], 0, 1, st)) return false;
+    act<float>(B, d[1], net->z, d[1], 0, 0, net->c[0], 1, nullptr, 0, 0, nullptr, 0, 0, net->a1b, k[1], 0, 1.0f,
+               train ? net->a1T : nullptr, Bp, 0, 1.0f, 1, st);
+    if (!gemm(B, d[2], k[1], net->a1b, 0, net->WnT[1], 0, net->z, d[2], 0, 1, st)) return false;
+    act<float>(B, d[2], net->z, d[2], 0, 0, net->c[1], 1, nullptr, 0, 0, nullptr, 0, 0, net->a2b, k[2], 0, 1.0f,
+               train ? net->a2T : nullptr, Bp, 0, 1.0f, 1, st);
+    if (!gemm(B, d[3], k[2], net->a2b, 0, net->WnT[2], 0, net->y, d[3], 0, 1, st)) return false;
+    act<float>(B, d[3], net->y, d[3], 0, 0, net->c[2], 0, nullptr, 0, 0, net->y, d[3], 0, nullptr, 0, 0, 1.0f,
+               nullptr, 0, 0, 1.0f, 1, st);
+    return true;
 }
 
 }  // namespace
@@ -273,16 +354,19 @@ hps_status hps_mlp_create(int device, int n_in, int n_h1, int n_h2, int m, int r
     if (!net) return HPS_ENOMEM;
     net->device = device;
     net->dims[0] = n_in; net->dims[1] = n_h1; net->dims[2] = n_h2; net->dims[3] = 2 * m * rank;
+    for (int l = 0; l < 4; ++l) net->kp[l] = pad8(net->dims[l]);
     net->m = m;
     net->rank = rank;
+    net->rp = pad8(rank);
+    net->mp = pad8(m);
     unsigned long long s = seed;
     for (int l = 0; l < 3; ++l) {
         const size_t nw = (size_t)net->dims[l] * net->dims[l + 1], nc = net->dims[l + 1];
-        bool ok = cudaMalloc(&net->W[l], nw * 4) == cudaSuccess && cudaMalloc(&net->c[l], nc * 4) == cudaSuccess &&
-                  cudaMalloc(&net->Wb[l], nw * 2) == cudaSuccess && cudaMalloc(&net->gW[l], nw * 4) == cudaSuccess &&
-                  cudaMalloc(&net->gc[l], nc * 4) == cudaSuccess && cudaMalloc(&net->mW[l], nw * 4) == cudaSuccess &&
-                  cudaMalloc(&net->vW[l], nw * 4) == cudaSuccess && cudaMalloc(&net->mc[l], nc * 4) == cudaSuccess &&
-                  cudaMalloc(&net->vc[l], nc * 4) == cudaSuccess;
+        bool ok = alloc_n(net->W[l], nw) && alloc_n(net->c[l], nc) &&
+                  alloc_n(net->WnT[l], (size_t)net->dims[l + 1] * net->kp[l]) &&
+                  alloc_n(net->Wn[l], (size_t)net->dims[l] * net->kp[l + 1]) && alloc_n(net->gW[l], nw) &&
+                  alloc_n(net->gc[l], nc) && alloc_n(net->mW[l], nw) && alloc_n(net->vW[l], nw) &&
+                  alloc_n(net->mc[l], nc) && alloc_n(net->vc[l], nc);
         if (!ok) { cudaGetLastError(); free_mlp(net); delete net; return HPS_ENOMEM; }
         // He-uniform weights (scaled down on the output layer), zero biases.
         std::vector<float> w(nw);
@@ -292,9 +376,9 @@ hps_status hps_mlp_create(int device, int n_in, int n_h1, int n_h2, int m, int r
         cudaMemset(net->c[l], 0, nc * 4);
         cudaMemset(net->mW[l], 0, nw * 4); cudaMemset(net->vW[l], 0, nw * 4);
         cudaMemset(net->mc[l], 0, nc * 4); cudaMemset(net->vc[l], 0, nc * 4);
-        k_to_bf16<<<blocks_for(nw), 256>>>((long long)nw, net->W[l], net->Wb[l]);
+        refresh_copies(net, l, nullptr);
     }
-    if (cudaMalloc(&net->loss, sizeof(double)) != cudaSuccess) { cudaGetLastError(); free_mlp(net); delete net; return HPS_ENOMEM; }
+    if (!alloc_n(net->loss, 1)) { cudaGetLastError(); free_mlp(net); delete net; return HPS_ENOMEM; }
     if (cudaDeviceSynchronize() != cudaSuccess) { free_mlp(net); delete net; return HPS_ECUDA; }
     *out = net;
     return HPS_OK;
@@ -321,6 +405,7 @@ size_t hps_mlp_num_params(const hps_mlp* net)
 hps_status hps_mlp_copy_params(hps_mlp* net, int which, float* host, int to_device)
 {
     if (!net || !host || which < 0 || which > 1) return HPS_EINVAL;
+    if (to_device && which) return HPS_EINVAL;
     if (cudaSetDevice(net->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return HPS_ECUDA;
     size_t off = 0;
     for (int l = 0; l < 3; ++l) {
@@ -328,7 +413,6 @@ hps_status hps_mlp_copy_params(hps_mlp* net, int which, float* host, int to_devi
         float* w = which ? net->gW[l] : net->W[l];
         float* c = which ? net->gc[l] : net->c[l];
         cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
-        if (to_device && which) return HPS_EINVAL;
         if (cudaMemcpy(to_device ? (void*)w : (void*)(host + off), to_device ? (void*)(host + off) : (void*)w, nw * 4,
                        kind) != cudaSuccess)
             return HPS_ECUDA;
@@ -337,7 +421,7 @@ hps_status hps_mlp_copy_params(hps_mlp* net, int which, float* host, int to_devi
                        kind) != cudaSuccess)
             return HPS_ECUDA;
         off += nc;
-        if (to_device) k_to_bf16<<<blocks_for(nw), 256>>>((long long)nw, net->W[l], net->Wb[l]);
+        if (to_device) refresh_copies(net, l, nullptr);
     }
     return cudaDeviceSynchronize() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -347,10 +431,10 @@ hps_status hps_mlp_forward(hps_mlp* net, int B, const double* b_in, double* U, d
     if (!net || B < 0 || (B > 0 && (!b_in || !U || !V))) return HPS_EINVAL;
     if (B == 0) return HPS_OK;
     if (cudaSetDevice(net->device) != cudaSuccess) return HPS_ECUDA;
-    hps_status rc = ensure_batch(net, B);
+    hps_status rc = ensure_fwd(net, B);
     if (rc != HPS_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    forward(net, B, b_in, st);
+    if (!forward(net, B, b_in, false, st)) return HPS_ECUDA;
     const int mr = net->m * net->rank;
     k_split_uv<<<blocks_for((long long)B * mr), 256, 0, st>>>(B, mr, net->y, net->dims[3], U, V);
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
@@ -361,40 +445,49 @@ hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T
 {
     if (!net || B < 1 || !b_in || !T || !T0 || !(scale > 0)) return HPS_EINVAL;
     if (cudaSetDevice(net->device) != cudaSuccess) return HPS_ECUDA;
-    hps_status rc = ensure_batch(net, B);
+    hps_status rc = ensure_fwd(net, B);
+    if (rc == HPS_OK) rc = ensure_train(net, B);
     if (rc != HPS_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int* d = net->dims;
-    const int m = net->m, r = net->rank, mr = m * r;
+    const int* k = net->kp;
+    const int m = net->m, r = net->rank, mr = m * r, rp = net->rp, mp = net->mp, Bp = pad8(B);
     const long long mm2 = (long long)m * m;
-    forward(net, B, b_in, st);
-    // E = U V^T - (T - T0) / s ; loss = mean E^2
-    mm<float>(m, m, r, net->y, d[3], r, 0, net->y + mr, d[3], r, 1, net->E, mm2, m, 1.f, 0.f, nullptr, 0, nullptr, 0, B,
-              st);
+    bool ok = forward(net, B, b_in, true, st);
+    // BF16 factors: -U and V [m][rp] for E = U V^T, U^T and V^T [r][mp] for E^T U and E V
+    act<float>(m, r, net->y, r, d[3], 0, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->Un, rp, (long long)m * rp,
+               -1.0f, net->UT, mp, (long long)r * mp, 1.0f, B, st);
+    act<float>(m, r, net->y + mr, r, d[3], 0, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->Vb, rp,
+               (long long)m * rp, 1.0f, net->VT, mp, (long long)r * mp, 1.0f, B, st);
+    ok = ok && gemm(m, m, rp, net->Un, (long long)m * rp, net->Vb, (long long)m * rp, net->E, m, mm2, B, st);
+    // e = U V^T - (T - T0) / s, loss = mean e^2, G = (2 / (B m^2)) e
     cudaMemsetAsync(net->loss, 0, sizeof(double), st);
-    k_residual_target<<<blocks_for(B * mm2), 256, 0, st>>>(B * mm2, mm2, net->E, T, T0, 1.0 / scale, net->loss);
-    // dU = (2 / (B m^2)) E V ; dV = (2 / (B m^2)) E^T U
-    const float g = 2.0f / float((double)B * mm2);
-    mm<float>(m, r, m, net->E, mm2, m, 0, net->y + mr, d[3], r, 0, net->dy, d[3], r, g, 0.f, nullptr, 0, nullptr, 0, B,
-              st);
-    mm<float>(m, r, m, net->E, mm2, m, 1, net->y, d[3], r, 0, net->dy + mr, d[3], r, g, 0.f, nullptr, 0, nullptr, 0, B,
-              st);
-    // layer 3
-    mm<float>(d[2], d[3], B, net->a2, 0, d[2], 1, net->dy, 0, d[3], 0, net->gW[2], 0, d[3], 1.f, 0.f, nullptr, 0,
-              nullptr, 0, 1, st);
+    {
+        const dim3 grd((unsigned)((mp + 31) / 32), (unsigned)((mp + 31) / 32), (unsigned)B);
+        k_loss<<<grd, dim3(32, 8), 0, st>>>(m, net->E, T, T0, 1.0 / scale, 2.0f / float((double)B * mm2), net->Gn,
+                                            net->GnT, mp, net->loss);
+    }
+    // dU = G V, dV = G^T U into dy
+    ok = ok && gemm(m, r, mp, net->Gn, (long long)m * mp, net->VT, (long long)r * mp, net->dy, r, d[3], B, st);
+    ok = ok && gemm(m, r, mp, net->GnT, (long long)m * mp, net->UT, (long long)r * mp, net->dy + mr, r, d[3], B, st);
+    // layer 3: gc2 from dy, gW2 = a2^T dy, d2 = (dy W2^T) * [a2 > 0]
     k_colsum<<<(d[3] + 255) / 256, 256, 0, st>>>(B, d[3], net->dy, net->gc[2]);
-    mm<__nv_bfloat16>(B, d[2], d[3], net->dy, 0, d[3], 0, net->Wb[2], 0, d[3], 1, net->d2, 0, d[2], 1.f, 0.f, nullptr, 0,
-                      net->a2, d[2], 1, st);
+    act<float>(B, d[3], net->dy, d[3], 0, 0, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->dyb, k[3], 0, 1.0f,
+               net->dyTn, Bp, 0, -1.0f, 1, st);
+    ok = ok && gemm(d[2], d[3], Bp, net->a2T, 0, net->dyTn, 0, net->gW[2], d[3], 0, 1, st);
+    ok = ok && gemm(B, d[2], k[3], net->dyb, 0, net->Wn[2], 0, net->d2, d[2], 0, 1, st);
+    act<float>(B, d[2], net->d2, d[2], 0, 0, nullptr, 0, net->a2b, k[2], 0, net->d2, d[2], 0, net->d2b, k[2], 0, 1.0f,
+               net->d2Tn, Bp, 0, -1.0f, 1, st);
     // layer 2
-    mm<float>(d[1], d[2], B, net->a1, 0, d[1], 1, net->d2, 0, d[2], 0, net->gW[1], 0, d[2], 1.f, 0.f, nullptr, 0,
-              nullptr, 0, 1, st);
     k_colsum<<<(d[2] + 255) / 256, 256, 0, st>>>(B, d[2], net->d2, net->gc[1]);
-    mm<__nv_bfloat16>(B, d[1], d[2], net->d2, 0, d[2], 0, net->Wb[1], 0, d[2], 1, net->d1, 0, d[1], 1.f, 0.f, nullptr, 0,
-                      net->a1, d[1], 1, st);
+    ok = ok && gemm(d[1], d[2], Bp, net->a1T, 0, net->d2Tn, 0, net->gW[1], d[2], 0, 1, st);
+    ok = ok && gemm(B, d[1], k[2], net->d2b, 0, net->Wn[1], 0, net->d1, d[1], 0, 1, st);
+    act<float>(B, d[1], net->d1, d[1], 0, 0, nullptr, 0, net->a1b, k[1], 0, net->d1, d[1], 0, nullptr, 0, 0, 1.0f,
+               net->d1Tn, Bp, 0, -1.0f, 1, st);
     // layer 1
-    mm<float>(d[0], d[1], B, net->x, 0, d[0], 1, net->d1, 0, d[1], 0, net->gW[0], 0, d[1], 1.f, 0.f, nullptr, 0,
-              nullptr, 0, 1, st);
     k_colsum<<<(d[1] + 255) / 256, 256, 0, st>>>(B, d[1], net->d1, net->gc[0]);
+    ok = ok && gemm(d[0], d[1], Bp, net->xT, 0, net->d1Tn, 0, net->gW[0], d[1], 0, 1, st);
+    if (!ok) return HPS_ECUDA;
     if (loss_out) {
         double l = 0.0;
         if (cudaMemcpyAsync(&l, net->loss, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -415,10 +508,11 @@ hps_status hps_mlp_adam_step(hps_mlp* net, float lr, float beta1, float beta2, f
     const float bc2 = 1.0f - std::pow(beta2, (float)net->adam_t);
     for (int l = 0; l < 3; ++l) {
         const long long nw = (long long)net->dims[l] * net->dims[l + 1], nc = net->dims[l + 1];
-        k_adam<<<blocks_for(nw), 256, 0, st>>>(nw, net->W[l], net->gW[l], net->mW[l], net->vW[l], net->Wb[l], lr, beta1,
-                                              beta2, eps, bc1, bc2);
-        k_adam<<<blocks_for(nc), 256, 0, st>>>(nc, net->c[l], net->gc[l], net->mc[l], net->vc[l], nullptr, lr, beta1,
-                                              beta2, eps, bc1, bc2);
+        k_adam<<<blocks_for(nw), 256, 0, st>>>(nw, net->W[l], net->gW[l], net->mW[l], net->vW[l], lr, beta1, beta2, eps,
+                                              bc1, bc2);
+        k_adam<<<blocks_for(nc), 256, 0, st>>>(nc, net->c[l], net->gc[l], net->mc[l], net->vc[l], lr, beta1, beta2, eps,
+                                              bc1, bc2);
+        refresh_copies(net, l, st);
     }
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
