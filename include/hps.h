@@ -235,8 +235,10 @@ hps_status hps_leaf_groups(hps_ctx* ctx, int ngroups, const hps_leaf_group* grou
  * computes T exactly).  A three-layer MLP maps the p^3 samples of b of a box
  * (input x = 2 (b - 1)) to factors U, V (m x rank); the predicted map is
  * T_hat = T0 + s U V^T with T0 the DtN map of the same box for b = 1.
- * Weights live in FP32 (master, Adam moments) and enter every product as
- * BF16 with FP32 accumulation; all kernels are this library's own. */
+ * Weights live in FP32 (master, Adam moments); every product runs on the
+ * tensor cores (tcgen05) with BF16 operands -- weights, activations, deltas
+ * and the scaled loss residual rounded to BF16 where they are made -- and
+ * FP32 accumulation; all kernels are this library's own. */
 typedef struct hps_mlp hps_mlp;
 
 /* n_in -> n_h1 -> n_h2 -> 2 m rank, ReLU hidden layers, He-uniform weights
@@ -257,9 +259,21 @@ hps_status hps_mlp_forward(hps_mlp* net, int B, const double* b_in, double* U, d
 /* Gradients of L = mean over boxes and entries of (U V^T - (T - T0) / scale)^2
  * for a batch b_in [B][n_in], exact maps T [B][m][m] and the b = 1 map
  * T0 [m][m] (device); the loss is returned on the host when loss_out is
- * non-NULL (this synchronises). */
+ * non-NULL (this synchronises).  Equivalent to hps_mlp_target into a buffer
+ * the network owns, then hps_mlp_grad_target. */
 hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T, const double* T0, double scale,
                         double* loss_out, void* stream);
+
+/* Training targets D[b] = float((T[b] - T0) / scale) (device; T [nbox][m][m],
+ * T0 [m][m] shared, D [nbox][m][m] FP32), formed once per training set so
+ * that each step reads 4 bytes per entry instead of two FP64 maps. */
+hps_status hps_mlp_target(int nbox, int m, const double* T, const double* T0, double scale, float* D, void* stream);
+
+/* Gradients of L = mean over boxes and entries of (U V^T - D)^2 for a batch
+ * b_in [B][n_in] and FP32 targets D [B][m][m] (device); loss as in
+ * hps_mlp_grad. */
+hps_status hps_mlp_grad_target(hps_mlp* net, int B, const double* b_in, const float* D, double* loss_out,
+                               void* stream);
 
 /* One Adam update with the last gradients. */
 hps_status hps_mlp_adam_step(hps_mlp* net, float lr, float beta1, float beta2, float eps, void* stream);

@@ -24,7 +24,8 @@ __all__ = [
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
     "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_LU_UNIT", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
-    "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
+    "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_target", "hps_mlp_grad_target",
+    "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
@@ -46,7 +47,8 @@ EXPORTED_SYMBOLS = (
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
-    "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_adam_step", "hps_lowrank_dtn",
+    "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_target", "hps_mlp_grad_target",
+    "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
     "hps_leaf_reconstruct_factored", "hps_leaf_factors_destroy", "hps_leaf_apply",
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
@@ -154,6 +156,8 @@ def load_library() -> ctypes.CDLL:
         "hps_mlp_copy_params": (i, [vp, i, ctypes.POINTER(ctypes.c_float), i]),
         "hps_mlp_forward": (i, [vp, i, vp, vp, vp, vp]),
         "hps_mlp_grad": (i, [vp, i, vp, vp, vp, d, dp, vp]),
+        "hps_mlp_target": (i, [i, i, vp, vp, d, vp, vp]),
+        "hps_mlp_grad_target": (i, [vp, i, vp, vp, dp, vp]),
         "hps_mlp_adam_step": (i, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]),
         "hps_lowrank_dtn": (i, [i, i, i, vp, d, vp, vp, vp, vp]),
         "hps_dtn_gate": (i, [vp, kp, i, vp, vp, i, ctypes.c_ulonglong, i, d, vp, vp, vp]),
@@ -605,6 +609,22 @@ def hps_mlp_grad(net, B: int, b, T, T0, scale: float, want_loss: bool = True, st
     loss = ctypes.c_double()
     _check(load_library().hps_mlp_grad(net, int(B), _ptr(b, f64), _ptr(T, f64), _ptr(T0, f64), float(scale),
                                        ctypes.byref(loss) if want_loss else None, _stream(stream)), "hps_mlp_grad")
+    return loss.value if want_loss else None
+
+
+def hps_mlp_target(nbox: int, m: int, T, T0, scale: float, D, stream=None) -> None:
+    """D = float((T - T0) / scale) on the device (D a float32 tensor)."""
+    import torch
+    _check(load_library().hps_mlp_target(int(nbox), int(m), _ptr(T, _f64()), _ptr(T0, _f64()), float(scale),
+                                         _ptr(D, torch.float32), _stream(stream)), "hps_mlp_target")
+
+
+def hps_mlp_grad_target(net, B: int, b, D, want_loss: bool = True, stream=None):
+    import torch
+    loss = ctypes.c_double()
+    _check(load_library().hps_mlp_grad_target(net, int(B), _ptr(b, _f64()), _ptr(D, torch.float32),
+                                              ctypes.byref(loss) if want_loss else None, _stream(stream)),
+           "hps_mlp_grad_target")
     return loss.value if want_loss else None
 
 

@@ -405,11 +405,13 @@ void lu_backward(const Plan& P, Work<T>& w, int nbox, int c0, int nc, const int*
 // with tc_abort_raised, cleared by tc_reset_abort) and marks its box
 // HPS_ETIMEOUT.
 // C = (accumulate ? C : 0) - A B^T on tcgen05 with BF16 A [M][K], B [N][K]
-// (K-major) and FP32 C [M][N] (pitch ldc), batch strides sA, sB, sC; K a
-// multiple of 8.  False when the operands cannot be described to TMA.
-bool tc_gemm_bf16(int M, int N, int K, const void* A, long long sA, const void* B, long long sB, float* C,
-                  long long ldc, long long sC, bool accumulate, int batch, cudaStream_t st);
+// (K-major, row pitches lda, ldb multiples of 8) and FP32 C [M][N] (pitch
+// ldc), batch strides sA, sB, sC.  False when the operands cannot be
+// described to TMA.
+bool tc_gemm_bf16(int M, int N, int K, const void* A, long long lda, long long sA, const void* B, long long ldb,
+                  long long sB, float* C, long long ldc, long long sC, bool accumulate, int batch, cudaStream_t st);
 void tc_reset_abort(cudaStream_t st);
+
 // Test hook: the next tensor-core launch of a call that writes box status
 // makes its first mbarrier wait run out (nothing is issued to fill it); that
 // launch and the rest of the call end with HPS_ETIMEOUT in box_status.

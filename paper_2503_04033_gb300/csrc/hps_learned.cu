@@ -64,6 +64,11 @@ struct hps_mlp {
     __nv_bfloat16 *dyb = nullptr, *d2b = nullptr;                              // [B][kp]
     __nv_bfloat16 *dyTn = nullptr, *d2Tn = nullptr, *d1Tn = nullptr;           // -transposes [F][pad8(B)]
     double* loss = nullptr;
+    double* lpart = nullptr;           // per (box, 32-row tile) sums of e^2 [cap_t][ceil(m / 32)]
+    float* part = nullptr;             // split-K partial products
+    long long part_cap = 0;
+    float* dtarget = nullptr;          // hps_mlp_grad's FP32 targets (T - T0)/s
+    size_t dcap = 0;
 };
 
 namespace {
@@ -85,25 +90,35 @@ k_act(int R, int C, const TI* __restrict__ Z, long long ldz, long long sZ, int i
     const long long z = blockIdx.z;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int rr = ty; rr < 32; rr += 8) {
-        const int r = r0 + rr, cc = c0 + tx;
-        float v = 0.0f;
-        if (r < R && cc < C) {
+    const int cc = c0 + tx;
+    // all loads first (Zo may alias Z), then the stores
+    float v[4];
+    bool in[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty + 8 * i;
+        in[i] = r < R && cc < C;
+        v[i] = 0.0f;
+        if (in[i]) {
             const TI zin = Z[z * sZ + (long long)r * ldz + cc];
-            v = in_kind == 1 ? float(2.0 * ((double)zin - 1.0)) : float(zin);
-            if (bias) v += bias[cc];
-            if (relu) v = fmaxf(v, 0.0f);
-            if (mask && !(__bfloat162float(mask[z * sMask + (long long)r * ldmask + cc]) > 0.0f)) v = 0.0f;
-            if (Zo) Zo[z * sZo + (long long)r * ldzo + cc] = v;
+            v[i] = in_kind == 1 ? float(2.0 * ((double)zin - 1.0)) : float(zin);
+            if (bias) v[i] += bias[cc];
+            if (relu) v[i] = fmaxf(v[i], 0.0f);
+            if (mask && !(__bfloat162float(mask[z * sMask + (long long)r * ldmask + cc]) > 0.0f)) v[i] = 0.0f;
         }
-        tile[rr][tx] = v;
-        if (Nb && r < R && cc < ldn) Nb[z * sN_ + (long long)r * ldn + cc] = __float2bfloat16_rn(sgnN * v);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int rr = ty + 8 * i, r = r0 + rr;
+        if (in[i] && Zo) Zo[z * sZo + (long long)r * ldzo + cc] = v[i];
+        tile[rr][tx] = v[i];
+        if (Nb && r < R && cc < ldn) Nb[z * sN_ + (long long)r * ldn + cc] = __float2bfloat16_rn(sgnN * v[i]);
     }
     if (!Tb) return;
     __syncthreads();
     for (int cr = ty; cr < 32; cr += 8) {
-        const int cc = c0 + cr, r = r0 + tx;
-        if (cc < C && r < ldt) Tb[z * sT_ + (long long)cc * ldt + r] = __float2bfloat16_rn(sgnT * tile[tx][cr]);
+        const int tc = c0 + cr, r = r0 + tx;
+        if (tc < C && r < ldt) Tb[z * sT_ + (long long)tc * ldt + r] = __float2bfloat16_rn(sgnT * tile[tx][cr]);
     }
 }
 
@@ -120,43 +135,90 @@ void act(int R, int C, const TI* Z, long long ldz, long long sZ, int in_kind, co
                                            Nb, ldn, sN_, sgnN, Tb, ldt, sT_, sgnT);
 }
 
-// Loss stage on 32 x 32 tiles of box blockIdx.z: e = E - (T - T0) / s (FP32),
-// sum of e^2 into *loss (FP64), and G = g e written as -bf16(G) to Gn
-// [m][ldg] and -bf16(G^T) to GnT [m][ldg] (columns m..ldg-1 zero).
+// Loss stage of box blockIdx.y, tile row blockIdx.x (32 rows), walking the
+// tile columns: e = E - D (FP32, D the box's target (T - T0)/s), the block's
+// sum of e^2 to part[box][tile row] (FP32 per thread, FP64 across them),
+// and G = g e written as -bf16(G) to Gn [m][ldg] and -bf16(G^T) to GnT
+// [m][ldg] (columns m..ldg-1 zero).
 __global__ void __launch_bounds__(256)
-k_loss(int m, const float* __restrict__ E, const double* __restrict__ T, const double* __restrict__ T0, double inv_s,
-       float g, __nv_bfloat16* __restrict__ Gn, __nv_bfloat16* __restrict__ GnT, int ldg, double* loss)
+k_loss(int m, const float* __restrict__ E, const float* __restrict__ D, float g, __nv_bfloat16* __restrict__ Gn,
+       __nv_bfloat16* __restrict__ GnT, int ldg, double* __restrict__ part)
 {
     __shared__ float tile[32][33];
     __shared__ double red[8];
-    const long long z = blockIdx.z, mm2 = (long long)m * m, gpl = (long long)m * ldg;
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const long long z = blockIdx.y, mm2 = (long long)m * m, gpl = (long long)m * ldg;
+    const int r0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    double acc = 0.0;
-    for (int rr = ty; rr < 32; rr += 8) {
-        const int r = r0 + rr, cc = c0 + tx;
-        float e = 0.0f;
-        if (r < m && cc < m) {
-            const long long i = (long long)r * m + cc;
-            e = E[z * mm2 + i] - float((T[z * mm2 + i] - T0[i]) * inv_s);
-            acc += (double)e * e;
-        }
-        const float gv = g * e;
-        tile[rr][tx] = gv;
-        if (r < m && cc < ldg) Gn[z * gpl + (long long)r * ldg + cc] = __float2bfloat16_rn(-gv);
-    }
+    float acc = 0.0f;
+    for (int c0 = 0; c0 < ldg; c0 += 32) {
+        const int cc = c0 + tx;
+        float e[4];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (tx == 0) red[ty] = acc;
+        for (int i = 0; i < 4; ++i) {
+            const int r = r0 + ty + 8 * i;
+            e[i] = 0.0f;
+            if (r < m && cc < m) {
+                const long long ix = z * mm2 + (long long)r * m + cc;
+                e[i] = E[ix] - D[ix];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int rr = ty + 8 * i, r = r0 + rr;
+            acc = fmaf(e[i], e[i], acc);
+            const float gv = g * e[i];
+            tile[rr][tx] = gv;
+            if (r < m && cc < ldg) Gn[z * gpl + (long long)r * ldg + cc] = __float2bfloat16_rn(-gv);
+        }
+        __syncthreads();
+        for (int cr = ty; cr < 32; cr += 8) {
+            const int tc = c0 + cr, r = r0 + tx;
+            if (tc < m && r < ldg) GnT[z * gpl + (long long)tc * ldg + r] = __float2bfloat16_rn(-tile[tx][cr]);
+        }
+        __syncthreads();
+    }
+    double dacc = acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
+    if (tx == 0) red[ty] = dacc;
     __syncthreads();
     if (tx == 0 && ty == 0) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += red[w];
-        atomicAdd(loss, t);
+        part[z * gridDim.x + blockIdx.x] = t;
     }
-    for (int cr = ty; cr < 32; cr += 8) {
-        const int cc = c0 + cr, r = r0 + tx;
-        if (cc < m && r < ldg) GnT[z * gpl + (long long)cc * ldg + r] = __float2bfloat16_rn(-tile[tx][cr]);
+}
+
+// D = float((T - T0) / s) for every box (T0 [m][m] shared).
+__global__ void k_target(long long n, long long mm2, const double* __restrict__ T, const double* __restrict__ T0,
+                         double inv_s, float* __restrict__ D)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        D[i] = float((T[i] - T0[i % mm2]) * inv_s);
+}
+
+// *out = sum of part[0..n) in a fixed order (one CTA).
+__global__ void k_sum(int n, const double* __restrict__ part, double* __restrict__ out)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// C[i] = sum over s < S of P[s][i] (split-K partial products), i < n.
+__global__ void k_reduce_splits(long long n, int S, const float* __restrict__ P, float* __restrict__ C)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int q = 0; q < S; ++q) acc += P[q * n + i];
+        C[i] = acc;
     }
 }
 
@@ -224,6 +286,9 @@ int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 4
 template <typename T>
 void free_all(T*& p) { cudaFree(p); p = nullptr; }
 
+template <typename T>
+bool alloc_n(T*& p, size_t n) { return cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)) == cudaSuccess; }
+
 void free_fwd(hps_mlp* net)
 {
     free_all(net->xb); free_all(net->a1b); free_all(net->a2b); free_all(net->z); free_all(net->y);
@@ -236,7 +301,7 @@ void free_train(hps_mlp* net)
     free_all(net->Un); free_all(net->Vb); free_all(net->UT); free_all(net->VT);
     free_all(net->E); free_all(net->Gn); free_all(net->GnT);
     free_all(net->dy); free_all(net->d2); free_all(net->d1); free_all(net->dyb); free_all(net->d2b);
-    free_all(net->dyTn); free_all(net->d2Tn); free_all(net->d1Tn);
+    free_all(net->dyTn); free_all(net->d2Tn); free_all(net->d1Tn); free_all(net->lpart);
     net->cap_t = 0;
 }
 
@@ -250,10 +315,26 @@ void free_mlp(hps_mlp* net)
     free_fwd(net);
     free_train(net);
     free_all(net->loss);
+    free_all(net->part);
+    net->part_cap = 0;
+    free_all(net->dtarget);
+    net->dcap = 0;
 }
 
-template <typename T>
-bool alloc_n(T*& p, size_t n) { return cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)) == cudaSuccess; }
+long long split_need(const hps_mlp* net, int B);
+
+// The split-K partial buffer for batches of up to B boxes.
+hps_status ensure_part(hps_mlp* net, int B)
+{
+    const long long need = split_need(net, B);
+    if (need <= net->part_cap) return HPS_OK;
+    cudaDeviceSynchronize();
+    free_all(net->part);
+    net->part_cap = 0;
+    if (!alloc_n(net->part, (size_t)need)) { cudaGetLastError(); return HPS_ENOMEM; }
+    net->part_cap = need;
+    return HPS_OK;
+}
 
 hps_status ensure_fwd(hps_mlp* net, int B)
 {
@@ -286,7 +367,8 @@ hps_status ensure_train(hps_mlp* net, int B)
         !alloc_n(net->VT, Bz * r * mp) || !alloc_n(net->E, Bz * m * m) || !alloc_n(net->Gn, Bz * m * mp) ||
         !alloc_n(net->GnT, Bz * m * mp) || !alloc_n(net->dy, Bz * d[3]) || !alloc_n(net->d2, Bz * d[2]) ||
         !alloc_n(net->d1, Bz * d[1]) || !alloc_n(net->dyb, Bz * k[3]) || !alloc_n(net->d2b, Bz * k[2]) ||
-        !alloc_n(net->dyTn, d[3] * Bp) || !alloc_n(net->d2Tn, d[2] * Bp) || !alloc_n(net->d1Tn, d[1] * Bp)) {
+        !alloc_n(net->dyTn, d[3] * Bp) || !alloc_n(net->d2Tn, d[2] * Bp) || !alloc_n(net->d1Tn, d[1] * Bp) ||
+        !alloc_n(net->lpart, Bz * ((m + 31) / 32))) {
         cudaGetLastError();
         free_train(net);
         return HPS_ENOMEM;
@@ -304,17 +386,70 @@ void refresh_copies(hps_mlp* net, int l, cudaStream_t st)
                k[l + 1], 0, -1.0f, net->WnT[l], k[l], 0, -1.0f, 1, st);
 }
 
+// Split-K partial products: a product of one batch entry with fewer output
+// tiles than half the SMs and K >= 256 runs as S products over K ranges of
+// Ks (a multiple of 32) into partial buffers, summed by k_reduce_splits.
+constexpr int kSplitMaxTiles = 76, kSplitMinK = 128;
+
+int split_count(int M, int N, int K, int batch, long long ldc)
+{
+    const int bn = N > 128 ? 256 : (N > 64 ? 128 : 64);
+    const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn) * batch;
+    if (batch != 1 || ldc != N || tiles >= kSplitMaxTiles || K < 2 * kSplitMinK) return 1;
+    return (int)std::min<long long>((152 + tiles - 1) / tiles, K / kSplitMinK);
+}
+
 // C [M][N] = A B^T for BF16 operands with a negated side (see the header);
-// batch strides of 0 for one entry are given a valid value for the tensor maps.
-bool gemm(int M, int N, int K, const __nv_bfloat16* A, long long sA, const __nv_bfloat16* B, long long sB, float* C,
-          long long ldc, long long sC, int batch, cudaStream_t st)
+// A [M][lda], B [N][ldb], K the used extent.  Batch strides of 0 for one
+// entry are given a valid value for the tensor maps.
+bool gemm(hps_mlp* net, int M, int N, int K, const __nv_bfloat16* A, long long lda, long long sA,
+          const __nv_bfloat16* B, long long ldb, long long sB, float* C, long long ldc, long long sC, int batch,
+          cudaStream_t st)
 {
     if (batch == 1) {
-        sA = (long long)M * K;
-        sB = (long long)N * K;
+        sA = (long long)M * lda;
+        sB = (long long)N * ldb;
         sC = (long long)M * ldc;
     }
-    return hps::tc_gemm_bf16(M, N, K, A, sA, B, sB, C, ldc, sC, false, batch, st);
+    int S = split_count(M, N, K, batch, ldc);
+    if (S <= 1 || !net->part) return hps::tc_gemm_bf16(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, false, batch, st);
+    const int Ks = ((K + S - 1) / S + 31) / 32 * 32;
+    S = (K + Ks - 1) / Ks;
+    const long long mn = (long long)M * N;
+    if ((long long)S * mn > net->part_cap) return hps::tc_gemm_bf16(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, false,
+                                                                     batch, st);
+    // S - 1 full ranges as batch entries (operand batch stride Ks), then the
+    // last range; the plain product if the ranges cannot be described to TMA
+    // (nothing is launched then)
+    if (!hps::tc_gemm_bf16(M, N, Ks, A, lda, Ks, B, ldb, Ks, net->part, N, mn, false, S - 1, st))
+        return hps::tc_gemm_bf16(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, false, batch, st);
+    const long long k0 = (long long)(S - 1) * Ks;
+    if (!hps::tc_gemm_bf16(M, N, (int)(K - k0), A + k0, lda, sA, B + k0, ldb, sB, net->part + (S - 1) * mn, N, mn,
+                           false, 1, st))
+        return false;
+    k_reduce_splits<<<blocks_for(mn), 256, 0, st>>>(mn, S, net->part, C);
+    return true;
+}
+
+// Largest split-K partial buffer (floats) any product of the network needs
+// for a batch of B boxes.
+long long split_need(const hps_mlp* net, int B)
+{
+    const int* d = net->dims;
+    const int* k = net->kp;
+    const int Bp = pad8(B);
+    const int shapes[8][3] = {{B, d[1], k[0]},  {B, d[2], k[1]},  {B, d[3], k[2]},  {d[2], d[3], Bp},
+                              {B, d[2], k[3]}, {d[1], d[2], Bp}, {B, d[1], k[2]}, {d[0], d[1], Bp}};
+    long long need = 0;
+    for (const auto& sh : shapes) {
+        int S = split_count(sh[0], sh[1], sh[2], 1, sh[1]);
+        if (S > 1) {
+            const int Ks = ((sh[2] + S - 1) / S + 31) / 32 * 32;
+            S = (sh[2] + Ks - 1) / Ks;
+            need = std::max(need, (long long)S * sh[0] * sh[1]);
+        }
+    }
+    return need;
 }
 
 // Forward pass of B boxes into net->y (bias included); with `train`, the
@@ -326,13 +461,13 @@ bool forward(hps_mlp* net, int B, const double* b_in, bool train, cudaStream_t s
     const int Bp = pad8(B);
     act<double>(B, d[0], b_in, d[0], 0, 1, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->xb, k[0], 0, 1.0f,
                 train ? net->xT : nullptr, Bp, 0, 1.0f, 1, st);
-    if (!gemm(B, d[1], k[0], net->xb, 0, net->WnT[0], 0, net->z, d[1], 0, 1, st)) return false;
+    if (!gemm(net, B, d[1], k[0], net->xb, k[0], 0, net->WnT[0], k[0], 0, net->z, d[1], 0, 1, st)) return false;
     act<float>(B, d[1], net->z, d[1], 0, 0, net->c[0], 1, nullptr, 0, 0, nullptr, 0, 0, net->a1b, k[1], 0, 1.0f,
                train ? net->a1T : nullptr, Bp, 0, 1.0f, 1, st);
-    if (!gemm(B, d[2], k[1], net->a1b, 0, net->WnT[1], 0, net->z, d[2], 0, 1, st)) return false;
+    if (!gemm(net, B, d[2], k[1], net->a1b, k[1], 0, net->WnT[1], k[1], 0, net->z, d[2], 0, 1, st)) return false;
     act<float>(B, d[2], net->z, d[2], 0, 0, net->c[1], 1, nullptr, 0, 0, nullptr, 0, 0, net->a2b, k[2], 0, 1.0f,
                train ? net->a2T : nullptr, Bp, 0, 1.0f, 1, st);
-    if (!gemm(B, d[3], k[2], net->a2b, 0, net->WnT[2], 0, net->y, d[3], 0, 1, st)) return false;
+    if (!gemm(net, B, d[3], k[2], net->a2b, k[2], 0, net->WnT[2], k[2], 0, net->y, d[3], 0, 1, st)) return false;
     act<float>(B, d[3], net->y, d[3], 0, 0, net->c[2], 0, nullptr, 0, 0, net->y, d[3], 0, nullptr, 0, 0, 1.0f,
                nullptr, 0, 0, 1.0f, 1, st);
     return true;
@@ -432,6 +567,7 @@ hps_status hps_mlp_forward(hps_mlp* net, int B, const double* b_in, double* U, d
     if (B == 0) return HPS_OK;
     if (cudaSetDevice(net->device) != cudaSuccess) return HPS_ECUDA;
     hps_status rc = ensure_fwd(net, B);
+    if (rc == HPS_OK) rc = ensure_part(net, B);
     if (rc != HPS_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!forward(net, B, b_in, false, st)) return HPS_ECUDA;
@@ -440,13 +576,22 @@ hps_status hps_mlp_forward(hps_mlp* net, int B, const double* b_in, double* U, d
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
-hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T, const double* T0, double scale,
-                        double* loss_out, void* stream)
+hps_status hps_mlp_target(int nbox, int m, const double* T, const double* T0, double scale, float* D, void* stream)
 {
-    if (!net || B < 1 || !b_in || !T || !T0 || !(scale > 0)) return HPS_EINVAL;
+    if (nbox < 0 || m < 1 || !(scale > 0) || (nbox > 0 && (!T || !T0 || !D))) return HPS_EINVAL;
+    if (nbox == 0) return HPS_OK;
+    const long long mm2 = (long long)m * m, n = (long long)nbox * mm2;
+    k_target<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, mm2, T, T0, 1.0 / scale, D);
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+hps_status hps_mlp_grad_target(hps_mlp* net, int B, const double* b_in, const float* D, double* loss_out, void* stream)
+{
+    if (!net || B < 1 || !b_in || !D) return HPS_EINVAL;
     if (cudaSetDevice(net->device) != cudaSuccess) return HPS_ECUDA;
     hps_status rc = ensure_fwd(net, B);
     if (rc == HPS_OK) rc = ensure_train(net, B);
+    if (rc == HPS_OK) rc = ensure_part(net, B);
     if (rc != HPS_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int* d = net->dims;
@@ -459,34 +604,35 @@ hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T
                -1.0f, net->UT, mp, (long long)r * mp, 1.0f, B, st);
     act<float>(m, r, net->y + mr, r, d[3], 0, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->Vb, rp,
                (long long)m * rp, 1.0f, net->VT, mp, (long long)r * mp, 1.0f, B, st);
-    ok = ok && gemm(m, m, rp, net->Un, (long long)m * rp, net->Vb, (long long)m * rp, net->E, m, mm2, B, st);
-    // e = U V^T - (T - T0) / s, loss = mean e^2, G = (2 / (B m^2)) e
-    cudaMemsetAsync(net->loss, 0, sizeof(double), st);
+    ok = ok && gemm(net, m, m, rp, net->Un, rp, (long long)m * rp, net->Vb, rp, (long long)m * rp, net->E, m, mm2, B, st);
+    // e = U V^T - D, loss = mean e^2, G = (2 / (B m^2)) e
     {
-        const dim3 grd((unsigned)((mp + 31) / 32), (unsigned)((mp + 31) / 32), (unsigned)B);
-        k_loss<<<grd, dim3(32, 8), 0, st>>>(m, net->E, T, T0, 1.0 / scale, 2.0f / float((double)B * mm2), net->Gn,
-                                            net->GnT, mp, net->loss);
+        const int rt = (m + 31) / 32;
+        k_loss<<<dim3((unsigned)rt, (unsigned)B), dim3(32, 8), 0, st>>>(m, net->E, D, 2.0f / float((double)B * mm2),
+                                                                       net->Gn, net->GnT, mp, net->lpart);
+        k_sum<<<1, 256, 0, st>>>(rt * B, net->lpart, net->loss);
     }
     // dU = G V, dV = G^T U into dy
-    ok = ok && gemm(m, r, mp, net->Gn, (long long)m * mp, net->VT, (long long)r * mp, net->dy, r, d[3], B, st);
-    ok = ok && gemm(m, r, mp, net->GnT, (long long)m * mp, net->UT, (long long)r * mp, net->dy + mr, r, d[3], B, st);
+    ok = ok && gemm(net, m, r, mp, net->Gn, mp, (long long)m * mp, net->VT, mp, (long long)r * mp, net->dy, r, d[3], B, st);
+    ok = ok && gemm(net, m, r, mp, net->GnT, mp, (long long)m * mp, net->UT, mp, (long long)r * mp, net->dy + mr, r, d[3],
+                    B, st);
     // layer 3: gc2 from dy, gW2 = a2^T dy, d2 = (dy W2^T) * [a2 > 0]
     k_colsum<<<(d[3] + 255) / 256, 256, 0, st>>>(B, d[3], net->dy, net->gc[2]);
     act<float>(B, d[3], net->dy, d[3], 0, 0, nullptr, 0, nullptr, 0, 0, nullptr, 0, 0, net->dyb, k[3], 0, 1.0f,
                net->dyTn, Bp, 0, -1.0f, 1, st);
-    ok = ok && gemm(d[2], d[3], Bp, net->a2T, 0, net->dyTn, 0, net->gW[2], d[3], 0, 1, st);
-    ok = ok && gemm(B, d[2], k[3], net->dyb, 0, net->Wn[2], 0, net->d2, d[2], 0, 1, st);
+    ok = ok && gemm(net, d[2], d[3], Bp, net->a2T, Bp, 0, net->dyTn, Bp, 0, net->gW[2], d[3], 0, 1, st);
+    ok = ok && gemm(net, B, d[2], k[3], net->dyb, k[3], 0, net->Wn[2], k[3], 0, net->d2, d[2], 0, 1, st);
     act<float>(B, d[2], net->d2, d[2], 0, 0, nullptr, 0, net->a2b, k[2], 0, net->d2, d[2], 0, net->d2b, k[2], 0, 1.0f,
                net->d2Tn, Bp, 0, -1.0f, 1, st);
     // layer 2
     k_colsum<<<(d[2] + 255) / 256, 256, 0, st>>>(B, d[2], net->d2, net->gc[1]);
-    ok = ok && gemm(d[1], d[2], Bp, net->a1T, 0, net->d2Tn, 0, net->gW[1], d[2], 0, 1, st);
-    ok = ok && gemm(B, d[1], k[2], net->d2b, 0, net->Wn[1], 0, net->d1, d[1], 0, 1, st);
+    ok = ok && gemm(net, d[1], d[2], Bp, net->a1T, Bp, 0, net->d2Tn, Bp, 0, net->gW[1], d[2], 0, 1, st);
+    ok = ok && gemm(net, B, d[1], k[2], net->d2b, k[2], 0, net->Wn[1], k[2], 0, net->d1, d[1], 0, 1, st);
     act<float>(B, d[1], net->d1, d[1], 0, 0, nullptr, 0, net->a1b, k[1], 0, net->d1, d[1], 0, nullptr, 0, 0, 1.0f,
                net->d1Tn, Bp, 0, -1.0f, 1, st);
     // layer 1
     k_colsum<<<(d[1] + 255) / 256, 256, 0, st>>>(B, d[1], net->d1, net->gc[0]);
-    ok = ok && gemm(d[0], d[1], Bp, net->xT, 0, net->d1Tn, 0, net->gW[0], d[1], 0, 1, st);
+    ok = ok && gemm(net, d[0], d[1], Bp, net->xT, Bp, 0, net->d1Tn, Bp, 0, net->gW[0], d[1], 0, 1, st);
     if (!ok) return HPS_ECUDA;
     if (loss_out) {
         double l = 0.0;
@@ -496,6 +642,24 @@ hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T
         *loss_out = l / ((double)B * mm2);
     }
     return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+hps_status hps_mlp_grad(hps_mlp* net, int B, const double* b_in, const double* T, const double* T0, double scale,
+                        double* loss_out, void* stream)
+{
+    if (!net || B < 1 || !b_in || !T || !T0 || !(scale > 0)) return HPS_EINVAL;
+    if (cudaSetDevice(net->device) != cudaSuccess) return HPS_ECUDA;
+    const size_t need = (size_t)B * net->m * net->m;
+    if (need > net->dcap) {
+        cudaDeviceSynchronize();
+        free_all(net->dtarget);
+        net->dcap = 0;
+        if (!alloc_n(net->dtarget, need)) { cudaGetLastError(); return HPS_ENOMEM; }
+        net->dcap = need;
+    }
+    hps_status rc = hps_mlp_target(B, net->m, T, T0, scale, net->dtarget, stream);
+    if (rc != HPS_OK) return rc;
+    return hps_mlp_grad_target(net, B, b_in, net->dtarget, loss_out, stream);
 }
 
 hps_status hps_mlp_adam_step(hps_mlp* net, float lr, float beta1, float beta2, float eps, void* stream)

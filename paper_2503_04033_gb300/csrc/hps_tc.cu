@@ -1162,13 +1162,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 // the box in elements of format FMT, one 64-byte row of K per box row.
 template <int FMT>
 bool make_map(CUtensorMap* tm, const void* base, int K, long long rows, long long plane_elems, long long box_elems,
-              int nbox, int box_rows)
+              int nbox, int box_rows, long long pitch = 0)
 {
     using Fm = TcFmt<FMT>;
     auto fn = encode_fn();
     if (!fn) return false;
+    if (pitch <= 0) pitch = K;
     cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)Fm::NPL, (cuuint64_t)nbox};
-    cuuint64_t strides[3] = {(cuuint64_t)K * Fm::EB, (cuuint64_t)plane_elems * Fm::EB, (cuuint64_t)box_elems * Fm::EB};
+    cuuint64_t strides[3] = {(cuuint64_t)pitch * Fm::EB, (cuuint64_t)plane_elems * Fm::EB,
+                             (cuuint64_t)box_elems * Fm::EB};
     cuuint32_t boxd[4] = {(cuuint32_t)Fm::KPC, (cuuint32_t)box_rows, 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = FMT == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -1184,12 +1186,13 @@ bool make_map(CUtensorMap* tm, const void* base, int K, long long rows, long lon
 // LU steps (a unit), part i with rows[i] rows per box of NB values, K[i] of
 // them used (only the last part may be ragged), its row 0 at row off[i] of
 // the product.  Pointers and strides are in elements of the plan's operand
-// format.
+// format; ld[i] is part i's row pitch (0: NB).
 struct TcLeft {
     int nparts;
     const void* A[kMaxParts];
     long long rows[kMaxParts], sA[kMaxParts];
     int K[kMaxParts], off[kMaxParts];
+    long long ld[kMaxParts];
 };
 
 TcLeft left1(const void* A, long long rows, long long sA, int K)
@@ -1202,7 +1205,7 @@ TcLeft left1(const void* A, long long rows, long long sA, int K)
 
 template <int FMT, int BNT>
 bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool* fused)
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, bool* fused, long long ldg = 0)
 {
     using Fm = TcFmt<FMT>;
     int K = 0;
@@ -1244,9 +1247,10 @@ bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long
     a.units = a.units_per_box * nbox;
     TcMaps maps{};
     for (int i = 0; i < L.nparts; ++i)
-        if (!make_map<FMT>(&maps.A[i], L.A[i], NB, L.rows[i], L.rows[i] * NB, L.sA[i], nbox, TC_BM)) return false;
+        if (!make_map<FMT>(&maps.A[i], L.A[i], NB, L.rows[i], L.rows[i] * NB, L.sA[i], nbox, TC_BM, L.ld[i]))
+            return false;
     for (int i = L.nparts; i < kMaxParts; ++i) maps.A[i] = maps.A[0];
-    if (!make_map<FMT>(&maps.B, Gp, gK, args.N, g_plane, sGp, nbox, BNT)) return false;
+    if (!make_map<FMT>(&maps.B, Gp, gK, args.N, g_plane, sGp, nbox, BNT, ldg)) return false;
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     a.vec = al16(a.O) && (a.ldo % 4 == 0) && (a.sO % 4 == 0) && (a.N % 4 == 0) &&
             (!a.W || (al16(a.W) && a.ldw % 4 == 0 && a.sW % 4 == 0));
@@ -1283,16 +1287,17 @@ bool launch_tc_update_w(const TcLeft& L, const void* Gp, long long g_plane, long
 
 template <int FMT>
 bool launch_tc_update_f(const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
-                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, int bn_max, bool* fused)
+                        const TcArgs& args, int nbox, cudaStream_t st, bool allow_tma, int bn_max, bool* fused,
+                        long long ldg = 0)
 {
     if (args.N <= TC_BN_NARROW && TcFmt<FMT>::BN > TC_BN_NARROW)
         return launch_tc_update_w<FMT, TC_BN_NARROW>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
-                                                     fused);
+                                                     fused, ldg);
     if ((args.N <= 2 * TC_BN_NARROW || bn_max <= 2 * TC_BN_NARROW) && TcFmt<FMT>::BN > 2 * TC_BN_NARROW)
         return launch_tc_update_w<FMT, 2 * TC_BN_NARROW>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
-                                                         fused);
+                                                         fused, ldg);
     return launch_tc_update_w<FMT, TcFmt<FMT>::BN>(L, Gp, g_plane, sGp, gK, NB, args, nbox, st, allow_tma,
-                                                   fused);
+                                                   fused, ldg);
 }
 
 bool launch_tc_update(int fmt, const TcLeft& L, const void* Gp, long long g_plane, long long sGp, int gK, int NB,
@@ -1376,17 +1381,18 @@ TcArgs targs(float* O, long long ldo, long long sO, int M, int N, int mode, int 
 
 // C = (accumulate ? C : 0) - A B^T per batch entry on tcgen05 with BF16
 // operands (format 3) and FP32 accumulation: A [M][K] and B [N][K] BF16,
-// K-major, batch strides sA, sB; C [M][N] FP32 with row pitch ldc, batch
-// stride sC.  K must be a multiple of 8 (16-byte rows for TMA); false when a
-// tensor map cannot be encoded.
-bool tc_gemm_bf16(int M, int N, int K, const void* A, long long sA, const void* B, long long sB, float* C,
-                  long long ldc, long long sC, bool accumulate, int batch, cudaStream_t st)
+// K-major with row pitches lda, ldb (multiples of 8: 16-byte TMA rows) and
+// batch strides sA, sB; C [M][N] FP32 with row pitch ldc, batch stride sC.
+// K chunks past K read as zeros.  False when a tensor map cannot be encoded.
+bool tc_gemm_bf16(int M, int N, int K, const void* A, long long lda, long long sA, const void* B, long long ldb,
+                  long long sB, float* C, long long ldc, long long sC, bool accumulate, int batch, cudaStream_t st)
 {
-    if (K % 8 != 0) return false;
+    if (K <= 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K) return false;
     if (M <= 0 || N <= 0 || batch <= 0) return true;
     TcLeft L = left1(A, M, sA, K);
+    L.ld[0] = lda;
     TcArgs a = targs(C, ldc, sC, M, N, accumulate ? GM_ACC : GM_SET, 0);
-    return launch_tc_update_f<3>(L, B, (long long)N * K, sB, K, K, a, batch, st, true, 256, nullptr);
+    return launch_tc_update_f<3>(L, B, (long long)N * ldb, sB, K, K, a, batch, st, true, 256, nullptr, ldb);
 }
 
 void tc_test_stall_next(int on) { g_test_stall_next = on ? 1 : 0; }

@@ -13,7 +13,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import (HPS_FP32_IR, LeafKind, hps_dtn_gate, hps_leaf_build_dtn, hps_leaf_sizes, hps_lowrank_dtn,
-               hps_mlp_adam_step, hps_mlp_create, hps_mlp_destroy, hps_mlp_forward, hps_mlp_grad)
+               hps_mlp_adam_step, hps_mlp_create, hps_mlp_destroy, hps_mlp_forward, hps_mlp_grad,
+               hps_mlp_grad_target, hps_mlp_target)
 
 
 class LearnedDtN:
@@ -60,13 +61,16 @@ class LearnedDtN:
     def fit(self, b, T, epochs: int = 20, batch: int = 128, lr: float = 1e-3, seed: int = 0, log=None):
         """Adam on mean (U V^T - (T - T0)/s)^2; s is fixed from the data at the
         start (root-mean-square of T - T0, measured by the loss kernel on a
-        first batch while U V^T is still near zero)."""
+        first batch while U V^T is still near zero).  The FP32 targets
+        (T - T0)/s are formed once for the whole set."""
         import torch
         N = b.shape[0]
         first = min(N, batch)
         self.scale = 1.0
         l0 = hps_mlp_grad(self.net, first, b[:first].contiguous(), T[:first].contiguous(), self.T0, 1.0)
         self.scale = float(np.sqrt(max(l0, 1e-300)))
+        D = torch.empty(T.shape, dtype=torch.float32, device=self.dev)
+        hps_mlp_target(N, self.m, T.contiguous(), self.T0, self.scale, D)
         rng = np.random.default_rng(seed)
         steps = max(1, epochs * ((N + batch - 1) // batch))
         losses, step = [], 0
@@ -75,9 +79,9 @@ class LearnedDtN:
             for i in range(0, N, batch):
                 idx = order[i:i + batch]
                 bb = b.index_select(0, idx).contiguous()
-                tt = T.index_select(0, idx).contiguous()
+                dd = D.index_select(0, idx).contiguous()
                 want = (i == 0)
-                loss = hps_mlp_grad(self.net, idx.numel(), bb, tt, self.T0, self.scale, want_loss=want)
+                loss = hps_mlp_grad_target(self.net, idx.numel(), bb, dd, want_loss=want)
                 cur = lr * 0.5 * (1.0 + np.cos(np.pi * step / steps))
                 hps_mlp_adam_step(self.net, cur)
                 step += 1

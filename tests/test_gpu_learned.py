@@ -169,3 +169,30 @@ def test_learned_correction_gain_and_gated_serving(ctx):
         assert 0 < acc.sum() < len(acc)
     finally:
         model.close()
+
+
+def test_fp32_targets_and_target_gradient():
+    """hps_mlp_target is float((T - T0) * (1/s)) bit for bit, and the
+    gradient from those targets equals hps_mlp_grad's from T and T0."""
+    import torch
+    p, h1, h2, rank, B = 4, 16, 16, 2, 6
+    n, m = H.hps_leaf_sizes(p)
+    net = H.hps_mlp_create(0, p ** 3, h1, h2, m, rank, 5)
+    try:
+        rng = np.random.default_rng(8)
+        b = 1 + 0.3 * rng.standard_normal((B, p ** 3))
+        T = rng.standard_normal((B, m, m))
+        T0 = rng.standard_normal((m, m))
+        s = 0.7
+        D = torch.empty(B, m, m, dtype=torch.float32, device="cuda")
+        H.hps_mlp_target(B, m, _dev(T), _dev(T0), s, D)
+        torch.cuda.synchronize()
+        want = ((T - T0[None]) * (1.0 / s)).astype(np.float32)
+        assert np.array_equal(D.cpu().numpy(), want)
+        l1 = H.hps_mlp_grad(net, B, _dev(b), _dev(T), _dev(T0), s)
+        g1 = H.hps_mlp_copy_params(net, 1).copy()
+        l2 = H.hps_mlp_grad_target(net, B, _dev(b), D)
+        g2 = H.hps_mlp_copy_params(net, 1)
+        assert l1 == l2 and np.array_equal(g1, g2)
+    finally:
+        H.hps_mlp_destroy(net)
