@@ -534,6 +534,28 @@ hps_status hps_leaf_cross_solve(int p, const double h[3], double kappa, int nbox
 hps_status hps_leaf_cross_reconstruct(int p, int nbox, int nrhs, const double* S, const double* v, const double* ub,
                                       double* ui, void* stream);
 
+/* ---- Leaf impedance-to-impedance maps (the ItI variant of HPS that the
+ * two-level scheme adapts to, Sec. 6).  For each box, R [m][m] (complex)
+ * takes impedance data f = du/dn + i eta u on the face nodes to
+ * g = du/dn - i eta u for the solution of the homogeneous equation, from the
+ * kept-node collocation system of Sec. 2.1 / Eq. 2 with i eta added on the
+ * face rows' own unknowns:
+ *     [A_ii, A_ib; A_bi, A_bb + i eta I] [u_i; u_b] = [0; f],  R f = f - 2 i eta u_b.
+ * A_ii is never inverted on its own, so R exists where kappa^2 is a
+ * Dirichlet eigenvalue of the box; elsewhere R = (T - i eta I)(T + i eta I)^{-1}.
+ * FP64: each box's system, in real form (size 2 (n + m), m right-hand
+ * sides), is factored by the batched LU with partial pivoting.
+ * kind: p in 4..16, h, kappa as for hps_leaf_build_dtn, beta NULL (no
+ * first-order term); eta finite, nonzero;
+ * b: device [nbox][p^3]; R: device [nbox][m][m] complex, interleaved (real,
+ * imaginary) FP64 pairs, row r = output face node, column c = input face
+ * node, face order as for T.  box_status: device [nbox] or NULL, as for the
+ * other leaf calls.  Workspace from the stream-ordered allocator
+ * (2 (n + m) x (2 (n + m) + m) doubles per box), released on the stream;
+ * HPS_EINVAL for bad arguments, HPS_ENOMEM when it cannot be allocated. */
+hps_status hps_leaf_iti(const hps_leaf_kind* kind, double eta, int nbox, const double* b, double* R, int* box_status,
+                        void* stream);
+
 /* The collocation operator applied to full nodal fields: out = A u at every
  * interior node of each box, the interior rows of Eq. 2 (-Laplacian by the
  * three grid lines through the node, minus kappa^2 b u), and 0 at the face,

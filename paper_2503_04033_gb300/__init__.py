@@ -31,7 +31,7 @@ __all__ = [
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
     "hps_leaf2d_sizes", "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes",
-    "hps_leaf_cross_nodes", "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct",
+    "hps_leaf_cross_nodes", "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -54,7 +54,7 @@ EXPORTED_SYMBOLS = (
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
     "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes", "hps_leaf_cross_nodes",
-    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct",
+    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti",
 )
 
 # Kernel classes of hps_profile_get.
@@ -138,6 +138,7 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_cross_nodes": (i, [i, dp, dp, dp]),
         "hps_leaf_cross_solve": (i, [i, dp, d, i, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp]),
         "hps_leaf_cross_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
+        "hps_leaf_iti": (i, [kp, d, i, vp, vp, vp, vp]),
         "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
         "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
         "hps_interface_destroy": (None, [vp]),
@@ -477,6 +478,19 @@ def hps_leaf_cross_reconstruct(p: int, nbox: int, nrhs: int, S, v, ub, ui, strea
     _check(load_library().hps_leaf_cross_reconstruct(int(p), int(nbox), int(nrhs), _ptr(S, f64), _ptr(v, f64),
                                                      _ptr(ub, f64), _ptr(ui, f64), _stream(stream)),
            "hps_leaf_cross_reconstruct")
+
+
+def hps_leaf_iti(kind: LeafKind, eta: float, nbox: int, b, R, box_status=None, stream=None) -> None:
+    """Leaf impedance-to-impedance maps R [nbox][m][m] (a complex128 tensor)
+    of boxes b [nbox][p^3] (see include/hps.h)."""
+    import torch
+    if not isinstance(R, int) and R.dtype != torch.complex128:
+        raise ValueError("R must be complex128")
+    f64 = _f64() if not isinstance(b, int) else None
+    _check(load_library().hps_leaf_iti(
+        ctypes.byref(kind), float(eta), int(nbox), _ptr(b, f64), _ptr(R, None),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_iti")
 
 
 def hps_last_refinement(ctx, nbox: int):
