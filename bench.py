@@ -112,7 +112,7 @@ def parse_args():
     ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
                     help="hps_set_option before timing, e.g. LU_UNIT=2 (name without HPS_OPT_)")
     ap.add_argument("--workload", choices=("fourier16", "uneven", "learned", "factored", "timestep", "dirichlet",
-                                                 "accuracy", "leaf2d"),
+                                                 "accuracy", "leaf2d", "cross", "iti"),
                     default="fourier16",
                     help="fourier16: the p=16 headline workload; uneven: 1024 boxes of mixed p/kappa with 32 "
                          "loads; learned: the learned DtN correction at p=12")
@@ -1257,6 +1257,137 @@ def run_leaf2d(args):
     print(json.dumps(line), flush=True)
 
 
+def _fp64_leaf_line(metric, value, ms, args, workload, flops_per_box, worst, fails, clocks, cpu_rate, cpu_n,
+                    extra=None):
+    tflops = value * flops_per_box / 1e12
+    import oracle
+    line = {"metric": metric, "value": value, "unit": "boxes/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "l2": "inputs and workspace larger than L2, no flush"},
+            "tflops": tflops,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 issue rate 152 SMs x 2.07 GHz x 2 FMA/clk (the whole call, its LU "
+                                        "on the CUDA-core FP64 path)"},
+            "rel_err_vs_oracle_max": worst, "box_failures": fails, "clocks": clocks.summary(),
+            "cpu_baseline": {"value": cpu_rate, "unit": "boxes/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{cpu_n} boxes spread over the batch, FP64 oracle, one box at a time"}}
+    if extra:
+        line.update(extra)
+    return line
+
+
+def _timed_steps(step, args, dev):
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / args.steps, clocks
+
+
+def run_cross(args):
+    """Leaves of the curved domain of Sec. 4.3 on Legendre face grids (FP64,
+    cross-term operator through the parameter map): 512 boxes at p = 10
+    (n = 512, m = 486), kappa = |k|; a step is one hps_leaf_cross_solve (T and
+    S of every box).  Parity on a sample against the oracle."""
+    import torch
+    import paper_2503_04033_gb300 as H
+    import oracle
+    from oracle import cross as cx
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p, nbx = 10, 8
+    kappa = float(np.linalg.norm(hi.CURVED_K))
+    h = np.asarray(hi.CURVED_L, dtype=np.float64) / nbx
+    lows = np.stack([np.asarray(hi.CURVED_LO) + h * np.array([i % nbx, (i // nbx) % nbx, i // (nbx * nbx)])
+                     for i in range(nbx ** 3)])
+    nbox = len(lows)
+    n, m = H.hps_leaf_cross_sizes(p)
+    Cs, ds = [], []
+    for lo in lows:
+        Cx, dx = hi.curved_coefficients(H.hps_leaf_nodes(p, lo, h))
+        Cs.append(Cx)
+        ds.append(dx)
+    C = torch.from_numpy(np.ascontiguousarray(np.stack(Cs))).to(dev)
+    d = torch.from_numpy(np.ascontiguousarray(np.stack(ds))).to(dev)
+    bb = torch.ones(nbox, p ** 3, dtype=torch.float64, device=dev)
+    T = torch.empty(nbox, m, m, dtype=torch.float64, device=dev)
+    S = torch.empty(nbox, n, m, dtype=torch.float64, device=dev)
+    st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+
+    def step():
+        H.hps_leaf_cross_solve(p, h, kappa, nbox, C, d, bb, 0, None, T, S, None, None, st)
+
+    ms, clocks = _timed_steps(step, args, dev)
+    sel = np.linspace(0, nbox - 1, 6).astype(int)
+    worst, t0 = 0.0, time.perf_counter()
+    for bx in sel:
+        Cx, dx = hi.curved_coefficients(oracle.node_coords(p, lows[bx], h))
+        To, _, _, _ = cx.leaf_cross(p, h, kappa, Cx, dx, np.ones(p ** 3), None)
+        worst = max(worst, float(np.abs(T[bx].cpu().numpy() - To).max() / np.abs(To).max()))
+    cpu_s = time.perf_counter() - t0
+    flops = 2.0 / 3.0 * n ** 3 + 2.0 * n * n * m
+    line = _fp64_leaf_line("cross-term leaf DtN builds/s at p=10 on Legendre face grids (FP64; T and S per box)",
+                           nbox / (ms / 1e3), ms, args,
+                           f"{nbx}^3 boxes of the curved domain of Sec. 4.3 (parameter map of the box "
+                           f"{tuple(hi.CURVED_LO)} + {tuple(hi.CURVED_L)}), p = {p} (n = {n}, m = {m} Legendre face "
+                           f"nodes), kappa = {kappa:.4f}, full-tensor coefficients of the map",
+                           flops, worst, int((st != 0).sum().item()), clocks, len(sel) / cpu_s, len(sel))
+    print(json.dumps(line), flush=True)
+
+
+def run_iti(args):
+    """Leaf impedance-to-impedance maps (FP64): 512 boxes (8^3, h = 1/8) at
+    p = 8, kappa = 20, eta = kappa, b from the seeded Fourier law; a step is
+    one hps_leaf_iti (R of every box).  Parity on a sample against the
+    oracle."""
+    import torch
+    import paper_2503_04033_gb300 as H
+    import oracle
+    from oracle import iti
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p, kappa = 8, 20.0
+    lows, h = hi.box_grid_lo((8, 8, 8))
+    field = hi.fourier_b_field()
+    b_np = np.stack([field.b(H.hps_leaf_nodes(p, lo, h)) for lo in lows])
+    nbox = len(lows)
+    n, m = H.hps_leaf_sizes(p)
+    kind = H.LeafKind(p, h, kappa)
+    b = torch.from_numpy(b_np).to(dev)
+    R = torch.empty(nbox, m, m, dtype=torch.complex128, device=dev)
+    st = torch.zeros(nbox, dtype=torch.int32, device=dev)
+
+    def step():
+        H.hps_leaf_iti(kind, kappa, nbox, b, R, st)
+
+    ms, clocks = _timed_steps(step, args, dev)
+    sel = np.linspace(0, nbox - 1, 8).astype(int)
+    worst, t0 = 0.0, time.perf_counter()
+    for bx in sel:
+        Ro = iti.leaf_iti(p, h, kappa, b_np[bx], kappa)
+        worst = max(worst, float(np.abs(R[bx].cpu().numpy() - Ro).max() / np.abs(Ro).max()))
+    cpu_s = time.perf_counter() - t0
+    N2 = 2 * (n + m)
+    flops = 2.0 / 3.0 * N2 ** 3 + 2.0 * N2 * N2 * m
+    line = _fp64_leaf_line("leaf ItI maps/s at p=8 (FP64; the real form of the impedance system, size 2(n+m))",
+                           nbox / (ms / 1e3), ms, args,
+                           f"8x8x8 leaf boxes (h=1/8), p = {p} (n = {n}, m = {m}), kappa = {kappa}, eta = kappa, "
+                           "b = the seeded Fourier law (seed 20250304)",
+                           flops, worst, int((st != 0).sum().item()), clocks, len(sel) / cpu_s, len(sel),
+                           {"flops_definition": "2/3 (2N)^3 + 2 (2N)^2 m per box, N = n + m"})
+    print(json.dumps(line), flush=True)
+
+
 def run_timestep(args):
     """Crank-Nicolson steps of the heat equation u_t = kappa_d Lap u on the unit
     cube (u = 0 on its boundary), 4 x 4 x 4 boxes at p = 12, as in Sec. 4.4:
@@ -1484,6 +1615,10 @@ def main():
         run_accuracy(args)
     elif args.workload == "leaf2d":
         run_leaf2d(args)
+    elif args.workload == "cross":
+        run_cross(args)
+    elif args.workload == "iti":
+        run_iti(args)
     else:
         run_ours(args)
 

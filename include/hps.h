@@ -534,6 +534,44 @@ hps_status hps_leaf_cross_solve(int p, const double h[3], double kappa, int nbox
 hps_status hps_leaf_cross_reconstruct(int p, int nbox, int nrhs, const double* S, const double* v, const double* ub,
                                       double* ui, void* stream);
 
+/* ---- Mixed orders (adaptive p; Sec. 6 names adaptivity in the local order
+ * as a setting the two-level scheme can serve).  Box tau of the grid
+ * nb[0] x nb[1] x nb[2] (index bx + nx (by + ny bz), as for
+ * hps_assemble_interface_blocks) has order p_box[tau] (3..24) and its own DtN
+ * map T_tau [m_tau][m_tau] and flux h_tau [m_tau] from hps_leaf_groups.  A
+ * face shared by boxes of different orders carries its unknowns on the face
+ * grid of the higher order (its interior Chebyshev-Lobatto points in each
+ * free direction); the other box sees them through polynomial interpolation
+ * P to its own face nodes and returns its fluxes through the interpolation
+ * Q the other way.  Interface system: sum_tau Q_tau T_tau P_tau u = -sum_tau
+ * Q_tau h_tau on the interface unknowns, the Dirichlet unknowns carrying g.
+ * Numbering: faces as for hps_assemble_interface_blocks (interface faces,
+ * then Dirichlet faces), each face's unknowns contiguous in face-local order
+ * (lower free axis fastest); Dirichlet unknowns after the interface ones.
+ * Host routines, O(q^6) per box for the assembly; HPS_EINVAL for bad sizes,
+ * orders or NULL arrays.
+ * hps_mixed_layout: the counts, face orders face_p [n_faces] and the first
+ * unknown of each face face_off [n_faces + 1] (either may be NULL).
+ * hps_mixed_face_coords: coordinates [n_iface + n_dir][3] of every unknown
+ * for the domain [lo, lo + L].
+ * hps_mixed_assemble: unsummed COO triplets of the interface x interface
+ * (rows, cols, vals) and interface x Dirichlet (rows_d, cols_d: Dirichlet
+ * index, vals_d) blocks from the host maps T[tau]; NULL arrays query nnz and
+ * nnz_d.
+ * hps_mixed_reduce: r [n_iface + n_dir] = sum_tau Q_tau h_tau from host
+ * fluxes hflux[tau] [m_tau].
+ * hps_mixed_traces: ub[tau] [m_tau] = P_tau u for the host vector u
+ * [n_iface + n_dir] (interface solution, then Dirichlet values). */
+hps_status hps_mixed_layout(const int nb[3], const int* p_box, int64_t* n_iface, int64_t* n_dir, int* face_p,
+                            int64_t* face_off);
+hps_status hps_mixed_face_coords(const int nb[3], const int* p_box, const double lo[3], const double L[3],
+                                 double* xyz);
+hps_status hps_mixed_assemble(const int nb[3], const int* p_box, const double* const* T, int64_t* nnz, int64_t* rows,
+                              int64_t* cols, double* vals, int64_t* nnz_d, int64_t* rows_d, int64_t* cols_d,
+                              double* vals_d);
+hps_status hps_mixed_reduce(const int nb[3], const int* p_box, const double* const* hflux, double* r);
+hps_status hps_mixed_traces(const int nb[3], const int* p_box, const double* u, double* const* ub);
+
 /* ---- Leaf impedance-to-impedance maps (the ItI variant of HPS that the
  * two-level scheme adapts to, Sec. 6).  For each box, R [m][m] (complex)
  * takes impedance data f = du/dn + i eta u on the face nodes to

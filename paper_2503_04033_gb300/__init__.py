@@ -32,6 +32,7 @@ __all__ = [
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
     "hps_leaf2d_sizes", "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes",
     "hps_leaf_cross_nodes", "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti",
+    "hps_mixed_layout", "hps_mixed_face_coords", "hps_mixed_assemble", "hps_mixed_reduce", "hps_mixed_traces",
 ]
 
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ENOCONV, HPS_ECUDA, HPS_ETIMEOUT = range(7)
@@ -54,7 +55,8 @@ EXPORTED_SYMBOLS = (
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
     "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes", "hps_leaf_cross_nodes",
-    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti",
+    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti", "hps_mixed_layout",
+    "hps_mixed_face_coords", "hps_mixed_assemble", "hps_mixed_reduce", "hps_mixed_traces",
 )
 
 # Kernel classes of hps_profile_get.
@@ -139,6 +141,11 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_cross_solve": (i, [i, dp, d, i, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp]),
         "hps_leaf_cross_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
         "hps_leaf_iti": (i, [kp, d, i, vp, vp, vp, vp]),
+        "hps_mixed_layout": (i, [vp, vp, vp, vp, vp, vp]),
+        "hps_mixed_face_coords": (i, [vp, vp, vp, vp, vp]),
+        "hps_mixed_assemble": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "hps_mixed_reduce": (i, [vp, vp, vp, vp]),
+        "hps_mixed_traces": (i, [vp, vp, vp, vp]),
         "hps_interface_solve": (i, [vp, i, vp, vp, vp, vp]),
         "hps_interface_info": (i, [vp, ip, ip, ip, ctypes.POINTER(sz)]),
         "hps_interface_destroy": (None, [vp]),
@@ -491,6 +498,93 @@ def hps_leaf_iti(kind: LeafKind, eta: float, nbox: int, b, R, box_status=None, s
         ctypes.byref(kind), float(eta), int(nbox), _ptr(b, f64), _ptr(R, None),
         _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
         _stream(stream)), "hps_leaf_iti")
+
+
+def _mixed_args(nb, p_box):
+    import numpy as np
+    nb3 = np.ascontiguousarray(nb, dtype=np.int32).reshape(3)
+    pb = np.ascontiguousarray(p_box, dtype=np.int32).reshape(-1)
+    if pb.size != int(np.prod(nb3)):
+        raise ValueError("p_box needs one order per box")
+    return nb3, pb
+
+
+def _host_ptrs(arrs):
+    """A C array of host addresses of float64 numpy arrays (kept alive by the caller)."""
+    import numpy as np
+    for a in arrs:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise ValueError("expected contiguous float64 numpy arrays")
+    return (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+
+
+def hps_mixed_layout(nb, p_box):
+    """(n_iface, n_dir, face_p, face_off) of a mixed-order grid (host)."""
+    import numpy as np
+    nb3, pb = _mixed_args(nb, p_box)
+    nx, ny, nz = (int(v) for v in nb3)
+    nfaces = (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1) + 2 * (ny * nz + nx * nz + nx * ny)
+    nfaces = max(nfaces, 1) if min(nx, ny, nz) >= 1 else 1   # bad sizes: the library answers HPS_EINVAL
+    ni, nd = ctypes.c_int64(), ctypes.c_int64()
+    fp = np.zeros(nfaces, dtype=np.int32)
+    fo = np.zeros(nfaces + 1, dtype=np.int64)
+    _check(load_library().hps_mixed_layout(nb3.ctypes.data, pb.ctypes.data, ctypes.byref(ni), ctypes.byref(nd),
+                                           fp.ctypes.data, fo.ctypes.data), "hps_mixed_layout")
+    return ni.value, nd.value, fp, fo
+
+
+def hps_mixed_face_coords(nb, p_box, lo, L):
+    import numpy as np
+    nb3, pb = _mixed_args(nb, p_box)
+    ni, nd, _, _ = hps_mixed_layout(nb, p_box)
+    lo3 = np.ascontiguousarray(lo, dtype=np.float64).reshape(3)
+    L3 = np.ascontiguousarray(L, dtype=np.float64).reshape(3)
+    xyz = np.empty((ni + nd, 3))
+    _check(load_library().hps_mixed_face_coords(nb3.ctypes.data, pb.ctypes.data, lo3.ctypes.data, L3.ctypes.data,
+                                                xyz.ctypes.data), "hps_mixed_face_coords")
+    return xyz
+
+
+def hps_mixed_assemble(nb, p_box, T_boxes):
+    """COO triplets (rows, cols, vals, rows_d, cols_d, vals_d) of the
+    interface system from host DtN maps T_boxes[tau] [m_tau, m_tau]."""
+    import numpy as np
+    nb3, pb = _mixed_args(nb, p_box)
+    Ts = [np.ascontiguousarray(t, dtype=np.float64) for t in T_boxes]
+    ptrs = _host_ptrs(Ts)
+    lib = load_library()
+    nnz, nnz_d = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.hps_mixed_assemble(nb3.ctypes.data, pb.ctypes.data, ptrs, ctypes.byref(nnz), None, None, None,
+                                  ctypes.byref(nnz_d), None, None, None), "hps_mixed_assemble")
+    r, c, v = np.empty(nnz.value, np.int64), np.empty(nnz.value, np.int64), np.empty(nnz.value)
+    rd, cd, vd = np.empty(nnz_d.value, np.int64), np.empty(nnz_d.value, np.int64), np.empty(nnz_d.value)
+    _check(lib.hps_mixed_assemble(nb3.ctypes.data, pb.ctypes.data, ptrs, ctypes.byref(nnz), r.ctypes.data,
+                                  c.ctypes.data, v.ctypes.data, ctypes.byref(nnz_d), rd.ctypes.data, cd.ctypes.data,
+                                  vd.ctypes.data), "hps_mixed_assemble")
+    return r, c, v, rd, cd, vd
+
+
+def hps_mixed_reduce(nb, p_box, h_boxes):
+    """sum_tau Q_tau h_tau [n_iface + n_dir] from host fluxes h_boxes[tau] [m_tau]."""
+    import numpy as np
+    nb3, pb = _mixed_args(nb, p_box)
+    hs = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in h_boxes]
+    ni, nd, _, _ = hps_mixed_layout(nb, p_box)
+    r = np.empty(ni + nd)
+    _check(load_library().hps_mixed_reduce(nb3.ctypes.data, pb.ctypes.data, _host_ptrs(hs), r.ctypes.data),
+           "hps_mixed_reduce")
+    return r
+
+
+def hps_mixed_traces(nb, p_box, u):
+    """Per box the face-node values P_tau u (list of host arrays [m_tau])."""
+    import numpy as np
+    nb3, pb = _mixed_args(nb, p_box)
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    out = [np.empty(6 * (int(p) - 2) ** 2) for p in pb]
+    _check(load_library().hps_mixed_traces(nb3.ctypes.data, pb.ctypes.data, uu.ctypes.data, _host_ptrs(out)),
+           "hps_mixed_traces")
+    return out
 
 
 def hps_last_refinement(ctx, nbox: int):
