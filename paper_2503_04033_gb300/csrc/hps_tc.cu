@@ -40,7 +40,19 @@ namespace {
 constexpr int TC_BM = 128;                                  // tile rows = TMEM lanes
 constexpr uint32_t ROWB = 64;                               // bytes of an operand row in one K chunk (64B swizzle)
 constexpr uint32_t A_TILE = TC_BM * ROWB;                   // 8 KiB per plane
-constexpr int TC_STAGES = 3;
+#ifndef HPS_TC_STAGES
+#define HPS_TC_STAGES 3
+#endif
+#ifndef HPS_TE_PRE
+#define HPS_TE_PRE 5
+#endif
+#ifndef HPS_TE_LA
+#define HPS_TE_LA 3
+#endif
+#ifndef HPS_TC_PRE
+#define HPS_TC_PRE 3
+#endif
+constexpr int TC_STAGES = HPS_TC_STAGES;   // operand stages of the TMA -> MMA ring
 constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 
@@ -91,15 +103,17 @@ static_assert(stage_bytes<0>() == STAGE_BYTES && stage_bytes<1>() == STAGE_BYTES
                   stage_bytes<3>() <= STAGE_BYTES,
               "one shared-memory layout");
 constexpr uint32_t TBUF_FLOATS = 32 * 32;                   // per-epilogue-warp transpose buffer (XOR-swizzled)
-constexpr int TC_PRE = 3;                                   // source chunks in flight per epilogue warp
+constexpr int TC_PRE = HPS_TC_PRE;                          // source chunks in flight per epilogue warp
 constexpr uint32_t EPI_FLOATS = TBUF_FLOATS * (1 + TC_PRE) + 64;   // transpose + source ring + row pointers
-constexpr int TE_PRE = 5;                                  // TMA epilogue: 32 x 32 chunk buffers per warp
-constexpr int TE_LA = 3;                                   // chunks fetched ahead (one store may still read)
+constexpr int TE_PRE = HPS_TE_PRE;                         // TMA epilogue: 32 x 32 chunk buffers per warp
+constexpr int TE_LA = HPS_TE_LA;                           // chunks fetched ahead (TE_PRE - TE_LA - 1 stores may still read)
+static_assert(TE_LA >= 1 && TE_LA < TE_PRE, "the epilogue ring needs a buffer beyond the fetched-ahead chunks");
 constexpr uint32_t TE_CHUNK = 32 * 32 * 4;                 // 4 KiB, 128-byte rows, 128B swizzle
 constexpr size_t EPI_BYTES_CP = (size_t)TC_EPI_WARPS * EPI_FLOATS * 4;
 constexpr size_t EPI_BYTES_TMA = (size_t)TC_EPI_WARPS * TE_PRE * TE_CHUNK;
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + (EPI_BYTES_CP > EPI_BYTES_TMA ? EPI_BYTES_CP : EPI_BYTES_TMA) +
                            1024;
+static_assert(TC_SMEM <= 227 * 1024, "operand stages and epilogue buffers exceed a CTA's shared memory");
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s per wait (TcArgs.wait_ns)
 
 // Tensor maps of one update product: up to eight parts of the left operand
