@@ -183,6 +183,24 @@ def _check(status: int, where: str) -> None:
         raise HpsError(status, where)
 
 
+def _sizes_or_zero(p: int):
+    """(n, m) of order p, or (0, 0) when the library rejects p (the call
+    itself then reports it)."""
+    n, m = ctypes.c_int(), ctypes.c_int()
+    if load_library().hps_leaf_sizes(int(p), ctypes.byref(n), ctypes.byref(m)) != HPS_OK:
+        return 0, 0
+    return n.value, m.value
+
+
+def _need(x, count: int, what: str) -> None:
+    """Refuses (ValueError, before any launch) a tensor with fewer than
+    count elements where the library will read or write count; addresses
+    passed as ints are the caller's responsibility."""
+    import torch
+    if isinstance(x, torch.Tensor) and x.numel() < count:
+        raise ValueError(f"{what}: {x.numel()} elements, the call needs {count}")
+
+
 def _ptr(x, dtype=None):
     """Device address of a tensor (checked), an int, or None."""
     if x is None:
@@ -275,6 +293,11 @@ def hps_workspace_per_box(p: int, prec: int = HPS_FP32_IR) -> int:
 
 def hps_leaf_build_dtn(ctx, kind: LeafKind, nbox: int, b, T, S=None, prec: int = HPS_FP32_IR,
                        box_status=None, stream=None) -> None:
+    n, m = _sizes_or_zero(kind.p)
+    _need(b, nbox * kind.p ** 3, "b")
+    _need(T, nbox * m * m, "T")
+    _need(S, nbox * n * m, "S")
+    _need(box_status, nbox, "box_status")
     f64 = _f64() if not isinstance(b, int) else None
     _check(load_library().hps_leaf_build_dtn(
         ctx, ctypes.byref(kind), int(nbox), _ptr(b, f64), _ptr(T, f64), _ptr(S, f64), int(prec),
@@ -284,6 +307,12 @@ def hps_leaf_build_dtn(ctx, kind: LeafKind, nbox: int, b, T, S=None, prec: int =
 
 def hps_leaf_particular(ctx, kind: LeafKind, nbox: int, nrhs: int, b, f, v, h, prec: int = HPS_FP32_IR,
                         box_status=None, stream=None) -> None:
+    n, m = _sizes_or_zero(kind.p)
+    _need(b, nbox * kind.p ** 3, "b")
+    _need(f, nbox * nrhs * kind.p ** 3, "f")
+    _need(v, nbox * nrhs * n, "v")
+    _need(h, nbox * nrhs * m, "h")
+    _need(box_status, nbox, "box_status")
     f64 = _f64() if not isinstance(b, int) else None
     _check(load_library().hps_leaf_particular(
         ctx, ctypes.byref(kind), int(nbox), int(nrhs), _ptr(b, f64), _ptr(f, f64), _ptr(v, f64), _ptr(h, f64),
@@ -293,6 +322,14 @@ def hps_leaf_particular(ctx, kind: LeafKind, nbox: int, nrhs: int, b, f, v, h, p
 
 def hps_leaf_reconstruct(ctx, kind: LeafKind, nbox: int, nrhs: int, b, S, v, ub, ui, prec: int = HPS_FP32_IR,
                          box_status=None, stream=None) -> None:
+    n, m = _sizes_or_zero(kind.p)
+    if S is None:
+        _need(b, nbox * kind.p ** 3, "b")
+    _need(S, nbox * n * m, "S")
+    _need(v, nbox * nrhs * n, "v")
+    _need(ub, nbox * nrhs * m, "ub")
+    _need(ui, nbox * nrhs * n, "ui")
+    _need(box_status, nbox, "box_status")
     f64 = _f64() if not isinstance(ub, int) else None
     _check(load_library().hps_leaf_reconstruct(
         ctx, ctypes.byref(kind), int(nbox), int(nrhs), _ptr(b, f64), _ptr(S, f64), _ptr(v, f64), _ptr(ub, f64),

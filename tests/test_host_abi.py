@@ -94,3 +94,21 @@ def test_assembly_rejects_bad_arguments(H):
         H.hps_assemble_interface_blocks(2, (2, 2, 2))
     with pytest.raises(H.HpsError):
         H.hps_assemble_interface_blocks(8, (0, 2, 2))
+
+
+def test_binding_refuses_short_arrays_before_any_launch():
+    """The leaf bindings check tensor sizes against nbox and p on the host:
+    a b with fewer than nbox p^3 entries is refused before the library is
+    called (no device access happens)."""
+    import pytest
+    import torch
+    import paper_2503_04033_gb300 as H
+    kind = H.LeafKind(8, 0.125, 10.0)
+    n, m = H.hps_leaf_sizes(8)
+    b = torch.zeros(3 * 8 ** 3, dtype=torch.float64)
+    T = torch.zeros(4 * m * m, dtype=torch.float64)
+    with pytest.raises(ValueError, match="b:"):
+        H.hps_leaf_build_dtn(None, kind, 4, b, T)
+    with pytest.raises(ValueError, match="ub:"):
+        H.hps_leaf_reconstruct(None, kind, 4, 1, torch.zeros(4 * 8 ** 3, dtype=torch.float64), None, None,
+                               torch.zeros(4 * m - 1, dtype=torch.float64), torch.zeros(4 * n, dtype=torch.float64))
