@@ -530,6 +530,10 @@ def hps_leaf_iti(kind: LeafKind, eta: float, nbox: int, b, R, box_status=None, s
     import torch
     if not isinstance(R, int) and R.dtype != torch.complex128:
         raise ValueError("R must be complex128")
+    n, m = _sizes_or_zero(kind.p)
+    _need(b, nbox * kind.p ** 3, "b")
+    _need(R, nbox * m * m, "R")
+    _need(box_status, nbox, "box_status")
     f64 = _f64() if not isinstance(b, int) else None
     _check(load_library().hps_leaf_iti(
         ctypes.byref(kind), float(eta), int(nbox), _ptr(b, f64), _ptr(R, None),
@@ -702,6 +706,15 @@ def hps_leaf_groups(ctx, groups, prec: int = HPS_FP32_IR, stream=None) -> None:
         arr[i].h = (ctypes.c_double * 3)(*[float(x) for x in hh])
         arr[i].nbox = int(len(kap))
         arr[i].kappa = kap.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        n_g, m_g = _sizes_or_zero(int(g["p"]))
+        nb_g, nr_g = int(len(kap)), (int(v.shape[1]) if v is not None else 0)
+        _need(g["b"], nb_g * int(g["p"]) ** 3, "b")
+        _need(g.get("T"), nb_g * m_g * m_g, "T")
+        _need(g.get("S"), nb_g * n_g * m_g, "S")
+        _need(g.get("f"), nb_g * nr_g * int(g["p"]) ** 3, "f")
+        _need(v, nb_g * nr_g * n_g, "v")
+        _need(g.get("hflux"), nb_g * nr_g * m_g, "hflux")
+        _need(g.get("box_status"), nb_g, "box_status")
         arr[i].b = _ptr(g["b"], f64)
         arr[i].T = _ptr(g.get("T"), f64)
         arr[i].S = _ptr(g.get("S"), f64)
