@@ -530,10 +530,11 @@ def hps_leaf_iti(kind: LeafKind, eta: float, nbox: int, b, R, box_status=None, s
     import torch
     if not isinstance(R, int) and R.dtype != torch.complex128:
         raise ValueError("R must be complex128")
-    n, m = _sizes_or_zero(kind.p)
-    _need(b, nbox * kind.p ** 3, "b")
-    _need(R, nbox * m * m, "R")
-    _need(box_status, nbox, "box_status")
+    if 4 <= kind.p <= 16:                  # the orders hps_leaf_iti accepts (others: HPS_EINVAL from the call)
+        n, m = _sizes_or_zero(kind.p)
+        _need(b, nbox * kind.p ** 3, "b")
+        _need(R, nbox * m * m, "R")
+        _need(box_status, nbox, "box_status")
     f64 = _f64() if not isinstance(b, int) else None
     _check(load_library().hps_leaf_iti(
         ctypes.byref(kind), float(eta), int(nbox), _ptr(b, f64), _ptr(R, None),
