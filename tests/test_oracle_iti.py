@@ -85,3 +85,49 @@ def test_iti_large_eta_limit():
     p, h, kappa = 6, np.array([0.25, 0.25, 0.25]), 5.0
     R = iti.leaf_iti(p, h, kappa, np.ones(p ** 3), 1e9)
     assert np.abs(R + np.eye(R.shape[0])).max() < 1e-5
+
+
+def _resonant_setup(p=8):
+    """2 x 2 x 2 boxes of side 1/2 with kappa^2 the smallest eigenvalue of the
+    interior block of a b = 1 box; only the corner box at the origin has
+    b = 1 (the others 1.25), so the whole domain is not resonant."""
+    from oracle.global_solve import InterfaceGrid
+    grid = InterfaceGrid(p, (2, 2, 2))
+    n, m = oracle.sizes(p)
+    Aii = oracle.leaf_matrix(p, grid.h, 0.0, np.ones(p ** 3))[:n, :n]
+    ev = np.linalg.eigvals(Aii)
+    kappa = float(np.sqrt(np.sort(ev[np.abs(ev.imag) < 1e-8].real)[0]))
+    b_fn = lambda x: np.where((x[:, 0] < 0.5 - 1e-12) & (x[:, 1] < 0.5 - 1e-12) & (x[:, 2] < 0.5 - 1e-12), 1.0, 1.25)
+    return grid, kappa, b_fn
+
+
+def test_iti_global_solve_equals_the_dtn_solve():
+    """Away from resonances the two-level solve on ItI maps gives the DtN
+    solve's discrete solution (variable b, a load, Dirichlet data)."""
+    from oracle.global_solve import InterfaceGrid, hps_solve
+    grid = InterfaceGrid(6, (2, 2, 2))
+    b_fn = lambda x: 1 + 0.3 * np.sin(x[:, 0] + 2 * x[:, 1])
+    f_fn = lambda x: np.cos(x[:, 2])
+    g_fn = lambda x: x[:, 0] * x[:, 1] + np.sin(x[:, 2])
+    rd = hps_solve(grid, 5.0, b_fn, f_fn, g_fn)
+    for eta in (5.0, 2.0):
+        ri = iti.iti_solve(grid, 5.0, eta, b_fn, f_fn, g_fn)
+        scale = max(np.abs(u).max() for u in rd["u_int"])
+        assert max(np.abs(a - b).max() for a, b in zip(ri["u_int"], rd["u_int"])) < 1e-11 * scale
+
+
+def test_iti_global_solve_survives_a_resonant_box():
+    """With one box at a Dirichlet resonance the DtN solve is wrong by
+    several per cent (its A_ii is singular to rounding), while the ItI solve
+    equals the dense collocation solve of the whole system, which never
+    inverts a box's interior block."""
+    from oracle.global_solve import dense_global_solve, hps_solve
+    grid, kappa, b_fn = _resonant_setup()
+    zero = lambda x: np.zeros(len(x))
+    g_fn = lambda x: np.cos(3 * x[:, 0] + x[:, 1]) + x[:, 2]
+    ref = np.asarray(dense_global_solve(grid, kappa, b_fn, zero, g_fn)["u_int"])
+    scale = np.abs(ref).max()
+    ri = np.array(iti.iti_solve(grid, kappa, kappa, b_fn, zero, g_fn)["u_int"])
+    assert np.abs(ri - ref).max() < 1e-12 * scale
+    rd = np.array(hps_solve(grid, kappa, b_fn, zero, g_fn)["u_int"])
+    assert np.abs(rd - ref).max() > 1e-3 * scale
