@@ -594,6 +594,42 @@ hps_status hps_mixed_traces(const int nb[3], const int* p_box, const double* u, 
 hps_status hps_leaf_iti(const hps_leaf_kind* kind, double eta, int nbox, const double* b, double* R, int* box_status,
                         void* stream);
 
+/* The same system with more outputs (all complex, interleaved, device;
+ * NULL where not wanted): R as above; S [nbox][n][m], the interior solution
+ * for unit incoming impedance data; for nrhs (0..256) loads f [nbox][nrhs][p^3]
+ * (real, interior values read) solved with zero incoming impedance data, the
+ * interior solution v [nbox][nrhs][n] and its outgoing impedance data
+ * hout [nbox][nrhs][m] = -2 i eta u_b.  HPS_EINVAL as for hps_leaf_iti, or
+ * when nothing is requested. */
+hps_status hps_leaf_iti_solve(const hps_leaf_kind* kind, double eta, int nbox, const double* b, int nrhs,
+                              const double* f, double* R, double* S, double* v, double* hout, int* box_status,
+                              void* stream);
+
+/* Box solutions from incoming impedance data fin [nbox][nrhs][m] (device,
+ * complex): u_i = S fin + v into ui [nbox][nrhs][n] (needs S; v may be
+ * NULL) and the face values u_b = (fin - (R fin + hout)) / (2 i eta) into
+ * ub [nbox][nrhs][m] (needs R; hout may be NULL); either output may be
+ * NULL, not both. */
+hps_status hps_leaf_iti_reconstruct(int p, double eta, int nbox, int nrhs, const double* R, const double* S,
+                                    const double* v, const double* hout, const double* fin, double* ui, double* ub,
+                                    void* stream);
+
+/* Host assembly of the two-level system on ItI maps for an nb[0] x nb[1] x
+ * nb[2] grid of order-p boxes (4..16; box index bx + nx (by + ny bz)).
+ * Unknowns: each box's incoming impedance data on its m face nodes, index
+ * box m + r.  A face shared by boxes tau and sigma: the incoming data of one
+ * side is minus the outgoing data of the other, f_tau + R_sigma f_sigma =
+ * -hout_sigma at the matching node (same within-face index on the opposite
+ * local face); a Dirichlet face (u = g): (R_tau - I) f_tau = -hout_tau -
+ * 2 i eta g.  hps_iti_assemble: unsummed COO triplets (complex vals,
+ * interleaved) from the host maps R [nbox][m][m]; NULL arrays query nnz.
+ * hps_iti_rhs: rhs [nbox m] (complex) from host hout [nbox][m] (one load,
+ * or NULL) and the real Dirichlet values g_face [nbox][m] at each box's face
+ * nodes (read on boundary faces only; NULL for g = 0). */
+hps_status hps_iti_assemble(int p, const int nb[3], const double* R, int64_t* nnz, int64_t* rows, int64_t* cols,
+                            double* vals);
+hps_status hps_iti_rhs(int p, const int nb[3], double eta, const double* hout, const double* g_face, double* rhs);
+
 /* The collocation operator applied to full nodal fields: out = A u at every
  * interior node of each box, the interior rows of Eq. 2 (-Laplacian by the
  * three grid lines through the node, minus kappa^2 b u), and 0 at the face,

@@ -32,6 +32,7 @@ __all__ = [
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
     "hps_leaf2d_sizes", "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes",
     "hps_leaf_cross_nodes", "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti",
+    "hps_leaf_iti_solve", "hps_leaf_iti_reconstruct", "hps_iti_assemble", "hps_iti_rhs",
     "hps_mixed_layout", "hps_mixed_face_coords", "hps_mixed_assemble", "hps_mixed_reduce", "hps_mixed_traces",
 ]
 
@@ -55,7 +56,8 @@ EXPORTED_SYMBOLS = (
     "hps_interface_factor", "hps_interface_solve", "hps_interface_info", "hps_interface_destroy",
     "hps_interface_plan", "hps_interface_last_refinement", "hps_leaf2d_solve", "hps_leaf2d_reconstruct",
     "hps_interface2d_factor", "hps_interface2d_plan", "hps_leaf_cross_sizes", "hps_leaf_cross_nodes",
-    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti", "hps_mixed_layout",
+    "hps_leaf_cross_solve", "hps_leaf_cross_reconstruct", "hps_leaf_iti", "hps_leaf_iti_solve",
+    "hps_leaf_iti_reconstruct", "hps_iti_assemble", "hps_iti_rhs", "hps_mixed_layout",
     "hps_mixed_face_coords", "hps_mixed_assemble", "hps_mixed_reduce", "hps_mixed_traces",
 )
 
@@ -141,6 +143,10 @@ def load_library() -> ctypes.CDLL:
         "hps_leaf_cross_solve": (i, [i, dp, d, i, vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp]),
         "hps_leaf_cross_reconstruct": (i, [i, i, i, vp, vp, vp, vp, vp]),
         "hps_leaf_iti": (i, [kp, d, i, vp, vp, vp, vp]),
+        "hps_leaf_iti_solve": (i, [kp, d, i, vp, i, vp, vp, vp, vp, vp, vp, vp]),
+        "hps_leaf_iti_reconstruct": (i, [i, d, i, i, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "hps_iti_assemble": (i, [i, vp, vp, vp, vp, vp, vp]),
+        "hps_iti_rhs": (i, [i, vp, d, vp, vp, vp]),
         "hps_mixed_layout": (i, [vp, vp, vp, vp, vp, vp]),
         "hps_mixed_face_coords": (i, [vp, vp, vp, vp, vp]),
         "hps_mixed_assemble": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -626,6 +632,76 @@ def hps_mixed_traces(nb, p_box, u):
     out = [np.empty(6 * (int(p) - 2) ** 2) for p in pb]
     _check(load_library().hps_mixed_traces(nb3.ctypes.data, pb.ctypes.data, uu.ctypes.data, _host_ptrs(out)),
            "hps_mixed_traces")
+    return out
+
+
+def hps_leaf_iti_solve(kind: LeafKind, eta: float, nbox: int, b, nrhs: int = 0, f=None, R=None, S=None, v=None,
+                       hout=None, box_status=None, stream=None) -> None:
+    """ItI maps with the interior operator and loads (complex128 outputs; see include/hps.h)."""
+    import torch
+    for name, t in (("R", R), ("S", S), ("v", v), ("hout", hout)):
+        if t is not None and not isinstance(t, int) and t.dtype != torch.complex128:
+            raise ValueError(f"{name} must be complex128")
+    if 4 <= kind.p <= 16:
+        n, m = _sizes_or_zero(kind.p)
+        _need(b, nbox * kind.p ** 3, "b")
+        _need(f, nbox * nrhs * kind.p ** 3, "f")
+        _need(R, nbox * m * m, "R")
+        _need(S, nbox * n * m, "S")
+        _need(v, nbox * nrhs * n, "v")
+        _need(hout, nbox * nrhs * m, "hout")
+        _need(box_status, nbox, "box_status")
+    f64 = _f64()
+    _check(load_library().hps_leaf_iti_solve(
+        ctypes.byref(kind), float(eta), int(nbox), _ptr(b, f64), int(nrhs), _ptr(f, f64), _ptr(R, None),
+        _ptr(S, None), _ptr(v, None), _ptr(hout, None),
+        _ptr(box_status, _i32() if box_status is not None and not isinstance(box_status, int) else None),
+        _stream(stream)), "hps_leaf_iti_solve")
+
+
+def hps_leaf_iti_reconstruct(p: int, eta: float, nbox: int, nrhs: int, R, S, v, hout, fin, ui=None, ub=None,
+                             stream=None) -> None:
+    if 4 <= p <= 16:
+        n, m = _sizes_or_zero(p)
+        _need(fin, nbox * nrhs * m, "fin")
+        _need(ui, nbox * nrhs * n, "ui")
+        _need(ub, nbox * nrhs * m, "ub")
+        _need(R, nbox * m * m, "R")
+        _need(S, nbox * n * m, "S")
+    _check(load_library().hps_leaf_iti_reconstruct(int(p), float(eta), int(nbox), int(nrhs), _ptr(R, None),
+                                                   _ptr(S, None), _ptr(v, None), _ptr(hout, None), _ptr(fin, None),
+                                                   _ptr(ui, None), _ptr(ub, None), _stream(stream)),
+           "hps_leaf_iti_reconstruct")
+
+
+def hps_iti_assemble(p: int, nb, R_host):
+    """COO (rows, cols, vals complex) of the two-level ItI system from host
+    maps R_host [nbox, m, m] (complex128 numpy)."""
+    import numpy as np
+    nb3 = np.ascontiguousarray(nb, dtype=np.int32).reshape(3)
+    Rh = np.ascontiguousarray(R_host, dtype=np.complex128)
+    lib = load_library()
+    nnz = ctypes.c_int64()
+    _check(lib.hps_iti_assemble(int(p), nb3.ctypes.data, Rh.ctypes.data, ctypes.byref(nnz), None, None, None),
+           "hps_iti_assemble")
+    r, c = np.empty(nnz.value, np.int64), np.empty(nnz.value, np.int64)
+    v = np.empty(nnz.value, np.complex128)
+    _check(lib.hps_iti_assemble(int(p), nb3.ctypes.data, Rh.ctypes.data, ctypes.byref(nnz), r.ctypes.data,
+                                c.ctypes.data, v.ctypes.data), "hps_iti_assemble")
+    return r, c, v
+
+
+def hps_iti_rhs(p: int, nb, eta: float, hout_host=None, g_face=None):
+    """rhs [nbox m] (complex128) of the two-level ItI system (host)."""
+    import numpy as np
+    nb3 = np.ascontiguousarray(nb, dtype=np.int32).reshape(3)
+    nbox = int(np.prod(nb3))
+    m = 6 * (int(p) - 2) ** 2
+    ho = None if hout_host is None else np.ascontiguousarray(hout_host, dtype=np.complex128).reshape(nbox, m)
+    gf = None if g_face is None else np.ascontiguousarray(g_face, dtype=np.float64).reshape(nbox, m)
+    out = np.empty(nbox * m, np.complex128)
+    _check(load_library().hps_iti_rhs(int(p), nb3.ctypes.data, float(eta), None if ho is None else ho.ctypes.data,
+                                      None if gf is None else gf.ctypes.data, out.ctypes.data), "hps_iti_rhs")
     return out
 
 

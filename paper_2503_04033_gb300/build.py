@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libhps.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hps_abi.cu", "hps_lu.cu", "hps_tc.cu", "hps_learned.cu", "hps_noalloc.cu", "hps_iface.cu", "hps_leaf2d.cu", "hps_cross.cu", "hps_iti.cu", "hps_assemble.cpp",
-           "hps_iface_plan.cpp", "hps_mixed.cpp"]
+           "hps_iface_plan.cpp", "hps_mixed.cpp", "hps_iti_host.cpp"]
 
 
 def _nvcc() -> str:

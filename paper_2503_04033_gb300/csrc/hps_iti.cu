@@ -39,8 +39,8 @@ constexpr int kItiRows = 4;   // rows per CTA of the build
 // [3][p][p] (axis-major), b [nbox][p^3].
 __global__ void __launch_bounds__(256)
 k_build_iti(int p, int n, int m, const double* __restrict__ D, const double* __restrict__ D2, double kappa2,
-            double eta, const double* __restrict__ b, double* __restrict__ M, long long ldm, long long sM,
-            int* status)
+            double eta, const double* __restrict__ b, int nrhs, const double* __restrict__ f, double* __restrict__ M,
+            long long ldm, long long sM, int* status)
 {
     const int box = blockIdx.y;
     const int N = n + m, N2 = 2 * N;
@@ -89,6 +89,14 @@ k_build_iti(int p, int n, int m, const double* __restrict__ D, const double* __r
                 }
                 row[off + col(ii, jj, kk)] = v;
             }
+            if (half == 0) {   // the loads' interior values: right-hand sides m .. m + nrhs - 1
+                const long long gi = i + p * j + (long long)pp * k;
+                for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+                    const double fv = __ldg(f + ((long long)box * nrhs + c) * p * pp + gi);
+                    if (!isfinite(fv)) status[box] = HPS_EINVAL;
+                    row[N2 + m + c] = fv;
+                }
+            }
         } else {
             const int r = lr - n, f = r / qq, s = r - f * qq, axis = f >> 1;
             const int a = s % q + 1, c = s / q + 1, e = (f & 1) ? p - 1 : 0;
@@ -131,26 +139,115 @@ __global__ void k_extract_iti(int n, int m, const double* __restrict__ M, long l
     }
 }
 
+// S[box][i][c] = x_r[i][c] + i x_i[i][c] (interior rows, unit impedance data).
+__global__ void k_extract_iti_s(int n, int m, const double* __restrict__ M, long long ldm, long long sM,
+                                double* __restrict__ S)
+{
+    const int box = blockIdx.y;
+    const int N = n + m;
+    const long long nm = (long long)n * m;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nm; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / m), c = (int)(e - (long long)i * m);
+        const double* X = M + box * sM + 2 * N;
+        double* o = S + 2 * (box * nm + e);
+        o[0] = X[(long long)i * ldm + c];
+        o[1] = X[(long long)(N + i) * ldm + c];
+    }
+}
+
+// Loads: v[box][c][i] = x[i][m + c] (interior) and hout[box][c][r] =
+// -2 i eta x[n + r][m + c] (the outgoing impedance with zero incoming data).
+__global__ void k_extract_iti_loads(int n, int m, int nrhs, const double* __restrict__ M, long long ldm, long long sM,
+                                    double eta, double* __restrict__ v, double* __restrict__ hout)
+{
+    const int box = blockIdx.y;
+    const int N = n + m;
+    const long long tot = (long long)nrhs * (n + m);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / (n + m)), r = (int)(e - (long long)c * (n + m));
+        const double* X = M + box * sM + 2 * N + m + c;
+        const double xr = X[(long long)r * ldm], xi = X[(long long)(N + r) * ldm];
+        if (r < n) {
+            if (v) {
+                double* o = v + 2 * (((long long)box * nrhs + c) * n + r);
+                o[0] = xr;
+                o[1] = xi;
+            }
+        } else if (hout) {
+            double* o = hout + 2 * (((long long)box * nrhs + c) * m + (r - n));
+            o[0] = 2.0 * eta * xi;
+            o[1] = -2.0 * eta * xr;
+        }
+    }
+}
+
+// Box solution from incoming impedance data fin [box][c][m] (complex): the
+// interior u_i = S fin + v and the face values u_b = (fin - g) / (2 i eta),
+// g = R fin + hout.  One CTA per (row block, load, box); rows 0..n-1 interior,
+// n..n+m-1 face (complex arithmetic written out on (re, im) pairs).
+__global__ void __launch_bounds__(256)
+k_iti_reconstruct(int n, int m, int nrhs, double eta, const double* __restrict__ R, const double* __restrict__ S,
+                  const double* __restrict__ v, const double* __restrict__ hout, const double* __restrict__ fin,
+                  double* __restrict__ ui, double* __restrict__ ub)
+{
+    const int c = blockIdx.y, box = blockIdx.z;
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * warps + (threadIdx.x >> 5);
+    if (row >= n + m) return;
+    const bool face = row >= n;
+    if (face ? !ub : !ui) return;
+    const int r = face ? row - n : row;
+    const double* A = face ? R + 2 * (((long long)box * m + r) * m) : S + 2 * (((long long)box * n + r) * m);
+    const double* x = fin + 2 * (((long long)box * nrhs + c) * m);
+    double ar = 0.0, ai = 0.0;
+    for (int l = lane; l < m; l += 32) {
+        const double a0 = A[2 * l], a1 = A[2 * l + 1], x0 = x[2 * l], x1 = x[2 * l + 1];
+        ar = fma(a0, x0, fma(-a1, x1, ar));
+        ai = fma(a0, x1, fma(a1, x0, ai));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, off);
+        ai += __shfl_xor_sync(0xffffffffu, ai, off);
+    }
+    if (lane != 0) return;
+    if (!face) {
+        double* o = ui + 2 * (((long long)box * nrhs + c) * n + r);
+        const double* vv = v ? v + 2 * (((long long)box * nrhs + c) * n + r) : nullptr;
+        o[0] = ar + (vv ? vv[0] : 0.0);
+        o[1] = ai + (vv ? vv[1] : 0.0);
+    } else {
+        // g = R fin + hout; u_b = (fin - g) / (2 i eta) = -i (fin - g) / (2 eta)
+        const double* hh = hout ? hout + 2 * (((long long)box * nrhs + c) * m + r) : nullptr;
+        const double gr = ar + (hh ? hh[0] : 0.0), gim = ai + (hh ? hh[1] : 0.0);
+        const double dr = x[2 * r] - gr, di = x[2 * r + 1] - gim;
+        double* o = ub + 2 * (((long long)box * nrhs + c) * m + r);
+        o[0] = di / (2.0 * eta);
+        o[1] = -dr / (2.0 * eta);
+    }
+}
+
 }  // namespace
 
 extern "C" {
 
-hps_status hps_leaf_iti(const hps_leaf_kind* kind, double eta, int nbox, const double* b, double* R, int* box_status,
-                        void* stream)
+hps_status hps_leaf_iti_solve(const hps_leaf_kind* kind, double eta, int nbox, const double* b, int nrhs,
+                              const double* f, double* R, double* S, double* v, double* hout, int* box_status,
+                              void* stream)
 {
     if (!kind || kind->p < 4 || kind->p > kItiMaxP || !std::isfinite(kind->kappa) || !std::isfinite(eta) ||
-        !(eta != 0.0) || nbox < 0 || kind->beta)
+        !(eta != 0.0) || nbox < 0 || nrhs < 0 || nrhs > 256 || kind->beta)
         return HPS_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!(kind->h[a] > 0.0) || !std::isfinite(kind->h[a])) return HPS_EINVAL;
     if (nbox == 0) return HPS_OK;
-    if (!b || !R) return HPS_EINVAL;
+    if (!b || (!R && !S && nrhs == 0) || (nrhs > 0 && (!f || (!v && !hout)))) return HPS_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int p = kind->p, q = p - 2, n = q * q * q, m = 6 * q * q, N2 = 2 * (n + m), pp = p * p;
     std::vector<double> Dhat(pp), tab(6 * pp);
     hps::cheb_diff(p, Dhat.data());
     hps::geometry_tables(p, Dhat.data(), kind->h, tab.data(), tab.data() + 3 * pp);
-    hps::Plan PL = hps::make_plan(N2, m, HPS_FP64, 0, false, false);
+    hps::Plan PL = hps::make_plan(N2, m + nrhs, HPS_FP64, 0, false, false);
     const size_t tab_bytes = hps::align_up(sizeof(double) * tab.size(), 256);
     const size_t st_bytes = hps::align_up(sizeof(int) * (size_t)nbox, 256);
     const size_t bytes = tab_bytes + st_bytes + PL.per_box * (size_t)nbox;
@@ -167,16 +264,48 @@ hps_status hps_leaf_iti(const hps_leaf_kind* kind, double eta, int nbox, const d
         rc = HPS_ECUDA;
     if (rc == HPS_OK) {
         k_build_iti<<<dim3((unsigned)((N2 + kItiRows - 1) / kItiRows), (unsigned)nbox), 256, 0, st>>>(
-            p, n, m, dtab, dtab + 3 * pp, kind->kappa * kind->kappa, eta, b, w.M, PL.ldm, w.sM, status);
+            p, n, m, dtab, dtab + 3 * pp, kind->kappa * kind->kappa, eta, b, nrhs, f, w.M, PL.ldm, w.sM, status);
         hps::lu_factor<double>(PL, w, nbox, status, st);
-        hps::lu_backward<double>(PL, w, nbox, N2, m, nullptr, st);
-        const long long mm = (long long)m * m;
-        k_extract_iti<<<dim3((unsigned)std::min<long long>((mm + 255) / 256, 1024), (unsigned)nbox), 256, 0, st>>>(
-            n, m, w.M, PL.ldm, w.sM, eta, R);
+        hps::lu_backward<double>(PL, w, nbox, N2, m + nrhs, nullptr, st);
+        const long long mm = (long long)m * m, nm = (long long)n * m;
+        if (R)
+            k_extract_iti<<<dim3((unsigned)std::min<long long>((mm + 255) / 256, 1024), (unsigned)nbox), 256, 0, st>>>(
+                n, m, w.M, PL.ldm, w.sM, eta, R);
+        if (S)
+            k_extract_iti_s<<<dim3((unsigned)std::min<long long>((nm + 255) / 256, 1024), (unsigned)nbox), 256, 0,
+                              st>>>(n, m, w.M, PL.ldm, w.sM, S);
+        if (nrhs > 0) {
+            const long long tot = (long long)nrhs * (n + m);
+            k_extract_iti_loads<<<dim3((unsigned)std::min<long long>((tot + 255) / 256, 1024), (unsigned)nbox), 256, 0,
+                                  st>>>(n, m, nrhs, w.M, PL.ldm, w.sM, eta, v, hout);
+        }
         if (cudaGetLastError() != cudaSuccess) rc = HPS_ECUDA;
     }
     if (cudaFreeAsync(ws, st) != cudaSuccess && rc == HPS_OK) rc = HPS_ECUDA;
     return rc;
+}
+
+hps_status hps_leaf_iti(const hps_leaf_kind* kind, double eta, int nbox, const double* b, double* R, int* box_status,
+                        void* stream)
+{
+    if (!R && nbox > 0) return HPS_EINVAL;
+    return hps_leaf_iti_solve(kind, eta, nbox, b, 0, nullptr, R, nullptr, nullptr, nullptr, box_status, stream);
+}
+
+hps_status hps_leaf_iti_reconstruct(int p, double eta, int nbox, int nrhs, const double* R, const double* S,
+                                    const double* v, const double* hout, const double* fin, double* ui, double* ub,
+                                    void* stream)
+{
+    if (p < 4 || p > kItiMaxP || !std::isfinite(eta) || !(eta != 0.0) || nbox < 0 || nrhs < 1 || nrhs > 256)
+        return HPS_EINVAL;
+    if (nbox == 0) return HPS_OK;
+    if (!fin || (!ui && !ub) || (ui && !S) || (ub && !R)) return HPS_EINVAL;
+    const int q = p - 2, n = q * q * q, m = 6 * q * q;
+    const int warps = 8;
+    dim3 grd((unsigned)((n + m + warps - 1) / warps), (unsigned)nrhs, (unsigned)nbox);
+    k_iti_reconstruct<<<grd, 32 * warps, 0, static_cast<cudaStream_t>(stream)>>>(n, m, nrhs, eta, R, S, v, hout, fin,
+                                                                                  ui, ub);
+    return cudaGetLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 }  // extern "C"
