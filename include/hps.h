@@ -142,6 +142,9 @@ typedef enum {
                                    values (hi + lo, 22 bits as with 3 x TF32) under exact power-of-two scales
                                    of the left operand's K columns and the right operand's columns, which
                                    halves the operand bytes and doubles the MMA rate; 0: 3 x TF32 */
+    HPS_OPT_GROUPS_CONCURRENT = 14, /* 1 (default): the groups of one hps_leaf_groups call run concurrently, each
+                                   on its own stream and workspace slice, when the whole batch's workspace
+                                   fits at once (else one after another, chunked); 0: one after another */
     HPS_OPT_TEST_SINGULAR_BOX = 100, /* test hook: zero row 0 of A_ii of this box index (-1 = off),
                                         which makes that box exactly singular (host-side fault injection) */
     HPS_OPT_TEST_TC_TIMEOUT = 101    /* test hook: 1 arms it once.  In the next FP32_IR / BF16_IR call on the

@@ -23,7 +23,7 @@ __all__ = [
     "hps_leaf_build_dtn", "hps_leaf_particular", "hps_leaf_reconstruct", "hps_assemble_interface_blocks",
     "hps_last_refinement", "hps_profile_enable", "hps_profile_reset", "hps_profile_get", "hps_status_string",
     "EXPORTED_SYMBOLS", "KERNEL_CLASSES", "hps_leaf_build_dtn_noalloc", "hps_leaf_groups", "LeafGroup",
-    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_LU_UNIT", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
+    "HPS_OPT_AUTOTUNE", "HPS_OPT_GRAPHS", "HPS_OPT_TC_EPILOGUE", "HPS_OPT_LU_UNIT", "HPS_OPT_TC_FUSE", "HPS_OPT_RESIDUAL_DF", "HPS_OPT_FP16_OPERANDS", "HPS_OPT_GROUPS_CONCURRENT", "hps_mlp_create", "hps_mlp_destroy", "hps_mlp_num_params",
     "hps_mlp_copy_params", "hps_mlp_forward", "hps_mlp_grad", "hps_mlp_target", "hps_mlp_grad_target",
     "hps_mlp_adam_step", "hps_lowrank_dtn",
     "hps_dtn_gate", "hps_selftest_conversions", "hps_leaf_factor", "hps_leaf_solve_factored",
@@ -41,6 +41,7 @@ HPS_FP64, HPS_FP32_IR, HPS_BF16_IR = 0, 1, 2
 HPS_OPT_IR_MAX_ITERS, HPS_OPT_IR_TOL, HPS_OPT_BLOCK, HPS_OPT_TENSOR_CORES, HPS_OPT_SYNC = 1, 2, 3, 4, 5
 HPS_OPT_AUTOTUNE, HPS_OPT_GRAPHS, HPS_OPT_TC_EPILOGUE, HPS_OPT_LU_UNIT, HPS_OPT_TC_FUSE = 6, 7, 8, 10, 11
 HPS_OPT_RESIDUAL_DF, HPS_OPT_FP16_OPERANDS = 12, 13
+HPS_OPT_GROUPS_CONCURRENT = 14
 HPS_OPT_TEST_SINGULAR_BOX = 100
 HPS_OPT_TEST_TC_TIMEOUT = 101
 

@@ -95,6 +95,11 @@ struct hps_ctx {
     int tc_fuse = -1;           // -1: fused gathers where they measured faster, 0: never, 1: backward sweeps
     int res_df = 3;             // residual precision (HPS_OPT_RESIDUAL_DF): double-float, routed per box
     int fp16_ops = 1;           // FP32_IR tensor-core products on scaled 2 x FP16 operands (format 2)
+    int concurrent = 1;         // HPS_OPT_GROUPS_CONCURRENT: the groups of a mixed batch on their own streams
+    std::vector<cudaStream_t> side;   // one stream per group of a concurrent mixed batch
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t side_fork = nullptr;
+    std::vector<size_t> ws_off;       // workspace offset of each job of the current call (concurrent layout)
     int use_tc = 1;
     int sync = 0;
     int zero_row_box = -1;
@@ -421,10 +426,40 @@ hps_status ensure_workspace(hps_ctx* ctx, const std::vector<Plan>& plans, const 
     }
     size_t need = 0;
     chunk.assign(jobs.size(), 0);
-    for (size_t i = 0; i < jobs.size(); ++i) {
-        if (plans[i].per_box > limit) return HPS_ENOMEM;
-        chunk[i] = (int)std::min<size_t>((size_t)jobs[i].nbox, limit / plans[i].per_box);
-        need = std::max(need, plans[i].per_box * (size_t)chunk[i]);
+    ctx->ws_off.assign(jobs.size(), 0);
+    // Concurrent layout (several groups): every job whole, in its own slice,
+    // when all of them fit at once; else one slice reused job after job.
+    if (ctx->concurrent && jobs.size() > 1) {
+        size_t sum = 0;
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            ctx->ws_off[i] = sum;
+            sum += align_up(plans[i].per_box * (size_t)jobs[i].nbox, 256);
+        }
+        if (sum <= limit) {
+            for (size_t i = 0; i < jobs.size(); ++i) chunk[i] = jobs[i].nbox;
+            need = sum;
+        } else {
+            ctx->ws_off.assign(jobs.size(), 0);
+        }
+    }
+    if (need == 0)
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            if (plans[i].per_box > limit) return HPS_ENOMEM;
+            chunk[i] = (int)std::min<size_t>((size_t)jobs[i].nbox, limit / plans[i].per_box);
+            need = std::max(need, plans[i].per_box * (size_t)chunk[i]);
+        }
+    // streams and events of a concurrent call (created before any capture)
+    const bool conc = jobs.size() > 1 && ctx->ws_off.back() > 0;
+    if (conc) {
+        if (!ctx->side_fork) HPS_CUDA_TRY(cudaEventCreateWithFlags(&ctx->side_fork, cudaEventDisableTiming));
+        while (ctx->side.size() < jobs.size()) {
+            cudaStream_t sst = nullptr;
+            cudaEvent_t ev = nullptr;
+            HPS_CUDA_TRY(cudaStreamCreateWithFlags(&sst, cudaStreamNonBlocking));
+            ctx->side.push_back(sst);
+            HPS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            ctx->side_done.push_back(ev);
+        }
     }
     if (need > ctx->ws_bytes) {
         if (ctx->ws) {
@@ -564,14 +599,14 @@ hps_status refine_chunk(hps_ctx* ctx, const Geometry& g, const CallSpec& cs, con
 // Everything a job enqueues: per chunk, the solve and the products that turn
 // the solution X into the requested outputs (T, S, v, h, u_i).
 template <typename T>
-hps_status enqueue_job(hps_ctx* ctx, const Job& j, const Plan& P, int chunk, cudaStream_t st)
+hps_status enqueue_job(hps_ctx* ctx, const Job& j, const Plan& P, int chunk, cudaStream_t st, void* ws)
 {
     const Geometry& g = *j.g;
     const int n = g.n, m = g.m, r = job_cols(j);
     const long long p3 = (long long)g.p * g.p * g.p, s_rhs = job_srhs(j);
     for (int b0 = 0; b0 < j.nbox; b0 += chunk) {
         const int nc = std::min(chunk, j.nbox - b0);
-        Work<T> w = carve<T>(P, ctx->ws, nc);
+        Work<T> w = carve<T>(P, ws, nc);
         CallSpec cs;
         cs.rhs_kind = j.rhs_kind;
         cs.r = r;
@@ -619,10 +654,22 @@ hps_status enqueue_all(hps_ctx* ctx, const std::vector<Job>& jobs, const std::ve
     HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int) * total, st));
     HPS_CUDA_TRY(cudaMemsetAsync(ctx->d_relcorr, 0, sizeof(double) * total, st));
     for (const Job& j : jobs) HPS_CUDA_TRY(cudaMemsetAsync(j.status, 0, sizeof(int) * j.nbox, st));
+    // Groups of a mixed batch run concurrently, each on its own stream and
+    // workspace slice (ensure_workspace chose the layout), joined back to st.
+    const bool conc = jobs.size() > 1 && ctx->ws_off.size() == jobs.size() && ctx->ws_off.back() > 0 &&
+                      ctx->side.size() >= jobs.size();
+    if (conc) HPS_CUDA_TRY(cudaEventRecord(ctx->side_fork, st));
     for (size_t i = 0; i < jobs.size(); ++i) {
-        hps_status rc = prec == HPS_FP64 ? enqueue_job<double>(ctx, jobs[i], plans[i], chunk[i], st)
-                                         : enqueue_job<float>(ctx, jobs[i], plans[i], chunk[i], st);
+        cudaStream_t js = conc ? ctx->side[i] : st;
+        void* ws = static_cast<char*>(ctx->ws) + (conc ? ctx->ws_off[i] : 0);
+        if (conc) HPS_CUDA_TRY(cudaStreamWaitEvent(js, ctx->side_fork, 0));
+        hps_status rc = prec == HPS_FP64 ? enqueue_job<double>(ctx, jobs[i], plans[i], chunk[i], js, ws)
+                                         : enqueue_job<float>(ctx, jobs[i], plans[i], chunk[i], js, ws);
         if (rc != HPS_OK) return rc;
+        if (conc) {
+            HPS_CUDA_TRY(cudaEventRecord(ctx->side_done[i], js));
+            HPS_CUDA_TRY(cudaStreamWaitEvent(st, ctx->side_done[i], 0));
+        }
     }
     return HPS_OK;
 }
@@ -746,7 +793,7 @@ hps_status run_jobs(hps_ctx* ctx, std::vector<Job>& jobs, hps_precision prec, cu
     const bool use_graph = ctx->graphs && !ctx->prof_on && !tc_test_stall_armed();
     if (!use_graph) return enqueue_all(ctx, jobs, plans, chunk, prec, total, st);
     std::ostringstream key;
-    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->lu_unit << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->fp16_ops << ' ' << ctx->ws << ' '
+    key << (int)prec << ' ' << ctx->ir_iters << ' ' << ctx->ir_tol << ' ' << ctx->use_tc << ' ' << ctx->tc_epi_cp << ' ' << ctx->lu_unit << ' ' << ctx->tc_fuse << ' ' << ctx->res_df << ' ' << ctx->fp16_ops << ' ' << ctx->concurrent << ' ' << ctx->ws << ' '
         << ctx->d_iters << ' ' << ctx->d_relcorr;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const Job& j = jobs[i];
@@ -1085,6 +1132,9 @@ void hps_destroy(hps_ctx* ctx)
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& kv : ctx->a0inv) cudaFree(kv.second);
     if (ctx->gate_buf) cudaFree(ctx->gate_buf);
+    for (cudaStream_t sst : ctx->side) cudaStreamDestroy(sst);
+    for (cudaEvent_t ev : ctx->side_done) cudaEventDestroy(ev);
+    if (ctx->side_fork) cudaEventDestroy(ctx->side_fork);
     for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     delete ctx;
 }
@@ -1136,6 +1186,10 @@ hps_status hps_set_option(hps_ctx* ctx, int option, double value)
     case HPS_OPT_FP16_OPERANDS:
         if (!(value == 0 || value == 1)) return HPS_EINVAL;
         ctx->fp16_ops = (int)value;
+        return HPS_OK;
+    case HPS_OPT_GROUPS_CONCURRENT:
+        if (!(value == 0 || value == 1)) return HPS_EINVAL;
+        ctx->concurrent = (int)value;
         return HPS_OK;
     case HPS_OPT_TEST_SINGULAR_BOX:
         ctx->zero_row_box = (int)value;
