@@ -484,7 +484,8 @@ hps_status hps_interface2d_plan(int p, const int nb[2], int* n_merge, int* n_lis
  * nrhs = 0); f, v, h are required when nrhs > 0.  h[2] > 0 are the box
  * sides, p in 3..24.  box_status (device [nbox] or NULL) as for the 3-D
  * calls.  Workspace comes from the stream-ordered allocator
- * (cudaMallocAsync) and is released on the stream.  HPS_EINVAL for bad
+ * (cudaMallocAsync) and is released on the stream; the differentiation
+ * tables travel as kernel parameters, so the call makes no host copy.  HPS_EINVAL for bad
  * arguments, HPS_ENOMEM when the workspace cannot be allocated.
  *
  * hps_leaf2d_reconstruct: u_i = v + S u_b (Sec. 2.2 step 4) with S from
@@ -527,6 +528,9 @@ hps_status hps_leaf2d_reconstruct(int p, int nbox, int nrhs, const double* S, co
  * be NULL (not both when nrhs = 0).  box_status as for the other leaf calls.
  * Workspace from the stream-ordered allocator, released on the stream;
  * HPS_EINVAL for bad arguments, HPS_ENOMEM when it cannot be allocated.
+ * The interpolation tables (T_E alone is m x m doubles) are built on the
+ * host and copied from pageable memory: the copy is staged before the call
+ * returns, and the call cannot be captured into a CUDA graph.
  * hps_leaf_cross_reconstruct: u_i = v + S u_b with S from hps_leaf_cross_solve
  * (v may be NULL), u_b [nbox][nrhs][m] on the Legendre grids. */
 hps_status hps_leaf_cross_sizes(int p, int* n, int* m);
@@ -593,7 +597,9 @@ hps_status hps_mixed_traces(const int nb[3], const int* p_box, const double* u, 
  * node, face order as for T.  box_status: device [nbox] or NULL, as for the
  * other leaf calls.  Workspace from the stream-ordered allocator
  * (2 (n + m) x (2 (n + m) + m) doubles per box), released on the stream;
- * HPS_EINVAL for bad arguments, HPS_ENOMEM when it cannot be allocated. */
+ * the differentiation tables are formed on the device, so the call makes no
+ * host copy.  HPS_EINVAL for bad arguments, HPS_ENOMEM when it cannot be
+ * allocated. */
 hps_status hps_leaf_iti(const hps_leaf_kind* kind, double eta, int nbox, const double* b, double* R, int* box_status,
                         void* stream);
 

@@ -22,7 +22,6 @@
 // Im R = -2 eta x_r,b.
 #include <algorithm>
 #include <cmath>
-#include <vector>
 
 #include "hps_internal.h"
 
@@ -30,6 +29,20 @@ namespace {
 
 constexpr int kItiMaxP = 16;
 constexpr int kItiRows = 4;   // rows per CTA of the build
+
+// The reference Chebyshev matrix and the box size by value: the D and D2
+// tables are formed on the device (the helper of the context path), so the
+// call makes no host-to-device copy and stays stream-ordered.
+struct ItiTables {
+    int p;
+    double h[3];
+    double Dhat[kItiMaxP * kItiMaxP];
+};
+
+__global__ void k_iti_tables(const ItiTables a, double* D, double* D2)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) hps::geometry_tables(a.p, a.Dhat, a.h, D, D2);
+}
 
 // Writes rows [r0, r0 + kItiRows) of box blockIdx.y's augmented real system
 // [K | F] (2N x (2N + m), row pitch ldm).  Row layout of each half: the n
@@ -244,11 +257,12 @@ hps_status hps_leaf_iti_solve(const hps_leaf_kind* kind, double eta, int nbox, c
     if (!b || (!R && !S && nrhs == 0) || (nrhs > 0 && (!f || (!v && !hout)))) return HPS_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int p = kind->p, q = p - 2, n = q * q * q, m = 6 * q * q, N2 = 2 * (n + m), pp = p * p;
-    std::vector<double> Dhat(pp), tab(6 * pp);
-    hps::cheb_diff(p, Dhat.data());
-    hps::geometry_tables(p, Dhat.data(), kind->h, tab.data(), tab.data() + 3 * pp);
+    ItiTables ta;
+    ta.p = p;
+    for (int a = 0; a < 3; ++a) ta.h[a] = kind->h[a];
+    hps::cheb_diff(p, ta.Dhat);
     hps::Plan PL = hps::make_plan(N2, m + nrhs, HPS_FP64, 0, false, false);
-    const size_t tab_bytes = hps::align_up(sizeof(double) * tab.size(), 256);
+    const size_t tab_bytes = hps::align_up(sizeof(double) * 6 * pp, 256);
     const size_t st_bytes = hps::align_up(sizeof(int) * (size_t)nbox, 256);
     const size_t bytes = tab_bytes + st_bytes + PL.per_box * (size_t)nbox;
     void* ws = nullptr;
@@ -258,10 +272,8 @@ hps_status hps_leaf_iti_solve(const hps_leaf_kind* kind, double eta, int nbox, c
     int* status = box_status ? box_status : reinterpret_cast<int*>(base + tab_bytes);
     hps::Work<double> w = hps::carve<double>(PL, base + tab_bytes + st_bytes, nbox);
     hps_status rc = HPS_OK;
-    // pageable source: the copy is staged before the call returns
-    if (cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(status, 0, sizeof(int) * (size_t)nbox, st) != cudaSuccess)
-        rc = HPS_ECUDA;
+    k_iti_tables<<<1, 1, 0, st>>>(ta, dtab, dtab + 3 * pp);
+    if (cudaMemsetAsync(status, 0, sizeof(int) * (size_t)nbox, st) != cudaSuccess) rc = HPS_ECUDA;
     if (rc == HPS_OK) {
         k_build_iti<<<dim3((unsigned)((N2 + kItiRows - 1) / kItiRows), (unsigned)nbox), 256, 0, st>>>(
             p, n, m, dtab, dtab + 3 * pp, kind->kappa * kind->kappa, eta, b, nrhs, f, w.M, PL.ldm, w.sM, status);

@@ -18,6 +18,19 @@
 
 namespace {
 
+// The per-axis D and D^2 tables by value: one small kernel writes them to the
+// workspace, so the call makes no host-to-device copy and stays
+// stream-ordered (kernel parameters are captured at launch).
+struct Tables2d {
+    double t[4 * hps::kMaxP * hps::kMaxP];
+};
+static_assert(sizeof(Tables2d) <= 32000, "kernel parameter space");
+
+__global__ void k_tables2d(const Tables2d a, int count, double* __restrict__ out)
+{
+    for (int k = threadIdx.x; k < count; k += blockDim.x) out[k] = a.t[k];
+}
+
 // M = [A_ii | -A_ib | f_i] of each box (row r = interior node (i, j)).
 //   A_ii(r, c) = -D2x[i][i'] [j' = j] - D2y[j][j'] [i' = i] - kappa^2 b(i, j) [c = r]
 //   A_ib(r, e) for edge node e at grid (gi, gj): the same two terms.
@@ -118,11 +131,13 @@ hps_status hps_leaf2d_solve(int p, const double h[2], double kappa, int nbox, co
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int q = p - 2, n = q * q, m = 4 * q;
     // physical D and D^2 per axis, [2][p][p]
-    std::vector<double> Dhat((size_t)p * p), tab((size_t)4 * p * p);
+    std::vector<double> Dhat((size_t)p * p);
+    Tables2d tab;
+    const int ntab = 4 * p * p;
     hps::cheb_diff(p, Dhat.data());
     for (int a = 0; a < 2; ++a) {
-        double* Da = tab.data() + (size_t)a * p * p;
-        double* D2a = tab.data() + (size_t)(2 + a) * p * p;
+        double* Da = tab.t + (size_t)a * p * p;
+        double* D2a = tab.t + (size_t)(2 + a) * p * p;
         const double s = 2.0 / h[a];
         for (int k = 0; k < p * p; ++k) Da[k] = s * Dhat[k];
         for (int i = 0; i < p; ++i)
@@ -133,7 +148,7 @@ hps_status hps_leaf2d_solve(int p, const double h[2], double kappa, int nbox, co
             }
     }
     hps::Plan PL = hps::make_plan(n, m + nrhs, HPS_FP64, 0, false, false);
-    const size_t tab_bytes = hps::align_up(sizeof(double) * tab.size(), 256);
+    const size_t tab_bytes = hps::align_up(sizeof(double) * (size_t)ntab, 256);
     const size_t st_bytes = hps::align_up(sizeof(int) * (size_t)nbox, 256);
     const size_t bytes = tab_bytes + st_bytes + PL.per_box * (size_t)nbox;
     void* ws = nullptr;
@@ -143,9 +158,8 @@ hps_status hps_leaf2d_solve(int p, const double h[2], double kappa, int nbox, co
     int* status = box_status ? box_status : reinterpret_cast<int*>(base + tab_bytes);
     hps::Work<double> w = hps::carve<double>(PL, base + tab_bytes + st_bytes, nbox);
     hps_status rc = HPS_OK;
-    if (cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(status, 0, sizeof(int) * (size_t)nbox, st) != cudaSuccess)
-        rc = HPS_ECUDA;
+    k_tables2d<<<1, 256, 0, st>>>(tab, ntab, dtab);
+    if (cudaMemsetAsync(status, 0, sizeof(int) * (size_t)nbox, st) != cudaSuccess) rc = HPS_ECUDA;
     if (rc == HPS_OK) {
         const double* dD = dtab;
         const double* dD2 = dtab + 2 * p * p;
