@@ -1010,6 +1010,125 @@ __global__ void k_pack_f16(const float* __restrict__ src, long long lds, long lo
         split_store<2>(db, (long long)r * NB + c, total, c < nb ? sb[(long long)r * lds + c] * sc : 0.0f);
 }
 
+// The same pack reading src once: a cluster of kPackCl CTAs per 32-column
+// strip, each CTA holding a contiguous share of the rows in shared memory.
+// Each CTA forms its share's column maxima, the cluster exchanges them
+// through distributed shared memory, and every CTA scales and splits its
+// rows from shared memory.  The maxima are over the same entries as
+// k_pack_f16's, so the planes and rc are the same bit for bit.
+constexpr int kPackCl = 8;
+
+__global__ void __cluster_dims__(kPackCl, 1, 1) __launch_bounds__(256)
+k_pack_f16_cl(const float* __restrict__ src, long long lds, long long sS, int rows, int NB, int nb,
+              __half* __restrict__ dst, long long sD, float* __restrict__ rc, long long sC, int chunk)
+{
+    extern __shared__ float4 tile[];   // [chunk][8] float4: this CTA's rows of the strip
+    __shared__ float red[32][33];
+    __shared__ float part[32];         // this CTA's column maxima (read by the cluster)
+    __shared__ float scl[32];
+    unsigned rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const int box = blockIdx.y, strip = blockIdx.x / kPackCl;
+    const int tid = threadIdx.x, tq = tid & 7, tr = tid >> 3;   // 4 columns 4 tq.., rows tr, tr + 32, ..
+    const int c0 = strip * 32, cq = c0 + 4 * tq;
+    const int r0 = (int)rank * chunk, r1 = min(rows, r0 + chunk);
+    const float* sb = src + box * sS;
+    const bool vec = cq + 4 <= nb && ((reinterpret_cast<uintptr_t>(sb + cq) & 15) == 0) && (lds & 3) == 0;
+    float mx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    constexpr int U = 4;   // rows per thread in flight
+    for (int rb = r0 + tr; rb < r1; rb += 32 * U) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = rb + 32 * u;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < r1) {
+                const float* rp = sb + (long long)r * lds + cq;
+                if (vec) v[u] = __ldg(reinterpret_cast<const float4*>(rp));
+                else {
+                    if (cq + 0 < nb) v[u].x = rp[0];
+                    if (cq + 1 < nb) v[u].y = rp[1];
+                    if (cq + 2 < nb) v[u].z = rp[2];
+                    if (cq + 3 < nb) v[u].w = rp[3];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = rb + 32 * u;
+            if (r < r1) {
+                tile[(r - r0) * 8 + tq] = v[u];
+                mx[0] = fmaxf(mx[0], fabsf(v[u].x));
+                mx[1] = fmaxf(mx[1], fabsf(v[u].y));
+                mx[2] = fmaxf(mx[2], fabsf(v[u].z));
+                mx[3] = fmaxf(mx[3], fabsf(v[u].w));
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[tr][4 * tq + u] = mx[u];
+    __syncthreads();
+    if (tid < 32) {
+        float m = red[0][tid];
+        for (int i = 1; i < 32; ++i) m = fmaxf(m, red[i][tid]);
+        part[tid] = m;
+    }
+    // every CTA's maxima written and visible to the cluster
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (tid < 32) {
+        const unsigned local = (unsigned)__cvta_generic_to_shared(&part[tid]);
+        float m = 0.0f;
+        for (unsigned q = 0; q < (unsigned)kPackCl; ++q) {
+            unsigned remote;
+            float v;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(q));
+            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+            m = fmaxf(m, v);
+        }
+        const int e = scale_exp(m);
+        scl[tid] = pow2f(e);
+        if (rank == 0 && c0 + tid < NB) rc[box * sC + c0 + tid] = pow2f(-e);
+    }
+    // the peers' maxima are read: a CTA may leave once every CTA has arrived
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+    if (cq < NB) {
+        const float s0 = scl[4 * tq], s1 = scl[4 * tq + 1], s2 = scl[4 * tq + 2], s3 = scl[4 * tq + 3];
+        const long long total = (long long)rows * NB;
+        __half* db = dst + box * sD;
+        const bool vst = cq + 4 <= NB && (NB & 3) == 0 && (sD & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(dst) & 7) == 0);
+        for (int r = r0 + tr; r < r1; r += 32) {
+            const float4 v = tile[(r - r0) * 8 + tq];
+            const float x[4] = {v.x * s0, v.y * s1, v.z * s2, v.w * s3};
+            __half hi[4], lo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                hi[u] = __float2half_rn(x[u]);
+                lo[u] = __float2half_rn(x[u] - __half2float(hi[u]));
+            }
+            const long long idx = (long long)r * NB + cq;
+            if (vst) {
+                uint2 ph, pl;
+                ph.x = (uint32_t)__half_as_ushort(hi[0]) | ((uint32_t)__half_as_ushort(hi[1]) << 16);
+                ph.y = (uint32_t)__half_as_ushort(hi[2]) | ((uint32_t)__half_as_ushort(hi[3]) << 16);
+                pl.x = (uint32_t)__half_as_ushort(lo[0]) | ((uint32_t)__half_as_ushort(lo[1]) << 16);
+                pl.y = (uint32_t)__half_as_ushort(lo[2]) | ((uint32_t)__half_as_ushort(lo[3]) << 16);
+                *reinterpret_cast<uint2*>(db + idx) = ph;
+                *reinterpret_cast<uint2*>(db + total + idx) = pl;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (cq + u < NB) {
+                        db[idx + u] = hi[u];
+                        db[total + idx + u] = lo[u];
+                    }
+            }
+        }
+    }
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Format 2 right operand: as k_gather_pack, with row i of the gathered block
 // multiplied by rc[i] (the left operand's K scale inverse) and then each
 // column c scaled by 2^t_c (scale_exp of its maximum); invt[c] = 2^-t_c for
@@ -1337,8 +1456,22 @@ void launch_pack_split(int fmt, const float* src, long long lds, long long sS, i
     const dim3 blk(32, 8);   // 8 rows of 32-column strips per CTA
     prof_begin(KC_PACK, st);
     if (fmt == 2) {
-        k_pack_f16<<<dim3((unsigned)((NB + 31) / 32), (unsigned)nbox), blk, 0, st>>>(
-            src, lds, sS, rows, NB, nb, static_cast<__half*>(dst), sD, rc, sC);
+        // one read of src when a cluster's shares fit in shared memory
+        constexpr size_t kClSmemMax = 192 * 1024;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_pack_f16_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmemMax);
+            attr = true;
+        }
+        const int chunk = (rows + kPackCl - 1) / kPackCl;
+        const size_t smem = (size_t)chunk * 32 * sizeof(float);
+        if (smem <= kClSmemMax && chunk > 0) {
+            k_pack_f16_cl<<<dim3((unsigned)(((NB + 31) / 32) * kPackCl), (unsigned)nbox), 256, smem, st>>>(
+                src, lds, sS, rows, NB, nb, static_cast<__half*>(dst), sD, rc, sC, chunk);
+        } else {
+            k_pack_f16<<<dim3((unsigned)((NB + 31) / 32), (unsigned)nbox), blk, 0, st>>>(
+                src, lds, sS, rows, NB, nb, static_cast<__half*>(dst), sD, rc, sC);
+        }
         prof_end(KC_PACK, st, 0.0, (double)nbox * total * (4.0 + 4.0));
         return;
     }
