@@ -43,18 +43,23 @@ constexpr uint32_t A_TILE = TC_BM * ROWB;                   // 8 KiB per plane
 #ifndef HPS_TC_STAGES
 #define HPS_TC_STAGES 3
 #endif
+#ifndef HPS_TE_WARPS
+#define HPS_TE_WARPS 8
+#endif
 #ifndef HPS_TE_PRE
-#define HPS_TE_PRE 5
+#define HPS_TE_PRE 2
 #endif
 #ifndef HPS_TE_LA
-#define HPS_TE_LA 3
+#define HPS_TE_LA 1
 #endif
 #ifndef HPS_TC_PRE
 #define HPS_TC_PRE 3
 #endif
 constexpr int TC_STAGES = HPS_TC_STAGES;   // operand stages of the TMA -> MMA ring
-constexpr int TC_EPI_WARPS = 4;                             // one per TMEM lane quarter
-constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;          // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
+constexpr int TC_EPI_WARPS = 4;                             // cp.async epilogue: one per TMEM lane quarter
+constexpr int TE_WARPS = HPS_TE_WARPS;                      // TMA epilogue: 4 or 8 (two per lane quarter)
+static_assert(TE_WARPS == 4 || TE_WARPS == 8, "the TMA epilogue takes one or two warps per TMEM lane quarter");
+constexpr int TC_THREADS = 64 + 32 * TE_WARPS;              // warp 0 TMA, warp 1 MMA, warps 2.. epilogue
 
 // Operand formats of the update product.  FMT 0: each operand x = hi + lo with
 // hi = tf32(x), lo = tf32(x - hi) (2 planes of FP32 containers, kind::tf32,
@@ -110,7 +115,7 @@ constexpr int TE_LA = HPS_TE_LA;                           // chunks fetched ahe
 static_assert(TE_LA >= 1 && TE_LA < TE_PRE, "the epilogue ring needs a buffer beyond the fetched-ahead chunks");
 constexpr uint32_t TE_CHUNK = 32 * 32 * 4;                 // 4 KiB, 128-byte rows, 128B swizzle
 constexpr size_t EPI_BYTES_CP = (size_t)TC_EPI_WARPS * EPI_FLOATS * 4;
-constexpr size_t EPI_BYTES_TMA = (size_t)TC_EPI_WARPS * TE_PRE * TE_CHUNK;
+constexpr size_t EPI_BYTES_TMA = (size_t)TE_WARPS * TE_PRE * TE_CHUNK;
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE_BYTES + (EPI_BYTES_CP > EPI_BYTES_TMA ? EPI_BYTES_CP : EPI_BYTES_TMA) +
                            1024;
 static_assert(TC_SMEM <= 227 * 1024, "operand stages and epilogue buffers exceed a CTA's shared memory");
@@ -426,6 +431,11 @@ __device__ __forceinline__ void scale_chunk(uint32_t (&v)[32], float (&its8)[8])
 #pragma unroll
     for (int c8 = 0; c8 < 7; ++c8) its8[c8] = its8[c8 + 1];
 }
+__device__ __forceinline__ void shift_scales(float (&its8)[8])
+{
+#pragma unroll
+    for (int c8 = 0; c8 < 7; ++c8) its8[c8] = its8[c8 + 1];
+}
 __device__ __forceinline__ void load_tile_scales(float (&its8)[8], const float* ib, int nch, int lane)
 {
 #pragma unroll
@@ -454,7 +464,7 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
     constexpr uint32_t B_TILE = (uint32_t)BN * ROWB;
     constexpr uint32_t STAGE_TX = (uint32_t)NPL * (A_TILE + B_TILE);   // bytes a stage receives
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t ld_bar[TC_EPI_WARPS][TE_PRE];
+    __shared__ __align__(8) uint64_t ld_bar[TE_WARPS][TE_PRE];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2];
@@ -482,9 +492,9 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull_bar[b]), 1);
-            mbar_init(smem_u32(&tempty_bar[b]), TC_EPI_WARPS);
+            mbar_init(smem_u32(&tempty_bar[b]), a.tma_epi ? TE_WARPS : TC_EPI_WARPS);
         }
-        for (int w = 0; w < TC_EPI_WARPS; ++w)
+        for (int w = 0; w < TE_WARPS; ++w)
             for (int q = 0; q < TE_PRE; ++q) mbar_init(smem_u32(&ld_bar[w][q]), 1);
         mbar_init(smem_u32(&mdrain_bar), 1);
         fail_sh = 0;
@@ -606,8 +616,11 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
             }
         }
     } else if (a.tma_epi) {
-        // Epilogue warps 2..5, TMA form: warp w owns TMEM lane quarter qd = w % 4
-        // (tile rows 32 qd .. +31) and a ring of TE_PRE 32 x 32 buffers.  Lane 0
+        // Epilogue warps 2.., TMA form: warp w owns TMEM lane quarter qd = w % 4
+        // (tile rows 32 qd .. +31) and a ring of TE_PRE 32 x 32 buffers; with
+        // eight warps two share a quarter and take alternate 32-column chunks
+        // of each tile (warp w the chunks h, h + 2, .. with h = (w - 2) / 4),
+        // so that two chains of TMEM loads, staging and stores overlap.  Lane 0
         // fetches each chunk's source rows from O by TMA TE_LA chunks ahead
         // (across tiles; rows and columns past O's edge arrive as zeros); each
         // lane then owns one row: it reads the accumulator row from TMEM,
@@ -618,6 +631,8 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
         // in FWD, below the split in BWD) or a saved row W (FWD rows whose
         // pivot source lies above the split) ignore the staged row.
         const int qd = warp & 3, ew = warp - 2;
+        constexpr int CST = TE_WARPS / 4;   // chunk stride of a warp within a tile
+        const int h = ew / 4;               // its first chunk
         const uint32_t ring = sbase + TC_STAGES * STAGE_BYTES + (uint32_t)ew * (TE_PRE * TE_CHUNK);
         unsigned char* ring_p = sbase_ptr + TC_STAGES * STAGE_BYTES + (size_t)ew * (TE_PRE * TE_CHUNK);
         const uint32_t lbar0 = smem_u32(&ld_bar[ew][0]);
@@ -629,8 +644,18 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
             nch = (min(BN, a.N - n0) + 31) / 32;
         };
         // load cursor (lane 0): next chunk to fetch is number lg, chunk lcc of unit lt
-        int lt = first_from(sc.u0), lcc = 0;
+        int lt = first_from(sc.u0), lcc = h;
         uint32_t lg = 0;
+        auto settle = [&]() {   // past the tiles that hold no chunk of this warp
+            while (lt < sc.units) {
+                int box, m0, n0, nch;
+                geom(lt, box, m0, n0, nch);
+                if (lcc < nch) return;
+                lt = first_from(lt + sc.ustep);
+                lcc = h;
+            }
+        };
+        settle();
         auto issue = [&]() {
             int box, m0, n0, nch;
             geom(lt, box, m0, n0, nch);
@@ -638,10 +663,8 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
             mbar_expect_tx(lbar0 + 8 * buf, TE_CHUNK);
             tma_load_3d(ring + buf * TE_CHUNK, &tmO, lbar0 + 8 * buf, n0 + 32 * lcc, m0 + 32 * qd, box);
             ++lg;
-            if (++lcc == nch) {
-                lcc = 0;
-                lt = first_from(lt + sc.ustep);
-            }
+            lcc += CST;
+            settle();
         };
         if (lane == 0 && need_src)
             for (int i = 0; i < TE_LA && lt < sc.units; ++i) issue();
@@ -652,11 +675,20 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
             geom(t, box, m0, n0, nch);
             const int b = j & 1;
             float its8[8];   // format 2 column scales (the loads overlap the wait)
-            if constexpr (FMT == 2) load_tile_scales(its8, a.invt + box * a.sInvt + n0, nch, lane);
+            if constexpr (FMT == 2) {
+                load_tile_scales(its8, a.invt + box * a.sInvt + n0, nch, lane);
+                if (h) shift_scales(its8);
+            }
             if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[b]), (j >> 1) & 1, a.wait_ns);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
+            if (h >= nch) {   // no chunk of this tile for this warp: hand the buffer back at once
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[b]));
+                continue;
+            }
             // this lane's row: source 0 = zero, 1 = staged O row, 2 = saved row of W
             const int myr = m0 + qd * 32 + lane;
             int ngi = -1, nwr = -1;   // the row's K index in the next product's G, its row in the next W
@@ -688,7 +720,7 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
                     srck = 1;
                 }
             }
-            for (int cc = 0; cc < nch; ++cc, ++g) {
+            for (int cc = h; cc < nch; cc += CST, ++g) {
                 const uint32_t buf = g % TE_PRE;
                 if (lane == 0) {
                     if (need_src) {
@@ -703,7 +735,7 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
                 __syncwarp();
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * BN + cc * 32), v);
-                if (cc == nch - 1) {
+                if (cc + CST >= nch) {
                     // the accumulator is in registers: hand the TMEM buffer back
                     tc_fence_before();
                     __syncwarp();
@@ -716,7 +748,10 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
                 }
                 float4* rowp = reinterpret_cast<float4*>(ring_p + buf * TE_CHUNK + lane * 128);
                 const int cb = n0 + cc * 32;
-                if constexpr (FMT == 2) scale_chunk(v, its8);
+                if constexpr (FMT == 2) {
+                    scale_chunk(v, its8);
+                    if (CST == 2) shift_scales(its8);
+                }
                 // all eight source reads first, then the eight results
                 float4 sv[8];
 #pragma unroll
@@ -765,7 +800,7 @@ k_tc_update(const __grid_constant__ TcMaps tm, TcArgs a)
             bulk_wait_all();
         }
         __syncwarp();
-    } else {
+    } else if (warp < 2 + TC_EPI_WARPS) {
         // Epilogue warps 2..5: warp w owns TMEM lane quarter qd = w % 4 (tile
         // rows 32 qd .. 32 qd + 31).  The source rows of each 32 x 32 chunk are
         // brought into shared memory with cp.async TC_PRE chunks ahead (absent
