@@ -27,6 +27,12 @@
  * Face rows of T and h take the OUTWARD normal derivative of each box (the
  * flux-continuity rows of Eq. 4 sum the two boxes' outward derivatives).
  *
+ * "Device memory" means any address the GPU can dereference: an output such
+ * as T may also be pinned (page-locked, mapped) host memory, which the
+ * kernels then write across the host link (T is written once, by the D_n
+ * products at the end of the call), so no separate download is needed.
+ * Inputs are read several times and belong in device memory proper.
+ *
  * Ownership: the caller owns every input and output buffer.  The context owns
  * its workspace (device memory it allocates on first use, up to the limit given
  * to hps_create) and small per-(p, h) operator tables.

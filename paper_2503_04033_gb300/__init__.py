@@ -209,7 +209,8 @@ def _need(x, count: int, what: str) -> None:
 
 
 def _ptr(x, dtype=None):
-    """Device address of a tensor (checked), an int, or None."""
+    """Device address of a tensor (checked), an int, or None.  A pinned host
+    tensor passes too: its address is device-accessible (mapped)."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -217,8 +218,8 @@ def _ptr(x, dtype=None):
     import torch
     if not isinstance(x, torch.Tensor):
         raise TypeError(f"expected a torch tensor, int or None, got {type(x)}")
-    if not x.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+    if not x.is_cuda and not x.is_pinned():
+        raise ValueError("expected a CUDA tensor or a pinned host tensor")
     if not x.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     if dtype is not None and x.dtype != dtype:

@@ -370,6 +370,28 @@ def test_chunked_workspace_matches(ctx):
     np.testing.assert_array_equal(T_all, T_ch)
 
 
+@pytest.mark.parametrize("prec", [H.HPS_FP64, H.HPS_FP32_IR], ids=["fp64", "fp32ir"])
+def test_dtn_into_pinned_host_memory(ctx, prec):
+    """T written by the call straight into pinned host memory (the kernels
+    store across the host link) equals T written to device memory, bit for
+    bit, and matches the oracle."""
+    import torch
+    p, h, kappa = 12, np.array([0.125] * 3), 30.0
+    lows = _lows(5, h, 12)
+    b = box_b(H.hps_leaf_nodes, p, lows, h, hi.fourier_b_field().b)
+    T_dev, _, _ = gpu_dtn(ctx, p, h, kappa, b, prec, 2 if prec != H.HPS_FP64 else 0, want_S=False)
+    n, m = H.hps_leaf_sizes(p)
+    T_host = torch.full((len(lows), m, m), float("nan"), dtype=torch.float64).pin_memory()
+    st = torch.full((len(lows),), -1, dtype=torch.int32, device="cuda")
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    H.hps_leaf_build_dtn(ctx, H.LeafKind(p, h, kappa), len(lows), bt, T_host, None, prec, st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    np.testing.assert_array_equal(T_host.numpy(), T_dev)
+    To, _, info = oracle.leaf_dtn(p, h, kappa, b[0], want_S=False)
+    assert info == 0 and max_rel(T_host.numpy()[:1], To[None]) < 1e-10
+
+
 def test_end_to_end_manufactured(ctx):
     """Config of the manufactured solution: the GPU's T, v, h feed the library's
     interface assembly and a host sparse LU; the GPU reconstructs u_i.  Matches
