@@ -78,7 +78,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12
 # traffic grows with the boxes).  None when not captured for the current
 # kernel: every change to the product kernel resets it to None until it is
 # captured again.
-NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): 2.2476e9, ("update_tcgen05", "3 x TF32"): None}
+NCU_TRAFFIC_PER_LAUNCH = {("update_tcgen05", "scaled 2 x FP16"): 2.2486e9, ("update_tcgen05", "3 x TF32"): None}
 
 
 def dtype_label(prec, opts):
