@@ -1205,8 +1205,19 @@ __device__ __forceinline__ void eo_line_f32(const float* __restrict__ src, int s
 // lo rounds at 2^-48 of x): A_ii hi in double-float as above, A_ii lo in FP32
 // (eo_line_f32, added to the pairs' low parts), R written to X0R (which is
 // then output only).  Otherwise X0R holds X0 and receives R.
+// CTAs per SM the double-float residual is built for up to q = 16: shared
+// memory (the column, its low parts and the accumulator) and registers (72 a
+// thread) both allow four at q = 14; larger q keep the FP64 kernel's bound
+// (a tighter one spills there).
+template <int Q>
+__host__ __device__ constexpr int res_df_min_blocks()
+{
+    return Q > 16 ? res_min_blocks<Q>()
+                  : (65536 / (res_threads<Q>() * 72) > 1 ? 65536 / (res_threads<Q>() * 72) : 1);
+}
+
 template <int Q, bool X64>
-__global__ void __launch_bounds__(res_threads<Q>(), res_min_blocks<Q>())
+__global__ void __launch_bounds__(res_threads<Q>(), res_df_min_blocks<Q>())
 k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restrict__ kbs, int rhs_kind,
               const double* __restrict__ rhs, long long s_rhs, float* X0R, long long ld, long long sbx,
               const int* skip, const double* __restrict__ Xin, long long ldx, long long sX64)
@@ -1219,25 +1230,48 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
     const int cw = blockIdx.x;
     float4* tab = reinterpret_cast<float4*>(smem_raw);       // [3][TF]
     float2* Ac = reinterpret_cast<float2*>(tab + 3 * TF);   // [n]
-    float2* Ks = Ac + n;                                     // [n] kappa^2 b
-    float* Xs = reinterpret_cast<float*>(Ks + n);           // [n]
+    float* Xs = reinterpret_cast<float*>(Ac + n);           // [n]
     float* Xl = Xs + n;                                      // [n] low parts (X64 only)
     float* col = X0R + box * sbx + cw;
-    const float2* kbb = kbs + (long long)box * n;
+    const float2* kbb = kbs + (long long)box * n;            // kappa^2 b (hi, lo), read where used
+    // The column (one entry per row, rows ld apart): every load of a thread
+    // issued before its stores, so one memory latency covers the column.
     if constexpr (X64) {
         const double* xc = Xin + box * sX64 + cw;
-#pragma unroll 4
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            const double x = xc[(long long)r * ldx];
-            const float hi = d2f_rn(x);
-            Xs[r] = hi;
-            Xl[r] = d2f_rn(x - f2d(hi));
+        constexpr int LU = 8;
+        for (int r0 = threadIdx.x; r0 < n; r0 += LU * blockDim.x) {
+            double v[LU];
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                const int r = r0 + u * blockDim.x;
+                v[u] = r < n ? xc[(long long)r * ldx] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                const int r = r0 + u * blockDim.x;
+                if (r < n) {
+                    const float hi = d2f_rn(v[u]);
+                    Xs[r] = hi;
+                    Xl[r] = d2f_rn(v[u] - f2d(hi));
+                }
+            }
         }
     } else {
-#pragma unroll 4
-        for (int r = threadIdx.x; r < n; r += blockDim.x) Xs[r] = col[(long long)r * ld];
+        constexpr int LU = 16;
+        for (int r0 = threadIdx.x; r0 < n; r0 += LU * blockDim.x) {
+            float v[LU];
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                const int r = r0 + u * blockDim.x;
+                v[u] = r < n ? col[(long long)r * ld] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < LU; ++u) {
+                const int r = r0 + u * blockDim.x;
+                if (r < n) Xs[r] = v[u];
+            }
+        }
     }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) Ks[r] = kbb[r];
     for (int idx = threadIdx.x; idx < 3 * TF; idx += blockDim.x) tab[idx] = DF[idx];
     __syncthreads();
     const int ln = threadIdx.x;
@@ -1269,7 +1303,7 @@ k_residual_df(int p, int n, const float4* __restrict__ DF, const float2* __restr
             const int k = k0 + 1, r = ln + qq * k0;
             float2 a = Ac[r];
             df_add(a.x, a.y, h, l);
-            const float2 kk = Ks[r];
+            const float2 kk = __ldg(kbb + r);
             df_mac1(a.x, a.y, kk.x, kk.y, Xs[r]);
             if constexpr (X64) a.y = fmaf(kk.x, Xl[r], a.y);
             float out;
@@ -1794,7 +1828,7 @@ void residual_df_q(const Geometry& g, int nbox, int rhs_kind, int nrhs, const do
                    const double* X64, long long ldx, long long sX64)
 {
     const size_t smem = (size_t)3 * df_tab_q<Q>() * sizeof(float4) +
-                        (size_t)g.n * (2 * sizeof(float2) + (X64 ? 2 : 1) * sizeof(float));
+                        (size_t)g.n * (sizeof(float2) + (X64 ? 2 : 1) * sizeof(float));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_residual_df<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -1822,7 +1856,7 @@ void residual_df_q(const Geometry& g, int nbox, int rhs_kind, int nrhs, const do
 bool residual_df_fits(const Geometry& g, bool x64)
 {
     const size_t smem = (size_t)3 * df_tab_f4(g.q) * sizeof(float4) +
-                        (size_t)g.n * (2 * sizeof(float2) + (x64 ? 2 : 1) * sizeof(float));
+                        (size_t)g.n * (sizeof(float2) + (x64 ? 2 : 1) * sizeof(float));
     return smem <= 227 * 1024;
 }
 
