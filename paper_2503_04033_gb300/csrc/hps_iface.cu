@@ -549,7 +549,13 @@ hps_status factor_level(IfLevel& L, int qq, void** ws, size_t* ws_bytes, int** d
 {
     const int s = L.s_pad, e = L.e_pad;
     const hps_precision prec = sizeof(MT) == 8 ? HPS_FP64 : HPS_FP32_IR;
-    hps::Plan PL = hps::make_plan(s, e + s, prec, 0, false, false);
+    // FP32 factors: the leaf path's tensor-core LU with 3 x BF16 operands and
+    // FP32 accumulation (FP32's 24 bits: the interface systems are less well
+    // conditioned than the leaves, and the scaled 2 x FP16 form's 22 bits
+    // leave the refinement of some of them without contraction); the solve's
+    // FP64 refinement recovers the digits
+    const bool tc = sizeof(MT) == 4 && s >= 256;
+    hps::Plan PL = hps::make_plan(s, e + s, tc ? HPS_BF16_IR : prec, 0, tc, false);
     const size_t need = PL.per_box * (size_t)L.nn;
     if (need > *ws_bytes) {
         if (*ws) { cudaStreamSynchronize(st); cudaFree(*ws); *ws = nullptr; *ws_bytes = 0; }
@@ -568,8 +574,20 @@ hps_status factor_level(IfLevel& L, int qq, void** ws, size_t* ws_bytes, int** d
     if (e > 0)
         k_if_gather_et<MT><<<dim3((unsigned)e, (unsigned)L.nn), 256, 0, st>>>(
             L.d_desc, L.d_lists, qq, s, e, static_cast<MT*>(L.E), static_cast<MT*>(L.Tn));
-    hps::lu_factor<MT>(PL, w, L.nn, *d_status, st);
-    hps::lu_backward<MT>(PL, w, L.nn, s, e + s, nullptr, st);
+    bool tc_done = false;
+    if constexpr (sizeof(MT) == 4) {
+        if (PL.tc) {
+            hps::tc_reset_abort(st);
+            if (!hps::tc_lu_factor(PL, w, L.nn, *d_status, st) ||
+                !hps::tc_lu_backward(PL, w, L.nn, s, e + s, nullptr, st))
+                return HPS_ECUDA;
+            tc_done = true;
+        }
+    }
+    if (!tc_done) {
+        hps::lu_factor<MT>(PL, w, L.nn, *d_status, st);
+        hps::lu_backward<MT>(PL, w, L.nn, s, e + s, nullptr, st);
+    }
     k_if_extract<MT><<<dim3((unsigned)s, (unsigned)L.nn), 256, 0, st>>>(w.M, PL.ldm, w.sM, s, e,
                                                                          static_cast<MT*>(L.S),
                                                                          static_cast<MT*>(L.Winv));

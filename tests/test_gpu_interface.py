@@ -204,6 +204,35 @@ def test_interface_fp32_refinement_reaches_fp64_factors(ctx):
     assert out[H.HPS_FP32_IR][1][0] >= 1
 
 
+@pytest.mark.parametrize("p,nb", [(7, (4, 4, 3)), (6, (4, 4, 4)), (9, (3, 3, 2))])
+def test_interface_fp32_factors_on_large_separators(ctx, p, nb):
+    """Grids whose upper separators hold 256 and more unknowns (their FP32
+    factors come from the tensor-core LU): the FP32-factor solve refines to
+    the FP64-factor solve's answer."""
+    import torch
+    kappa = 7.0
+    grid = gs.InterfaceGrid(p, nb)
+    n, m = oracle.sizes(p)
+    b, f, g_dir = _problem(grid, 2, 11)
+    kind = H.LeafKind(p, grid.h, kappa)
+    T = torch.empty(grid.nbox, m, m, dtype=torch.float64, device="cuda")
+    H.hps_leaf_build_dtn(ctx, kind, grid.nbox, _dev(b), T, None, H.HPS_FP64)
+    hv = _dev(np.random.default_rng(7).standard_normal((grid.nbox, 2, m)))
+    g = _dev(_g_boxes(grid, g_dir, m, np.random.default_rng(8)))
+    out = {}
+    for iprec in (H.HPS_FP64, H.HPS_FP32_IR):
+        F = H.hps_interface_factor(ctx, p, grid.nb, T, 2, iprec)
+        try:
+            assert H.hps_interface_info(F)[2] >= 256
+            u = torch.empty(grid.nbox, 2, m, dtype=torch.float64, device="cuda")
+            H.hps_interface_solve(F, 2, hv, g, u)
+            torch.cuda.synchronize()
+            out[iprec] = u.cpu().numpy()
+        finally:
+            H.hps_interface_destroy(F)
+    assert np.abs(out[H.HPS_FP32_IR] - out[H.HPS_FP64]).max() < 1e-11 * np.abs(out[H.HPS_FP64]).max()
+
+
 def test_interface_nrhs_change_and_errors(ctx):
     """Solves with fewer loads than the handle was sized for give the same
     columns; out-of-range arguments are rejected."""
