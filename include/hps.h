@@ -412,8 +412,10 @@ void hps_leaf_factors_destroy(hps_leaf_factors* factors);
  * fastest, then y, then z), read during the call only (their columns on the
  * outer faces are copied for the Dirichlet term).  nrhs_max (1..256): the
  * largest nrhs of later solves.  precision: HPS_FP64 factors and stores every
- * W^{-1}, S and merged-map block in FP64; HPS_FP32_IR does so in FP32 (CUDA-
- * core FP32 LU and products) and keeps a copy of T in FP64, from which each
+ * W^{-1}, S and merged-map block in FP64; HPS_FP32_IR does so in FP32 (the
+ * tensor-core LU with 3 x BF16 operands and FP32 accumulation for separators
+ * of 256 and more unknowns, the CUDA-core FP32 LU below) and keeps a copy of
+ * T in FP64, from which each
  * solve refines its answer: with u the current face values, every box's flux
  * T^tau u^tau + h^tau sums, over the boxes sharing a node, to the residual of
  * the interface equations, and solving the system with those fluxes as loads
