@@ -470,3 +470,27 @@ def test_largest_orders_mixed_vs_fp64(ctx, p):
         assert max_rel(T, T64) < 1e-10
     torch.cuda.empty_cache()
 
+
+
+def test_every_order_fp32ir_matches_fp64_path(ctx):
+    """Every order p = 3..24 (one to 84 LU steps, last steps from 1 to 128
+    columns wide, every unit layout): the tensor-core FP32 + refinement T of
+    two boxes equals the FP64 path's T to 1e-11 of its largest entry."""
+    import torch
+    set_tc(ctx, 2)
+    H.hps_set_option(ctx, H.HPS_OPT_BLOCK, 0)
+    h = np.array([0.125] * 3)
+    for p in range(3, 25):
+        n, m = H.hps_leaf_sizes(p)
+        b = np.stack([1 + 0.3 * np.sin(2 * oracle.node_coords(p, np.array([0.1 * i, 0.0, 0.2]), h)[:, 0])
+                      for i in range(2)])
+        bt = _dev(b)
+        out = {}
+        for prec in (H.HPS_FP64, H.HPS_FP32_IR):
+            T = torch.empty(2, m, m, dtype=torch.float64, device="cuda")
+            st = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+            H.hps_leaf_build_dtn(ctx, H.LeafKind(p, h, 12.0), 2, bt, T, None, prec, st)
+            torch.cuda.synchronize()
+            assert (st.cpu().numpy() == 0).all(), (p, prec)
+            out[prec] = T.cpu().numpy()
+        assert max_rel(out[H.HPS_FP32_IR], out[H.HPS_FP64]) < 1e-11, p
