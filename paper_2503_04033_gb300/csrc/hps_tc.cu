@@ -423,18 +423,17 @@ __device__ __forceinline__ void split_store(void* dst, long long idx, long long 
 // scale.  Lane l holds the scales of columns l, l + 32, ... of the tile in
 // its8 (loaded once per tile); each chunk takes its8[0] by shuffles and
 // shifts the rest down.
+__device__ __forceinline__ void shift_scales(float (&its8)[8])
+{
+#pragma unroll
+    for (int c8 = 0; c8 < 7; ++c8) its8[c8] = its8[c8 + 1];
+}
 __device__ __forceinline__ void scale_chunk(uint32_t (&v)[32], float (&its8)[8])
 {
     const float sl = its8[0];
 #pragma unroll
     for (int c = 0; c < 32; ++c) v[c] = __float_as_uint(__uint_as_float(v[c]) * __shfl_sync(0xffffffffu, sl, c));
-#pragma unroll
-    for (int c8 = 0; c8 < 7; ++c8) its8[c8] = its8[c8 + 1];
-}
-__device__ __forceinline__ void shift_scales(float (&its8)[8])
-{
-#pragma unroll
-    for (int c8 = 0; c8 < 7; ++c8) its8[c8] = its8[c8 + 1];
+    shift_scales(its8);
 }
 __device__ __forceinline__ void load_tile_scales(float (&its8)[8], const float* ib, int nch, int lane)
 {
