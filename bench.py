@@ -12,7 +12,9 @@ flush is needed between steps.
 
 Also reported: the plain FP64 GPU path on a 32-box sample of the same
 workload (speedup and max relative difference), the end-to-end rate through
-the C ABI with host buffers (b in, T out, copies inside the timed region),
+the C ABI with host buffers (b uploaded from pinned memory and T written by
+the call into pinned host memory, both inside the timed region; the same
+with an explicit T download beside it),
 per-kernel-class CUDA-event timings with the roofline of the dominant class,
 and the FP64 CPU oracle's rate on a bounded sample of boxes.
 
